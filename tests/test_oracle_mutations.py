@@ -1,0 +1,92 @@
+"""The oracle's pins must be sharp: plant one plausible mistake at a time in a
+copy of the oracle source (on the CPU), rebuild it, and check that at least
+one pin fails.  Each mutant names the pins expected to catch it."""
+import os
+import subprocess
+import tempfile
+
+import numpy as np
+import pytest
+
+import oracle
+import tests.test_oracle_pins as pins
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "linprim_oracle.c")
+
+MUTANTS = {
+    "eq1_drop_099": ("-log1p(-0.99 * P->opacity[i])", "-log1p(-P->opacity[i])",
+                     ["thin_axis"]),
+    "eq1_drop_factor_2": ("/ (2.0 * pp->dmin);", "/ (pp->dmin);", ["thin_axis"]),
+    "stop_threshold": ("if (T < ORC_STOP_T) break;", "if (T < 1e-4) break;", ["early_stop"]),
+    "stop_exclusive": ("        T = Tn;\n        /* reading",
+                       "        if (Tn < ORC_STOP_T) break;\n        T = Tn;\n        /* reading",
+                       ["early_stop"]),
+    "blend_drop_T": ("C[ch] += T * o * pp->rgb[ch];", "C[ch] += o * pp->rgb[ch];", ["two_layer"]),
+    "order_back_to_front": ("if (zi != zj) return zi < zj ? -1 : 1;",
+                            "if (zi != zj) return zi > zj ? -1 : 1;", ["two_layer"]),
+    "mtia_swap_uv_depth": ("*depth = (1.0 - u - v) * p0[2] + u * p1[2] + v * p2[2];",
+                           "*depth = (1.0 - u - v) * p0[2] + v * p1[2] + u * p2[2];",
+                           ["linear_solve"]),
+    "mtia_grad_sign": ("dD[0][0] = p2[1] - p1[1];", "dD[0][0] = p1[1] - p2[1];", ["mtia_fd"]),
+    "jacobian_sign": ("J[0][2] = -cam->fx * t[0] / (tz * tz);",
+                      "J[0][2] = cam->fx * t[0] / (tz * tz);", ["first_order"]),
+    "jacobian_row2": ("J[2][0] = t[0] / len;", "J[2][0] = 0.0;", ["chord"]),
+    "sh_sign": ("Y[1] = -c1 * y;", "Y[1] = c1 * y;", ["scipy"]),
+    "sh_deriv": ("SETD(4, c2a * y, c2a * x, 0.0);", "SETD(4, c2a * x, c2a * y, 0.0);", ["sh_fd"]),
+    "chain_transpose_J": ("dtv[k][a] += pp->J[m][a] * gm;", "dtv[k][a] += pp->J[a][m] * gm;",
+                          ["fd_tetra"]),
+    "chain_drop_tau": ("pg->dsigma += dL_do * c->s * c->tau;", "pg->dsigma += dL_do * c->s;",
+                       ["fd_tetra"]),
+    "chain_dist_sh": ("dcentre[3 * i + a] += s / pp->dist;", "dcentre[3 * i + a] += s;",
+                      ["fd_octa"]),
+    "chain_B_recursion": ("B[ch] = c->o * pp->rgb[ch] + c->tau * B[ch];",
+                          "B[ch] = c->o * pp->rgb[ch] + B[ch];", ["fd_tetra"]),
+    "rect_round": ("fx0 = ceilf(xmin - 0.5f);", "fx0 = floorf(xmin - 0.5f);", ["keyfields"]),
+    "key_tie_order": ("return (x->seq > y->seq) - (x->seq < y->seq);",
+                      "return (x->seq < y->seq) - (x->seq > y->seq);", ["ties"]),
+    "render_tie_order": ("return (i > j) - (i < j);", "return (i < j) - (i > j);", ["ties"]),
+}
+
+CHECKS = {
+    "thin_axis": lambda o: [pins.test_thin_axis_opacity_is_099_alpha(o, a) for a in (0.5, 0.9)],
+    "early_stop": lambda o: [pins.test_early_stop_at_cumulative_opacity_0999(o, a) for a in (0.5, 0.8)],
+    "two_layer": pins.test_two_layer_compositing_and_background,
+    "linear_solve": pins.test_mtia_matches_linear_solve,
+    "mtia_fd": pins.test_mtia_gradient_fd,
+    "first_order": pins.test_ray_space_map_is_first_order_perspective,
+    "chord": lambda o: pins.test_span_centre_pixel_equals_world_chord(o, 6),
+    "scipy": pins.test_sh_basis_matches_scipy,
+    "sh_fd": pins.test_sh_basis_derivative_fd,
+    "fd_tetra": pins.test_adjoint_fd_tetrahedra,
+    "fd_octa": pins.test_adjoint_fd_octahedra_sh3,
+    "keyfields": pins.test_keyfields_are_binary32_replay,
+    "keys_structure": pins.test_keys_structure,
+    "ties": pins.test_depth_ties_keep_index_order,
+}
+
+
+@pytest.fixture(scope="module")
+def tmpdir_mut():
+    with tempfile.TemporaryDirectory() as d:
+        yield d
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_mutant_is_caught(name, tmpdir_mut, orc):
+    old, new, checks = MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation site for {name} not unique"
+    path_c = os.path.join(tmpdir_mut, f"{name}.c")
+    path_so = os.path.join(tmpdir_mut, f"{name}.so")
+    open(path_c, "w").write(src.replace(old, new))
+    subprocess.run(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-ffp-contract=off", path_c,
+                    "-o", path_so, "-lm"], check=True)
+    caught = False
+    with oracle.use_library(path_so):
+        for c in checks:
+            try:
+                CHECKS[c](oracle)
+            except AssertionError:
+                caught = True
+                break
+    assert caught, f"mutant {name} survived {checks}"
