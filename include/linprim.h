@@ -1,0 +1,207 @@
+/*
+ * linprim.h -- C ABI of the GB300 (sm_103a) LinPrim rasterizer.
+ *
+ * Differentiable tile rasterization of transparent, homogeneous octahedra and
+ * tetrahedra as defined in "LinPrim: Linear Primitives for Differentiable
+ * Volumetric Rendering" (arXiv 2501.16312):
+ *
+ *   render(primitives, cameras) -> images                 Sec. 3.2
+ *   render_backward(dL/dimage)  -> dL/d{centre, vertices, opacity, SH}
+ *                                                          Sec. 3.4, App.
+ *                                                          "Gradient Computation"
+ *
+ * Every step of both calls runs in hand-written CUDA kernels on the device
+ * the context was created for; there is no CPU path.
+ *
+ * Conventions shared by all calls
+ * -------------------------------
+ * - Pointers named "device" are CUDA device pointers owned by the caller; the
+ *   library never frees them.  "host" pointers are read (or written) before
+ *   the call returns.
+ * - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is
+ *   enqueued asynchronously on it; outputs are valid once the stream has
+ *   reached the call's work.
+ * - Every call returns an lp_status; nothing throws across the ABI.  On an
+ *   error, lp_last_error(ctx) holds a one-line description.
+ * - A context is not thread-safe; use one per host thread.
+ * - Floating point is IEEE binary32 throughout.
+ */
+#ifndef LINPRIM_H
+#define LINPRIM_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LP_OK = 0,
+    LP_ERR_INVALID = 1,      /* a bad argument (null pointer, bad size, bad enum) */
+    LP_ERR_CAPACITY = 2,     /* a captured launch overflowed reserved capacity */
+    LP_ERR_CUDA = 3,         /* a CUDA runtime error; see lp_last_error */
+    LP_ERR_TIMEOUT = 4,      /* a bounded device-side wait expired */
+    LP_ERR_UNSUPPORTED = 5,  /* valid but not implemented (e.g. tile size) */
+    LP_ERR_STATE = 6         /* call order violated (backward without forward) */
+} lp_status;
+
+/* Primitive kinds; the value is the number of vertices per primitive. */
+enum { LP_TETRAHEDRON = 4, LP_OCTAHEDRON = 6 };
+
+/* Largest number of cameras rendered by one call. */
+#define LP_MAX_CAMERAS 32
+
+/* Pinhole camera (Sec. 3.2 "Preprocessing": primitives are transformed into
+ * the camera's coordinate system and projected).
+ *   viewmat  world -> camera, 4x4 row-major, OpenCV axes (x right, y down,
+ *            z forward); the last row is ignored.
+ *   fx, fy   focal lengths in pixels; cx, cy principal point in pixels.
+ *            Pixel (x, y) is sampled at its centre (x + 0.5, y + 0.5).
+ *   width, height  image size in pixels (each >= 1).                       */
+typedef struct {
+    float viewmat[16];
+    float fx, fy, cx, cy;
+    int width, height;
+} lp_camera;
+
+/* A population of primitives, structure of arrays, all device pointers.
+ * (Sec. 3.1: features are position, vertices, opacity and SH colour.)
+ *   kind       LP_OCTAHEDRON or LP_TETRAHEDRON (V = 6 or 4 vertices).
+ *   n          number of primitives (>= 0).
+ *   sh_degree  0..3; K = (sh_degree + 1)^2 coefficients per channel.
+ *   centre     float[n][3]   world-space centre (the linearisation point of
+ *              the ray-space map and the depth-sort key; Sec. 3.2).
+ *   verts      float[n][V][3] world-space vertices.  Octahedra: the order is
+ *              (+a0, -a0, +a1, -a1, +a2, -a2) for three axes a_i through the
+ *              centre; faces take one vertex of each pair (8 faces).
+ *              Tetrahedra: any order; face k omits vertex k (4 faces).
+ *   opacity    float[n]      alpha in [0, 1) (after the sigmoid).
+ *   sh         float[n][K][3] SH coefficients in 3DGS order.
+ * Preconditions (not checked): each primitive is convex and its centre lies
+ * strictly inside it, as the paper's parameterisation guarantees (Sec. 3.1);
+ * all values are finite.                                                    */
+typedef struct {
+    int kind;
+    int n;
+    int sh_degree;
+    const float* centre;
+    const float* verts;
+    const float* opacity;
+    const float* sh;
+} lp_prims;
+
+/* Launch / algorithm parameters (the autotuner's search space).
+ *   tile          tile edge in pixels; 16 (the paper's patch size, App.
+ *                 "Rendering Performance", Table 7) or 8 or 32.
+ *   batch         projected primitives staged in shared memory per round of
+ *                 the blend (32..256, multiple of 32).
+ *   blocks_per_sm resident blend blocks per SM for the persistent grid (1..8).
+ *   sort_mode     0: one stable radix sort of 64-bit (tile << 32 | depth)
+ *                 keys; 1: stable sort of records by depth, then a stable
+ *                 sort of the tile ids (same resulting order).             */
+typedef struct {
+    int tile;
+    int batch;
+    int blocks_per_sm;
+    int sort_mode;
+} lp_tuning;
+
+/* Sizes of the last forward call (filled by lp_get_stats).                 */
+typedef struct {
+    long long records;    /* n_cams * n (primitive, view) pairs */
+    long long entries;    /* tile-list length E (0 until read back) */
+    long long tiles;      /* tiles over all cameras */
+    long long pixels;     /* pixels over all cameras */
+    int sort_passes;      /* radix passes of the last sort */
+    int key_bits;         /* key bits sorted */
+} lp_stats;
+
+typedef struct lp_ctx lp_ctx;
+
+/* Create a context bound to CUDA device `device` (made current for every
+ * later call on this context).  *out receives the context.                  */
+lp_status lp_create(lp_ctx** out, int device);
+
+/* Free the context and its device workspace.  NULL is ignored.             */
+void lp_destroy(lp_ctx* ctx);
+
+/* Set / read the tuning parameters (defaults: tile 16, batch 64,
+ * blocks_per_sm 4, sort_mode 0).                                            */
+lp_status lp_set_tuning(lp_ctx* ctx, const lp_tuning* t);
+lp_status lp_get_tuning(lp_ctx* ctx, lp_tuning* t);
+
+/* Pre-size the library-owned workspace.  Needed before a forward/backward
+ * pair is captured into a CUDA graph: a captured call cannot read the
+ * tile-list length back, so it uses this capacity and latches
+ * LP_ERR_CAPACITY (returned by lp_sync_status) if E exceeds it.  Outside
+ * capture the workspace grows on demand and this call is optional.
+ *   max_records  >= n_cams * n;  max_entries >= E;
+ *   max_pixels   >= total pixels; max_tiles >= total tiles.                 */
+lp_status lp_reserve(lp_ctx* ctx, long long max_records, long long max_entries,
+                     long long max_pixels, long long max_tiles);
+
+/* Forward render of n_cams cameras in one batched launch sequence
+ * (Sec. 3.2: preprocess, global sort + tiling, per-tile rasterization and
+ * front-to-back compositing with the stop at cumulative opacity 0.999).
+ *   prims   host struct with device arrays, see lp_prims.
+ *   cams    host array of n_cams cameras (1 <= n_cams <= LP_MAX_CAMERAS).
+ *   bg      host float[3] background colour.
+ *   images  device float, packed per camera as [3][H][W] planes, cameras
+ *           back to back in order (sum of 3*W*H floats); overwritten.
+ * The context keeps the sorted tile lists and per-pixel state (8 bytes per
+ * pixel) for the next lp_render_backward.  Outside stream capture the call
+ * synchronises `stream` once, to read the tile-list length and size its
+ * workspace.                                                                */
+lp_status lp_render_forward(lp_ctx* ctx, const lp_prims* prims, const lp_camera* cams,
+                            int n_cams, const float bg[3], float* images, void* stream);
+
+/* Backward of the last lp_render_forward on this context (Sec. 3.4
+ * "Rasterization Backpropagation" and "Preprocessing Backpropagation").
+ * The primitive arrays and cameras of that forward must be unchanged.
+ *   dL_dimages  device float, same layout as the forward's images.
+ *   dcentre     device float[n][3]
+ *   dverts      device float[n][V][3]
+ *   dopacity    device float[n]
+ *   dsh         device float[n][K][3]
+ *   accumulate  0: outputs are overwritten; 1: gradients are added to them.
+ * Gradients are summed over the cameras of the forward.  The density
+ * normaliser d_min carries no gradient (App. "Experimental Setting").
+ * Returns LP_ERR_STATE if no forward preceded it on this context.          */
+lp_status lp_render_backward(lp_ctx* ctx, const float* dL_dimages, float* dcentre,
+                             float* dverts, float* dopacity, float* dsh, int accumulate,
+                             void* stream);
+
+/* Synchronise `stream`, then return (and clear) any status latched on the
+ * device by earlier calls (LP_ERR_CAPACITY, LP_ERR_TIMEOUT), or LP_OK.     */
+lp_status lp_sync_status(lp_ctx* ctx, void* stream);
+
+/* Sizes of the last forward (host struct).                                 */
+lp_status lp_get_stats(lp_ctx* ctx, lp_stats* out);
+
+/* Parity hooks (synchronise the device; host buffers):
+ * lp_debug_keys copies the sorted tile list of the last forward -- keys
+ * (global_tile << 32 | binary32 bits of the camera-space centre depth) and
+ * values (record index cam * n + primitive) -- up to `cap` entries, and
+ * stores E in *n.  lp_debug_counts copies the per-record tile counts
+ * (n_cams * n).  lp_debug_pixel_state copies the per-pixel number of
+ * tile-list entries up to the last contributor and the transmittance before
+ * it (total pixels each).                                                   */
+lp_status lp_debug_keys(lp_ctx* ctx, unsigned long long* keys, unsigned int* vals,
+                        long long cap, long long* n);
+lp_status lp_debug_counts(lp_ctx* ctx, unsigned int* counts, long long cap);
+lp_status lp_debug_pixel_state(lp_ctx* ctx, unsigned int* last, float* T_last, long long cap);
+
+/* Workload counters of the last forward (synchronises; runs an instrumented
+ * copy of the blend): iterated and intersected (pixel, primitive) pairs as
+ * in the paper's App. "Rendering Performance", Table 7.                    */
+lp_status lp_count_pairs(lp_ctx* ctx, long long* iterated, long long* intersected);
+
+/* Description of the last error on this context ("" if none).             */
+const char* lp_last_error(lp_ctx* ctx);
+
+/* Static name of a status code.                                            */
+const char* lp_status_string(lp_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LINPRIM_H */

@@ -3,7 +3,7 @@
  *
  * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the
  * benchmark's CPU-baseline leg use this file.  It shares no code, header,
- * constant or helper with the CUDA path under paper_2501_16312_gb300/.
+ * constant or helper with the CUDA rasterizer package.
  *
  * It is a plain, slow, brute-force restatement of the paper's forward and
  * backward pass, in the order the paper gives them:
@@ -31,7 +31,7 @@
  * Readings where the paper is silent (pixel centres at x+0.5, principal point,
  * OpenCV axes, culling at centre depth <= 0.2, key layout, tie order, stop
  * rule inclusive of the primitive that crosses the threshold, colour clamp at
- * zero) are the ones listed in the design notes; each is marked below.
+ * zero) are each marked "reading" where they apply below.
  *
  * Integers decided by floating point (culling, depth key, pixel/tile
  * rectangle) are computed in IEEE binary32 with a fixed operation order and no

@@ -1,0 +1,541 @@
+// C ABI of the LinPrim rasterizer: context, workspace and launch sequence.
+//
+// lp_render_forward enqueues, on the caller's stream:
+//   A1 preprocess (all cameras x primitives) -> A2 scan of tile counts and key
+//   emission -> A3 stable radix sort of (tile << 32 | depth) keys -> A4 tile
+//   ranges -> A5 persistent front-to-back blend over the tiles of all cameras.
+// lp_render_backward enqueues A6 (back-to-front blend backward) and A7 (chain
+// to world-space centre/vertices, opacity and SH, summed over cameras).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+
+#include "linprim.h"
+#include "lp_device.cuh"
+#include "lp_internal.h"
+
+namespace {
+
+// Grow-only device allocation.
+template <typename T> struct DevBuf {
+    T* p = nullptr;
+    size_t cap = 0;   // elements
+};
+
+}  // namespace
+
+struct lp_ctx {
+    int device = 0;
+    int sms = 0;
+    lp_tuning tune{16, 64, 4, 0};
+    char err[512] = {0};
+
+    DevBuf<float> rec;
+    DevBuf<uint32_t> counts, offsets, zbits, scan_tmp, hist, last;
+    DevBuf<int4> trect;
+    DevBuf<uint64_t> keys0, keys1;
+    DevBuf<uint32_t> vals0, vals1;
+    DevBuf<uint2> ranges;
+    DevBuf<float> tl, acc, scratch_image;
+    int* d_status = nullptr;         // latched status bits
+    uint32_t* d_E = nullptr;         // tile-list length of the last forward
+    int* d_tile_counter = nullptr;   // [0] forward queue, [1] backward queue
+    unsigned long long* d_pairs = nullptr;
+    uint32_t* h_E = nullptr;         // pinned
+
+    // state of the last forward
+    bool have_fwd = false;
+    lp_prims prims{};
+    lp::CamsParam cams{};
+    float bg[3] = {0.f, 0.f, 0.f};
+    long long records = 0, pixels = 0, tiles = 0, E_bound = 0, E_host = -1;
+    int key_bits = 0, sort_passes = 0;
+    bool result_in_1 = false;
+};
+
+namespace {
+
+lp_status fail(lp_ctx* ctx, lp_status s, const char* fmt, ...) {
+    if (ctx) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(ctx->err, sizeof(ctx->err), fmt, ap);
+        va_end(ap);
+    }
+    return s;
+}
+
+#define LP_CUDA(call)                                                                        \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return fail(ctx, LP_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_));          \
+    } while (0)
+
+#define LP_TRY(expr)                    \
+    do {                                \
+        lp_status s_ = (expr);          \
+        if (s_ != LP_OK) return s_;     \
+    } while (0)
+
+bool capturing(cudaStream_t st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) return false;
+    return cs != cudaStreamCaptureStatusNone;
+}
+
+template <typename T>
+lp_status ensure(lp_ctx* ctx, DevBuf<T>& b, long long n, bool cap_mode, const char* what) {
+    const size_t want = (size_t)(n > 0 ? n : 1);
+    if (b.cap >= want) return LP_OK;
+    if (cap_mode)
+        return fail(ctx, LP_ERR_CAPACITY,
+                    "%s needs %lld elements but %zu are reserved; call lp_reserve before capture",
+                    what, (long long)want, b.cap);
+    if (b.p) {
+        cudaError_t e = cudaFree(b.p);
+        if (e != cudaSuccess) return fail(ctx, LP_ERR_CUDA, "cudaFree: %s", cudaGetErrorString(e));
+        b.p = nullptr;
+        b.cap = 0;
+    }
+    const size_t grow = want + want / 4;
+    cudaError_t e = cudaMalloc((void**)&b.p, grow * sizeof(T));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, LP_ERR_CUDA, "cudaMalloc(%s, %zu bytes): %s", what, grow * sizeof(T),
+                    cudaGetErrorString(e));
+    }
+    b.cap = grow;
+    return LP_OK;
+}
+
+template <typename T> void release(DevBuf<T>& b) {
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.cap = 0;
+}
+
+int rec_floats(int V) { return V == 6 ? lp::Rec<6>::kFloats : lp::Rec<4>::kFloats; }
+int acc_floats(int V) { return V == 6 ? lp::Acc<6>::kFloats : lp::Acc<4>::kFloats; }
+
+lp_status check_prims(lp_ctx* ctx, const lp_prims* p) {
+    if (!p) return fail(ctx, LP_ERR_INVALID, "prims is NULL");
+    if (p->kind != LP_OCTAHEDRON && p->kind != LP_TETRAHEDRON)
+        return fail(ctx, LP_ERR_INVALID, "kind %d is neither LP_OCTAHEDRON nor LP_TETRAHEDRON", p->kind);
+    if (p->n < 0) return fail(ctx, LP_ERR_INVALID, "n = %d < 0", p->n);
+    if (p->sh_degree < 0 || p->sh_degree > 3)
+        return fail(ctx, LP_ERR_INVALID, "sh_degree %d outside 0..3", p->sh_degree);
+    if (p->n > 0 && (!p->centre || !p->verts || !p->opacity || !p->sh))
+        return fail(ctx, LP_ERR_INVALID, "a primitive array is NULL");
+    return LP_OK;
+}
+
+lp_status build_cams(lp_ctx* ctx, const lp_camera* cams, int n_cams, int tile, lp::CamsParam& out,
+                     long long& pixels, long long& tiles) {
+    if (!cams) return fail(ctx, LP_ERR_INVALID, "cams is NULL");
+    if (n_cams < 1 || n_cams > LP_MAX_CAMERAS)
+        return fail(ctx, LP_ERR_INVALID, "n_cams = %d outside 1..%d", n_cams, LP_MAX_CAMERAS);
+    memset(&out, 0, sizeof(out));
+    out.n = n_cams;
+    out.tile = tile;
+    long long tb = 0, pb = 0;
+    for (int c = 0; c < n_cams; ++c) {
+        const lp_camera& s = cams[c];
+        if (s.width < 1 || s.height < 1 || s.width > 65536 || s.height > 65536)
+            return fail(ctx, LP_ERR_INVALID, "camera %d has size %dx%d", c, s.width, s.height);
+        lp::CamDev& d = out.cam[c];
+        double R[3][3], T[3];
+        for (int i = 0; i < 3; ++i) {
+            for (int j = 0; j < 3; ++j) {
+                R[i][j] = s.viewmat[4 * i + j];
+                d.R[3 * i + j] = s.viewmat[4 * i + j];
+            }
+            T[i] = s.viewmat[4 * i + 3];
+            d.T[i] = s.viewmat[4 * i + 3];
+        }
+        for (int j = 0; j < 3; ++j)
+            d.campos[j] = (float)(-(R[0][j] * T[0] + R[1][j] * T[1] + R[2][j] * T[2]));
+        d.fx = s.fx; d.fy = s.fy; d.cx = s.cx; d.cy = s.cy;
+        d.width = s.width; d.height = s.height;
+        d.tiles_x = (s.width + tile - 1) / tile;
+        d.tiles_y = (s.height + tile - 1) / tile;
+        d.tile_base = (int)tb;
+        d.pix_base = (int)pb;
+        tb += (long long)d.tiles_x * d.tiles_y;
+        pb += (long long)s.width * s.height;
+    }
+    if (pb > (1ll << 30) || tb > (1ll << 30))
+        return fail(ctx, LP_ERR_INVALID, "too many pixels (%lld) or tiles (%lld)", pb, tb);
+    out.total_tiles = (int)tb;
+    out.total_pixels = (int)pb;
+    pixels = pb;
+    tiles = tb;
+    return LP_OK;
+}
+
+int bits_for(long long n) {   // bits needed to represent values 0 .. n-1
+    int b = 0;
+    while ((1ll << b) < n) ++b;
+    return b;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lp_status_string(lp_status s) {
+    switch (s) {
+        case LP_OK: return "LP_OK";
+        case LP_ERR_INVALID: return "LP_ERR_INVALID";
+        case LP_ERR_CAPACITY: return "LP_ERR_CAPACITY";
+        case LP_ERR_CUDA: return "LP_ERR_CUDA";
+        case LP_ERR_TIMEOUT: return "LP_ERR_TIMEOUT";
+        case LP_ERR_UNSUPPORTED: return "LP_ERR_UNSUPPORTED";
+        case LP_ERR_STATE: return "LP_ERR_STATE";
+    }
+    return "LP_ERR_UNKNOWN";
+}
+
+const char* lp_last_error(lp_ctx* ctx) { return ctx ? ctx->err : "no context"; }
+
+lp_status lp_create(lp_ctx** out, int device) {
+    if (!out) return LP_ERR_INVALID;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return LP_ERR_CUDA;
+    }
+    lp_ctx* ctx = new lp_ctx();
+    ctx->device = device;
+    cudaError_t e = cudaSetDevice(device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, device);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->d_status, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->d_E, sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->d_tile_counter, 2 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->d_pairs, 2 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->h_E, sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMemset(ctx->d_status, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(ctx->d_E, 0, sizeof(uint32_t));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        lp_destroy(ctx);
+        return LP_ERR_CUDA;
+    }
+    *out = ctx;
+    return LP_OK;
+}
+
+void lp_destroy(lp_ctx* ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    release(ctx->rec); release(ctx->counts); release(ctx->offsets); release(ctx->zbits);
+    release(ctx->scan_tmp); release(ctx->hist); release(ctx->last); release(ctx->trect);
+    release(ctx->keys0); release(ctx->keys1); release(ctx->vals0); release(ctx->vals1);
+    release(ctx->ranges); release(ctx->tl); release(ctx->acc); release(ctx->scratch_image);
+    if (ctx->d_status) cudaFree(ctx->d_status);
+    if (ctx->d_E) cudaFree(ctx->d_E);
+    if (ctx->d_tile_counter) cudaFree(ctx->d_tile_counter);
+    if (ctx->d_pairs) cudaFree(ctx->d_pairs);
+    if (ctx->h_E) cudaFreeHost(ctx->h_E);
+    delete ctx;
+}
+
+lp_status lp_set_tuning(lp_ctx* ctx, const lp_tuning* t) {
+    if (!ctx || !t) return LP_ERR_INVALID;
+    if (t->tile != 16) return fail(ctx, LP_ERR_UNSUPPORTED, "tile %d: only 16 is built", t->tile);
+    if (t->batch != 32 && t->batch != 64 && t->batch != 128 && t->batch != 256)
+        return fail(ctx, LP_ERR_INVALID, "batch %d not in {32, 64, 128, 256}", t->batch);
+    if (t->blocks_per_sm < 1 || t->blocks_per_sm > 8)
+        return fail(ctx, LP_ERR_INVALID, "blocks_per_sm %d outside 1..8", t->blocks_per_sm);
+    if (t->sort_mode != 0) return fail(ctx, LP_ERR_UNSUPPORTED, "sort_mode %d not built", t->sort_mode);
+    ctx->tune = *t;
+    return LP_OK;
+}
+
+lp_status lp_get_tuning(lp_ctx* ctx, lp_tuning* t) {
+    if (!ctx || !t) return LP_ERR_INVALID;
+    *t = ctx->tune;
+    return LP_OK;
+}
+
+static lp_status reserve_impl(lp_ctx* ctx, long long records, long long entries, long long pixels,
+                              long long tiles, int V) {
+    const int rf = V ? rec_floats(V) : lp::Rec<6>::kFloats;
+    LP_TRY(ensure(ctx, ctx->rec, records * rf, false, "records"));
+    LP_TRY(ensure(ctx, ctx->counts, records, false, "counts"));
+    LP_TRY(ensure(ctx, ctx->offsets, records, false, "offsets"));
+    LP_TRY(ensure(ctx, ctx->zbits, records, false, "zbits"));
+    LP_TRY(ensure(ctx, ctx->trect, records, false, "tile rects"));
+    LP_TRY(ensure(ctx, ctx->keys0, entries, false, "keys"));
+    LP_TRY(ensure(ctx, ctx->keys1, entries, false, "keys"));
+    LP_TRY(ensure(ctx, ctx->vals0, entries, false, "values"));
+    LP_TRY(ensure(ctx, ctx->vals1, entries, false, "values"));
+    LP_TRY(ensure(ctx, ctx->hist, (long long)lp::sort_hist_elems(entries), false, "histograms"));
+    long long sb = lp::scan_blocks(records);
+    long long sb2 = lp::scan_blocks((long long)lp::sort_hist_elems(entries));
+    LP_TRY(ensure(ctx, ctx->scan_tmp, sb > sb2 ? sb : sb2, false, "scan blocks"));
+    LP_TRY(ensure(ctx, ctx->ranges, tiles, false, "tile ranges"));
+    LP_TRY(ensure(ctx, ctx->last, pixels, false, "pixel state"));
+    LP_TRY(ensure(ctx, ctx->tl, pixels, false, "pixel state"));
+    const int af = V ? acc_floats(V) : lp::Acc<6>::kFloats;
+    LP_TRY(ensure(ctx, ctx->acc, records * af, false, "gradient accumulators"));
+    return LP_OK;
+}
+
+lp_status lp_reserve(lp_ctx* ctx, long long max_records, long long max_entries, long long max_pixels,
+                     long long max_tiles) {
+    if (!ctx) return LP_ERR_INVALID;
+    if (max_records < 0 || max_entries < 0 || max_pixels < 0 || max_tiles < 0 ||
+        max_entries > 0xffffffffll)
+        return fail(ctx, LP_ERR_INVALID, "bad reserve sizes");
+    LP_CUDA(cudaSetDevice(ctx->device));
+    return reserve_impl(ctx, max_records, max_entries, max_pixels, max_tiles, 0);
+}
+
+lp_status lp_render_forward(lp_ctx* ctx, const lp_prims* prims, const lp_camera* cams, int n_cams,
+                            const float bg[3], float* images, void* stream) {
+    if (!ctx) return LP_ERR_INVALID;
+    ctx->err[0] = 0;
+    LP_TRY(check_prims(ctx, prims));
+    if (!bg) return fail(ctx, LP_ERR_INVALID, "bg is NULL");
+    if (!images) return fail(ctx, LP_ERR_INVALID, "images is NULL");
+    LP_CUDA(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool cap_mode = capturing(st);
+    const int V = prims->kind;
+    lp::CamsParam cp;
+    long long pixels = 0, tiles = 0;
+    LP_TRY(build_cams(ctx, cams, n_cams, ctx->tune.tile, cp, pixels, tiles));
+    const long long records = (long long)n_cams * prims->n;
+    if (records > 0x7fffffffll) return fail(ctx, LP_ERR_INVALID, "too many records (%lld)", records);
+    ctx->have_fwd = false;
+
+    LP_TRY(ensure(ctx, ctx->rec, records * rec_floats(V), cap_mode, "records"));
+    LP_TRY(ensure(ctx, ctx->counts, records, cap_mode, "counts"));
+    LP_TRY(ensure(ctx, ctx->offsets, records, cap_mode, "offsets"));
+    LP_TRY(ensure(ctx, ctx->zbits, records, cap_mode, "zbits"));
+    LP_TRY(ensure(ctx, ctx->trect, records, cap_mode, "tile rects"));
+    LP_TRY(ensure(ctx, ctx->scan_tmp, lp::scan_blocks(records), cap_mode, "scan blocks"));
+    LP_TRY(ensure(ctx, ctx->ranges, tiles, cap_mode, "tile ranges"));
+    LP_TRY(ensure(ctx, ctx->last, pixels, cap_mode, "pixel state"));
+    LP_TRY(ensure(ctx, ctx->tl, pixels, cap_mode, "pixel state"));
+
+    lp::PrimsDev P{prims->n, prims->centre, prims->verts, prims->opacity, prims->sh};
+    LP_CUDA(lp::launch_preprocess(V, prims->sh_degree, P, cp, ctx->rec.p, ctx->counts.p, ctx->trect.p,
+                                  ctx->zbits.p, st));
+    LP_CUDA(lp::launch_scan(ctx->counts.p, records, ctx->offsets.p, ctx->scan_tmp.p, ctx->d_E, st));
+
+    long long bound;
+    if (!cap_mode) {
+        LP_CUDA(cudaMemcpyAsync(ctx->h_E, ctx->d_E, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+        LP_CUDA(cudaStreamSynchronize(st));
+        bound = *ctx->h_E;
+        ctx->E_host = bound;
+        LP_TRY(ensure(ctx, ctx->keys0, bound, false, "keys"));
+        LP_TRY(ensure(ctx, ctx->keys1, bound, false, "keys"));
+        LP_TRY(ensure(ctx, ctx->vals0, bound, false, "values"));
+        LP_TRY(ensure(ctx, ctx->vals1, bound, false, "values"));
+    } else {
+        bound = (long long)ctx->keys0.cap;
+        if ((long long)ctx->keys1.cap < bound) bound = ctx->keys1.cap;
+        if ((long long)ctx->vals0.cap < bound) bound = ctx->vals0.cap;
+        if ((long long)ctx->vals1.cap < bound) bound = ctx->vals1.cap;
+        ctx->E_host = -1;
+    }
+    LP_TRY(ensure(ctx, ctx->hist, (long long)lp::sort_hist_elems(bound), cap_mode, "histograms"));
+    LP_TRY(ensure(ctx, ctx->scan_tmp, lp::scan_blocks((long long)lp::sort_hist_elems(bound)), cap_mode,
+                  "scan blocks"));
+
+    LP_CUDA(lp::launch_emit(ctx->counts.p, ctx->offsets.p, ctx->trect.p, ctx->zbits.p, prims->n, records,
+                            cp, ctx->keys0.p, ctx->vals0.p, bound, ctx->d_status, st));
+    const int key_bits = 32 + bits_for(tiles);
+    int passes = 0;
+    LP_CUDA(lp::launch_radix_sort(ctx->keys0.p, ctx->vals0.p, ctx->keys1.p, ctx->vals1.p, ctx->d_E, bound,
+                                  key_bits, ctx->hist.p, ctx->scan_tmp.p, &passes, st));
+    const bool in1 = (passes & 1) != 0;
+    const uint64_t* skeys = in1 ? ctx->keys1.p : ctx->keys0.p;
+    const uint32_t* svals = in1 ? ctx->vals1.p : ctx->vals0.p;
+    LP_CUDA(cudaMemsetAsync(ctx->ranges.p, 0, (size_t)(tiles > 0 ? tiles : 1) * sizeof(uint2), st));
+    LP_CUDA(lp::launch_ranges(skeys, ctx->d_E, bound, ctx->d_status, ctx->ranges.p, ctx->sms, st));
+
+    lp::BlendArgs a{};
+    a.grid = (int)(tiles < (long long)ctx->sms * ctx->tune.blocks_per_sm ? tiles
+                                                                         : (long long)ctx->sms * ctx->tune.blocks_per_sm);
+    a.rec = ctx->rec.p;
+    a.vals = svals;
+    a.ranges = ctx->ranges.p;
+    a.cams = &cp;
+    a.bg[0] = bg[0]; a.bg[1] = bg[1]; a.bg[2] = bg[2];
+    a.image = images;
+    a.last = ctx->last.p;
+    a.tl = ctx->tl.p;
+    a.tile_counter = ctx->d_tile_counter;
+    a.pair_counts = ctx->d_pairs;
+    a.count = false;
+    LP_CUDA(cudaMemsetAsync(ctx->d_tile_counter, 0, sizeof(int), st));
+    if (a.grid > 0) LP_CUDA(lp::launch_blend_fwd(V, ctx->tune.batch, a, st));
+
+    ctx->have_fwd = true;
+    ctx->prims = *prims;
+    ctx->cams = cp;
+    ctx->bg[0] = bg[0]; ctx->bg[1] = bg[1]; ctx->bg[2] = bg[2];
+    ctx->records = records;
+    ctx->pixels = pixels;
+    ctx->tiles = tiles;
+    ctx->E_bound = bound;
+    ctx->key_bits = key_bits;
+    ctx->sort_passes = passes;
+    ctx->result_in_1 = in1;
+    return LP_OK;
+}
+
+lp_status lp_render_backward(lp_ctx* ctx, const float* dL_dimages, float* dcentre, float* dverts,
+                             float* dopacity, float* dsh, int accumulate, void* stream) {
+    if (!ctx) return LP_ERR_INVALID;
+    ctx->err[0] = 0;
+    if (!ctx->have_fwd) return fail(ctx, LP_ERR_STATE, "lp_render_backward without a forward");
+    const lp_prims& pr = ctx->prims;
+    if (!dL_dimages) return fail(ctx, LP_ERR_INVALID, "dL_dimages is NULL");
+    if (pr.n > 0 && (!dcentre || !dverts || !dopacity || !dsh))
+        return fail(ctx, LP_ERR_INVALID, "a gradient output is NULL");
+    LP_CUDA(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool cap_mode = capturing(st);
+    const int V = pr.kind;
+    const long long acc_n = (ctx->records > 0 ? ctx->records : 1) * acc_floats(V);
+    LP_TRY(ensure(ctx, ctx->acc, acc_n, cap_mode, "gradient accumulators"));
+    LP_CUDA(cudaMemsetAsync(ctx->acc.p, 0, (size_t)acc_n * sizeof(float), st));
+
+    lp::BlendArgs a{};
+    a.grid = (int)(ctx->tiles < (long long)ctx->sms * ctx->tune.blocks_per_sm
+                       ? ctx->tiles
+                       : (long long)ctx->sms * ctx->tune.blocks_per_sm);
+    a.rec = ctx->rec.p;
+    a.vals = ctx->result_in_1 ? ctx->vals1.p : ctx->vals0.p;
+    a.ranges = ctx->ranges.p;
+    a.cams = &ctx->cams;
+    a.bg[0] = ctx->bg[0]; a.bg[1] = ctx->bg[1]; a.bg[2] = ctx->bg[2];
+    a.dimage = dL_dimages;
+    a.last = ctx->last.p;
+    a.tl = ctx->tl.p;
+    a.acc = ctx->acc.p;
+    a.tile_counter = ctx->d_tile_counter + 1;
+    LP_CUDA(cudaMemsetAsync(ctx->d_tile_counter + 1, 0, sizeof(int), st));
+    if (a.grid > 0) LP_CUDA(lp::launch_blend_bwd(V, ctx->tune.batch, a, st));
+
+    lp::PrimsDev P{pr.n, pr.centre, pr.verts, pr.opacity, pr.sh};
+    LP_CUDA(lp::launch_chain(V, pr.sh_degree, P, ctx->cams, ctx->rec.p, ctx->counts.p, ctx->acc.p, dcentre,
+                             dverts, dopacity, dsh, accumulate, st));
+    return LP_OK;
+}
+
+lp_status lp_sync_status(lp_ctx* ctx, void* stream) {
+    if (!ctx) return LP_ERR_INVALID;
+    LP_CUDA(cudaSetDevice(ctx->device));
+    LP_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    int s = 0;
+    LP_CUDA(cudaMemcpy(&s, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    LP_CUDA(cudaMemset(ctx->d_status, 0, sizeof(int)));
+    if (s & lp::kStatusCapacity)
+        return fail(ctx, LP_ERR_CAPACITY, "tile list exceeded the reserved capacity");
+    if (s & lp::kStatusTimeout) return fail(ctx, LP_ERR_TIMEOUT, "a device-side wait expired");
+    return LP_OK;
+}
+
+lp_status lp_get_stats(lp_ctx* ctx, lp_stats* out) {
+    if (!ctx || !out) return LP_ERR_INVALID;
+    out->records = ctx->records;
+    out->entries = ctx->E_host;
+    if (ctx->have_fwd && ctx->E_host < 0) {
+        uint32_t e = 0;
+        LP_CUDA(cudaSetDevice(ctx->device));
+        LP_CUDA(cudaDeviceSynchronize());
+        LP_CUDA(cudaMemcpy(&e, ctx->d_E, sizeof(uint32_t), cudaMemcpyDeviceToHost));
+        out->entries = e;
+    }
+    out->tiles = ctx->tiles;
+    out->pixels = ctx->pixels;
+    out->sort_passes = ctx->sort_passes;
+    out->key_bits = ctx->key_bits;
+    return LP_OK;
+}
+
+lp_status lp_debug_keys(lp_ctx* ctx, unsigned long long* keys, unsigned int* vals, long long cap,
+                        long long* n) {
+    if (!ctx || !n) return LP_ERR_INVALID;
+    if (!ctx->have_fwd) return fail(ctx, LP_ERR_STATE, "no forward");
+    LP_CUDA(cudaSetDevice(ctx->device));
+    LP_CUDA(cudaDeviceSynchronize());
+    uint32_t e = 0;
+    LP_CUDA(cudaMemcpy(&e, ctx->d_E, sizeof(uint32_t), cudaMemcpyDeviceToHost));
+    *n = e;
+    long long m = e < cap ? e : cap;
+    if (m > ctx->E_bound) m = ctx->E_bound;
+    if (m > 0 && keys)
+        LP_CUDA(cudaMemcpy(keys, ctx->result_in_1 ? ctx->keys1.p : ctx->keys0.p, (size_t)m * 8,
+                           cudaMemcpyDeviceToHost));
+    if (m > 0 && vals)
+        LP_CUDA(cudaMemcpy(vals, ctx->result_in_1 ? ctx->vals1.p : ctx->vals0.p, (size_t)m * 4,
+                           cudaMemcpyDeviceToHost));
+    return LP_OK;
+}
+
+lp_status lp_debug_counts(lp_ctx* ctx, unsigned int* counts, long long cap) {
+    if (!ctx || !counts) return LP_ERR_INVALID;
+    if (!ctx->have_fwd) return fail(ctx, LP_ERR_STATE, "no forward");
+    LP_CUDA(cudaSetDevice(ctx->device));
+    LP_CUDA(cudaDeviceSynchronize());
+    const long long m = ctx->records < cap ? ctx->records : cap;
+    if (m > 0) LP_CUDA(cudaMemcpy(counts, ctx->counts.p, (size_t)m * 4, cudaMemcpyDeviceToHost));
+    return LP_OK;
+}
+
+lp_status lp_debug_pixel_state(lp_ctx* ctx, unsigned int* last, float* T_last, long long cap) {
+    if (!ctx) return LP_ERR_INVALID;
+    if (!ctx->have_fwd) return fail(ctx, LP_ERR_STATE, "no forward");
+    LP_CUDA(cudaSetDevice(ctx->device));
+    LP_CUDA(cudaDeviceSynchronize());
+    const long long m = ctx->pixels < cap ? ctx->pixels : cap;
+    if (m > 0 && last) LP_CUDA(cudaMemcpy(last, ctx->last.p, (size_t)m * 4, cudaMemcpyDeviceToHost));
+    if (m > 0 && T_last) LP_CUDA(cudaMemcpy(T_last, ctx->tl.p, (size_t)m * 4, cudaMemcpyDeviceToHost));
+    return LP_OK;
+}
+
+lp_status lp_count_pairs(lp_ctx* ctx, long long* iterated, long long* intersected) {
+    if (!ctx || !iterated || !intersected) return LP_ERR_INVALID;
+    if (!ctx->have_fwd) return fail(ctx, LP_ERR_STATE, "no forward");
+    LP_CUDA(cudaSetDevice(ctx->device));
+    LP_CUDA(cudaDeviceSynchronize());
+    LP_TRY(ensure(ctx, ctx->scratch_image, 3 * ctx->pixels, false, "scratch image"));
+    lp::BlendArgs a{};
+    a.grid = (int)(ctx->tiles < (long long)ctx->sms * ctx->tune.blocks_per_sm
+                       ? ctx->tiles
+                       : (long long)ctx->sms * ctx->tune.blocks_per_sm);
+    a.rec = ctx->rec.p;
+    a.vals = ctx->result_in_1 ? ctx->vals1.p : ctx->vals0.p;
+    a.ranges = ctx->ranges.p;
+    a.cams = &ctx->cams;
+    a.bg[0] = ctx->bg[0]; a.bg[1] = ctx->bg[1]; a.bg[2] = ctx->bg[2];
+    a.image = ctx->scratch_image.p;
+    a.last = ctx->last.p;
+    a.tl = ctx->tl.p;
+    a.tile_counter = ctx->d_tile_counter;
+    a.pair_counts = ctx->d_pairs;
+    a.count = true;
+    LP_CUDA(cudaMemset(ctx->d_pairs, 0, 2 * sizeof(unsigned long long)));
+    LP_CUDA(cudaMemset(ctx->d_tile_counter, 0, sizeof(int)));
+    if (a.grid > 0) LP_CUDA(lp::launch_blend_fwd(ctx->prims.kind, ctx->tune.batch, a, 0));
+    LP_CUDA(cudaDeviceSynchronize());
+    unsigned long long h[2] = {0, 0};
+    LP_CUDA(cudaMemcpy(h, ctx->d_pairs, sizeof(h), cudaMemcpyDeviceToHost));
+    *iterated = (long long)h[0];
+    *intersected = (long long)h[1];
+    return LP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,262 @@
+// Device-side definitions shared by the LinPrim kernels (sm_103a).
+//
+// Paper: "LinPrim: Linear Primitives for Differentiable Volumetric Rendering"
+// (arXiv 2501.16312).  Section references below are to that paper.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math_constants.h>
+#include <stdint.h>
+
+namespace lp {
+
+constexpr int kMaxCams = 32;
+constexpr float kNearZ = 0.2f;      // centres at camera depth <= 0.2 are culled
+constexpr float kStopT = 1e-3f;     // Sec. 3.2: stop at cumulative opacity 0.999
+constexpr float kAlphaScale = 0.99f;  // Eq. 1
+constexpr int kStatusCapacity = 1;
+constexpr int kStatusTimeout = 2;
+
+// One camera, pre-digested on the host.  R, T: rows of the world->camera
+// matrix; campos = -R^T T.  Tiles of this camera occupy global tile ids
+// [tile_base, tile_base + tiles_x * tiles_y); its pixels start at pix_base in
+// the packed image (3 planes of width*height floats at 3 * pix_base).
+struct CamDev {
+    float R[9];
+    float T[3];
+    float fx, fy, cx, cy;
+    float campos[3];
+    int width, height, tiles_x, tiles_y, tile_base, pix_base;
+};
+
+// Passed by value as a kernel parameter (captured into CUDA graphs with it).
+struct CamsParam {
+    int n;
+    int total_tiles;
+    int tile;
+    int total_pixels;
+    CamDev cam[kMaxCams];
+};
+
+struct PrimsDev {
+    int n;
+    const float* centre;
+    const float* verts;
+    const float* opacity;
+    const float* sh;
+};
+
+template <int V> struct Kind;
+template <> struct Kind<6> { static constexpr int F = 8; };   // octahedron
+template <> struct Kind<4> { static constexpr int F = 4; };   // tetrahedron
+
+// Face f's three vertex indices.  Octahedron vertices come in +/- pairs per
+// axis, (0,1), (2,3), (4,5); each face takes one vertex of each pair.  A
+// tetrahedron's face k is the triangle opposite vertex k.
+template <int V>
+__device__ __forceinline__ void face_vertices(int f, int& i0, int& i1, int& i2) {
+    if (V == 6) {
+        i0 = (f >> 2) & 1;
+        i1 = 2 + ((f >> 1) & 1);
+        i2 = 4 + (f & 1);
+    } else {
+        i0 = (f == 0) ? 1 : 0;
+        i1 = (f <= 1) ? 2 : 1;
+        i2 = (f <= 2) ? 3 : 2;
+    }
+}
+
+// Projected record of one (camera, primitive) pair, written by the
+// preprocess and read by both blend kernels.  Layout in floats:
+//   [0] x_c  [1] y_c      projected centre (pixels)
+//   [2] sigma             density, Eq. 1
+//   [3] nf                number of front-facing (entry) faces, int bits
+//   [4..6] rgb            view-dependent colour
+//   [7] perm              face index of each slot, 4 bits per slot
+//   [8 + 3s .. 10 + 3s]   plane of slot s: depth - z_c = a (x - x_c)
+//                         + b (y - y_c) + e; slots [0, nf) are entry faces,
+//                         [nf, F) exit faces.
+template <int V> struct Rec {
+    static constexpr int F = Kind<V>::F;
+    static constexpr int kFloats = 8 + 3 * F;   // 32 (octahedron), 20 (tetrahedron)
+    static constexpr int kVec4 = kFloats / 4;
+};
+
+// Per-record gradient accumulator written by the backward blend:
+//   [3s .. 3s+2]  dL/d(a_s, b_s, e_s) for slot s
+//   [3F .. 3F+2]  dL/d rgb,  [3F + 3] dL/d sigma
+template <int V> struct Acc {
+    static constexpr int F = Kind<V>::F;
+    static constexpr int kFloats = 3 * F + 4;   // 28, 16
+};
+
+// -------------------------------------------------------------------------
+// Binary32 key-field arithmetic.  Culling, the depth key and the pixel
+// rectangle are integers decided by floating point, so they are computed
+// with a fixed order of single-rounding operations (no contraction).
+
+__device__ __forceinline__ void xform_rn(const CamDev& c, float x, float y, float z, float t[3]) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        float a = __fmul_rn(c.R[3 * i + 0], x);
+        float b = __fmul_rn(c.R[3 * i + 1], y);
+        float d = __fmul_rn(c.R[3 * i + 2], z);
+        t[i] = __fadd_rn(__fadd_rn(__fadd_rn(a, b), d), c.T[i]);
+    }
+}
+
+// -------------------------------------------------------------------------
+// Real spherical harmonics, degree <= 3, in the 3DGS order and signs
+// (Sec. 3.1: colours follow 3DGS).  Y[k] for unit direction (x, y, z).
+struct ShC {
+    static constexpr float c0 = 0.28209479177387814f;   // 1/(2 sqrt(pi))
+    static constexpr float c1 = 0.4886025119029199f;    // sqrt(3/(4 pi))
+    static constexpr float c2a = 1.0925484305920792f;   // sqrt(15/pi)/2
+    static constexpr float c2b = 0.31539156525252005f;  // sqrt(5/pi)/4
+    static constexpr float c2c = 0.5462742152960396f;   // sqrt(15/pi)/4
+    static constexpr float c3a = 0.5900435899266435f;   // sqrt(35/(2 pi))/4
+    static constexpr float c3b = 2.890611442640554f;    // sqrt(105/pi)/2
+    static constexpr float c3c = 0.4570457994644658f;   // sqrt(21/(2 pi))/4
+    static constexpr float c3d = 0.3731763325901154f;   // sqrt(7/pi)/4
+    static constexpr float c3e = 1.445305721320277f;    // sqrt(105/pi)/4
+};
+
+template <int DEG>
+__device__ __forceinline__ void sh_basis(float x, float y, float z, float* Y) {
+    Y[0] = ShC::c0;
+    if (DEG < 1) return;
+    Y[1] = -ShC::c1 * y;
+    Y[2] = ShC::c1 * z;
+    Y[3] = -ShC::c1 * x;
+    if (DEG < 2) return;
+    const float xx = x * x, yy = y * y, zz = z * z;
+    Y[4] = ShC::c2a * x * y;
+    Y[5] = -ShC::c2a * y * z;
+    Y[6] = ShC::c2b * (2.f * zz - xx - yy);
+    Y[7] = -ShC::c2a * x * z;
+    Y[8] = ShC::c2c * (xx - yy);
+    if (DEG < 3) return;
+    Y[9] = -ShC::c3a * y * (3.f * xx - yy);
+    Y[10] = ShC::c3b * x * y * z;
+    Y[11] = -ShC::c3c * y * (4.f * zz - xx - yy);
+    Y[12] = ShC::c3d * z * (2.f * zz - 3.f * xx - 3.f * yy);
+    Y[13] = -ShC::c3c * x * (4.f * zz - xx - yy);
+    Y[14] = ShC::c3e * z * (xx - yy);
+    Y[15] = -ShC::c3a * x * (xx - 3.f * yy);
+}
+
+// Gradient of sum_k Y_k(d) w_k with respect to the (unit) direction d.
+template <int DEG>
+__device__ __forceinline__ void sh_basis_vjp(float x, float y, float z, const float* w, float g[3]) {
+    g[0] = g[1] = g[2] = 0.f;
+    if (DEG < 1) return;
+    g[0] += -ShC::c1 * w[3];
+    g[1] += -ShC::c1 * w[1];
+    g[2] += ShC::c1 * w[2];
+    if (DEG < 2) return;
+    const float xx = x * x, yy = y * y, zz = z * z;
+    g[0] += ShC::c2a * y * w[4] - ShC::c2a * z * w[7] - 2.f * ShC::c2b * x * w[6] +
+            2.f * ShC::c2c * x * w[8];
+    g[1] += ShC::c2a * x * w[4] - ShC::c2a * z * w[5] - 2.f * ShC::c2b * y * w[6] -
+            2.f * ShC::c2c * y * w[8];
+    g[2] += -ShC::c2a * y * w[5] + 4.f * ShC::c2b * z * w[6] - ShC::c2a * x * w[7];
+    if (DEG < 3) return;
+    g[0] += -ShC::c3a * 6.f * x * y * w[9] + ShC::c3b * y * z * w[10] +
+            ShC::c3c * 2.f * x * y * w[11] - ShC::c3d * 6.f * x * z * w[12] -
+            ShC::c3c * (4.f * zz - 3.f * xx - yy) * w[13] + ShC::c3e * 2.f * x * z * w[14] -
+            ShC::c3a * (3.f * xx - 3.f * yy) * w[15];
+    g[1] += -ShC::c3a * (3.f * xx - 3.f * yy) * w[9] + ShC::c3b * x * z * w[10] -
+            ShC::c3c * (4.f * zz - xx - 3.f * yy) * w[11] - ShC::c3d * 6.f * y * z * w[12] +
+            ShC::c3c * 2.f * x * y * w[13] - ShC::c3e * 2.f * y * z * w[14] +
+            ShC::c3a * 6.f * x * y * w[15];
+    g[2] += ShC::c3b * x * y * w[10] - ShC::c3c * 8.f * y * z * w[11] +
+            ShC::c3d * (6.f * zz - 3.f * xx - 3.f * yy) * w[12] - ShC::c3c * 8.f * x * z * w[13] +
+            ShC::c3e * (xx - yy) * w[14];
+}
+
+// -------------------------------------------------------------------------
+// A record staged in shared memory for one tile: the planes are re-based to
+// the tile's first pixel centre (ox, oy) so that a pixel at offset (lx, ly)
+// within the tile evaluates depth = a lx + b ly + e' with small operands.
+// The forward and backward blends both stage through stage_record() and
+// evaluate through span_*(), so they compute bit-identical spans.
+template <int V> struct Staged {
+    static constexpr int F = Kind<V>::F;
+    float pl[3 * F];   // (a, b, e') per slot
+    float sigma;
+    float rgb[3];
+    float dx0, dy0;    // ox - x_c, oy - y_c
+    int nf;
+    int rec;           // record index (camera * n + primitive)
+};
+
+template <int V>
+__device__ __forceinline__ void stage_record(const float* __restrict__ rec, int r, float ox, float oy,
+                                             Staged<V>& s) {
+    constexpr int F = Kind<V>::F;
+    const float4* src = reinterpret_cast<const float4*>(rec + (size_t)r * Rec<V>::kFloats);
+    float buf[Rec<V>::kFloats];
+#pragma unroll
+    for (int q = 0; q < Rec<V>::kVec4; ++q) {
+        float4 v = __ldg(src + q);
+        buf[4 * q + 0] = v.x; buf[4 * q + 1] = v.y; buf[4 * q + 2] = v.z; buf[4 * q + 3] = v.w;
+    }
+    const float dx0 = __fsub_rn(ox, buf[0]);
+    const float dy0 = __fsub_rn(oy, buf[1]);
+#pragma unroll
+    for (int f = 0; f < F; ++f) {
+        const float a = buf[8 + 3 * f], b = buf[9 + 3 * f], e = buf[10 + 3 * f];
+        s.pl[3 * f] = a;
+        s.pl[3 * f + 1] = b;
+        s.pl[3 * f + 2] = __fmaf_rn(a, dx0, __fmaf_rn(b, dy0, e));
+    }
+    s.sigma = buf[2];
+    s.nf = __float_as_int(buf[3]);
+    s.rgb[0] = buf[4]; s.rgb[1] = buf[5]; s.rgb[2] = buf[6];
+    s.dx0 = dx0; s.dy0 = dy0;
+    s.rec = r;
+}
+
+// Ray/primitive span at tile-local pixel offset (lx, ly): half-space
+// clipping of the pixel ray against the convex primitive (entry = max over
+// entry faces, exit = min over exit faces).  This equals the distance
+// between the two MTIA hits of Sec. 3.2 "Rasterization".
+template <int V>
+__device__ __forceinline__ float span_at(const Staged<V>& s, float lx, float ly) {
+    constexpr int F = Kind<V>::F;
+    float tf = -CUDART_INF_F, tb = CUDART_INF_F;
+#pragma unroll
+    for (int f = 0; f < F; ++f) {
+        const float d = __fmaf_rn(s.pl[3 * f], lx, __fmaf_rn(s.pl[3 * f + 1], ly, s.pl[3 * f + 2]));
+        if (f < s.nf) tf = fmaxf(tf, d); else tb = fminf(tb, d);
+    }
+    return __fsub_rn(tb, tf);
+}
+
+// Same, also returning the arg-max entry slot and arg-min exit slot.
+template <int V>
+__device__ __forceinline__ float span_arg(const Staged<V>& s, float lx, float ly, int& sf, int& sb) {
+    constexpr int F = Kind<V>::F;
+    float tf = -CUDART_INF_F, tb = CUDART_INF_F;
+    sf = 0; sb = F - 1;
+#pragma unroll
+    for (int f = 0; f < F; ++f) {
+        const float d = __fmaf_rn(s.pl[3 * f], lx, __fmaf_rn(s.pl[3 * f + 1], ly, s.pl[3 * f + 2]));
+        if (f < s.nf) { if (d > tf) { tf = d; sf = f; } }
+        else          { if (d < tb) { tb = d; sb = f; } }
+    }
+    return __fsub_rn(tb, tf);
+}
+
+// Opacity of a span, App. "Gradient Computation": o = 1 - exp(-sigma s).
+__device__ __forceinline__ float span_tau(float sigma, float s) {
+    return __expf(-__fmul_rn(sigma, s));
+}
+
+__device__ __forceinline__ int camera_of_tile(const CamsParam& cams, int tile) {
+    int c = 0;
+    while (c + 1 < cams.n && tile >= cams.cam[c + 1].tile_base) ++c;
+    return c;
+}
+
+}  // namespace lp

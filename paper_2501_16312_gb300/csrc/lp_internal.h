@@ -1,0 +1,57 @@
+// Host-side launchers shared between the kernel translation units and the
+// C ABI implementation.  Not part of the public interface.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lp {
+
+struct CamsParam;
+struct PrimsDev;
+
+cudaError_t launch_preprocess(int V, int deg, const PrimsDev& P, const CamsParam& cams, float* rec,
+                              uint32_t* counts, int4* trect, uint32_t* zbits, cudaStream_t st);
+
+cudaError_t launch_chain(int V, int deg, const PrimsDev& P, const CamsParam& cams, const float* rec,
+                         const uint32_t* counts, const float* acc, float* dc, float* dv, float* dop,
+                         float* dsh, int accumulate, cudaStream_t st);
+
+int scan_blocks(long long n);
+cudaError_t launch_scan(const uint32_t* in, long long n, uint32_t* out, uint32_t* block_sums,
+                        uint32_t* total, cudaStream_t st);
+
+cudaError_t launch_emit(const uint32_t* counts, const uint32_t* offsets, const int4* trect,
+                        const uint32_t* zbits, int n, long long n_records, const CamsParam& cams,
+                        uint64_t* keys, uint32_t* vals, long long cap, int* status, cudaStream_t st);
+
+int sort_blocks(long long bound);
+size_t sort_hist_elems(long long bound);
+cudaError_t launch_radix_sort(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1,
+                              const uint32_t* n_dev, long long bound, int key_bits, uint32_t* hist,
+                              uint32_t* scan_tmp, int* passes_out, cudaStream_t st);
+
+cudaError_t launch_ranges(const uint64_t* keys, const uint32_t* n_dev, long long bound,
+                          const int* status, uint2* ranges, int sms, cudaStream_t st);
+
+struct BlendArgs {
+    int grid;
+    const float* rec;
+    const uint32_t* vals;
+    const uint2* ranges;
+    const CamsParam* cams;
+    float bg[3];
+    float* image;          // forward output
+    const float* dimage;   // backward input
+    uint32_t* last;
+    float* tl;
+    float* acc;
+    int* tile_counter;
+    unsigned long long* pair_counts;
+    bool count;
+};
+
+cudaError_t launch_blend_fwd(int V, int batch, const BlendArgs& a, cudaStream_t st);
+cudaError_t launch_blend_bwd(int V, int batch, const BlendArgs& a, cudaStream_t st);
+
+}  // namespace lp

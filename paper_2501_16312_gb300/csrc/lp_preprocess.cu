@@ -1,0 +1,462 @@
+// Per-primitive preprocess (forward) and its backward chain (sm_103a).
+//
+// Forward, Sec. 3.2 "Preprocessing": transform the centre and vertices to
+// camera space, map the vertices into the EWA 3D affine ray space linearised
+// at the centre (App. "Ray Space Approximation"), build the faces' ray-space
+// planes, evaluate Eq. 1's density and the view-dependent SH colour, and
+// bound the projection by a pixel/tile rectangle.
+//
+// Backward, Sec. 3.4 "Preprocessing Backpropagation": chain the per-face
+// plane, colour and density gradients collected by the backward blend through
+// the plane construction, the ray-space map and the view transform to the
+// world-space centre and vertices, the SH coefficients and the opacity.
+//
+// One thread per primitive; the thread loops over the cameras so that each
+// primitive's inputs are read from HBM once per call.
+#include "lp_device.cuh"
+#include "lp_internal.h"
+
+namespace lp {
+
+namespace {
+
+struct Geom {
+    float tc[3];       // camera-space centre (binary32 replay)
+    float xc, yc;      // projected centre
+    float j00, j02, j11, j12;   // rows 0,1 of the EWA Jacobian
+    float j2[3];       // row 2: tc / |tc|
+    float len;         // |tc|
+};
+
+// Camera-space centre, projected centre and the EWA Jacobian at the centre,
+// J = d phi / d t with phi(t) = (fx tx/tz + cx, fy ty/tz + cy, |t|).
+__device__ __forceinline__ bool centre_geom(const CamDev& cm, const float c[3], Geom& g) {
+    xform_rn(cm, c[0], c[1], c[2], g.tc);
+    if (!(g.tc[2] > kNearZ)) return false;
+    const float u = __fdiv_rn(g.tc[0], g.tc[2]);
+    const float w = __fdiv_rn(g.tc[1], g.tc[2]);
+    g.xc = __fadd_rn(__fmul_rn(cm.fx, u), cm.cx);
+    g.yc = __fadd_rn(__fmul_rn(cm.fy, w), cm.cy);
+    g.j00 = __fdiv_rn(cm.fx, g.tc[2]);
+    g.j02 = -__fmul_rn(g.j00, u);
+    g.j11 = __fdiv_rn(cm.fy, g.tc[2]);
+    g.j12 = -__fmul_rn(g.j11, w);
+    g.len = sqrtf(g.tc[0] * g.tc[0] + g.tc[1] * g.tc[1] + g.tc[2] * g.tc[2]);
+    const float il = 1.f / g.len;
+    g.j2[0] = g.tc[0] * il; g.j2[1] = g.tc[1] * il; g.j2[2] = g.tc[2] * il;
+    return true;
+}
+
+// Local ray-space offset q = J (t - tc) of one vertex; d receives t - tc.
+__device__ __forceinline__ void vertex_local(const CamDev& cm, const Geom& g, const float v[3],
+                                             float q[3], float d[3]) {
+    float t[3];
+    xform_rn(cm, v[0], v[1], v[2], t);
+    d[0] = __fsub_rn(t[0], g.tc[0]);
+    d[1] = __fsub_rn(t[1], g.tc[1]);
+    d[2] = __fsub_rn(t[2], g.tc[2]);
+    q[0] = __fadd_rn(__fmul_rn(g.j00, d[0]), __fmul_rn(g.j02, d[2]));
+    q[1] = __fadd_rn(__fmul_rn(g.j11, d[1]), __fmul_rn(g.j12, d[2]));
+    q[2] = g.j2[0] * d[0] + g.j2[1] * d[1] + g.j2[2] * d[2];
+}
+
+// Unnormalised face normal n = (q1 - q0) x (q2 - q0).
+__device__ __forceinline__ void face_normal(const float* q0, const float* q1, const float* q2,
+                                            float n[3]) {
+    const float e1[3] = {q1[0] - q0[0], q1[1] - q0[1], q1[2] - q0[2]};
+    const float e2[3] = {q2[0] - q0[0], q2[1] - q0[1], q2[2] - q0[2]};
+    n[0] = e1[1] * e2[2] - e1[2] * e2[1];
+    n[1] = e1[2] * e2[0] - e1[0] * e2[2];
+    n[2] = e1[0] * e2[1] - e1[1] * e2[0];
+}
+
+// A face is treated as seen exactly edge-on (no depth plane) when its normal
+// has |n_z| below this fraction of |n_x| + |n_y|; its plane is then clamped.
+constexpr float kEdgeOn = 1e-30f;
+
+__device__ __forceinline__ bool plane_degenerate(const float n[3]) {
+    return !(fabsf(n[2]) >= kEdgeOn * (fabsf(n[0]) + fabsf(n[1]))) || n[2] == 0.f;
+}
+
+template <int V, int DEG>
+__global__ void __launch_bounds__(128) k_preprocess(PrimsDev P, CamsParam cams, float* __restrict__ rec,
+                                                    uint32_t* __restrict__ counts,
+                                                    int4* __restrict__ trect,
+                                                    uint32_t* __restrict__ zbits) {
+    constexpr int F = Kind<V>::F;
+    constexpr int K = (DEG + 1) * (DEG + 1);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P.n) return;
+
+    float c[3], v[V][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) c[a] = __ldg(P.centre + 3 * (size_t)i + a);
+#pragma unroll
+    for (int k = 0; k < V; ++k)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) v[k][a] = __ldg(P.verts + ((size_t)i * V + k) * 3 + a);
+    const float alpha = __ldg(P.opacity + i);
+    float sh[K * 3];
+#pragma unroll
+    for (int q = 0; q < K * 3; ++q) sh[q] = __ldg(P.sh + (size_t)i * K * 3 + q);
+
+    // Eq. 1: sigma = -log(1 - 0.99 alpha) / (2 d_min), d_min the smallest
+    // centre-vertex distance (for an octahedron min(d_x, d_y, d_z)).
+    float dmin = CUDART_INF_F;
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+        const float dx = v[k][0] - c[0], dy = v[k][1] - c[1], dz = v[k][2] - c[2];
+        dmin = fminf(dmin, sqrtf(dx * dx + dy * dy + dz * dz));
+    }
+    const float sigma = -log1pf(-kAlphaScale * alpha) / (2.f * dmin);
+
+    for (int cv = 0; cv < cams.n; ++cv) {
+        const CamDev& cm = cams.cam[cv];
+        const size_t r = (size_t)cv * P.n + i;
+        Geom g;
+        const bool vis = centre_geom(cm, c, g);
+        zbits[r] = __float_as_uint(g.tc[2]);
+        if (!vis) {
+            counts[r] = 0;
+            trect[r] = make_int4(1, 1, 0, 0);
+            continue;
+        }
+        float q[V][3];
+        float qxmin = CUDART_INF_F, qxmax = -CUDART_INF_F, qymin = CUDART_INF_F, qymax = -CUDART_INF_F;
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+            float d[3];
+            vertex_local(cm, g, v[k], q[k], d);
+            qxmin = fminf(qxmin, q[k][0]); qxmax = fmaxf(qxmax, q[k][0]);
+            qymin = fminf(qymin, q[k][1]); qymax = fmaxf(qymax, q[k][1]);
+        }
+        // Pixel p is covered when its centre p + 0.5 lies in the projected box.
+        float fx0 = ceilf(__fsub_rn(__fadd_rn(g.xc, qxmin), 0.5f));
+        float fx1 = floorf(__fsub_rn(__fadd_rn(g.xc, qxmax), 0.5f));
+        float fy0 = ceilf(__fsub_rn(__fadd_rn(g.yc, qymin), 0.5f));
+        float fy1 = floorf(__fsub_rn(__fadd_rn(g.yc, qymax), 0.5f));
+        fx0 = fmaxf(fx0, 0.f); fx1 = fminf(fx1, (float)(cm.width - 1));
+        fy0 = fmaxf(fy0, 0.f); fy1 = fminf(fy1, (float)(cm.height - 1));
+        if (fx0 > fx1 || fy0 > fy1) {
+            counts[r] = 0;
+            trect[r] = make_int4(1, 1, 0, 0);
+            continue;
+        }
+        const int T = cams.tile;
+        const int tx0 = (int)fx0 / T, tx1 = (int)fx1 / T, ty0 = (int)fy0 / T, ty1 = (int)fy1 / T;
+        counts[r] = (uint32_t)((tx1 - tx0 + 1) * (ty1 - ty0 + 1));
+        trect[r] = make_int4(tx0, ty0, tx1, ty1);
+
+        // Face planes in the local frame (origin at the ray-space centre,
+        // which lies inside the primitive): outward normal n, entry face iff
+        // n_z < 0; depth - z_c = a x + b y + e with a = -n_x/n_z, b = -n_y/n_z,
+        // e = (n . q0) / n_z.
+        float out[Rec<V>::kFloats];
+        int nf = 0;
+        float pl[F][3];
+        bool front[F];
+#pragma unroll
+        for (int f = 0; f < F; ++f) {
+            int i0, i1, i2;
+            face_vertices<V>(f, i0, i1, i2);
+            float n[3];
+            face_normal(q[i0], q[i1], q[i2], n);
+            const float h = n[0] * q[i0][0] + n[1] * q[i0][1] + n[2] * q[i0][2];
+            const float sgn = h < 0.f ? -1.f : 1.f;
+            n[0] *= sgn; n[1] *= sgn; n[2] *= sgn;
+            float nz = n[2];
+            if (plane_degenerate(n)) {
+                const float m = kEdgeOn * (fabsf(n[0]) + fabsf(n[1]));
+                nz = (n[2] < 0.f) ? -fmaxf(m, 1e-37f) : fmaxf(m, 1e-37f);
+            }
+            const float inz = 1.f / nz;
+            pl[f][0] = -n[0] * inz;
+            pl[f][1] = -n[1] * inz;
+            pl[f][2] = (n[0] * q[i0][0] + n[1] * q[i0][1] + n[2] * q[i0][2]) * inz;
+            front[f] = nz < 0.f;
+            nf += front[f] ? 1 : 0;
+        }
+        uint32_t perm = 0;
+        int sf = 0, sb = nf;
+#pragma unroll
+        for (int f = 0; f < F; ++f) {
+            const int s = front[f] ? sf++ : sb++;
+            perm |= (uint32_t)f << (4 * s);
+            out[8 + 3 * s] = pl[f][0];
+            out[9 + 3 * s] = pl[f][1];
+            out[10 + 3 * s] = pl[f][2];
+        }
+
+        // Colour: rgb = max(0, sum_k Y_k(dir) sh_k + 0.5), dir from the camera
+        // to the centre (3DGS convention, Sec. 3.1).
+        float dir[3] = {c[0] - cm.campos[0], c[1] - cm.campos[1], c[2] - cm.campos[2]};
+        const float idl = rsqrtf(dir[0] * dir[0] + dir[1] * dir[1] + dir[2] * dir[2]);
+        dir[0] *= idl; dir[1] *= idl; dir[2] *= idl;
+        float Y[16];
+        sh_basis<DEG>(dir[0], dir[1], dir[2], Y);
+        float rgb[3];
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            float s = 0.5f;
+#pragma unroll
+            for (int k = 0; k < K; ++k) s = fmaf(Y[k], sh[3 * k + ch], s);
+            rgb[ch] = fmaxf(s, 0.f);
+        }
+        out[0] = g.xc; out[1] = g.yc; out[2] = sigma; out[3] = __int_as_float(nf);
+        out[4] = rgb[0]; out[5] = rgb[1]; out[6] = rgb[2]; out[7] = __uint_as_float(perm);
+        float4* dst = reinterpret_cast<float4*>(rec + r * Rec<V>::kFloats);
+#pragma unroll
+        for (int k = 0; k < Rec<V>::kVec4; ++k)
+            dst[k] = make_float4(out[4 * k], out[4 * k + 1], out[4 * k + 2], out[4 * k + 3]);
+    }
+}
+
+// ------------------------------------------------------------------ backward
+template <int V, int DEG>
+__global__ void __launch_bounds__(128) k_chain(PrimsDev P, CamsParam cams,
+                                               const float* __restrict__ rec,
+                                               const uint32_t* __restrict__ counts,
+                                               const float* __restrict__ acc,
+                                               float* __restrict__ dcentre, float* __restrict__ dverts,
+                                               float* __restrict__ dopacity, float* __restrict__ dsh,
+                                               int accumulate) {
+    constexpr int F = Kind<V>::F;
+    constexpr int K = (DEG + 1) * (DEG + 1);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P.n) return;
+
+    float c[3], v[V][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) c[a] = __ldg(P.centre + 3 * (size_t)i + a);
+#pragma unroll
+    for (int k = 0; k < V; ++k)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) v[k][a] = __ldg(P.verts + ((size_t)i * V + k) * 3 + a);
+    const float alpha = __ldg(P.opacity + i);
+    float sh[K * 3];
+#pragma unroll
+    for (int q = 0; q < K * 3; ++q) sh[q] = __ldg(P.sh + (size_t)i * K * 3 + q);
+    float dmin = CUDART_INF_F;
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+        const float dx = v[k][0] - c[0], dy = v[k][1] - c[1], dz = v[k][2] - c[2];
+        dmin = fminf(dmin, sqrtf(dx * dx + dy * dy + dz * dz));
+    }
+
+    float gc[3] = {0.f, 0.f, 0.f};
+    float gv[V][3];
+#pragma unroll
+    for (int k = 0; k < V; ++k) gv[k][0] = gv[k][1] = gv[k][2] = 0.f;
+    float gsh[K * 3];
+#pragma unroll
+    for (int q = 0; q < K * 3; ++q) gsh[q] = 0.f;
+    float gsigma = 0.f;
+
+    for (int cv = 0; cv < cams.n; ++cv) {
+        const size_t r = (size_t)cv * P.n + i;
+        if (counts[r] == 0) continue;
+        const CamDev& cm = cams.cam[cv];
+        const float* A = acc + r * Acc<V>::kFloats;
+        float ga_rgb[3], ga_sig;
+        ga_rgb[0] = A[3 * F]; ga_rgb[1] = A[3 * F + 1]; ga_rgb[2] = A[3 * F + 2];
+        ga_sig = A[3 * F + 3];
+        const uint32_t perm = __float_as_uint(rec[r * Rec<V>::kFloats + 7]);
+
+        Geom g;
+        centre_geom(cm, c, g);
+        float q[V][3], d[V][3];
+#pragma unroll
+        for (int k = 0; k < V; ++k) vertex_local(cm, g, v[k], q[k], d[k]);
+
+        // planes -> local ray-space vertices q, and the projected centre.
+        // Faces are visited in a fixed order; the record's permutation gives
+        // the slot whose accumulator holds each face's gradient.
+        float gq[V][3];
+#pragma unroll
+        for (int k = 0; k < V; ++k) gq[k][0] = gq[k][1] = gq[k][2] = 0.f;
+        float gxc = 0.f, gyc = 0.f;
+#pragma unroll
+        for (int f = 0; f < F; ++f) {
+            int s = 0;
+#pragma unroll
+            for (int t = 0; t < F; ++t)
+                if (((perm >> (4 * t)) & 15u) == (uint32_t)f) s = t;
+            const float Ga = A[3 * s], Gb = A[3 * s + 1], Ge = A[3 * s + 2];
+            if (Ga == 0.f && Gb == 0.f && Ge == 0.f) continue;
+            int i0, i1, i2;
+            face_vertices<V>(f, i0, i1, i2);
+            float n[3];
+            face_normal(q[i0], q[i1], q[i2], n);
+            if (plane_degenerate(n)) continue;
+            const float inz = 1.f / n[2];
+            const float a = -n[0] * inz, b = -n[1] * inz;
+            const float e = (n[0] * q[i0][0] + n[1] * q[i0][1] + n[2] * q[i0][2]) * inz;
+            // the pixel offset from the projected centre is (x - x_c, y - y_c)
+            gxc -= a * Ge;
+            gyc -= b * Ge;
+            // a = -n_x/n_z, b = -n_y/n_z, e = (n . q0)/n_z
+            float gn[3];
+            gn[0] = (Ge * q[i0][0] - Ga) * inz;
+            gn[1] = (Ge * q[i0][1] - Gb) * inz;
+            gn[2] = (Ge * (q[i0][2] - e) - Ga * a - Gb * b) * inz;
+            const float e1[3] = {q[i1][0] - q[i0][0], q[i1][1] - q[i0][1], q[i1][2] - q[i0][2]};
+            const float e2[3] = {q[i2][0] - q[i0][0], q[i2][1] - q[i0][1], q[i2][2] - q[i0][2]};
+            // n = e1 x e2: dL/de1 = e2 x gn, dL/de2 = gn x e1
+            const float g1[3] = {e2[1] * gn[2] - e2[2] * gn[1], e2[2] * gn[0] - e2[0] * gn[2],
+                                 e2[0] * gn[1] - e2[1] * gn[0]};
+            const float g2[3] = {gn[1] * e1[2] - gn[2] * e1[1], gn[2] * e1[0] - gn[0] * e1[2],
+                                 gn[0] * e1[1] - gn[1] * e1[0]};
+#pragma unroll
+            for (int m = 0; m < 3; ++m) {
+                gq[i1][m] += g1[m];
+                gq[i2][m] += g2[m];
+                gq[i0][m] += Ge * n[m] * inz - g1[m] - g2[m];
+            }
+        }
+
+        // q_k = J (t_k - tc); x_c = phi_x(tc), y_c = phi_y(tc)
+        float gtc[3] = {0.f, 0.f, 0.f};
+        float gJ00 = 0.f, gJ02 = 0.f, gJ11 = 0.f, gJ12 = 0.f, gJ2[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+            const float gd0 = g.j00 * gq[k][0] + g.j2[0] * gq[k][2];
+            const float gd1 = g.j11 * gq[k][1] + g.j2[1] * gq[k][2];
+            const float gd2 = g.j02 * gq[k][0] + g.j12 * gq[k][1] + g.j2[2] * gq[k][2];
+            gJ00 += gq[k][0] * d[k][0];
+            gJ02 += gq[k][0] * d[k][2];
+            gJ11 += gq[k][1] * d[k][1];
+            gJ12 += gq[k][1] * d[k][2];
+            gJ2[0] += gq[k][2] * d[k][0];
+            gJ2[1] += gq[k][2] * d[k][1];
+            gJ2[2] += gq[k][2] * d[k][2];
+            gtc[0] -= gd0; gtc[1] -= gd1; gtc[2] -= gd2;
+            // world vertex: t = R v + T
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+                gv[k][a] += cm.R[a] * gd0 + cm.R[3 + a] * gd1 + cm.R[6 + a] * gd2;
+        }
+        const float tx = g.tc[0], ty = g.tc[1], tz = g.tc[2];
+        const float itz = 1.f / tz, itz2 = itz * itz;
+        // d phi_xy / d tc = J rows 0, 1
+        gtc[0] += g.j00 * gxc;
+        gtc[1] += g.j11 * gyc;
+        gtc[2] += g.j02 * gxc + g.j12 * gyc;
+        // d J / d tc
+        gtc[2] += gJ00 * (-cm.fx * itz2);
+        gtc[0] += gJ02 * (-cm.fx * itz2);
+        gtc[2] += gJ02 * (2.f * cm.fx * tx * itz2 * itz);
+        gtc[2] += gJ11 * (-cm.fy * itz2);
+        gtc[1] += gJ12 * (-cm.fy * itz2);
+        gtc[2] += gJ12 * (2.f * cm.fy * ty * itz2 * itz);
+        {
+            const float il = 1.f / g.len;
+            const float dot = gJ2[0] * g.j2[0] + gJ2[1] * g.j2[1] + gJ2[2] * g.j2[2];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) gtc[a] += (gJ2[a] - g.j2[a] * dot) * il;
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+            gc[a] += cm.R[a] * gtc[0] + cm.R[3 + a] * gtc[1] + cm.R[6 + a] * gtc[2];
+
+        // colour -> SH coefficients and view direction
+        float dir[3] = {c[0] - cm.campos[0], c[1] - cm.campos[1], c[2] - cm.campos[2]};
+        const float dist = sqrtf(dir[0] * dir[0] + dir[1] * dir[1] + dir[2] * dir[2]);
+        const float idl = 1.f / dist;
+        dir[0] *= idl; dir[1] *= idl; dir[2] *= idl;
+        float Y[16];
+        sh_basis<DEG>(dir[0], dir[1], dir[2], Y);
+        float grgb[3];
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            float s = 0.5f;
+#pragma unroll
+            for (int k = 0; k < K; ++k) s = fmaf(Y[k], sh[3 * k + ch], s);
+            grgb[ch] = s > 0.f ? ga_rgb[ch] : 0.f;
+        }
+        float w[16];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            w[k] = sh[3 * k] * grgb[0] + sh[3 * k + 1] * grgb[1] + sh[3 * k + 2] * grgb[2];
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) gsh[3 * k + ch] += Y[k] * grgb[ch];
+        }
+        float gdir[3];
+        sh_basis_vjp<DEG>(dir[0], dir[1], dir[2], w, gdir);
+        const float dd = gdir[0] * dir[0] + gdir[1] * dir[1] + gdir[2] * dir[2];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) gc[a] += (gdir[a] - dir[a] * dd) * idl;
+
+        gsigma += ga_sig;
+    }
+
+    // Eq. 1 with d_min frozen: d sigma / d alpha = 0.99 / ((1 - 0.99 alpha) 2 d_min)
+    const float galpha = gsigma * kAlphaScale / ((1.f - kAlphaScale * alpha) * 2.f * dmin);
+    if (accumulate) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) dcentre[3 * (size_t)i + a] += gc[a];
+#pragma unroll
+        for (int k = 0; k < V; ++k)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) dverts[((size_t)i * V + k) * 3 + a] += gv[k][a];
+        dopacity[i] += galpha;
+#pragma unroll
+        for (int q = 0; q < K * 3; ++q) dsh[(size_t)i * K * 3 + q] += gsh[q];
+    } else {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) dcentre[3 * (size_t)i + a] = gc[a];
+#pragma unroll
+        for (int k = 0; k < V; ++k)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) dverts[((size_t)i * V + k) * 3 + a] = gv[k][a];
+        dopacity[i] = galpha;
+#pragma unroll
+        for (int q = 0; q < K * 3; ++q) dsh[(size_t)i * K * 3 + q] = gsh[q];
+    }
+}
+
+template <int V, int DEG>
+cudaError_t launch_pre_t(const PrimsDev& P, const CamsParam& cams, float* rec, uint32_t* counts,
+                         int4* trect, uint32_t* zbits, cudaStream_t st) {
+    const int bs = 128;
+    const int grid = (P.n + bs - 1) / bs;
+    if (grid > 0) k_preprocess<V, DEG><<<grid, bs, 0, st>>>(P, cams, rec, counts, trect, zbits);
+    return cudaGetLastError();
+}
+
+template <int V, int DEG>
+cudaError_t launch_chain_t(const PrimsDev& P, const CamsParam& cams, const float* rec,
+                           const uint32_t* counts, const float* acc, float* dc, float* dv, float* dop,
+                           float* dsh, int accumulate, cudaStream_t st) {
+    const int bs = 128;
+    const int grid = (P.n + bs - 1) / bs;
+    if (grid > 0)
+        k_chain<V, DEG><<<grid, bs, 0, st>>>(P, cams, rec, counts, acc, dc, dv, dop, dsh, accumulate);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+#define LP_DISPATCH(V, DEG, CALL)                                        \
+    switch (DEG) {                                                       \
+        case 0: return (V == 6) ? CALL(6, 0) : CALL(4, 0);               \
+        case 1: return (V == 6) ? CALL(6, 1) : CALL(4, 1);               \
+        case 2: return (V == 6) ? CALL(6, 2) : CALL(4, 2);               \
+        default: return (V == 6) ? CALL(6, 3) : CALL(4, 3);              \
+    }
+
+cudaError_t launch_preprocess(int V, int deg, const PrimsDev& P, const CamsParam& cams, float* rec,
+                              uint32_t* counts, int4* trect, uint32_t* zbits, cudaStream_t st) {
+#define CALL(v, d) launch_pre_t<v, d>(P, cams, rec, counts, trect, zbits, st)
+    LP_DISPATCH(V, deg, CALL)
+#undef CALL
+}
+
+cudaError_t launch_chain(int V, int deg, const PrimsDev& P, const CamsParam& cams, const float* rec,
+                         const uint32_t* counts, const float* acc, float* dc, float* dv, float* dop,
+                         float* dsh, int accumulate, cudaStream_t st) {
+#define CALL(v, d) launch_chain_t<v, d>(P, cams, rec, counts, acc, dc, dv, dop, dsh, accumulate, st)
+    LP_DISPATCH(V, deg, CALL)
+#undef CALL
+}
+
+}  // namespace lp

@@ -1,0 +1,287 @@
+// Global sorting and tiling (Sec. 3.2 "Global Sorting and Tiling"): exclusive
+// scan of per-record tile counts, key emission, a hand-written stable LSD
+// radix sort of 64-bit (tile << 32 | depth) keys over the used bits, and the
+// per-tile ranges of the sorted list.
+//
+// Every kernel that depends on the tile-list length E reads it from device
+// memory, so the same launch sequence works when E is only known on the
+// device (inside a CUDA graph); the host supplies an upper bound for grids.
+#include "lp_device.cuh"
+#include "lp_internal.h"
+
+namespace lp {
+
+namespace {
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 16;
+constexpr int kScanTile = kScanThreads * kScanItems;   // 4096 elements per block
+
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    return x;
+}
+
+// Exclusive block scan of one value per thread; returns the block total.
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t x, uint32_t& total) {
+    __shared__ uint32_t warp_sums[kScanThreads / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const uint32_t incl = warp_incl_scan(x);
+    if (lane == 31) warp_sums[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        uint32_t s = lane < kScanThreads / 32 ? warp_sums[lane] : 0u;
+        s = warp_incl_scan(s);
+        if (lane < kScanThreads / 32) warp_sums[lane] = s;
+    }
+    __syncthreads();
+    const uint32_t before = w > 0 ? warp_sums[w - 1] : 0u;
+    total = warp_sums[kScanThreads / 32 - 1];
+    __syncthreads();
+    return before + incl - x;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t* __restrict__ in, long long n,
+                                                              uint32_t* __restrict__ block_sums) {
+    const long long base = (long long)blockIdx.x * kScanTile + (long long)threadIdx.x * kScanItems;
+    uint32_t s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k)
+        if (base + k < n) s += in[base + k];
+    uint32_t total;
+    block_excl_scan(s, total);
+    if (threadIdx.x == 0) block_sums[blockIdx.x] = total;
+}
+
+// Single block: exclusive scan of the block sums in place; total -> *sum_out.
+__global__ void __launch_bounds__(kScanThreads) k_scan_sums(uint32_t* __restrict__ sums, int nb,
+                                                            uint32_t* __restrict__ sum_out) {
+    uint32_t carry = 0;
+    for (int base = 0; base < nb; base += kScanThreads) {
+        const int i = base + threadIdx.x;
+        const uint32_t x = i < nb ? sums[i] : 0u;
+        uint32_t total;
+        const uint32_t ex = block_excl_scan(x, total);
+        if (i < nb) sums[i] = carry + ex;
+        carry += total;
+    }
+    if (threadIdx.x == 0 && sum_out) *sum_out = carry;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_down(const uint32_t* __restrict__ in, long long n,
+                                                            const uint32_t* __restrict__ block_off,
+                                                            uint32_t* __restrict__ out) {
+    const long long base = (long long)blockIdx.x * kScanTile + (long long)threadIdx.x * kScanItems;
+    uint32_t v[kScanItems];
+    uint32_t s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        v[k] = base + k < n ? in[base + k] : 0u;
+        s += v[k];
+    }
+    uint32_t total;
+    uint32_t run = block_excl_scan(s, total) + block_off[blockIdx.x];
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        if (base + k < n) out[base + k] = run;
+        run += v[k];
+    }
+}
+
+// ------------------------------------------------------------- key emission
+__global__ void __launch_bounds__(256) k_emit(const uint32_t* __restrict__ counts,
+                                              const uint32_t* __restrict__ offsets,
+                                              const int4* __restrict__ trect,
+                                              const uint32_t* __restrict__ zbits, int n,
+                                              long long n_records, CamsParam cams,
+                                              uint64_t* __restrict__ keys, uint32_t* __restrict__ vals,
+                                              long long cap, int* __restrict__ status) {
+    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n_records) return;
+    const uint32_t cnt = counts[r];
+    if (cnt == 0) return;
+    const long long off = offsets[r];
+    if (off + cnt > cap) {
+        atomicOr(status, kStatusCapacity);
+        return;
+    }
+    const int cv = (int)(r / n);
+    const CamDev& cm = cams.cam[cv];
+    const int4 t = trect[r];
+    const uint64_t z = zbits[r];
+    long long k = off;
+    for (int ty = t.y; ty <= t.w; ++ty)
+        for (int tx = t.x; tx <= t.z; ++tx) {
+            const uint64_t gt = (uint64_t)(cm.tile_base + ty * cm.tiles_x + tx);
+            keys[k] = (gt << 32) | z;
+            vals[k] = (uint32_t)r;
+            ++k;
+        }
+}
+
+// ---------------------------------------------------------- LSD radix sort
+// Digit width 8.  A block owns a contiguous chunk of kSortChunk items; warp w
+// of the block owns the w-th contiguous sub-chunk, which keeps the pass
+// stable: ranks follow (block, warp, round, lane) = input order.
+constexpr int kSortThreads = 256;
+constexpr int kSortWarps = kSortThreads / 32;
+constexpr int kSortPerWarp = 512;
+constexpr int kSortChunk = kSortWarps * kSortPerWarp;   // 4096
+constexpr int kRadix = 256;
+
+__global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint64_t* __restrict__ keys,
+                                                             const uint32_t* __restrict__ n_dev,
+                                                             long long bound, int shift, int nblocks,
+                                                             uint32_t* __restrict__ hist) {
+    __shared__ uint32_t h[kRadix];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const long long n = min((long long)*n_dev, bound);
+    const long long base = (long long)blockIdx.x * kSortChunk;
+    for (int k = threadIdx.x; k < kSortChunk; k += kSortThreads) {
+        const long long q = base + k;
+        if (q < n) atomicAdd(&h[(uint32_t)(keys[q] >> shift) & (kRadix - 1)], 1u);
+    }
+    __syncthreads();
+    hist[(size_t)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
+    const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin,
+    uint64_t* __restrict__ kout, uint32_t* __restrict__ vout, const uint32_t* __restrict__ n_dev,
+    long long bound, int shift, int nblocks, const uint32_t* __restrict__ offs) {
+    __shared__ uint32_t cnt[kSortWarps][kRadix];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const long long n = min((long long)*n_dev, bound);
+    const long long wbase = (long long)blockIdx.x * kSortChunk + (long long)w * kSortPerWarp;
+    for (int d = lane; d < kRadix; d += 32) cnt[w][d] = 0;
+    __syncwarp();
+    // per-warp digit counts
+    for (int k = lane; k < kSortPerWarp; k += 32) {
+        const long long q = wbase + k;
+        if (q < n) atomicAdd(&cnt[w][(uint32_t)(kin[q] >> shift) & (kRadix - 1)], 1u);
+    }
+    __syncthreads();
+    // running offsets: global digit base of this block + earlier warps' counts
+    {
+        const int d = threadIdx.x;   // kSortThreads == kRadix
+        uint32_t run = offs[(size_t)d * nblocks + blockIdx.x];
+#pragma unroll
+        for (int ww = 0; ww < kSortWarps; ++ww) {
+            const uint32_t c = cnt[ww][d];
+            cnt[ww][d] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+    const unsigned lt = (1u << lane) - 1u;
+    for (int k = 0; k < kSortPerWarp; k += 32) {
+        const long long q = wbase + k + lane;
+        const bool ok = q < n;
+        uint64_t key = 0;
+        uint32_t val = 0, digit = kRadix;   // out-of-range lanes form their own group
+        if (ok) {
+            key = kin[q];
+            val = vin[q];
+            digit = (uint32_t)(key >> shift) & (kRadix - 1);
+        }
+        const unsigned peers = __match_any_sync(0xffffffffu, digit);
+        const int rank = __popc(peers & lt);
+        uint32_t pos = 0;
+        if (ok) pos = cnt[w][digit] + rank;
+        __syncwarp();
+        if (ok && rank == 0) cnt[w][digit] += __popc(peers);
+        __syncwarp();
+        if (ok) {
+            kout[pos] = key;
+            vout[pos] = val;
+        }
+    }
+}
+
+// ------------------------------------------------------------- tile ranges
+// Skipped entirely when the emission overflowed: the list then holds stale
+// entries whose tile ids need not be valid, and all ranges stay empty.
+__global__ void __launch_bounds__(256) k_ranges(const uint64_t* __restrict__ keys,
+                                                const uint32_t* __restrict__ n_dev, long long bound,
+                                                const int* __restrict__ status,
+                                                uint2* __restrict__ ranges) {
+    if (*status & kStatusCapacity) return;
+    const long long n = min((long long)*n_dev, bound);
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const uint32_t t = (uint32_t)(keys[i] >> 32);
+        if (i == 0 || (uint32_t)(keys[i - 1] >> 32) != t) ranges[t].x = (uint32_t)i;
+        if (i == n - 1 || (uint32_t)(keys[i + 1] >> 32) != t) ranges[t].y = (uint32_t)(i + 1);
+    }
+}
+
+}  // namespace
+
+int scan_blocks(long long n) { return (int)((n + kScanTile - 1) / kScanTile); }
+
+cudaError_t launch_scan(const uint32_t* in, long long n, uint32_t* out, uint32_t* block_sums,
+                        uint32_t* total, cudaStream_t st) {
+    const int nb = scan_blocks(n);
+    if (nb == 0) {
+        if (total) return cudaMemsetAsync(total, 0, sizeof(uint32_t), st);
+        return cudaSuccess;
+    }
+    k_scan_reduce<<<nb, kScanThreads, 0, st>>>(in, n, block_sums);
+    k_scan_sums<<<1, kScanThreads, 0, st>>>(block_sums, nb, total);
+    k_scan_down<<<nb, kScanThreads, 0, st>>>(in, n, block_sums, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_emit(const uint32_t* counts, const uint32_t* offsets, const int4* trect,
+                        const uint32_t* zbits, int n, long long n_records, const CamsParam& cams,
+                        uint64_t* keys, uint32_t* vals, long long cap, int* status, cudaStream_t st) {
+    if (n_records == 0) return cudaSuccess;
+    const int grid = (int)((n_records + 255) / 256);
+    k_emit<<<grid, 256, 0, st>>>(counts, offsets, trect, zbits, n, n_records, cams, keys, vals, cap,
+                                 status);
+    return cudaGetLastError();
+}
+
+int sort_blocks(long long bound) { return (int)((bound + kSortChunk - 1) / kSortChunk); }
+
+cudaError_t launch_radix_sort(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1,
+                              const uint32_t* n_dev, long long bound, int key_bits,
+                              uint32_t* hist, uint32_t* scan_tmp, int* passes_out, cudaStream_t st) {
+    const int nb = sort_blocks(bound);
+    int passes = 0;
+    if (nb > 0) {
+        uint64_t* kin = k0; uint32_t* vin = v0;
+        uint64_t* kout = k1; uint32_t* vout = v1;
+        for (int shift = 0; shift < key_bits; shift += 8) {
+            k_radix_hist<<<nb, kSortThreads, 0, st>>>(kin, n_dev, bound, shift, nb, hist);
+            cudaError_t e = launch_scan(hist, (long long)kRadix * nb, hist, scan_tmp, nullptr, st);
+            if (e != cudaSuccess) return e;
+            k_radix_scatter<<<nb, kSortThreads, 0, st>>>(kin, vin, kout, vout, n_dev, bound, shift, nb,
+                                                         hist);
+            uint64_t* tk = kin; kin = kout; kout = tk;
+            uint32_t* tv = vin; vin = vout; vout = tv;
+            ++passes;
+        }
+    }
+    *passes_out = passes;
+    return cudaGetLastError();
+}
+
+size_t sort_hist_elems(long long bound) { return (size_t)kRadix * (size_t)sort_blocks(bound); }
+
+cudaError_t launch_ranges(const uint64_t* keys, const uint32_t* n_dev, long long bound,
+                          const int* status, uint2* ranges, int sms, cudaStream_t st) {
+    if (bound == 0) return cudaSuccess;
+    long long want = (bound + 255) / 256;
+    const int grid = (int)(want < (long long)sms * 8 ? want : (long long)sms * 8);
+    k_ranges<<<grid, 256, 0, st>>>(keys, n_dev, bound, status, ranges);
+    return cudaGetLastError();
+}
+
+}  // namespace lp

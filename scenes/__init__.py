@@ -188,9 +188,12 @@ def look_at(eye, target=(0.0, 0.0, 0.0), up=(0.0, 1.0, 0.0)) -> np.ndarray:
 
 
 def make_camera(eye, width, height, fov_y_deg, target=(0.0, 0.0, 0.0)) -> Camera:
+    """Camera whose matrix and intrinsics are exactly representable in binary32,
+    so both the binary32 renderer and a binary64 reference see the same values."""
+    f32 = lambda x: float(np.float32(x))
     fx, fy, cx, cy = intrinsics(width, height, fov_y_deg)
-    return Camera(look_at(eye, target).astype(np.float32), float(fx), float(fy),
-                  float(cx), float(cy), int(width), int(height))
+    return Camera(look_at(eye, target).astype(np.float32), f32(fx), f32(fy),
+                  f32(cx), f32(cy), int(width), int(height))
 
 
 def _unit_vectors(rng, n):

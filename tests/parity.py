@@ -1,0 +1,68 @@
+"""Shared helpers of the GPU parity tests: run the CUDA path through the C ABI
+and compare it with the FP64 oracle on the same seeded inputs.
+
+Tolerances (from the rasterizer's specification):
+  * tile lists, keys, values and per-record tile counts: bit-exact;
+  * images: |gpu - oracle| <= 1e-4 per channel, except pixels the oracle
+    flags as borderline (the transmittance at some step is within 1e-4
+    relative of the 1e-3 stop threshold, so binary32 and binary64 may stop at
+    different primitives); those may number at most max(2, 1e-4 * pixels);
+  * gradients: per array, ||g - g*|| / ||g*|| <= 1e-3.
+"""
+import numpy as np
+
+IMG_TOL = 1e-4
+GRAD_REL_L2 = 1e-3
+
+
+def gpu_forward_backward(rast, scene, cameras, bg, dL=None, device="cuda:0"):
+    import torch
+    from paper_2501_16312_gb300 import Primitives
+    prims = Primitives.from_scene(scene, device)
+    img = rast.forward(prims, cameras, bg)
+    grads = None
+    if dL is not None:
+        g = rast.backward(torch.as_tensor(dL, dtype=torch.float32, device=device))
+        grads = {k: v.cpu().numpy().astype(np.float64) for k, v in g.items()}
+    torch.cuda.synchronize()
+    rast.sync_status()
+    return img.cpu().numpy().astype(np.float64), grads
+
+
+def compare_images(gpu, ref, info, cameras):
+    """Returns (max error over non-borderline pixels, #borderline violations)."""
+    P = sum(c.width * c.height for c in cameras)
+    err = np.zeros(P)
+    off = 0
+    for c in cameras:
+        n = c.width * c.height
+        e = np.abs(gpu[3 * off:3 * (off + n)] - ref[3 * off:3 * (off + n)]).reshape(3, n).max(0)
+        err[off:off + n] = e
+        off += n
+    border = info[:, 2] > 0
+    bad = err > IMG_TOL
+    return float(err[~border].max(initial=0.0)), int((bad & border).sum()), int(bad.sum())
+
+
+def assert_images_match(gpu, ref, info, cameras):
+    P = sum(c.width * c.height for c in cameras)
+    max_clean, n_border_bad, n_bad = compare_images(gpu, ref, info, cameras)
+    assert max_clean <= IMG_TOL, f"max image error {max_clean:.3e} on non-borderline pixels"
+    assert n_border_bad <= max(2, 1e-4 * P), f"{n_border_bad} borderline pixels differ"
+    return max_clean
+
+
+def rel_l2(a, b):
+    a, b = np.asarray(a, np.float64).reshape(-1), np.asarray(b, np.float64).reshape(-1)
+    nb = np.linalg.norm(b)
+    return float(np.linalg.norm(a - b) / nb) if nb > 0 else float(np.linalg.norm(a))
+
+
+def assert_grads_match(gpu, ref, tol=GRAD_REL_L2):
+    out = {}
+    for k in ("centre", "verts", "opacity", "sh"):
+        r = rel_l2(gpu[k], ref[k])
+        out[k] = r
+    bad = {k: v for k, v in out.items() if not v <= tol}
+    assert not bad, f"gradient relative L2 errors {out}"
+    return out

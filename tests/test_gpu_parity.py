@@ -1,0 +1,205 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Sizes are chosen so the oracle finishes in seconds while spanning many tiles
+with ragged edges; the full-size workload is checked on sampled pixels."""
+import numpy as np
+import pytest
+
+import oracle
+import scenes
+from tests.parity import (assert_grads_match, assert_images_match, gpu_forward_backward,
+                          rel_l2)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rast():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2501_16312_gb300 import Rasterizer
+    return Rasterizer(0)
+
+
+def multiview_small():
+    """Mixed-resolution cameras (ragged tile edges) on a scaled-down version of
+    the 1M-tetrahedron box workload."""
+    w = scenes.workload(3, scale=0.004)
+    rng = np.random.default_rng(3)
+    sizes = [(200, 120), (97, 61), (64, 48)]
+    cams = scenes.sphere_cameras(rng, sizes, 6.0, 60.0)
+    return scenes.Workload("tetra4k_3mixed", w.scene, cams)
+
+
+CASES = {
+    "cfg0_tetra64": lambda: scenes.workload(0),
+    "cfg1_octa10k": lambda: scenes.workload(1),
+    "multiview_tetra": multiview_small,
+}
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_tile_lists_bit_exact(rast, case):
+    w = CASES[case]()
+    gpu_forward_backward(rast, w.scene, w.cameras, (0, 0, 0))
+    k, v = rast.debug_keys()
+    ko, vo, co = oracle.keys(w.scene, w.cameras, tile=16)
+    np.testing.assert_array_equal(rast.debug_counts(), co)
+    assert k.shape == ko.shape
+    np.testing.assert_array_equal(k, ko)
+    np.testing.assert_array_equal(v, vo)
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_forward_backward_parity(rast, case):
+    w = CASES[case]()
+    bg = (0.1, 0.2, 0.3)
+    dL = scenes.image_gradient(w, seed=1)
+    img, grads = gpu_forward_backward(rast, w.scene, w.cameras, bg, dL)
+    ref, info, ref_g = oracle.render(w.scene, w.cameras, bg=bg, dL_dimage=dL.astype(np.float64),
+                                     info=True)
+    err = assert_images_match(img, ref, info, w.cameras)
+    rel = assert_grads_match(grads, ref_g)
+    print(f"{case}: max image err {err:.2e}, grad rel L2 {rel}")
+
+
+def test_full_size_sampled_pixels(rast):
+    """The 500k-octahedron, 8 x 1264x832 workload in the launch configuration
+    the benchmark times: sampled pixels of two views against the oracle."""
+    w = scenes.workload(2)
+    img, _ = gpu_forward_backward(rast, w.scene, w.cameras, (0, 0, 0))
+    rng = np.random.default_rng(7)
+    off = 0
+    for ci, cam in enumerate(w.cameras):
+        n = cam.width * cam.height
+        if ci in (0, 5):
+            q = rng.choice(n, 1500, replace=False)
+            px, py = (q % cam.width).astype(np.int32), (q // cam.width).astype(np.int32)
+            ref, info = oracle.render_pixels(w.scene, cam, px, py)
+            got = img[3 * off:3 * (off + n)].reshape(3, n)[:, q].T
+            err = np.abs(got - ref).max(1)
+            clean = info[:, 2] == 0
+            assert err[clean].max() <= 1e-4, err[clean].max()
+            assert (err[~clean] > 1e-4).sum() <= 2
+        off += n
+
+
+def test_permutation_invariance(rast):
+    w = scenes.workload(1, scale=0.3)
+    img, _ = gpu_forward_backward(rast, w.scene, w.cameras, (0, 0, 0))
+    perm = np.random.default_rng(4).permutation(w.scene.n)
+    img_p, _ = gpu_forward_backward(rast, w.scene.subset(perm), w.cameras, (0, 0, 0))
+    np.testing.assert_array_equal(img, img_p)
+
+
+def test_batched_equals_per_view(rast):
+    w = multiview_small()
+    img, _ = gpu_forward_backward(rast, w.scene, w.cameras, (0.2, 0.2, 0.2))
+    parts = [gpu_forward_backward(rast, w.scene, [c], (0.2, 0.2, 0.2))[0] for c in w.cameras]
+    np.testing.assert_array_equal(img, np.concatenate(parts))
+
+
+def test_per_view_accumulated_gradients_equal_batched(rast):
+    import torch
+    from paper_2501_16312_gb300 import Primitives
+    w = multiview_small()
+    dL = scenes.image_gradient(w, seed=2)
+    _, gb = gpu_forward_backward(rast, w.scene, w.cameras, (0, 0, 0), dL)
+    prims = Primitives.from_scene(w.scene, "cuda:0")
+    acc = None
+    off = 0
+    for c in w.cameras:
+        n = 3 * c.width * c.height
+        rast.forward(prims, [c])
+        g = torch.as_tensor(dL[off:off + n], device="cuda:0")
+        acc = rast.backward(g, grads=acc, accumulate=acc is not None)
+        off += n
+    for k in gb:
+        assert rel_l2(acc[k].cpu().numpy(), gb[k]) <= 1e-5, k
+
+
+@pytest.mark.parametrize("kind", ["empty", "culled", "ragged", "huge", "one_pixel"])
+def test_edge_cases(rast, kind):
+    bg = (0.25, 0.5, 0.75)
+    if kind == "empty":
+        sc = scenes.workload(0).scene.subset(np.arange(0))
+        cams = [scenes.make_camera((0, 0, 4), 40, 24, 60)]
+    elif kind == "culled":
+        sc = scenes.workload(0).scene
+        cams = [scenes.make_camera((0, 0, 4), 48, 32, 60, target=(0, 0, 8))]   # looks away
+    elif kind == "ragged":
+        sc = scenes.workload(0).scene
+        cams = [scenes.make_camera((0.3, 0.2, 3.5), 37, 23, 60)]
+    elif kind == "huge":
+        # one primitive around the camera's view axis covering the whole image
+        c = np.array([[0.0, 0.0, 2.5]])
+        R = np.eye(3)[None]
+        v = scenes.octahedra_from_axes(c, R, np.array([[3.0, 2.0, 0.5]]))
+        sh = scenes.sh_from_rgb(np.array([[0.9, 0.1, 0.4]]))[:, None, :]
+        sc = scenes.Scene(6, c.astype(np.float32), v.astype(np.float32),
+                          np.array([0.7], np.float32), sh.astype(np.float32), 0)
+        cams = [scenes.make_camera((0, 0, 4), 160, 96, 60)]
+    else:
+        sc = scenes.workload(0).scene
+        cams = [scenes.make_camera((0, 0, 4), 1, 1, 60)]
+    P = sum(c.width * c.height for c in cams)
+    dL = np.random.default_rng(0).normal(size=3 * P).astype(np.float32)
+    img, grads = gpu_forward_backward(rast, sc, cams, bg, dL)
+    ref, info, ref_g = oracle.render(sc, cams, bg=bg, dL_dimage=dL.astype(np.float64), info=True)
+    assert_images_match(img, ref, info, cams)
+    if kind in ("empty", "culled"):
+        np.testing.assert_array_equal(img.reshape(3, -1), np.repeat(np.array(bg)[:, None], P, 1).astype(np.float32))
+        for k in grads:
+            assert np.all(grads[k] == 0)
+    else:
+        assert_grads_match(grads, ref_g)
+
+
+def test_autograd_function(rast):
+    import torch
+    from paper_2501_16312_gb300 import render
+    w = scenes.workload(0)
+    t = lambda a: torch.tensor(a, device="cuda:0", requires_grad=True)
+    leaves = [t(w.scene.centre), t(w.scene.verts), t(w.scene.opacity), t(w.scene.sh)]
+    img = render(*leaves, w.cameras, kind=w.scene.kind, rasterizer=rast)
+    g = torch.as_tensor(scenes.image_gradient(w), device="cuda:0")
+    (img * g).sum().backward()
+    _, ref_g = oracle.render(w.scene, w.cameras, dL_dimage=g.cpu().numpy().astype(np.float64))
+    for leaf, k in zip(leaves, ("centre", "verts", "opacity", "sh")):
+        assert rel_l2(leaf.grad.cpu().numpy(), ref_g[k]) <= 1e-3, k
+
+
+def test_cuda_graph_capture_replays(rast):
+    import torch
+    from paper_2501_16312_gb300 import Primitives, Rasterizer
+    w = multiview_small()
+    r2 = Rasterizer(0)
+    prims = Primitives.from_scene(w.scene, "cuda:0")
+    P = w.pixels
+    img0 = r2.forward(prims, w.cameras, (0, 0, 0)).clone()
+    g = torch.as_tensor(scenes.image_gradient(w), device="cuda:0")
+    gr0 = {k: v.clone() for k, v in r2.backward(g).items()}
+    st = r2.stats()
+    r2.reserve(st["records"], 2 * st["entries"] + 1024, P, st["tiles"])
+    img = torch.empty(3 * P, device="cuda:0")
+    grads = {k: torch.empty_like(v) for k, v in gr0.items()}
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        r2.forward(prims, w.cameras, (0, 0, 0), images=img)     # warm-up outside capture
+        r2.backward(g, grads=grads)
+    torch.cuda.current_stream().wait_stream(s)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        r2.forward(prims, w.cameras, (0, 0, 0), images=img)
+        r2.backward(g, grads=grads)
+    img.zero_()
+    for k in grads:
+        grads[k].zero_()
+    graph.replay()
+    torch.cuda.synchronize()
+    r2.sync_status()
+    assert torch.equal(img, img0)
+    for k in grads:
+        assert rel_l2(grads[k].cpu().numpy(), gr0[k].cpu().numpy()) <= 1e-5
