@@ -190,11 +190,19 @@ static void keyfields_f32(const orc_prims* P, const orc_camera* cam, int i, orc_
     j00 = fx / tc[2]; j02 = -(j00 * u);
     j11 = fy / tc[2]; j12 = -(j11 * w);
     for (k = 0; k < P->nv; ++k) {
-        float v[3], t[3], d0, d1, d2, qx, qy, a, b;
+        float v[3], w[3], dd[3], d0, d2, d1, qx, qy, a, b;
         int m;
+        /* vertex offset from the centre, rotated into the camera frame */
         for (m = 0; m < 3; ++m) v[m] = (float)P->verts[(size_t)(i * P->nv + k) * 3 + m];
-        f32_transform(M, v, t);
-        d0 = t[0] - tc[0]; d1 = t[1] - tc[1]; d2 = t[2] - tc[2];
+        for (m = 0; m < 3; ++m) w[m] = v[m] - c[m];
+        for (m = 0; m < 3; ++m) {
+            float r0 = M[4 * m + 0] * w[0];
+            float r1 = M[4 * m + 1] * w[1];
+            float r2 = M[4 * m + 2] * w[2];
+            float s = r0 + r1;
+            dd[m] = s + r2;
+        }
+        d0 = dd[0]; d1 = dd[1]; d2 = dd[2];
         a = j00 * d0; b = j02 * d2; qx = a + b;
         a = j11 * d1; b = j12 * d2; qy = a + b;
         if (qx < qxmin) qxmin = qx;

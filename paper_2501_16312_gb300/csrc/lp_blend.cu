@@ -56,7 +56,7 @@ __global__ void __launch_bounds__(kThreads) k_blend_fwd(
         const int ty = lt / cm.tiles_x, tx = lt - ty * cm.tiles_x;
         const int px = tx * kTile + lx, py = ty * kTile + ly;
         const bool inside = px < cm.width && py < cm.height;
-        const float ox = (float)(tx * kTile) + 0.5f, oy = (float)(ty * kTile) + 0.5f;
+        const int tx0 = tx * kTile, ty0 = ty * kTile;
         const uint2 rg = ranges[tile];
         const int n = (int)(rg.y - rg.x);
         float T = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f, tl = 1.f;
@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(kThreads) k_blend_fwd(
         for (int b0 = 0; b0 < n; b0 += BATCH) {
             if (__syncthreads_count(!done) == 0) break;
             const int nb = min(BATCH, n - b0);
-            for (int j = tid; j < nb; j += kThreads) stage_record<V>(rec, vals[rg.x + b0 + j], ox, oy, sm[j]);
+            for (int j = tid; j < nb; j += kThreads) stage_record<V>(rec, vals[rg.x + b0 + j], tx0, ty0, sm[j]);
             __syncthreads();
             if (!done) {
                 for (int j = 0; j < nb; ++j) {
@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(kThreads) k_blend_bwd(
         const int ty = lt / cm.tiles_x, tx = lt - ty * cm.tiles_x;
         const int px = tx * kTile + lx, py = ty * kTile + ly;
         const bool inside = px < cm.width && py < cm.height;
-        const float ox = (float)(tx * kTile) + 0.5f, oy = (float)(ty * kTile) + 0.5f;
+        const int tx0 = tx * kTile, ty0 = ty * kTile;
         const uint2 rg = ranges[tile];
         float g0 = 0.f, g1 = 0.f, g2 = 0.f, tl = 1.f;
         uint32_t last = 0;
@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(kThreads) k_blend_bwd(
             const int lo = max(0, hi - BATCH);
             const int nb = hi - lo;
             __syncthreads();
-            for (int j = tid; j < nb; j += kThreads) stage_record<V>(rec, vals[rg.x + lo + j], ox, oy, sm[j]);
+            for (int j = tid; j < nb; j += kThreads) stage_record<V>(rec, vals[rg.x + lo + j], tx0, ty0, sm[j]);
             __syncthreads();
             for (int j = nb - 1; j >= 0; --j) {
                 const Staged<V>& p = sm[j];
@@ -188,6 +188,7 @@ __global__ void __launch_bounds__(kThreads) k_blend_bwd(
                     gs = dLdo * p.sigma * tau;      // dL/d span
                     gsig = dLdo * s * tau;          // dL/d sigma
                 }
+                // integer pixel offsets from the record's anchor (X0, Y0)
                 const float lxc = (float)lx + p.dx0, lyc = (float)ly + p.dy0;
                 float* A = acc + (size_t)p.rec * ACC;
                 gr0 = warp_sum(gr0); gr1 = warp_sum(gr1); gr2 = warp_sum(gr2); gsig = warp_sum(gsig);
@@ -197,7 +198,7 @@ __global__ void __launch_bounds__(kThreads) k_blend_bwd(
                     atomicAdd(A + 3 * F + 2, gr2);
                     atomicAdd(A + 3 * F + 3, gsig);
                 }
-                // span = exit(x, y) - entry(x, y); plane depth = a lxc + b lyc + e
+                // span = exit - entry; plane depth = a lxc + b lyc + e0
                 unsigned used = __reduce_or_sync(0xffffffffu, c ? ((1u << sf) | (1u << sb)) : 0u);
                 while (used) {
                     const int f = __ffs(used) - 1;

@@ -67,28 +67,54 @@ __device__ __forceinline__ void face_vertices(int f, int& i0, int& i1, int& i2) 
 }
 
 // Projected record of one (camera, primitive) pair, written by the
-// preprocess and read by both blend kernels.  Layout in floats:
-//   [0] x_c  [1] y_c      projected centre (pixels)
+// preprocess and read by both blend kernels.  Layout in 32-bit words:
+//   [0] X0  [1] Y0        integer pixel near the projected centre (int bits)
 //   [2] sigma             density, Eq. 1
-//   [3] nf                number of front-facing (entry) faces, int bits
+//   [3] meta              bits 0-3: nf, the number of entry faces; then 3 bits
+//                         per slot: the face index held by that slot
 //   [4..6] rgb            view-dependent colour
-//   [7] perm              face index of each slot, 4 bits per slot
-//   [8 + 3s .. 10 + 3s]   plane of slot s: depth - z_c = a (x - x_c)
-//                         + b (y - y_c) + e; slots [0, nf) are entry faces,
-//                         [nf, F) exit faces.
+//   [7]                   unused
+//   [8 + 3s .. 10 + 3s]   plane of slot s: depth - z_c = a (px - X0)
+//                         + b (py - Y0) + e0 at the centre of pixel (px, py);
+//                         slots [0, nf) are entry faces, [nf, F) exit faces.
+// Anchoring the planes to an integer pixel keeps every pixel offset an exact
+// integer in binary32, so steep faces lose no accuracy to the offset.
 template <int V> struct Rec {
     static constexpr int F = Kind<V>::F;
     static constexpr int kFloats = 8 + 3 * F;   // 32 (octahedron), 20 (tetrahedron)
     static constexpr int kVec4 = kFloats / 4;
 };
 
+__device__ __forceinline__ int meta_nf(uint32_t meta) { return (int)(meta & 15u); }
+__device__ __forceinline__ int meta_face(uint32_t meta, int slot) {
+    return (int)((meta >> (4 + 3 * slot)) & 7u);
+}
+
 // Per-record gradient accumulator written by the backward blend:
-//   [3s .. 3s+2]  dL/d(a_s, b_s, e_s) for slot s
+//   [3s .. 3s+2]  sums of g * (px - X0, py - Y0, 1) over the pixels where slot
+//                 s bounds the span, g = dL/d(plane depth)
 //   [3F .. 3F+2]  dL/d rgb,  [3F + 3] dL/d sigma
 template <int V> struct Acc {
     static constexpr int F = Kind<V>::F;
     static constexpr int kFloats = 3 * F + 4;   // 28, 16
 };
+
+// -------------------------------------------------------------------------
+// Error-free transformations (Knuth's TwoSum, FMA-based TwoProduct) used to
+// carry the projected centre as an unevaluated sum hi + lo of two floats.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    e = __fsub_rn(b, __fsub_rn(s, a));
+}
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+    p = __fmul_rn(a, b);
+    e = __fmaf_rn(a, b, -p);
+}
 
 // -------------------------------------------------------------------------
 // Binary32 key-field arithmetic.  Culling, the depth key and the pixel
@@ -176,22 +202,22 @@ __device__ __forceinline__ void sh_basis_vjp(float x, float y, float z, const fl
 
 // -------------------------------------------------------------------------
 // A record staged in shared memory for one tile: the planes are re-based to
-// the tile's first pixel centre (ox, oy) so that a pixel at offset (lx, ly)
-// within the tile evaluates depth = a lx + b ly + e' with small operands.
-// The forward and backward blends both stage through stage_record() and
-// evaluate through span_*(), so they compute bit-identical spans.
+// the tile's first pixel (tx0, ty0), an exact integer offset (dx0, dy0) from
+// (X0, Y0), so that pixel (tx0 + lx, ty0 + ly) evaluates depth = a lx + b ly
+// + e'.  The forward and backward blends both stage through stage_record()
+// and evaluate through span_*(), so they compute bit-identical spans.
 template <int V> struct Staged {
     static constexpr int F = Kind<V>::F;
     float pl[3 * F];   // (a, b, e') per slot
     float sigma;
     float rgb[3];
-    float dx0, dy0;    // ox - x_c, oy - y_c
+    float dx0, dy0;    // tx0 - X0, ty0 - Y0 (integers)
     int nf;
     int rec;           // record index (camera * n + primitive)
 };
 
 template <int V>
-__device__ __forceinline__ void stage_record(const float* __restrict__ rec, int r, float ox, float oy,
+__device__ __forceinline__ void stage_record(const float* __restrict__ rec, int r, int tx0, int ty0,
                                              Staged<V>& s) {
     constexpr int F = Kind<V>::F;
     const float4* src = reinterpret_cast<const float4*>(rec + (size_t)r * Rec<V>::kFloats);
@@ -201,8 +227,8 @@ __device__ __forceinline__ void stage_record(const float* __restrict__ rec, int 
         float4 v = __ldg(src + q);
         buf[4 * q + 0] = v.x; buf[4 * q + 1] = v.y; buf[4 * q + 2] = v.z; buf[4 * q + 3] = v.w;
     }
-    const float dx0 = __fsub_rn(ox, buf[0]);
-    const float dy0 = __fsub_rn(oy, buf[1]);
+    const float dx0 = (float)(tx0 - __float_as_int(buf[0]));
+    const float dy0 = (float)(ty0 - __float_as_int(buf[1]));
 #pragma unroll
     for (int f = 0; f < F; ++f) {
         const float a = buf[8 + 3 * f], b = buf[9 + 3 * f], e = buf[10 + 3 * f];
@@ -211,7 +237,7 @@ __device__ __forceinline__ void stage_record(const float* __restrict__ rec, int 
         s.pl[3 * f + 2] = __fmaf_rn(a, dx0, __fmaf_rn(b, dy0, e));
     }
     s.sigma = buf[2];
-    s.nf = __float_as_int(buf[3]);
+    s.nf = meta_nf(__float_as_uint(buf[3]));
     s.rgb[0] = buf[4]; s.rgb[1] = buf[5]; s.rgb[2] = buf[6];
     s.dx0 = dx0; s.dy0 = dy0;
     s.rec = r;

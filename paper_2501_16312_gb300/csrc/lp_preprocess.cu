@@ -21,12 +21,54 @@ namespace lp {
 namespace {
 
 struct Geom {
-    float tc[3];       // camera-space centre (binary32 replay)
-    float xc, yc;      // projected centre
+    float tc[3];       // camera-space centre (binary32 key-field sequence)
+    float xc, yc;      // projected centre (binary32 key-field sequence)
     float j00, j02, j11, j12;   // rows 0,1 of the EWA Jacobian
     float j2[3];       // row 2: tc / |tc|
     float len;         // |tc|
+    int X0, Y0;        // integer pixel anchoring the record's planes
+    float fxo, fyo;    // accurate projected centre minus (X0 + 0.5, Y0 + 0.5)
 };
+
+// Camera-space centre t = R c + T as unevaluated pairs hi + lo.
+__device__ __forceinline__ void xform_df(const CamDev& cm, const float c[3], float hi[3], float lo[3]) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        float s = cm.T[i], l = 0.f;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            float p, pe, s2, se;
+            two_prod(cm.R[3 * i + j], c[j], p, pe);
+            two_sum(s, p, s2, se);
+            s = s2;
+            l = __fadd_rn(l, __fadd_rn(se, pe));
+        }
+        fast_two_sum(s, l, hi[i], lo[i]);
+    }
+}
+
+// x = f (t / z) + cc with t, z given as pairs; result as a pair.  The
+// remainder th - u zh of the correctly rounded quotient is exact.
+__device__ __forceinline__ void project_df(float f, float cc, float th, float tl, float zh, float zl,
+                                           float& xh, float& xl) {
+    const float u = __fdiv_rn(th, zh);
+    float r = __fmaf_rn(-u, zh, th);
+    r = __fadd_rn(r, tl);
+    r = __fmaf_rn(-u, zl, r);
+    const float ul = __fdiv_rn(r, zh);
+    float p, pe, sum, se;
+    two_prod(f, u, p, pe);
+    pe = __fmaf_rn(f, ul, pe);
+    two_sum(p, cc, sum, se);
+    fast_two_sum(sum, __fadd_rn(se, pe), xh, xl);
+}
+
+__device__ __forceinline__ void anchor(float xh, float xl, int& X0, float& fo) {
+    xh = fminf(fmaxf(xh, -16777216.f), 16777216.f);
+    const float f0 = floorf(xh);
+    X0 = (int)f0;
+    fo = __fadd_rn(__fsub_rn(__fsub_rn(xh, f0), 0.5f), xl);
+}
 
 // Camera-space centre, projected centre and the EWA Jacobian at the centre,
 // J = d phi / d t with phi(t) = (fx tx/tz + cx, fy ty/tz + cy, |t|).
@@ -44,17 +86,26 @@ __device__ __forceinline__ bool centre_geom(const CamDev& cm, const float c[3], 
     g.len = sqrtf(g.tc[0] * g.tc[0] + g.tc[1] * g.tc[1] + g.tc[2] * g.tc[2]);
     const float il = 1.f / g.len;
     g.j2[0] = g.tc[0] * il; g.j2[1] = g.tc[1] * il; g.j2[2] = g.tc[2] * il;
+    // accurate projected centre for the plane anchor
+    float th[3], tl[3], xh, xl, yh, yl;
+    xform_df(cm, c, th, tl);
+    project_df(cm.fx, cm.cx, th[0], tl[0], th[2], tl[2], xh, xl);
+    project_df(cm.fy, cm.cy, th[1], tl[1], th[2], tl[2], yh, yl);
+    anchor(xh, xl, g.X0, g.fxo);
+    anchor(yh, yl, g.Y0, g.fyo);
     return true;
 }
 
-// Local ray-space offset q = J (t - tc) of one vertex; d receives t - tc.
+// Local ray-space offset q = J d of one vertex, d = R (v - c) its offset
+// from the centre rotated into the camera frame (binary32 key-field
+// sequence; rotating the small offset keeps its relative accuracy).
 __device__ __forceinline__ void vertex_local(const CamDev& cm, const Geom& g, const float v[3],
-                                             float q[3], float d[3]) {
-    float t[3];
-    xform_rn(cm, v[0], v[1], v[2], t);
-    d[0] = __fsub_rn(t[0], g.tc[0]);
-    d[1] = __fsub_rn(t[1], g.tc[1]);
-    d[2] = __fsub_rn(t[2], g.tc[2]);
+                                             const float c[3], float q[3], float d[3]) {
+    const float w0 = __fsub_rn(v[0], c[0]), w1 = __fsub_rn(v[1], c[1]), w2 = __fsub_rn(v[2], c[2]);
+#pragma unroll
+    for (int m = 0; m < 3; ++m)
+        d[m] = __fadd_rn(__fadd_rn(__fmul_rn(cm.R[3 * m], w0), __fmul_rn(cm.R[3 * m + 1], w1)),
+                         __fmul_rn(cm.R[3 * m + 2], w2));
     q[0] = __fadd_rn(__fmul_rn(g.j00, d[0]), __fmul_rn(g.j02, d[2]));
     q[1] = __fadd_rn(__fmul_rn(g.j11, d[1]), __fmul_rn(g.j12, d[2]));
     q[2] = g.j2[0] * d[0] + g.j2[1] * d[1] + g.j2[2] * d[2];
@@ -126,7 +177,7 @@ __global__ void __launch_bounds__(128) k_preprocess(PrimsDev P, CamsParam cams, 
 #pragma unroll
         for (int k = 0; k < V; ++k) {
             float d[3];
-            vertex_local(cm, g, v[k], q[k], d);
+            vertex_local(cm, g, v[k], c, q[k], d);
             qxmin = fminf(qxmin, q[k][0]); qxmax = fmaxf(qxmax, q[k][0]);
             qymin = fminf(qymin, q[k][1]); qymax = fmaxf(qymax, q[k][1]);
         }
@@ -176,15 +227,16 @@ __global__ void __launch_bounds__(128) k_preprocess(PrimsDev P, CamsParam cams, 
             front[f] = nz < 0.f;
             nf += front[f] ? 1 : 0;
         }
-        uint32_t perm = 0;
+        // re-anchor to pixel (X0, Y0): e0 = e - a fxo - b fyo
+        uint32_t meta = (uint32_t)nf;
         int sf = 0, sb = nf;
 #pragma unroll
         for (int f = 0; f < F; ++f) {
             const int s = front[f] ? sf++ : sb++;
-            perm |= (uint32_t)f << (4 * s);
+            meta |= (uint32_t)f << (4 + 3 * s);
             out[8 + 3 * s] = pl[f][0];
             out[9 + 3 * s] = pl[f][1];
-            out[10 + 3 * s] = pl[f][2];
+            out[10 + 3 * s] = __fmaf_rn(-pl[f][0], g.fxo, __fmaf_rn(-pl[f][1], g.fyo, pl[f][2]));
         }
 
         // Colour: rgb = max(0, sum_k Y_k(dir) sh_k + 0.5), dir from the camera
@@ -202,8 +254,9 @@ __global__ void __launch_bounds__(128) k_preprocess(PrimsDev P, CamsParam cams, 
             for (int k = 0; k < K; ++k) s = fmaf(Y[k], sh[3 * k + ch], s);
             rgb[ch] = fmaxf(s, 0.f);
         }
-        out[0] = g.xc; out[1] = g.yc; out[2] = sigma; out[3] = __int_as_float(nf);
-        out[4] = rgb[0]; out[5] = rgb[1]; out[6] = rgb[2]; out[7] = __uint_as_float(perm);
+        out[0] = __int_as_float(g.X0); out[1] = __int_as_float(g.Y0); out[2] = sigma;
+        out[3] = __uint_as_float(meta);
+        out[4] = rgb[0]; out[5] = rgb[1]; out[6] = rgb[2]; out[7] = 0.f;
         float4* dst = reinterpret_cast<float4*>(rec + r * Rec<V>::kFloats);
 #pragma unroll
         for (int k = 0; k < Rec<V>::kVec4; ++k)
@@ -260,13 +313,13 @@ __global__ void __launch_bounds__(128) k_chain(PrimsDev P, CamsParam cams,
         float ga_rgb[3], ga_sig;
         ga_rgb[0] = A[3 * F]; ga_rgb[1] = A[3 * F + 1]; ga_rgb[2] = A[3 * F + 2];
         ga_sig = A[3 * F + 3];
-        const uint32_t perm = __float_as_uint(rec[r * Rec<V>::kFloats + 7]);
+        const uint32_t meta = __float_as_uint(rec[r * Rec<V>::kFloats + 3]);
 
         Geom g;
         centre_geom(cm, c, g);
         float q[V][3], d[V][3];
 #pragma unroll
-        for (int k = 0; k < V; ++k) vertex_local(cm, g, v[k], q[k], d[k]);
+        for (int k = 0; k < V; ++k) vertex_local(cm, g, v[k], c, q[k], d[k]);
 
         // planes -> local ray-space vertices q, and the projected centre.
         // Faces are visited in a fixed order; the record's permutation gives
@@ -280,8 +333,11 @@ __global__ void __launch_bounds__(128) k_chain(PrimsDev P, CamsParam cams,
             int s = 0;
 #pragma unroll
             for (int t = 0; t < F; ++t)
-                if (((perm >> (4 * t)) & 15u) == (uint32_t)f) s = t;
-            const float Ga = A[3 * s], Gb = A[3 * s + 1], Ge = A[3 * s + 2];
+                if (meta_face(meta, t) == f) s = t;
+            // accumulators hold sums over g (px - X0, py - Y0, 1); the pixel's
+            // offset from the projected centre is (px - X0 - fxo, py - Y0 - fyo)
+            const float Ge = A[3 * s + 2];
+            const float Ga = A[3 * s] - g.fxo * Ge, Gb = A[3 * s + 1] - g.fyo * Ge;
             if (Ga == 0.f && Gb == 0.f && Ge == 0.f) continue;
             int i0, i1, i2;
             face_vertices<V>(f, i0, i1, i2);

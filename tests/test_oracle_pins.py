@@ -306,8 +306,10 @@ def test_permutation_invariance(orc):
 
 def test_keyfields_are_binary32_replay(orc):
     """The culling / depth key / pixel rectangle come from binary32 with one
-    rounding per operation; numpy float32 scalars reproduce them exactly, and
-    the rectangle brackets the binary64 footprint to within one pixel."""
+    rounding per operation (the centre transformed to the camera frame, each
+    vertex's offset from the centre rotated into it and mapped by the ray-space
+    Jacobian); numpy float32 scalars reproduce them exactly, and the rectangle
+    brackets the binary64 footprint to within one pixel."""
     w = scenes.workload(1, scale=0.05)
     sc, cam = w.scene, w.cameras[0]
     pp = orc.preprocess(sc, cam)
@@ -329,9 +331,10 @@ def test_keyfields_are_binary32_replay(orc):
         j00, j11 = f(f(cam.fx) / tc[2]), f(f(cam.fy) / tc[2])
         j02, j12 = -f(j00 * u), -f(j11 * w_)
         qx, qy = [], []
+        c32 = sc.centre[i].astype(np.float32)
         for v in sc.verts[i]:
-            t = tr(v)
-            d = [f(t[k] - tc[k]) for k in range(3)]
+            wv = [f(f(v[k]) - c32[k]) for k in range(3)]
+            d = [f(f(f(M[k, 0] * wv[0]) + f(M[k, 1] * wv[1])) + f(M[k, 2] * wv[2])) for k in range(3)]
             qx.append(f(f(j00 * d[0]) + f(j02 * d[2])))
             qy.append(f(f(j11 * d[1]) + f(j12 * d[2])))
         x0 = max(np.ceil(f(f(xc + min(qx)) - f(0.5))), f(0))
