@@ -1,0 +1,447 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 LinPrim rasterizer: forward + backward Mpixel/s.
+
+One step = the whole hot path over one batch: preprocess, key emission, radix
+sort, tile ranges, front-to-back blend, back-to-front blend backward and the
+chain to world-space gradients, for every camera of the workload.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--config 2|3]
+  python bench.py --impl reference ...      (the FP64 CPU oracle arm)
+
+Default workload: 500,000 capture-like octahedra, SH degree 3, eight
+1264x832 cameras (8.4 Mpixel per step), rendered as one batched launch
+sequence captured in a CUDA graph.  Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "fwd+bwd Mpixel/s at 1080p-class (batched vs per-view, same GB300, ≤1e-4 img err)"
+UNIT = "Mpixel/s"
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--config", type=int, default=2, choices=[1, 2, 3])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-per-view", action="store_true")
+    p.add_argument("--scale", type=float, default=1.0,
+                   help="primitive-count scale of the workload (profiling runs only)")
+    p.add_argument("--cpu-seconds", type=float, default=12.0,
+                   help="target CPU time of the oracle baseline sample")
+    return p.parse_args()
+
+
+# ------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        for r in self.rows:
+            for name, val in zip(self.NAMES, r[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.rows)}
+
+
+# ------------------------------------------------------------------- helpers
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# Algorithmic FP32 work of the blend kernels, in flops (an FMA counts 2):
+#   forward, per iterated (pixel, primitive) pair: F planes x 2 FMA + F
+#   min/max + span subtraction + span test       = 5F + 2
+#   forward, per intersected pair: sigma*s, exp, 1 - tau, T*(1-tau),
+#   3 colour FMA, T*tau, stop test               = 12
+#   backward, per evaluated pair: the same 5F + 2; per contributor: tau,
+#   T division, 3 colour grads, dL/do (3 FMA), suffix colour (3 FMA + 3 mul),
+#   span/sigma grads and the (lx, ly, 1) weights of two faces ~ 40
+def blend_flops(F, iterated, intersected, evaluated_bwd):
+    fwd = (5 * F + 2) * iterated + 12 * intersected
+    bwd = (5 * F + 2) * evaluated_bwd + 40 * intersected
+    return fwd, bwd
+
+
+def hbm_bytes(kind_v, K, n, n_cams, E, passes, tiles):
+    """Algorithmic bytes per launch of the HBM-bound stages."""
+    F = 8 if kind_v == 6 else 4
+    rec = (8 + 3 * F) * 4
+    prim_in = (3 + 3 * kind_v + 1 + 3 * K) * 4
+    return {
+        "preprocess": n * prim_in + n_cams * n * (rec + 4 + 16 + 4),
+        "scan_emit": n_cams * n * (4 + 4 + 4 + 16 + 4) + E * 12,
+        "sort": passes * E * 24,
+        "ranges": E * 8 + tiles * 8,
+        "chain": n * prim_in + n_cams * n * (F * 3 + 4 + 1) * 4 + n * prim_in,
+    }
+
+
+# ---------------------------------------------------------------- CPU oracle
+def cpu_baseline(workload, target_s, gpu_image=None, seed=11):
+    """Time the FP64 oracle (forward + adjoint) on a bounded sample of pixels
+    of camera 0; returns the rate scaled to Mpixel/s."""
+    import numpy as np
+    import oracle
+    cam = workload.cameras[0]
+    rng = np.random.default_rng(seed)
+    n_all = cam.width * cam.height
+
+    def run(npix):
+        q = rng.choice(n_all, npix, replace=False)
+        px, py = (q % cam.width).astype(np.int32), (q // cam.width).astype(np.int32)
+        g = rng.normal(size=(npix, 3))
+        t0 = time.perf_counter()
+        rgb, info, _ = oracle.render_pixels(workload.scene, cam, px, py, bg=workload.bg, dL_dC=g)
+        return time.perf_counter() - t0, q, rgb, info
+
+    dt, _, _, _ = run(64)
+    npix = int(min(n_all, max(256, 64 * target_s / max(dt, 1e-3))))
+    dt, q, rgb, info = run(npix)
+    out = {"value": npix / dt / 1e6, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+           "sample": f"{npix} random pixels of camera 0 ({cam.width}x{cam.height}), forward + "
+                     f"adjoint, binary64, OpenMP over pixels", "seconds": round(dt, 2)}
+    if gpu_image is not None:
+        n = cam.width * cam.height
+        got = gpu_image[:3 * n].reshape(3, n)[:, q].T
+        clean = info[:, 2] == 0
+        out["max_img_err_vs_gpu"] = float(np.abs(got - rgb)[clean].max()) if clean.any() else None
+        out["borderline_pixels"] = int((~clean).sum())
+    return out
+
+
+def reference_arm(args, workload):
+    """--impl reference: the FP64 oracle on the host cores, each step a
+    bounded sample of the workload's pixels (forward + adjoint)."""
+    import numpy as np
+    import oracle
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    cam = workload.cameras[0]
+    n_all = cam.width * cam.height
+    rng = np.random.default_rng(5)
+    per_step_s = max(1.0, min(8.0, 150.0 / max(1, args.steps + args.warmup)))
+
+    def step(npix):
+        q = rng.choice(n_all, npix, replace=False)
+        px, py = (q % cam.width).astype(np.int32), (q // cam.width).astype(np.int32)
+        g = rng.normal(size=(npix, 3))
+        t0 = time.perf_counter()
+        oracle.render_pixels(workload.scene, cam, px, py, bg=workload.bg, dL_dC=g)
+        return time.perf_counter() - t0
+
+    dt = step(64)
+    npix = int(min(n_all, max(256, 64 * per_step_s / max(dt, 1e-3))))
+    for _ in range(args.warmup):
+        step(npix)
+    times = [step(npix) for _ in range(args.steps)]
+    total = sum(times)
+    value = npix * args.steps / total / 1e6
+    sample = (f"{npix} random pixels of camera 0 ({cam.width}x{cam.height}) per step, "
+              "forward + adjoint, binary64, OpenMP over pixels")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_dict(args, workload),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def config_dict(args, w):
+    s = w.scene
+    return {"workload": w.name + f" (workload {args.config})",
+            "primitives": s.n, "kind": "octahedron" if s.kind == 6 else "tetrahedron",
+            "sh_degree": s.sh_degree, "cameras": len(w.cameras),
+            "resolutions": sorted({f"{c.width}x{c.height}" for c in w.cameras}),
+            "pixels_per_step": w.pixels, "tile": 16,
+            "form": "batched: all cameras in one launch sequence, fwd+bwd captured in one CUDA graph",
+            "l2": "inputs larger than L2 (primitives, records, tile lists and images > 129 MB)",
+            "parallelism": f"replicas x{args.gpus}"}
+
+
+# ------------------------------------------------------------------- our arm
+def ours(args, workload):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    import scenes
+    from paper_2501_16312_gb300 import Primitives, Rasterizer
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    w = workload
+    P = w.pixels
+    rast = Rasterizer(local)
+    prims = Primitives.from_scene(w.scene, dev)
+    dL = torch.as_tensor(scenes.image_gradient(w), device=dev)
+    img = torch.empty(3 * P, device=dev)
+    grads = dict(centre=torch.empty_like(prims.centre), verts=torch.empty_like(prims.verts),
+                 opacity=torch.empty_like(prims.opacity), sh=torch.empty_like(prims.sh))
+
+    # size the workspace with one plain call, then capture fwd+bwd in a graph
+    rast.forward(prims, w.cameras, w.bg, images=img)
+    rast.backward(dL, grads=grads)
+    torch.cuda.synchronize()
+    st = rast.stats()
+    E = st["entries"]
+    rast.reserve(st["records"], int(E * 1.1) + 4096, P, st["tiles"])
+    rast.set_timing(True)
+    side = torch.cuda.Stream(dev)
+    side.wait_stream(torch.cuda.current_stream(dev))
+    with torch.cuda.stream(side):
+        rast.forward(prims, w.cameras, w.bg, images=img)
+        rast.backward(dL, grads=grads)
+    torch.cuda.current_stream(dev).wait_stream(side)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        rast.forward(prims, w.cameras, w.bg, images=img)
+        rast.backward(dL, grads=grads)
+    stream = torch.cuda.current_stream(dev)
+
+    for _ in range(args.warmup):
+        graph.replay()
+    torch.cuda.synchronize()
+    rast.sync_status()
+
+    clocks = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    stage_sum = {}
+    step_ms = []
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    for _ in range(args.steps):
+        ev0.record(stream)
+        graph.replay()
+        ev1.record(stream)
+        ev1.synchronize()
+        step_ms.append(ev0.elapsed_time(ev1))
+        for k, v in rast.stage_times().items():
+            stage_sum[k] = stage_sum.get(k, 0.0) + v
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    rast.sync_status()
+    t_step = max_over_ranks(sum(step_ms) / len(step_ms))
+    stages = {k: v / args.steps for k, v in stage_sum.items()}
+    value = world * P / (t_step * 1e-3) / 1e6
+
+    # ---- per-view form: one camera per launch sequence, plain (not captured)
+    per_view = None
+    if not args.no_per_view:
+        rast.set_timing(False)
+        pv_img = torch.empty(3 * P, device=dev)
+        offs = np.cumsum([0] + [3 * c.width * c.height for c in w.cameras])
+
+        def per_view_step():
+            for ci, cam in enumerate(w.cameras):
+                rast.forward(prims, [cam], w.bg, images=pv_img[offs[ci]:offs[ci + 1]])
+                rast.backward(dL[offs[ci]:offs[ci + 1]], grads=grads, accumulate=ci > 0)
+
+        for _ in range(max(2, args.warmup // 2)):
+            per_view_step()
+        torch.cuda.synchronize()
+        barrier()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            per_view_step()
+        ev1.record(stream)
+        ev1.synchronize()
+        t_pv = max_over_ranks(ev0.elapsed_time(ev1) / args.steps)
+        per_view = {"value": world * P / (t_pv * 1e-3) / 1e6, "ms_per_step": t_pv,
+                    "form": "one camera per launch sequence, not captured, same kernels",
+                    "batched_over_per_view": t_pv / t_step}
+
+    # ---- end to end through the public API with host buffers
+    host = {k: getattr(prims, k).cpu().pin_memory() for k in ("centre", "verts", "opacity", "sh")}
+    h_dL = dL.cpu().pin_memory()
+    h_img = torch.empty(3 * P, pin_memory=True)
+    h_grads = {k: torch.empty(v.shape, pin_memory=True) for k, v in grads.items()}
+    d_in = {k: torch.empty_like(getattr(prims, k)) for k in host}
+    d_dL = torch.empty_like(dL)
+    e2e_prims = Primitives(prims.kind, d_in["centre"], d_in["verts"], d_in["opacity"], d_in["sh"],
+                           prims.sh_degree)
+    e_img = torch.empty(3 * P, device=dev)
+    e_grads = {k: torch.empty_like(v) for k, v in grads.items()}
+
+    def e2e_step():
+        for k in host:
+            d_in[k].copy_(host[k], non_blocking=True)
+        d_dL.copy_(h_dL, non_blocking=True)
+        rast.forward(e2e_prims, w.cameras, w.bg, images=e_img)
+        rast.backward(d_dL, grads=e_grads)
+        h_img.copy_(e_img, non_blocking=True)
+        for k in e_grads:
+            h_grads[k].copy_(e_grads[k], non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    t_e2e = max_over_ranks(max(ev0.elapsed_time(ev1), 1000 * (time.perf_counter() - t0)) / args.steps)
+    h2d = sum(v.numel() * 4 for v in host.values()) + h_dL.numel() * 4
+    d2h = h_img.numel() * 4 + sum(v.numel() * 4 for v in h_grads.values())
+    e2e = {"value": world * P / (t_e2e * 1e-3) / 1e6, "unit": UNIT, "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": d2h, "ms_per_step": t_e2e,
+           "path": "pinned host -> device, lp_render_forward + lp_render_backward, device -> host"}
+
+    # ---- roofline of the dominant kernel
+    graph.replay()
+    torch.cuda.synchronize()
+    iterated, intersected = rast.count_pairs()
+    last, _ = rast.pixel_state()
+    evaluated_bwd = int(last.astype(np.int64).sum())
+    st = rast.stats()
+    F = 8 if w.scene.kind == 6 else 4
+    fl_fwd, fl_bwd = blend_flops(F, iterated, intersected, evaluated_bwd)
+    peaks, peak_src = measured_peaks()
+    props = torch.cuda.get_device_properties(dev)
+    sm_max = peaks.get("sm_max_mhz") or clk.get("sm_max_mhz") or 2070.0
+    alu_peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12   # TFLOP/s
+    hb = hbm_bytes(w.scene.kind, (w.scene.sh_degree + 1) ** 2, w.scene.n, len(w.cameras),
+                   st["entries"], st["sort_passes"], st["tiles"])
+    dom = max(stages, key=stages.get)
+    if dom in ("blend_fwd", "blend_bwd"):
+        work = fl_fwd if dom == "blend_fwd" else fl_bwd
+        achieved = work / (stages[dom] * 1e-3) / 1e12
+        roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": alu_peak,
+                "unit": "TFLOP/s", "frac": achieved / alu_peak, "traffic": None,
+                "peak_source": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 flop x "
+                               f"{sm_max:.0f} MHz ({peak_src} max clock)"}
+    else:
+        achieved = hb[dom] / (stages[dom] * 1e-3) / 1e9
+        roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                "peak_source": f"{peak_src} copy bandwidth"}
+
+    stage_report = {}
+    for k, ms in stages.items():
+        if k in hb:
+            stage_report[k] = {"ms": ms, "GB/s": hb[k] / (ms * 1e-3) / 1e9 if ms > 0 else None}
+        elif k == "blend_fwd":
+            stage_report[k] = {"ms": ms, "TFLOP/s": fl_fwd / (ms * 1e-3) / 1e12 if ms > 0 else None}
+        else:
+            stage_report[k] = {"ms": ms, "TFLOP/s": fl_bwd / (ms * 1e-3) / 1e12 if ms > 0 else None}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(w, args.cpu_seconds, gpu_image=img.cpu().numpy().astype(np.float64))
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": config_dict(args, w), "per_view": per_view, "e2e": e2e,
+                "gpu_launches": (st["launches_fwd"] + st["launches_bwd"]) * args.steps,
+                "roofline": roof, "stages": stage_report, "clocks": clk,
+                "workload_counts": {"records": st["records"], "tile_list_entries": st["entries"],
+                                    "iterated_pairs": iterated, "intersected_pairs": intersected,
+                                    "bwd_evaluated_pairs": evaluated_bwd,
+                                    "sort_passes": st["sort_passes"]},
+                "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse_args()
+    import scenes
+    w = scenes.workload(args.config, scale=args.scale)
+    if args.impl == "reference":
+        reference_arm(args, w)
+    else:
+        ours(args, w)
+
+
+if __name__ == "__main__":
+    main()

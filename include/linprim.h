@@ -112,7 +112,21 @@ typedef struct {
     long long pixels;     /* pixels over all cameras */
     int sort_passes;      /* radix passes of the last sort */
     int key_bits;         /* key bits sorted */
+    int launches_fwd;     /* kernels the last forward launched */
+    int launches_bwd;     /* kernels a backward launches */
 } lp_stats;
+
+/* Stages timed by lp_stage_times, in launch order. */
+enum {
+    LP_STAGE_PREPROCESS = 0,   /* A1: project, planes, density, colour, rectangle */
+    LP_STAGE_SCAN_EMIT = 1,    /* A2: scan of tile counts, key emission */
+    LP_STAGE_SORT = 2,         /* A3: radix sort of the tile list */
+    LP_STAGE_RANGES = 3,       /* A4: per-tile ranges */
+    LP_STAGE_BLEND_FWD = 4,    /* A5: front-to-back blend */
+    LP_STAGE_BLEND_BWD = 5,    /* A6: back-to-front blend backward */
+    LP_STAGE_CHAIN = 6,        /* A7: chain to world-space features */
+    LP_NUM_STAGES = 7
+};
 
 typedef struct lp_ctx lp_ctx;
 
@@ -193,6 +207,15 @@ lp_status lp_debug_pixel_state(lp_ctx* ctx, unsigned int* last, float* T_last, l
  * copy of the blend): iterated and intersected (pixel, primitive) pairs as
  * in the paper's App. "Rendering Performance", Table 7.                    */
 lp_status lp_count_pairs(lp_ctx* ctx, long long* iterated, long long* intersected);
+
+/* Per-stage device timing.  When enabled, forward and backward record CUDA
+ * events between their stages on the call's stream (inside stream capture
+ * they become event-record nodes of the graph, re-recorded on each replay).
+ * lp_stage_times waits for the last recorded events and writes the duration
+ * of each stage of the most recent forward/backward, in milliseconds, to
+ * ms[LP_NUM_STAGES] (host).  Stages not run yet read as 0.                  */
+lp_status lp_set_timing(lp_ctx* ctx, int enabled);
+lp_status lp_stage_times(lp_ctx* ctx, float* ms);
 
 /* Description of the last error on this context ("" if none).             */
 const char* lp_last_error(lp_ctx* ctx);

@@ -183,6 +183,14 @@ class Rasterizer:
                       "lp_debug_pixel_state")
         return last[:m], tl[:m]
 
+    def set_timing(self, enabled=True):
+        _native.check(self.ctx, self.lib.lp_set_timing(self.ctx, int(bool(enabled))), "lp_set_timing")
+
+    def stage_times(self) -> dict:
+        ms = (C.c_float * len(_native.STAGES))()
+        _native.check(self.ctx, self.lib.lp_stage_times(self.ctx, ms), "lp_stage_times")
+        return dict(zip(_native.STAGES, [float(x) for x in ms]))
+
     def count_pairs(self):
         a, b = C.c_longlong(0), C.c_longlong(0)
         _native.check(self.ctx, self.lib.lp_count_pairs(self.ctx, C.byref(a), C.byref(b)),

@@ -18,7 +18,8 @@ LP_MAX_CAMERAS = 32
 EXPORTS = ("lp_create", "lp_destroy", "lp_set_tuning", "lp_get_tuning", "lp_reserve",
            "lp_render_forward", "lp_render_backward", "lp_sync_status", "lp_get_stats",
            "lp_debug_keys", "lp_debug_counts", "lp_debug_pixel_state", "lp_count_pairs",
-           "lp_last_error", "lp_status_string")
+           "lp_last_error", "lp_status_string", "lp_set_timing", "lp_stage_times")
+STAGES = ("preprocess", "scan_emit", "sort", "ranges", "blend_fwd", "blend_bwd", "chain")
 
 
 class lp_camera(C.Structure):
@@ -39,7 +40,8 @@ class lp_tuning(C.Structure):
 
 class lp_stats(C.Structure):
     _fields_ = [("records", C.c_longlong), ("entries", C.c_longlong), ("tiles", C.c_longlong),
-                ("pixels", C.c_longlong), ("sort_passes", C.c_int), ("key_bits", C.c_int)]
+                ("pixels", C.c_longlong), ("sort_passes", C.c_int), ("key_bits", C.c_int),
+                ("launches_fwd", C.c_int), ("launches_bwd", C.c_int)]
 
 
 class LinPrimError(RuntimeError):
@@ -81,6 +83,8 @@ def load(path: str = LIB_PATH):
     L.lp_last_error.restype = C.c_char_p
     L.lp_status_string.argtypes = [i]
     L.lp_status_string.restype = C.c_char_p
+    L.lp_set_timing.argtypes = [vp, i]
+    L.lp_stage_times.argtypes = [vp, C.POINTER(C.c_float)]
     for name in EXPORTS:
         getattr(L, name)
     _lib = L

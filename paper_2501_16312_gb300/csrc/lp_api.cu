@@ -53,7 +53,13 @@ struct lp_ctx {
     float bg[3] = {0.f, 0.f, 0.f};
     long long records = 0, pixels = 0, tiles = 0, E_bound = 0, E_host = -1;
     int key_bits = 0, sort_passes = 0;
+    int launches_fwd = 0;
     bool result_in_1 = false;
+
+    // stage timing: events 0..5 bracket the forward stages, 6..8 the backward
+    bool timing = false;
+    cudaEvent_t ev[9] = {};
+    bool fwd_timed = false, bwd_timed = false;
 };
 
 namespace {
@@ -176,6 +182,11 @@ lp_status build_cams(lp_ctx* ctx, const lp_camera* cams, int n_cams, int tile, l
     return LP_OK;
 }
 
+void mark(lp_ctx* ctx, cudaStream_t st, int i, bool cap_mode) {
+    if (!ctx->timing) return;
+    cudaEventRecordWithFlags(ctx->ev[i], st, cap_mode ? cudaEventRecordExternal : cudaEventRecordDefault);
+}
+
 int bits_for(long long n) {   // bits needed to represent values 0 .. n-1
     int b = 0;
     while ((1ll << b) < n) ++b;
@@ -242,6 +253,8 @@ void lp_destroy(lp_ctx* ctx) {
     if (ctx->d_tile_counter) cudaFree(ctx->d_tile_counter);
     if (ctx->d_pairs) cudaFree(ctx->d_pairs);
     if (ctx->h_E) cudaFreeHost(ctx->h_E);
+    for (cudaEvent_t& e : ctx->ev)
+        if (e) cudaEventDestroy(e);
     delete ctx;
 }
 
@@ -326,8 +339,10 @@ lp_status lp_render_forward(lp_ctx* ctx, const lp_prims* prims, const lp_camera*
     LP_TRY(ensure(ctx, ctx->tl, pixels, cap_mode, "pixel state"));
 
     lp::PrimsDev P{prims->n, prims->centre, prims->verts, prims->opacity, prims->sh};
+    mark(ctx, st, 0, cap_mode);
     LP_CUDA(lp::launch_preprocess(V, prims->sh_degree, P, cp, ctx->rec.p, ctx->counts.p, ctx->trect.p,
                                   ctx->zbits.p, st));
+    mark(ctx, st, 1, cap_mode);
     LP_CUDA(lp::launch_scan(ctx->counts.p, records, ctx->offsets.p, ctx->scan_tmp.p, ctx->d_E, st));
 
     long long bound;
@@ -353,6 +368,7 @@ lp_status lp_render_forward(lp_ctx* ctx, const lp_prims* prims, const lp_camera*
 
     LP_CUDA(lp::launch_emit(ctx->counts.p, ctx->offsets.p, ctx->trect.p, ctx->zbits.p, prims->n, records,
                             cp, ctx->keys0.p, ctx->vals0.p, bound, ctx->d_status, st));
+    mark(ctx, st, 2, cap_mode);
     const int key_bits = 32 + bits_for(tiles);
     int passes = 0;
     LP_CUDA(lp::launch_radix_sort(ctx->keys0.p, ctx->vals0.p, ctx->keys1.p, ctx->vals1.p, ctx->d_E, bound,
@@ -360,8 +376,10 @@ lp_status lp_render_forward(lp_ctx* ctx, const lp_prims* prims, const lp_camera*
     const bool in1 = (passes & 1) != 0;
     const uint64_t* skeys = in1 ? ctx->keys1.p : ctx->keys0.p;
     const uint32_t* svals = in1 ? ctx->vals1.p : ctx->vals0.p;
+    mark(ctx, st, 3, cap_mode);
     LP_CUDA(cudaMemsetAsync(ctx->ranges.p, 0, (size_t)(tiles > 0 ? tiles : 1) * sizeof(uint2), st));
     LP_CUDA(lp::launch_ranges(skeys, ctx->d_E, bound, ctx->d_status, ctx->ranges.p, ctx->sms, st));
+    mark(ctx, st, 4, cap_mode);
 
     lp::BlendArgs a{};
     a.grid = (int)(tiles < (long long)ctx->sms * ctx->tune.blocks_per_sm ? tiles
@@ -379,6 +397,10 @@ lp_status lp_render_forward(lp_ctx* ctx, const lp_prims* prims, const lp_camera*
     a.count = false;
     LP_CUDA(cudaMemsetAsync(ctx->d_tile_counter, 0, sizeof(int), st));
     if (a.grid > 0) LP_CUDA(lp::launch_blend_fwd(V, ctx->tune.batch, a, st));
+    mark(ctx, st, 5, cap_mode);
+    ctx->fwd_timed = ctx->timing;
+    ctx->launches_fwd = 1 + (records > 0 ? 3 : 0) + (records > 0 ? 1 : 0) + 5 * passes +
+                        (bound > 0 ? 1 : 0) + (a.grid > 0 ? 1 : 0);
 
     ctx->have_fwd = true;
     ctx->prims = *prims;
@@ -407,6 +429,7 @@ lp_status lp_render_backward(lp_ctx* ctx, const float* dL_dimages, float* dcentr
     cudaStream_t st = (cudaStream_t)stream;
     const bool cap_mode = capturing(st);
     const int V = pr.kind;
+    mark(ctx, st, 6, cap_mode);
     const long long acc_n = (ctx->records > 0 ? ctx->records : 1) * acc_floats(V);
     LP_TRY(ensure(ctx, ctx->acc, acc_n, cap_mode, "gradient accumulators"));
     LP_CUDA(cudaMemsetAsync(ctx->acc.p, 0, (size_t)acc_n * sizeof(float), st));
@@ -427,10 +450,13 @@ lp_status lp_render_backward(lp_ctx* ctx, const float* dL_dimages, float* dcentr
     a.tile_counter = ctx->d_tile_counter + 1;
     LP_CUDA(cudaMemsetAsync(ctx->d_tile_counter + 1, 0, sizeof(int), st));
     if (a.grid > 0) LP_CUDA(lp::launch_blend_bwd(V, ctx->tune.batch, a, st));
+    mark(ctx, st, 7, cap_mode);
 
     lp::PrimsDev P{pr.n, pr.centre, pr.verts, pr.opacity, pr.sh};
     LP_CUDA(lp::launch_chain(V, pr.sh_degree, P, ctx->cams, ctx->rec.p, ctx->counts.p, ctx->acc.p, dcentre,
                              dverts, dopacity, dsh, accumulate, st));
+    mark(ctx, st, 8, cap_mode);
+    ctx->bwd_timed = ctx->timing;
     return LP_OK;
 }
 
@@ -462,6 +488,35 @@ lp_status lp_get_stats(lp_ctx* ctx, lp_stats* out) {
     out->pixels = ctx->pixels;
     out->sort_passes = ctx->sort_passes;
     out->key_bits = ctx->key_bits;
+    out->launches_fwd = ctx->launches_fwd;
+    out->launches_bwd = (ctx->tiles > 0 ? 1 : 0) + (ctx->prims.n > 0 ? 1 : 0);
+    return LP_OK;
+}
+
+lp_status lp_set_timing(lp_ctx* ctx, int enabled) {
+    if (!ctx) return LP_ERR_INVALID;
+    LP_CUDA(cudaSetDevice(ctx->device));
+    if (enabled)
+        for (cudaEvent_t& e : ctx->ev)
+            if (!e) LP_CUDA(cudaEventCreate(&e));
+    ctx->timing = enabled != 0;
+    return LP_OK;
+}
+
+lp_status lp_stage_times(lp_ctx* ctx, float* ms) {
+    if (!ctx || !ms) return LP_ERR_INVALID;
+    for (int i = 0; i < LP_NUM_STAGES; ++i) ms[i] = 0.f;
+    if (!ctx->timing) return fail(ctx, LP_ERR_STATE, "timing is not enabled");
+    LP_CUDA(cudaSetDevice(ctx->device));
+    if (ctx->fwd_timed) {
+        LP_CUDA(cudaEventSynchronize(ctx->ev[5]));
+        for (int i = 0; i < 5; ++i) LP_CUDA(cudaEventElapsedTime(&ms[i], ctx->ev[i], ctx->ev[i + 1]));
+    }
+    if (ctx->bwd_timed) {
+        LP_CUDA(cudaEventSynchronize(ctx->ev[8]));
+        LP_CUDA(cudaEventElapsedTime(&ms[LP_STAGE_BLEND_BWD], ctx->ev[6], ctx->ev[7]));
+        LP_CUDA(cudaEventElapsedTime(&ms[LP_STAGE_CHAIN], ctx->ev[7], ctx->ev[8]));
+    }
     return LP_OK;
 }
 
