@@ -155,8 +155,12 @@ def cpu_baseline(workload, target_s, gpu_image=None, seed=11):
         rgb, info, _ = oracle.render_pixels(workload.scene, cam, px, py, bg=workload.bg, dL_dC=g)
         return time.perf_counter() - t0, q, rgb, info
 
-    dt, _, _, _ = run(64)
-    npix = int(min(n_all, max(256, 64 * target_s / max(dt, 1e-3))))
+    # fixed (preprocess + sort of all primitives) and per-pixel cost
+    t1 = run(256)[0]
+    t2 = run(1024)[0]
+    per_px = max((t2 - t1) / 768, 1e-7)
+    fixed = max(t1 - 256 * per_px, 0.0)
+    npix = int(min(n_all, max(1024, (target_s - fixed) / per_px)))
     dt, q, rgb, info = run(npix)
     out = {"value": npix / dt / 1e6, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
            "sample": f"{npix} random pixels of camera 0 ({cam.width}x{cam.height}), forward + "
@@ -191,8 +195,10 @@ def reference_arm(args, workload):
         oracle.render_pixels(workload.scene, cam, px, py, bg=workload.bg, dL_dC=g)
         return time.perf_counter() - t0
 
-    dt = step(64)
-    npix = int(min(n_all, max(256, 64 * per_step_s / max(dt, 1e-3))))
+    t1, t2 = step(256), step(1024)
+    per_px = max((t2 - t1) / 768, 1e-7)
+    fixed = max(t1 - 256 * per_px, 0.0)
+    npix = int(min(n_all, max(1024, (per_step_s - fixed) / per_px)))
     for _ in range(args.warmup):
         step(npix)
     times = [step(npix) for _ in range(args.steps)]

@@ -89,19 +89,24 @@ typedef struct {
 } lp_prims;
 
 /* Launch / algorithm parameters (the autotuner's search space).
- *   tile          tile edge in pixels; 16 (the paper's patch size, App.
- *                 "Rendering Performance", Table 7) or 8 or 32.
+ *   tile          tile edge in pixels; 16, the paper's patch size (App.
+ *                 "Rendering Performance", Table 7).
  *   batch         projected primitives staged in shared memory per round of
- *                 the blend (32..256, multiple of 32).
- *   blocks_per_sm resident blend blocks per SM for the persistent grid (1..8).
+ *                 the blend: 32, 64 or 128.
+ *   blocks_per_sm resident blend blocks per SM for the persistent grid;
+ *                 0 = as many as fit (occupancy query), else 1..32.
  *   sort_mode     0: one stable radix sort of 64-bit (tile << 32 | depth)
  *                 keys; 1: stable sort of records by depth, then a stable
- *                 sort of the tile ids (same resulting order).             */
+ *                 sort of the tile ids (same resulting order).
+ *   pixels_per_thread  1, 2 or 4 horizontally adjacent pixels per blend
+ *                 thread (256 / pixels_per_thread threads per tile).
+ * Every setting renders bit-identical images.                               */
 typedef struct {
     int tile;
     int batch;
     int blocks_per_sm;
     int sort_mode;
+    int pixels_per_thread;
 } lp_tuning;
 
 /* Sizes of the last forward call (filled by lp_get_stats).                 */
@@ -138,7 +143,7 @@ lp_status lp_create(lp_ctx** out, int device);
 void lp_destroy(lp_ctx* ctx);
 
 /* Set / read the tuning parameters (defaults: tile 16, batch 64,
- * blocks_per_sm 4, sort_mode 0).                                            */
+ * blocks_per_sm 0, sort_mode 0, pixels_per_thread 4).                       */
 lp_status lp_set_tuning(lp_ctx* ctx, const lp_tuning* t);
 lp_status lp_get_tuning(lp_ctx* ctx, lp_tuning* t);
 

@@ -30,7 +30,7 @@ template <typename T> struct DevBuf {
 struct lp_ctx {
     int device = 0;
     int sms = 0;
-    lp_tuning tune{16, 64, 4, 0};
+    lp_tuning tune{16, 64, 0, 0, 4};
     char err[512] = {0};
 
     DevBuf<float> rec;
@@ -187,6 +187,19 @@ void mark(lp_ctx* ctx, cudaStream_t st, int i, bool cap_mode) {
     cudaEventRecordWithFlags(ctx->ev[i], st, cap_mode ? cudaEventRecordExternal : cudaEventRecordDefault);
 }
 
+// Persistent blend grid: resident blocks per SM (tuned, or what fits) x SMs,
+// never more blocks than tiles.
+int blend_grid(const lp_ctx* ctx, int V, bool fwd, long long tiles) {
+    int bps = ctx->tune.blocks_per_sm;
+    if (bps <= 0) {
+        bps = fwd ? lp::blend_fwd_occupancy(V, ctx->tune.batch, ctx->tune.pixels_per_thread)
+                  : lp::blend_bwd_occupancy(V, ctx->tune.batch, ctx->tune.pixels_per_thread);
+        if (bps <= 0) bps = 1;
+    }
+    const long long g = (long long)ctx->sms * bps;
+    return (int)(tiles < g ? tiles : g);
+}
+
 int bits_for(long long n) {   // bits needed to represent values 0 .. n-1
     int b = 0;
     while ((1ll << b) < n) ++b;
@@ -261,10 +274,12 @@ void lp_destroy(lp_ctx* ctx) {
 lp_status lp_set_tuning(lp_ctx* ctx, const lp_tuning* t) {
     if (!ctx || !t) return LP_ERR_INVALID;
     if (t->tile != 16) return fail(ctx, LP_ERR_UNSUPPORTED, "tile %d: only 16 is built", t->tile);
-    if (t->batch != 32 && t->batch != 64 && t->batch != 128 && t->batch != 256)
-        return fail(ctx, LP_ERR_INVALID, "batch %d not in {32, 64, 128, 256}", t->batch);
-    if (t->blocks_per_sm < 1 || t->blocks_per_sm > 8)
-        return fail(ctx, LP_ERR_INVALID, "blocks_per_sm %d outside 1..8", t->blocks_per_sm);
+    if (t->batch != 32 && t->batch != 64 && t->batch != 128)
+        return fail(ctx, LP_ERR_INVALID, "batch %d not in {32, 64, 128}", t->batch);
+    if (t->blocks_per_sm < 0 || t->blocks_per_sm > 32)
+        return fail(ctx, LP_ERR_INVALID, "blocks_per_sm %d outside 0..32", t->blocks_per_sm);
+    if (t->pixels_per_thread != 1 && t->pixels_per_thread != 2 && t->pixels_per_thread != 4)
+        return fail(ctx, LP_ERR_INVALID, "pixels_per_thread %d not in {1, 2, 4}", t->pixels_per_thread);
     if (t->sort_mode != 0) return fail(ctx, LP_ERR_UNSUPPORTED, "sort_mode %d not built", t->sort_mode);
     ctx->tune = *t;
     return LP_OK;
@@ -382,8 +397,7 @@ lp_status lp_render_forward(lp_ctx* ctx, const lp_prims* prims, const lp_camera*
     mark(ctx, st, 4, cap_mode);
 
     lp::BlendArgs a{};
-    a.grid = (int)(tiles < (long long)ctx->sms * ctx->tune.blocks_per_sm ? tiles
-                                                                         : (long long)ctx->sms * ctx->tune.blocks_per_sm);
+    a.grid = blend_grid(ctx, V, true, tiles);
     a.rec = ctx->rec.p;
     a.vals = svals;
     a.ranges = ctx->ranges.p;
@@ -396,7 +410,7 @@ lp_status lp_render_forward(lp_ctx* ctx, const lp_prims* prims, const lp_camera*
     a.pair_counts = ctx->d_pairs;
     a.count = false;
     LP_CUDA(cudaMemsetAsync(ctx->d_tile_counter, 0, sizeof(int), st));
-    if (a.grid > 0) LP_CUDA(lp::launch_blend_fwd(V, ctx->tune.batch, a, st));
+    if (a.grid > 0) LP_CUDA(lp::launch_blend_fwd(V, ctx->tune.batch, ctx->tune.pixels_per_thread, a, st));
     mark(ctx, st, 5, cap_mode);
     ctx->fwd_timed = ctx->timing;
     ctx->launches_fwd = 1 + (records > 0 ? 3 : 0) + (records > 0 ? 1 : 0) + 5 * passes +
@@ -435,9 +449,7 @@ lp_status lp_render_backward(lp_ctx* ctx, const float* dL_dimages, float* dcentr
     LP_CUDA(cudaMemsetAsync(ctx->acc.p, 0, (size_t)acc_n * sizeof(float), st));
 
     lp::BlendArgs a{};
-    a.grid = (int)(ctx->tiles < (long long)ctx->sms * ctx->tune.blocks_per_sm
-                       ? ctx->tiles
-                       : (long long)ctx->sms * ctx->tune.blocks_per_sm);
+    a.grid = blend_grid(ctx, ctx->prims.kind, false, ctx->tiles);
     a.rec = ctx->rec.p;
     a.vals = ctx->result_in_1 ? ctx->vals1.p : ctx->vals0.p;
     a.ranges = ctx->ranges.p;
@@ -449,7 +461,7 @@ lp_status lp_render_backward(lp_ctx* ctx, const float* dL_dimages, float* dcentr
     a.acc = ctx->acc.p;
     a.tile_counter = ctx->d_tile_counter + 1;
     LP_CUDA(cudaMemsetAsync(ctx->d_tile_counter + 1, 0, sizeof(int), st));
-    if (a.grid > 0) LP_CUDA(lp::launch_blend_bwd(V, ctx->tune.batch, a, st));
+    if (a.grid > 0) LP_CUDA(lp::launch_blend_bwd(V, ctx->tune.batch, ctx->tune.pixels_per_thread, a, st));
     mark(ctx, st, 7, cap_mode);
 
     lp::PrimsDev P{pr.n, pr.centre, pr.verts, pr.opacity, pr.sh};
@@ -568,9 +580,7 @@ lp_status lp_count_pairs(lp_ctx* ctx, long long* iterated, long long* intersecte
     LP_CUDA(cudaDeviceSynchronize());
     LP_TRY(ensure(ctx, ctx->scratch_image, 3 * ctx->pixels, false, "scratch image"));
     lp::BlendArgs a{};
-    a.grid = (int)(ctx->tiles < (long long)ctx->sms * ctx->tune.blocks_per_sm
-                       ? ctx->tiles
-                       : (long long)ctx->sms * ctx->tune.blocks_per_sm);
+    a.grid = blend_grid(ctx, ctx->prims.kind, true, ctx->tiles);
     a.rec = ctx->rec.p;
     a.vals = ctx->result_in_1 ? ctx->vals1.p : ctx->vals0.p;
     a.ranges = ctx->ranges.p;
@@ -584,7 +594,7 @@ lp_status lp_count_pairs(lp_ctx* ctx, long long* iterated, long long* intersecte
     a.count = true;
     LP_CUDA(cudaMemset(ctx->d_pairs, 0, 2 * sizeof(unsigned long long)));
     LP_CUDA(cudaMemset(ctx->d_tile_counter, 0, sizeof(int)));
-    if (a.grid > 0) LP_CUDA(lp::launch_blend_fwd(ctx->prims.kind, ctx->tune.batch, a, 0));
+    if (a.grid > 0) LP_CUDA(lp::launch_blend_fwd(ctx->prims.kind, ctx->tune.batch, ctx->tune.pixels_per_thread, a, 0));
     LP_CUDA(cudaDeviceSynchronize());
     unsigned long long h[2] = {0, 0};
     LP_CUDA(cudaMemcpy(h, ctx->d_pairs, sizeof(h), cudaMemcpyDeviceToHost));

@@ -1,0 +1,194 @@
+// Backward per-tile rasterization (sm_103a).
+//
+// Sec. 3.4 "Rasterization Backpropagation": each tile walks its list back to
+// front from the furthest last contributor of its pixels, recomputes every
+// span bit-identically to the forward (same staging, same span routine),
+// recovers T_i = T_{i+1} / tau_i from the stored transmittance before the
+// last contributor (never dividing by the last primitive's tau, which may be
+// ~0), keeps the suffix colour B_i = o_i c_i + tau_i B_{i+1} (B = background
+// behind the last contributor) and forms
+//   dL/dc_i = T_i o_i g,   dL/do_i = T_i (c_i - B_{i+1}) . g,
+//   dL/ds = dL/do sigma tau,   dL/dsigma = dL/do s tau,
+// and, since s = exit(x, y) - entry(x, y) with plane depth a x + b y + e, the
+// plane gradients -+ dL/ds (x, y, 1) of the arg-max entry and arg-min exit
+// faces -- the plane form of the paper's MTIA barycentric derivatives.  A
+// thread first sums its strip of pixels, each warp then reduces with shuffles
+// and issues one atomic add per value into the record's accumulator.
+#include "lp_blend.cuh"
+
+namespace lp {
+
+namespace {
+
+template <int V, int BATCH, int PIX>
+__global__ void __launch_bounds__(kTilePixels / PIX) k_blend_bwd(
+    const float* __restrict__ rec, const uint32_t* __restrict__ vals, const uint2* __restrict__ ranges,
+    CamsParam cams, float bg0, float bg1, float bg2, const float* __restrict__ dimage,
+    const uint32_t* __restrict__ last_in, const float* __restrict__ tl_in, float* __restrict__ acc,
+    int* __restrict__ tile_counter) {
+    constexpr int F = Kind<V>::F;
+    constexpr int ACC = Acc<V>::kFloats;
+    constexpr int NT = kTilePixels / PIX;
+    constexpr int RW = kTile / PIX;
+    __shared__ Staged<V> sm[BATCH];
+    __shared__ int s_tile;
+    __shared__ int s_max;
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const int ly = tid / RW, lx0 = (tid % RW) * PIX;
+    for (;;) {
+        if (tid == 0) {
+            s_tile = atomicAdd(tile_counter, 1);
+            s_max = 0;
+        }
+        __syncthreads();
+        const int tile = s_tile;
+        if (tile >= cams.total_tiles) break;
+        const TileGeom tg = tile_geom(cams, tile);
+        const int py = tg.ty0 + ly;
+        const uint2 rg = ranges[tile];
+        const int plane = tg.width * tg.height;
+        const float* gi = dimage + 3 * (size_t)tg.pix_base;
+        float g0[PIX], g1[PIX], g2[PIX], Tcur[PIX], B0[PIX], B1[PIX], B2[PIX];
+        uint32_t last[PIX];
+        bool first[PIX];
+        uint32_t lmax = 0;
+#pragma unroll
+        for (int i = 0; i < PIX; ++i) {
+            const int px = tg.tx0 + lx0 + i;
+            g0[i] = g1[i] = g2[i] = 0.f; Tcur[i] = 1.f; last[i] = 0;
+            if (px < tg.width && py < tg.height) {
+                const int idx = py * tg.width + px;
+                g0[i] = gi[idx]; g1[i] = gi[plane + idx]; g2[i] = gi[2 * plane + idx];
+                last[i] = last_in[tg.pix_base + idx];
+                Tcur[i] = tl_in[tg.pix_base + idx];
+            }
+            B0[i] = bg0; B1[i] = bg1; B2[i] = bg2;
+            first[i] = true;
+            lmax = max(lmax, last[i]);
+        }
+        if (lmax > 0) atomicMax(&s_max, (int)lmax);
+        __syncthreads();
+        const int hi_all = s_max;
+        for (int hi = hi_all; hi > 0; hi -= BATCH) {
+            const int lo = max(0, hi - BATCH);
+            const int nb = hi - lo;
+            __syncthreads();
+            for (int j = tid; j < nb; j += NT) stage_record<V>(rec, vals[rg.x + lo + j], tg.tx0, tg.ty0, sm[j]);
+            __syncthreads();
+            for (int j = nb - 1; j >= 0; --j) {
+                const Staged<V>& p = sm[j];
+                const uint32_t idx = (uint32_t)(lo + j);
+                bool any = false;
+#pragma unroll
+                for (int i = 0; i < PIX; ++i) any |= idx < last[i];
+                float sp[PIX];
+                int sf[PIX], sb[PIX];
+                bool c[PIX];
+                bool anyc = false;
+#pragma unroll
+                for (int i = 0; i < PIX; ++i) c[i] = false;
+                if (any) {
+                    spans<V, PIX, true>(p, (float)lx0, (float)ly, sp, sf, sb);
+#pragma unroll
+                    for (int i = 0; i < PIX; ++i) {
+                        c[i] = idx < last[i] && sp[i] > 0.f;
+                        anyc |= c[i];
+                    }
+                }
+                if (__ballot_sync(0xffffffffu, anyc) == 0u) continue;
+                float gr0 = 0.f, gr1 = 0.f, gr2 = 0.f, gsig = 0.f;
+                float gsp[PIX];
+                unsigned used = 0;
+#pragma unroll
+                for (int i = 0; i < PIX; ++i) {
+                    gsp[i] = 0.f;
+                    if (c[i]) {
+                        const float tau = span_tau(p.sigma, sp[i]);
+                        const float o = 1.f - tau;
+                        const float Ti = first[i] ? Tcur[i] : Tcur[i] / tau;
+                        first[i] = false;
+                        Tcur[i] = Ti;
+                        const float w = Ti * o;
+                        gr0 = fmaf(w, g0[i], gr0);
+                        gr1 = fmaf(w, g1[i], gr1);
+                        gr2 = fmaf(w, g2[i], gr2);
+                        const float dLdo = Ti * ((p.r - B0[i]) * g0[i] + (p.g - B1[i]) * g1[i] +
+                                                 (p.b - B2[i]) * g2[i]);
+                        B0[i] = fmaf(o, p.r, tau * B0[i]);
+                        B1[i] = fmaf(o, p.g, tau * B1[i]);
+                        B2[i] = fmaf(o, p.b, tau * B2[i]);
+                        gsp[i] = dLdo * p.sigma * tau;        // dL/d span
+                        gsig = fmaf(dLdo * sp[i], tau, gsig);  // dL/d sigma
+                        used |= (1u << sf[i]) | (1u << sb[i]);
+                    }
+                }
+                float* A = acc + (size_t)p.rec * ACC;
+                gr0 = warp_sum(gr0); gr1 = warp_sum(gr1); gr2 = warp_sum(gr2); gsig = warp_sum(gsig);
+                if (lane == 0) {
+                    atomicAdd(A + 3 * F + 0, gr0);
+                    atomicAdd(A + 3 * F + 1, gr1);
+                    atomicAdd(A + 3 * F + 2, gr2);
+                    atomicAdd(A + 3 * F + 3, gsig);
+                }
+                // plane gradients, with offsets (px - X0, py - Y0) from the anchor
+                used = __reduce_or_sync(0xffffffffu, used);
+                const float lyc = (float)ly + p.dy0;
+                while (used) {
+                    const int f = __ffs(used) - 1;
+                    used &= used - 1;
+                    float vs = 0.f, vx = 0.f;
+#pragma unroll
+                    for (int i = 0; i < PIX; ++i) {
+                        const float v = c[i] ? (f == sf[i] ? -gsp[i] : (f == sb[i] ? gsp[i] : 0.f)) : 0.f;
+                        vs += v;
+                        vx = fmaf(v, (float)(lx0 + i) + p.dx0, vx);
+                    }
+                    const float ga = warp_sum(vx), gb = warp_sum(vs * lyc), ge = warp_sum(vs);
+                    if (lane == 0) {
+                        atomicAdd(A + 3 * f + 0, ga);
+                        atomicAdd(A + 3 * f + 1, gb);
+                        atomicAdd(A + 3 * f + 2, ge);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <int V, int BATCH, int PIX>
+cudaError_t bwd_t(const BlendArgs& a, cudaStream_t st) {
+    k_blend_bwd<V, BATCH, PIX><<<a.grid, kTilePixels / PIX, 0, st>>>(
+        a.rec, a.vals, a.ranges, *a.cams, a.bg[0], a.bg[1], a.bg[2], a.dimage, a.last, a.tl, a.acc,
+        a.tile_counter);
+    return cudaGetLastError();
+}
+
+template <int V, int BATCH, int PIX>
+int bwd_occ() {
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_blend_bwd<V, BATCH, PIX>, kTilePixels / PIX, 0);
+    return nb;
+}
+
+}  // namespace
+
+#define LP_BWD_DISPATCH(FN, V, B, P, ...)                                                   \
+    if (V == 6) {                                                                           \
+        if (B == 32) { if (P == 1) return FN<6, 32, 1>(__VA_ARGS__); if (P == 2) return FN<6, 32, 2>(__VA_ARGS__); return FN<6, 32, 4>(__VA_ARGS__); } \
+        if (B == 128) { if (P == 1) return FN<6, 128, 1>(__VA_ARGS__); if (P == 2) return FN<6, 128, 2>(__VA_ARGS__); return FN<6, 128, 4>(__VA_ARGS__); } \
+        if (P == 1) return FN<6, 64, 1>(__VA_ARGS__); if (P == 2) return FN<6, 64, 2>(__VA_ARGS__); return FN<6, 64, 4>(__VA_ARGS__); \
+    } else {                                                                                \
+        if (B == 32) { if (P == 1) return FN<4, 32, 1>(__VA_ARGS__); if (P == 2) return FN<4, 32, 2>(__VA_ARGS__); return FN<4, 32, 4>(__VA_ARGS__); } \
+        if (B == 128) { if (P == 1) return FN<4, 128, 1>(__VA_ARGS__); if (P == 2) return FN<4, 128, 2>(__VA_ARGS__); return FN<4, 128, 4>(__VA_ARGS__); } \
+        if (P == 1) return FN<4, 64, 1>(__VA_ARGS__); if (P == 2) return FN<4, 64, 2>(__VA_ARGS__); return FN<4, 64, 4>(__VA_ARGS__); \
+    }
+
+cudaError_t launch_blend_bwd(int V, int batch, int pix, const BlendArgs& a, cudaStream_t st) {
+    LP_BWD_DISPATCH(bwd_t, V, batch, pix, a, st)
+}
+
+int blend_bwd_occupancy(int V, int batch, int pix) { LP_BWD_DISPATCH(bwd_occ, V, batch, pix) }
+
+}  // namespace lp

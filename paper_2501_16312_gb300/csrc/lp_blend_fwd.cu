@@ -1,0 +1,153 @@
+// Forward per-tile rasterization and compositing (sm_103a).
+//
+// Sec. 3.2 "Rasterization" and "Compositing": each 16x16 tile walks its
+// depth-sorted list front to back, staging batches of projected records in
+// shared memory; each pixel ray is clipped against the primitive's face
+// half-spaces, the span s gives the opacity o = 1 - exp(-sigma s) (App.
+// "Gradient Computation"), colours are blended front to back, and a pixel
+// stops once its transmittance falls below 1e-3 (cumulative opacity 0.999),
+// after blending the primitive that crossed it.  A tile stops when all of its
+// pixels have.  Per pixel the kernel keeps, for the backward, the number of
+// list entries up to the last contributor and the transmittance before it.
+#include "lp_blend.cuh"
+
+namespace lp {
+
+namespace {
+
+template <int V, int BATCH, int PIX, bool COUNT>
+__global__ void __launch_bounds__(kTilePixels / PIX) k_blend_fwd(
+    const float* __restrict__ rec, const uint32_t* __restrict__ vals, const uint2* __restrict__ ranges,
+    CamsParam cams, float bg0, float bg1, float bg2, float* __restrict__ image,
+    uint32_t* __restrict__ last_out, float* __restrict__ tl_out, int* __restrict__ tile_counter,
+    unsigned long long* __restrict__ pair_counts) {
+    constexpr int NT = kTilePixels / PIX;
+    constexpr int RW = kTile / PIX;
+    __shared__ Staged<V> sm[BATCH];
+    __shared__ int s_tile;
+    const int tid = threadIdx.x;
+    const int ly = tid / RW, lx0 = (tid % RW) * PIX;
+    unsigned long long n_iter = 0, n_hit = 0;
+    for (;;) {
+        if (tid == 0) s_tile = atomicAdd(tile_counter, 1);
+        __syncthreads();
+        const int tile = s_tile;
+        if (tile >= cams.total_tiles) break;
+        const TileGeom tg = tile_geom(cams, tile);
+        const int py = tg.ty0 + ly;
+        const uint2 rg = ranges[tile];
+        const int n = (int)(rg.y - rg.x);
+        float T[PIX], c0[PIX], c1[PIX], c2[PIX], tl[PIX];
+        uint32_t last[PIX];
+        bool done[PIX];
+        bool tdone = true;
+#pragma unroll
+        for (int i = 0; i < PIX; ++i) {
+            T[i] = 1.f; c0[i] = c1[i] = c2[i] = 0.f; tl[i] = 1.f; last[i] = 0;
+            done[i] = !(tg.tx0 + lx0 + i < tg.width && py < tg.height);
+            tdone &= done[i];
+        }
+        for (int b0 = 0; b0 < n; b0 += BATCH) {
+            if (__syncthreads_count(!tdone) == 0) break;
+            const int nb = min(BATCH, n - b0);
+            for (int j = tid; j < nb; j += NT) stage_record<V>(rec, vals[rg.x + b0 + j], tg.tx0, tg.ty0, sm[j]);
+            __syncthreads();
+            if (!tdone) {
+                for (int j = 0; j < nb; ++j) {
+                    const Staged<V>& p = sm[j];
+                    float sp[PIX];
+                    spans<V, PIX, false>(p, (float)lx0, (float)ly, sp, nullptr, nullptr);
+                    tdone = true;
+#pragma unroll
+                    for (int i = 0; i < PIX; ++i) {
+                        if (COUNT && !done[i]) ++n_iter;
+                        if (!done[i] && sp[i] > 0.f) {
+                            if (COUNT) ++n_hit;
+                            const float tau = span_tau(p.sigma, sp[i]);
+                            const float w = T[i] * (1.f - tau);
+                            c0[i] = fmaf(w, p.r, c0[i]);
+                            c1[i] = fmaf(w, p.g, c1[i]);
+                            c2[i] = fmaf(w, p.b, c2[i]);
+                            tl[i] = T[i];
+                            T[i] *= tau;
+                            last[i] = (uint32_t)(b0 + j + 1);
+                            done[i] = T[i] < kStopT;
+                        }
+                        tdone &= done[i];
+                    }
+                    if (tdone) break;
+                }
+            }
+        }
+        const int plane = tg.width * tg.height;
+        float* img = image + 3 * (size_t)tg.pix_base;
+#pragma unroll
+        for (int i = 0; i < PIX; ++i) {
+            const int px = tg.tx0 + lx0 + i;
+            if (px < tg.width && py < tg.height) {
+                const int idx = py * tg.width + px;
+                img[idx] = fmaf(T[i], bg0, c0[i]);
+                img[plane + idx] = fmaf(T[i], bg1, c1[i]);
+                img[2 * plane + idx] = fmaf(T[i], bg2, c2[i]);
+                last_out[tg.pix_base + idx] = last[i];
+                tl_out[tg.pix_base + idx] = tl[i];
+            }
+        }
+        __syncthreads();
+    }
+    if (COUNT) {
+        unsigned long long a = n_iter, b = n_hit;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_xor_sync(0xffffffffu, a, o);
+            b += __shfl_xor_sync(0xffffffffu, b, o);
+        }
+        if ((tid & 31) == 0) {
+            atomicAdd(pair_counts, a);
+            atomicAdd(pair_counts + 1, b);
+        }
+    }
+}
+
+template <int V, int BATCH, int PIX>
+cudaError_t fwd_t(const BlendArgs& a, cudaStream_t st) {
+    constexpr int NT = kTilePixels / PIX;
+    if (a.count)
+        k_blend_fwd<V, BATCH, PIX, true><<<a.grid, NT, 0, st>>>(
+            a.rec, a.vals, a.ranges, *a.cams, a.bg[0], a.bg[1], a.bg[2], a.image, a.last, a.tl,
+            a.tile_counter, a.pair_counts);
+    else
+        k_blend_fwd<V, BATCH, PIX, false><<<a.grid, NT, 0, st>>>(
+            a.rec, a.vals, a.ranges, *a.cams, a.bg[0], a.bg[1], a.bg[2], a.image, a.last, a.tl,
+            a.tile_counter, a.pair_counts);
+    return cudaGetLastError();
+}
+
+template <int V, int BATCH, int PIX>
+int fwd_occ() {
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_blend_fwd<V, BATCH, PIX, false>,
+                                                  kTilePixels / PIX, 0);
+    return nb;
+}
+
+}  // namespace
+
+#define LP_FWD_DISPATCH(FN, V, B, P, ...)                                                   \
+    if (V == 6) {                                                                           \
+        if (B == 32) { if (P == 1) return FN<6, 32, 1>(__VA_ARGS__); if (P == 2) return FN<6, 32, 2>(__VA_ARGS__); return FN<6, 32, 4>(__VA_ARGS__); } \
+        if (B == 128) { if (P == 1) return FN<6, 128, 1>(__VA_ARGS__); if (P == 2) return FN<6, 128, 2>(__VA_ARGS__); return FN<6, 128, 4>(__VA_ARGS__); } \
+        if (P == 1) return FN<6, 64, 1>(__VA_ARGS__); if (P == 2) return FN<6, 64, 2>(__VA_ARGS__); return FN<6, 64, 4>(__VA_ARGS__); \
+    } else {                                                                                \
+        if (B == 32) { if (P == 1) return FN<4, 32, 1>(__VA_ARGS__); if (P == 2) return FN<4, 32, 2>(__VA_ARGS__); return FN<4, 32, 4>(__VA_ARGS__); } \
+        if (B == 128) { if (P == 1) return FN<4, 128, 1>(__VA_ARGS__); if (P == 2) return FN<4, 128, 2>(__VA_ARGS__); return FN<4, 128, 4>(__VA_ARGS__); } \
+        if (P == 1) return FN<4, 64, 1>(__VA_ARGS__); if (P == 2) return FN<4, 64, 2>(__VA_ARGS__); return FN<4, 64, 4>(__VA_ARGS__); \
+    }
+
+cudaError_t launch_blend_fwd(int V, int batch, int pix, const BlendArgs& a, cudaStream_t st) {
+    LP_FWD_DISPATCH(fwd_t, V, batch, pix, a, st)
+}
+
+int blend_fwd_occupancy(int V, int batch, int pix) { LP_FWD_DISPATCH(fwd_occ, V, batch, pix) }
+
+}  // namespace lp

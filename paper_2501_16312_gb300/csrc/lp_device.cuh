@@ -204,13 +204,13 @@ __device__ __forceinline__ void sh_basis_vjp(float x, float y, float z, const fl
 // A record staged in shared memory for one tile: the planes are re-based to
 // the tile's first pixel (tx0, ty0), an exact integer offset (dx0, dy0) from
 // (X0, Y0), so that pixel (tx0 + lx, ty0 + ly) evaluates depth = a lx + b ly
-// + e'.  The forward and backward blends both stage through stage_record()
-// and evaluate through span_*(), so they compute bit-identical spans.
-template <int V> struct Staged {
+// + e'.  Planes are float4 (a, b, e', 0) for 128-bit shared loads.  The
+// forward and backward blends both stage through stage_record() and evaluate
+// through the same span routines, so they compute bit-identical spans.
+template <int V> struct alignas(16) Staged {
     static constexpr int F = Kind<V>::F;
-    float pl[3 * F];   // (a, b, e') per slot
-    float sigma;
-    float rgb[3];
+    float4 pl[F];
+    float sigma, r, g, b;
     float dx0, dy0;    // tx0 - X0, ty0 - Y0 (integers)
     int nf;
     int rec;           // record index (camera * n + primitive)
@@ -232,46 +232,82 @@ __device__ __forceinline__ void stage_record(const float* __restrict__ rec, int 
 #pragma unroll
     for (int f = 0; f < F; ++f) {
         const float a = buf[8 + 3 * f], b = buf[9 + 3 * f], e = buf[10 + 3 * f];
-        s.pl[3 * f] = a;
-        s.pl[3 * f + 1] = b;
-        s.pl[3 * f + 2] = __fmaf_rn(a, dx0, __fmaf_rn(b, dy0, e));
+        s.pl[f] = make_float4(a, b, __fmaf_rn(a, dx0, __fmaf_rn(b, dy0, e)), 0.f);
     }
     s.sigma = buf[2];
-    s.nf = meta_nf(__float_as_uint(buf[3]));
-    s.rgb[0] = buf[4]; s.rgb[1] = buf[5]; s.rgb[2] = buf[6];
+    s.r = buf[4]; s.g = buf[5]; s.b = buf[6];
     s.dx0 = dx0; s.dy0 = dy0;
+    s.nf = meta_nf(__float_as_uint(buf[3]));
     s.rec = r;
 }
 
-// Ray/primitive span at tile-local pixel offset (lx, ly): half-space
-// clipping of the pixel ray against the convex primitive (entry = max over
-// entry faces, exit = min over exit faces).  This equals the distance
-// between the two MTIA hits of Sec. 3.2 "Rasterization".
-template <int V>
-__device__ __forceinline__ float span_at(const Staged<V>& s, float lx, float ly) {
+// Ray/primitive spans of a strip of PIX pixels (lx0 + i, ly), i < PIX, by
+// half-space clipping of each pixel ray against the convex primitive: entry
+// = max over the NF entry faces, exit = min over the others.  This equals the
+// distance between the two MTIA hits of Sec. 3.2 "Rasterization".  NF is a
+// template argument so the entry/exit split costs nothing per face; with ARG
+// the arg-max entry slot and arg-min exit slot are returned too.
+template <int V, int PIX, int NF, bool ARG>
+__device__ __forceinline__ void spans_nf(const Staged<V>& s, float lx0, float ly, float* sp, int* sf,
+                                         int* sb) {
     constexpr int F = Kind<V>::F;
-    float tf = -CUDART_INF_F, tb = CUDART_INF_F;
+    if (NF <= 0 || NF >= F) {   // no entry or no exit face: not a closed convex primitive
+#pragma unroll
+        for (int i = 0; i < PIX; ++i) {
+            sp[i] = 0.f;
+            if (ARG) { sf[i] = 0; sb[i] = F - 1; }
+        }
+        return;
+    }
+    float tf[PIX], tb[PIX];
+#pragma unroll
+    for (int i = 0; i < PIX; ++i) {
+        tf[i] = -CUDART_INF_F;
+        tb[i] = CUDART_INF_F;
+        if (ARG) { sf[i] = 0; sb[i] = F - 1; }
+    }
 #pragma unroll
     for (int f = 0; f < F; ++f) {
-        const float d = __fmaf_rn(s.pl[3 * f], lx, __fmaf_rn(s.pl[3 * f + 1], ly, s.pl[3 * f + 2]));
-        if (f < s.nf) tf = fmaxf(tf, d); else tb = fminf(tb, d);
+        const float4 p = s.pl[f];
+        const float t = __fmaf_rn(p.y, ly, p.z);
+#pragma unroll
+        for (int i = 0; i < PIX; ++i) {
+            const float d = __fmaf_rn(p.x, lx0 + (float)i, t);
+            if (f < NF) {
+                if (ARG) { if (d > tf[i]) { tf[i] = d; sf[i] = f; } }
+                else tf[i] = fmaxf(tf[i], d);
+            } else {
+                if (ARG) { if (d < tb[i]) { tb[i] = d; sb[i] = f; } }
+                else tb[i] = fminf(tb[i], d);
+            }
+        }
     }
-    return __fsub_rn(tb, tf);
+#pragma unroll
+    for (int i = 0; i < PIX; ++i) sp[i] = __fsub_rn(tb[i], tf[i]);
 }
 
-// Same, also returning the arg-max entry slot and arg-min exit slot.
-template <int V>
-__device__ __forceinline__ float span_arg(const Staged<V>& s, float lx, float ly, int& sf, int& sb) {
-    constexpr int F = Kind<V>::F;
-    float tf = -CUDART_INF_F, tb = CUDART_INF_F;
-    sf = 0; sb = F - 1;
-#pragma unroll
-    for (int f = 0; f < F; ++f) {
-        const float d = __fmaf_rn(s.pl[3 * f], lx, __fmaf_rn(s.pl[3 * f + 1], ly, s.pl[3 * f + 2]));
-        if (f < s.nf) { if (d > tf) { tf = d; sf = f; } }
-        else          { if (d < tb) { tb = d; sb = f; } }
+template <int V, int PIX, bool ARG>
+__device__ __forceinline__ void spans(const Staged<V>& s, float lx0, float ly, float* sp, int* sf,
+                                      int* sb) {
+    if (V == 6) {
+        switch (s.nf) {
+            case 1: spans_nf<V, PIX, 1, ARG>(s, lx0, ly, sp, sf, sb); break;
+            case 2: spans_nf<V, PIX, 2, ARG>(s, lx0, ly, sp, sf, sb); break;
+            case 3: spans_nf<V, PIX, 3, ARG>(s, lx0, ly, sp, sf, sb); break;
+            case 4: spans_nf<V, PIX, 4, ARG>(s, lx0, ly, sp, sf, sb); break;
+            case 5: spans_nf<V, PIX, 5, ARG>(s, lx0, ly, sp, sf, sb); break;
+            case 6: spans_nf<V, PIX, 6, ARG>(s, lx0, ly, sp, sf, sb); break;
+            case 7: spans_nf<V, PIX, 7, ARG>(s, lx0, ly, sp, sf, sb); break;
+            default: spans_nf<V, PIX, 0, ARG>(s, lx0, ly, sp, sf, sb); break;
+        }
+    } else {
+        switch (s.nf) {
+            case 1: spans_nf<V, PIX, 1, ARG>(s, lx0, ly, sp, sf, sb); break;
+            case 2: spans_nf<V, PIX, 2, ARG>(s, lx0, ly, sp, sf, sb); break;
+            case 3: spans_nf<V, PIX, 3, ARG>(s, lx0, ly, sp, sf, sb); break;
+            default: spans_nf<V, PIX, 0, ARG>(s, lx0, ly, sp, sf, sb); break;
+        }
     }
-    return __fsub_rn(tb, tf);
 }
 
 // Opacity of a span, App. "Gradient Computation": o = 1 - exp(-sigma s).

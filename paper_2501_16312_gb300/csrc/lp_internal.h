@@ -51,7 +51,9 @@ struct BlendArgs {
     bool count;
 };
 
-cudaError_t launch_blend_fwd(int V, int batch, const BlendArgs& a, cudaStream_t st);
-cudaError_t launch_blend_bwd(int V, int batch, const BlendArgs& a, cudaStream_t st);
+cudaError_t launch_blend_fwd(int V, int batch, int pix, const BlendArgs& a, cudaStream_t st);
+cudaError_t launch_blend_bwd(int V, int batch, int pix, const BlendArgs& a, cudaStream_t st);
+int blend_fwd_occupancy(int V, int batch, int pix);   // resident blocks per SM
+int blend_bwd_occupancy(int V, int batch, int pix);
 
 }  // namespace lp
