@@ -11,6 +11,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 
 #include "linprim.h"
@@ -40,6 +41,7 @@ struct lp_ctx {
     DevBuf<uint32_t> vals0, vals1;
     DevBuf<uint2> ranges;
     DevBuf<float> tl, acc, scratch_image;
+    DevBuf<uint32_t> dkeys0, dkeys1, dvals0, dvals1, counts_sorted;   // two-stage sort
     int* d_status = nullptr;         // latched status bits
     uint32_t* d_E = nullptr;         // tile-list length of the last forward
     int* d_tile_counter = nullptr;   // [0] forward queue, [1] backward queue
@@ -55,6 +57,7 @@ struct lp_ctx {
     int key_bits = 0, sort_passes = 0;
     int launches_fwd = 0;
     bool result_in_1 = false;
+    bool keys32 = false;        // tile list keyed by 32-bit tile ids (two-stage sort)
 
     // stage timing: events 0..5 bracket the forward stages, 6..8 the backward
     bool timing = false;
@@ -261,6 +264,8 @@ void lp_destroy(lp_ctx* ctx) {
     release(ctx->scan_tmp); release(ctx->hist); release(ctx->last); release(ctx->trect);
     release(ctx->keys0); release(ctx->keys1); release(ctx->vals0); release(ctx->vals1);
     release(ctx->ranges); release(ctx->tl); release(ctx->acc); release(ctx->scratch_image);
+    release(ctx->dkeys0); release(ctx->dkeys1); release(ctx->dvals0); release(ctx->dvals1);
+    release(ctx->counts_sorted);
     if (ctx->d_status) cudaFree(ctx->d_status);
     if (ctx->d_E) cudaFree(ctx->d_E);
     if (ctx->d_tile_counter) cudaFree(ctx->d_tile_counter);
@@ -280,7 +285,8 @@ lp_status lp_set_tuning(lp_ctx* ctx, const lp_tuning* t) {
         return fail(ctx, LP_ERR_INVALID, "blocks_per_sm %d outside 0..32", t->blocks_per_sm);
     if (t->pixels_per_thread != 1 && t->pixels_per_thread != 2 && t->pixels_per_thread != 4)
         return fail(ctx, LP_ERR_INVALID, "pixels_per_thread %d not in {1, 2, 4}", t->pixels_per_thread);
-    if (t->sort_mode != 0) return fail(ctx, LP_ERR_UNSUPPORTED, "sort_mode %d not built", t->sort_mode);
+    if (t->sort_mode != 0 && t->sort_mode != 1)
+        return fail(ctx, LP_ERR_INVALID, "sort_mode %d not in {0, 1}", t->sort_mode);
     ctx->tune = *t;
     return LP_OK;
 }
@@ -303,9 +309,15 @@ static lp_status reserve_impl(lp_ctx* ctx, long long records, long long entries,
     LP_TRY(ensure(ctx, ctx->keys1, entries, false, "keys"));
     LP_TRY(ensure(ctx, ctx->vals0, entries, false, "values"));
     LP_TRY(ensure(ctx, ctx->vals1, entries, false, "values"));
-    LP_TRY(ensure(ctx, ctx->hist, (long long)lp::sort_hist_elems(entries), false, "histograms"));
+    LP_TRY(ensure(ctx, ctx->dkeys0, records, false, "depth keys"));
+    LP_TRY(ensure(ctx, ctx->dkeys1, records, false, "depth keys"));
+    LP_TRY(ensure(ctx, ctx->dvals0, records, false, "depth values"));
+    LP_TRY(ensure(ctx, ctx->dvals1, records, false, "depth values"));
+    LP_TRY(ensure(ctx, ctx->counts_sorted, records, false, "sorted counts"));
+    const long long hmax = entries > records ? entries : records;
+    LP_TRY(ensure(ctx, ctx->hist, (long long)lp::sort_hist_elems(hmax), false, "histograms"));
     long long sb = lp::scan_blocks(records);
-    long long sb2 = lp::scan_blocks((long long)lp::sort_hist_elems(entries));
+    long long sb2 = lp::scan_blocks((long long)lp::sort_hist_elems(hmax));
     LP_TRY(ensure(ctx, ctx->scan_tmp, sb > sb2 ? sb : sb2, false, "scan blocks"));
     LP_TRY(ensure(ctx, ctx->ranges, tiles, false, "tile ranges"));
     LP_TRY(ensure(ctx, ctx->last, pixels, false, "pixel state"));
@@ -358,7 +370,29 @@ lp_status lp_render_forward(lp_ctx* ctx, const lp_prims* prims, const lp_camera*
     LP_CUDA(lp::launch_preprocess(V, prims->sh_degree, P, cp, ctx->rec.p, ctx->counts.p, ctx->trect.p,
                                   ctx->zbits.p, st));
     mark(ctx, st, 1, cap_mode);
-    LP_CUDA(lp::launch_scan(ctx->counts.p, records, ctx->offsets.p, ctx->scan_tmp.p, ctx->d_E, st));
+    const int mode = ctx->tune.sort_mode;
+    int passes = 0, passes1 = 0;
+    const uint32_t* order = nullptr;   // mode 1: records in depth order
+    if (mode == 1) {
+        LP_TRY(ensure(ctx, ctx->dkeys0, records, cap_mode, "depth keys"));
+        LP_TRY(ensure(ctx, ctx->dkeys1, records, cap_mode, "depth keys"));
+        LP_TRY(ensure(ctx, ctx->dvals0, records, cap_mode, "depth values"));
+        LP_TRY(ensure(ctx, ctx->dvals1, records, cap_mode, "depth values"));
+        LP_TRY(ensure(ctx, ctx->counts_sorted, records, cap_mode, "sorted counts"));
+        LP_TRY(ensure(ctx, ctx->hist, (long long)lp::sort_hist_elems(records), cap_mode, "histograms"));
+        LP_TRY(ensure(ctx, ctx->scan_tmp, lp::scan_blocks((long long)lp::sort_hist_elems(records)),
+                      cap_mode, "scan blocks"));
+        // stage 1: records by centre depth
+        LP_CUDA(lp::launch_depth_keys(ctx->counts.p, ctx->zbits.p, records, ctx->dkeys0.p, ctx->dvals0.p, st));
+        LP_CUDA(lp::launch_radix_sort32(ctx->dkeys0.p, ctx->dvals0.p, ctx->dkeys1.p, ctx->dvals1.p, nullptr,
+                                        records, 32, ctx->hist.p, ctx->scan_tmp.p, &passes1, st));
+        order = (passes1 & 1) ? ctx->dvals1.p : ctx->dvals0.p;
+        LP_CUDA(lp::launch_gather_counts(ctx->counts.p, order, records, ctx->counts_sorted.p, st));
+        LP_CUDA(lp::launch_scan(ctx->counts_sorted.p, records, ctx->offsets.p, ctx->scan_tmp.p, ctx->d_E,
+                                st));
+    } else {
+        LP_CUDA(lp::launch_scan(ctx->counts.p, records, ctx->offsets.p, ctx->scan_tmp.p, ctx->d_E, st));
+    }
 
     long long bound;
     if (!cap_mode) {
@@ -381,19 +415,41 @@ lp_status lp_render_forward(lp_ctx* ctx, const lp_prims* prims, const lp_camera*
     LP_TRY(ensure(ctx, ctx->scan_tmp, lp::scan_blocks((long long)lp::sort_hist_elems(bound)), cap_mode,
                   "scan blocks"));
 
-    LP_CUDA(lp::launch_emit(ctx->counts.p, ctx->offsets.p, ctx->trect.p, ctx->zbits.p, prims->n, records,
-                            cp, ctx->keys0.p, ctx->vals0.p, bound, ctx->d_status, st));
-    mark(ctx, st, 2, cap_mode);
-    const int key_bits = 32 + bits_for(tiles);
-    int passes = 0;
-    LP_CUDA(lp::launch_radix_sort(ctx->keys0.p, ctx->vals0.p, ctx->keys1.p, ctx->vals1.p, ctx->d_E, bound,
-                                  key_bits, ctx->hist.p, ctx->scan_tmp.p, &passes, st));
-    const bool in1 = (passes & 1) != 0;
-    const uint64_t* skeys = in1 ? ctx->keys1.p : ctx->keys0.p;
-    const uint32_t* svals = in1 ? ctx->vals1.p : ctx->vals0.p;
-    mark(ctx, st, 3, cap_mode);
-    LP_CUDA(cudaMemsetAsync(ctx->ranges.p, 0, (size_t)(tiles > 0 ? tiles : 1) * sizeof(uint2), st));
-    LP_CUDA(lp::launch_ranges(skeys, ctx->d_E, bound, ctx->d_status, ctx->ranges.p, ctx->sms, st));
+    const int tile_bits = bits_for(tiles);
+    int key_bits;
+    const uint32_t* svals;
+    if (mode == 1) {
+        // stage 2: entries in depth order, stably sorted by their tile id
+        uint32_t* t0 = reinterpret_cast<uint32_t*>(ctx->keys0.p);
+        uint32_t* t1 = reinterpret_cast<uint32_t*>(ctx->keys1.p);
+        LP_CUDA(lp::launch_emit_sorted(order, ctx->counts_sorted.p, ctx->offsets.p, ctx->trect.p, prims->n,
+                                       records, cp, t0, ctx->vals0.p, bound, ctx->d_status, st));
+        mark(ctx, st, 2, cap_mode);
+        key_bits = tile_bits;
+        LP_CUDA(lp::launch_radix_sort32(t0, ctx->vals0.p, t1, ctx->vals1.p, ctx->d_E, bound, key_bits,
+                                        ctx->hist.p, ctx->scan_tmp.p, &passes, st));
+        const bool in1 = (passes & 1) != 0;
+        svals = in1 ? ctx->vals1.p : ctx->vals0.p;
+        mark(ctx, st, 3, cap_mode);
+        LP_CUDA(cudaMemsetAsync(ctx->ranges.p, 0, (size_t)(tiles > 0 ? tiles : 1) * sizeof(uint2), st));
+        LP_CUDA(lp::launch_ranges32(in1 ? t1 : t0, ctx->d_E, bound, ctx->d_status, ctx->ranges.p, ctx->sms,
+                                    st));
+        ctx->result_in_1 = in1;
+    } else {
+        LP_CUDA(lp::launch_emit(ctx->counts.p, ctx->offsets.p, ctx->trect.p, ctx->zbits.p, prims->n,
+                                records, cp, ctx->keys0.p, ctx->vals0.p, bound, ctx->d_status, st));
+        mark(ctx, st, 2, cap_mode);
+        key_bits = 32 + tile_bits;
+        LP_CUDA(lp::launch_radix_sort(ctx->keys0.p, ctx->vals0.p, ctx->keys1.p, ctx->vals1.p, ctx->d_E,
+                                      bound, key_bits, ctx->hist.p, ctx->scan_tmp.p, &passes, st));
+        const bool in1 = (passes & 1) != 0;
+        svals = in1 ? ctx->vals1.p : ctx->vals0.p;
+        mark(ctx, st, 3, cap_mode);
+        LP_CUDA(cudaMemsetAsync(ctx->ranges.p, 0, (size_t)(tiles > 0 ? tiles : 1) * sizeof(uint2), st));
+        LP_CUDA(lp::launch_ranges(in1 ? ctx->keys1.p : ctx->keys0.p, ctx->d_E, bound, ctx->d_status,
+                                  ctx->ranges.p, ctx->sms, st));
+        ctx->result_in_1 = in1;
+    }
     mark(ctx, st, 4, cap_mode);
 
     lp::BlendArgs a{};
@@ -413,8 +469,8 @@ lp_status lp_render_forward(lp_ctx* ctx, const lp_prims* prims, const lp_camera*
     if (a.grid > 0) LP_CUDA(lp::launch_blend_fwd(V, ctx->tune.batch, ctx->tune.pixels_per_thread, a, st));
     mark(ctx, st, 5, cap_mode);
     ctx->fwd_timed = ctx->timing;
-    ctx->launches_fwd = 1 + (records > 0 ? 3 : 0) + (records > 0 ? 1 : 0) + 5 * passes +
-                        (bound > 0 ? 1 : 0) + (a.grid > 0 ? 1 : 0);
+    ctx->launches_fwd = 1 + (records > 0 ? 3 : 0) + (records > 0 ? 1 : 0) + 5 * (passes + passes1) +
+                        (mode == 1 && records > 0 ? 2 : 0) + (bound > 0 ? 1 : 0) + (a.grid > 0 ? 1 : 0);
 
     ctx->have_fwd = true;
     ctx->prims = *prims;
@@ -425,8 +481,8 @@ lp_status lp_render_forward(lp_ctx* ctx, const lp_prims* prims, const lp_camera*
     ctx->tiles = tiles;
     ctx->E_bound = bound;
     ctx->key_bits = key_bits;
-    ctx->sort_passes = passes;
-    ctx->result_in_1 = in1;
+    ctx->sort_passes = passes1 + passes;
+    ctx->keys32 = mode == 1;
     return LP_OK;
 }
 
@@ -543,12 +599,33 @@ lp_status lp_debug_keys(lp_ctx* ctx, unsigned long long* keys, unsigned int* val
     *n = e;
     long long m = e < cap ? e : cap;
     if (m > ctx->E_bound) m = ctx->E_bound;
-    if (m > 0 && keys)
-        LP_CUDA(cudaMemcpy(keys, ctx->result_in_1 ? ctx->keys1.p : ctx->keys0.p, (size_t)m * 8,
-                           cudaMemcpyDeviceToHost));
-    if (m > 0 && vals)
-        LP_CUDA(cudaMemcpy(vals, ctx->result_in_1 ? ctx->vals1.p : ctx->vals0.p, (size_t)m * 4,
-                           cudaMemcpyDeviceToHost));
+    const uint32_t* dvals = ctx->result_in_1 ? ctx->vals1.p : ctx->vals0.p;
+    if (m > 0 && vals) LP_CUDA(cudaMemcpy(vals, dvals, (size_t)m * 4, cudaMemcpyDeviceToHost));
+    if (m > 0 && keys) {
+        if (!ctx->keys32) {
+            LP_CUDA(cudaMemcpy(keys, ctx->result_in_1 ? ctx->keys1.p : ctx->keys0.p, (size_t)m * 8,
+                               cudaMemcpyDeviceToHost));
+        } else {
+            // the list is keyed by tile id only; the depth half is the record's depth bits
+            uint32_t* tk = (uint32_t*)malloc((size_t)m * 4);
+            uint32_t* tv = (uint32_t*)malloc((size_t)m * 4);
+            uint32_t* zb = (uint32_t*)malloc((size_t)(ctx->records > 0 ? ctx->records : 1) * 4);
+            if (!tk || !tv || !zb) {
+                free(tk); free(tv); free(zb);
+                return fail(ctx, LP_ERR_INVALID, "host allocation failed");
+            }
+            const uint64_t* src = ctx->result_in_1 ? ctx->keys1.p : ctx->keys0.p;
+            cudaError_t e1 = cudaMemcpy(tk, src, (size_t)m * 4, cudaMemcpyDeviceToHost);
+            cudaError_t e2 = cudaMemcpy(tv, dvals, (size_t)m * 4, cudaMemcpyDeviceToHost);
+            cudaError_t e3 = cudaMemcpy(zb, ctx->zbits.p, (size_t)ctx->records * 4, cudaMemcpyDeviceToHost);
+            if (e1 == cudaSuccess && e2 == cudaSuccess && e3 == cudaSuccess)
+                for (long long q = 0; q < m; ++q)
+                    keys[q] = ((unsigned long long)tk[q] << 32) | zb[tv[q]];
+            free(tk); free(tv); free(zb);
+            if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess)
+                return fail(ctx, LP_ERR_CUDA, "debug key copy failed");
+        }
+    }
     return LP_OK;
 }
 

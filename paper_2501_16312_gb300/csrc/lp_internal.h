@@ -34,6 +34,20 @@ cudaError_t launch_radix_sort(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t
 cudaError_t launch_ranges(const uint64_t* keys, const uint32_t* n_dev, long long bound,
                           const int* status, uint2* ranges, int sms, cudaStream_t st);
 
+// two-stage sort: records by depth, then entries by 32-bit tile id
+cudaError_t launch_radix_sort32(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1,
+                                const uint32_t* n_dev, long long bound, int key_bits,
+                                uint32_t* hist, uint32_t* scan_tmp, int* passes_out, cudaStream_t st);
+cudaError_t launch_depth_keys(const uint32_t* counts, const uint32_t* zbits, long long n, uint32_t* keys,
+                              uint32_t* vals, cudaStream_t st);
+cudaError_t launch_gather_counts(const uint32_t* counts, const uint32_t* order, long long n, uint32_t* out,
+                                 cudaStream_t st);
+cudaError_t launch_emit_sorted(const uint32_t* order, const uint32_t* counts_sorted, const uint32_t* offsets,
+                               const int4* trect, int n, long long n_records, const CamsParam& cams,
+                               uint32_t* keys, uint32_t* vals, long long cap, int* status, cudaStream_t st);
+cudaError_t launch_ranges32(const uint32_t* keys, const uint32_t* n_dev, long long bound,
+                            const int* status, uint2* ranges, int sms, cudaStream_t st);
+
 struct BlendArgs {
     int grid;
     const float* rec;

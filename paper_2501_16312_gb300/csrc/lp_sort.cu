@@ -134,14 +134,15 @@ constexpr int kSortPerWarp = 512;
 constexpr int kSortChunk = kSortWarps * kSortPerWarp;   // 4096
 constexpr int kRadix = 256;
 
-__global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint64_t* __restrict__ keys,
+template <typename K>
+__global__ void __launch_bounds__(kSortThreads) k_radix_hist(const K* __restrict__ keys,
                                                              const uint32_t* __restrict__ n_dev,
                                                              long long bound, int shift, int nblocks,
                                                              uint32_t* __restrict__ hist) {
     __shared__ uint32_t h[kRadix];
     h[threadIdx.x] = 0;
     __syncthreads();
-    const long long n = min((long long)*n_dev, bound);
+    const long long n = n_dev ? min((long long)*n_dev, bound) : bound;
     const long long base = (long long)blockIdx.x * kSortChunk;
     for (int k = threadIdx.x; k < kSortChunk; k += kSortThreads) {
         const long long q = base + k;
@@ -151,13 +152,14 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint64_t* __r
     hist[(size_t)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
 }
 
+template <typename K>
 __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
-    const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin,
-    uint64_t* __restrict__ kout, uint32_t* __restrict__ vout, const uint32_t* __restrict__ n_dev,
+    const K* __restrict__ kin, const uint32_t* __restrict__ vin,
+    K* __restrict__ kout, uint32_t* __restrict__ vout, const uint32_t* __restrict__ n_dev,
     long long bound, int shift, int nblocks, const uint32_t* __restrict__ offs) {
     __shared__ uint32_t cnt[kSortWarps][kRadix];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const long long n = min((long long)*n_dev, bound);
+    const long long n = n_dev ? min((long long)*n_dev, bound) : bound;
     const long long wbase = (long long)blockIdx.x * kSortChunk + (long long)w * kSortPerWarp;
     for (int d = lane; d < kRadix; d += 32) cnt[w][d] = 0;
     __syncwarp();
@@ -183,7 +185,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
     for (int k = 0; k < kSortPerWarp; k += 32) {
         const long long q = wbase + k + lane;
         const bool ok = q < n;
-        uint64_t key = 0;
+        K key = 0;
         uint32_t val = 0, digit = kRadix;   // out-of-range lanes form their own group
         if (ok) {
             key = kin[q];
@@ -204,10 +206,61 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
     }
 }
 
+// ------------------------------------------------ two-stage (depth, tile) sort
+// Stage 1 orders the records by the binary32 bits of their centre depth
+// (records that emit nothing get the largest key); stage 2 emits every record's
+// tiles in that order with a 32-bit tile key and stably sorts the tile ids.
+// Both sorts are stable, so entries end in (tile, depth, record) order --
+// exactly the order of the one-pass 64-bit (tile << 32 | depth) sort.
+__global__ void __launch_bounds__(256) k_depth_keys(const uint32_t* __restrict__ counts,
+                                                    const uint32_t* __restrict__ zbits, long long n,
+                                                    uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    keys[r] = counts[r] ? zbits[r] : 0xffffffffu;
+    vals[r] = (uint32_t)r;
+}
+
+__global__ void __launch_bounds__(256) k_gather_counts(const uint32_t* __restrict__ counts,
+                                                       const uint32_t* __restrict__ order, long long n,
+                                                       uint32_t* __restrict__ out) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) out[k] = counts[order[k]];
+}
+
+__global__ void __launch_bounds__(256) k_emit_sorted(const uint32_t* __restrict__ order,
+                                                     const uint32_t* __restrict__ counts_sorted,
+                                                     const uint32_t* __restrict__ offsets,
+                                                     const int4* __restrict__ trect, int n,
+                                                     long long n_records, CamsParam cams,
+                                                     uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
+                                                     long long cap, int* __restrict__ status) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n_records) return;
+    const uint32_t cnt = counts_sorted[k];
+    if (cnt == 0) return;
+    const long long off = offsets[k];
+    if (off + cnt > cap) {
+        atomicOr(status, kStatusCapacity);
+        return;
+    }
+    const uint32_t r = order[k];
+    const CamDev& cm = cams.cam[r / (uint32_t)n];
+    const int4 t = trect[r];
+    long long q = off;
+    for (int ty = t.y; ty <= t.w; ++ty)
+        for (int tx = t.x; tx <= t.z; ++tx) {
+            keys[q] = (uint32_t)(cm.tile_base + ty * cm.tiles_x + tx);
+            vals[q] = r;
+            ++q;
+        }
+}
+
 // ------------------------------------------------------------- tile ranges
 // Skipped entirely when the emission overflowed: the list then holds stale
 // entries whose tile ids need not be valid, and all ranges stay empty.
-__global__ void __launch_bounds__(256) k_ranges(const uint64_t* __restrict__ keys,
+template <typename K, int SHIFT>
+__global__ void __launch_bounds__(256) k_ranges(const K* __restrict__ keys,
                                                 const uint32_t* __restrict__ n_dev, long long bound,
                                                 const int* __restrict__ status,
                                                 uint2* __restrict__ ranges) {
@@ -215,9 +268,9 @@ __global__ void __launch_bounds__(256) k_ranges(const uint64_t* __restrict__ key
     const long long n = min((long long)*n_dev, bound);
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
-        const uint32_t t = (uint32_t)(keys[i] >> 32);
-        if (i == 0 || (uint32_t)(keys[i - 1] >> 32) != t) ranges[t].x = (uint32_t)i;
-        if (i == n - 1 || (uint32_t)(keys[i + 1] >> 32) != t) ranges[t].y = (uint32_t)(i + 1);
+        const uint32_t t = (uint32_t)(keys[i] >> SHIFT);
+        if (i == 0 || (uint32_t)(keys[i - 1] >> SHIFT) != t) ranges[t].x = (uint32_t)i;
+        if (i == n - 1 || (uint32_t)(keys[i + 1] >> SHIFT) != t) ranges[t].y = (uint32_t)(i + 1);
     }
 }
 
@@ -250,21 +303,22 @@ cudaError_t launch_emit(const uint32_t* counts, const uint32_t* offsets, const i
 
 int sort_blocks(long long bound) { return (int)((bound + kSortChunk - 1) / kSortChunk); }
 
-cudaError_t launch_radix_sort(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1,
-                              const uint32_t* n_dev, long long bound, int key_bits,
-                              uint32_t* hist, uint32_t* scan_tmp, int* passes_out, cudaStream_t st) {
+template <typename K>
+static cudaError_t radix_sort_t(K* k0, uint32_t* v0, K* k1, uint32_t* v1, const uint32_t* n_dev,
+                                long long bound, int key_bits, uint32_t* hist, uint32_t* scan_tmp,
+                                int* passes_out, cudaStream_t st) {
     const int nb = sort_blocks(bound);
     int passes = 0;
     if (nb > 0) {
-        uint64_t* kin = k0; uint32_t* vin = v0;
-        uint64_t* kout = k1; uint32_t* vout = v1;
+        K* kin = k0; uint32_t* vin = v0;
+        K* kout = k1; uint32_t* vout = v1;
         for (int shift = 0; shift < key_bits; shift += 8) {
-            k_radix_hist<<<nb, kSortThreads, 0, st>>>(kin, n_dev, bound, shift, nb, hist);
+            k_radix_hist<K><<<nb, kSortThreads, 0, st>>>(kin, n_dev, bound, shift, nb, hist);
             cudaError_t e = launch_scan(hist, (long long)kRadix * nb, hist, scan_tmp, nullptr, st);
             if (e != cudaSuccess) return e;
-            k_radix_scatter<<<nb, kSortThreads, 0, st>>>(kin, vin, kout, vout, n_dev, bound, shift, nb,
-                                                         hist);
-            uint64_t* tk = kin; kin = kout; kout = tk;
+            k_radix_scatter<K><<<nb, kSortThreads, 0, st>>>(kin, vin, kout, vout, n_dev, bound, shift, nb,
+                                                            hist);
+            K* tk = kin; kin = kout; kout = tk;
             uint32_t* tv = vin; vin = vout; vout = tv;
             ++passes;
         }
@@ -273,14 +327,59 @@ cudaError_t launch_radix_sort(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t
     return cudaGetLastError();
 }
 
+cudaError_t launch_radix_sort(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1,
+                              const uint32_t* n_dev, long long bound, int key_bits,
+                              uint32_t* hist, uint32_t* scan_tmp, int* passes_out, cudaStream_t st) {
+    return radix_sort_t<uint64_t>(k0, v0, k1, v1, n_dev, bound, key_bits, hist, scan_tmp, passes_out, st);
+}
+
+cudaError_t launch_radix_sort32(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1,
+                                const uint32_t* n_dev, long long bound, int key_bits,
+                                uint32_t* hist, uint32_t* scan_tmp, int* passes_out, cudaStream_t st) {
+    return radix_sort_t<uint32_t>(k0, v0, k1, v1, n_dev, bound, key_bits, hist, scan_tmp, passes_out, st);
+}
+
 size_t sort_hist_elems(long long bound) { return (size_t)kRadix * (size_t)sort_blocks(bound); }
+
+cudaError_t launch_depth_keys(const uint32_t* counts, const uint32_t* zbits, long long n, uint32_t* keys,
+                              uint32_t* vals, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    k_depth_keys<<<(int)((n + 255) / 256), 256, 0, st>>>(counts, zbits, n, keys, vals);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_counts(const uint32_t* counts, const uint32_t* order, long long n, uint32_t* out,
+                                 cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    k_gather_counts<<<(int)((n + 255) / 256), 256, 0, st>>>(counts, order, n, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_emit_sorted(const uint32_t* order, const uint32_t* counts_sorted, const uint32_t* offsets,
+                               const int4* trect, int n, long long n_records, const CamsParam& cams,
+                               uint32_t* keys, uint32_t* vals, long long cap, int* status, cudaStream_t st) {
+    if (n_records == 0) return cudaSuccess;
+    k_emit_sorted<<<(int)((n_records + 255) / 256), 256, 0, st>>>(order, counts_sorted, offsets, trect, n,
+                                                                  n_records, cams, keys, vals, cap, status);
+    return cudaGetLastError();
+}
+
+static int ranges_grid(long long bound, int sms) {
+    const long long want = (bound + 255) / 256;
+    return (int)(want < (long long)sms * 8 ? want : (long long)sms * 8);
+}
 
 cudaError_t launch_ranges(const uint64_t* keys, const uint32_t* n_dev, long long bound,
                           const int* status, uint2* ranges, int sms, cudaStream_t st) {
     if (bound == 0) return cudaSuccess;
-    long long want = (bound + 255) / 256;
-    const int grid = (int)(want < (long long)sms * 8 ? want : (long long)sms * 8);
-    k_ranges<<<grid, 256, 0, st>>>(keys, n_dev, bound, status, ranges);
+    k_ranges<uint64_t, 32><<<ranges_grid(bound, sms), 256, 0, st>>>(keys, n_dev, bound, status, ranges);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ranges32(const uint32_t* keys, const uint32_t* n_dev, long long bound,
+                            const int* status, uint2* ranges, int sms, cudaStream_t st) {
+    if (bound == 0) return cudaSuccess;
+    k_ranges<uint32_t, 0><<<ranges_grid(bound, sms), 256, 0, st>>>(keys, n_dev, bound, status, ranges);
     return cudaGetLastError();
 }
 
