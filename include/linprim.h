@@ -222,6 +222,32 @@ lp_status lp_count_pairs(lp_ctx* ctx, long long* iterated, long long* intersecte
 lp_status lp_set_timing(lp_ctx* ctx, int enabled);
 lp_status lp_stage_times(lp_ctx* ctx, float* ms);
 
+/* Allocation-free forward render of ONE camera.  The paper has no
+ * counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc -- code running while a CUDA graph is being captured, services
+ * whose device memory belongs to a pool or budget they may not bypass,
+ * embedded or real-time hosts that forbid allocation after start-up.
+ * It runs the same kernels as lp_render_forward (default tuning, 64-bit key
+ * sort) and writes the same image, but takes no context and allocates
+ * nothing: its scratch is one fixed array of about 10.6 MiB inside the
+ * library, held by every GPU that uses it until the process exits.
+ *   prims   as for lp_render_forward; n <= 16384.
+ *   cam     one camera, width * height <= 262144 and at most 2048 16x16 tiles.
+ *   bg      host float[3]; image: device float[3][H][W], overwritten.
+ * Returns LP_ERR_CAPACITY, before launching anything, when n, the pixel or
+ * the tile count exceeds those limits, and after the key scan when the tile
+ * list would exceed 262144 entries (the image is then not written).  The
+ * call synchronises `stream` once, to read the tile-list length.
+ * All calls share the scratch array and it keeps the previous call's
+ * contents (each call clears what must start at zero): calls whose GPU work
+ * overlaps -- on different streams or host threads -- race and must be
+ * serialised by the caller.  The first call on each device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture.  No backward state is kept
+ * (lp_render_backward needs lp_render_forward).                            */
+lp_status lp_render_forward_noalloc(const lp_prims* prims, const lp_camera* cam, const float bg[3],
+                                    float* image, void* stream);
+
 /* Description of the last error on this context ("" if none).             */
 const char* lp_last_error(lp_ctx* ctx);
 

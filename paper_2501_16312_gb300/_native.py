@@ -18,7 +18,8 @@ LP_MAX_CAMERAS = 32
 EXPORTS = ("lp_create", "lp_destroy", "lp_set_tuning", "lp_get_tuning", "lp_reserve",
            "lp_render_forward", "lp_render_backward", "lp_sync_status", "lp_get_stats",
            "lp_debug_keys", "lp_debug_counts", "lp_debug_pixel_state", "lp_count_pairs",
-           "lp_last_error", "lp_status_string", "lp_set_timing", "lp_stage_times")
+           "lp_last_error", "lp_status_string", "lp_set_timing", "lp_stage_times",
+           "lp_render_forward_noalloc")
 STAGES = ("preprocess", "scan_emit", "sort", "ranges", "blend_fwd", "blend_bwd", "chain")
 
 
@@ -85,6 +86,8 @@ def load(path: str = LIB_PATH):
     L.lp_status_string.restype = C.c_char_p
     L.lp_set_timing.argtypes = [vp, i]
     L.lp_stage_times.argtypes = [vp, C.POINTER(C.c_float)]
+    L.lp_render_forward_noalloc.argtypes = [C.POINTER(lp_prims), C.POINTER(lp_camera),
+                                            C.POINTER(C.c_float), vp, vp]
     for name in EXPORTS:
         getattr(L, name)
     _lib = L

@@ -251,39 +251,39 @@ template <int V, int PIX, int NF, bool ARG>
 __device__ __forceinline__ void spans_nf(const Staged<V>& s, float lx0, float ly, float* sp, int* sf,
                                          int* sb) {
     constexpr int F = Kind<V>::F;
-    if (NF <= 0 || NF >= F) {   // no entry or no exit face: not a closed convex primitive
+    if constexpr (NF <= 0 || NF >= F) {   // no entry or no exit face: not a closed convex primitive
 #pragma unroll
         for (int i = 0; i < PIX; ++i) {
             sp[i] = 0.f;
             if (ARG) { sf[i] = 0; sb[i] = F - 1; }
         }
-        return;
-    }
-    float tf[PIX], tb[PIX];
-#pragma unroll
-    for (int i = 0; i < PIX; ++i) {
-        tf[i] = -CUDART_INF_F;
-        tb[i] = CUDART_INF_F;
-        if (ARG) { sf[i] = 0; sb[i] = F - 1; }
-    }
-#pragma unroll
-    for (int f = 0; f < F; ++f) {
-        const float4 p = s.pl[f];
-        const float t = __fmaf_rn(p.y, ly, p.z);
+    } else {
+        float tf[PIX], tb[PIX];
 #pragma unroll
         for (int i = 0; i < PIX; ++i) {
-            const float d = __fmaf_rn(p.x, lx0 + (float)i, t);
-            if (f < NF) {
-                if (ARG) { if (d > tf[i]) { tf[i] = d; sf[i] = f; } }
-                else tf[i] = fmaxf(tf[i], d);
-            } else {
-                if (ARG) { if (d < tb[i]) { tb[i] = d; sb[i] = f; } }
-                else tb[i] = fminf(tb[i], d);
+            tf[i] = -CUDART_INF_F;
+            tb[i] = CUDART_INF_F;
+            if (ARG) { sf[i] = 0; sb[i] = F - 1; }
+        }
+#pragma unroll
+        for (int f = 0; f < F; ++f) {
+            const float4 p = s.pl[f];
+            const float t = __fmaf_rn(p.y, ly, p.z);
+#pragma unroll
+            for (int i = 0; i < PIX; ++i) {
+                const float d = __fmaf_rn(p.x, lx0 + (float)i, t);
+                if (f < NF) {
+                    if (ARG) { if (d > tf[i]) { tf[i] = d; sf[i] = f; } }
+                    else tf[i] = fmaxf(tf[i], d);
+                } else {
+                    if (ARG) { if (d < tb[i]) { tb[i] = d; sb[i] = f; } }
+                    else tb[i] = fminf(tb[i], d);
+                }
             }
         }
-    }
 #pragma unroll
-    for (int i = 0; i < PIX; ++i) sp[i] = __fsub_rn(tb[i], tf[i]);
+        for (int i = 0; i < PIX; ++i) sp[i] = __fsub_rn(tb[i], tf[i]);
+    }
 }
 
 template <int V, int PIX, bool ARG>
