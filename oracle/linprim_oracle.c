@@ -473,7 +473,7 @@ typedef struct {
     double rgb[3];
     int n_contrib;
     double T_final;
-    int borderline;     /* stop decision within 1e-4 (relative) of the threshold */
+    int borderline;     /* stop decision within 1e-3 (relative) of the threshold */
     double min_span;    /* smallest span among contributors (diagnostic) */
 } orc_pixel;
 
@@ -505,7 +505,12 @@ static int blend_pixel(const orc_prims* P, const orc_view* V, const double bg[3]
         }
         ++nc;
         if (s < out->min_span) out->min_span = s;
-        if (fabs(Tn - ORC_STOP_T) <= 1e-4 * ORC_STOP_T) out->borderline = 1;
+        /* the stop test is ambiguous in binary32 when T lands within 1e-3
+         * (relative) of the threshold: the product of tens of binary32
+         * transmittance factors, some from near-camera primitives whose
+         * planes are evaluated far from their anchor, carries relative
+         * errors of that order */
+        if (fabs(Tn - ORC_STOP_T) <= 1e-3 * ORC_STOP_T) out->borderline = 1;
         T = Tn;
         /* reading: the primitive that takes T below 1e-3 is blended, then stop */
         if (T < ORC_STOP_T) break;

@@ -69,9 +69,10 @@ def test_forward_backward_parity(rast, case):
     print(f"{case}: max image err {err:.2e}, grad rel L2 {rel}")
 
 
-def test_full_size_sampled_pixels(rast):
+def test_full_size_workload(rast):
     """The 500k-octahedron, 8 x 1264x832 workload in the launch configuration
-    the benchmark times: sampled pixels of two views against the oracle."""
+    the benchmark times: every pixel of camera 0 and sampled pixels of camera 5
+    against the oracle."""
     w = scenes.workload(2)
     img, _ = gpu_forward_backward(rast, w.scene, w.cameras, (0, 0, 0))
     rng = np.random.default_rng(7)
@@ -79,14 +80,14 @@ def test_full_size_sampled_pixels(rast):
     for ci, cam in enumerate(w.cameras):
         n = cam.width * cam.height
         if ci in (0, 5):
-            q = rng.choice(n, 1500, replace=False)
+            q = np.arange(n) if ci == 0 else rng.choice(n, 4000, replace=False)
             px, py = (q % cam.width).astype(np.int32), (q // cam.width).astype(np.int32)
             ref, info = oracle.render_pixels(w.scene, cam, px, py)
             got = img[3 * off:3 * (off + n)].reshape(3, n)[:, q].T
             err = np.abs(got - ref).max(1)
             clean = info[:, 2] == 0
             assert err[clean].max() <= 1e-4, err[clean].max()
-            assert (err[~clean] > 1e-4).sum() <= 2
+            assert (err[~clean] > 1e-4).sum() <= max(2, 1e-4 * len(q))
         off += n
 
 
