@@ -20,6 +20,10 @@ namespace lp {
 
 namespace {
 
+// Warps with at most this many contributing lanes skip the shuffle
+// reductions and let each contributing lane issue its own atomic adds.
+constexpr int kSparseLanes = 4;
+
 template <int V, int BATCH, int PIX>
 __global__ void __launch_bounds__(kTilePixels / PIX) k_blend_bwd(
     const float* __restrict__ rec, const uint32_t* __restrict__ vals, const uint2* __restrict__ ranges,
@@ -89,41 +93,71 @@ __global__ void __launch_bounds__(kTilePixels / PIX) k_blend_bwd(
 #pragma unroll
                 for (int i = 0; i < PIX; ++i) c[i] = false;
                 if (any) {
-                    spans<V, PIX, true>(p, (float)lx0, (float)ly, sp, sf, sb);
+                    spans<V, PIX, false>(p, (float)lx0, (float)ly, sp, nullptr, nullptr);
 #pragma unroll
                     for (int i = 0; i < PIX; ++i) {
                         c[i] = idx < last[i] && sp[i] > 0.f;
                         anyc |= c[i];
                     }
                 }
-                if (__ballot_sync(0xffffffffu, anyc) == 0u) continue;
+                const unsigned bal = __ballot_sync(0xffffffffu, anyc);
+                if (bal == 0u) continue;
                 float gr0 = 0.f, gr1 = 0.f, gr2 = 0.f, gsig = 0.f;
                 float gsp[PIX];
                 unsigned used = 0;
 #pragma unroll
-                for (int i = 0; i < PIX; ++i) {
-                    gsp[i] = 0.f;
-                    if (c[i]) {
-                        const float tau = span_tau(p.sigma, sp[i]);
-                        const float o = 1.f - tau;
-                        const float Ti = first[i] ? Tcur[i] : Tcur[i] / tau;
-                        first[i] = false;
-                        Tcur[i] = Ti;
-                        const float w = Ti * o;
-                        gr0 = fmaf(w, g0[i], gr0);
-                        gr1 = fmaf(w, g1[i], gr1);
-                        gr2 = fmaf(w, g2[i], gr2);
-                        const float dLdo = Ti * ((p.r - B0[i]) * g0[i] + (p.g - B1[i]) * g1[i] +
-                                                 (p.b - B2[i]) * g2[i]);
-                        B0[i] = fmaf(o, p.r, tau * B0[i]);
-                        B1[i] = fmaf(o, p.g, tau * B1[i]);
-                        B2[i] = fmaf(o, p.b, tau * B2[i]);
-                        gsp[i] = dLdo * p.sigma * tau;        // dL/d span
-                        gsig = fmaf(dLdo * sp[i], tau, gsig);  // dL/d sigma
-                        used |= (1u << sf[i]) | (1u << sb[i]);
+                for (int i = 0; i < PIX; ++i) gsp[i] = 0.f;
+                if (anyc) {
+                    // entry/exit faces only where a pixel contributes (same spans)
+                    spans<V, PIX, true>(p, (float)lx0, (float)ly, sp, sf, sb);
+#pragma unroll
+                    for (int i = 0; i < PIX; ++i) {
+                        if (c[i]) {
+                            const float tau = span_tau(p.sigma, sp[i]);
+                            const float o = 1.f - tau;
+                            const float Ti = first[i] ? Tcur[i] : Tcur[i] / tau;
+                            first[i] = false;
+                            Tcur[i] = Ti;
+                            const float w = Ti * o;
+                            gr0 = fmaf(w, g0[i], gr0);
+                            gr1 = fmaf(w, g1[i], gr1);
+                            gr2 = fmaf(w, g2[i], gr2);
+                            const float dLdo = Ti * ((p.r - B0[i]) * g0[i] + (p.g - B1[i]) * g1[i] +
+                                                     (p.b - B2[i]) * g2[i]);
+                            B0[i] = fmaf(o, p.r, tau * B0[i]);
+                            B1[i] = fmaf(o, p.g, tau * B1[i]);
+                            B2[i] = fmaf(o, p.b, tau * B2[i]);
+                            gsp[i] = dLdo * p.sigma * tau;        // dL/d span
+                            gsig = fmaf(dLdo * sp[i], tau, gsig);  // dL/d sigma
+                            used |= (1u << sf[i]) | (1u << sb[i]);
+                        }
                     }
                 }
                 float* A = acc + (size_t)p.rec * ACC;
+                // plane gradients use offsets (px - X0, py - Y0) from the anchor
+                const float lyc = (float)ly + p.dy0;
+                if (__popc(bal) <= kSparseLanes) {
+                    // few contributing lanes: each adds its own terms
+                    if (anyc) {
+                        atomicAdd(A + 3 * F + 0, gr0);
+                        atomicAdd(A + 3 * F + 1, gr1);
+                        atomicAdd(A + 3 * F + 2, gr2);
+                        atomicAdd(A + 3 * F + 3, gsig);
+#pragma unroll
+                        for (int i = 0; i < PIX; ++i) {
+                            if (c[i]) {
+                                const float lxc = (float)(lx0 + i) + p.dx0;
+                                atomicAdd(A + 3 * sf[i] + 0, -gsp[i] * lxc);
+                                atomicAdd(A + 3 * sf[i] + 1, -gsp[i] * lyc);
+                                atomicAdd(A + 3 * sf[i] + 2, -gsp[i]);
+                                atomicAdd(A + 3 * sb[i] + 0, gsp[i] * lxc);
+                                atomicAdd(A + 3 * sb[i] + 1, gsp[i] * lyc);
+                                atomicAdd(A + 3 * sb[i] + 2, gsp[i]);
+                            }
+                        }
+                    }
+                    continue;
+                }
                 gr0 = warp_sum(gr0); gr1 = warp_sum(gr1); gr2 = warp_sum(gr2); gsig = warp_sum(gsig);
                 if (lane == 0) {
                     atomicAdd(A + 3 * F + 0, gr0);
@@ -131,9 +165,7 @@ __global__ void __launch_bounds__(kTilePixels / PIX) k_blend_bwd(
                     atomicAdd(A + 3 * F + 2, gr2);
                     atomicAdd(A + 3 * F + 3, gsig);
                 }
-                // plane gradients, with offsets (px - X0, py - Y0) from the anchor
                 used = __reduce_or_sync(0xffffffffu, used);
-                const float lyc = (float)ly + p.dy0;
                 while (used) {
                     const int f = __ffs(used) - 1;
                     used &= used - 1;

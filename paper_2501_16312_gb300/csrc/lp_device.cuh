@@ -201,6 +201,19 @@ __device__ __forceinline__ void sh_basis_vjp(float x, float y, float z, const fl
 }
 
 // -------------------------------------------------------------------------
+// 3-input FP32 min/max (Blackwell), as inline PTX; exact like fminf/fmaxf.
+__device__ __forceinline__ float max3f(float a, float b, float c) {
+    float d;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+__device__ __forceinline__ float min3f(float a, float b, float c) {
+    float d;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+
+// -------------------------------------------------------------------------
 // A record staged in shared memory for one tile: the planes are re-based to
 // the tile's first pixel (tx0, ty0), an exact integer offset (dx0, dy0) from
 // (X0, Y0), so that pixel (tx0 + lx, ty0 + ly) evaluates depth = a lx + b ly
@@ -257,13 +270,13 @@ __device__ __forceinline__ void spans_nf(const Staged<V>& s, float lx0, float ly
             sp[i] = 0.f;
             if (ARG) { sf[i] = 0; sb[i] = F - 1; }
         }
-    } else {
+    } else if constexpr (ARG) {
         float tf[PIX], tb[PIX];
 #pragma unroll
         for (int i = 0; i < PIX; ++i) {
             tf[i] = -CUDART_INF_F;
             tb[i] = CUDART_INF_F;
-            if (ARG) { sf[i] = 0; sb[i] = F - 1; }
+            sf[i] = 0; sb[i] = F - 1;
         }
 #pragma unroll
         for (int f = 0; f < F; ++f) {
@@ -272,17 +285,34 @@ __device__ __forceinline__ void spans_nf(const Staged<V>& s, float lx0, float ly
 #pragma unroll
             for (int i = 0; i < PIX; ++i) {
                 const float d = __fmaf_rn(p.x, lx0 + (float)i, t);
-                if (f < NF) {
-                    if (ARG) { if (d > tf[i]) { tf[i] = d; sf[i] = f; } }
-                    else tf[i] = fmaxf(tf[i], d);
-                } else {
-                    if (ARG) { if (d < tb[i]) { tb[i] = d; sb[i] = f; } }
-                    else tb[i] = fminf(tb[i], d);
-                }
+                if (f < NF) { if (d > tf[i]) { tf[i] = d; sf[i] = f; } }
+                else        { if (d < tb[i]) { tb[i] = d; sb[i] = f; } }
             }
         }
 #pragma unroll
         for (int i = 0; i < PIX; ++i) sp[i] = __fsub_rn(tb[i], tf[i]);
+    } else {
+        // depths of all faces, then entry max / exit min two faces per 3-input op
+        float d[F][PIX];
+#pragma unroll
+        for (int f = 0; f < F; ++f) {
+            const float4 p = s.pl[f];
+            const float t = __fmaf_rn(p.y, ly, p.z);
+#pragma unroll
+            for (int i = 0; i < PIX; ++i) d[f][i] = __fmaf_rn(p.x, lx0 + (float)i, t);
+        }
+#pragma unroll
+        for (int i = 0; i < PIX; ++i) {
+            float tf = d[0][i];
+#pragma unroll
+            for (int f = 1; f + 1 < NF; f += 2) tf = max3f(tf, d[f][i], d[f + 1][i]);
+            if ((NF - 1) % 2 == 1) tf = fmaxf(tf, d[NF - 1][i]);
+            float tb = d[NF][i];
+#pragma unroll
+            for (int f = NF + 1; f + 1 < F; f += 2) tb = min3f(tb, d[f][i], d[f + 1][i]);
+            if ((F - NF - 1) % 2 == 1) tb = fminf(tb, d[F - 1][i]);
+            sp[i] = __fsub_rn(tb, tf);
+        }
     }
 }
 

@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(128) k_preprocess(PrimsDev P, CamsParam cams, 
         zbits[r] = __float_as_uint(g.tc[2]);
         if (!vis) {
             counts[r] = 0;
-            trect[r] = make_int4(1, 1, 0, 0);
+            trect[r] = make_int4(0, 0, 0, 0);
             continue;
         }
         float q[V][3];
@@ -190,13 +190,14 @@ __global__ void __launch_bounds__(128) k_preprocess(PrimsDev P, CamsParam cams, 
         fy0 = fmaxf(fy0, 0.f); fy1 = fminf(fy1, (float)(cm.height - 1));
         if (fx0 > fx1 || fy0 > fy1) {
             counts[r] = 0;
-            trect[r] = make_int4(1, 1, 0, 0);
+            trect[r] = make_int4(0, 0, 0, 0);
             continue;
         }
         const int T = cams.tile;
         const int tx0 = (int)fx0 / T, tx1 = (int)fx1 / T, ty0 = (int)fy0 / T, ty1 = (int)fy1 / T;
         counts[r] = (uint32_t)((tx1 - tx0 + 1) * (ty1 - ty0 + 1));
-        trect[r] = make_int4(tx0, ty0, tx1, ty1);
+        // global id of the rectangle's first tile, row stride, width, height
+        trect[r] = make_int4(cm.tile_base + ty0 * cm.tiles_x + tx0, cm.tiles_x, tx1 - tx0 + 1, ty1 - ty0 + 1);
 
         // Face planes in the local frame (origin at the ray-space centre,
         // which lies inside the primitive): outward normal n, entry face iff
@@ -310,6 +311,10 @@ __global__ void __launch_bounds__(128) k_chain(PrimsDev P, CamsParam cams,
         if (counts[r] == 0) continue;
         const CamDev& cm = cams.cam[cv];
         const float* A = acc + r * Acc<V>::kFloats;
+        bool any = false;
+#pragma unroll
+        for (int q = 0; q < Acc<V>::kFloats; ++q) any |= A[q] != 0.f;
+        if (!any) continue;   // no pixel produced a gradient for this record
         float ga_rgb[3], ga_sig;
         ga_rgb[0] = A[3 * F]; ga_rgb[1] = A[3 * F + 1]; ga_rgb[2] = A[3 * F + 2];
         ga_sig = A[3 * F + 3];

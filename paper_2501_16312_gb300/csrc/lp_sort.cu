@@ -94,34 +94,72 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(const uint32_t* __re
 }
 
 // ------------------------------------------------------------- key emission
+// Each record's tile rectangle is (first global tile id, row stride, width,
+// height).  A lane writes the entries of a small rectangle itself; larger
+// rectangles are written by the whole warp, one record at a time, so that a
+// near-camera primitive covering thousands of tiles does not serialise on one
+// thread and its writes stay coalesced.
+constexpr uint32_t kEmitLaneMax = 8;
+
+template <typename WriteFn>
+__device__ __forceinline__ void emit_rect(const int4 t, long long off, uint32_t cnt, uint32_t first_q,
+                                          uint32_t step, WriteFn write) {
+    for (uint32_t q = first_q; q < cnt; q += step) {
+        const uint32_t row = q / (uint32_t)t.z, col = q - row * (uint32_t)t.z;
+        write(off + q, (uint32_t)t.x + row * (uint32_t)t.y + col);
+    }
+}
+
 __global__ void __launch_bounds__(256) k_emit(const uint32_t* __restrict__ counts,
                                               const uint32_t* __restrict__ offsets,
                                               const int4* __restrict__ trect,
-                                              const uint32_t* __restrict__ zbits, int n,
-                                              long long n_records, CamsParam cams,
-                                              uint64_t* __restrict__ keys, uint32_t* __restrict__ vals,
-                                              long long cap, int* __restrict__ status) {
+                                              const uint32_t* __restrict__ zbits,
+                                              long long n_records, uint64_t* __restrict__ keys,
+                                              uint32_t* __restrict__ vals, long long cap,
+                                              int* __restrict__ status) {
     const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= n_records) return;
-    const uint32_t cnt = counts[r];
-    if (cnt == 0) return;
-    const long long off = offsets[r];
-    if (off + cnt > cap) {
-        atomicOr(status, kStatusCapacity);
-        return;
-    }
-    const int cv = (int)(r / n);
-    const CamDev& cm = cams.cam[cv];
-    const int4 t = trect[r];
-    const uint64_t z = zbits[r];
-    long long k = off;
-    for (int ty = t.y; ty <= t.w; ++ty)
-        for (int tx = t.x; tx <= t.z; ++tx) {
-            const uint64_t gt = (uint64_t)(cm.tile_base + ty * cm.tiles_x + tx);
-            keys[k] = (gt << 32) | z;
-            vals[k] = (uint32_t)r;
-            ++k;
+    uint32_t cnt = 0;
+    long long off = 0;
+    int4 t = make_int4(0, 0, 0, 0);
+    uint32_t z = 0;
+    if (r < n_records) {
+        cnt = counts[r];
+        if (cnt) {
+            off = offsets[r];
+            if (off + cnt > cap) {
+                atomicOr(status, kStatusCapacity);
+                cnt = 0;
+            } else {
+                t = trect[r];
+                z = zbits[r];
+            }
         }
+    }
+    const bool have = cnt > 0;
+    if (have && cnt <= kEmitLaneMax)
+        emit_rect(t, off, cnt, 0, 1, [&](long long q, uint32_t tile) {
+            keys[q] = ((uint64_t)tile << 32) | z;
+            vals[q] = (uint32_t)r;
+        });
+    const int lane = threadIdx.x & 31;
+    unsigned big = __ballot_sync(0xffffffffu, have && cnt > kEmitLaneMax);
+    while (big) {
+        const int src = __ffs(big) - 1;
+        big &= big - 1;
+        const uint32_t c = __shfl_sync(0xffffffffu, cnt, src);
+        const long long o = __shfl_sync(0xffffffffu, off, src);
+        const uint32_t zz = __shfl_sync(0xffffffffu, z, src);
+        const long long rr = __shfl_sync(0xffffffffu, r, src);
+        int4 tt;
+        tt.x = __shfl_sync(0xffffffffu, t.x, src);
+        tt.y = __shfl_sync(0xffffffffu, t.y, src);
+        tt.z = __shfl_sync(0xffffffffu, t.z, src);
+        tt.w = __shfl_sync(0xffffffffu, t.w, src);
+        emit_rect(tt, o, c, lane, 32, [&](long long q, uint32_t tile) {
+            keys[q] = ((uint64_t)tile << 32) | zz;
+            vals[q] = (uint32_t)rr;
+        });
+    }
 }
 
 // ---------------------------------------------------------- LSD radix sort
@@ -231,32 +269,53 @@ __global__ void __launch_bounds__(256) k_gather_counts(const uint32_t* __restric
 __global__ void __launch_bounds__(256) k_emit_sorted(const uint32_t* __restrict__ order,
                                                      const uint32_t* __restrict__ counts_sorted,
                                                      const uint32_t* __restrict__ offsets,
-                                                     const int4* __restrict__ trect, int n,
-                                                     long long n_records, CamsParam cams,
-                                                     uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
-                                                     long long cap, int* __restrict__ status) {
+                                                     const int4* __restrict__ trect,
+                                                     long long n_records, uint32_t* __restrict__ keys,
+                                                     uint32_t* __restrict__ vals, long long cap,
+                                                     int* __restrict__ status) {
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n_records) return;
-    const uint32_t cnt = counts_sorted[k];
-    if (cnt == 0) return;
-    const long long off = offsets[k];
-    if (off + cnt > cap) {
-        atomicOr(status, kStatusCapacity);
-        return;
-    }
-    const uint32_t r = order[k];
-    const CamDev& cm = cams.cam[r / (uint32_t)n];
-    const int4 t = trect[r];
-    long long q = off;
-    for (int ty = t.y; ty <= t.w; ++ty)
-        for (int tx = t.x; tx <= t.z; ++tx) {
-            keys[q] = (uint32_t)(cm.tile_base + ty * cm.tiles_x + tx);
-            vals[q] = r;
-            ++q;
+    uint32_t cnt = 0, r = 0;
+    long long off = 0;
+    int4 t = make_int4(0, 0, 0, 0);
+    if (k < n_records) {
+        cnt = counts_sorted[k];
+        if (cnt) {
+            off = offsets[k];
+            if (off + cnt > cap) {
+                atomicOr(status, kStatusCapacity);
+                cnt = 0;
+            } else {
+                r = order[k];
+                t = trect[r];
+            }
         }
+    }
+    const bool have = cnt > 0;
+    if (have && cnt <= kEmitLaneMax)
+        emit_rect(t, off, cnt, 0, 1, [&](long long q, uint32_t tile) {
+            keys[q] = tile;
+            vals[q] = r;
+        });
+    const int lane = threadIdx.x & 31;
+    unsigned big = __ballot_sync(0xffffffffu, have && cnt > kEmitLaneMax);
+    while (big) {
+        const int src = __ffs(big) - 1;
+        big &= big - 1;
+        const uint32_t c = __shfl_sync(0xffffffffu, cnt, src);
+        const long long o = __shfl_sync(0xffffffffu, off, src);
+        const uint32_t rr = __shfl_sync(0xffffffffu, r, src);
+        int4 tt;
+        tt.x = __shfl_sync(0xffffffffu, t.x, src);
+        tt.y = __shfl_sync(0xffffffffu, t.y, src);
+        tt.z = __shfl_sync(0xffffffffu, t.z, src);
+        tt.w = __shfl_sync(0xffffffffu, t.w, src);
+        emit_rect(tt, o, c, lane, 32, [&](long long q, uint32_t tile) {
+            keys[q] = tile;
+            vals[q] = rr;
+        });
+    }
 }
 
-// ------------------------------------------------------------- tile ranges
 // Skipped entirely when the emission overflowed: the list then holds stale
 // entries whose tile ids need not be valid, and all ranges stay empty.
 template <typename K, int SHIFT>
@@ -294,10 +353,11 @@ cudaError_t launch_scan(const uint32_t* in, long long n, uint32_t* out, uint32_t
 cudaError_t launch_emit(const uint32_t* counts, const uint32_t* offsets, const int4* trect,
                         const uint32_t* zbits, int n, long long n_records, const CamsParam& cams,
                         uint64_t* keys, uint32_t* vals, long long cap, int* status, cudaStream_t st) {
+    (void)n;
+    (void)cams;
     if (n_records == 0) return cudaSuccess;
     const int grid = (int)((n_records + 255) / 256);
-    k_emit<<<grid, 256, 0, st>>>(counts, offsets, trect, zbits, n, n_records, cams, keys, vals, cap,
-                                 status);
+    k_emit<<<grid, 256, 0, st>>>(counts, offsets, trect, zbits, n_records, keys, vals, cap, status);
     return cudaGetLastError();
 }
 
@@ -358,9 +418,11 @@ cudaError_t launch_gather_counts(const uint32_t* counts, const uint32_t* order, 
 cudaError_t launch_emit_sorted(const uint32_t* order, const uint32_t* counts_sorted, const uint32_t* offsets,
                                const int4* trect, int n, long long n_records, const CamsParam& cams,
                                uint32_t* keys, uint32_t* vals, long long cap, int* status, cudaStream_t st) {
+    (void)n;
+    (void)cams;
     if (n_records == 0) return cudaSuccess;
-    k_emit_sorted<<<(int)((n_records + 255) / 256), 256, 0, st>>>(order, counts_sorted, offsets, trect, n,
-                                                                  n_records, cams, keys, vals, cap, status);
+    k_emit_sorted<<<(int)((n_records + 255) / 256), 256, 0, st>>>(order, counts_sorted, offsets, trect,
+                                                                  n_records, keys, vals, cap, status);
     return cudaGetLastError();
 }
 
