@@ -110,16 +110,16 @@ def measured_peaks():
 
 
 # Algorithmic FP32 work of the blend kernels, in flops (an FMA counts 2):
-#   forward, per iterated (pixel, primitive) pair: F planes x 2 FMA + F
-#   min/max + span subtraction + span test       = 5F + 2
+#   per evaluated (pixel, primitive) pair: F planes x 2 FMA + F min/max +
+#   span subtraction + span test                 = 5F + 2
 #   forward, per intersected pair: sigma*s, exp, 1 - tau, T*(1-tau),
 #   3 colour FMA, T*tau, stop test               = 12
-#   backward, per evaluated pair: the same 5F + 2; per contributor: tau,
-#   T division, 3 colour grads, dL/do (3 FMA), suffix colour (3 FMA + 3 mul),
-#   span/sigma grads and the (lx, ly, 1) weights of two faces ~ 40
-def blend_flops(F, iterated, intersected, evaluated_bwd):
-    fwd = (5 * F + 2) * iterated + 12 * intersected
-    bwd = (5 * F + 2) * evaluated_bwd + 40 * intersected
+#   backward, per pair evaluated up to the pixel's last contributor: 5F + 2;
+#   per contributor: tau, T division, 3 colour grads, dL/do (3 FMA), suffix
+#   colour (3 FMA + 3 mul), span/sigma grads, (x, y, 1) weights of two faces ~ 40
+def blend_flops(F, pairs):
+    fwd = (5 * F + 2) * pairs["evaluated"] + 12 * pairs["intersected"]
+    bwd = (5 * F + 2) * pairs["evaluated_to_last"] + 40 * pairs["intersected"]
     return fwd, bwd
 
 
@@ -391,12 +391,10 @@ def ours(args, workload):
     # ---- roofline of the dominant kernel
     graph.replay()
     torch.cuda.synchronize()
-    iterated, intersected = rast.count_pairs()
-    last, _ = rast.pixel_state()
-    evaluated_bwd = int(last.astype(np.int64).sum())
+    pairs = rast.count_pairs()
     st = rast.stats()
     F = 8 if w.scene.kind == 6 else 4
-    fl_fwd, fl_bwd = blend_flops(F, iterated, intersected, evaluated_bwd)
+    fl_fwd, fl_bwd = blend_flops(F, pairs)
     peaks, peak_src = measured_peaks()
     props = torch.cuda.get_device_properties(dev)
     sm_max = peaks.get("sm_max_mhz") or clk.get("sm_max_mhz") or 2070.0
@@ -440,8 +438,7 @@ def ours(args, workload):
                 "gpu_launches": (st["launches_fwd"] + st["launches_bwd"]) * args.steps,
                 "roofline": roof, "stages": stage_report, "clocks": clk,
                 "workload_counts": {"records": st["records"], "tile_list_entries": st["entries"],
-                                    "iterated_pairs": iterated, "intersected_pairs": intersected,
-                                    "bwd_evaluated_pairs": evaluated_bwd,
+                                    "pairs": pairs,
                                     "sort_passes": st["sort_passes"]},
                 "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)

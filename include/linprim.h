@@ -209,9 +209,17 @@ lp_status lp_debug_counts(lp_ctx* ctx, unsigned int* counts, long long cap);
 lp_status lp_debug_pixel_state(lp_ctx* ctx, unsigned int* last, float* T_last, long long cap);
 
 /* Workload counters of the last forward (synchronises; runs an instrumented
- * copy of the blend): iterated and intersected (pixel, primitive) pairs as
- * in the paper's App. "Rendering Performance", Table 7.                    */
-lp_status lp_count_pairs(lp_ctx* ctx, long long* iterated, long long* intersected);
+ * copy of the blend).  counts: host long long[4] receiving the numbers of
+ * (pixel, primitive) pairs
+ *   [0] iterated: tile-list entries each pixel visits before it stops,
+ *   [1] evaluated: of those, pairs whose face planes are evaluated (every
+ *       visited entry, in this implementation),
+ *   [2] intersected: the pixel ray crosses the primitive,
+ *   [3] evaluated up to each pixel's last contributor (the pairs the
+ *       backward re-evaluates).
+ * [0] and [2] are the "iterated" and "intersected" counts of the paper's
+ * App. "Rendering Performance and Efficiency", Table 7.                     */
+lp_status lp_count_pairs(lp_ctx* ctx, long long* counts);
 
 /* Per-stage device timing.  When enabled, forward and backward record CUDA
  * events between their stages on the call's stream (inside stream capture

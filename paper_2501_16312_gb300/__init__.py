@@ -192,11 +192,13 @@ class Rasterizer:
         _native.check(self.ctx, self.lib.lp_stage_times(self.ctx, ms), "lp_stage_times")
         return dict(zip(_native.STAGES, [float(x) for x in ms]))
 
-    def count_pairs(self):
-        a, b = C.c_longlong(0), C.c_longlong(0)
-        _native.check(self.ctx, self.lib.lp_count_pairs(self.ctx, C.byref(a), C.byref(b)),
-                      "lp_count_pairs")
-        return a.value, b.value
+    def count_pairs(self) -> dict:
+        """(pixel, primitive) pair counts of the last forward: iterated,
+        evaluated (face planes evaluated), intersected, and evaluated up to
+        each pixel's last contributor (the backward's work)."""
+        out = (C.c_longlong * 4)()
+        _native.check(self.ctx, self.lib.lp_count_pairs(self.ctx, out), "lp_count_pairs")
+        return dict(iterated=out[0], evaluated=out[1], intersected=out[2], evaluated_to_last=out[3])
 
 
 def _make_fn():

@@ -79,7 +79,7 @@ def load(path: str = LIB_PATH):
     L.lp_debug_keys.argtypes = [vp, vp, vp, ll, C.POINTER(ll)]
     L.lp_debug_counts.argtypes = [vp, vp, ll]
     L.lp_debug_pixel_state.argtypes = [vp, vp, vp, ll]
-    L.lp_count_pairs.argtypes = [vp, C.POINTER(ll), C.POINTER(ll)]
+    L.lp_count_pairs.argtypes = [vp, C.POINTER(ll)]
     L.lp_last_error.argtypes = [vp]
     L.lp_last_error.restype = C.c_char_p
     L.lp_status_string.argtypes = [i]

@@ -243,7 +243,7 @@ lp_status lp_create(lp_ctx** out, int device) {
     if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->d_status, sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->d_E, sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->d_tile_counter, 2 * sizeof(int));
-    if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->d_pairs, 2 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->d_pairs, 4 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->h_E, sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMemset(ctx->d_status, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(ctx->d_E, 0, sizeof(uint32_t));
@@ -650,8 +650,8 @@ lp_status lp_debug_pixel_state(lp_ctx* ctx, unsigned int* last, float* T_last, l
     return LP_OK;
 }
 
-lp_status lp_count_pairs(lp_ctx* ctx, long long* iterated, long long* intersected) {
-    if (!ctx || !iterated || !intersected) return LP_ERR_INVALID;
+lp_status lp_count_pairs(lp_ctx* ctx, long long* counts) {
+    if (!ctx || !counts) return LP_ERR_INVALID;
     if (!ctx->have_fwd) return fail(ctx, LP_ERR_STATE, "no forward");
     LP_CUDA(cudaSetDevice(ctx->device));
     LP_CUDA(cudaDeviceSynchronize());
@@ -669,14 +669,13 @@ lp_status lp_count_pairs(lp_ctx* ctx, long long* iterated, long long* intersecte
     a.tile_counter = ctx->d_tile_counter;
     a.pair_counts = ctx->d_pairs;
     a.count = true;
-    LP_CUDA(cudaMemset(ctx->d_pairs, 0, 2 * sizeof(unsigned long long)));
+    LP_CUDA(cudaMemset(ctx->d_pairs, 0, 4 * sizeof(unsigned long long)));
     LP_CUDA(cudaMemset(ctx->d_tile_counter, 0, sizeof(int)));
     if (a.grid > 0) LP_CUDA(lp::launch_blend_fwd(ctx->prims.kind, ctx->tune.batch, ctx->tune.pixels_per_thread, a, 0));
     LP_CUDA(cudaDeviceSynchronize());
-    unsigned long long h[2] = {0, 0};
+    unsigned long long h[4] = {0, 0, 0, 0};
     LP_CUDA(cudaMemcpy(h, ctx->d_pairs, sizeof(h), cudaMemcpyDeviceToHost));
-    *iterated = (long long)h[0];
-    *intersected = (long long)h[1];
+    for (int q = 0; q < 4; ++q) counts[q] = (long long)h[q];
     return LP_OK;
 }
 

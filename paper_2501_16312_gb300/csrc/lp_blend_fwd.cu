@@ -27,7 +27,7 @@ __global__ void __launch_bounds__(kTilePixels / PIX) k_blend_fwd(
     __shared__ int s_tile;
     const int tid = threadIdx.x;
     const int ly = tid / RW, lx0 = (tid % RW) * PIX;
-    unsigned long long n_iter = 0, n_hit = 0;
+    unsigned long long n_iter = 0, n_eval = 0, n_hit = 0, n_eval_last = 0;
     for (;;) {
         if (tid == 0) s_tile = atomicAdd(tile_counter, 1);
         __syncthreads();
@@ -39,11 +39,13 @@ __global__ void __launch_bounds__(kTilePixels / PIX) k_blend_fwd(
         const int n = (int)(rg.y - rg.x);
         float T[PIX], c0[PIX], c1[PIX], c2[PIX], tl[PIX];
         uint32_t last[PIX];
+        uint32_t ce[PIX], cl[PIX];   // counting only: evaluations so far / at the last contributor
         bool done[PIX];
         bool tdone = true;
 #pragma unroll
         for (int i = 0; i < PIX; ++i) {
             T[i] = 1.f; c0[i] = c1[i] = c2[i] = 0.f; tl[i] = 1.f; last[i] = 0;
+            ce[i] = cl[i] = 0;
             done[i] = !(tg.tx0 + lx0 + i < tg.width && py < tg.height);
             tdone &= done[i];
         }
@@ -55,14 +57,19 @@ __global__ void __launch_bounds__(kTilePixels / PIX) k_blend_fwd(
             if (!tdone) {
                 for (int j = 0; j < nb; ++j) {
                     const Staged<V>& p = sm[j];
+                    if (COUNT) {
+#pragma unroll
+                        for (int i = 0; i < PIX; ++i) n_iter += !done[i];
+                    }
                     float sp[PIX];
                     spans<V, PIX, false>(p, (float)lx0, (float)ly, sp, nullptr, nullptr);
                     tdone = true;
 #pragma unroll
                     for (int i = 0; i < PIX; ++i) {
-                        if (COUNT && !done[i]) ++n_iter;
-                        if (!done[i] && sp[i] > 0.f) {
-                            if (COUNT) ++n_hit;
+                        const bool in = !done[i];   // every visited entry is evaluated
+                        if (COUNT) { n_eval += in; ce[i] += in; }
+                        if (in && sp[i] > 0.f) {
+                            if (COUNT) { ++n_hit; cl[i] = ce[i]; }
                             const float tau = span_tau(p.sigma, sp[i]);
                             const float w = T[i] * (1.f - tau);
                             c0[i] = fmaf(w, p.r, c0[i]);
@@ -78,6 +85,10 @@ __global__ void __launch_bounds__(kTilePixels / PIX) k_blend_fwd(
                     if (tdone) break;
                 }
             }
+        }
+        if (COUNT) {
+#pragma unroll
+            for (int i = 0; i < PIX; ++i) n_eval_last += cl[i];
         }
         const int plane = tg.width * tg.height;
         float* img = image + 3 * (size_t)tg.pix_base;
@@ -96,15 +107,19 @@ __global__ void __launch_bounds__(kTilePixels / PIX) k_blend_fwd(
         __syncthreads();
     }
     if (COUNT) {
-        unsigned long long a = n_iter, b = n_hit;
+        unsigned long long a = n_iter, b = n_eval, c = n_hit, d = n_eval_last;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             a += __shfl_xor_sync(0xffffffffu, a, o);
             b += __shfl_xor_sync(0xffffffffu, b, o);
+            c += __shfl_xor_sync(0xffffffffu, c, o);
+            d += __shfl_xor_sync(0xffffffffu, d, o);
         }
         if ((tid & 31) == 0) {
             atomicAdd(pair_counts, a);
             atomicAdd(pair_counts + 1, b);
+            atomicAdd(pair_counts + 2, c);
+            atomicAdd(pair_counts + 3, d);
         }
     }
 }

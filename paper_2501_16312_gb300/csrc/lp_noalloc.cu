@@ -133,7 +133,7 @@ extern "C" lp_status lp_render_forward_noalloc(const lp_prims* prims, const lp_c
     uint32_t* d_E = reinterpret_cast<uint32_t*>(base + kOffMisc);
     int* d_status = reinterpret_cast<int*>(base + kOffMisc + 4);
     int* d_tile_counter = reinterpret_cast<int*>(base + kOffMisc + 8);
-    unsigned long long* d_pairs = reinterpret_cast<unsigned long long*>(base + kOffMisc + 16);
+    unsigned long long* d_pairs = reinterpret_cast<unsigned long long*>(base + kOffMisc + 16);   // 3 counters
 
     // camera, digested as for lp_render_forward
     lp::CamsParam cp;

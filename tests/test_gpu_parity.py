@@ -229,3 +229,18 @@ def test_every_tuning_renders_identical_images(rast):
                 assert rel_l2(g[k], ref_g[k]) <= 1e-5, (sm, pix, batch, bps, k)
     finally:
         rast.set_tuning(**base)
+
+
+def test_pair_counters_match_oracle_contributors(rast):
+    """The intersected-pair counter equals the oracle's number of blended
+    (pixel, primitive) pairs up to binary32 ties at silhouettes; the four
+    counters are ordered iterated >= evaluated >= evaluated-to-last and
+    evaluated >= intersected."""
+    w = scenes.workload(1)
+    gpu_forward_backward(rast, w.scene, w.cameras, (0, 0, 0))
+    c = rast.count_pairs()
+    _, info = oracle.render(w.scene, w.cameras, info=True)
+    n_contrib = int(info[:, 0].sum())
+    assert abs(c["intersected"] - n_contrib) <= 1e-4 * n_contrib + 2, (c, n_contrib)
+    assert c["iterated"] >= c["evaluated"] >= c["evaluated_to_last"] >= 0
+    assert c["evaluated"] >= c["intersected"] > 0
