@@ -115,7 +115,9 @@ __global__ void __launch_bounds__(kTilePixels / PIX) k_blend_bwd(
                         if (c[i]) {
                             const float tau = span_tau(p.sigma, sp[i]);
                             const float o = 1.f - tau;
-                            const float Ti = first[i] ? Tcur[i] : Tcur[i] / tau;
+                            // tau >= 1e-3 wherever we divide (T stayed >= 1e-3 before
+                            // the last contributor), so the fast division is safe
+                            const float Ti = first[i] ? Tcur[i] : __fdividef(Tcur[i], tau);
                             first[i] = false;
                             Tcur[i] = Ti;
                             const float w = Ti * o;
