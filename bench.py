@@ -40,6 +40,8 @@ def parse_args():
     p.add_argument("--config", type=int, default=2, choices=[1, 2, 3])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-per-view", action="store_true")
+    p.add_argument("--tuning", default="",
+                   help="fixed schedule instead of autotuning, e.g. sort_mode=1,pixels_per_thread=4,batch=32")
     p.add_argument("--scale", type=float, default=1.0,
                    help="primitive-count scale of the workload (profiling runs only)")
     p.add_argument("--cpu-seconds", type=float, default=12.0,
@@ -121,6 +123,34 @@ def blend_flops(F, pairs):
     fwd = (5 * F + 2) * pairs["evaluated"] + 12 * pairs["intersected"]
     bwd = (5 * F + 2) * pairs["evaluated_to_last"] + 40 * pairs["intersected"]
     return fwd, bwd
+
+
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of a
+# kernel from one ncu capture of this workload, keyed by a hash of the kernel's
+# sources: a kernel edited since its capture reports traffic null.
+MEASURED_TRAFFIC = {
+    # "blend_bwd": {"bytes": ..., "sources_sha1": "...", "capture": "..."},
+}
+KERNEL_SOURCES = {
+    "blend_fwd": ("lp_blend_fwd.cu", "lp_blend.cuh", "lp_device.cuh"),
+    "blend_bwd": ("lp_blend_bwd.cu", "lp_blend.cuh", "lp_device.cuh"),
+}
+
+
+def sources_sha1(kernel):
+    import hashlib
+    h = hashlib.sha1()
+    for f in KERNEL_SOURCES.get(kernel, ()):
+        with open(os.path.join(ROOT, "paper_2501_16312_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def measured_traffic(kernel):
+    t = MEASURED_TRAFFIC.get(kernel)
+    if not t or kernel not in KERNEL_SOURCES or t["sources_sha1"] != sources_sha1(kernel):
+        return None
+    return t["bytes"]
 
 
 def hbm_bytes(kind_v, K, n, n_cams, E, passes, tiles):
@@ -268,9 +298,15 @@ def ours(args, workload):
     # plain call, then capture fwd+bwd in a graph
     from paper_2501_16312_gb300 import autotune
     tuned_pv = None
-    if not args.no_per_view:
-        tuned_pv = autotune.tune(rast, prims, w.cameras[:1], w.bg, cache=None)["tuning"]
-    tuned = autotune.tune(rast, prims, w.cameras, w.bg, dL, cache=None)["tuning"]
+    if args.tuning:
+        fixed = dict(rast.tuning(), **{k: int(v) for k, v in
+                                       (kv.split("=") for kv in args.tuning.split(","))})
+        tuned = tuned_pv = fixed
+        rast.set_tuning(**fixed)
+    else:
+        if not args.no_per_view:
+            tuned_pv = autotune.tune(rast, prims, w.cameras[:1], w.bg, cache=None)["tuning"]
+        tuned = autotune.tune(rast, prims, w.cameras, w.bg, dL, cache=None)["tuning"]
     rast.forward(prims, w.cameras, w.bg, images=img)
     rast.backward(dL, grads=grads)
     torch.cuda.synchronize()
@@ -406,13 +442,13 @@ def ours(args, workload):
         work = fl_fwd if dom == "blend_fwd" else fl_bwd
         achieved = work / (stages[dom] * 1e-3) / 1e12
         roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": alu_peak,
-                "unit": "TFLOP/s", "frac": achieved / alu_peak, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / alu_peak, "traffic": measured_traffic(dom),
                 "peak_source": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 flop x "
                                f"{sm_max:.0f} MHz ({peak_src} max clock)"}
     else:
         achieved = hb[dom] / (stages[dom] * 1e-3) / 1e9
         roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
-                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": measured_traffic(dom),
                 "peak_source": f"{peak_src} copy bandwidth"}
 
     stage_report = {}
