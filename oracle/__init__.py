@@ -69,6 +69,8 @@ def _load(path):
     L.orc_span.argtypes = [dp, dp, C.c_int, C.c_double, C.c_double, dp]
     L.orc_mtia.argtypes = [dp, dp, dp, C.c_double, C.c_double, dp, dp]
     L.orc_sh_basis.argtypes = [C.c_int, dp, dp, dp]
+    L.orc_params_forward.argtypes = [C.c_int, C.c_int, dp, dp, dp, dp, dp, dp]
+    L.orc_params_backward.argtypes = [C.c_int, C.c_int, dp, dp, dp, dp, dp, dp, dp, dp, dp]
     return L
 
 
@@ -206,3 +208,28 @@ def sh_basis(degree, direction):
     dY = np.zeros(48)
     lib().orc_sh_basis(int(degree), _ptr(d), _ptr(Y), _ptr(dY))
     return Y, dY.reshape(16, 3)
+
+
+# ------------------------------------------------------------ parameter layer
+def params_forward(kind, centre, quat, dist, logit):
+    """Sec. 3.1 parameterisation: (centre, quaternion (w,x,y,z), distances,
+    opacity logit) -> (verts [n][kind][3], opacity [n]), binary64."""
+    c, q, d, l = (np.ascontiguousarray(a, np.float64) for a in (centre, quat, dist, logit))
+    n = c.shape[0]
+    v = np.zeros((n, kind, 3))
+    o = np.zeros(n)
+    lib().orc_params_forward(int(kind), n, _ptr(c), _ptr(q), _ptr(d), _ptr(l), _ptr(v), _ptr(o))
+    return v, o
+
+
+def params_backward(kind, quat, dist, logit, dverts, dopacity, dcentre_render=None):
+    """Adjoint of params_forward; dcentre includes the renderer's direct term."""
+    q, d, l = (np.ascontiguousarray(a, np.float64) for a in (quat, dist, logit))
+    gv = np.ascontiguousarray(dverts, np.float64)
+    go = np.ascontiguousarray(dopacity, np.float64)
+    n = q.shape[0]
+    dc = np.zeros((n, 3)) if dcentre_render is None else np.array(dcentre_render, np.float64)
+    dq, dd, dl = np.zeros_like(q), np.zeros_like(d), np.zeros_like(l)
+    lib().orc_params_backward(int(kind), n, _ptr(q), _ptr(d), _ptr(l), _ptr(gv), _ptr(go), _ptr(dc),
+                              _ptr(dq), _ptr(dd), _ptr(dl))
+    return dict(centre=dc, quat=dq, dist=dd, logit=dl)

@@ -832,3 +832,105 @@ int orc_span(const orc_prims* P, const orc_camera* cam, int i, double rx, double
     out[4] = c1; out[5] = c2;
     return 0;
 }
+
+/* ------------------------------------------------------ parameter layer
+ * Sec. 3.1: a primitive is its centre c, a rotation quaternion q = (w, x, y,
+ * z) (normalised), per-corner distances and an opacity logit; vertices are
+ *   octahedron  v_{2i} = c + d_i R e_i,  v_{2i+1} = c - d_i R e_i  (i = 0..2)
+ *   tetrahedron v_k   = c + d_k R b_k   (b_k: the four regular directions)
+ * and alpha = sigmoid(logit).  Reading: distances are linear (the paper
+ * scales their learning rate by the scene extent, App. "Experimental
+ * Setting"), so they are used as given. */
+static void quat_to_R(const double q_in[4], double R[3][3], double* norm) {
+    double n = sqrt(q_in[0] * q_in[0] + q_in[1] * q_in[1] + q_in[2] * q_in[2] + q_in[3] * q_in[3]);
+    double w = q_in[0] / n, x = q_in[1] / n, y = q_in[2] / n, z = q_in[3] / n;
+    R[0][0] = 1 - 2 * (y * y + z * z); R[0][1] = 2 * (x * y - w * z);     R[0][2] = 2 * (x * z + w * y);
+    R[1][0] = 2 * (x * y + w * z);     R[1][1] = 1 - 2 * (x * x + z * z); R[1][2] = 2 * (y * z - w * x);
+    R[2][0] = 2 * (x * z - w * y);     R[2][1] = 2 * (y * z + w * x);     R[2][2] = 1 - 2 * (x * x + y * y);
+    *norm = n;
+}
+
+static void tetra_dir(int k, double b[3]) {
+    static const double s[4][3] = {{1, 1, 1}, {1, -1, -1}, {-1, 1, -1}, {-1, -1, 1}};
+    double r = 1.0 / sqrt(3.0);
+    b[0] = s[k][0] * r; b[1] = s[k][1] * r; b[2] = s[k][2] * r;
+}
+
+/* Local direction of vertex k (before scaling by its distance) and the
+ * distance index it uses. */
+static void vertex_dir(int nv, int k, double e[3], int* di, double* sign) {
+    if (nv == 6) {
+        e[0] = e[1] = e[2] = 0.0;
+        e[k / 2] = 1.0;
+        *di = k / 2;
+        *sign = (k % 2) ? -1.0 : 1.0;
+    } else {
+        tetra_dir(k, e);
+        *di = k;
+        *sign = 1.0;
+    }
+}
+
+int orc_params_forward(int nv, int n, const double* centre, const double* quat, const double* dist,
+                       const double* logit, double* verts, double* opacity) {
+    int i, k, a, nd = nv == 6 ? 3 : 4;
+    for (i = 0; i < n; ++i) {
+        double R[3][3], qn;
+        quat_to_R(quat + 4 * (size_t)i, R, &qn);
+        for (k = 0; k < nv; ++k) {
+            double e[3], s;
+            int di;
+            vertex_dir(nv, k, e, &di, &s);
+            for (a = 0; a < 3; ++a) {
+                double r = R[a][0] * e[0] + R[a][1] * e[1] + R[a][2] * e[2];
+                verts[((size_t)i * nv + k) * 3 + a] = centre[3 * i + a] + s * dist[(size_t)i * nd + di] * r;
+            }
+        }
+        opacity[i] = 1.0 / (1.0 + exp(-logit[i]));
+    }
+    return 0;
+}
+
+/* Adjoint of orc_params_forward.  dcentre is ADDED to (it may already hold
+ * the renderer's direct centre gradient); dquat, ddist, dlogit are written. */
+int orc_params_backward(int nv, int n, const double* quat, const double* dist, const double* logit,
+                        const double* dverts, const double* dopacity, double* dcentre, double* dquat,
+                        double* ddist, double* dlogit) {
+    int i, k, a, b, nd = nv == 6 ? 3 : 4;
+    for (i = 0; i < n; ++i) {
+        const double* q = quat + 4 * (size_t)i;
+        double R[3][3], dR[3][3] = {{0}}, qn, w, x, y, z, g[4], dot;
+        quat_to_R(q, R, &qn);
+        for (k = 0; k < nd; ++k) ddist[(size_t)i * nd + k] = 0.0;
+        for (k = 0; k < nv; ++k) {
+            double e[3], s, r[3];
+            int di;
+            const double* gv = dverts + ((size_t)i * nv + k) * 3;
+            vertex_dir(nv, k, e, &di, &s);
+            for (a = 0; a < 3; ++a) r[a] = R[a][0] * e[0] + R[a][1] * e[1] + R[a][2] * e[2];
+            for (a = 0; a < 3; ++a) dcentre[3 * i + a] += gv[a];
+            ddist[(size_t)i * nd + di] += s * (r[0] * gv[0] + r[1] * gv[1] + r[2] * gv[2]);
+            for (a = 0; a < 3; ++a)
+                for (b = 0; b < 3; ++b) dR[a][b] += s * dist[(size_t)i * nd + di] * gv[a] * e[b];
+        }
+        /* R(q_hat) with q_hat = q / |q| */
+        w = q[0] / qn; x = q[1] / qn; y = q[2] / qn; z = q[3] / qn;
+        g[0] = 2 * (-z * dR[0][1] + y * dR[0][2] + z * dR[1][0] - x * dR[1][2] - y * dR[2][0] + x * dR[2][1]);
+        g[1] = 2 * (y * dR[0][1] + z * dR[0][2] + y * dR[1][0] - 2 * x * dR[1][1] - w * dR[1][2] +
+                    z * dR[2][0] + w * dR[2][1] - 2 * x * dR[2][2]);
+        g[2] = 2 * (-2 * y * dR[0][0] + x * dR[0][1] + w * dR[0][2] + x * dR[1][0] + z * dR[1][2] -
+                    w * dR[2][0] + z * dR[2][1] - 2 * y * dR[2][2]);
+        g[3] = 2 * (-2 * z * dR[0][0] - w * dR[0][1] + x * dR[0][2] + w * dR[1][0] - 2 * z * dR[1][1] +
+                    y * dR[1][2] + x * dR[2][0] + y * dR[2][1]);
+        dot = g[0] * w + g[1] * x + g[2] * y + g[3] * z;
+        dquat[4 * (size_t)i + 0] = (g[0] - dot * w) / qn;
+        dquat[4 * (size_t)i + 1] = (g[1] - dot * x) / qn;
+        dquat[4 * (size_t)i + 2] = (g[2] - dot * y) / qn;
+        dquat[4 * (size_t)i + 3] = (g[3] - dot * z) / qn;
+        {
+            double al = 1.0 / (1.0 + exp(-logit[i]));
+            dlogit[i] = dopacity[i] * al * (1.0 - al);
+        }
+    }
+    return 0;
+}

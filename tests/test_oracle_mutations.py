@@ -9,6 +9,7 @@ import numpy as np
 import pytest
 
 import oracle
+import tests.test_oracle_params as params_pins
 import tests.test_oracle_pins as pins
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "linprim_oracle.c")
@@ -45,6 +46,13 @@ MUTANTS = {
     "key_tie_order": ("return (x->seq > y->seq) - (x->seq < y->seq);",
                       "return (x->seq < y->seq) - (x->seq > y->seq);", ["ties"]),
     "render_tie_order": ("return (i > j) - (i < j);", "return (i < j) - (i > j);", ["ties"]),
+    "param_octa_sign": ("*sign = (k % 2) ? -1.0 : 1.0;", "*sign = 1.0;", ["param_scipy"]),
+    "param_quat_grad": ("g[0] = 2 * (-z * dR[0][1] + y * dR[0][2]", "g[0] = 2 * (z * dR[0][1] + y * dR[0][2]",
+                        ["param_fd"]),
+    "param_norm_grad": ("dquat[4 * (size_t)i + 0] = (g[0] - dot * w) / qn;",
+                        "dquat[4 * (size_t)i + 0] = g[0] / qn;", ["param_fd"]),
+    "param_sigmoid_grad": ("dlogit[i] = dopacity[i] * al * (1.0 - al);", "dlogit[i] = dopacity[i] * al;",
+                           ["param_fd"]),
 }
 
 CHECKS = {
@@ -62,6 +70,8 @@ CHECKS = {
     "keyfields": pins.test_keyfields_are_binary32_replay,
     "keys_structure": pins.test_keys_structure,
     "ties": pins.test_depth_ties_keep_index_order,
+    "param_scipy": lambda o: [params_pins.test_vertices_match_scipy_rotation(k) for k in (6, 4)],
+    "param_fd": lambda o: [params_pins.test_params_adjoint_fd(k) for k in (6, 4)],
 }
 
 
