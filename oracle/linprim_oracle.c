@@ -182,6 +182,12 @@ static void keyfields_f32(const orc_prims* P, const orc_camera* cam, int i, orc_
     kf->px0 = 1; kf->px1 = 0; kf->py0 = 1; kf->py1 = 0;
     memcpy(&kf->zbits, &tc[2], 4);
     if (!(tc[2] > ORC_NEAR)) return;
+    /* reading: Eq. 1 divides by the smallest centre-vertex distance, so a
+     * primitive with a vertex on its centre has no density; it is not visible */
+    for (k = 0; k < P->nv; ++k) {
+        const double* v = P->verts + (size_t)(i * P->nv + k) * 3;
+        if ((float)v[0] == c[0] && (float)v[1] == c[1] && (float)v[2] == c[2]) return;
+    }
     kf->visible = 1;
     u = tc[0] / tc[2];
     w = tc[1] / tc[2];

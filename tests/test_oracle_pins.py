@@ -510,3 +510,26 @@ def test_depth_ties_keep_index_order(orc):
     same = k[1:] == k[:-1]
     assert same.sum() > 100
     assert np.all(v[1:][same] > v[:-1][same])
+
+
+def test_degenerate_primitive_is_invisible(orc):
+    """Eq. 1 divides by the smallest centre-vertex distance: a primitive with a
+    vertex on its centre (a flat octahedron, d_z = 0) has no density and is
+    not visible -- no tile entries, no colour, zero and finite gradients."""
+    good = axis_octa((0.0, 0.0, 0.0), 0.6, 0.5, 0.4)
+    flat = axis_octa((0.1, 0.0, 0.2), 0.7, 0.6, 0.0)
+    both = one_scene(6, [[0.0, 0.0, 0.0], [0.1, 0.0, 0.2]], np.stack([good, flat]), 0.8,
+                     rgb=[[0.9, 0.2, 0.1], [0.1, 0.9, 0.2]])
+    alone = both.subset(np.array([0]))
+    cam = cam_on_axis(W=40, H=36)
+    dL = np.random.default_rng(4).normal(size=3 * 40 * 36)
+    img, g = orc.render(both, [cam], dL_dimage=dL)
+    img1, g1 = orc.render(alone, [cam], dL_dimage=dL)
+    np.testing.assert_array_equal(img, img1)
+    for k in g:
+        assert np.all(np.isfinite(g[k]))
+        assert np.all(g[k][1] == 0.0), k
+        np.testing.assert_allclose(g[k][0], g1[k][0], rtol=1e-12, atol=1e-13)   # summation order only
+    _, _, counts = orc.keys(both, [cam])
+    assert counts[1] == 0 and counts[0] > 0
+
