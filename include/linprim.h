@@ -230,6 +230,62 @@ lp_status lp_count_pairs(lp_ctx* ctx, long long* counts);
 lp_status lp_set_timing(lp_ctx* ctx, int enabled);
 lp_status lp_stage_times(lp_ctx* ctx, float* ms);
 
+/* ------------------------------------------------------------------------
+ * Optimisation step (context-free, asynchronous on `stream`, device pointers).
+ * ------------------------------------------------------------------------ */
+
+/* Parameter layer (Sec. 3.1): per primitive its centre c float[n][3], rotation
+ * quaternion q = (w, x, y, z) float[n][4] (normalised here), distances
+ * float[n][D] (D = 3 for octahedra: one per axis, shared by opposite vertices;
+ * D = 4 for tetrahedra: one per corner) and opacity logit float[n].  Writes
+ * verts float[n][V][3]: octahedra c + d_i R e_i, c - d_i R e_i for axis i in
+ * the vertex order of lp_prims; tetrahedra c + d_k R b_k with b_k the four
+ * directions (+1,+1,+1), (+1,-1,-1), (-1,+1,-1), (-1,-1,+1) over sqrt(3);
+ * and opacity float[n] = sigmoid(logit).  Distances are used as given.       */
+lp_status lp_params_forward(int kind, int n, const float* centre, const float* quat, const float* dist,
+                            const float* logit, float* verts, float* opacity, void* stream);
+
+/* Adjoint of lp_params_forward (Sec. 3.4: corner gradients split into the
+ * rotation and the distances).  dverts float[n][V][3] and dopacity float[n]
+ * are inputs; dcentre float[n][3] is ADDED to (pass the renderer's centre
+ * gradient); dquat float[n][4], ddist float[n][D], dlogit float[n] are
+ * overwritten.                                                               */
+lp_status lp_params_backward(int kind, int n, const float* quat, const float* dist, const float* logit,
+                             const float* dverts, const float* dopacity, float* dcentre, float* dquat,
+                             float* ddist, float* dlogit, void* stream);
+
+/* L1 image loss (the L1 term of Sec. 3.4's loss): grad[i] = sign(image[i] -
+ * target[i]) / count for count floats; if loss (device double) is non-NULL,
+ * mean |image - target| is ADDED to *loss.                                   */
+lp_status lp_l1_loss_grad(const float* image, const float* target, long long count, float* grad,
+                          double* loss, void* stream);
+
+/* Fused Adam (Sec. 3.4; Kingma & Ba) over parameter groups of one flat float
+ * array: groups[k] covers params[offset, offset + count); groups ascend and
+ * do not overlap (1 <= n_groups <= LP_ADAM_MAX_GROUPS).
+ * Learning rate of element j of a group (j counted from its offset) at step t
+ * (1-based): lr_tail when period > 0 and j % period >= head -- so one
+ * [n][K][3] SH array can give its DC term and its higher bands different
+ * rates (period 3K, head 3) -- else lr, or, when decay_steps > 0, the
+ * log-linear blend lr^(1-f) * lr_final^f with f = min(t / decay_steps, 1)
+ * (the exponential position schedule of 3DGS, which the paper keeps).
+ * m, v: first/second moments, same layout as params.  step: device int, the
+ * number of completed steps; the call uses t = step + 1 and then increments
+ * it on the device, so replays of a captured step advance.  */
+#define LP_ADAM_MAX_GROUPS 8
+typedef struct {
+    long long offset;
+    long long count;
+    float lr;
+    float lr_final;
+    int decay_steps;
+    int period;
+    int head;
+    float lr_tail;
+} lp_adam_group;
+lp_status lp_adam_step(float* params, const float* grads, float* m, float* v, const lp_adam_group* groups,
+                       int n_groups, float beta1, float beta2, float eps, int* step, void* stream);
+
 /* Allocation-free forward render of ONE camera.  The paper has no
  * counterpart: this entry point exists for callers that cannot call
  * cudaMalloc -- code running while a CUDA graph is being captured, services

@@ -19,7 +19,9 @@ EXPORTS = ("lp_create", "lp_destroy", "lp_set_tuning", "lp_get_tuning", "lp_rese
            "lp_render_forward", "lp_render_backward", "lp_sync_status", "lp_get_stats",
            "lp_debug_keys", "lp_debug_counts", "lp_debug_pixel_state", "lp_count_pairs",
            "lp_last_error", "lp_status_string", "lp_set_timing", "lp_stage_times",
-           "lp_render_forward_noalloc")
+           "lp_render_forward_noalloc", "lp_params_forward", "lp_params_backward",
+           "lp_l1_loss_grad", "lp_adam_step")
+LP_ADAM_MAX_GROUPS = 8
 STAGES = ("preprocess", "scan_emit", "sort", "ranges", "blend_fwd", "blend_bwd", "chain")
 
 
@@ -43,6 +45,12 @@ class lp_stats(C.Structure):
     _fields_ = [("records", C.c_longlong), ("entries", C.c_longlong), ("tiles", C.c_longlong),
                 ("pixels", C.c_longlong), ("sort_passes", C.c_int), ("key_bits", C.c_int),
                 ("launches_fwd", C.c_int), ("launches_bwd", C.c_int)]
+
+
+class lp_adam_group(C.Structure):
+    _fields_ = [("offset", C.c_longlong), ("count", C.c_longlong), ("lr", C.c_float),
+                ("lr_final", C.c_float), ("decay_steps", C.c_int), ("period", C.c_int),
+                ("head", C.c_int), ("lr_tail", C.c_float)]
 
 
 class LinPrimError(RuntimeError):
@@ -88,6 +96,11 @@ def load(path: str = LIB_PATH):
     L.lp_stage_times.argtypes = [vp, C.POINTER(C.c_float)]
     L.lp_render_forward_noalloc.argtypes = [C.POINTER(lp_prims), C.POINTER(lp_camera),
                                             C.POINTER(C.c_float), vp, vp]
+    L.lp_params_forward.argtypes = [i, i, vp, vp, vp, vp, vp, vp, vp]
+    L.lp_params_backward.argtypes = [i, i, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+    L.lp_l1_loss_grad.argtypes = [vp, vp, ll, vp, vp, vp]
+    L.lp_adam_step.argtypes = [vp, vp, vp, vp, C.POINTER(lp_adam_group), i, C.c_float, C.c_float,
+                               C.c_float, vp, vp]
     for name in EXPORTS:
         getattr(L, name)
     _lib = L

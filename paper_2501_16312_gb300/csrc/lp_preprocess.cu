@@ -154,18 +154,24 @@ __global__ void __launch_bounds__(128) k_preprocess(PrimsDev P, CamsParam cams, 
     // Eq. 1: sigma = -log(1 - 0.99 alpha) / (2 d_min), d_min the smallest
     // centre-vertex distance (for an octahedron min(d_x, d_y, d_z)).
     float dmin = CUDART_INF_F;
+    bool degenerate = false;
 #pragma unroll
     for (int k = 0; k < V; ++k) {
         const float dx = v[k][0] - c[0], dy = v[k][1] - c[1], dz = v[k][2] - c[2];
         dmin = fminf(dmin, sqrtf(dx * dx + dy * dy + dz * dz));
+        degenerate |= dx == 0.f && dy == 0.f && dz == 0.f;
     }
     const float sigma = -log1pf(-kAlphaScale * alpha) / (2.f * dmin);
+    // A vertex on the centre leaves Eq. 1 without a density: not visible.  The
+    // second test only catches offsets so small (below ~1e-19) that d_min
+    // underflows in binary32, and a non-finite opacity.
+    degenerate |= !(sigma < CUDART_INF_F);
 
     for (int cv = 0; cv < cams.n; ++cv) {
         const CamDev& cm = cams.cam[cv];
         const size_t r = (size_t)cv * P.n + i;
         Geom g;
-        const bool vis = centre_geom(cm, c, g);
+        const bool vis = centre_geom(cm, c, g) && !degenerate;
         zbits[r] = __float_as_uint(g.tc[2]);
         if (!vis) {
             counts[r] = 0;
@@ -451,7 +457,7 @@ __global__ void __launch_bounds__(128) k_chain(PrimsDev P, CamsParam cams,
     }
 
     // Eq. 1 with d_min frozen: d sigma / d alpha = 0.99 / ((1 - 0.99 alpha) 2 d_min)
-    const float galpha = gsigma * kAlphaScale / ((1.f - kAlphaScale * alpha) * 2.f * dmin);
+    const float galpha = gsigma != 0.f ? gsigma * kAlphaScale / ((1.f - kAlphaScale * alpha) * 2.f * dmin) : 0.f;
     if (accumulate) {
 #pragma unroll
         for (int a = 0; a < 3; ++a) dcentre[3 * (size_t)i + a] += gc[a];

@@ -1,0 +1,299 @@
+// Optimisation-step kernels (sm_103a): the paper's primitive parameter layer,
+// the L1 image-loss gradient and a fused Adam update.
+//
+// Sec. 3.1: a primitive is stored as its centre c, a rotation quaternion
+// q = (w, x, y, z), per-corner distances and an opacity logit; its vertices
+// are c +- d_i R(q) e_i (octahedron, opposite vertices share a distance) or
+// c + d_k R(q) b_k over the four regular-tetrahedron directions b_k, and
+// alpha = sigmoid(logit).  Distances are used as given (linear), as the paper
+// scales their learning rate by the scene extent (App. "Experimental
+// Setting").  Sec. 3.4: gradients flow back through the rotation into the
+// quaternion and distances ("the gradient flow w.r.t. the corners splits when
+// undoing the rotation"); for an octahedron the two vertices of an axis enter
+// with opposite signs.  Sec. 3.4 uses Adam.
+#include <cuda_runtime.h>
+
+#include "linprim.h"
+#include "lp_device.cuh"
+
+namespace lp {
+
+namespace {
+
+__device__ __forceinline__ void quat_rot(const float q[4], float R[3][3], float& norm) {
+    norm = sqrtf(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+    const float in = 1.f / norm;
+    const float w = q[0] * in, x = q[1] * in, y = q[2] * in, z = q[3] * in;
+    R[0][0] = 1.f - 2.f * (y * y + z * z); R[0][1] = 2.f * (x * y - w * z); R[0][2] = 2.f * (x * z + w * y);
+    R[1][0] = 2.f * (x * y + w * z); R[1][1] = 1.f - 2.f * (x * x + z * z); R[1][2] = 2.f * (y * z - w * x);
+    R[2][0] = 2.f * (x * z - w * y); R[2][1] = 2.f * (y * z + w * x); R[2][2] = 1.f - 2.f * (x * x + y * y);
+}
+
+// Local direction of vertex k, the distance it uses and its sign.
+template <int V>
+__device__ __forceinline__ void local_dir(int k, float e[3], int& di, float& sgn) {
+    if (V == 6) {
+        e[0] = e[1] = e[2] = 0.f;
+        e[k / 2] = 1.f;
+        di = k / 2;
+        sgn = (k & 1) ? -1.f : 1.f;
+    } else {
+        const float r = 0.57735026918962576f;   // 1 / sqrt(3)
+        e[0] = (k == 0 || k == 1) ? r : -r;
+        e[1] = (k == 0 || k == 2) ? r : -r;
+        e[2] = (k == 0 || k == 3) ? r : -r;
+        di = k;
+        sgn = 1.f;
+    }
+}
+
+template <int V>
+__global__ void __launch_bounds__(256) k_params_fwd(int n, const float* __restrict__ centre,
+                                                    const float* __restrict__ quat,
+                                                    const float* __restrict__ dist,
+                                                    const float* __restrict__ logit,
+                                                    float* __restrict__ verts, float* __restrict__ opacity) {
+    constexpr int ND = V == 6 ? 3 : 4;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float q[4], R[3][3], nrm, d[ND], c[3];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) q[a] = quat[4 * (size_t)i + a];
+#pragma unroll
+    for (int a = 0; a < ND; ++a) d[a] = dist[(size_t)i * ND + a];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) c[a] = centre[3 * (size_t)i + a];
+    quat_rot(q, R, nrm);
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+        float e[3], sgn;
+        int di;
+        local_dir<V>(k, e, di, sgn);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const float r = R[a][0] * e[0] + R[a][1] * e[1] + R[a][2] * e[2];
+            verts[((size_t)i * V + k) * 3 + a] = fmaf(sgn * d[di], r, c[a]);
+        }
+    }
+    opacity[i] = 1.f / (1.f + __expf(-logit[i]));
+}
+
+template <int V>
+__global__ void __launch_bounds__(256) k_params_bwd(int n, const float* __restrict__ quat,
+                                                    const float* __restrict__ dist,
+                                                    const float* __restrict__ logit,
+                                                    const float* __restrict__ dverts,
+                                                    const float* __restrict__ dopacity,
+                                                    float* __restrict__ dcentre, float* __restrict__ dquat,
+                                                    float* __restrict__ ddist, float* __restrict__ dlogit) {
+    constexpr int ND = V == 6 ? 3 : 4;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float q[4], R[3][3], nrm, d[ND], gd[ND], dR[3][3], gc[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int a = 0; a < 4; ++a) q[a] = quat[4 * (size_t)i + a];
+#pragma unroll
+    for (int a = 0; a < ND; ++a) { d[a] = dist[(size_t)i * ND + a]; gd[a] = 0.f; }
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) dR[a][b] = 0.f;
+    quat_rot(q, R, nrm);
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+        float e[3], sgn, g[3];
+        int di;
+        local_dir<V>(k, e, di, sgn);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            g[a] = dverts[((size_t)i * V + k) * 3 + a];
+            gc[a] += g[a];
+        }
+        float r[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) r[a] = R[a][0] * e[0] + R[a][1] * e[1] + R[a][2] * e[2];
+        gd[di] += sgn * (r[0] * g[0] + r[1] * g[1] + r[2] * g[2]);
+        const float s = sgn * d[di];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) dR[a][b] = fmaf(s * g[a], e[b], dR[a][b]);
+    }
+    // d R(q_hat) / d q_hat, then the normalisation q_hat = q / |q|
+    const float in = 1.f / nrm;
+    const float w = q[0] * in, x = q[1] * in, y = q[2] * in, z = q[3] * in;
+    float g[4];
+    g[0] = 2.f * (-z * dR[0][1] + y * dR[0][2] + z * dR[1][0] - x * dR[1][2] - y * dR[2][0] + x * dR[2][1]);
+    g[1] = 2.f * (y * dR[0][1] + z * dR[0][2] + y * dR[1][0] - 2.f * x * dR[1][1] - w * dR[1][2] +
+                  z * dR[2][0] + w * dR[2][1] - 2.f * x * dR[2][2]);
+    g[2] = 2.f * (-2.f * y * dR[0][0] + x * dR[0][1] + w * dR[0][2] + x * dR[1][0] + z * dR[1][2] -
+                  w * dR[2][0] + z * dR[2][1] - 2.f * y * dR[2][2]);
+    g[3] = 2.f * (-2.f * z * dR[0][0] - w * dR[0][1] + x * dR[0][2] + w * dR[1][0] - 2.f * z * dR[1][1] +
+                  y * dR[1][2] + x * dR[2][0] + y * dR[2][1]);
+    const float dot = g[0] * w + g[1] * x + g[2] * y + g[3] * z;
+    dquat[4 * (size_t)i + 0] = (g[0] - dot * w) * in;
+    dquat[4 * (size_t)i + 1] = (g[1] - dot * x) * in;
+    dquat[4 * (size_t)i + 2] = (g[2] - dot * y) * in;
+    dquat[4 * (size_t)i + 3] = (g[3] - dot * z) * in;
+#pragma unroll
+    for (int a = 0; a < ND; ++a) ddist[(size_t)i * ND + a] = gd[a];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) dcentre[3 * (size_t)i + a] += gc[a];
+    const float al = 1.f / (1.f + __expf(-logit[i]));
+    dlogit[i] = dopacity[i] * al * (1.f - al);
+}
+
+// L = mean |image - target|; dL/dimage = sign(image - target) / count.
+__global__ void __launch_bounds__(256) k_l1(const float* __restrict__ img, const float* __restrict__ tgt,
+                                            long long count, float* __restrict__ grad,
+                                            double* __restrict__ loss) {
+    const float inv = 1.f / (float)count;
+    float s = 0.f;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float d = img[i] - tgt[i];
+        grad[i] = d > 0.f ? inv : (d < 0.f ? -inv : 0.f);
+        s += fabsf(d);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    __shared__ float ws[8];
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += ws[w];
+        if (loss) atomicAdd(loss, t / (double)count);
+    }
+}
+
+struct AdamGroups {
+    int n;
+    long long offset[LP_ADAM_MAX_GROUPS];
+    long long count[LP_ADAM_MAX_GROUPS];
+    float lr[LP_ADAM_MAX_GROUPS];
+    float lr_final[LP_ADAM_MAX_GROUPS];
+    int decay_steps[LP_ADAM_MAX_GROUPS];
+    int period[LP_ADAM_MAX_GROUPS];
+    int head[LP_ADAM_MAX_GROUPS];
+    float lr_tail[LP_ADAM_MAX_GROUPS];
+};
+
+// Adam (Kingma & Ba) over every group in one launch.  The step counter lives
+// in device memory so that replays of a captured step advance it.
+__global__ void __launch_bounds__(256) k_adam(float* __restrict__ p, const float* __restrict__ g,
+                                              float* __restrict__ m, float* __restrict__ v, AdamGroups G,
+                                              long long total, float b1, float b2, float eps,
+                                              const int* __restrict__ step) {
+    const int t = *step + 1;
+    const float c1 = 1.f / (1.f - powf(b1, (float)t));
+    const float c2 = 1.f / (1.f - powf(b2, (float)t));
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        int k = 0;
+        while (k + 1 < G.n && i >= G.offset[k] + G.count[k]) ++k;
+        if (i < G.offset[k] || i >= G.offset[k] + G.count[k]) continue;   // gap between groups
+        const float gi = g[i];
+        const float mi = fmaf(b1, m[i], (1.f - b1) * gi);
+        const float vi = fmaf(b2, v[i], (1.f - b2) * gi * gi);
+        m[i] = mi;
+        v[i] = vi;
+        const long long j = i - G.offset[k];
+        float lr;
+        if (G.period[k] > 0 && j % G.period[k] >= G.head[k]) {
+            lr = G.lr_tail[k];
+        } else if (G.decay_steps[k] > 0) {
+            const float f = fminf((float)t / (float)G.decay_steps[k], 1.f);
+            lr = expf((1.f - f) * logf(G.lr[k]) + f * logf(G.lr_final[k]));
+        } else {
+            lr = G.lr[k];
+        }
+        p[i] -= lr * (mi * c1) / (sqrtf(vi * c2) + eps);
+    }
+}
+
+__global__ void k_increment(int* step) { *step += 1; }
+
+int grid_for(long long n, int bs, int cap) {
+    const long long g = (n + bs - 1) / bs;
+    return (int)(g < cap ? (g > 0 ? g : 1) : cap);
+}
+
+}  // namespace
+
+}  // namespace lp
+
+extern "C" {
+
+lp_status lp_params_forward(int kind, int n, const float* centre, const float* quat, const float* dist,
+                            const float* logit, float* verts, float* opacity, void* stream) {
+    if ((kind != LP_OCTAHEDRON && kind != LP_TETRAHEDRON) || n < 0) return LP_ERR_INVALID;
+    if (n == 0) return LP_OK;
+    if (!centre || !quat || !dist || !logit || !verts || !opacity) return LP_ERR_INVALID;
+    const int grid = (n + 255) / 256;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (kind == LP_OCTAHEDRON)
+        lp::k_params_fwd<6><<<grid, 256, 0, st>>>(n, centre, quat, dist, logit, verts, opacity);
+    else
+        lp::k_params_fwd<4><<<grid, 256, 0, st>>>(n, centre, quat, dist, logit, verts, opacity);
+    return cudaGetLastError() == cudaSuccess ? LP_OK : LP_ERR_CUDA;
+}
+
+lp_status lp_params_backward(int kind, int n, const float* quat, const float* dist, const float* logit,
+                             const float* dverts, const float* dopacity, float* dcentre, float* dquat,
+                             float* ddist, float* dlogit, void* stream) {
+    if ((kind != LP_OCTAHEDRON && kind != LP_TETRAHEDRON) || n < 0) return LP_ERR_INVALID;
+    if (n == 0) return LP_OK;
+    if (!quat || !dist || !logit || !dverts || !dopacity || !dcentre || !dquat || !ddist || !dlogit)
+        return LP_ERR_INVALID;
+    const int grid = (n + 255) / 256;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (kind == LP_OCTAHEDRON)
+        lp::k_params_bwd<6><<<grid, 256, 0, st>>>(n, quat, dist, logit, dverts, dopacity, dcentre, dquat,
+                                                  ddist, dlogit);
+    else
+        lp::k_params_bwd<4><<<grid, 256, 0, st>>>(n, quat, dist, logit, dverts, dopacity, dcentre, dquat,
+                                                  ddist, dlogit);
+    return cudaGetLastError() == cudaSuccess ? LP_OK : LP_ERR_CUDA;
+}
+
+lp_status lp_l1_loss_grad(const float* image, const float* target, long long count, float* grad,
+                          double* loss, void* stream) {
+    if (count < 0 || (count > 0 && (!image || !target || !grad))) return LP_ERR_INVALID;
+    if (count == 0) return LP_OK;
+    lp::k_l1<<<lp::grid_for(count, 256, 4096), 256, 0, (cudaStream_t)stream>>>(image, target, count, grad,
+                                                                               loss);
+    return cudaGetLastError() == cudaSuccess ? LP_OK : LP_ERR_CUDA;
+}
+
+lp_status lp_adam_step(float* params, const float* grads, float* m, float* v, const lp_adam_group* groups,
+                       int n_groups, float beta1, float beta2, float eps, int* step, void* stream) {
+    if (!params || !grads || !m || !v || !groups || !step) return LP_ERR_INVALID;
+    if (n_groups < 1 || n_groups > LP_ADAM_MAX_GROUPS) return LP_ERR_INVALID;
+    lp::AdamGroups G;
+    G.n = n_groups;
+    long long total = 0;
+    for (int k = 0; k < n_groups; ++k) {
+        if (groups[k].offset < 0 || groups[k].count < 0) return LP_ERR_INVALID;
+        if (k > 0 && groups[k].offset < groups[k - 1].offset + groups[k - 1].count) return LP_ERR_INVALID;
+        G.offset[k] = groups[k].offset;
+        G.count[k] = groups[k].count;
+        G.lr[k] = groups[k].lr;
+        if (groups[k].period < 0 || groups[k].head < 0 || groups[k].decay_steps < 0) return LP_ERR_INVALID;
+        if (groups[k].decay_steps > 0 && !(groups[k].lr > 0.f && groups[k].lr_final > 0.f)) return LP_ERR_INVALID;
+        G.lr_final[k] = groups[k].lr_final;
+        G.decay_steps[k] = groups[k].decay_steps;
+        G.period[k] = groups[k].period;
+        G.head[k] = groups[k].head;
+        G.lr_tail[k] = groups[k].lr_tail;
+        total = groups[k].offset + groups[k].count;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    if (total > 0)
+        lp::k_adam<<<lp::grid_for(total, 256, 152 * 16), 256, 0, st>>>(params, grads, m, v, G, total, beta1,
+                                                                      beta2, eps, step);
+    lp::k_increment<<<1, 1, 0, st>>>(step);
+    return cudaGetLastError() == cudaSuccess ? LP_OK : LP_ERR_CUDA;
+}
+
+}  // extern "C"

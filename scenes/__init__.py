@@ -255,6 +255,89 @@ def capture_like_octa_scene(seed=2, n=500_000, core_frac=0.7, sh_degree=3,
                    opacity, sh, sh_degree)
 
 
+@dataclasses.dataclass
+class ParamScene:
+    """Primitives in the optimised parameter form: centre [n,3], quaternion
+    (w, x, y, z) [n,4], distances [n,3] (octahedron) or [n,4] (tetrahedron),
+    opacity logit [n], SH [n,K,3]; all float32."""
+    kind: int
+    centre: np.ndarray
+    quat: np.ndarray
+    dist: np.ndarray
+    logit: np.ndarray
+    sh: np.ndarray
+    sh_degree: int
+
+    @property
+    def n(self) -> int:
+        return int(self.centre.shape[0])
+
+
+def random_quaternions(rng: np.random.Generator, n: int) -> np.ndarray:
+    """Uniform random unit quaternions (w, x, y, z) [n, 4] (Shoemake)."""
+    u1, u2, u3 = rng.random(n), rng.random(n), rng.random(n)
+    a, b = np.sqrt(1.0 - u1), np.sqrt(u1)
+    return np.stack([b * np.cos(2 * np.pi * u3), a * np.sin(2 * np.pi * u2),
+                     a * np.cos(2 * np.pi * u2), b * np.sin(2 * np.pi * u3)], axis=1)
+
+
+def capture_like_octa_params(n=2_000_000, core_frac=0.7, sh_degree=3, rng=None, seed=4) -> ParamScene:
+    """The capture-like octahedron distribution (object core plus background
+    shell, as capture_like_octa_scene) drawn directly in parameter form."""
+    rng = rng if rng is not None else np.random.default_rng(seed)
+    n_core = int(round(core_frac * n))
+    n_shell = n - n_core
+    centre = np.concatenate([
+        rng.normal(0.0, 1.0, (n_core, 3)),
+        _unit_vectors(rng, n_shell) * rng.uniform(8.0, 20.0, (n_shell, 1)),
+    ])
+    dist = np.concatenate([
+        log_uniform(rng, 0.01, 0.08, (n_core, 3)),
+        log_uniform(rng, 0.1, 0.5, (n_shell, 3)),
+    ])
+    quat = random_quaternions(rng, n)
+    logit = rng.normal(0.0, 1.5, n)
+    sh = draw_sh(rng, n, sh_degree, rng.uniform(0.0, 1.0, (n, 3)))
+    f = lambda a: np.ascontiguousarray(a, np.float32)
+    return ParamScene(OCTAHEDRON, f(centre), f(quat), f(dist), f(logit), f(sh), sh_degree)
+
+
+def perturb_params(p: ParamScene, rng, pos_std=0.01, sh_std=0.1, dist_floor=1e-3) -> ParamScene:
+    """Starting point of an optimisation towards p: centres and distances
+    moved by N(0, pos_std) (distances kept >= dist_floor), SH by N(0, sh_std);
+    rotations and opacities unchanged."""
+    f = lambda a: np.ascontiguousarray(a, np.float32)
+    centre = p.centre + rng.normal(0.0, pos_std, p.centre.shape)
+    dist = np.maximum(np.abs(p.dist + rng.normal(0.0, pos_std, p.dist.shape)), dist_floor)
+    sh = p.sh + rng.normal(0.0, sh_std, p.sh.shape)
+    return ParamScene(p.kind, f(centre), p.quat.copy(), f(dist), p.logit.copy(), f(sh), p.sh_degree)
+
+
+@dataclasses.dataclass
+class ParamWorkload:
+    name: str
+    truth: ParamScene
+    init: ParamScene
+    cameras: List[Camera]
+
+    @property
+    def pixels(self) -> int:
+        return sum(c.pixels for c in self.cameras)
+
+
+def optimisation_workload(scale: float = 1.0) -> ParamWorkload:
+    """The optimisation-step workload: 2M capture-like octahedra in parameter
+    form (ground truth), its perturbation (the starting point) and 4 views
+    1600x1064 (50 deg) on a radius-4 ring; `scale` scales the primitive count."""
+    rng = np.random.default_rng(4)
+    n = max(1, int(round(2_000_000 * scale)))
+    truth = capture_like_octa_params(n=n, rng=rng)
+    cams = ring_cameras(rng, 4, 4.0, 1600, 1064, 50.0)
+    init = perturb_params(truth, rng)
+    return ParamWorkload("octa2M_4x1600x1064_train" if n == 2_000_000 else f"octa{n}_4x1600x1064_train",
+                         truth, init, cams)
+
+
 def ring_cameras(rng, n_views, radius, width, height, fov_y_deg, jitter_deg=15.0):
     cams = []
     for i in range(n_views):

@@ -15,7 +15,7 @@ PKG = os.path.join(ROOT, "paper_2501_16312_gb300")
 def declared_functions():
     src = open(HEADER).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(lp_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(lp_[a-z0-9_]+)\s*\(", src)))
 
 
 @pytest.fixture(scope="module")

@@ -125,7 +125,7 @@ def test_per_view_accumulated_gradients_equal_batched(rast):
         assert rel_l2(acc[k].cpu().numpy(), gb[k]) <= 1e-5, k
 
 
-@pytest.mark.parametrize("kind", ["empty", "culled", "ragged", "huge", "one_pixel"])
+@pytest.mark.parametrize("kind", ["empty", "culled", "ragged", "huge", "one_pixel", "degenerate"])
 def test_edge_cases(rast, kind):
     bg = (0.25, 0.5, 0.75)
     if kind == "empty":
@@ -146,6 +146,11 @@ def test_edge_cases(rast, kind):
         sc = scenes.Scene(6, c.astype(np.float32), v.astype(np.float32),
                           np.array([0.7], np.float32), sh.astype(np.float32), 0)
         cams = [scenes.make_camera((0, 0, 4), 160, 96, 60)]
+    elif kind == "degenerate":
+        # every fourth primitive has a vertex on its centre: no density, not visible
+        sc = scenes.workload(0).scene.subset(np.arange(64))
+        sc.verts[::4, 1] = sc.centre[::4]
+        cams = [scenes.make_camera((0.3, 0.2, 3.5), 70, 50, 60)]
     else:
         sc = scenes.workload(0).scene
         cams = [scenes.make_camera((0, 0, 4), 1, 1, 60)]
@@ -160,6 +165,15 @@ def test_edge_cases(rast, kind):
             assert np.all(grads[k] == 0)
     else:
         assert_grads_match(grads, ref_g)
+    if kind == "degenerate":
+        k, v = rast.debug_keys()
+        ko, vo, co = oracle.keys(sc, cams, tile=16)
+        np.testing.assert_array_equal(k, ko)
+        np.testing.assert_array_equal(v, vo)
+        assert np.all(co[::4] == 0)
+        for name in grads:
+            assert np.all(np.isfinite(grads[name]))
+            assert np.all(grads[name][::4] == 0), name
 
 
 def test_autograd_function(rast):

@@ -1,0 +1,303 @@
+"""The optimisation step on the GPU: parameter layer, L1 gradient and fused
+Adam against their definitions and the FP64 oracle, the autograd route
+against the fused step, and a graph-captured optimisation whose final
+gradient on a 64x64 crop matches the oracle's adjoint."""
+
+import numpy as np
+import pytest
+
+import oracle
+import scenes
+from tests.parity import IMG_TOL, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+GRAD_REL_L2 = 1e-3
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+def random_params(kind, n, seed):
+    rng = np.random.default_rng(seed)
+    c = rng.normal(size=(n, 3))
+    q = rng.normal(size=(n, 4)) * rng.uniform(0.5, 2.0, (n, 1))     # not unit length
+    d = rng.uniform(0.01, 0.3, (n, 3 if kind == 6 else 4))
+    l = rng.normal(0.0, 2.0, n)
+    return [np.ascontiguousarray(a, np.float32) for a in (c, q, d, l)]
+
+
+def dev(torch, a):
+    return torch.as_tensor(np.ascontiguousarray(a, np.float32), device="cuda:0")
+
+
+@pytest.mark.parametrize("kind", [6, 4])
+def test_params_layer_forward_backward_vs_oracle(torch, kind):
+    from paper_2501_16312_gb300 import train
+    n = 5003                       # several blocks and a ragged tail
+    c, q, d, l = random_params(kind, n, 11 + kind)
+    v, o = train.params_forward(kind, dev(torch, c), dev(torch, q), dev(torch, d), dev(torch, l))
+    vo, oo = oracle.params_forward(kind, c, q, d, l)
+    np.testing.assert_allclose(v.cpu().numpy(), vo, atol=2e-6, rtol=0)
+    np.testing.assert_allclose(o.cpu().numpy(), oo, atol=1e-6, rtol=0)
+
+    rng = np.random.default_rng(7)
+    gv = rng.normal(size=(n, kind, 3)).astype(np.float32)
+    go = rng.normal(size=n).astype(np.float32)
+    gc = rng.normal(size=(n, 3)).astype(np.float32)
+    dc = dev(torch, gc)
+    dq, dd, dl = train.params_backward(kind, dev(torch, q), dev(torch, d), dev(torch, l), dev(torch, gv),
+                                       dev(torch, go), dc)
+    ref = oracle.params_backward(kind, q, d, l, gv, go, dcentre_render=gc)
+    for name, got in (("centre", dc), ("quat", dq), ("dist", dd), ("logit", dl)):
+        g = got.cpu().numpy().astype(np.float64)
+        assert rel_l2(g, ref[name]) <= 1e-5, name
+        np.testing.assert_allclose(g, ref[name], atol=1e-4 * np.abs(ref[name]).max(), rtol=0, err_msg=name)
+
+
+def test_params_layer_empty_and_invalid(torch):
+    from paper_2501_16312_gb300 import _native, train
+    L = _native.load()
+    import ctypes as C
+    z = C.c_void_p(0)
+    assert L.lp_params_forward(6, 0, z, z, z, z, z, z, z) == _native.LP_OK
+    assert L.lp_params_forward(5, 4, z, z, z, z, z, z, z) == _native.LP_ERR_INVALID
+    assert L.lp_params_forward(6, 4, z, z, z, z, z, z, z) == _native.LP_ERR_INVALID
+    assert L.lp_l1_loss_grad(z, z, 0, z, z, z) == _native.LP_OK
+    g = (_native.lp_adam_group * 2)(train.adam_group(0, 10, 1e-3), train.adam_group(5, 10, 1e-3))
+    x = torch.zeros(32, device="cuda:0")
+    s = torch.zeros(1, dtype=torch.int32, device="cuda:0")
+    p = C.c_void_p(x.data_ptr())
+    assert L.lp_adam_step(p, p, p, p, g, 2, 0.9, 0.999, 1e-8, C.c_void_p(s.data_ptr()), z) \
+        == _native.LP_ERR_INVALID      # overlapping groups
+    torch.cuda.synchronize()
+
+
+def test_l1_loss_grad(torch):
+    from paper_2501_16312_gb300 import train
+    rng = np.random.default_rng(5)
+    count = 3 * 1_000_003
+    a = rng.uniform(0, 1, count).astype(np.float32)
+    b = rng.uniform(0, 1, count).astype(np.float32)
+    b[::97] = a[::97]                                        # exact ties: zero gradient
+    loss, grad = train.l1_loss_grad(dev(torch, a), dev(torch, b))
+    inv = np.float32(1.0) / np.float32(count)
+    want = np.where(a > b, inv, np.where(a < b, -inv, np.float32(0))).astype(np.float32)
+    np.testing.assert_array_equal(grad.cpu().numpy(), want)
+    ref = np.abs(a.astype(np.float64) - b.astype(np.float64)).mean()
+    assert abs(loss.item() - ref) <= 1e-6 * ref
+
+
+def adam_reference(p, grads, groups, b1=0.9, b2=0.999, eps=1e-15):
+    """Adam (Kingma & Ba, Algorithm 1) in float64, one row of `grads` per step,
+    with the group learning-rate rules of the fused kernel."""
+    p = p.astype(np.float64).copy()
+    m = np.zeros_like(p)
+    v = np.zeros_like(p)
+    for t, g in enumerate(grads, start=1):
+        g = g.astype(np.float64)
+        m = b1 * m + (1 - b1) * g
+        v = b2 * v + (1 - b2) * g * g
+        mh = m / (1 - b1 ** t)
+        vh = v / (1 - b2 ** t)
+        for (off, cnt, lr, lr_final, decay, period, head, lr_tail) in groups:
+            j = np.arange(cnt)
+            f = min(t / decay, 1.0) if decay > 0 else 0.0
+            base = lr ** (1 - f) * lr_final ** f if decay > 0 else lr
+            lrs = np.where((period > 0) & (j % max(period, 1) >= head), lr_tail, base)
+            sl = slice(off, off + cnt)
+            p[sl] -= lrs * mh[sl] / (np.sqrt(vh[sl]) + eps)
+    return p
+
+
+def test_adam_matches_definition_and_torch(torch):
+    from paper_2501_16312_gb300 import train
+    rng = np.random.default_rng(9)
+    total = 70_001
+    groups = [(0, 30_000, 2e-3, 2e-5, 4, 0, 0, 0.0),          # log-linear decay over 4 steps
+              (30_000, 20_000, 1e-2, 0.0, 0, 0, 0, 0.0),
+              (50_000, 20_001, 2.5e-3, 0.0, 0, 48, 3, 1.25e-4)]   # SH: DC head, band tail
+    p0 = rng.normal(size=total).astype(np.float32)
+    grads = rng.normal(size=(6, total)).astype(np.float32)
+    P = dev(torch, p0)
+    G = torch.empty_like(P)
+    M = torch.zeros_like(P)
+    V = torch.zeros_like(P)
+    step = torch.zeros(1, dtype=torch.int32, device="cuda:0")
+    gs = [train.adam_group(*g) for g in groups]
+    for g in grads:
+        G.copy_(dev(torch, g))
+        train.adam_step(P, G, M, V, gs, step)
+    assert int(step.item()) == len(grads)
+    ref = adam_reference(p0, grads, groups)
+    got = P.cpu().numpy().astype(np.float64)
+    np.testing.assert_allclose(got, ref, atol=1e-5 * np.abs(ref).max(), rtol=0)
+    # the plain group against torch.optim.Adam
+    x = dev(torch, p0[30_000:50_000]).clone().requires_grad_(True)
+    opt = torch.optim.Adam([x], lr=1e-2, betas=(0.9, 0.999), eps=1e-15)
+    for g in grads:
+        x.grad = dev(torch, g[30_000:50_000])
+        opt.step()
+    np.testing.assert_allclose(got[30_000:50_000], x.detach().cpu().numpy(), atol=2e-6, rtol=0)
+
+
+# ------------------------------------------------------------------ training
+
+def render_targets(torch, rast, truth, cameras):
+    from paper_2501_16312_gb300 import Primitives, train
+    c = dev(torch, truth.centre)
+    v, o = train.params_forward(truth.kind, c, dev(torch, truth.quat), dev(torch, truth.dist),
+                                dev(torch, truth.logit))
+    img = rast.forward(Primitives(truth.kind, c, v, o, dev(torch, truth.sh)), cameras)
+    torch.cuda.synchronize()
+    rast.sync_status()
+    return img.clone()
+
+
+def test_fused_step_equals_autograd_route(torch):
+    """The fused step's gradient equals the one PyTorch autograd assembles
+    from the two autograd Functions (parameter layer, renderer) and torch's
+    own L1 loss; its Adam update equals torch.optim.Adam on each group."""
+    from paper_2501_16312_gb300 import Rasterizer, render, train
+    w = scenes.optimisation_workload(scale=0.005)
+    rast = Rasterizer(0)
+    target = render_targets(torch, rast, w.truth, w.cameras)
+    p = w.init
+    tr = train.Trainer(p.kind, p.centre, p.quat, p.dist, p.logit, p.sh, w.cameras, target,
+                       rasterizer=Rasterizer(0))
+    tr.step()
+    torch.cuda.synchronize()
+    tr.rast.sync_status()
+    leaves = {k: dev(torch, getattr(p, k)).requires_grad_(True) for k in ("centre", "quat", "dist", "logit", "sh")}
+    verts, opacity = train.params_layer(p.kind, leaves["centre"], leaves["quat"], leaves["dist"], leaves["logit"])
+    img = render(leaves["centre"], verts, opacity, leaves["sh"], w.cameras, kind=p.kind, rasterizer=rast)
+    loss = (img.reshape(-1) - target).abs().mean()
+    loss.backward()
+    assert abs(loss.item() - tr.loss.item()) <= 1e-5 * loss.item()
+    # the routes differ only in the order of the backward's float atomics
+    errs = {k: rel_l2(tr.g[k].cpu().numpy(), leaves[k].grad.cpu().numpy()) for k in leaves}
+    print("fused vs autograd relative L2:", errs)
+    assert all(v <= GRAD_REL_L2 for v in errs.values()), errs
+    # Adam: the fused update of the rotation group against torch.optim.Adam
+    q = leaves["quat"].detach().clone().requires_grad_(True)
+    opt = torch.optim.Adam([q], lr=tr.lr["quat"], betas=(0.9, 0.999), eps=1e-15)
+    q.grad = tr.g["quat"].clone()
+    opt.step()
+    np.testing.assert_allclose(tr.p["quat"].cpu().numpy(), q.detach().cpu().numpy(), atol=1e-6, rtol=0)
+
+
+def crop_pixels(cam, size=64):
+    x0 = (cam.width - size) // 2
+    y0 = (cam.height - size) // 2
+    yy, xx = np.mgrid[y0:y0 + size, x0:x0 + size]
+    return xx.reshape(-1).astype(np.int32), yy.reshape(-1).astype(np.int32)
+
+
+def footprint_subset(centre, verts, cam, px, py):
+    """A superset of the primitives that can touch the pixel block: the image
+    of each bounding sphere under the projection's Jacobian at the centre
+    (the local linearisation the renderer uses), padded by two pixels, must
+    meet the block; primitives at depth <= 0.25 are all kept."""
+    M = np.asarray(cam.viewmat, np.float64).reshape(4, 4)
+    c = centre.astype(np.float64) @ M[:3, :3].T + M[:3, 3]
+    r = np.linalg.norm(verts.astype(np.float64) - centre[:, None, :].astype(np.float64), axis=2).max(1)
+    near = c[:, 2] <= 0.25
+    z = np.where(near, 1.0, c[:, 2])
+    keep = near.copy()
+    ok = ~near
+    for axis, f, cc, lo, hi in ((0, cam.fx, cam.cx, px.min(), px.max() + 1.0),
+                                (1, cam.fy, cam.cy, py.min(), py.max() + 1.0)):
+        u = f * c[:, axis] / z + cc
+        h = r * f / z * np.sqrt(1.0 + (c[:, axis] / z) ** 2) + 2.0
+        ok &= (u + h >= lo) & (u - h <= hi)
+    return np.nonzero(keep | ok)[0]
+
+
+def check_crop_gradient(torch, tr, target):
+    """Gradient of the L1 loss restricted to a 64x64 crop of view 0 at the
+    trainer's current parameters: GPU path against the FP64 oracle."""
+    from paper_2501_16312_gb300 import Primitives, Rasterizer, train
+    kind = tr.kind
+    P = {k: v.detach().clone() for k, v in tr.p.items()}
+    rast = Rasterizer(0)
+    verts, opacity = train.params_forward(kind, P["centre"], P["quat"], P["dist"], P["logit"])
+    img = rast.forward(Primitives(kind, P["centre"], verts, opacity, P["sh"]), tr.cameras, tr.bg)
+    _, grad = train.l1_loss_grad(img, tr.targets)
+    cam = tr.cameras[0]
+    px, py = crop_pixels(cam)
+    npx = cam.width * cam.height
+    mask = torch.zeros(3, cam.height, cam.width, device="cuda:0")
+    mask[:, py.min():py.max() + 1, px.min():px.max() + 1] = 1.0
+    dL = torch.zeros_like(grad)
+    dL[:3 * npx] = grad[:3 * npx] * mask.reshape(-1)
+    g = rast.backward(dL)
+    dq, dd, dl = train.params_backward(kind, P["quat"], P["dist"], P["logit"], g["verts"], g["opacity"],
+                                       g["centre"])
+    torch.cuda.synchronize()
+    rast.sync_status()
+    gpu = dict(centre=g["centre"], quat=dq, dist=dd, logit=dl, sh=g["sh"])
+    gpu = {k: v.cpu().numpy().astype(np.float64) for k, v in gpu.items()}
+    Pn = {k: v.cpu().numpy() for k, v in P.items()}
+
+    # oracle side: parameter layer, then the crop's pixels, then the adjoint
+    vo, oo = oracle.params_forward(kind, Pn["centre"], Pn["quat"], Pn["dist"], Pn["logit"])
+    sub = footprint_subset(Pn["centre"], vo, cam, px, py)
+    sc = scenes.Scene(kind, Pn["centre"][sub], vo[sub], oo[sub], Pn["sh"][sub], int(tr.prims.sh_degree))
+    dLn = dL[:3 * npx].cpu().numpy().reshape(3, -1)[:, py * cam.width + px].T
+    rgb, info, og = oracle.render_pixels(sc, cam, px, py, bg=tr.bg, dL_dC=dLn)
+    gi = img[:3 * npx].cpu().numpy().reshape(3, -1)[:, py * cam.width + px].T
+    err = np.abs(gi - rgb).max(1)
+    border = info[:, 2] > 0
+    assert err[~border].max(initial=0.0) <= IMG_TOL
+    # the sign decisions of the L1 gradient agree wherever the residual is not tiny
+    tg = tr.targets[:3 * npx].cpu().numpy().reshape(3, -1)[:, py * cam.width + px].T
+    decided = np.abs(rgb - tg) > 1e-4
+    assert np.array_equal(np.sign(gi - tg)[decided], np.sign(rgb - tg)[decided])
+    full = {k: np.zeros((Pn["centre"].shape[0],) + og[k].shape[1:]) for k in ("centre", "verts", "opacity", "sh")}
+    for k in full:
+        full[k][sub] = og[k]
+    ref = oracle.params_backward(kind, Pn["quat"], Pn["dist"], Pn["logit"], full["verts"], full["opacity"],
+                                 dcentre_render=full["centre"])
+    ref["sh"] = full["sh"]
+    errs = {k: rel_l2(gpu[k], ref[k]) for k in ("centre", "quat", "dist", "logit", "sh")}
+    print(f"crop gradient vs oracle ({sub.size} primitives near the crop):", errs)
+    assert all(v <= GRAD_REL_L2 for v in errs.values()), errs
+    assert np.abs(ref["centre"]).sum() > 0
+    return errs
+
+
+def run_optimisation(torch, scale, iters):
+    from paper_2501_16312_gb300 import Rasterizer, train
+    w = scenes.optimisation_workload(scale=scale)
+    target = render_targets(torch, Rasterizer(0), w.truth, w.cameras)
+    p = w.init
+    tr = train.Trainer(p.kind, p.centre, p.quat, p.dist, p.logit, p.sh, w.cameras, target)
+    tr.capture()
+    losses = torch.zeros(iters, dtype=torch.float64, device="cuda:0")
+    tr.replay(iters, losses)
+    torch.cuda.synchronize()
+    tr.rast.sync_status()                      # the tile list stayed within the reserved capacity
+    assert tr.steps_done() == iters + 2          # capture() ran two real steps
+    return tr, target, losses.cpu().numpy()
+
+
+def test_graph_captured_optimisation_small(torch):
+    tr, target, losses = run_optimisation(torch, 0.01, 120)
+    print("loss every 10 steps:", losses[::10])
+    assert np.all(np.isfinite(losses))
+    assert losses[-10:].mean() < 0.6 * losses[:3].mean(), losses[::10]
+    check_crop_gradient(torch, tr, target)
+
+
+def test_graph_captured_optimisation_full_size(torch):
+    """2M octahedra, 4 views 1600x1064, 500 graph-replayed steps."""
+    tr, target, losses = run_optimisation(torch, 1.0, 500)
+    print("loss every 50 steps:", losses[::50])
+    assert np.all(np.isfinite(losses))
+    assert losses[-20:].mean() < 0.8 * losses[:5].mean(), losses[::50]
+    check_crop_gradient(torch, tr, target)
