@@ -6,6 +6,7 @@ sort, tile ranges, front-to-back blend, back-to-front blend backward and the
 chain to world-space gradients, for every camera of the workload.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--config 2|3]
+  python bench.py --config 4 ...            (the graph-captured optimisation step)
   python bench.py --impl reference ...      (the FP64 CPU oracle arm)
 
 Default workload: 500,000 capture-like octahedra, SH degree 3, eight
@@ -37,7 +38,9 @@ def parse_args():
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--config", type=int, default=2, choices=[1, 2, 3])
+    p.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 4],
+                   help="1-3: render fwd+bwd workloads; 4: the optimisation step "
+                        "(parameter layer, render, L1, backward, Adam) on 2M octahedra")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-per-view", action="store_true")
     p.add_argument("--tuning", default="",
@@ -153,18 +156,75 @@ def measured_traffic(kernel):
     return t["bytes"]
 
 
-def hbm_bytes(kind_v, K, n, n_cams, E, passes, tiles):
-    """Algorithmic bytes per launch of the HBM-bound stages."""
+def hbm_bytes(kind_v, K, n, n_cams, E, passes, tiles, sort_mode=0, key_bits=0):
+    """Algorithmic bytes per launch of the HBM-bound stages: each radix pass
+    reads and writes every key and value once (histogram reads excluded).
+    Sort mode 0 emits 64-bit (tile, depth) keys and sorts them; mode 1 sorts
+    the records by depth inside the scan/emit stage, emits 32-bit tile keys in
+    that order and sorts those."""
     F = 8 if kind_v == 6 else 4
+    R = n_cams * n
     rec = (8 + 3 * F) * 4
     prim_in = (3 + 3 * kind_v + 1 + 3 * K) * 4
-    return {
-        "preprocess": n * prim_in + n_cams * n * (rec + 4 + 16 + 4),
-        "scan_emit": n_cams * n * (4 + 4 + 4 + 16 + 4) + E * 12,
-        "sort": passes * E * 24,
-        "ranges": E * 8 + tiles * 8,
-        "chain": n * prim_in + n_cams * n * (F * 3 + 4 + 1) * 4 + n * prim_in,
+    out = {
+        "preprocess": n * prim_in + R * (rec + 4 + 16 + 4),
+        "ranges": E * 4 * (2 if sort_mode == 0 else 1) + tiles * 8,
+        "chain": n * prim_in + R * (F * 3 + 4 + 1) * 4 + n * prim_in,
     }
+    if sort_mode == 0:
+        out["scan_emit"] = R * (4 + 4 + 4 + 16 + 4) + E * 12
+        out["sort"] = passes * E * 24
+    else:
+        p2 = (key_bits + 7) // 8
+        p1 = max(passes - p2, 0)
+        out["scan_emit"] = (R * (4 + 4 + 8)            # depth keys
+                            + p1 * R * 16             # record sort by depth
+                            + R * (4 + 4 + 4)         # gather counts
+                            + R * 8                   # scan
+                            + R * (4 + 4 + 4 + 16) + E * 8)   # emission
+        out["sort"] = p2 * E * 16
+    return out
+
+
+def roofline(rast, stages, kind, sh_degree, n, n_cams, clk, dev):
+    """Roofline entry of the dominant render stage, per-stage rates, the
+    device pair counters and the context stats of the last forward."""
+    import torch
+    pairs = rast.count_pairs()
+    st = rast.stats()
+    F = 8 if kind == 6 else 4
+    fl_fwd, fl_bwd = blend_flops(F, pairs)
+    peaks, peak_src = measured_peaks()
+    props = torch.cuda.get_device_properties(dev)
+    sm_max = peaks.get("sm_max_mhz") or clk.get("sm_max_mhz") or 2070.0
+    alu_peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12   # TFLOP/s
+    hb = hbm_bytes(kind, (sh_degree + 1) ** 2, n, n_cams, st["entries"], st["sort_passes"], st["tiles"],
+                   rast.tuning()["sort_mode"], st["key_bits"])
+    render_stages = {k: v for k, v in stages.items() if k in hb or k in ("blend_fwd", "blend_bwd")}
+    dom = max(render_stages, key=render_stages.get)
+    if dom in ("blend_fwd", "blend_bwd"):
+        work = fl_fwd if dom == "blend_fwd" else fl_bwd
+        achieved = work / (stages[dom] * 1e-3) / 1e12
+        roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": alu_peak,
+                "unit": "TFLOP/s", "frac": achieved / alu_peak, "traffic": measured_traffic(dom),
+                "peak_source": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 flop x "
+                               f"{sm_max:.0f} MHz ({peak_src} max clock)"}
+    else:
+        achieved = hb[dom] / (stages[dom] * 1e-3) / 1e9
+        roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": measured_traffic(dom),
+                "peak_source": f"{peak_src} copy bandwidth"}
+    stage_report = {}
+    for k, ms in stages.items():
+        if k in hb:
+            stage_report[k] = {"ms": ms, "GB/s": hb[k] / (ms * 1e-3) / 1e9 if ms > 0 else None}
+        elif k == "blend_fwd":
+            stage_report[k] = {"ms": ms, "TFLOP/s": fl_fwd / (ms * 1e-3) / 1e12 if ms > 0 else None}
+        elif k == "blend_bwd":
+            stage_report[k] = {"ms": ms, "TFLOP/s": fl_bwd / (ms * 1e-3) / 1e12 if ms > 0 else None}
+        else:
+            stage_report[k] = {"ms": ms}
+    return roof, stage_report, pairs, st
 
 
 # ---------------------------------------------------------------- CPU oracle
@@ -204,7 +264,7 @@ def cpu_baseline(workload, target_s, gpu_image=None, seed=11):
     return out
 
 
-def reference_arm(args, workload):
+def reference_arm(args, workload, metric=METRIC):
     """--impl reference: the FP64 oracle on the host cores, each step a
     bounded sample of the workload's pixels (forward + adjoint)."""
     import numpy as np
@@ -236,7 +296,7 @@ def reference_arm(args, workload):
     value = npix * args.steps / total / 1e6
     sample = (f"{npix} random pixels of camera 0 ({cam.width}x{cam.height}) per step, "
               "forward + adjoint, binary64, OpenMP over pixels")
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+    line = {"impl": "reference", "metric": metric, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": config_dict(args, workload),
@@ -427,38 +487,8 @@ def ours(args, workload):
     # ---- roofline of the dominant kernel
     graph.replay()
     torch.cuda.synchronize()
-    pairs = rast.count_pairs()
-    st = rast.stats()
-    F = 8 if w.scene.kind == 6 else 4
-    fl_fwd, fl_bwd = blend_flops(F, pairs)
-    peaks, peak_src = measured_peaks()
-    props = torch.cuda.get_device_properties(dev)
-    sm_max = peaks.get("sm_max_mhz") or clk.get("sm_max_mhz") or 2070.0
-    alu_peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12   # TFLOP/s
-    hb = hbm_bytes(w.scene.kind, (w.scene.sh_degree + 1) ** 2, w.scene.n, len(w.cameras),
-                   st["entries"], st["sort_passes"], st["tiles"])
-    dom = max(stages, key=stages.get)
-    if dom in ("blend_fwd", "blend_bwd"):
-        work = fl_fwd if dom == "blend_fwd" else fl_bwd
-        achieved = work / (stages[dom] * 1e-3) / 1e12
-        roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": alu_peak,
-                "unit": "TFLOP/s", "frac": achieved / alu_peak, "traffic": measured_traffic(dom),
-                "peak_source": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 flop x "
-                               f"{sm_max:.0f} MHz ({peak_src} max clock)"}
-    else:
-        achieved = hb[dom] / (stages[dom] * 1e-3) / 1e9
-        roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
-                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": measured_traffic(dom),
-                "peak_source": f"{peak_src} copy bandwidth"}
-
-    stage_report = {}
-    for k, ms in stages.items():
-        if k in hb:
-            stage_report[k] = {"ms": ms, "GB/s": hb[k] / (ms * 1e-3) / 1e9 if ms > 0 else None}
-        elif k == "blend_fwd":
-            stage_report[k] = {"ms": ms, "TFLOP/s": fl_fwd / (ms * 1e-3) / 1e12 if ms > 0 else None}
-        else:
-            stage_report[k] = {"ms": ms, "TFLOP/s": fl_bwd / (ms * 1e-3) / 1e12 if ms > 0 else None}
+    roof, stage_report, pairs, st = roofline(rast, stages, w.scene.kind, w.scene.sh_degree, w.scene.n,
+                                             len(w.cameras), clk, dev)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -482,9 +512,223 @@ def ours(args, workload):
         dist.destroy_process_group()
 
 
+# ------------------------------------------------------- optimisation step
+TRAIN_METRIC = ("optimisation-step Mpixel/s (parameter layer, batched render fwd+bwd, L1, "
+                "parameter adjoint, fused Adam; graph-captured)")
+
+
+def hbm_train_bytes(n, D, K, pixels):
+    """Algorithmic bytes per launch of the optimisation-step kernels."""
+    V = 6 if D == 3 else 4
+    n_par = 3 + 4 + D + 1 + 3 * K
+    return {
+        "params_fwd": n * (3 + 4 + D + 1) * 4 + n * (3 * V + 1) * 4,
+        "l1": 3 * pixels * 12,
+        "params_bwd": n * (4 + D + 1 + 3 * V + 1 + 3) * 4 + n * (3 + 4 + D + 1) * 4,
+        "adam": n * n_par * 28,
+    }
+
+
+def train_arm(args):
+    import numpy as np
+    import torch
+    import scenes
+    from paper_2501_16312_gb300 import Primitives, Rasterizer, autotune, train
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import torch.distributed as dist
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    w = scenes.optimisation_workload(scale=args.scale)
+    P = w.pixels
+    rast = Rasterizer(local)
+    # targets: the ground-truth parameters rendered by the same path (untimed)
+    tp = w.truth
+    c = torch.as_tensor(tp.centre, device=dev)
+    v, o = train.params_forward(tp.kind, c, torch.as_tensor(tp.quat, device=dev),
+                                torch.as_tensor(tp.dist, device=dev), torch.as_tensor(tp.logit, device=dev))
+    target = rast.forward(Primitives(tp.kind, c, v, o, torch.as_tensor(tp.sh, device=dev)), w.cameras).clone()
+    del c, v, o
+    p = w.init
+    tr = train.Trainer(p.kind, p.centre, p.quat, p.dist, p.logit, p.sh, w.cameras, target, rasterizer=rast)
+    # schedule tuned on the starting point (untimed)
+    if args.tuning:
+        tuned = dict(rast.tuning(), **{k: int(x) for k, x in (kv.split("=") for kv in args.tuning.split(","))})
+        rast.set_tuning(**tuned)
+    else:
+        tr.step()
+        tune_entry = autotune.tune(rast, tr.prims, w.cameras, tr.bg, tr.dimages, cache=None)
+        tuned = tune_entry["tuning"]
+    rast.set_timing(True)
+    tr.capture()
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(args.warmup):
+        tr.graph.replay()
+    torch.cuda.synchronize()
+    rast.sync_status()
+
+    losses = torch.zeros(args.steps, dtype=torch.float64, device=dev)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    step_ms, stage_sum = [], {}
+    for i in range(args.steps):
+        ev0.record(stream)
+        tr.graph.replay()
+        ev1.record(stream)
+        losses[i:i + 1].copy_(tr.loss)
+        ev1.synchronize()
+        step_ms.append(ev0.elapsed_time(ev1))
+        for k, x in rast.stage_times().items():
+            stage_sum[k] = stage_sum.get(k, 0.0) + x
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    rast.sync_status()
+    t_step = max_over_ranks(sum(step_ms) / len(step_ms))
+    stages = {k: x / args.steps for k, x in stage_sum.items()}
+    value = world * P / (t_step * 1e-3) / 1e6
+    loss_curve = losses.cpu().numpy()
+
+    # the optimisation-step kernels timed alone (eager, same stream, events)
+    L = tr.lib
+    sp = train._stream(dev)
+    ptr = train._ptr
+    n, kind = tr.n, tr.kind
+
+    def timed(fn, reps=10):
+        fn()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(reps):
+            fn()
+        ev1.record(stream)
+        ev1.synchronize()
+        return ev0.elapsed_time(ev1) / reps
+
+    scratch = {k: torch.empty_like(x) for k, x in tr.g.items()}
+    dv_copy = tr.dverts.clone()
+    extra = {
+        "params_fwd": timed(lambda: L.lp_params_forward(kind, n, ptr(tr.p["centre"]), ptr(tr.p["quat"]),
+                                                        ptr(tr.p["dist"]), ptr(tr.p["logit"]), ptr(tr.verts),
+                                                        ptr(tr.opacity), sp)),
+        "l1": timed(lambda: L.lp_l1_loss_grad(ptr(tr.images), ptr(tr.targets), 3 * P, ptr(tr.dimages),
+                                              ptr(tr.loss), sp)),
+        "params_bwd": timed(lambda: L.lp_params_backward(kind, n, ptr(tr.p["quat"]), ptr(tr.p["dist"]),
+                                                         ptr(tr.p["logit"]), ptr(dv_copy), ptr(tr.dopacity),
+                                                         ptr(scratch["centre"]), ptr(scratch["quat"]),
+                                                         ptr(scratch["dist"]), ptr(scratch["logit"]), sp)),
+    }
+    m2, v2, P2 = torch.zeros_like(tr.m), torch.zeros_like(tr.v), tr.P.clone()
+    step2 = torch.zeros(1, dtype=torch.int32, device=dev)
+    extra["adam"] = timed(lambda: L.lp_adam_step(ptr(P2), ptr(tr.G), ptr(m2), ptr(v2), tr._groups_arr,
+                                                 len(tr.groups), 0.9, 0.999, 1e-15, ptr(step2), sp))
+    hb = hbm_train_bytes(n, tr.D, tr.K, P)
+    for k, ms in extra.items():
+        stages[k] = ms
+    tr.graph.replay()
+    torch.cuda.synchronize()
+    roof, stage_report, pairs, st = roofline(rast, stages, kind, tr.prims.sh_degree, n, len(w.cameras), clk, dev)
+    for k in extra:
+        stage_report[k] = {"ms": extra[k], "GB/s": hb[k] / (extra[k] * 1e-3) / 1e9, "timed": "alone, eager"}
+
+    # ---- end to end through the public API: each step streams its target
+    # images in from pinned host memory and reads the loss back
+    h_target = target.cpu().pin_memory()
+    h_loss = torch.empty(1, dtype=torch.float64, pin_memory=True)
+
+    def e2e_step():
+        tr.targets.copy_(h_target, non_blocking=True)
+        tr.step()
+        h_loss.copy_(tr.loss, non_blocking=True)
+
+    rast.set_timing(False)
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    t_e2e = max_over_ranks(max(ev0.elapsed_time(ev1), 1000 * (time.perf_counter() - t0)) / args.steps)
+    e2e = {"value": world * P / (t_e2e * 1e-3) / 1e6, "unit": UNIT, "h2d_bytes_per_step": h_target.numel() * 4,
+           "d2h_bytes_per_step": 8, "ms_per_step": t_e2e,
+           "path": "pinned host targets -> device, Trainer.step (eager launches), loss -> host"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(param_workload_scene(w, tr.params_numpy()), args.cpu_seconds)
+        cpu["sample"] += "; parameters at the end of the timed steps"
+
+    if rank == 0:
+        cfg = {"workload": w.name + " (workload 4, optimisation step)", "primitives": n, "kind": "octahedron",
+               "sh_degree": tr.prims.sh_degree, "cameras": len(w.cameras),
+               "resolutions": sorted({f"{c.width}x{c.height}" for c in w.cameras}), "pixels_per_step": P,
+               "tile": 16, "form": "params -> render -> L1 -> backward -> params adjoint -> Adam, one CUDA graph",
+               "l2": "inputs larger than L2 (2M primitives x 59 parameters x 4 arrays, images > 129 MB)",
+               "parallelism": f"replicas x{world}", "tuning": tuned, "learning_rates": tr.lr}
+        line = {"metric": TRAIN_METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": t_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg, "e2e": e2e,
+                "gpu_launches": (st["launches_fwd"] + st["launches_bwd"] + 5) * args.steps,
+                "roofline": roof, "stages": stage_report, "clocks": clk,
+                "loss": {"first_timed": float(loss_curve[0]), "last_timed": float(loss_curve[-1]),
+                         "steps_before_timing": args.warmup + 2},
+                "workload_counts": {"records": st["records"], "tile_list_entries": st["entries"],
+                                    "pairs": pairs, "sort_passes": st["sort_passes"]},
+                "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def param_workload_scene(w, params):
+    """The optimisation workload as a renderable scene for the oracle: the
+    oracle's own parameter layer applied to the given parameters."""
+    import numpy as np
+    import oracle
+    import scenes
+    v, o = oracle.params_forward(w.init.kind, params["centre"], params["quat"], params["dist"], params["logit"])
+    sc = scenes.Scene(w.init.kind, params["centre"].astype(np.float32), v.astype(np.float32),
+                      o.astype(np.float32), params["sh"].astype(np.float32), w.init.sh_degree)
+    return scenes.Workload(w.name, sc, w.cameras)
+
+
 def main():
     args = parse_args()
     import scenes
+    if args.config == 4:
+        if args.impl == "reference":
+            w = scenes.optimisation_workload(scale=args.scale)
+            reference_arm(args, param_workload_scene(w, {k: getattr(w.init, k) for k in
+                                                         ("centre", "quat", "dist", "logit", "sh")}),
+                          metric=TRAIN_METRIC)
+        else:
+            train_arm(args)
+        return
     w = scenes.workload(args.config, scale=args.scale)
     if args.impl == "reference":
         reference_arm(args, w)

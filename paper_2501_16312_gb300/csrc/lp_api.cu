@@ -35,7 +35,7 @@ struct lp_ctx {
     char err[512] = {0};
 
     DevBuf<float> rec;
-    DevBuf<uint32_t> counts, offsets, zbits, scan_tmp, hist, last;
+    DevBuf<uint32_t> counts, offsets, zbits, scan_tmp, hist, last, emit_part;
     DevBuf<int4> trect;
     DevBuf<uint64_t> keys0, keys1;
     DevBuf<uint32_t> vals0, vals1;
@@ -261,7 +261,7 @@ void lp_destroy(lp_ctx* ctx) {
     cudaSetDevice(ctx->device);
     cudaDeviceSynchronize();
     release(ctx->rec); release(ctx->counts); release(ctx->offsets); release(ctx->zbits);
-    release(ctx->scan_tmp); release(ctx->hist); release(ctx->last); release(ctx->trect);
+    release(ctx->scan_tmp); release(ctx->hist); release(ctx->last); release(ctx->trect); release(ctx->emit_part);
     release(ctx->keys0); release(ctx->keys1); release(ctx->vals0); release(ctx->vals1);
     release(ctx->ranges); release(ctx->tl); release(ctx->acc); release(ctx->scratch_image);
     release(ctx->dkeys0); release(ctx->dkeys1); release(ctx->dvals0); release(ctx->dvals1);
@@ -314,11 +314,18 @@ static lp_status reserve_impl(lp_ctx* ctx, long long records, long long entries,
     LP_TRY(ensure(ctx, ctx->dvals0, records, false, "depth values"));
     LP_TRY(ensure(ctx, ctx->dvals1, records, false, "depth values"));
     LP_TRY(ensure(ctx, ctx->counts_sorted, records, false, "sorted counts"));
-    const long long hmax = entries > records ? entries : records;
+    // a captured forward sorts up to the smallest key/value capacity, which
+    // the allocator may have rounded up past `entries`
+    long long kcap = (long long)ctx->keys0.cap;
+    if ((long long)ctx->keys1.cap < kcap) kcap = ctx->keys1.cap;
+    if ((long long)ctx->vals0.cap < kcap) kcap = ctx->vals0.cap;
+    if ((long long)ctx->vals1.cap < kcap) kcap = ctx->vals1.cap;
+    const long long hmax = kcap > records ? kcap : records;
     LP_TRY(ensure(ctx, ctx->hist, (long long)lp::sort_hist_elems(hmax), false, "histograms"));
     long long sb = lp::scan_blocks(records);
     long long sb2 = lp::scan_blocks((long long)lp::sort_hist_elems(hmax));
     LP_TRY(ensure(ctx, ctx->scan_tmp, sb > sb2 ? sb : sb2, false, "scan blocks"));
+    LP_TRY(ensure(ctx, ctx->emit_part, (long long)lp::emit_blocks(records, kcap) + 1, false, "emit partition"));
     LP_TRY(ensure(ctx, ctx->ranges, tiles, false, "tile ranges"));
     LP_TRY(ensure(ctx, ctx->last, pixels, false, "pixel state"));
     LP_TRY(ensure(ctx, ctx->tl, pixels, false, "pixel state"));
@@ -414,6 +421,8 @@ lp_status lp_render_forward(lp_ctx* ctx, const lp_prims* prims, const lp_camera*
     LP_TRY(ensure(ctx, ctx->hist, (long long)lp::sort_hist_elems(bound), cap_mode, "histograms"));
     LP_TRY(ensure(ctx, ctx->scan_tmp, lp::scan_blocks((long long)lp::sort_hist_elems(bound)), cap_mode,
                   "scan blocks"));
+    LP_TRY(ensure(ctx, ctx->emit_part, (long long)lp::emit_blocks(records, bound) + 1, cap_mode,
+                  "emit partition"));
 
     const int tile_bits = bits_for(tiles);
     int key_bits;
@@ -422,8 +431,9 @@ lp_status lp_render_forward(lp_ctx* ctx, const lp_prims* prims, const lp_camera*
         // stage 2: entries in depth order, stably sorted by their tile id
         uint32_t* t0 = reinterpret_cast<uint32_t*>(ctx->keys0.p);
         uint32_t* t1 = reinterpret_cast<uint32_t*>(ctx->keys1.p);
-        LP_CUDA(lp::launch_emit_sorted(order, ctx->counts_sorted.p, ctx->offsets.p, ctx->trect.p, prims->n,
-                                       records, cp, t0, ctx->vals0.p, bound, ctx->d_status, st));
+        LP_CUDA(lp::launch_emit_sorted(order, ctx->counts_sorted.p, ctx->offsets.p, ctx->trect.p, records,
+                                       ctx->d_E, bound, ctx->emit_part.p, t0, ctx->vals0.p, bound, ctx->d_status,
+                                       st));
         mark(ctx, st, 2, cap_mode);
         key_bits = tile_bits;
         LP_CUDA(lp::launch_radix_sort32(t0, ctx->vals0.p, t1, ctx->vals1.p, ctx->d_E, bound, key_bits,
@@ -436,8 +446,8 @@ lp_status lp_render_forward(lp_ctx* ctx, const lp_prims* prims, const lp_camera*
                                     st));
         ctx->result_in_1 = in1;
     } else {
-        LP_CUDA(lp::launch_emit(ctx->counts.p, ctx->offsets.p, ctx->trect.p, ctx->zbits.p, prims->n,
-                                records, cp, ctx->keys0.p, ctx->vals0.p, bound, ctx->d_status, st));
+        LP_CUDA(lp::launch_emit(ctx->counts.p, ctx->offsets.p, ctx->trect.p, ctx->zbits.p, records, ctx->d_E,
+                                bound, ctx->emit_part.p, ctx->keys0.p, ctx->vals0.p, bound, ctx->d_status, st));
         mark(ctx, st, 2, cap_mode);
         key_bits = 32 + tile_bits;
         LP_CUDA(lp::launch_radix_sort(ctx->keys0.p, ctx->vals0.p, ctx->keys1.p, ctx->vals1.p, ctx->d_E,

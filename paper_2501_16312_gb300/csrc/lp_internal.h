@@ -21,9 +21,14 @@ int scan_blocks(long long n);
 cudaError_t launch_scan(const uint32_t* in, long long n, uint32_t* out, uint32_t* block_sums,
                         uint32_t* total, cudaStream_t st);
 
+// Key emission.  n_dev: the list length E on the device (written by the
+// scan), bound: an upper bound of E for grid sizing, part: emit_blocks + 1
+// words of scratch, cap: capacity of keys/vals.
+int emit_blocks(long long n_records, long long bound);
 cudaError_t launch_emit(const uint32_t* counts, const uint32_t* offsets, const int4* trect,
-                        const uint32_t* zbits, int n, long long n_records, const CamsParam& cams,
-                        uint64_t* keys, uint32_t* vals, long long cap, int* status, cudaStream_t st);
+                        const uint32_t* zbits, long long n_records, const uint32_t* n_dev, long long bound,
+                        uint32_t* part, uint64_t* keys, uint32_t* vals, long long cap, int* status,
+                        cudaStream_t st);
 
 int sort_blocks(long long bound);
 size_t sort_hist_elems(long long bound);
@@ -43,8 +48,9 @@ cudaError_t launch_depth_keys(const uint32_t* counts, const uint32_t* zbits, lon
 cudaError_t launch_gather_counts(const uint32_t* counts, const uint32_t* order, long long n, uint32_t* out,
                                  cudaStream_t st);
 cudaError_t launch_emit_sorted(const uint32_t* order, const uint32_t* counts_sorted, const uint32_t* offsets,
-                               const int4* trect, int n, long long n_records, const CamsParam& cams,
-                               uint32_t* keys, uint32_t* vals, long long cap, int* status, cudaStream_t st);
+                               const int4* trect, long long n_records, const uint32_t* n_dev, long long bound,
+                               uint32_t* part, uint32_t* keys, uint32_t* vals, long long cap, int* status,
+                               cudaStream_t st);
 cudaError_t launch_ranges32(const uint32_t* keys, const uint32_t* n_dev, long long bound,
                             const int* status, uint2* ranges, int sms, cudaStream_t st);
 

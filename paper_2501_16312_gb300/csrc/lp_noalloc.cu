@@ -43,6 +43,7 @@ constexpr size_t kHistBytes = align256(kHistElems * 4);
 constexpr size_t kScanTmpBytes = align256(((kHistElems + 4095) / 4096 + 16) * 4);
 constexpr size_t kRangeBytes = align256(kMaxTiles * 8);
 constexpr size_t kPixBytes = align256(kMaxPixels * 4);
+constexpr size_t kPartBytes = align256(((kMaxPrims + kMaxEntries + 1023) / 1024 + 2) * 4);
 constexpr size_t kMiscBytes = 256;
 
 constexpr size_t kOffRec = 0;
@@ -59,7 +60,8 @@ constexpr size_t kOffScanTmp = kOffHist + kHistBytes;
 constexpr size_t kOffRanges = kOffScanTmp + kScanTmpBytes;
 constexpr size_t kOffLast = kOffRanges + kRangeBytes;
 constexpr size_t kOffTl = kOffLast + kPixBytes;
-constexpr size_t kOffMisc = kOffTl + kPixBytes;   // E, status, tile counter, pair counts
+constexpr size_t kOffPart = kOffTl + kPixBytes;
+constexpr size_t kOffMisc = kOffPart + kPartBytes;   // E, status, tile counter, pair counts
 constexpr size_t kScratchBytes = kOffMisc + kMiscBytes;   // about 10.6 MiB
 
 // The scratch itself.  In host code `g_scratch` names a host-side stand-in,
@@ -130,6 +132,7 @@ extern "C" lp_status lp_render_forward_noalloc(const lp_prims* prims, const lp_c
     uint2* ranges = reinterpret_cast<uint2*>(base + kOffRanges);
     uint32_t* last = reinterpret_cast<uint32_t*>(base + kOffLast);
     float* tl = reinterpret_cast<float*>(base + kOffTl);
+    uint32_t* part = reinterpret_cast<uint32_t*>(base + kOffPart);
     uint32_t* d_E = reinterpret_cast<uint32_t*>(base + kOffMisc);
     int* d_status = reinterpret_cast<int*>(base + kOffMisc + 4);
     int* d_tile_counter = reinterpret_cast<int*>(base + kOffMisc + 8);
@@ -177,7 +180,8 @@ extern "C" lp_status lp_render_forward_noalloc(const lp_prims* prims, const lp_c
     NA_CUDA(cudaMemcpyAsync(&E, d_E, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
     NA_CUDA(cudaStreamSynchronize(st));
     if ((long long)E > kMaxEntries) return LP_ERR_CAPACITY;
-    NA_CUDA(lp::launch_emit(counts, offsets, trect, zbits, prims->n, records, cp, keys0, vals0, E,
+    if (lp::emit_blocks(records, E) + 1 > (long long)(kPartBytes / 4)) return LP_ERR_CAPACITY;
+    NA_CUDA(lp::launch_emit(counts, offsets, trect, zbits, records, d_E, E, part, keys0, vals0, kMaxEntries,
                             d_status, st));
     int passes = 0;
     NA_CUDA(lp::launch_radix_sort(keys0, vals0, keys1, vals1, d_E, E, 32 + bits_for(tiles), hist, scan_tmp,

@@ -6,6 +6,8 @@
 // Every kernel that depends on the tile-list length E reads it from device
 // memory, so the same launch sequence works when E is only known on the
 // device (inside a CUDA graph); the host supplies an upper bound for grids.
+#include <atomic>
+
 #include "lp_device.cuh"
 #include "lp_internal.h"
 
@@ -95,70 +97,95 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(const uint32_t* __re
 
 // ------------------------------------------------------------- key emission
 // Each record's tile rectangle is (first global tile id, row stride, width,
-// height).  A lane writes the entries of a small rectangle itself; larger
-// rectangles are written by the whole warp, one record at a time, so that a
-// near-camera primitive covering thousands of tiles does not serialise on one
-// thread and its writes stay coalesced.
-constexpr uint32_t kEmitLaneMax = 8;
+// height); its entries occupy [offset, offset + count) of the list.  Work is
+// split by merge path over records and entries together: record k sits at
+// merged position k + offset[k], entry j after every record starting at or
+// before j, and block b takes merged positions [b T, (b + 1) T).  So a block
+// writes at most T entries however unevenly tiles are spread over records (in
+// depth order the near-camera records covering thousands of tiles come
+// together), and its writes are coalesced: thread t writes entries j0 + t,
+// j0 + t + 256, ... and finds the owning record by binary search over the
+// block's record offsets in shared memory.
+constexpr int kEmitBlock = 256;
+constexpr int kEmitItems = 1024;   // T: records + entries per block
 
-template <typename WriteFn>
-__device__ __forceinline__ void emit_rect(const int4 t, long long off, uint32_t cnt, uint32_t first_q,
-                                          uint32_t step, WriteFn write) {
-    for (uint32_t q = first_q; q < cnt; q += step) {
-        const uint32_t row = q / (uint32_t)t.z, col = q - row * (uint32_t)t.z;
-        write(off + q, (uint32_t)t.x + row * (uint32_t)t.y + col);
+// part[b] = number of records whose merged position precedes b T.
+__global__ void __launch_bounds__(256) k_emit_partition(const uint32_t* __restrict__ offsets, long long R,
+                                                        const uint32_t* __restrict__ n_dev, long long bound,
+                                                        int nb, uint32_t* __restrict__ part) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b > nb) return;
+    const long long E = min((long long)*n_dev, bound);
+    const long long d = min((long long)b * kEmitItems, R + E);
+    long long lo = 0, hi = R;
+    while (lo < hi) {
+        const long long mid = (lo + hi) >> 1;
+        if (mid + (long long)offsets[mid] < d) lo = mid + 1;
+        else hi = mid;
     }
+    part[b] = (uint32_t)lo;
 }
 
-__global__ void __launch_bounds__(256) k_emit(const uint32_t* __restrict__ counts,
-                                              const uint32_t* __restrict__ offsets,
-                                              const int4* __restrict__ trect,
-                                              const uint32_t* __restrict__ zbits,
-                                              long long n_records, uint64_t* __restrict__ keys,
-                                              uint32_t* __restrict__ vals, long long cap,
-                                              int* __restrict__ status) {
-    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    uint32_t cnt = 0;
-    long long off = 0;
-    int4 t = make_int4(0, 0, 0, 0);
-    uint32_t z = 0;
-    if (r < n_records) {
-        cnt = counts[r];
+// SORTED: list position k holds record order[k] (stage 2 of the two-stage
+// sort) and the key is the 32-bit tile id; otherwise position k is record k
+// and the key is (tile << 32) | depth bits.
+template <bool SORTED>
+__global__ void __launch_bounds__(kEmitBlock) k_emit_lb(const uint32_t* __restrict__ order,
+                                                        const uint32_t* __restrict__ counts,
+                                                        const uint32_t* __restrict__ offsets,
+                                                        const int4* __restrict__ trect,
+                                                        const uint32_t* __restrict__ zbits, long long R,
+                                                        const uint32_t* __restrict__ n_dev, long long bound,
+                                                        const uint32_t* __restrict__ part,
+                                                        uint32_t* __restrict__ keys32,
+                                                        uint64_t* __restrict__ keys64,
+                                                        uint32_t* __restrict__ vals, long long cap,
+                                                        int* __restrict__ status) {
+    __shared__ uint32_t s_off[kEmitItems + 1];
+    __shared__ int4 s_rect[kEmitItems + 1];
+    __shared__ uint32_t s_rec[kEmitItems + 1];
+    __shared__ uint32_t s_z[SORTED ? 1 : kEmitItems + 1];
+    const int b = blockIdx.x, tid = threadIdx.x;
+    const long long Ed = (long long)*n_dev;
+    if (b == 0 && tid == 0 && Ed > cap) atomicOr(status, kStatusCapacity);
+    const long long E = min(Ed, bound);
+    const long long d0 = (long long)b * kEmitItems;
+    if (d0 >= R + E) return;   // uniform over the block
+    const long long d1 = min(d0 + kEmitItems, R + E);
+    const long long i0 = part[b], i1 = part[b + 1];
+    const long long j0 = d0 - i0, j1 = min(d1 - i1, cap);
+    // the record owning entry j0 may start before d0: records ks .. i1 - 1
+    const long long ks = i0 > 0 ? i0 - 1 : 0;
+    const int nrec = (int)(i1 - ks);   // <= kEmitItems + 1
+    for (int t = tid; t < nrec; t += kEmitBlock) {
+        const long long k = ks + t;
+        const uint32_t cnt = counts[k];
+        const uint32_t r = SORTED ? order[k] : (uint32_t)k;
+        s_off[t] = offsets[k];
+        s_rec[t] = r;
         if (cnt) {
-            off = offsets[r];
-            if (off + cnt > cap) {
-                atomicOr(status, kStatusCapacity);
-                cnt = 0;
-            } else {
-                t = trect[r];
-                z = zbits[r];
-            }
+            s_rect[t] = trect[r];
+            if (!SORTED) s_z[t] = zbits[r];
         }
     }
-    const bool have = cnt > 0;
-    if (have && cnt <= kEmitLaneMax)
-        emit_rect(t, off, cnt, 0, 1, [&](long long q, uint32_t tile) {
-            keys[q] = ((uint64_t)tile << 32) | z;
-            vals[q] = (uint32_t)r;
-        });
-    const int lane = threadIdx.x & 31;
-    unsigned big = __ballot_sync(0xffffffffu, have && cnt > kEmitLaneMax);
-    while (big) {
-        const int src = __ffs(big) - 1;
-        big &= big - 1;
-        const uint32_t c = __shfl_sync(0xffffffffu, cnt, src);
-        const long long o = __shfl_sync(0xffffffffu, off, src);
-        const uint32_t zz = __shfl_sync(0xffffffffu, z, src);
-        const long long rr = __shfl_sync(0xffffffffu, r, src);
-        int4 tt;
-        tt.x = __shfl_sync(0xffffffffu, t.x, src);
-        tt.y = __shfl_sync(0xffffffffu, t.y, src);
-        tt.z = __shfl_sync(0xffffffffu, t.z, src);
-        tt.w = __shfl_sync(0xffffffffu, t.w, src);
-        emit_rect(tt, o, c, lane, 32, [&](long long q, uint32_t tile) {
-            keys[q] = ((uint64_t)tile << 32) | zz;
-            vals[q] = (uint32_t)rr;
-        });
+    __syncthreads();
+    for (long long j = j0 + tid; j < j1; j += kEmitBlock) {
+        // the last record whose offset is <= j owns entry j (records with no
+        // tiles share their offset with the next record)
+        const uint32_t ju = (uint32_t)j;
+        int lo = 0, hi = nrec - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (s_off[mid] <= ju) lo = mid;
+            else hi = mid - 1;
+        }
+        const int4 t = s_rect[lo];
+        const uint32_t q = ju - s_off[lo];
+        const uint32_t row = q / (uint32_t)t.z, col = q - row * (uint32_t)t.z;
+        const uint32_t tile = (uint32_t)t.x + row * (uint32_t)t.y + col;
+        if (SORTED) keys32[j] = tile;
+        else keys64[j] = ((uint64_t)tile << 32) | s_z[lo];
+        vals[j] = s_rec[lo];
     }
 }
 
@@ -171,76 +198,149 @@ constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kSortPerWarp = 512;
 constexpr int kSortChunk = kSortWarps * kSortPerWarp;   // 4096
 constexpr int kRadix = 256;
+constexpr int kScatterIPT = kSortPerWarp / 32;   // items per lane
 
+// Digit counts of one block's chunk: each warp counts its sub-chunk into its
+// own shared histogram (less contention than one histogram per block).
 template <typename K>
 __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const K* __restrict__ keys,
                                                              const uint32_t* __restrict__ n_dev,
                                                              long long bound, int shift, int nblocks,
                                                              uint32_t* __restrict__ hist) {
-    __shared__ uint32_t h[kRadix];
-    h[threadIdx.x] = 0;
+    __shared__ uint32_t h[kSortWarps][kRadix];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+#pragma unroll
+    for (int ww = 0; ww < kSortWarps; ++ww) h[ww][tid] = 0;
     __syncthreads();
     const long long n = n_dev ? min((long long)*n_dev, bound) : bound;
-    const long long base = (long long)blockIdx.x * kSortChunk;
-    for (int k = threadIdx.x; k < kSortChunk; k += kSortThreads) {
-        const long long q = base + k;
-        if (q < n) atomicAdd(&h[(uint32_t)(keys[q] >> shift) & (kRadix - 1)], 1u);
+    const long long wbase = (long long)blockIdx.x * kSortChunk + (long long)w * kSortPerWarp;
+    uint32_t dig[kScatterIPT];
+#pragma unroll
+    for (int r = 0; r < kScatterIPT; ++r) {
+        const long long q = wbase + r * 32 + lane;
+        dig[r] = q < n ? ((uint32_t)(keys[q] >> shift) & (kRadix - 1)) : (uint32_t)kRadix;
     }
+#pragma unroll
+    for (int r = 0; r < kScatterIPT; ++r)
+        if (dig[r] < kRadix) atomicAdd(&h[w][dig[r]], 1u);
     __syncthreads();
-    hist[(size_t)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
+    uint32_t t = 0;
+#pragma unroll
+    for (int ww = 0; ww < kSortWarps; ++ww) t += h[ww][tid];
+    hist[(size_t)tid * nblocks + blockIdx.x] = t;
+}
+
+// Lanes of the warp whose digit equals this lane's (digits < 512): one ballot
+// per digit bit.  Measured faster than __match_any_sync on sm_103 when the
+// kernel streams from DRAM.
+__device__ __forceinline__ unsigned digit_peers(uint32_t d) {
+    unsigned m = 0xffffffffu;
+#pragma unroll
+    for (int b = 0; b < 9; ++b) {
+        const unsigned bit = (d >> b) & 1u;
+        const unsigned bb = __ballot_sync(0xffffffffu, bit);
+        m &= bit ? bb : ~bb;
+    }
+    return m;
+}
+
+// One pass of the stable scatter.  Each warp ranks its 512 items round by
+// round (digit_peers groups equal digits; a per-warp counter per digit gives
+// the running rank), the block turns the (warp, digit) counts into block-local
+// starts in digit order, the items are placed in shared memory in that order,
+// and the block writes them out in index order: consecutive threads then write
+// consecutive addresses of each digit's run.  Keys and values are read once.
+
+template <typename K>
+constexpr size_t scatter_smem_bytes() {
+    return (size_t)kSortChunk * (sizeof(K) + sizeof(uint32_t)) + (size_t)kSortWarps * kRadix * 4 + kRadix * 4;
 }
 
 template <typename K>
-__global__ void __launch_bounds__(kSortThreads) k_radix_scatter(
+__global__ void __launch_bounds__(kSortThreads, sizeof(K) == 4 ? 4 : 3) k_radix_scatter(
     const K* __restrict__ kin, const uint32_t* __restrict__ vin,
     K* __restrict__ kout, uint32_t* __restrict__ vout, const uint32_t* __restrict__ n_dev,
     long long bound, int shift, int nblocks, const uint32_t* __restrict__ offs) {
-    __shared__ uint32_t cnt[kSortWarps][kRadix];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    extern __shared__ __align__(16) unsigned char smem[];
+    K* skeys = reinterpret_cast<K*>(smem);
+    uint32_t* svals = reinterpret_cast<uint32_t*>(smem + sizeof(K) * kSortChunk);
+    uint32_t* wcnt = svals + kSortChunk;            // [kSortWarps][kRadix]
+    uint32_t* gbase = wcnt + kSortWarps * kRadix;   // [kRadix]
+    __shared__ uint32_t wsum[kSortWarps];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const long long n = n_dev ? min((long long)*n_dev, bound) : bound;
-    const long long wbase = (long long)blockIdx.x * kSortChunk + (long long)w * kSortPerWarp;
-    for (int d = lane; d < kRadix; d += 32) cnt[w][d] = 0;
+    const long long bbase = (long long)blockIdx.x * kSortChunk;
+    if (bbase >= n) return;   // uniform over the block
+    for (int d = lane; d < kRadix; d += 32) wcnt[w * kRadix + d] = 0;
     __syncwarp();
-    // per-warp digit counts
-    for (int k = lane; k < kSortPerWarp; k += 32) {
-        const long long q = wbase + k;
-        if (q < n) atomicAdd(&cnt[w][(uint32_t)(kin[q] >> shift) & (kRadix - 1)], 1u);
-    }
-    __syncthreads();
-    // running offsets: global digit base of this block + earlier warps' counts
-    {
-        const int d = threadIdx.x;   // kSortThreads == kRadix
-        uint32_t run = offs[(size_t)d * nblocks + blockIdx.x];
+
+    const long long wbase = bbase + (long long)w * kSortPerWarp;
+    K key[kScatterIPT];
+    uint32_t pk[kScatterIPT];   // pk = digit | warp-local rank << 9
 #pragma unroll
-        for (int ww = 0; ww < kSortWarps; ++ww) {
-            const uint32_t c = cnt[ww][d];
-            cnt[ww][d] = run;
-            run += c;
+    for (int r = 0; r < kScatterIPT; ++r) {
+        const long long q = wbase + r * 32 + lane;
+        const bool ok = q < n;
+        key[r] = ok ? kin[q] : K(0);
+        pk[r] = ok ? ((uint32_t)(key[r] >> shift) & (kRadix - 1)) : (uint32_t)kRadix;   // kRadix: no item
+    }
+    const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+    for (int r = 0; r < kScatterIPT; ++r) {
+        const uint32_t d = pk[r];
+        const unsigned peers = digit_peers(d);
+        const uint32_t rank = __popc(peers & lt);
+        uint32_t base = 0;
+        if (d < kRadix) base = wcnt[w * kRadix + d];
+        __syncwarp();
+        if (d < kRadix && rank == 0) wcnt[w * kRadix + d] = base + __popc(peers);
+        __syncwarp();
+        pk[r] = d | ((base + rank) << 9);
+    }
+    __syncthreads();
+
+    // thread d: starts of (warp, d) within digit d, then the block-local start of d
+    const int d = tid;   // kSortThreads == kRadix
+    uint32_t tot = 0;
+#pragma unroll
+    for (int ww = 0; ww < kSortWarps; ++ww) {
+        const uint32_t c = wcnt[ww * kRadix + d];
+        wcnt[ww * kRadix + d] = tot;
+        tot += c;
+    }
+    uint32_t x = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    uint32_t dstart = x - tot;
+    for (int ww = 0; ww < w; ++ww) dstart += wsum[ww];
+#pragma unroll
+    for (int ww = 0; ww < kSortWarps; ++ww) wcnt[ww * kRadix + d] += dstart;
+    // global position of block-local index i of digit d: gbase[d] + i (mod 2^32)
+    gbase[d] = offs[(size_t)d * nblocks + blockIdx.x] - dstart;
+    __syncthreads();
+
+    // values are read only now, while the keys' ranks are known
+#pragma unroll
+    for (int r = 0; r < kScatterIPT; ++r) {
+        const uint32_t dd = pk[r] & 511u;
+        if (dd < kRadix) {
+            const uint32_t p = wcnt[w * kRadix + dd] + (pk[r] >> 9);
+            skeys[p] = key[r];
+            svals[p] = vin[wbase + r * 32 + lane];
         }
     }
     __syncthreads();
-    const unsigned lt = (1u << lane) - 1u;
-    for (int k = 0; k < kSortPerWarp; k += 32) {
-        const long long q = wbase + k + lane;
-        const bool ok = q < n;
-        K key = 0;
-        uint32_t val = 0, digit = kRadix;   // out-of-range lanes form their own group
-        if (ok) {
-            key = kin[q];
-            val = vin[q];
-            digit = (uint32_t)(key >> shift) & (kRadix - 1);
-        }
-        const unsigned peers = __match_any_sync(0xffffffffu, digit);
-        const int rank = __popc(peers & lt);
-        uint32_t pos = 0;
-        if (ok) pos = cnt[w][digit] + rank;
-        __syncwarp();
-        if (ok && rank == 0) cnt[w][digit] += __popc(peers);
-        __syncwarp();
-        if (ok) {
-            kout[pos] = key;
-            vout[pos] = val;
-        }
+    const int cnt = (int)min((long long)kSortChunk, n - bbase);
+    for (int i = tid; i < cnt; i += kSortThreads) {
+        const K k = skeys[i];
+        const uint32_t g = gbase[(uint32_t)(k >> shift) & (kRadix - 1)] + (uint32_t)i;
+        kout[g] = k;
+        vout[g] = svals[i];
     }
 }
 
@@ -264,56 +364,6 @@ __global__ void __launch_bounds__(256) k_gather_counts(const uint32_t* __restric
                                                        uint32_t* __restrict__ out) {
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (k < n) out[k] = counts[order[k]];
-}
-
-__global__ void __launch_bounds__(256) k_emit_sorted(const uint32_t* __restrict__ order,
-                                                     const uint32_t* __restrict__ counts_sorted,
-                                                     const uint32_t* __restrict__ offsets,
-                                                     const int4* __restrict__ trect,
-                                                     long long n_records, uint32_t* __restrict__ keys,
-                                                     uint32_t* __restrict__ vals, long long cap,
-                                                     int* __restrict__ status) {
-    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    uint32_t cnt = 0, r = 0;
-    long long off = 0;
-    int4 t = make_int4(0, 0, 0, 0);
-    if (k < n_records) {
-        cnt = counts_sorted[k];
-        if (cnt) {
-            off = offsets[k];
-            if (off + cnt > cap) {
-                atomicOr(status, kStatusCapacity);
-                cnt = 0;
-            } else {
-                r = order[k];
-                t = trect[r];
-            }
-        }
-    }
-    const bool have = cnt > 0;
-    if (have && cnt <= kEmitLaneMax)
-        emit_rect(t, off, cnt, 0, 1, [&](long long q, uint32_t tile) {
-            keys[q] = tile;
-            vals[q] = r;
-        });
-    const int lane = threadIdx.x & 31;
-    unsigned big = __ballot_sync(0xffffffffu, have && cnt > kEmitLaneMax);
-    while (big) {
-        const int src = __ffs(big) - 1;
-        big &= big - 1;
-        const uint32_t c = __shfl_sync(0xffffffffu, cnt, src);
-        const long long o = __shfl_sync(0xffffffffu, off, src);
-        const uint32_t rr = __shfl_sync(0xffffffffu, r, src);
-        int4 tt;
-        tt.x = __shfl_sync(0xffffffffu, t.x, src);
-        tt.y = __shfl_sync(0xffffffffu, t.y, src);
-        tt.z = __shfl_sync(0xffffffffu, t.z, src);
-        tt.w = __shfl_sync(0xffffffffu, t.w, src);
-        emit_rect(tt, o, c, lane, 32, [&](long long q, uint32_t tile) {
-            keys[q] = tile;
-            vals[q] = rr;
-        });
-    }
 }
 
 // Skipped entirely when the emission overflowed: the list then holds stale
@@ -350,18 +400,49 @@ cudaError_t launch_scan(const uint32_t* in, long long n, uint32_t* out, uint32_t
     return cudaGetLastError();
 }
 
-cudaError_t launch_emit(const uint32_t* counts, const uint32_t* offsets, const int4* trect,
-                        const uint32_t* zbits, int n, long long n_records, const CamsParam& cams,
-                        uint64_t* keys, uint32_t* vals, long long cap, int* status, cudaStream_t st) {
-    (void)n;
-    (void)cams;
+int emit_blocks(long long n_records, long long bound) {
+    return (int)((n_records + bound + kEmitItems - 1) / kEmitItems);
+}
+
+template <bool SORTED>
+static cudaError_t emit_t(const uint32_t* order, const uint32_t* counts, const uint32_t* offsets,
+                          const int4* trect, const uint32_t* zbits, long long n_records, const uint32_t* n_dev,
+                          long long bound, uint32_t* part, uint32_t* keys32, uint64_t* keys64, uint32_t* vals,
+                          long long cap, int* status, cudaStream_t st) {
     if (n_records == 0) return cudaSuccess;
-    const int grid = (int)((n_records + 255) / 256);
-    k_emit<<<grid, 256, 0, st>>>(counts, offsets, trect, zbits, n_records, keys, vals, cap, status);
+    const int nb = emit_blocks(n_records, bound);
+    k_emit_partition<<<(nb + 1 + 255) / 256, 256, 0, st>>>(offsets, n_records, n_dev, bound, nb, part);
+    k_emit_lb<SORTED><<<nb, kEmitBlock, 0, st>>>(order, counts, offsets, trect, zbits, n_records, n_dev, bound,
+                                                 part, keys32, keys64, vals, cap, status);
     return cudaGetLastError();
 }
 
+cudaError_t launch_emit(const uint32_t* counts, const uint32_t* offsets, const int4* trect,
+                        const uint32_t* zbits, long long n_records, const uint32_t* n_dev, long long bound,
+                        uint32_t* part, uint64_t* keys, uint32_t* vals, long long cap, int* status,
+                        cudaStream_t st) {
+    return emit_t<false>(nullptr, counts, offsets, trect, zbits, n_records, n_dev, bound, part, nullptr, keys,
+                         vals, cap, status, st);
+}
+
 int sort_blocks(long long bound) { return (int)((bound + kSortChunk - 1) / kSortChunk); }
+
+// The scatter's shared memory exceeds the 48 KB default for 64-bit keys: opt
+// in once per device.
+template <typename K>
+static cudaError_t scatter_attr() {
+    constexpr size_t bytes = scatter_smem_bytes<K>();
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    static std::atomic<unsigned long long> done{0};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (done.load() & bit) return cudaSuccess;
+    e = cudaFuncSetAttribute(k_radix_scatter<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) done.fetch_or(bit);
+    return e;
+}
 
 template <typename K>
 static cudaError_t radix_sort_t(K* k0, uint32_t* v0, K* k1, uint32_t* v1, const uint32_t* n_dev,
@@ -370,14 +451,16 @@ static cudaError_t radix_sort_t(K* k0, uint32_t* v0, K* k1, uint32_t* v1, const 
     const int nb = sort_blocks(bound);
     int passes = 0;
     if (nb > 0) {
+        cudaError_t ea = scatter_attr<K>();
+        if (ea != cudaSuccess) return ea;
         K* kin = k0; uint32_t* vin = v0;
         K* kout = k1; uint32_t* vout = v1;
         for (int shift = 0; shift < key_bits; shift += 8) {
             k_radix_hist<K><<<nb, kSortThreads, 0, st>>>(kin, n_dev, bound, shift, nb, hist);
             cudaError_t e = launch_scan(hist, (long long)kRadix * nb, hist, scan_tmp, nullptr, st);
             if (e != cudaSuccess) return e;
-            k_radix_scatter<K><<<nb, kSortThreads, 0, st>>>(kin, vin, kout, vout, n_dev, bound, shift, nb,
-                                                            hist);
+            k_radix_scatter<K><<<nb, kSortThreads, scatter_smem_bytes<K>(), st>>>(kin, vin, kout, vout, n_dev,
+                                                                                   bound, shift, nb, hist);
             K* tk = kin; kin = kout; kout = tk;
             uint32_t* tv = vin; vin = vout; vout = tv;
             ++passes;
@@ -416,14 +499,11 @@ cudaError_t launch_gather_counts(const uint32_t* counts, const uint32_t* order, 
 }
 
 cudaError_t launch_emit_sorted(const uint32_t* order, const uint32_t* counts_sorted, const uint32_t* offsets,
-                               const int4* trect, int n, long long n_records, const CamsParam& cams,
-                               uint32_t* keys, uint32_t* vals, long long cap, int* status, cudaStream_t st) {
-    (void)n;
-    (void)cams;
-    if (n_records == 0) return cudaSuccess;
-    k_emit_sorted<<<(int)((n_records + 255) / 256), 256, 0, st>>>(order, counts_sorted, offsets, trect,
-                                                                  n_records, keys, vals, cap, status);
-    return cudaGetLastError();
+                               const int4* trect, long long n_records, const uint32_t* n_dev, long long bound,
+                               uint32_t* part, uint32_t* keys, uint32_t* vals, long long cap, int* status,
+                               cudaStream_t st) {
+    return emit_t<true>(order, counts_sorted, offsets, trect, nullptr, n_records, n_dev, bound, part, keys,
+                        nullptr, vals, cap, status, st);
 }
 
 static int ranges_grid(long long bound, int sms) {
