@@ -7,6 +7,7 @@
 // memory, so the same launch sequence works when E is only known on the
 // device (inside a CUDA graph); the host supplies an upper bound for grids.
 #include <atomic>
+#include <cstdint>
 
 #include "lp_device.cuh"
 #include "lp_internal.h"
@@ -48,13 +49,31 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t x, uint32_t& total)
     return before + incl - x;
 }
 
+// A thread's kScanItems consecutive elements, with 16-byte loads when the
+// whole run is in range and the array is 16-byte aligned.
+__device__ __forceinline__ void scan_load(const uint32_t* __restrict__ in, long long n, long long base,
+                                          bool vec, uint32_t v[kScanItems]) {
+    if (vec && base + kScanItems <= n) {
+        const uint4* p = reinterpret_cast<const uint4*>(in + base);
+#pragma unroll
+        for (int k = 0; k < kScanItems / 4; ++k) {
+            const uint4 x = p[k];
+            v[4 * k] = x.x; v[4 * k + 1] = x.y; v[4 * k + 2] = x.z; v[4 * k + 3] = x.w;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < kScanItems; ++k) v[k] = base + k < n ? in[base + k] : 0u;
+    }
+}
+
 __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t* __restrict__ in, long long n,
                                                               uint32_t* __restrict__ block_sums) {
     const long long base = (long long)blockIdx.x * kScanTile + (long long)threadIdx.x * kScanItems;
+    uint32_t v[kScanItems];
+    scan_load(in, n, base, ((uintptr_t)in & 15) == 0, v);
     uint32_t s = 0;
 #pragma unroll
-    for (int k = 0; k < kScanItems; ++k)
-        if (base + k < n) s += in[base + k];
+    for (int k = 0; k < kScanItems; ++k) s += v[k];
     uint32_t total;
     block_excl_scan(s, total);
     if (threadIdx.x == 0) block_sums[blockIdx.x] = total;
@@ -79,19 +98,31 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(const uint32_t* __re
                                                             const uint32_t* __restrict__ block_off,
                                                             uint32_t* __restrict__ out) {
     const long long base = (long long)blockIdx.x * kScanTile + (long long)threadIdx.x * kScanItems;
+    const bool vec = (((uintptr_t)in | (uintptr_t)out) & 15) == 0;
     uint32_t v[kScanItems];
+    scan_load(in, n, base, vec, v);
     uint32_t s = 0;
 #pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
-        v[k] = base + k < n ? in[base + k] : 0u;
-        s += v[k];
-    }
+    for (int k = 0; k < kScanItems; ++k) s += v[k];
     uint32_t total;
     uint32_t run = block_excl_scan(s, total) + block_off[blockIdx.x];
+    if (vec && base + kScanItems <= n) {
+        uint4* p = reinterpret_cast<uint4*>(out + base);
 #pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
-        if (base + k < n) out[base + k] = run;
-        run += v[k];
+        for (int k = 0; k < kScanItems / 4; ++k) {
+            uint4 x;
+            x.x = run; run += v[4 * k];
+            x.y = run; run += v[4 * k + 1];
+            x.z = run; run += v[4 * k + 2];
+            x.w = run; run += v[4 * k + 3];
+            p[k] = x;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < kScanItems; ++k) {
+            if (base + k < n) out[base + k] = run;
+            run += v[k];
+        }
     }
 }
 

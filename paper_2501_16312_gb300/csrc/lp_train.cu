@@ -13,6 +13,8 @@
 // with opposite signs.  Sec. 3.4 uses Adam.
 #include <cuda_runtime.h>
 
+#include <cstdint>
+
 #include "linprim.h"
 #include "lp_device.cuh"
 
@@ -181,6 +183,28 @@ struct AdamGroups {
 
 // Adam (Kingma & Ba) over every group in one launch.  The step counter lives
 // in device memory so that replays of a captured step advance it.
+__device__ __forceinline__ float adam_lr(const AdamGroups& G, int k, uint32_t j, int t) {
+    if (G.period[k] > 0 && j % (uint32_t)G.period[k] >= (uint32_t)G.head[k]) return G.lr_tail[k];
+    if (G.decay_steps[k] > 0) {
+        const float f = fminf((float)t / (float)G.decay_steps[k], 1.f);
+        return expf((1.f - f) * logf(G.lr[k]) + f * logf(G.lr_final[k]));
+    }
+    return G.lr[k];
+}
+
+__device__ __forceinline__ void adam_one(float& p, float g, float& m, float& v, float lr, float b1, float b2,
+                                         float eps, float c1, float c2) {
+    m = fmaf(b1, m, (1.f - b1) * g);
+    v = fmaf(b2, v, (1.f - b2) * g * g);
+    p -= lr * (m * c1) / (sqrtf(v * c2) + eps);
+}
+
+__device__ __forceinline__ int adam_group_of(const AdamGroups& G, long long i) {
+    int k = 0;
+    while (k + 1 < G.n && i >= G.offset[k] + G.count[k]) ++k;
+    return (i < G.offset[k] || i >= G.offset[k] + G.count[k]) ? -1 : k;   // -1: gap between groups
+}
+
 __global__ void __launch_bounds__(256) k_adam(float* __restrict__ p, const float* __restrict__ g,
                                               float* __restrict__ m, float* __restrict__ v, AdamGroups G,
                                               long long total, float b1, float b2, float eps,
@@ -190,25 +214,41 @@ __global__ void __launch_bounds__(256) k_adam(float* __restrict__ p, const float
     const float c2 = 1.f / (1.f - powf(b2, (float)t));
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
          i += (long long)gridDim.x * blockDim.x) {
-        int k = 0;
-        while (k + 1 < G.n && i >= G.offset[k] + G.count[k]) ++k;
-        if (i < G.offset[k] || i >= G.offset[k] + G.count[k]) continue;   // gap between groups
-        const float gi = g[i];
-        const float mi = fmaf(b1, m[i], (1.f - b1) * gi);
-        const float vi = fmaf(b2, v[i], (1.f - b2) * gi * gi);
+        const int k = adam_group_of(G, i);
+        if (k < 0) continue;
+        const float lr = adam_lr(G, k, (uint32_t)(i - G.offset[k]), t);
+        float pi = p[i], mi = m[i], vi = v[i];
+        adam_one(pi, g[i], mi, vi, lr, b1, b2, eps, c1, c2);
+        p[i] = pi;
         m[i] = mi;
         v[i] = vi;
-        const long long j = i - G.offset[k];
-        float lr;
-        if (G.period[k] > 0 && j % G.period[k] >= G.head[k]) {
-            lr = G.lr_tail[k];
-        } else if (G.decay_steps[k] > 0) {
-            const float f = fminf((float)t / (float)G.decay_steps[k], 1.f);
-            lr = expf((1.f - f) * logf(G.lr[k]) + f * logf(G.lr_final[k]));
-        } else {
-            lr = G.lr[k];
-        }
-        p[i] -= lr * (mi * c1) / (sqrtf(vi * c2) + eps);
+    }
+}
+
+// Same update, four elements per thread with 16-byte accesses; used when the
+// arrays are 16-byte aligned and every group's offset and count are
+// multiples of 4 (so a vector never straddles two groups).
+__global__ void __launch_bounds__(256) k_adam4(float4* __restrict__ p, const float4* __restrict__ g,
+                                               float4* __restrict__ m, float4* __restrict__ v, AdamGroups G,
+                                               long long total4, float b1, float b2, float eps,
+                                               const int* __restrict__ step) {
+    const int t = *step + 1;
+    const float c1 = 1.f / (1.f - powf(b1, (float)t));
+    const float c2 = 1.f / (1.f - powf(b2, (float)t));
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total4;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int k = adam_group_of(G, 4 * i);
+        if (k < 0) continue;
+        const uint32_t j = (uint32_t)(4 * i - G.offset[k]);
+        float4 pp = p[i], mm = m[i], vv = v[i];
+        const float4 gg = g[i];
+        adam_one(pp.x, gg.x, mm.x, vv.x, adam_lr(G, k, j, t), b1, b2, eps, c1, c2);
+        adam_one(pp.y, gg.y, mm.y, vv.y, adam_lr(G, k, j + 1, t), b1, b2, eps, c1, c2);
+        adam_one(pp.z, gg.z, mm.z, vv.z, adam_lr(G, k, j + 2, t), b1, b2, eps, c1, c2);
+        adam_one(pp.w, gg.w, mm.w, vv.w, adam_lr(G, k, j + 3, t), b1, b2, eps, c1, c2);
+        p[i] = pp;
+        m[i] = mm;
+        v[i] = vv;
     }
 }
 
@@ -274,7 +314,7 @@ lp_status lp_adam_step(float* params, const float* grads, float* m, float* v, co
     G.n = n_groups;
     long long total = 0;
     for (int k = 0; k < n_groups; ++k) {
-        if (groups[k].offset < 0 || groups[k].count < 0) return LP_ERR_INVALID;
+        if (groups[k].offset < 0 || groups[k].count < 0 || groups[k].count > 0xffffffffll) return LP_ERR_INVALID;
         if (k > 0 && groups[k].offset < groups[k - 1].offset + groups[k - 1].count) return LP_ERR_INVALID;
         G.offset[k] = groups[k].offset;
         G.count[k] = groups[k].count;
@@ -289,7 +329,13 @@ lp_status lp_adam_step(float* params, const float* grads, float* m, float* v, co
         total = groups[k].offset + groups[k].count;
     }
     cudaStream_t st = (cudaStream_t)stream;
-    if (total > 0)
+    bool vec = ((uintptr_t)params | (uintptr_t)grads | (uintptr_t)m | (uintptr_t)v) % 16 == 0;
+    for (int k = 0; k < n_groups; ++k) vec = vec && groups[k].offset % 4 == 0 && groups[k].count % 4 == 0;
+    if (total > 0 && vec)
+        lp::k_adam4<<<lp::grid_for(total / 4, 256, 152 * 8), 256, 0, st>>>(
+            reinterpret_cast<float4*>(params), reinterpret_cast<const float4*>(grads), reinterpret_cast<float4*>(m),
+            reinterpret_cast<float4*>(v), G, total / 4, beta1, beta2, eps, step);
+    else if (total > 0)
         lp::k_adam<<<lp::grid_for(total, 256, 152 * 16), 256, 0, st>>>(params, grads, m, v, G, total, beta1,
                                                                       beta2, eps, step);
     lp::k_increment<<<1, 1, 0, st>>>(step);
