@@ -334,16 +334,11 @@ def ours(args, workload):
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
 
-    def barrier():
-        if world > 1:
-            dist.barrier()
+    from paper_2501_16312_gb300 import dist as pdist
+    barrier = pdist.barrier
 
     def max_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return pdist.max_over_ranks(x, dev)
 
     w = workload
     P = w.pixels
@@ -544,16 +539,11 @@ def train_arm(args):
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
 
-    def max_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    from paper_2501_16312_gb300 import dist as pdist
+    barrier = pdist.barrier
 
-    def barrier():
-        if world > 1:
-            dist.barrier()
+    def max_over_ranks(x):
+        return pdist.max_over_ranks(x, dev)
 
     w = scenes.optimisation_workload(scale=args.scale)
     P = w.pixels
