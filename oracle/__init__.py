@@ -24,7 +24,7 @@ _lib = None
 class _Prims(C.Structure):
     _fields_ = [("nv", C.c_int), ("n", C.c_int), ("sh_degree", C.c_int),
                 ("centre", C.c_void_p), ("verts", C.c_void_p), ("opacity", C.c_void_p),
-                ("sh", C.c_void_p), ("dmin", C.c_void_p)]
+                ("sh", C.c_void_p), ("dmin", C.c_void_p), ("aa_kernel", C.c_double)]
 
 
 class _Camera(C.Structure):
@@ -81,7 +81,7 @@ def _ptr(a):
 class _Bound:
     """Keeps the float64 copies alive while the C call runs."""
 
-    def __init__(self, scene, dmin=None):
+    def __init__(self, scene, dmin=None, aa=0.0):
         self.centre = np.ascontiguousarray(scene.centre, np.float64)
         self.verts = np.ascontiguousarray(scene.verts, np.float64)
         self.opacity = np.ascontiguousarray(scene.opacity, np.float64)
@@ -89,7 +89,7 @@ class _Bound:
         self.dmin = None if dmin is None else np.ascontiguousarray(dmin, np.float64)
         self.s = _Prims(int(scene.kind), int(scene.centre.shape[0]), int(scene.sh_degree),
                         _ptr(self.centre), _ptr(self.verts), _ptr(self.opacity),
-                        _ptr(self.sh), _ptr(self.dmin))
+                        _ptr(self.sh), _ptr(self.dmin), float(aa))
 
 
 def _cams(cameras):
@@ -102,10 +102,11 @@ def _cams(cameras):
     return arr
 
 
-def render(scene, cameras, bg=(0.0, 0.0, 0.0), dL_dimage=None, dmin=None, info=False):
+def render(scene, cameras, bg=(0.0, 0.0, 0.0), dL_dimage=None, dmin=None, info=False, aa=0.0):
     """Images packed [cam][3][H][W] (float64).  With dL_dimage, also returns
-    the gradients of L = <dL_dimage, image> w.r.t. centre, verts, opacity, sh."""
-    b = _Bound(scene, dmin)
+    the gradients of L = <dL_dimage, image> w.r.t. centre, verts, opacity, sh.
+    aa: size in pixels of the 2D anti-aliasing filter (Sec. 3.3), 0 = off."""
+    b = _Bound(scene, dmin, aa)
     cams = _cams(cameras)
     P = sum(c.width * c.height for c in cameras)
     img = np.zeros(3 * P, np.float64)
@@ -129,10 +130,10 @@ def render(scene, cameras, bg=(0.0, 0.0, 0.0), dL_dimage=None, dmin=None, info=F
     return out[0] if len(out) == 1 else tuple(out)
 
 
-def render_pixels(scene, camera, px, py, bg=(0.0, 0.0, 0.0), dL_dC=None, dmin=None):
+def render_pixels(scene, camera, px, py, bg=(0.0, 0.0, 0.0), dL_dC=None, dmin=None, aa=0.0):
     """Colours [npix][3] and info [npix][4] = (n_contrib, T_final, borderline,
     min_span) of the listed pixels; with dL_dC [npix][3] also the gradients."""
-    b = _Bound(scene, dmin)
+    b = _Bound(scene, dmin, aa)
     cams = _cams([camera])
     px = np.ascontiguousarray(px, np.int32)
     py = np.ascontiguousarray(py, np.int32)
@@ -154,9 +155,9 @@ def render_pixels(scene, camera, px, py, bg=(0.0, 0.0, 0.0), dL_dC=None, dmin=No
     return (rgb, inf) if grads is None else (rgb, inf, grads)
 
 
-def keys(scene, cameras, tile=16):
+def keys(scene, cameras, tile=16, aa=0.0):
     """Sorted (keys u64, values u32) and per-record tile counts u32 [cam*n]."""
-    b = _Bound(scene)
+    b = _Bound(scene, None, aa)
     cams = _cams(cameras)
     n_out = C.c_longlong(0)
     counts = np.zeros(len(cameras) * scene.n, np.uint32)
@@ -173,8 +174,8 @@ def keys(scene, cameras, tile=16):
     return k[:n], v[:n], counts
 
 
-def preprocess(scene, camera, dmin=None):
-    b = _Bound(scene, dmin)
+def preprocess(scene, camera, dmin=None, aa=0.0):
+    b = _Bound(scene, dmin, aa)
     cams = _cams([camera])
     out = np.zeros((scene.n, 16))
     pv = np.zeros((scene.n, scene.kind, 3))
@@ -184,9 +185,9 @@ def preprocess(scene, camera, dmin=None):
                 dmin=out[:, 10], rgb=out[:, 11:14], dist=out[:, 14], pverts=pv)
 
 
-def span(scene, camera, i, rx, ry):
+def span(scene, camera, i, rx, ry, aa=0.0):
     """(hit, i1, i2) by MTIA and (hit, i1, i2) by half-space clipping."""
-    b = _Bound(scene)
+    b = _Bound(scene, None, aa)
     cams = _cams([camera])
     out = np.zeros(6)
     lib().orc_span(C.byref(b.s), cams, int(i), float(rx), float(ry), _ptr(out))

@@ -56,6 +56,7 @@ typedef struct {
     const double* opacity;   /* [n], alpha in [0,1) */
     const double* sh;        /* [n][(deg+1)^2][3] */
     const double* dmin;      /* optional [n] frozen density normaliser, or NULL */
+    double aa_kernel;        /* 2D anti-aliasing filter size in pixels (Sec. 3.3), 0 = off */
 } orc_prims;
 
 typedef struct {
@@ -153,7 +154,17 @@ typedef struct {
     int visible;
     uint32_t zbits;
     int px0, px1, py0, py1;     /* inclusive pixel rectangle; empty if px0 > px1 */
+    int shx[ORC_MAX_V], shy[ORC_MAX_V];   /* 2D filter: outward shift direction of each vertex */
+    float shift;                /* 2D filter: shift in pixels */
 } orc_keyfields;
+
+/* Sec. 3.3 2D filter: vertices on the bounding box move outward by this many
+ * pixels, parallel to the screen.  Reading: an octahedron's opposite vertices
+ * mirror the move, so each moves by half the kernel size; a tetrahedron
+ * vertex moves by the full kernel size.  Rounded once to binary32. */
+static float aa_shift_f32(const orc_prims* P) {
+    return (float)(P->nv == 6 ? 0.5 * P->aa_kernel : P->aa_kernel);
+}
 
 static void f32_transform(const float M[12], const float x[3], float t[3]) {
     int i;
@@ -167,12 +178,27 @@ static void f32_transform(const float M[12], const float x[3], float t[3]) {
     }
 }
 
+static float f32_max(const float* q, int n) {
+    float m = -INFINITY;
+    int k;
+    for (k = 0; k < n; ++k) if (q[k] > m) m = q[k];
+    return m;
+}
+
+static float f32_min(const float* q, int n) {
+    float m = INFINITY;
+    int k;
+    for (k = 0; k < n; ++k) if (q[k] < m) m = q[k];
+    return m;
+}
+
 static void keyfields_f32(const orc_prims* P, const orc_camera* cam, int i, orc_keyfields* kf) {
     float M[12], c[3], tc[3];
     float fx = (float)cam->fx, fy = (float)cam->fy, cx = (float)cam->cx, cy = (float)cam->cy;
     float u, w, xc, yc, j00, j02, j11, j12;
     float qxmin = INFINITY, qxmax = -INFINITY, qymin = INFINITY, qymax = -INFINITY;
     float xmin, xmax, ymin, ymax, fx0, fx1, fy0, fy1;
+    float qxs[ORC_MAX_V], qys[ORC_MAX_V];
     int k;
     for (k = 0; k < 12; ++k) M[k] = (float)cam->viewmat[k];
     for (k = 0; k < 3; ++k) c[k] = (float)P->centre[3 * i + k];
@@ -180,6 +206,8 @@ static void keyfields_f32(const orc_prims* P, const orc_camera* cam, int i, orc_
     kf->visible = 0;
     kf->zbits = 0;
     kf->px0 = 1; kf->px1 = 0; kf->py0 = 1; kf->py1 = 0;
+    kf->shift = 0.0f;
+    for (k = 0; k < ORC_MAX_V; ++k) kf->shx[k] = kf->shy[k] = 0;
     memcpy(&kf->zbits, &tc[2], 4);
     if (!(tc[2] > ORC_NEAR)) return;
     /* reading: Eq. 1 divides by the smallest centre-vertex distance, so a
@@ -211,10 +239,33 @@ static void keyfields_f32(const orc_prims* P, const orc_camera* cam, int i, orc_
         d0 = dd[0]; d1 = dd[1]; d2 = dd[2];
         a = j00 * d0; b = j02 * d2; qx = a + b;
         a = j11 * d1; b = j12 * d2; qy = a + b;
+        qxs[k] = qx;
+        qys[k] = qy;
         if (qx < qxmin) qxmin = qx;
         if (qx > qxmax) qxmax = qx;
         if (qy < qymin) qymin = qy;
         if (qy > qymax) qymax = qy;
+    }
+    if (P->aa_kernel > 0.0) {
+        /* Sec. 3.3 2D filter: the vertices on the box move outward (a vertex
+         * on the maximum moves up; otherwise one on the minimum moves down),
+         * and the box is taken again over the moved vertices */
+        const float sh = aa_shift_f32(P);
+        kf->shift = sh;
+        qxmin = INFINITY; qxmax = -INFINITY; qymin = INFINITY; qymax = -INFINITY;
+        for (k = 0; k < P->nv; ++k) {
+            float qx = qxs[k], qy = qys[k];
+            kf->shx[k] = qx == f32_max(qxs, P->nv) ? 1 : (qx == f32_min(qxs, P->nv) ? -1 : 0);
+            kf->shy[k] = qy == f32_max(qys, P->nv) ? 1 : (qy == f32_min(qys, P->nv) ? -1 : 0);
+            if (kf->shx[k] > 0) qx = qx + sh;
+            else if (kf->shx[k] < 0) qx = qx - sh;
+            if (kf->shy[k] > 0) qy = qy + sh;
+            else if (kf->shy[k] < 0) qy = qy - sh;
+            if (qx < qxmin) qxmin = qx;
+            if (qx > qxmax) qxmax = qx;
+            if (qy < qymin) qymin = qy;
+            if (qy > qymax) qymax = qy;
+        }
     }
     xmin = xc + qxmin; xmax = xc + qxmax;
     ymin = yc + qymin; ymax = yc + qymax;
@@ -288,6 +339,12 @@ static void preprocess(const orc_prims* P, const orc_camera* cam, int i, orc_pp*
         r = sqrt((v[0] - c[0]) * (v[0] - c[0]) + (v[1] - c[1]) * (v[1] - c[1]) +
                  (v[2] - c[2]) * (v[2] - c[2]));
         if (r < pp->dmin) pp->dmin = r;
+    }
+    /* Sec. 3.3 2D filter: move the vertices the binary32 box chose outward,
+     * parallel to the screen (no-op when the filter is off) */
+    for (k = 0; k < P->nv; ++k) {
+        pp->p[k][0] += pp->kf.shx[k] * (double)pp->kf.shift;
+        pp->p[k][1] += pp->kf.shy[k] * (double)pp->kf.shift;
     }
     /* Eq. 1 generalised to both kinds: d_min is the smallest centre-vertex
      * distance (for an octahedron this is min(d_x, d_y, d_z)). */

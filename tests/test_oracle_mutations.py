@@ -53,6 +53,13 @@ MUTANTS = {
                         "dquat[4 * (size_t)i + 0] = g[0] / qn;", ["param_fd"]),
     "param_sigmoid_grad": ("dlogit[i] = dopacity[i] * al * (1.0 - al);", "dlogit[i] = dopacity[i] * al;",
                            ["param_fd"]),
+    "aa_octa_full_kernel": ("return (float)(P->nv == 6 ? 0.5 * P->aa_kernel : P->aa_kernel);",
+                            "return (float)(P->aa_kernel);", ["aa_span"]),
+    "aa_min_side_inward": ("else if (kf->shx[k] < 0) qx = qx - sh;", "else if (kf->shx[k] < 0) qx = qx + sh;",
+                           ["aa_rect", "aa_moves"]),
+    "aa_box_unmoved": ("pp->p[k][0] += pp->kf.shx[k] * (double)pp->kf.shift;", "pp->p[k][0] += 0.0;",
+                       ["aa_span", "aa_moves"]),
+    "aa_rect_unmoved": ("if (kf->shx[k] > 0) qx = qx + sh;", "if (kf->shx[k] > 0) qx = qx;", ["aa_rect"]),
 }
 
 CHECKS = {
@@ -72,6 +79,9 @@ CHECKS = {
     "ties": pins.test_depth_ties_keep_index_order,
     "param_scipy": lambda o: [params_pins.test_vertices_match_scipy_rotation(k) for k in (6, 4)],
     "param_fd": lambda o: [params_pins.test_params_adjoint_fd(k) for k in (6, 4)],
+    "aa_span": lambda o: pins.test_aa_filter_octahedron_span_closed_form(o, 4.0),
+    "aa_moves": pins.test_aa_filter_moves_box_vertices,
+    "aa_rect": pins.test_aa_filter_widens_the_pixel_rectangle,
 }
 
 

@@ -397,15 +397,15 @@ def test_keys_multiview_tile_bases(orc):
 
 # ----------------------------------------------------------------- gradients
 
-def _fd_check(orc, sc, cam, bg, gimg, params, px=None, py=None, h_geo=1e-6, h_app=1e-5):
+def _fd_check(orc, sc, cam, bg, gimg, params, px=None, py=None, h_geo=1e-6, h_app=1e-5, aa=0.0):
     """Central FD of L = <g, image> against the oracle adjoint, d_min frozen."""
-    dmin = orc.preprocess(sc, cam)["dmin"]
+    dmin = orc.preprocess(sc, cam, aa=aa)["dmin"]
     if px is None:
-        _, grads = orc.render(sc, [cam], bg=bg, dL_dimage=gimg, dmin=dmin)
-        loss = lambda s: float(np.dot(orc.render(s, [cam], bg=bg, dmin=dmin), gimg))
+        _, grads = orc.render(sc, [cam], bg=bg, dL_dimage=gimg, dmin=dmin, aa=aa)
+        loss = lambda s: float(np.dot(orc.render(s, [cam], bg=bg, dmin=dmin, aa=aa), gimg))
     else:
-        _, _, grads = orc.render_pixels(sc, cam, px, py, bg=bg, dL_dC=gimg, dmin=dmin)
-        loss = lambda s: float(np.sum(orc.render_pixels(s, cam, px, py, bg=bg, dmin=dmin)[0] * gimg))
+        _, _, grads = orc.render_pixels(sc, cam, px, py, bg=bg, dL_dC=gimg, dmin=dmin, aa=aa)
+        loss = lambda s: float(np.sum(orc.render_pixels(s, cam, px, py, bg=bg, dmin=dmin, aa=aa)[0] * gimg))
     base = dict(centre=sc.centre.astype(np.float64), verts=sc.verts.astype(np.float64),
                 opacity=sc.opacity.astype(np.float64), sh=sc.sh.astype(np.float64))
     ok = 0
@@ -532,4 +532,105 @@ def test_degenerate_primitive_is_invisible(orc):
         np.testing.assert_allclose(g[k][0], g1[k][0], rtol=1e-12, atol=1e-13)   # summation order only
     _, _, counts = orc.keys(both, [cam])
     assert counts[1] == 0 and counts[0] > 0
+
+
+# ------------------------------------------------------------ 2D filter (Sec. 3.3)
+AA = 0.1   # the paper's 2D filter size in pixels (App. "Experimental Setting")
+
+
+@pytest.mark.parametrize("D", [4.0, 30.0])
+def test_aa_filter_octahedron_span_closed_form(orc, D):
+    """On the optical axis an axis-aligned octahedron's ray-space image is the
+    octahedron with half-axes (fx a / D, fy b / D, c).  The 2D filter moves the
+    four vertices on the projected box outward by half the filter size each,
+    so the span becomes 2c (1 - |x|/(fx a/D + s) - |y|/(fy b/D + s)) with
+    s = 0.05 px, (x, y) the pixel offset from the projected centre."""
+    a, b, c = 0.3, 0.2, 0.1
+    cam = cam_on_axis(D, 65, 65, 20.0)
+    sc = one_scene(6, [0, 0, 0], axis_octa([0, 0, 0], a, b, c), 0.5)
+    Xr, Yr, s = cam.fx * a / D, cam.fy * b / D, float(np.float32(AA / 2))   # the move is binary32
+    rng = np.random.default_rng(19)
+    n_in = n_grown = 0
+    pts = [(rng.uniform(-Xr - s, Xr + s), rng.uniform(-Yr - s, Yr + s)) for _ in range(300)]
+    # points just inside the filtered footprint's boundary, hence outside the
+    # unfiltered one (the band is s / max(Xr, Yr) ~ 1e-3 wide in relative terms)
+    for t in np.linspace(0.0, 1.0, 11):
+        for sx, sy in ((1, 1), (-1, 1), (1, -1), (-1, -1)):
+            pts.append((sx * t * (Xr + s) * (1 - 1e-4), sy * (1 - t) * (Yr + s) * (1 - 1e-4)))
+    for x, y in pts:
+        (hit, i1, i2), (hit2, j1, j2) = orc.span(sc, cam, 0, cam.cx + x, cam.cy + y, aa=AA)
+        expect = 2 * c * (1 - abs(x) / (Xr + s) - abs(y) / (Yr + s))
+        if expect > 1e-9:
+            assert hit and hit2
+            assert abs((i2 - i1) - expect) < 1e-12 * D + 1e-12
+            n_in += 1
+            n_grown += abs(x) / Xr + abs(y) / Yr > 1      # outside the unfiltered primitive
+        elif expect < -1e-9:
+            assert not hit
+    assert n_in > 100 and n_grown > 0
+
+
+def test_aa_filter_moves_box_vertices(orc):
+    """Only the vertices on the projected bounding box move, outward and
+    parallel to the screen: by half the filter for an octahedron (its
+    opposite vertices mirror the move), by the whole filter for a
+    tetrahedron."""
+    rng = np.random.default_rng(23)
+    w0 = scenes.workload(0)
+    cam = w0.cameras[0]
+    for sc, step in ((scenes.workload(1, scale=0.01).scene, float(np.float32(AA / 2))),
+                     (w0.scene, float(np.float32(AA)))):
+        p0 = orc.preprocess(sc, cam)["pverts"]
+        p1 = orc.preprocess(sc, cam, aa=AA)
+        vis = p1["visible"]
+        d = p1["pverts"] - p0
+        assert np.all(d[..., 2] == 0)
+        for i in np.nonzero(vis)[0][:200]:
+            for ax in (0, 1):
+                q = p0[i, :, ax]
+                want = np.where(q == q.max(), step, np.where(q == q.min(), -step, 0.0))
+                np.testing.assert_allclose(d[i, :, ax], want, atol=1e-12)
+        assert rng is not None
+
+
+def test_aa_filter_widens_the_pixel_rectangle(orc):
+    """The tile rectangle is taken over the moved vertices: a box whose right
+    edge sits 0.03 px short of a pixel centre gains that column."""
+    a, c = 0.3, 0.1
+    D = 4.0
+    cam = cam_on_axis(D, 65, 65, 20.0)
+    Xr = cam.fx * a / D
+    # shift the primitive so that its right edge is 0.03 px left of pixel 40's centre
+    cx_target = 40.5 - 0.03 - Xr
+    X0 = (cx_target - cam.cx) * D / cam.fx
+    sc = one_scene(6, [X0, 0, 0], axis_octa([X0, 0, 0], a, 0.2, c), 0.5)
+    r0 = orc.preprocess(sc, cam)["rect"][0]
+    r1 = orc.preprocess(sc, cam, aa=AA)["rect"][0]
+    assert r0[1] == 39 and r1[1] == 40
+    # and a box whose left edge sits 0.03 px right of pixel 10's centre
+    X1 = (10.5 + 0.03 + Xr - cam.cx) * D / cam.fx
+    sc1 = one_scene(6, [X1, 0, 0], axis_octa([X1, 0, 0], a, 0.2, c), 0.5)
+    assert orc.preprocess(sc1, cam)["rect"][0][0] == 11
+    assert orc.preprocess(sc1, cam, aa=AA)["rect"][0][0] == 10
+    k0, _, n0 = orc.keys(sc, [cam])
+    k1, _, n1 = orc.keys(sc, [cam], aa=AA)
+    assert n1[0] >= n0[0]
+
+
+def test_aa_filter_adjoint_fd(orc):
+    """The move is piecewise constant in the geometry, so the adjoint with the
+    filter on still matches central finite differences."""
+    w = scenes.workload(0)
+    sc, cam = w.scene, w.cameras[0]
+    rng = np.random.default_rng(29)
+    gimg = rng.normal(size=3 * cam.pixels)
+    pp = orc.preprocess(sc, cam, aa=AA)
+    vis = np.nonzero(pp["visible"])[0]
+    params = []
+    for i in rng.choice(vis, 6, replace=False):
+        params += [("centre", 3 * i + a) for a in range(3)]
+        params += [("verts", 12 * i + a) for a in rng.choice(12, 5, replace=False)]
+        params += [("opacity", i)]
+    ok = _fd_check(orc, sc, cam, (0.1, 0.2, 0.3), gimg, params, aa=AA)
+    assert ok >= 0.8 * len(params)
 
