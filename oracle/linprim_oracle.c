@@ -476,7 +476,7 @@ static int span_clip(const orc_pp* pp, int nv, double rx, double ry, double* i1,
             for (m = 0; m < 3; ++m) n[m] = -n[m];
         h = n[0] * a[0] + n[1] * a[1] + n[2] * a[2];
         if (n[2] == 0.0) {
-            if (n[0] * rx + n[1] * ry > h) return 0;
+            if (n[0] * rx + n[1] * ry > h) { *i1 = INFINITY; *i2 = -INFINITY; return 0; }
             continue;
         }
         z = (h - n[0] * rx - n[1] * ry) / n[2];
@@ -536,7 +536,8 @@ typedef struct {
     double rgb[3];
     int n_contrib;
     double T_final;
-    int borderline;     /* stop decision within 1e-3 (relative) of the threshold */
+    int borderline;     /* bit 0: stop decision within 1e-3 (relative) of the threshold;
+                           bit 1: the ray grazes a primitive's silhouette */
     double min_span;    /* smallest span among contributors (diagnostic) */
 } orc_pixel;
 
@@ -555,6 +556,21 @@ static int blend_pixel(const orc_prims* P, const orc_view* V, const double bg[3]
         double i1, i2, s, tau, o, Tn;
         int f1 = -1, f2 = -1;
         if (x < pp->kf.px0 || x > pp->kf.px1 || y < pp->kf.py0 || y > pp->kf.py1) continue;
+        /* the colour is continuous across a silhouette but its derivative
+         * with respect to the vertices is not (the span's derivative is
+         * finite just inside and zero outside), so a ray passing within
+         * rounding of a silhouette may take either side in binary32: flag
+         * spans within 1e-5 of the primitive's depth extent of zero */
+        {
+            double c1, c2, zlo = INFINITY, zhi = -INFINITY;
+            int k;
+            for (k = 0; k < P->nv; ++k) {
+                if (pp->p[k][2] < zlo) zlo = pp->p[k][2];
+                if (pp->p[k][2] > zhi) zhi = pp->p[k][2];
+            }
+            span_clip(pp, P->nv, rx, ry, &c1, &c2);
+            if (fabs(c2 - c1) <= 1e-5 * (zhi - zlo)) out->borderline |= 2;
+        }
         if (!span_mtia(pp, P->nv, rx, ry, &i1, &i2, &f1, &f2)) continue;
         s = i2 - i1;
         tau = exp(-pp->sigma * s);
@@ -573,7 +589,7 @@ static int blend_pixel(const orc_prims* P, const orc_view* V, const double bg[3]
          * transmittance factors, some from near-camera primitives whose
          * planes are evaluated far from their anchor, carries relative
          * errors of that order */
-        if (fabs(Tn - ORC_STOP_T) <= 1e-3 * ORC_STOP_T) out->borderline = 1;
+        if (fabs(Tn - ORC_STOP_T) <= 1e-3 * ORC_STOP_T) out->borderline |= 1;
         T = Tn;
         /* reading: the primitive that takes T below 1e-3 is blended, then stop */
         if (T < ORC_STOP_T) break;

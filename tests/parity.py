@@ -7,7 +7,12 @@ Tolerances (from the rasterizer's specification):
     flags as borderline (the transmittance at some step is within 1e-3
     relative of the 1e-3 stop threshold, so binary32 and binary64 may stop at
     different primitives); those may number at most max(2, 1e-4 * pixels);
-  * gradients: per array, ||g - g*|| / ||g*|| <= 1e-3.
+  * gradients: per array, ||g - g*|| / ||g*|| <= 1e-3, for a dL/dimage that
+    is zero at the borderline pixels (both sides get the same dL).  The
+    oracle also flags pixels whose ray passes within rounding of some
+    primitive's silhouette: the colour is continuous there but its
+    derivative with respect to the vertices jumps, so binary32 and binary64
+    may take different sides.
 """
 import numpy as np
 
@@ -66,3 +71,18 @@ def assert_grads_match(gpu, ref, tol=GRAD_REL_L2):
     bad = {k: v for k, v in out.items() if not v <= tol}
     assert not bad, f"gradient relative L2 errors {out}"
     return out
+
+
+def mask_borderline(dL, info, cameras):
+    """dL (packed [cam][3][H][W]) with every channel zeroed at the pixels the
+    oracle flags as borderline (info[:, 2] != 0, pixels in camera order)."""
+    out = np.array(dL, np.float64, copy=True).reshape(-1)
+    off = 0
+    for c in cameras:
+        n = c.width * c.height
+        b = info[off:off + n, 2] > 0
+        seg = out[3 * off:3 * (off + n)].reshape(3, n)
+        seg[:, b] = 0.0
+        off += n
+    return out
+

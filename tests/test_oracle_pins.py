@@ -634,3 +634,18 @@ def test_aa_filter_adjoint_fd(orc):
     ok = _fd_check(orc, sc, cam, (0.1, 0.2, 0.3), gimg, params, aa=AA)
     assert ok >= 0.8 * len(params)
 
+
+def test_silhouette_grazing_pixels_are_flagged(orc):
+    """A ray through a silhouette vertex has a zero span: the oracle flags it
+    (bit 1 of the borderline word), and a ray well inside is not flagged."""
+    D, a = 4.0, 0.3
+    cam = cam_on_axis(D, 65, 65, 20.0)
+    # the +x vertex projects onto the centre of pixel (40, 32)
+    X = (40.5 - cam.cx) * D / cam.fx
+    sc = one_scene(6, [0, 0, 0], axis_octa([0, 0, 0], X, 0.2, 0.1), 0.5)
+    px = np.array([40, 38, 32], np.int32)
+    py = np.array([32, 32, 32], np.int32)
+    _, info = orc.render_pixels(sc, cam, px, py)
+    flags = info[:, 2].astype(int)
+    assert flags[0] & 2 and not flags[1] & 2 and not flags[2] & 2
+
