@@ -147,6 +147,19 @@ void lp_destroy(lp_ctx* ctx);
 lp_status lp_set_tuning(lp_ctx* ctx, const lp_tuning* t);
 lp_status lp_get_tuning(lp_ctx* ctx, lp_tuning* t);
 
+/* The 2D anti-aliasing filter (Sec. 3.3; the paper uses a size of 0.1 px,
+ * App. "Experimental Setting").  kernel_px = 0 turns it off (the default).
+ * When on, every vertex on a primitive's projected (ray-space) bounding box
+ * moves outward parallel to the screen -- in x for the x-extremes, in y for
+ * the y-extremes -- by kernel_px / 2 for an octahedron (its opposite vertices
+ * mirror the move) and kernel_px for a tetrahedron; the face planes, spans
+ * and the tile rectangle then come from the moved vertices, and the backward
+ * treats the move as a constant.  Applies to later forward calls on the
+ * context (a backward uses the setting of its forward).  Errors:
+ * LP_ERR_INVALID unless 0 <= kernel_px <= 16 and finite.                     */
+lp_status lp_set_filter_2d(lp_ctx* ctx, float kernel_px);
+lp_status lp_get_filter_2d(lp_ctx* ctx, float* kernel_px);
+
 /* Pre-size the library-owned workspace.  Needed before a forward/backward
  * pair is captured into a CUDA graph: a captured call cannot read the
  * tile-list length back, so it uses this capacity and latches

@@ -108,6 +108,16 @@ class Rasterizer:
                 setattr(t, k, int(v))
         _native.check(self.ctx, self.lib.lp_set_tuning(self.ctx, C.byref(t)), "lp_set_tuning")
 
+    def set_filter_2d(self, kernel_px: float):
+        """Sec. 3.3 2D anti-aliasing filter size in pixels (0 = off; the paper
+        uses 0.1).  Applies to later forward calls."""
+        _native.check(self.ctx, self.lib.lp_set_filter_2d(self.ctx, float(kernel_px)), "lp_set_filter_2d")
+
+    def filter_2d(self) -> float:
+        v = C.c_float()
+        _native.check(self.ctx, self.lib.lp_get_filter_2d(self.ctx, C.byref(v)), "lp_get_filter_2d")
+        return v.value
+
     def tuning(self) -> dict:
         t = _native.lp_tuning()
         _native.check(self.ctx, self.lib.lp_get_tuning(self.ctx, C.byref(t)), "lp_get_tuning")

@@ -15,7 +15,8 @@ LP_TETRAHEDRON, LP_OCTAHEDRON = 4, 6
 LP_MAX_CAMERAS = 32
 
 # Every symbol include/linprim.h declares.
-EXPORTS = ("lp_create", "lp_destroy", "lp_set_tuning", "lp_get_tuning", "lp_reserve",
+EXPORTS = ("lp_create", "lp_destroy", "lp_set_tuning", "lp_get_tuning", "lp_set_filter_2d", "lp_get_filter_2d",
+           "lp_reserve",
            "lp_render_forward", "lp_render_backward", "lp_sync_status", "lp_get_stats",
            "lp_debug_keys", "lp_debug_counts", "lp_debug_pixel_state", "lp_count_pairs",
            "lp_last_error", "lp_status_string", "lp_set_timing", "lp_stage_times",
@@ -78,6 +79,8 @@ def load(path: str = LIB_PATH):
     L.lp_destroy.restype = None
     L.lp_set_tuning.argtypes = [vp, C.POINTER(lp_tuning)]
     L.lp_get_tuning.argtypes = [vp, C.POINTER(lp_tuning)]
+    L.lp_set_filter_2d.argtypes = [vp, C.c_float]
+    L.lp_get_filter_2d.argtypes = [vp, C.POINTER(C.c_float)]
     L.lp_reserve.argtypes = [vp, ll, ll, ll, ll]
     L.lp_render_forward.argtypes = [vp, C.POINTER(lp_prims), C.POINTER(lp_camera), i,
                                     C.POINTER(C.c_float), vp, vp]

@@ -32,6 +32,7 @@ struct lp_ctx {
     int device = 0;
     int sms = 0;
     lp_tuning tune{16, 64, 0, 0, 4};
+    float aa_kernel = 0.f;      // 2D filter size in pixels (0 = off)
     char err[512] = {0};
 
     DevBuf<float> rec;
@@ -297,6 +298,20 @@ lp_status lp_get_tuning(lp_ctx* ctx, lp_tuning* t) {
     return LP_OK;
 }
 
+lp_status lp_set_filter_2d(lp_ctx* ctx, float kernel_px) {
+    if (!ctx) return LP_ERR_INVALID;
+    if (!(kernel_px >= 0.f && kernel_px <= 16.f))
+        return fail(ctx, LP_ERR_INVALID, "2D filter size %g outside [0, 16] px", (double)kernel_px);
+    ctx->aa_kernel = kernel_px;
+    return LP_OK;
+}
+
+lp_status lp_get_filter_2d(lp_ctx* ctx, float* kernel_px) {
+    if (!ctx || !kernel_px) return LP_ERR_INVALID;
+    *kernel_px = ctx->aa_kernel;
+    return LP_OK;
+}
+
 static lp_status reserve_impl(lp_ctx* ctx, long long records, long long entries, long long pixels,
                               long long tiles, int V) {
     const int rf = V ? rec_floats(V) : lp::Rec<6>::kFloats;
@@ -358,6 +373,9 @@ lp_status lp_render_forward(lp_ctx* ctx, const lp_prims* prims, const lp_camera*
     lp::CamsParam cp;
     long long pixels = 0, tiles = 0;
     LP_TRY(build_cams(ctx, cams, n_cams, ctx->tune.tile, cp, pixels, tiles));
+    // the 2D filter's vertex move, rounded once to binary32 from the size
+    cp.aa_half = (float)(0.5 * (double)ctx->aa_kernel);
+    cp.aa_full = ctx->aa_kernel;
     const long long records = (long long)n_cams * prims->n;
     if (records > 0x7fffffffll) return fail(ctx, LP_ERR_INVALID, "too many records (%lld)", records);
     ctx->have_fwd = false;

@@ -35,6 +35,9 @@ struct CamsParam {
     int total_tiles;
     int tile;
     int total_pixels;
+    // Sec. 3.3 2D filter: outward move of the bounding-box vertices in
+    // pixels, for octahedra (half the filter) and tetrahedra; 0 = off
+    float aa_half, aa_full;
     CamDev cam[kMaxCams];
 };
 

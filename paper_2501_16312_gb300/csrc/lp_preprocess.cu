@@ -129,6 +129,30 @@ __device__ __forceinline__ bool plane_degenerate(const float n[3]) {
     return !(fabsf(n[2]) >= kEdgeOn * (fabsf(n[0]) + fabsf(n[1]))) || n[2] == 0.f;
 }
 
+// Sec. 3.3 2D filter: the vertices on the projected bounding box move
+// outward, parallel to the screen (a vertex on the maximum moves up, else one
+// on the minimum moves down), by half the filter size for an octahedron,
+// whose opposite vertices mirror the move, and the whole size for a
+// tetrahedron.  Decided and applied in binary32 on the key-field values.
+template <int V>
+__device__ __forceinline__ void aa_widen(const CamsParam& cams, float (&q)[V][3]) {
+    const float s = V == 6 ? cams.aa_half : cams.aa_full;
+    if (!(s > 0.f)) return;
+    float xmin = q[0][0], xmax = q[0][0], ymin = q[0][1], ymax = q[0][1];
+#pragma unroll
+    for (int k = 1; k < V; ++k) {
+        xmin = fminf(xmin, q[k][0]); xmax = fmaxf(xmax, q[k][0]);
+        ymin = fminf(ymin, q[k][1]); ymax = fmaxf(ymax, q[k][1]);
+    }
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+        if (q[k][0] == xmax) q[k][0] = __fadd_rn(q[k][0], s);
+        else if (q[k][0] == xmin) q[k][0] = __fsub_rn(q[k][0], s);
+        if (q[k][1] == ymax) q[k][1] = __fadd_rn(q[k][1], s);
+        else if (q[k][1] == ymin) q[k][1] = __fsub_rn(q[k][1], s);
+    }
+}
+
 template <int V, int DEG>
 __global__ void __launch_bounds__(128) k_preprocess(PrimsDev P, CamsParam cams, float* __restrict__ rec,
                                                     uint32_t* __restrict__ counts,
@@ -179,11 +203,15 @@ __global__ void __launch_bounds__(128) k_preprocess(PrimsDev P, CamsParam cams, 
             continue;
         }
         float q[V][3];
-        float qxmin = CUDART_INF_F, qxmax = -CUDART_INF_F, qymin = CUDART_INF_F, qymax = -CUDART_INF_F;
 #pragma unroll
         for (int k = 0; k < V; ++k) {
             float d[3];
             vertex_local(cm, g, v[k], c, q[k], d);
+        }
+        aa_widen<V>(cams, q);
+        float qxmin = CUDART_INF_F, qxmax = -CUDART_INF_F, qymin = CUDART_INF_F, qymax = -CUDART_INF_F;
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
             qxmin = fminf(qxmin, q[k][0]); qxmax = fmaxf(qxmax, q[k][0]);
             qymin = fminf(qymin, q[k][1]); qymax = fmaxf(qymax, q[k][1]);
         }
@@ -331,6 +359,7 @@ __global__ void __launch_bounds__(128) k_chain(PrimsDev P, CamsParam cams,
         float q[V][3], d[V][3];
 #pragma unroll
         for (int k = 0; k < V; ++k) vertex_local(cm, g, v[k], c, q[k], d[k]);
+        aa_widen<V>(cams, q);   // the planes were built on the moved vertices (constant move)
 
         // planes -> local ray-space vertices q, and the projected centre.
         // Faces are visited in a fixed order; the record's permutation gives

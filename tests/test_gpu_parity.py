@@ -8,7 +8,7 @@ import pytest
 import oracle
 import scenes
 from tests.parity import (assert_grads_match, assert_images_match, gpu_forward_backward,
-                          rel_l2)
+                          mask_borderline, rel_l2)
 
 pytestmark = pytest.mark.gpu
 
@@ -60,13 +60,53 @@ def test_tile_lists_bit_exact(rast, case, sort_mode):
 def test_forward_backward_parity(rast, case):
     w = CASES[case]()
     bg = (0.1, 0.2, 0.3)
-    dL = scenes.image_gradient(w, seed=1)
+    ref, info = oracle.render(w.scene, w.cameras, bg=bg, info=True)
+    dL = mask_borderline(scenes.image_gradient(w, seed=1), info, w.cameras)
     img, grads = gpu_forward_backward(rast, w.scene, w.cameras, bg, dL)
-    ref, info, ref_g = oracle.render(w.scene, w.cameras, bg=bg, dL_dimage=dL.astype(np.float64),
-                                     info=True)
+    _, ref_g = oracle.render(w.scene, w.cameras, bg=bg, dL_dimage=dL)
     err = assert_images_match(img, ref, info, w.cameras)
     rel = assert_grads_match(grads, ref_g)
     print(f"{case}: max image err {err:.2e}, grad rel L2 {rel}")
+
+
+AA = float(np.float32(0.1))   # the paper's 2D filter size; both sides get the same binary32 value
+
+
+@pytest.mark.parametrize("sort_mode", [0, 1])
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_filter_2d_parity(rast, case, sort_mode):
+    """Sec. 3.3 2D filter on: tile lists bit-exact, images and gradients
+    within the parity bars, and the filter visibly changes the image."""
+    w = CASES[case]()
+    bg = (0.1, 0.2, 0.3)
+    ref, info = oracle.render(w.scene, w.cameras, bg=bg, info=True, aa=AA)
+    dL = mask_borderline(scenes.image_gradient(w, seed=2), info, w.cameras)
+    rast.set_tuning(sort_mode=sort_mode)
+    rast.set_filter_2d(AA)
+    try:
+        assert rast.filter_2d() == AA
+        img, grads = gpu_forward_backward(rast, w.scene, w.cameras, bg, dL)
+        k, v = rast.debug_keys()
+    finally:
+        rast.set_filter_2d(0.0)
+        rast.set_tuning(sort_mode=0)
+    ko, vo, _ = oracle.keys(w.scene, w.cameras, tile=16, aa=AA)
+    np.testing.assert_array_equal(k, ko)
+    np.testing.assert_array_equal(v, vo)
+    _, ref_g = oracle.render(w.scene, w.cameras, bg=bg, dL_dimage=dL, aa=AA)
+    err = assert_images_match(img, ref, info, w.cameras)
+    rel = assert_grads_match(grads, ref_g)
+    img0, _ = gpu_forward_backward(rast, w.scene, w.cameras, bg)
+    assert np.abs(img - img0).max() > 1e-3
+    print(f"{case}: 2D filter on, max image err {err:.2e}, grad rel L2 {rel}")
+
+
+def test_filter_2d_rejects_bad_sizes(rast):
+    from paper_2501_16312_gb300 import LinPrimError
+    for bad in (-0.1, 17.0, float("nan")):
+        with pytest.raises(LinPrimError):
+            rast.set_filter_2d(bad)
+    assert rast.filter_2d() == 0.0
 
 
 def test_full_size_workload(rast):
@@ -155,9 +195,10 @@ def test_edge_cases(rast, kind):
         sc = scenes.workload(0).scene
         cams = [scenes.make_camera((0, 0, 4), 1, 1, 60)]
     P = sum(c.width * c.height for c in cams)
-    dL = np.random.default_rng(0).normal(size=3 * P).astype(np.float32)
+    ref, info = oracle.render(sc, cams, bg=bg, info=True)
+    dL = mask_borderline(np.random.default_rng(0).normal(size=3 * P), info, cams)
     img, grads = gpu_forward_backward(rast, sc, cams, bg, dL)
-    ref, info, ref_g = oracle.render(sc, cams, bg=bg, dL_dimage=dL.astype(np.float64), info=True)
+    _, ref_g = oracle.render(sc, cams, bg=bg, dL_dimage=dL)
     assert_images_match(img, ref, info, cams)
     if kind in ("empty", "culled"):
         np.testing.assert_array_equal(img.reshape(3, -1), np.repeat(np.array(bg)[:, None], P, 1).astype(np.float32))
