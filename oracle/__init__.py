@@ -65,6 +65,7 @@ def _load(path):
     L.orc_render.argtypes = [dp, dp, C.c_int, dp, dp, dp, dp, dp, dp, dp, dp]
     L.orc_render_pixels.argtypes = [dp, dp, dp, C.c_longlong, dp, dp, dp, dp, dp, dp, dp, dp, dp]
     L.orc_keys.argtypes = [dp, dp, C.c_int, C.c_int, dp, dp, C.c_longlong, dp, dp]
+    L.orc_depth_pixels.argtypes = [dp, dp, C.c_longlong, dp, dp, dp, dp]
     L.orc_preprocess.argtypes = [dp, dp, dp, dp]
     L.orc_span.argtypes = [dp, dp, C.c_int, C.c_double, C.c_double, dp]
     L.orc_mtia.argtypes = [dp, dp, dp, C.c_double, C.c_double, dp, dp]
@@ -153,6 +154,34 @@ def render_pixels(scene, camera, px, py, bg=(0.0, 0.0, 0.0), dL_dC=None, dmin=No
     if rc:
         raise RuntimeError(f"oracle render_pixels failed ({rc})")
     return (rgb, inf) if grads is None else (rgb, inf, grads)
+
+
+def depth_pixels(scene, camera, px, py, aa=0.0):
+    """Depth (App. "Depth and Surface Reconstruction") of the listed pixels:
+    the ray entry depth of the first primitive after which the cumulative
+    opacity exceeds 0.5, 0 where it never does; and each pixel's borderline
+    word (bit 2: the 0.5 crossing is within 1e-4 of 0.5)."""
+    b = _Bound(scene, None, aa)
+    cams = _cams([camera])
+    px = np.ascontiguousarray(px, np.int32)
+    py = np.ascontiguousarray(py, np.int32)
+    d = np.zeros(px.shape[0])
+    f = np.zeros(px.shape[0], np.int32)
+    rc = lib().orc_depth_pixels(C.byref(b.s), cams, px.shape[0], _ptr(px), _ptr(py), _ptr(d), _ptr(f))
+    if rc:
+        raise RuntimeError(f"oracle depth_pixels failed ({rc})")
+    return d, f
+
+
+def depth(scene, cameras, aa=0.0):
+    """Depth maps packed [cam][H][W] and the borderline words, all pixels."""
+    ds, fs = [], []
+    for c in cameras:
+        yy, xx = np.mgrid[0:c.height, 0:c.width]
+        d, f = depth_pixels(scene, c, xx.reshape(-1), yy.reshape(-1), aa=aa)
+        ds.append(d)
+        fs.append(f)
+    return np.concatenate(ds), np.concatenate(fs)
 
 
 def keys(scene, cameras, tile=16, aa=0.0):

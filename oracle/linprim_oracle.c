@@ -537,8 +537,12 @@ typedef struct {
     int n_contrib;
     double T_final;
     int borderline;     /* bit 0: stop decision within 1e-3 (relative) of the threshold;
-                           bit 1: the ray grazes a primitive's silhouette */
+                           bit 1: the ray grazes a primitive's silhouette;
+                           bit 2: the depth decision (T crossing 0.5) within 1e-4 of 0.5 */
     double min_span;    /* smallest span among contributors (diagnostic) */
+    double depth;       /* App. "Depth and Surface Reconstruction": ray entry depth of the
+                           first primitive after which the cumulative opacity exceeds 0.5;
+                           0 when it never does */
 } orc_pixel;
 
 /* Forward for one pixel; fills `list` (capacity cap) with the contributors
@@ -550,6 +554,7 @@ static int blend_pixel(const orc_prims* P, const orc_view* V, const double bg[3]
     int j, nc = 0, ch;
     out->borderline = 0;
     out->min_span = INFINITY;
+    out->depth = 0.0;
     for (j = 0; j < V->n_order; ++j) {
         int i = V->order[j];
         const orc_pp* pp = &V->pp[i];
@@ -590,6 +595,10 @@ static int blend_pixel(const orc_prims* P, const orc_view* V, const double bg[3]
          * planes are evaluated far from their anchor, carries relative
          * errors of that order */
         if (fabs(Tn - ORC_STOP_T) <= 1e-3 * ORC_STOP_T) out->borderline |= 1;
+        /* depth: the first primitive that takes the cumulative opacity 1 - T
+         * above 0.5; reading: its distance is where the ray enters it */
+        if (out->depth == 0.0 && T >= 0.5 && Tn < 0.5) out->depth = i1;
+        if (fabs(Tn - 0.5) <= 1e-4 * 0.5) out->borderline |= 4;
         T = Tn;
         /* reading: the primitive that takes T below 1e-3 is blended, then stop */
         if (T < ORC_STOP_T) break;
@@ -816,6 +825,36 @@ int orc_render(const orc_prims* P, const orc_camera* cams, int ncams, const doub
         off += npix;
     }
     return 0;
+}
+
+/* Depth map of the listed pixels of one camera: depth_out[q] as defined in
+ * orc_pixel, flags_out[q] the pixel's borderline word. */
+int orc_depth_pixels(const orc_prims* P, const orc_camera* cam, long long npix, const int* px,
+                     const int* py, double* depth_out, int* flags_out) {
+    orc_view V;
+    long long q;
+    int rc = 0;
+    if (view_build(P, cam, &V)) return -1;
+#pragma omp parallel
+    {
+        orc_contrib* list = (orc_contrib*)malloc(sizeof(orc_contrib) * ORC_LIST_CAP);
+        if (!list) {
+#pragma omp atomic write
+            rc = -1;
+        } else {
+#pragma omp for schedule(dynamic, 64)
+            for (q = 0; q < npix; ++q) {
+                orc_pixel o;
+                const double bg[3] = {0.0, 0.0, 0.0};
+                blend_pixel(P, &V, bg, px[q], py[q], list, ORC_LIST_CAP, &o);
+                depth_out[q] = o.depth;
+                if (flags_out) flags_out[q] = o.borderline;
+            }
+        }
+        free(list);
+    }
+    view_free(&V);
+    return rc;
 }
 
 /* ----------------------------------------------------------- keys / sorting

@@ -59,6 +59,10 @@ MUTANTS = {
                            ["aa_rect", "aa_moves"]),
     "aa_box_unmoved": ("pp->p[k][0] += pp->kf.shx[k] * (double)pp->kf.shift;", "pp->p[k][0] += 0.0;",
                        ["aa_span", "aa_moves"]),
+    "depth_exit_not_entry": ("if (out->depth == 0.0 && T >= 0.5 && Tn < 0.5) out->depth = i1;",
+                             "if (out->depth == 0.0 && T >= 0.5 && Tn < 0.5) out->depth = i2;", ["depth_surface"]),
+    "depth_threshold": ("if (out->depth == 0.0 && T >= 0.5 && Tn < 0.5) out->depth = i1;",
+                        "if (out->depth == 0.0 && T >= 0.1 && Tn < 0.1) out->depth = i1;", ["depth_layers"]),
     "aa_rect_unmoved": ("if (kf->shx[k] > 0) qx = qx + sh;", "if (kf->shx[k] > 0) qx = qx;", ["aa_rect"]),
 }
 
@@ -79,6 +83,8 @@ CHECKS = {
     "ties": pins.test_depth_ties_keep_index_order,
     "param_scipy": lambda o: [params_pins.test_vertices_match_scipy_rotation(k) for k in (6, 4)],
     "param_fd": lambda o: [params_pins.test_params_adjoint_fd(k) for k in (6, 4)],
+    "depth_surface": pins.test_depth_front_surface_closed_form,
+    "depth_layers": pins.test_depth_two_layers,
     "aa_span": lambda o: pins.test_aa_filter_octahedron_span_closed_form(o, 4.0),
     "aa_moves": pins.test_aa_filter_moves_box_vertices,
     "aa_rect": pins.test_aa_filter_widens_the_pixel_rectangle,

@@ -649,3 +649,46 @@ def test_silhouette_grazing_pixels_are_flagged(orc):
     flags = info[:, 2].astype(int)
     assert flags[0] & 2 and not flags[1] & 2 and not flags[2] & 2
 
+
+# --------------------------------------------------- depth (App. "Depth and Surface Reconstruction")
+def test_depth_front_surface_closed_form(orc):
+    """An opaque-enough axis-aligned octahedron on the optical axis: the depth
+    of pixel offset (x, y) is where the ray enters its front surface,
+    D - c (1 - |x|/X - |y|/Y) with (X, Y) its projected half-axes; pixels whose
+    span is too short to reach opacity 0.5 get no depth (0)."""
+    D, a, b, c = 4.0, 0.3, 0.2, 0.1
+    cam = cam_on_axis(D, 65, 65, 20.0)
+    sc = one_scene(6, [0, 0, 0], axis_octa([0, 0, 0], a, b, c), 0.95)
+    X, Y = cam.fx * a / D, cam.fy * b / D
+    yy, xx = np.mgrid[0:65, 0:65]
+    px, py = xx.reshape(-1).astype(np.int32), yy.reshape(-1).astype(np.int32)
+    d, f = orc.depth_pixels(sc, cam, px, py)
+    x = px + 0.5 - cam.cx
+    y = py + 0.5 - cam.cy
+    u = 1 - np.abs(x) / X - np.abs(y) / Y
+    pp = orc.preprocess(sc, cam)
+    sigma = pp["sigma"][0]
+    reach = 1 - np.exp(-sigma * 2 * c * np.clip(u, 0, None)) > 0.5     # opacity of the full span
+    ok = (f == 0)
+    np.testing.assert_allclose(d[reach & ok], (D - c * u)[reach & ok], atol=1e-12)
+    assert np.all(d[~reach & ok] == 0)
+    assert reach.sum() > 100 and (~reach & (u > 0)).sum() > 10
+
+
+def test_depth_two_layers(orc):
+    """A front layer of opacity 0.3 leaves the depth to the layer behind it;
+    one of opacity 0.7 takes it; the background never does."""
+    cam = cam_on_axis(4.0, 33, 33, 40.0)
+    front = axis_octa([0, 0, 1.0], 1.0, 1.0, 0.05)
+    back = axis_octa([0, 0, -1.0], 1.0, 1.0, 0.05)
+    for a_front, want in ((0.30, 5.0 - 0.05), (0.70, 3.0 - 0.05)):
+        sc = one_scene(6, [[0, 0, 1.0], [0, 0, -1.0]], np.stack([front, back]), [a_front, 0.9])
+        sig = orc.preprocess(sc, cam)["sigma"]
+        # through the centres each layer's span is its full thickness 2c: opacity 0.99 alpha
+        assert abs((1 - np.exp(-sig[0] * 0.1)) - 0.99 * a_front) < 1e-12
+        d, f = orc.depth_pixels(sc, cam, np.array([16], np.int32), np.array([16], np.int32))
+        assert f[0] == 0 and abs(d[0] - want) < 1e-12, (a_front, d[0])
+    empty = one_scene(6, [0, 0, 0], axis_octa([0, 0, 0], 0.1, 0.1, 0.1), 0.9)
+    d, _ = orc.depth_pixels(empty, cam, np.array([0], np.int32), np.array([0], np.int32))
+    assert d[0] == 0.0
+
