@@ -147,6 +147,17 @@ void lp_destroy(lp_ctx* ctx);
 lp_status lp_set_tuning(lp_ctx* ctx, const lp_tuning* t);
 lp_status lp_get_tuning(lp_ctx* ctx, lp_tuning* t);
 
+/* Depth map of the last forward on this context (App. "Depth and Surface
+ * Reconstruction"): for every pixel, the distance along the ray (ray-space
+ * depth, world units) at which it enters the first primitive after which the
+ * cumulative opacity exceeds 0.5; 0 where the opacity never exceeds 0.5.
+ * depth: device, float, packed [cam][H][W] like one channel of the images,
+ * caller-owned, overwritten.  Runs a front-to-back pass over the forward's
+ * tile lists that stops each pixel at opacity 0.5; it leaves the forward's
+ * state (and so a later backward) untouched.  Asynchronous on `stream`.
+ * Errors: LP_ERR_STATE without a forward, LP_ERR_INVALID for NULL.         */
+lp_status lp_render_depth(lp_ctx* ctx, float* depth, void* stream);
+
 /* The 2D anti-aliasing filter (Sec. 3.3; the paper uses a size of 0.1 px,
  * App. "Experimental Setting").  kernel_px = 0 turns it off (the default).
  * When on, every vertex on a primitive's projected (ray-space) bounding box

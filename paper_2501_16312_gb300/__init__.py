@@ -157,6 +157,20 @@ class Rasterizer:
         _native.check(self.ctx, st, "lp_render_backward")
         return grads
 
+    def depth(self, out=None):
+        """Depth map of the last forward (App. "Depth and Surface
+        Reconstruction"): per pixel, packed [cam][H][W], the distance at which
+        the ray enters the first primitive taking the cumulative opacity above
+        0.5; 0 where none does."""
+        torch = _torch()
+        if self._fwd is None:
+            raise LinPrimError(_native.LP_ERR_STATE, "depth without forward")
+        P = sum(c.width * c.height for c in self._fwd[1])
+        if out is None:
+            out = torch.empty(P, dtype=torch.float32, device=self.device)
+        _native.check(self.ctx, self.lib.lp_render_depth(self.ctx, _fptr(out), self._stream()), "lp_render_depth")
+        return out
+
     def sync_status(self):
         _native.check(self.ctx, self.lib.lp_sync_status(self.ctx, self._stream()), "lp_sync_status")
 

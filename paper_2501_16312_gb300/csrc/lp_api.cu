@@ -678,6 +678,29 @@ lp_status lp_debug_pixel_state(lp_ctx* ctx, unsigned int* last, float* T_last, l
     return LP_OK;
 }
 
+lp_status lp_render_depth(lp_ctx* ctx, float* depth, void* stream) {
+    if (!ctx) return LP_ERR_INVALID;
+    if (!depth) return fail(ctx, LP_ERR_INVALID, "depth is NULL");
+    if (!ctx->have_fwd) return fail(ctx, LP_ERR_STATE, "no forward");
+    LP_CUDA(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    lp::BlendArgs a{};
+    a.grid = blend_grid(ctx, ctx->prims.kind, true, ctx->tiles);
+    a.rec = ctx->rec.p;
+    a.vals = ctx->result_in_1 ? ctx->vals1.p : ctx->vals0.p;
+    a.ranges = ctx->ranges.p;
+    a.cams = &ctx->cams;
+    a.tile_counter = ctx->d_tile_counter;
+    a.pair_counts = ctx->d_pairs;
+    a.depth = depth;
+    LP_CUDA(cudaMemsetAsync(ctx->d_tile_counter, 0, sizeof(int), st));
+    if (a.grid > 0)
+        LP_CUDA(lp::launch_blend_fwd(ctx->prims.kind, ctx->tune.batch, ctx->tune.pixels_per_thread, a, st));
+    else if (ctx->pixels > 0)
+        LP_CUDA(cudaMemsetAsync(depth, 0, (size_t)ctx->pixels * sizeof(float), st));
+    return LP_OK;
+}
+
 lp_status lp_count_pairs(lp_ctx* ctx, long long* counts) {
     if (!ctx || !counts) return LP_ERR_INVALID;
     if (!ctx->have_fwd) return fail(ctx, LP_ERR_STATE, "no forward");

@@ -9,18 +9,26 @@
 // after blending the primitive that crossed it.  A tile stops when all of its
 // pixels have.  Per pixel the kernel keeps, for the backward, the number of
 // list entries up to the last contributor and the transmittance before it.
+//
+// MODE 1 also counts (pixel, primitive) pairs.  MODE 2 is the depth pass
+// (App. "Depth and Surface Reconstruction"): the same walk, stopping each
+// pixel at the first primitive that takes the cumulative opacity above 0.5
+// and writing the depth where the ray enters that primitive (0 if none).
 #include "lp_blend.cuh"
 
 namespace lp {
 
 namespace {
 
-template <int V, int BATCH, int PIX, bool COUNT>
+template <int V, int BATCH, int PIX, int MODE>
 __global__ void __launch_bounds__(kTilePixels / PIX) k_blend_fwd(
     const float* __restrict__ rec, const uint32_t* __restrict__ vals, const uint2* __restrict__ ranges,
     CamsParam cams, float bg0, float bg1, float bg2, float* __restrict__ image,
     uint32_t* __restrict__ last_out, float* __restrict__ tl_out, int* __restrict__ tile_counter,
-    unsigned long long* __restrict__ pair_counts) {
+    unsigned long long* __restrict__ pair_counts, float* __restrict__ depth_out) {
+    constexpr bool COUNT = MODE == 1;
+    constexpr bool DEPTH = MODE == 2;
+    constexpr float kStop = DEPTH ? 0.5f : kStopT;
     constexpr int NT = kTilePixels / PIX;
     constexpr int RW = kTile / PIX;
     __shared__ Staged<V> sm[BATCH];
@@ -40,12 +48,14 @@ __global__ void __launch_bounds__(kTilePixels / PIX) k_blend_fwd(
         float T[PIX], c0[PIX], c1[PIX], c2[PIX], tl[PIX];
         uint32_t last[PIX];
         uint32_t ce[PIX], cl[PIX];   // counting only: evaluations so far / at the last contributor
+        float dep[PIX];              // depth pass only
         bool done[PIX];
         bool tdone = true;
 #pragma unroll
         for (int i = 0; i < PIX; ++i) {
             T[i] = 1.f; c0[i] = c1[i] = c2[i] = 0.f; tl[i] = 1.f; last[i] = 0;
             ce[i] = cl[i] = 0;
+            dep[i] = 0.f;
             done[i] = !(tg.tx0 + lx0 + i < tg.width && py < tg.height);
             tdone &= done[i];
         }
@@ -78,7 +88,15 @@ __global__ void __launch_bounds__(kTilePixels / PIX) k_blend_fwd(
                             tl[i] = T[i];
                             T[i] *= tau;
                             last[i] = (uint32_t)(b0 + j + 1);
-                            done[i] = T[i] < kStopT;
+                            done[i] = T[i] < kStop;
+                            if (DEPTH && done[i]) {
+                                // entry depth: centre depth + max over the entry faces
+                                float e = -CUDART_INF_F;
+                                for (int f = 0; f < p.nf; ++f)
+                                    e = fmaxf(e, __fmaf_rn(p.pl[f].x, (float)(lx0 + i),
+                                                           __fmaf_rn(p.pl[f].y, (float)ly, p.pl[f].z)));
+                                dep[i] = __fadd_rn(p.pl[0].w, e);
+                            }
                         }
                         tdone &= done[i];
                     }
@@ -95,6 +113,10 @@ __global__ void __launch_bounds__(kTilePixels / PIX) k_blend_fwd(
 #pragma unroll
         for (int i = 0; i < PIX; ++i) {
             const int px = tg.tx0 + lx0 + i;
+            if (DEPTH) {
+                if (px < tg.width && py < tg.height) depth_out[tg.pix_base + py * tg.width + px] = dep[i];
+                continue;
+            }
             if (px < tg.width && py < tg.height) {
                 const int idx = py * tg.width + px;
                 img[idx] = fmaf(T[i], bg0, c0[i]);
@@ -127,21 +149,25 @@ __global__ void __launch_bounds__(kTilePixels / PIX) k_blend_fwd(
 template <int V, int BATCH, int PIX>
 cudaError_t fwd_t(const BlendArgs& a, cudaStream_t st) {
     constexpr int NT = kTilePixels / PIX;
-    if (a.count)
-        k_blend_fwd<V, BATCH, PIX, true><<<a.grid, NT, 0, st>>>(
+    if (a.depth)
+        k_blend_fwd<V, BATCH, PIX, 2><<<a.grid, NT, 0, st>>>(
             a.rec, a.vals, a.ranges, *a.cams, a.bg[0], a.bg[1], a.bg[2], a.image, a.last, a.tl,
-            a.tile_counter, a.pair_counts);
+            a.tile_counter, a.pair_counts, a.depth);
+    else if (a.count)
+        k_blend_fwd<V, BATCH, PIX, 1><<<a.grid, NT, 0, st>>>(
+            a.rec, a.vals, a.ranges, *a.cams, a.bg[0], a.bg[1], a.bg[2], a.image, a.last, a.tl,
+            a.tile_counter, a.pair_counts, nullptr);
     else
-        k_blend_fwd<V, BATCH, PIX, false><<<a.grid, NT, 0, st>>>(
+        k_blend_fwd<V, BATCH, PIX, 0><<<a.grid, NT, 0, st>>>(
             a.rec, a.vals, a.ranges, *a.cams, a.bg[0], a.bg[1], a.bg[2], a.image, a.last, a.tl,
-            a.tile_counter, a.pair_counts);
+            a.tile_counter, a.pair_counts, nullptr);
     return cudaGetLastError();
 }
 
 template <int V, int BATCH, int PIX>
 int fwd_occ() {
     int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_blend_fwd<V, BATCH, PIX, false>,
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_blend_fwd<V, BATCH, PIX, 0>,
                                                   kTilePixels / PIX, 0);
     return nb;
 }

@@ -223,6 +223,8 @@ __device__ __forceinline__ float min3f(float a, float b, float c) {
 // + e'.  Planes are float4 (a, b, e', 0) for 128-bit shared loads.  The
 // forward and backward blends both stage through stage_record() and evaluate
 // through the same span routines, so they compute bit-identical spans.
+// pl[0].w carries the ray-space depth of the centre, to which the planes'
+// depths are relative (used by the depth pass only).
 template <int V> struct alignas(16) Staged {
     static constexpr int F = Kind<V>::F;
     float4 pl[F];
@@ -250,6 +252,7 @@ __device__ __forceinline__ void stage_record(const float* __restrict__ rec, int 
         const float a = buf[8 + 3 * f], b = buf[9 + 3 * f], e = buf[10 + 3 * f];
         s.pl[f] = make_float4(a, b, __fmaf_rn(a, dx0, __fmaf_rn(b, dy0, e)), 0.f);
     }
+    s.pl[0].w = buf[7];
     s.sigma = buf[2];
     s.r = buf[4]; s.g = buf[5]; s.b = buf[6];
     s.dx0 = dx0; s.dy0 = dy0;

@@ -69,6 +69,7 @@ struct BlendArgs {
     int* tile_counter;
     unsigned long long* pair_counts;
     bool count;
+    float* depth;          // depth pass output (forward kernel in depth mode when non-null)
 };
 
 cudaError_t launch_blend_fwd(int V, int batch, int pix, const BlendArgs& a, cudaStream_t st);

@@ -291,7 +291,8 @@ __global__ void __launch_bounds__(128) k_preprocess(PrimsDev P, CamsParam cams, 
         }
         out[0] = __int_as_float(g.X0); out[1] = __int_as_float(g.Y0); out[2] = sigma;
         out[3] = __uint_as_float(meta);
-        out[4] = rgb[0]; out[5] = rgb[1]; out[6] = rgb[2]; out[7] = 0.f;
+        out[4] = rgb[0]; out[5] = rgb[1]; out[6] = rgb[2];
+        out[7] = g.len;   // ray-space depth of the centre (the planes are relative to it)
         float4* dst = reinterpret_cast<float4*>(rec + r * Rec<V>::kFloats);
 #pragma unroll
         for (int k = 0; k < Rec<V>::kVec4; ++k)

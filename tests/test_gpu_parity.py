@@ -109,12 +109,40 @@ def test_filter_2d_rejects_bad_sizes(rast):
     assert rast.filter_2d() == 0.0
 
 
+def _depth_match(d, do, flags, tol=2e-5):
+    ok = flags == 0
+    assert np.array_equal(d[ok] == 0, do[ok] == 0), "pixels with / without depth differ"
+    np.testing.assert_allclose(d[ok], do[ok], rtol=tol, atol=tol)
+    return int(ok.sum()), int((do[ok] > 0).sum())
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_depth_parity(rast, case):
+    """App. "Depth and Surface Reconstruction": depth of the first primitive
+    taking the cumulative opacity above 0.5, against the oracle on every
+    pixel that is not borderline."""
+    w = CASES[case]()
+    dL = scenes.image_gradient(w, seed=3)
+    _, g_ref = gpu_forward_backward(rast, w.scene, w.cameras, (0, 0, 0), dL)
+    d = rast.depth().cpu().numpy().astype(np.float64)
+    # the depth pass leaves the forward state alone: a backward now is unchanged
+    import torch
+    g2 = rast.backward(torch.as_tensor(dL, device="cuda:0"))
+    for k in g_ref:
+        assert rel_l2(g2[k].cpu().numpy(), g_ref[k]) <= 1e-5, k   # float atomics reorder
+    do, flags = oracle.depth(w.scene, w.cameras)
+    n_ok, n_valid = _depth_match(d, do, flags)
+    assert n_valid > 0
+    print(f"{case}: depth on {n_ok} pixels ({n_valid} with a depth)")
+
+
 def test_full_size_workload(rast):
     """The 500k-octahedron, 8 x 1264x832 workload in the launch configuration
     the benchmark times: every pixel of camera 0 and sampled pixels of camera 5
     against the oracle."""
     w = scenes.workload(2)
     img, _ = gpu_forward_backward(rast, w.scene, w.cameras, (0, 0, 0))
+    depth = rast.depth().cpu().numpy().astype(np.float64)
     rng = np.random.default_rng(7)
     off = 0
     for ci, cam in enumerate(w.cameras):
@@ -128,6 +156,10 @@ def test_full_size_workload(rast):
             clean = info[:, 2] == 0
             assert err[clean].max() <= 1e-4, err[clean].max()
             assert (err[~clean] > 1e-4).sum() <= max(2, 1e-4 * len(q))
+            s = q[:4000] if ci == 0 else q
+            do, flags = oracle.depth_pixels(w.scene, cam, (s % cam.width).astype(np.int32),
+                                            (s // cam.width).astype(np.int32))
+            _depth_match(depth[off:off + n][s], do, flags)
         off += n
 
 
