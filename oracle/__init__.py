@@ -24,7 +24,7 @@ _lib = None
 class _Prims(C.Structure):
     _fields_ = [("nv", C.c_int), ("n", C.c_int), ("sh_degree", C.c_int),
                 ("centre", C.c_void_p), ("verts", C.c_void_p), ("opacity", C.c_void_p),
-                ("sh", C.c_void_p), ("dmin", C.c_void_p), ("aa_kernel", C.c_double)]
+                ("sh", C.c_void_p), ("dmin", C.c_void_p), ("aa_kernel", C.c_double), ("exact", C.c_int)]
 
 
 class _Camera(C.Structure):
@@ -82,7 +82,7 @@ def _ptr(a):
 class _Bound:
     """Keeps the float64 copies alive while the C call runs."""
 
-    def __init__(self, scene, dmin=None, aa=0.0):
+    def __init__(self, scene, dmin=None, aa=0.0, exact=False):
         self.centre = np.ascontiguousarray(scene.centre, np.float64)
         self.verts = np.ascontiguousarray(scene.verts, np.float64)
         self.opacity = np.ascontiguousarray(scene.opacity, np.float64)
@@ -90,7 +90,7 @@ class _Bound:
         self.dmin = None if dmin is None else np.ascontiguousarray(dmin, np.float64)
         self.s = _Prims(int(scene.kind), int(scene.centre.shape[0]), int(scene.sh_degree),
                         _ptr(self.centre), _ptr(self.verts), _ptr(self.opacity),
-                        _ptr(self.sh), _ptr(self.dmin), float(aa))
+                        _ptr(self.sh), _ptr(self.dmin), float(aa), int(bool(exact)))
 
 
 def _cams(cameras):
@@ -103,11 +103,13 @@ def _cams(cameras):
     return arr
 
 
-def render(scene, cameras, bg=(0.0, 0.0, 0.0), dL_dimage=None, dmin=None, info=False, aa=0.0):
+def render(scene, cameras, bg=(0.0, 0.0, 0.0), dL_dimage=None, dmin=None, info=False, aa=0.0, exact=False):
     """Images packed [cam][3][H][W] (float64).  With dL_dimage, also returns
     the gradients of L = <dL_dimage, image> w.r.t. centre, verts, opacity, sh.
-    aa: size in pixels of the 2D anti-aliasing filter (Sec. 3.3), 0 = off."""
-    b = _Bound(scene, dmin, aa)
+    aa: size in pixels of the 2D anti-aliasing filter (Sec. 3.3), 0 = off.
+    exact: spans along the true perspective ray instead of the ray-space
+    approximation (App. "Ray Space Approximation"; the filter is then off)."""
+    b = _Bound(scene, dmin, aa, exact)
     cams = _cams(cameras)
     P = sum(c.width * c.height for c in cameras)
     img = np.zeros(3 * P, np.float64)
@@ -131,10 +133,10 @@ def render(scene, cameras, bg=(0.0, 0.0, 0.0), dL_dimage=None, dmin=None, info=F
     return out[0] if len(out) == 1 else tuple(out)
 
 
-def render_pixels(scene, camera, px, py, bg=(0.0, 0.0, 0.0), dL_dC=None, dmin=None, aa=0.0):
+def render_pixels(scene, camera, px, py, bg=(0.0, 0.0, 0.0), dL_dC=None, dmin=None, aa=0.0, exact=False):
     """Colours [npix][3] and info [npix][4] = (n_contrib, T_final, borderline,
     min_span) of the listed pixels; with dL_dC [npix][3] also the gradients."""
-    b = _Bound(scene, dmin, aa)
+    b = _Bound(scene, dmin, aa, exact)
     cams = _cams([camera])
     px = np.ascontiguousarray(px, np.int32)
     py = np.ascontiguousarray(py, np.int32)
@@ -156,12 +158,12 @@ def render_pixels(scene, camera, px, py, bg=(0.0, 0.0, 0.0), dL_dC=None, dmin=No
     return (rgb, inf) if grads is None else (rgb, inf, grads)
 
 
-def depth_pixels(scene, camera, px, py, aa=0.0):
+def depth_pixels(scene, camera, px, py, aa=0.0, exact=False):
     """Depth (App. "Depth and Surface Reconstruction") of the listed pixels:
     the ray entry depth of the first primitive after which the cumulative
     opacity exceeds 0.5, 0 where it never does; and each pixel's borderline
     word (bit 2: the 0.5 crossing is within 1e-4 of 0.5)."""
-    b = _Bound(scene, None, aa)
+    b = _Bound(scene, None, aa, exact)
     cams = _cams([camera])
     px = np.ascontiguousarray(px, np.int32)
     py = np.ascontiguousarray(py, np.int32)
@@ -173,20 +175,20 @@ def depth_pixels(scene, camera, px, py, aa=0.0):
     return d, f
 
 
-def depth(scene, cameras, aa=0.0):
+def depth(scene, cameras, aa=0.0, exact=False):
     """Depth maps packed [cam][H][W] and the borderline words, all pixels."""
     ds, fs = [], []
     for c in cameras:
         yy, xx = np.mgrid[0:c.height, 0:c.width]
-        d, f = depth_pixels(scene, c, xx.reshape(-1), yy.reshape(-1), aa=aa)
+        d, f = depth_pixels(scene, c, xx.reshape(-1), yy.reshape(-1), aa=aa, exact=exact)
         ds.append(d)
         fs.append(f)
     return np.concatenate(ds), np.concatenate(fs)
 
 
-def keys(scene, cameras, tile=16, aa=0.0):
+def keys(scene, cameras, tile=16, aa=0.0, exact=False):
     """Sorted (keys u64, values u32) and per-record tile counts u32 [cam*n]."""
-    b = _Bound(scene, None, aa)
+    b = _Bound(scene, None, aa, exact)
     cams = _cams(cameras)
     n_out = C.c_longlong(0)
     counts = np.zeros(len(cameras) * scene.n, np.uint32)
@@ -203,8 +205,8 @@ def keys(scene, cameras, tile=16, aa=0.0):
     return k[:n], v[:n], counts
 
 
-def preprocess(scene, camera, dmin=None, aa=0.0):
-    b = _Bound(scene, dmin, aa)
+def preprocess(scene, camera, dmin=None, aa=0.0, exact=False):
+    b = _Bound(scene, dmin, aa, exact)
     cams = _cams([camera])
     out = np.zeros((scene.n, 16))
     pv = np.zeros((scene.n, scene.kind, 3))
@@ -214,9 +216,9 @@ def preprocess(scene, camera, dmin=None, aa=0.0):
                 dmin=out[:, 10], rgb=out[:, 11:14], dist=out[:, 14], pverts=pv)
 
 
-def span(scene, camera, i, rx, ry, aa=0.0):
+def span(scene, camera, i, rx, ry, aa=0.0, exact=False):
     """(hit, i1, i2) by MTIA and (hit, i1, i2) by half-space clipping."""
-    b = _Bound(scene, None, aa)
+    b = _Bound(scene, None, aa, exact)
     cams = _cams([camera])
     out = np.zeros(6)
     lib().orc_span(C.byref(b.s), cams, int(i), float(rx), float(ry), _ptr(out))

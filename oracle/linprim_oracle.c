@@ -57,6 +57,7 @@ typedef struct {
     const double* sh;        /* [n][(deg+1)^2][3] */
     const double* dmin;      /* optional [n] frozen density normaliser, or NULL */
     double aa_kernel;        /* 2D anti-aliasing filter size in pixels (Sec. 3.3), 0 = off */
+    int exact;               /* 1: no ray-space approximation (App. "Ray Space Approximation") */
 } orc_prims;
 
 typedef struct {
@@ -237,8 +238,18 @@ static void keyfields_f32(const orc_prims* P, const orc_camera* cam, int i, orc_
             dd[m] = s + r2;
         }
         d0 = dd[0]; d1 = dd[1]; d2 = dd[2];
+        if (P->exact) {
+            /* exact mode: the vertex's camera-space position tc + d and its
+             * perspective projection, as offsets from the projected centre */
+            float X = tc[0] + d0, Y = tc[1] + d1, Z = tc[2] + d2, uu, ww;
+            if (!(Z > ORC_NEAR)) { kf->visible = 0; return; }   /* reading: every vertex in front */
+            uu = X / Z; ww = Y / Z;
+            qx = fx * uu; qx = qx + cx; qx = qx - xc;
+            qy = fy * ww; qy = qy + cy; qy = qy - yc;
+        } else {
         a = j00 * d0; b = j02 * d2; qx = a + b;
         a = j11 * d1; b = j12 * d2; qy = a + b;
+        }
         qxs[k] = qx;
         qys[k] = qy;
         if (qx < qxmin) qxmin = qx;
@@ -246,7 +257,7 @@ static void keyfields_f32(const orc_prims* P, const orc_camera* cam, int i, orc_
         if (qy < qymin) qymin = qy;
         if (qy > qymax) qymax = qy;
     }
-    if (P->aa_kernel > 0.0) {
+    if (P->aa_kernel > 0.0 && !P->exact) {
         /* Sec. 3.3 2D filter: the vertices on the box move outward (a vertex
          * on the maximum moves up; otherwise one on the minimum moves down),
          * and the box is taken again over the moved vertices */
@@ -289,6 +300,8 @@ typedef struct {
     double p[ORC_MAX_V][3];     /* ray-space vertices phi(tc) + J (tv - tc) */
     double dmin, sigma;
     double dir[3], dist;        /* unit world view direction, |c - campos| */
+    int exact;                  /* spans by the true perspective ray (p = tv) */
+    double fx, fy, cx, cy;      /* intrinsics, for the exact ray direction */
     double rgb_raw[3], rgb[3];
 } orc_pp;
 
@@ -339,6 +352,14 @@ static void preprocess(const orc_prims* P, const orc_camera* cam, int i, orc_pp*
         r = sqrt((v[0] - c[0]) * (v[0] - c[0]) + (v[1] - c[1]) * (v[1] - c[1]) +
                  (v[2] - c[2]) * (v[2] - c[2]));
         if (r < pp->dmin) pp->dmin = r;
+    }
+    pp->exact = P->exact;
+    pp->fx = cam->fx; pp->fy = cam->fy; pp->cx = cam->cx; pp->cy = cam->cy;
+    if (P->exact) {
+        /* no ray-space map: the primitive stays in camera space */
+        for (k = 0; k < P->nv; ++k)
+            for (m = 0; m < 3; ++m) pp->p[k][m] = pp->tv[k][m];
+        for (m = 0; m < 3; ++m) pp->pc[m] = pp->tc[m];
     }
     /* Sec. 3.3 2D filter: move the vertices the binary32 box chose outward,
      * parallel to the screen (no-op when the filter is off) */
@@ -436,17 +457,78 @@ int orc_mtia(const double* p0, const double* p1, const double* p2, double rx, do
     return hit;
 }
 
+/* Exact mode (App. "Ray Space Approximation", the variant without it): the
+ * pixel ray from the camera centre (the camera-space origin) along
+ * d = ((rx - cx)/fx, (ry - cy)/fy, 1), intersected with the camera-space
+ * triangle by Moller-Trumbore; lam is the ray parameter (the hit is lam d). */
+static int mtia_ray(const double p0[3], const double p1[3], const double p2[3], const double d[3],
+                    double* lam) {
+    double e1[3], e2[3], pv[3], tv[3], qv[3], det, u, v;
+    int m;
+    for (m = 0; m < 3; ++m) { e1[m] = p1[m] - p0[m]; e2[m] = p2[m] - p0[m]; tv[m] = -p0[m]; }
+    pv[0] = d[1] * e2[2] - d[2] * e2[1];
+    pv[1] = d[2] * e2[0] - d[0] * e2[2];
+    pv[2] = d[0] * e2[1] - d[1] * e2[0];
+    det = e1[0] * pv[0] + e1[1] * pv[1] + e1[2] * pv[2];
+    if (det == 0.0) return 0;
+    u = (tv[0] * pv[0] + tv[1] * pv[1] + tv[2] * pv[2]) / det;
+    qv[0] = tv[1] * e1[2] - tv[2] * e1[1];
+    qv[1] = tv[2] * e1[0] - tv[0] * e1[2];
+    qv[2] = tv[0] * e1[1] - tv[1] * e1[0];
+    v = (d[0] * qv[0] + d[1] * qv[1] + d[2] * qv[2]) / det;
+    *lam = (e2[0] * qv[0] + e2[1] * qv[1] + e2[2] * qv[2]) / det;
+    return u >= 0.0 && v >= 0.0 && u + v <= 1.0 && *lam > 0.0;
+}
+
+/* d lam / d (p0, p1, p2) of the ray's hit with the triangle's plane: with
+ * n = (p1 - p0) x (p2 - p0), lam = (p0 . n) / (d . n), so
+ * d lam = [dp0 . n + (p0 - lam d) . dn] / (d . n), and with a = (p0 - lam d)/(d . n),
+ * a . dn = de1 . (e2 x a) + de2 . (a x e1). */
+static void mtia_ray_grad(const double p0[3], const double p1[3], const double p2[3], const double d[3],
+                          double lam, double g[3][3]) {
+    double e1[3], e2[3], n[3], a[3], dn;
+    int m;
+    for (m = 0; m < 3; ++m) { e1[m] = p1[m] - p0[m]; e2[m] = p2[m] - p0[m]; }
+    n[0] = e1[1] * e2[2] - e1[2] * e2[1];
+    n[1] = e1[2] * e2[0] - e1[0] * e2[2];
+    n[2] = e1[0] * e2[1] - e1[1] * e2[0];
+    dn = d[0] * n[0] + d[1] * n[1] + d[2] * n[2];
+    for (m = 0; m < 3; ++m) a[m] = (p0[m] - lam * d[m]) / dn;
+    g[1][0] = e2[1] * a[2] - e2[2] * a[1];
+    g[1][1] = e2[2] * a[0] - e2[0] * a[2];
+    g[1][2] = e2[0] * a[1] - e2[1] * a[0];
+    g[2][0] = a[1] * e1[2] - a[2] * e1[1];
+    g[2][1] = a[2] * e1[0] - a[0] * e1[2];
+    g[2][2] = a[0] * e1[1] - a[1] * e1[0];
+    for (m = 0; m < 3; ++m) g[0][m] = n[m] / dn - g[1][m] - g[2][m];
+}
+
+static double exact_dir(const orc_pp* pp, double rx, double ry, double d[3]) {
+    d[0] = (rx - pp->cx) / pp->fx;
+    d[1] = (ry - pp->cy) / pp->fy;
+    d[2] = 1.0;
+    return sqrt(d[0] * d[0] + d[1] * d[1] + 1.0);
+}
+
 /* Span of the pixel ray through a primitive by MTIA over all faces (Sec. 3.2
  * "Rasterization"): i1 = nearest hit, i2 = farthest hit.  Returns 1 when the
  * ray crosses the primitive (two hits with i2 > i1). */
 static int span_mtia(const orc_pp* pp, int nv, double rx, double ry, double* i1, double* i2,
                      int* f1, int* f2) {
     int f, F = n_faces(nv), nhit = 0;
-    double lo = INFINITY, hi = -INFINITY;
+    double lo = INFINITY, hi = -INFINITY, d[3], dl = 0.0;
+    if (pp->exact) dl = exact_dir(pp, rx, ry, d);
     for (f = 0; f < F; ++f) {
         const int* fv = face_vertices(nv, f);
-        double u, v, det, depth;
-        if (mtia(pp->p[fv[0]], pp->p[fv[1]], pp->p[fv[2]], rx, ry, &u, &v, &det, &depth)) {
+        double u, v, det, depth, lam;
+        int hit;
+        if (pp->exact) {
+            hit = mtia_ray(pp->p[fv[0]], pp->p[fv[1]], pp->p[fv[2]], d, &lam);
+            depth = lam * dl;   /* distance along the ray */
+        } else {
+            hit = mtia(pp->p[fv[0]], pp->p[fv[1]], pp->p[fv[2]], rx, ry, &u, &v, &det, &depth);
+        }
+        if (hit) {
             ++nhit;
             if (depth < lo) { lo = depth; *f1 = f; }
             if (depth > hi) { hi = depth; *f2 = f; }
@@ -462,6 +544,32 @@ static int span_mtia(const orc_pp* pp, int nv, double rx, double ry, double* i1,
 static int span_clip(const orc_pp* pp, int nv, double rx, double ry, double* i1, double* i2) {
     int f, F = n_faces(nv);
     double lo = -INFINITY, hi = INFINITY;
+    if (pp->exact) {
+        /* the ray lam d against each face's half-space n . t <= h (outward n) */
+        double d[3], dl = exact_dir(pp, rx, ry, d);
+        for (f = 0; f < F; ++f) {
+            const int* fv = face_vertices(nv, f);
+            const double *a = pp->p[fv[0]], *b = pp->p[fv[1]], *c = pp->p[fv[2]];
+            double e1[3], e2[3], n[3], h, den;
+            int m;
+            for (m = 0; m < 3; ++m) { e1[m] = b[m] - a[m]; e2[m] = c[m] - a[m]; }
+            n[0] = e1[1] * e2[2] - e1[2] * e2[1];
+            n[1] = e1[2] * e2[0] - e1[0] * e2[2];
+            n[2] = e1[0] * e2[1] - e1[1] * e2[0];
+            if (n[0] * (a[0] - pp->pc[0]) + n[1] * (a[1] - pp->pc[1]) + n[2] * (a[2] - pp->pc[2]) < 0)
+                for (m = 0; m < 3; ++m) n[m] = -n[m];
+            h = n[0] * a[0] + n[1] * a[1] + n[2] * a[2];
+            den = n[0] * d[0] + n[1] * d[1] + n[2] * d[2];
+            if (den == 0.0) {
+                if (h < 0.0) { *i1 = INFINITY; *i2 = -INFINITY; return 0; }
+                continue;
+            }
+            if (den < 0) { if (h / den * dl > lo) lo = h / den * dl; }
+            else         { if (h / den * dl < hi) hi = h / den * dl; }
+        }
+        *i1 = lo; *i2 = hi;
+        return hi > lo && lo > 0.0;
+    }
     for (f = 0; f < F; ++f) {
         const int* fv = face_vertices(nv, f);
         const double *a = pp->p[fv[0]], *b = pp->p[fv[1]], *c = pp->p[fv[2]];
@@ -642,8 +750,17 @@ static void blend_pixel_backward(const orc_prims* P, const orc_view* V, const do
         dL_ds = dL_do * pp->sigma * c->tau;
         pg->dsigma += dL_do * c->s * c->tau;
         /* s = i2 - i1 */
-        mtia_grad(pp->p[fv1[0]], pp->p[fv1[1]], pp->p[fv1[2]], rx, ry, di1);
-        mtia_grad(pp->p[fv2[0]], pp->p[fv2[1]], pp->p[fv2[2]], rx, ry, di2);
+        if (pp->exact) {
+            /* i = lam |d|: d i / dp = |d| d lam / dp */
+            double d[3], dl = exact_dir(pp, rx, ry, d);
+            mtia_ray_grad(pp->p[fv1[0]], pp->p[fv1[1]], pp->p[fv1[2]], d, c->i1 / dl, di1);
+            mtia_ray_grad(pp->p[fv2[0]], pp->p[fv2[1]], pp->p[fv2[2]], d, c->i2 / dl, di2);
+            for (k = 0; k < 3; ++k)
+                for (a = 0; a < 3; ++a) { di1[k][a] *= dl; di2[k][a] *= dl; }
+        } else {
+            mtia_grad(pp->p[fv1[0]], pp->p[fv1[1]], pp->p[fv1[2]], rx, ry, di1);
+            mtia_grad(pp->p[fv2[0]], pp->p[fv2[1]], pp->p[fv2[2]], rx, ry, di2);
+        }
         for (k = 0; k < 3; ++k)
             for (a = 0; a < 3; ++a) {
                 pg->dp[fv1[k]][a] += -dL_ds * di1[k][a];
@@ -664,6 +781,12 @@ static void chain_primitive(const orc_prims* P, const orc_camera* cam, int i, co
     double tx = pp->tc[0], ty = pp->tc[1], tz = pp->tc[2];
     double len = pp->pc[2];
     cam_rotation(cam, R, T);
+    if (pp->exact) {
+        /* p_k = tv_k: the gradients are camera-space already; the centre
+         * enters only through the colour (below) */
+        for (k = 0; k < P->nv; ++k)
+            for (a = 0; a < 3; ++a) dtv[k][a] = pg->dp[k][a];
+    } else {
     /* p_k = phi(tc) + J(tc) (tv_k - tc) */
     for (k = 0; k < P->nv; ++k) {
         for (a = 0; a < 3; ++a) dtv[k][a] = 0.0;
@@ -692,6 +815,7 @@ static void chain_primitive(const orc_prims* P, const orc_camera* cam, int i, co
             double d_ab = (a == b ? 1.0 : 0.0) - pp->tc[a] * pp->tc[b] / (len * len);
             dtc[b] += dJ[2][a] * d_ab / len;
         }
+    }
     /* camera space -> world: t = R x + T */
     for (a = 0; a < 3; ++a) {
         double s = 0.0;

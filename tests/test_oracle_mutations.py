@@ -63,6 +63,10 @@ MUTANTS = {
                              "if (out->depth == 0.0 && T >= 0.5 && Tn < 0.5) out->depth = i2;", ["depth_surface"]),
     "depth_threshold": ("if (out->depth == 0.0 && T >= 0.5 && Tn < 0.5) out->depth = i1;",
                         "if (out->depth == 0.0 && T >= 0.1 && Tn < 0.1) out->depth = i1;", ["depth_layers"]),
+    "exact_no_dir_length": ("depth = lam * dl;   /* distance along the ray */", "depth = lam;",
+                            ["exact_chord"]),
+    "exact_grad_sign": ("for (m = 0; m < 3; ++m) a[m] = (p0[m] - lam * d[m]) / dn;",
+                        "for (m = 0; m < 3; ++m) a[m] = (p0[m] + lam * d[m]) / dn;", ["exact_fd"]),
     "aa_rect_unmoved": ("if (kf->shx[k] > 0) qx = qx + sh;", "if (kf->shx[k] > 0) qx = qx;", ["aa_rect"]),
 }
 
@@ -84,6 +88,8 @@ CHECKS = {
     "param_scipy": lambda o: [params_pins.test_vertices_match_scipy_rotation(k) for k in (6, 4)],
     "param_fd": lambda o: [params_pins.test_params_adjoint_fd(k) for k in (6, 4)],
     "depth_surface": pins.test_depth_front_surface_closed_form,
+    "exact_chord": lambda o: pins.test_exact_span_is_the_world_chord(o, 6),
+    "exact_fd": lambda o: [pins.test_exact_adjoint_fd(o, k) for k in (6, 4)],
     "depth_layers": pins.test_depth_two_layers,
     "aa_span": lambda o: pins.test_aa_filter_octahedron_span_closed_form(o, 4.0),
     "aa_moves": pins.test_aa_filter_moves_box_vertices,

@@ -692,3 +692,126 @@ def test_depth_two_layers(orc):
     d, _ = orc.depth_pixels(empty, cam, np.array([0], np.int32), np.array([0], np.int32))
     assert d[0] == 0.0
 
+
+# ------------------------------------------- exact mode (App. "Ray Space Approximation")
+def _hull_chord(verts_world, cam_pos, w):
+    """Length of the ray cam_pos + l w (l > 0) inside the convex hull of the
+    vertices, from scipy's hull facets (independent of the face topology)."""
+    from scipy.spatial import ConvexHull
+    h = ConvexHull(verts_world)
+    lo, hi = 0.0, np.inf
+    for eq in h.equations:                    # n . x + off <= 0 inside
+        n, off = eq[:3], eq[3]
+        den = n @ w
+        num = -(off + n @ cam_pos)
+        if abs(den) < 1e-15:
+            if num < 0:
+                return 0.0
+            continue
+        t = num / den
+        if den > 0:
+            hi = min(hi, t)
+        else:
+            lo = max(lo, t)
+    return max(hi - lo, 0.0) * np.linalg.norm(w)
+
+
+@pytest.mark.parametrize("kind", [6, 4])
+def test_exact_span_is_the_world_chord(orc, kind):
+    """Without the ray-space approximation the span of any pixel is the
+    length of that pixel's perspective ray inside the primitive."""
+    rng = np.random.default_rng(31 + kind)
+    cam = scenes.make_camera((0.4, -0.3, 3.0), 96, 80, 50.0)
+    cam.viewmat = scenes.look_at((0.4, -0.3, 3.0))        # exactly orthonormal (binary64)
+    M = np.asarray(cam.viewmat, np.float64).reshape(4, 4)
+    Rm, Tv = M[:3, :3], M[:3, 3]
+    cam_pos = -Rm.T @ Tv
+    R = scenes.random_rotations(rng, 1)
+    c = np.array([[0.1, 0.05, -0.2]])
+    if kind == 6:
+        v = scenes.octahedra_from_axes(c, R, np.array([[0.5, 0.35, 0.25]]))[0]
+    else:
+        v = scenes.tetrahedra_from_scale(c, R, np.array([0.6]))[0]
+    sc = one_scene(kind, c[0], v, 0.5)
+    rect = orc.preprocess(sc, cam, exact=True)["rect"][0]
+    n_hit = 0
+    for _ in range(400):
+        x, y = rng.uniform(rect[0] - 3, rect[1] + 4), rng.uniform(rect[2] - 3, rect[3] + 4)
+        d_cam = np.array([(x - cam.cx) / cam.fx, (y - cam.cy) / cam.fy, 1.0])
+        w = Rm.T @ d_cam
+        want = _hull_chord(v, cam_pos, w)
+        (hit, i1, i2), (hit2, j1, j2) = orc.span(sc, cam, 0, x, y, exact=True)
+        if want > 1e-9:
+            assert hit and hit2
+            assert abs((i2 - i1) - want) < 1e-10
+            assert abs((j2 - j1) - want) < 1e-10
+            n_hit += 1
+        elif want == 0.0:
+            assert not hit
+    assert n_hit > 50
+    # every pixel whose centre ray meets the primitive lies in the tile rectangle
+    for py in range(cam.height):
+        for px in range(cam.width):
+            (hit, _, _), _ = orc.span(sc, cam, 0, px + 0.5, py + 0.5, exact=True)
+            if hit:
+                assert rect[0] <= px <= rect[1] and rect[2] <= py <= rect[3]
+
+
+def test_exact_culls_primitives_reaching_the_near_plane(orc):
+    """Reading: in exact mode the perspective box needs every vertex in front,
+    so a primitive with a vertex at depth <= 0.2 is not visible."""
+    cam = cam_on_axis(4.0, 33, 33, 40.0)
+    near = one_scene(6, [0, 0, 3.5], axis_octa([0, 0, 3.5], 0.2, 0.2, 0.35), 0.5)   # front vertex at depth 0.15
+    far = one_scene(6, [0, 0, 3.5], axis_octa([0, 0, 3.5], 0.2, 0.2, 0.25), 0.5)    # front vertex at depth 0.25
+    assert not orc.preprocess(near, cam, exact=True)["visible"][0]
+    assert orc.preprocess(near, cam)["visible"][0]                # the ray-space mode keeps it
+    assert orc.preprocess(far, cam, exact=True)["visible"][0]
+
+
+@pytest.mark.parametrize("kind", [6, 4])
+def test_exact_adjoint_fd(orc, kind):
+    if kind == 4:
+        w = scenes.workload(0)
+    else:
+        w = scenes.workload(1, scale=0.02)
+    sc, cam = w.scene, w.cameras[0]
+    rng = np.random.default_rng(37 + kind)
+    pp = orc.preprocess(sc, cam, exact=True)
+    area = (pp["rect"][:, 1] - pp["rect"][:, 0]) * (pp["rect"][:, 3] - pp["rect"][:, 2])
+    cand = np.nonzero(pp["visible"] & (area > 30))[0]
+    params = []
+    mask = np.zeros((cam.height, cam.width), bool)
+    for i in rng.choice(cand, min(4, cand.size), replace=False):
+        params += [("centre", 3 * i + a) for a in range(3)]
+        params += [("verts", 3 * kind * i + a) for a in rng.choice(3 * kind, 6, replace=False)]
+        params += [("opacity", i)]
+        r = pp["rect"][i]
+        mask[max(r[2] - 2, 0):r[3] + 3, max(r[0] - 2, 0):r[1] + 3] = True
+    py, px = [a.astype(np.int32) for a in np.nonzero(mask)]
+    gpx = rng.normal(size=(px.shape[0], 3))
+    ok = _fd_check_exact(orc, sc, cam, gpx, params, px, py)
+    assert ok >= 0.8 * len(params)
+
+
+def _fd_check_exact(orc, sc, cam, gimg, params, px, py, h=1e-6):
+    dmin = orc.preprocess(sc, cam, exact=True)["dmin"]
+    _, _, grads = orc.render_pixels(sc, cam, px, py, dL_dC=gimg, dmin=dmin, exact=True)
+    base = dict(centre=sc.centre.astype(np.float64), verts=sc.verts.astype(np.float64),
+                opacity=sc.opacity.astype(np.float64), sh=sc.sh.astype(np.float64))
+    ok = 0
+    for name, idx in params:
+        hh = 1e-5 if name == "opacity" else h
+        def L(delta):
+            arrs = {k: v.copy() for k, v in base.items()}
+            arrs[name].reshape(-1)[idx] += delta
+            s2 = scenes.Scene(sc.kind, arrs["centre"], arrs["verts"], arrs["opacity"], arrs["sh"], sc.sh_degree)
+            return float(np.sum(orc.render_pixels(s2, cam, px, py, dmin=dmin, exact=True)[0] * gimg))
+        fd1 = (L(hh) - L(-hh)) / (2 * hh)
+        fd2 = (L(hh / 2) - L(-hh / 2)) / hh
+        if abs(fd1 - fd2) > 1e-4 * max(abs(fd1), 1e-3):
+            continue
+        g = grads[name].reshape(-1)[idx]
+        assert abs(g - fd1) <= 2e-4 * max(abs(fd1), 1e-2), (name, idx, g, fd1)
+        ok += 1
+    return ok
+
