@@ -147,6 +147,19 @@ void lp_destroy(lp_ctx* ctx);
 lp_status lp_set_tuning(lp_ctx* ctx, const lp_tuning* t);
 lp_status lp_get_tuning(lp_ctx* ctx, lp_tuning* t);
 
+/* Exact spans (App. "Ray Space Approximation", the variant without the
+ * approximation).  exact = 1: later forwards clip each pixel's true
+ * perspective ray -- from the camera centre through the pixel centre --
+ * against the primitive's camera-space faces; the span and the depth are
+ * distances along that ray.  The tile rectangle is then the box of the
+ * perspectively projected vertices, a primitive with a vertex at camera depth
+ * <= 0.2 is not drawn, and the 2D filter is not applied.  exact = 0 (the
+ * default) uses the EWA ray-space approximation.  A backward, depth pass or
+ * pair count uses the mode of its forward.  The exact mode runs one fixed
+ * schedule (32 records per batch, 4 pixels per thread) whatever the tuning. */
+lp_status lp_set_exact(lp_ctx* ctx, int exact);
+lp_status lp_get_exact(lp_ctx* ctx, int* exact);
+
 /* Depth map of the last forward on this context (App. "Depth and Surface
  * Reconstruction"): for every pixel, the distance along the ray (ray-space
  * depth, world units) at which it enters the first primitive after which the

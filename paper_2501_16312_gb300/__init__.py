@@ -113,6 +113,17 @@ class Rasterizer:
         uses 0.1).  Applies to later forward calls."""
         _native.check(self.ctx, self.lib.lp_set_filter_2d(self.ctx, float(kernel_px)), "lp_set_filter_2d")
 
+    def set_exact(self, exact: bool):
+        """Spans along the true perspective ray instead of the ray-space
+        approximation (App. "Ray Space Approximation"); applies to later
+        forward calls."""
+        _native.check(self.ctx, self.lib.lp_set_exact(self.ctx, int(bool(exact))), "lp_set_exact")
+
+    def exact(self) -> bool:
+        v = C.c_int()
+        _native.check(self.ctx, self.lib.lp_get_exact(self.ctx, C.byref(v)), "lp_get_exact")
+        return bool(v.value)
+
     def filter_2d(self) -> float:
         v = C.c_float()
         _native.check(self.ctx, self.lib.lp_get_filter_2d(self.ctx, C.byref(v)), "lp_get_filter_2d")

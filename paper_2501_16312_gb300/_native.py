@@ -21,7 +21,7 @@ EXPORTS = ("lp_create", "lp_destroy", "lp_set_tuning", "lp_get_tuning", "lp_set_
            "lp_debug_keys", "lp_debug_counts", "lp_debug_pixel_state", "lp_count_pairs",
            "lp_last_error", "lp_status_string", "lp_set_timing", "lp_stage_times",
            "lp_render_forward_noalloc", "lp_params_forward", "lp_params_backward",
-           "lp_l1_loss_grad", "lp_adam_step", "lp_render_depth")
+           "lp_l1_loss_grad", "lp_adam_step", "lp_render_depth", "lp_set_exact", "lp_get_exact")
 LP_ADAM_MAX_GROUPS = 8
 STAGES = ("preprocess", "scan_emit", "sort", "ranges", "blend_fwd", "blend_bwd", "chain")
 
@@ -92,6 +92,8 @@ def load(path: str = LIB_PATH):
     L.lp_debug_pixel_state.argtypes = [vp, vp, vp, ll]
     L.lp_count_pairs.argtypes = [vp, C.POINTER(ll)]
     L.lp_render_depth.argtypes = [vp, vp, vp]
+    L.lp_set_exact.argtypes = [vp, i]
+    L.lp_get_exact.argtypes = [vp, C.POINTER(i)]
     L.lp_last_error.argtypes = [vp]
     L.lp_last_error.restype = C.c_char_p
     L.lp_status_string.argtypes = [i]

@@ -8,6 +8,8 @@
 // to world-space centre/vertices, opacity and SH, summed over cameras).
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -33,6 +35,8 @@ struct lp_ctx {
     int sms = 0;
     lp_tuning tune{16, 64, 0, 0, 4};
     float aa_kernel = 0.f;      // 2D filter size in pixels (0 = off)
+    bool exact = false;         // spans along the true perspective ray
+    bool fwd_exact = false;     // mode of the last forward
     char err[512] = {0};
 
     DevBuf<float> rec;
@@ -130,6 +134,11 @@ template <typename T> void release(DevBuf<T>& b) {
 
 int rec_floats(int V) { return V == 6 ? lp::Rec<6>::kFloats : lp::Rec<4>::kFloats; }
 int acc_floats(int V) { return V == 6 ? lp::Acc<6>::kFloats : lp::Acc<4>::kFloats; }
+int rec_floats_mode(int V, bool exact) { return exact ? lp::rec_floats_x(V) : rec_floats(V); }
+int acc_floats_mode(int V, bool exact) { return exact ? lp::acc_floats_x(V) : acc_floats(V); }
+// the largest record / accumulator of either kind and mode (for lp_reserve)
+int rec_floats_max() { return std::max(rec_floats(6), lp::rec_floats_x(6)); }
+int acc_floats_max() { return std::max(acc_floats(6), lp::acc_floats_x(6)); }
 
 lp_status check_prims(lp_ctx* ctx, const lp_prims* p) {
     if (!p) return fail(ctx, LP_ERR_INVALID, "prims is NULL");
@@ -193,9 +202,12 @@ void mark(lp_ctx* ctx, cudaStream_t st, int i, bool cap_mode) {
 
 // Persistent blend grid: resident blocks per SM (tuned, or what fits) x SMs,
 // never more blocks than tiles.
-int blend_grid(const lp_ctx* ctx, int V, bool fwd, long long tiles) {
+int blend_grid(const lp_ctx* ctx, int V, bool fwd, long long tiles, bool exact = false) {
     int bps = ctx->tune.blocks_per_sm;
-    if (bps <= 0) {
+    if (exact) {
+        bps = lp::blend_x_occupancy(V, fwd);
+        if (bps <= 0) bps = 1;
+    } else if (bps <= 0) {
         bps = fwd ? lp::blend_fwd_occupancy(V, ctx->tune.batch, ctx->tune.pixels_per_thread)
                   : lp::blend_bwd_occupancy(V, ctx->tune.batch, ctx->tune.pixels_per_thread);
         if (bps <= 0) bps = 1;
@@ -306,6 +318,18 @@ lp_status lp_set_filter_2d(lp_ctx* ctx, float kernel_px) {
     return LP_OK;
 }
 
+lp_status lp_set_exact(lp_ctx* ctx, int exact) {
+    if (!ctx) return LP_ERR_INVALID;
+    ctx->exact = exact != 0;
+    return LP_OK;
+}
+
+lp_status lp_get_exact(lp_ctx* ctx, int* exact) {
+    if (!ctx || !exact) return LP_ERR_INVALID;
+    *exact = ctx->exact ? 1 : 0;
+    return LP_OK;
+}
+
 lp_status lp_get_filter_2d(lp_ctx* ctx, float* kernel_px) {
     if (!ctx || !kernel_px) return LP_ERR_INVALID;
     *kernel_px = ctx->aa_kernel;
@@ -314,7 +338,7 @@ lp_status lp_get_filter_2d(lp_ctx* ctx, float* kernel_px) {
 
 static lp_status reserve_impl(lp_ctx* ctx, long long records, long long entries, long long pixels,
                               long long tiles, int V) {
-    const int rf = V ? rec_floats(V) : lp::Rec<6>::kFloats;
+    const int rf = V ? rec_floats_mode(V, ctx->exact) : rec_floats_max();
     LP_TRY(ensure(ctx, ctx->rec, records * rf, false, "records"));
     LP_TRY(ensure(ctx, ctx->counts, records, false, "counts"));
     LP_TRY(ensure(ctx, ctx->offsets, records, false, "offsets"));
@@ -344,7 +368,7 @@ static lp_status reserve_impl(lp_ctx* ctx, long long records, long long entries,
     LP_TRY(ensure(ctx, ctx->ranges, tiles, false, "tile ranges"));
     LP_TRY(ensure(ctx, ctx->last, pixels, false, "pixel state"));
     LP_TRY(ensure(ctx, ctx->tl, pixels, false, "pixel state"));
-    const int af = V ? acc_floats(V) : lp::Acc<6>::kFloats;
+    const int af = V ? acc_floats_mode(V, ctx->exact) : acc_floats_max();
     LP_TRY(ensure(ctx, ctx->acc, records * af, false, "gradient accumulators"));
     return LP_OK;
 }
@@ -373,14 +397,16 @@ lp_status lp_render_forward(lp_ctx* ctx, const lp_prims* prims, const lp_camera*
     lp::CamsParam cp;
     long long pixels = 0, tiles = 0;
     LP_TRY(build_cams(ctx, cams, n_cams, ctx->tune.tile, cp, pixels, tiles));
-    // the 2D filter's vertex move, rounded once to binary32 from the size
-    cp.aa_half = (float)(0.5 * (double)ctx->aa_kernel);
-    cp.aa_full = ctx->aa_kernel;
+    // the 2D filter's vertex move, rounded once to binary32 from the size (the
+    // exact mode has no filter)
+    const bool exact = ctx->exact;
+    cp.aa_half = exact ? 0.f : (float)(0.5 * (double)ctx->aa_kernel);
+    cp.aa_full = exact ? 0.f : ctx->aa_kernel;
     const long long records = (long long)n_cams * prims->n;
     if (records > 0x7fffffffll) return fail(ctx, LP_ERR_INVALID, "too many records (%lld)", records);
     ctx->have_fwd = false;
 
-    LP_TRY(ensure(ctx, ctx->rec, records * rec_floats(V), cap_mode, "records"));
+    LP_TRY(ensure(ctx, ctx->rec, records * rec_floats_mode(V, exact), cap_mode, "records"));
     LP_TRY(ensure(ctx, ctx->counts, records, cap_mode, "counts"));
     LP_TRY(ensure(ctx, ctx->offsets, records, cap_mode, "offsets"));
     LP_TRY(ensure(ctx, ctx->zbits, records, cap_mode, "zbits"));
@@ -392,8 +418,12 @@ lp_status lp_render_forward(lp_ctx* ctx, const lp_prims* prims, const lp_camera*
 
     lp::PrimsDev P{prims->n, prims->centre, prims->verts, prims->opacity, prims->sh};
     mark(ctx, st, 0, cap_mode);
-    LP_CUDA(lp::launch_preprocess(V, prims->sh_degree, P, cp, ctx->rec.p, ctx->counts.p, ctx->trect.p,
-                                  ctx->zbits.p, st));
+    if (exact)
+        LP_CUDA(lp::launch_preprocess_x(V, prims->sh_degree, P, cp, ctx->rec.p, ctx->counts.p, ctx->trect.p,
+                                        ctx->zbits.p, st));
+    else
+        LP_CUDA(lp::launch_preprocess(V, prims->sh_degree, P, cp, ctx->rec.p, ctx->counts.p, ctx->trect.p,
+                                      ctx->zbits.p, st));
     mark(ctx, st, 1, cap_mode);
     const int mode = ctx->tune.sort_mode;
     int passes = 0, passes1 = 0;
@@ -481,7 +511,7 @@ lp_status lp_render_forward(lp_ctx* ctx, const lp_prims* prims, const lp_camera*
     mark(ctx, st, 4, cap_mode);
 
     lp::BlendArgs a{};
-    a.grid = blend_grid(ctx, V, true, tiles);
+    a.grid = blend_grid(ctx, V, true, tiles, exact);
     a.rec = ctx->rec.p;
     a.vals = svals;
     a.ranges = ctx->ranges.p;
@@ -494,7 +524,10 @@ lp_status lp_render_forward(lp_ctx* ctx, const lp_prims* prims, const lp_camera*
     a.pair_counts = ctx->d_pairs;
     a.count = false;
     LP_CUDA(cudaMemsetAsync(ctx->d_tile_counter, 0, sizeof(int), st));
-    if (a.grid > 0) LP_CUDA(lp::launch_blend_fwd(V, ctx->tune.batch, ctx->tune.pixels_per_thread, a, st));
+    if (a.grid > 0) {
+        if (exact) LP_CUDA(lp::launch_blend_fwd_x(V, a, st));
+        else LP_CUDA(lp::launch_blend_fwd(V, ctx->tune.batch, ctx->tune.pixels_per_thread, a, st));
+    }
     mark(ctx, st, 5, cap_mode);
     ctx->fwd_timed = ctx->timing;
     ctx->launches_fwd = 1 + (records > 0 ? 3 : 0) + (records > 0 ? 1 : 0) + 5 * (passes + passes1) +
@@ -511,6 +544,7 @@ lp_status lp_render_forward(lp_ctx* ctx, const lp_prims* prims, const lp_camera*
     ctx->key_bits = key_bits;
     ctx->sort_passes = passes1 + passes;
     ctx->keys32 = mode == 1;
+    ctx->fwd_exact = exact;
     return LP_OK;
 }
 
@@ -528,12 +562,13 @@ lp_status lp_render_backward(lp_ctx* ctx, const float* dL_dimages, float* dcentr
     const bool cap_mode = capturing(st);
     const int V = pr.kind;
     mark(ctx, st, 6, cap_mode);
-    const long long acc_n = (ctx->records > 0 ? ctx->records : 1) * acc_floats(V);
+    const bool exact = ctx->fwd_exact;
+    const long long acc_n = (ctx->records > 0 ? ctx->records : 1) * acc_floats_mode(V, exact);
     LP_TRY(ensure(ctx, ctx->acc, acc_n, cap_mode, "gradient accumulators"));
     LP_CUDA(cudaMemsetAsync(ctx->acc.p, 0, (size_t)acc_n * sizeof(float), st));
 
     lp::BlendArgs a{};
-    a.grid = blend_grid(ctx, ctx->prims.kind, false, ctx->tiles);
+    a.grid = blend_grid(ctx, ctx->prims.kind, false, ctx->tiles, exact);
     a.rec = ctx->rec.p;
     a.vals = ctx->result_in_1 ? ctx->vals1.p : ctx->vals0.p;
     a.ranges = ctx->ranges.p;
@@ -545,12 +580,19 @@ lp_status lp_render_backward(lp_ctx* ctx, const float* dL_dimages, float* dcentr
     a.acc = ctx->acc.p;
     a.tile_counter = ctx->d_tile_counter + 1;
     LP_CUDA(cudaMemsetAsync(ctx->d_tile_counter + 1, 0, sizeof(int), st));
-    if (a.grid > 0) LP_CUDA(lp::launch_blend_bwd(V, ctx->tune.batch, ctx->tune.pixels_per_thread, a, st));
+    if (a.grid > 0) {
+        if (exact) LP_CUDA(lp::launch_blend_bwd_x(V, a, st));
+        else LP_CUDA(lp::launch_blend_bwd(V, ctx->tune.batch, ctx->tune.pixels_per_thread, a, st));
+    }
     mark(ctx, st, 7, cap_mode);
 
     lp::PrimsDev P{pr.n, pr.centre, pr.verts, pr.opacity, pr.sh};
-    LP_CUDA(lp::launch_chain(V, pr.sh_degree, P, ctx->cams, ctx->rec.p, ctx->counts.p, ctx->acc.p, dcentre,
-                             dverts, dopacity, dsh, accumulate, st));
+    if (exact)
+        LP_CUDA(lp::launch_chain_x(V, pr.sh_degree, P, ctx->cams, ctx->counts.p, ctx->acc.p, dcentre, dverts,
+                                   dopacity, dsh, accumulate, st));
+    else
+        LP_CUDA(lp::launch_chain(V, pr.sh_degree, P, ctx->cams, ctx->rec.p, ctx->counts.p, ctx->acc.p, dcentre,
+                                 dverts, dopacity, dsh, accumulate, st));
     mark(ctx, st, 8, cap_mode);
     ctx->bwd_timed = ctx->timing;
     return LP_OK;
@@ -685,7 +727,7 @@ lp_status lp_render_depth(lp_ctx* ctx, float* depth, void* stream) {
     LP_CUDA(cudaSetDevice(ctx->device));
     cudaStream_t st = (cudaStream_t)stream;
     lp::BlendArgs a{};
-    a.grid = blend_grid(ctx, ctx->prims.kind, true, ctx->tiles);
+    a.grid = blend_grid(ctx, ctx->prims.kind, true, ctx->tiles, ctx->fwd_exact);
     a.rec = ctx->rec.p;
     a.vals = ctx->result_in_1 ? ctx->vals1.p : ctx->vals0.p;
     a.ranges = ctx->ranges.p;
@@ -694,7 +736,9 @@ lp_status lp_render_depth(lp_ctx* ctx, float* depth, void* stream) {
     a.pair_counts = ctx->d_pairs;
     a.depth = depth;
     LP_CUDA(cudaMemsetAsync(ctx->d_tile_counter, 0, sizeof(int), st));
-    if (a.grid > 0)
+    if (a.grid > 0 && ctx->fwd_exact)
+        LP_CUDA(lp::launch_blend_fwd_x(ctx->prims.kind, a, st));
+    else if (a.grid > 0)
         LP_CUDA(lp::launch_blend_fwd(ctx->prims.kind, ctx->tune.batch, ctx->tune.pixels_per_thread, a, st));
     else if (ctx->pixels > 0)
         LP_CUDA(cudaMemsetAsync(depth, 0, (size_t)ctx->pixels * sizeof(float), st));
@@ -708,7 +752,7 @@ lp_status lp_count_pairs(lp_ctx* ctx, long long* counts) {
     LP_CUDA(cudaDeviceSynchronize());
     LP_TRY(ensure(ctx, ctx->scratch_image, 3 * ctx->pixels, false, "scratch image"));
     lp::BlendArgs a{};
-    a.grid = blend_grid(ctx, ctx->prims.kind, true, ctx->tiles);
+    a.grid = blend_grid(ctx, ctx->prims.kind, true, ctx->tiles, ctx->fwd_exact);
     a.rec = ctx->rec.p;
     a.vals = ctx->result_in_1 ? ctx->vals1.p : ctx->vals0.p;
     a.ranges = ctx->ranges.p;
@@ -722,7 +766,9 @@ lp_status lp_count_pairs(lp_ctx* ctx, long long* counts) {
     a.count = true;
     LP_CUDA(cudaMemset(ctx->d_pairs, 0, 4 * sizeof(unsigned long long)));
     LP_CUDA(cudaMemset(ctx->d_tile_counter, 0, sizeof(int)));
-    if (a.grid > 0) LP_CUDA(lp::launch_blend_fwd(ctx->prims.kind, ctx->tune.batch, ctx->tune.pixels_per_thread, a, 0));
+    if (a.grid > 0 && ctx->fwd_exact) LP_CUDA(lp::launch_blend_fwd_x(ctx->prims.kind, a, 0));
+    else if (a.grid > 0)
+        LP_CUDA(lp::launch_blend_fwd(ctx->prims.kind, ctx->tune.batch, ctx->tune.pixels_per_thread, a, 0));
     LP_CUDA(cudaDeviceSynchronize());
     unsigned long long h[4] = {0, 0, 0, 0};
     LP_CUDA(cudaMemcpy(h, ctx->d_pairs, sizeof(h), cudaMemcpyDeviceToHost));

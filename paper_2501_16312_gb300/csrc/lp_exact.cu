@@ -1,0 +1,748 @@
+// Exact spans, without the ray-space approximation (sm_103a).
+//
+// App. "Ray Space Approximation" evaluates a variant that renders with the
+// true perspective ray of each pixel instead of the EWA affine ray space, at
+// about twice the rasterization cost.  The ray of pixel centre (x, y) is
+// lambda d with d = ((x - cx)/fx, (y - cy)/fy, 1) in camera space; it enters
+// a convex primitive at the largest entry-face hit and leaves at the smallest
+// exit-face hit, and the span is the distance between them, (lam_out - lam_in)
+// |d| (world units).  Which faces enter depends on the pixel, so each face is
+// classified per pixel by the sign of n . d.
+//
+// Each face is stored as the camera-space half-space n' . (t - c) <= 1 around
+// the primitive's centre c (outward normal n scaled so the right side is 1),
+// evaluated relative to the centre depth: with L = n'_x (x - x_c)/fx +
+// n'_y (y - y_c)/fy (x_c, y_c the projected centre), D = n' . d = L + D0 and
+// D0 = n' . c / c_z, the hit is lambda = c_z + (1 - c_z L)/D.  The stored
+// quantities are small offsets, so the span does not cancel between two large
+// depths.  Per face a record keeps float4 (p, q, L0, D0) with p = n'_x/fx,
+// q = n'_y/fy and L0 = L at the anchor pixel (X0, Y0).
+//
+// The tile rectangle is the box of the perspectively projected vertices,
+// which needs every vertex in front: a primitive with a vertex at depth
+// <= 0.2 is not drawn in this mode.  The 2D filter does not apply.  One
+// schedule is built (32 records per batch, 4 pixels per thread).
+#include "lp_blend.cuh"
+#include "lp_geom.cuh"
+
+namespace lp {
+
+namespace {
+
+constexpr int kBatchX = 32;
+constexpr int kPixX = 4;
+constexpr int kThreadsX = kTilePixels / kPixX;
+
+template <int V> struct RecX {
+    static constexpr int F = Kind<V>::F;
+    static constexpr int kFloats = 8 + 4 * F;   // 40 (octahedron), 24 (tetrahedron)
+    static constexpr int kVec4 = kFloats / 4;
+};
+
+// per face slot (= face) dL/d(p, q, L0, D0); then rgb, sigma, c_z (the last
+// is collected by the backward but not needed by the chain, see k_chain_x)
+template <int V> struct AccX {
+    static constexpr int F = Kind<V>::F;
+    static constexpr int kFloats = 4 * F + 5;   // 37, 21
+};
+
+// Camera-space offsets d = R (v - c) of a vertex (the key-field sequence).
+__device__ __forceinline__ void vertex_offset(const CamDev& cm, const float v[3], const float c[3], float d[3]) {
+    const float w0 = __fsub_rn(v[0], c[0]), w1 = __fsub_rn(v[1], c[1]), w2 = __fsub_rn(v[2], c[2]);
+#pragma unroll
+    for (int m = 0; m < 3; ++m)
+        d[m] = __fadd_rn(__fadd_rn(__fmul_rn(cm.R[3 * m], w0), __fmul_rn(cm.R[3 * m + 1], w1)),
+                         __fmul_rn(cm.R[3 * m + 2], w2));
+}
+
+// Face f as n' = n / h with n the normal of the offsets' triangle and
+// h = n . d0 (the centre is inside, so h != 0 for a proper primitive; a face
+// through the centre gets n' = 0, a constraint every ray meets).
+template <int V>
+__device__ __forceinline__ void face_plane_x(const float d[V][3], int f, float np[3], float& h) {
+    int i0, i1, i2;
+    face_vertices<V>(f, i0, i1, i2);
+    float n[3];
+    face_normal(d[i0], d[i1], d[i2], n);
+    h = n[0] * d[i0][0] + n[1] * d[i0][1] + n[2] * d[i0][2];
+    const float ih = h != 0.f ? 1.f / h : 0.f;
+    np[0] = n[0] * ih; np[1] = n[1] * ih; np[2] = n[2] * ih;
+}
+
+template <int V, int DEG>
+__global__ void __launch_bounds__(128) k_preprocess_x(PrimsDev P, CamsParam cams, float* __restrict__ rec,
+                                                      uint32_t* __restrict__ counts, int4* __restrict__ trect,
+                                                      uint32_t* __restrict__ zbits) {
+    constexpr int F = Kind<V>::F;
+    constexpr int K = (DEG + 1) * (DEG + 1);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P.n) return;
+    float c[3], v[V][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) c[a] = __ldg(P.centre + 3 * (size_t)i + a);
+#pragma unroll
+    for (int k = 0; k < V; ++k)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) v[k][a] = __ldg(P.verts + ((size_t)i * V + k) * 3 + a);
+    const float alpha = __ldg(P.opacity + i);
+    float sh[K * 3];
+#pragma unroll
+    for (int q = 0; q < K * 3; ++q) sh[q] = __ldg(P.sh + (size_t)i * K * 3 + q);
+    // Eq. 1 (d_min from the world-space vertices) and the degenerate case, as
+    // in the ray-space mode
+    float dmin = CUDART_INF_F;
+    bool degenerate = false;
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+        const float dx = v[k][0] - c[0], dy = v[k][1] - c[1], dz = v[k][2] - c[2];
+        dmin = fminf(dmin, sqrtf(dx * dx + dy * dy + dz * dz));
+        degenerate |= dx == 0.f && dy == 0.f && dz == 0.f;
+    }
+    const float sigma = -log1pf(-kAlphaScale * alpha) / (2.f * dmin);
+    degenerate |= !(sigma < CUDART_INF_F);
+
+    for (int cv = 0; cv < cams.n; ++cv) {
+        const CamDev& cm = cams.cam[cv];
+        const size_t r = (size_t)cv * P.n + i;
+        Geom g;
+        bool vis = centre_geom(cm, c, g) && !degenerate;
+        zbits[r] = __float_as_uint(g.tc[2]);
+        float d[V][3];
+        float qxmin = CUDART_INF_F, qxmax = -CUDART_INF_F, qymin = CUDART_INF_F, qymax = -CUDART_INF_F;
+        if (vis) {
+#pragma unroll
+            for (int k = 0; k < V; ++k) {
+                vertex_offset(cm, v[k], c, d[k]);
+                // the vertex's perspective projection, as an offset from the
+                // projected centre (binary32 key-field sequence)
+                const float X = __fadd_rn(g.tc[0], d[k][0]), Y = __fadd_rn(g.tc[1], d[k][1]);
+                const float Z = __fadd_rn(g.tc[2], d[k][2]);
+                vis = vis && Z > kNearZ;
+                const float uu = __fdiv_rn(X, Z), ww = __fdiv_rn(Y, Z);
+                const float qx = __fsub_rn(__fadd_rn(__fmul_rn(cm.fx, uu), cm.cx), g.xc);
+                const float qy = __fsub_rn(__fadd_rn(__fmul_rn(cm.fy, ww), cm.cy), g.yc);
+                qxmin = fminf(qxmin, qx); qxmax = fmaxf(qxmax, qx);
+                qymin = fminf(qymin, qy); qymax = fmaxf(qymax, qy);
+            }
+        }
+        if (!vis) {
+            counts[r] = 0;
+            trect[r] = make_int4(0, 0, 0, 0);
+            continue;
+        }
+        float fx0 = ceilf(__fsub_rn(__fadd_rn(g.xc, qxmin), 0.5f));
+        float fx1 = floorf(__fsub_rn(__fadd_rn(g.xc, qxmax), 0.5f));
+        float fy0 = ceilf(__fsub_rn(__fadd_rn(g.yc, qymin), 0.5f));
+        float fy1 = floorf(__fsub_rn(__fadd_rn(g.yc, qymax), 0.5f));
+        fx0 = fmaxf(fx0, 0.f); fx1 = fminf(fx1, (float)(cm.width - 1));
+        fy0 = fmaxf(fy0, 0.f); fy1 = fminf(fy1, (float)(cm.height - 1));
+        if (fx0 > fx1 || fy0 > fy1) {
+            counts[r] = 0;
+            trect[r] = make_int4(0, 0, 0, 0);
+            continue;
+        }
+        const int T = cams.tile;
+        const int tx0 = (int)fx0 / T, tx1 = (int)fx1 / T, ty0 = (int)fy0 / T, ty1 = (int)fy1 / T;
+        counts[r] = (uint32_t)((tx1 - tx0 + 1) * (ty1 - ty0 + 1));
+        trect[r] = make_int4(cm.tile_base + ty0 * cm.tiles_x + tx0, cm.tiles_x, tx1 - tx0 + 1, ty1 - ty0 + 1);
+
+        float out[RecX<V>::kFloats];
+        const float icz = 1.f / g.tc[2];
+#pragma unroll
+        for (int f = 0; f < F; ++f) {
+            float np[3], h;
+            face_plane_x<V>(d, f, np, h);
+            const float p = np[0] / cm.fx, q = np[1] / cm.fy;
+            out[8 + 4 * f + 0] = p;
+            out[8 + 4 * f + 1] = q;
+            out[8 + 4 * f + 2] = -__fmaf_rn(p, g.fxo, __fmul_rn(q, g.fyo));
+            out[8 + 4 * f + 3] = (np[0] * g.tc[0] + np[1] * g.tc[1] + np[2] * g.tc[2]) * icz;
+        }
+        float dir[3] = {c[0] - cm.campos[0], c[1] - cm.campos[1], c[2] - cm.campos[2]};
+        const float idl = rsqrtf(dir[0] * dir[0] + dir[1] * dir[1] + dir[2] * dir[2]);
+        dir[0] *= idl; dir[1] *= idl; dir[2] *= idl;
+        float Y[16];
+        sh_basis<DEG>(dir[0], dir[1], dir[2], Y);
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            float s = 0.5f;
+#pragma unroll
+            for (int k = 0; k < K; ++k) s = fmaf(Y[k], sh[3 * k + ch], s);
+            out[4 + ch] = fmaxf(s, 0.f);
+        }
+        out[0] = __int_as_float(g.X0); out[1] = __int_as_float(g.Y0); out[2] = sigma;
+        out[3] = __uint_as_float((uint32_t)F);
+        out[7] = g.tc[2];
+        float4* dst = reinterpret_cast<float4*>(rec + r * RecX<V>::kFloats);
+#pragma unroll
+        for (int k = 0; k < RecX<V>::kVec4; ++k)
+            dst[k] = make_float4(out[4 * k], out[4 * k + 1], out[4 * k + 2], out[4 * k + 3]);
+    }
+}
+
+// ------------------------------------------------------------------- blend
+template <int V> struct alignas(16) StagedX {
+    static constexpr int F = Kind<V>::F;
+    float4 pl[F];      // (p, q, L at the tile's first pixel, D0)
+    float sigma, r, g, b;
+    float cz, dx0, dy0;
+    int rec;
+};
+
+template <int V>
+__device__ __forceinline__ void stage_record_x(const float* __restrict__ rec, int r, int tx0, int ty0,
+                                               StagedX<V>& s) {
+    constexpr int F = Kind<V>::F;
+    const float4* src = reinterpret_cast<const float4*>(rec + (size_t)r * RecX<V>::kFloats);
+    const float4 h0 = __ldg(src), h1 = __ldg(src + 1);
+    const float dx0 = (float)(tx0 - __float_as_int(h0.x));
+    const float dy0 = (float)(ty0 - __float_as_int(h0.y));
+#pragma unroll
+    for (int f = 0; f < F; ++f) {
+        const float4 pl = __ldg(src + 2 + f);
+        s.pl[f] = make_float4(pl.x, pl.y, __fmaf_rn(pl.x, dx0, __fmaf_rn(pl.y, dy0, pl.z)), pl.w);
+    }
+    s.sigma = h0.z;
+    s.r = h1.x; s.g = h1.y; s.b = h1.z;
+    s.cz = h1.w;
+    s.dx0 = dx0; s.dy0 = dy0;
+    s.rec = r;
+}
+
+// Spans of a strip of PIX pixels.  rn[i] = |d| of pixel i.  With ARG the
+// entry / exit faces are returned too; ent[i] = entry hit minus c_z.
+template <int V, int PIX, bool ARG>
+__device__ __forceinline__ void spans_x(const StagedX<V>& s, float lx0, float ly, const float* rn, float* sp,
+                                        int* sf, int* sb, float* ent_out) {
+    constexpr int F = Kind<V>::F;
+    float en[PIX], ex[PIX];
+    bool miss[PIX];
+#pragma unroll
+    for (int i = 0; i < PIX; ++i) {
+        en[i] = -s.cz;   // lambda > 0: the hit must lie in front of the camera
+        ex[i] = CUDART_INF_F;
+        miss[i] = false;
+        if (ARG) { sf[i] = 0; sb[i] = 0; }
+    }
+#pragma unroll
+    for (int f = 0; f < F; ++f) {
+        const float4 p = s.pl[f];
+        const float t = __fmaf_rn(p.y, ly, p.z);
+#pragma unroll
+        for (int i = 0; i < PIX; ++i) {
+            const float L = __fmaf_rn(p.x, lx0 + (float)i, t);
+            const float D = __fadd_rn(L, p.w);
+            const float N = __fmaf_rn(-s.cz, L, 1.f);
+            const float dl = __fdividef(N, D);
+            if (ARG) {
+                if (D < 0.f && dl > en[i]) { en[i] = dl; sf[i] = f; }
+                if (D > 0.f && dl < ex[i]) { ex[i] = dl; sb[i] = f; }
+            } else {
+                en[i] = D < 0.f ? fmaxf(en[i], dl) : en[i];
+                ex[i] = D > 0.f ? fminf(ex[i], dl) : ex[i];
+            }
+            miss[i] = miss[i] || (D == 0.f && N < 0.f);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < PIX; ++i) {
+        sp[i] = miss[i] ? -1.f : __fmul_rn(__fsub_rn(ex[i], en[i]), rn[i]);
+        if (ent_out) ent_out[i] = en[i];
+    }
+}
+
+__device__ __forceinline__ float ray_norm(const CamDev& cm, int px, int py) {
+    const float rx = ((float)px + 0.5f - cm.cx) / cm.fx;
+    const float ry = ((float)py + 0.5f - cm.cy) / cm.fy;
+    return sqrtf(1.f + rx * rx + ry * ry);
+}
+
+// MODE 0: image; 1: also the pair counters; 2: depth pass.
+template <int V, int MODE>
+__global__ void __launch_bounds__(kThreadsX) k_blend_fwd_x(
+    const float* __restrict__ rec, const uint32_t* __restrict__ vals, const uint2* __restrict__ ranges,
+    CamsParam cams, float bg0, float bg1, float bg2, float* __restrict__ image,
+    uint32_t* __restrict__ last_out, float* __restrict__ tl_out, int* __restrict__ tile_counter,
+    unsigned long long* __restrict__ pair_counts, float* __restrict__ depth_out) {
+    constexpr int PIX = kPixX, NT = kThreadsX, RW = kTile / PIX, BATCH = kBatchX;
+    constexpr bool COUNT = MODE == 1, DEPTH = MODE == 2;
+    constexpr float kStop = DEPTH ? 0.5f : kStopT;
+    __shared__ StagedX<V> sm[BATCH];
+    __shared__ int s_tile;
+    const int tid = threadIdx.x;
+    const int ly = tid / RW, lx0 = (tid % RW) * PIX;
+    unsigned long long n_iter = 0, n_eval = 0, n_hit = 0, n_eval_last = 0;
+    for (;;) {
+        if (tid == 0) s_tile = atomicAdd(tile_counter, 1);
+        __syncthreads();
+        const int tile = s_tile;
+        if (tile >= cams.total_tiles) break;
+        const TileGeom tg = tile_geom(cams, tile);
+        const CamDev& cm = cams.cam[camera_of_tile(cams, tile)];
+        const int py = tg.ty0 + ly;
+        const uint2 rg = ranges[tile];
+        const int n = (int)(rg.y - rg.x);
+        float T[PIX], c0[PIX], c1[PIX], c2[PIX], tl[PIX], rn[PIX], dep[PIX];
+        uint32_t last[PIX], ce[PIX], cl[PIX];
+        bool done[PIX];
+        bool tdone = true;
+#pragma unroll
+        for (int i = 0; i < PIX; ++i) {
+            T[i] = 1.f; c0[i] = c1[i] = c2[i] = 0.f; tl[i] = 1.f; last[i] = 0; dep[i] = 0.f;
+            ce[i] = cl[i] = 0;
+            rn[i] = ray_norm(cm, tg.tx0 + lx0 + i, py);
+            done[i] = !(tg.tx0 + lx0 + i < tg.width && py < tg.height);
+            tdone &= done[i];
+        }
+        for (int b0 = 0; b0 < n; b0 += BATCH) {
+            if (__syncthreads_count(!tdone) == 0) break;
+            const int nb = min(BATCH, n - b0);
+            for (int j = tid; j < nb; j += NT) stage_record_x<V>(rec, vals[rg.x + b0 + j], tg.tx0, tg.ty0, sm[j]);
+            __syncthreads();
+            if (!tdone) {
+                for (int j = 0; j < nb; ++j) {
+                    const StagedX<V>& p = sm[j];
+                    if (COUNT) {
+#pragma unroll
+                        for (int i = 0; i < PIX; ++i) n_iter += !done[i];
+                    }
+                    float sp[PIX], en[PIX];
+                    spans_x<V, PIX, false>(p, (float)lx0, (float)ly, rn, sp, nullptr, nullptr, DEPTH ? en : nullptr);
+                    tdone = true;
+#pragma unroll
+                    for (int i = 0; i < PIX; ++i) {
+                        const bool in = !done[i];
+                        if (COUNT) { n_eval += in; ce[i] += in; }
+                        if (in && sp[i] > 0.f) {
+                            if (COUNT) { ++n_hit; cl[i] = ce[i]; }
+                            const float tau = span_tau(p.sigma, sp[i]);
+                            const float w = T[i] * (1.f - tau);
+                            c0[i] = fmaf(w, p.r, c0[i]);
+                            c1[i] = fmaf(w, p.g, c1[i]);
+                            c2[i] = fmaf(w, p.b, c2[i]);
+                            tl[i] = T[i];
+                            T[i] *= tau;
+                            last[i] = (uint32_t)(b0 + j + 1);
+                            done[i] = T[i] < kStop;
+                            if (DEPTH && done[i]) dep[i] = __fmul_rn(__fadd_rn(p.cz, en[i]), rn[i]);
+                        }
+                        tdone &= done[i];
+                    }
+                    if (tdone) break;
+                }
+            }
+        }
+        if (COUNT) {
+#pragma unroll
+            for (int i = 0; i < PIX; ++i) n_eval_last += cl[i];
+        }
+        const int plane = tg.width * tg.height;
+        float* img = image + 3 * (size_t)tg.pix_base;
+#pragma unroll
+        for (int i = 0; i < PIX; ++i) {
+            const int px = tg.tx0 + lx0 + i;
+            if (!(px < tg.width && py < tg.height)) continue;
+            const int idx = py * tg.width + px;
+            if (DEPTH) {
+                depth_out[tg.pix_base + idx] = dep[i];
+                continue;
+            }
+            img[idx] = fmaf(T[i], bg0, c0[i]);
+            img[plane + idx] = fmaf(T[i], bg1, c1[i]);
+            img[2 * plane + idx] = fmaf(T[i], bg2, c2[i]);
+            last_out[tg.pix_base + idx] = last[i];
+            tl_out[tg.pix_base + idx] = tl[i];
+        }
+        __syncthreads();
+    }
+    if (COUNT) {
+        unsigned long long a = n_iter, b = n_eval, c = n_hit, d = n_eval_last;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_xor_sync(0xffffffffu, a, o);
+            b += __shfl_xor_sync(0xffffffffu, b, o);
+            c += __shfl_xor_sync(0xffffffffu, c, o);
+            d += __shfl_xor_sync(0xffffffffu, d, o);
+        }
+        if ((tid & 31) == 0) {
+            atomicAdd(pair_counts, a);
+            atomicAdd(pair_counts + 1, b);
+            atomicAdd(pair_counts + 2, c);
+            atomicAdd(pair_counts + 3, d);
+        }
+    }
+}
+
+// Backward: the blend recurrences are those of the ray-space mode; the span
+// s = (delta_out - delta_in) |d| of a face f with delta = N / D, N = 1 - c_z L,
+// D = L + D0, L = p X + q Y + L0 (X, Y the pixel offsets from the anchor) has
+//   d delta/dL = -(c_z + delta)/D,  d delta/dD0 = -delta/D,  d delta/dc_z = -L/D.
+template <int V>
+__global__ void __launch_bounds__(kThreadsX) k_blend_bwd_x(
+    const float* __restrict__ rec, const uint32_t* __restrict__ vals, const uint2* __restrict__ ranges,
+    CamsParam cams, float bg0, float bg1, float bg2, const float* __restrict__ dimage,
+    const uint32_t* __restrict__ last_in, const float* __restrict__ tl_in, float* __restrict__ acc,
+    int* __restrict__ tile_counter) {
+    constexpr int F = Kind<V>::F;
+    constexpr int ACC = AccX<V>::kFloats;
+    constexpr int PIX = kPixX, NT = kThreadsX, RW = kTile / PIX, BATCH = kBatchX;
+    __shared__ StagedX<V> sm[BATCH];
+    __shared__ int s_tile;
+    __shared__ int s_max;
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const int ly = tid / RW, lx0 = (tid % RW) * PIX;
+    for (;;) {
+        if (tid == 0) {
+            s_tile = atomicAdd(tile_counter, 1);
+            s_max = 0;
+        }
+        __syncthreads();
+        const int tile = s_tile;
+        if (tile >= cams.total_tiles) break;
+        const TileGeom tg = tile_geom(cams, tile);
+        const CamDev& cm = cams.cam[camera_of_tile(cams, tile)];
+        const int py = tg.ty0 + ly;
+        const uint2 rg = ranges[tile];
+        const int plane = tg.width * tg.height;
+        const float* gi = dimage + 3 * (size_t)tg.pix_base;
+        float g0[PIX], g1[PIX], g2[PIX], Tcur[PIX], B0[PIX], B1[PIX], B2[PIX], rn[PIX];
+        uint32_t last[PIX];
+        bool first[PIX];
+        uint32_t lmax = 0;
+#pragma unroll
+        for (int i = 0; i < PIX; ++i) {
+            const int px = tg.tx0 + lx0 + i;
+            g0[i] = g1[i] = g2[i] = 0.f; Tcur[i] = 1.f; last[i] = 0;
+            rn[i] = ray_norm(cm, px, py);
+            if (px < tg.width && py < tg.height) {
+                const int idx = py * tg.width + px;
+                g0[i] = gi[idx]; g1[i] = gi[plane + idx]; g2[i] = gi[2 * plane + idx];
+                last[i] = last_in[tg.pix_base + idx];
+                Tcur[i] = tl_in[tg.pix_base + idx];
+            }
+            B0[i] = bg0; B1[i] = bg1; B2[i] = bg2;
+            first[i] = true;
+            lmax = max(lmax, last[i]);
+        }
+        if (lmax > 0) atomicMax(&s_max, (int)lmax);
+        __syncthreads();
+        const int hi_all = s_max;
+        for (int hi = hi_all; hi > 0; hi -= BATCH) {
+            const int lo = max(0, hi - BATCH);
+            const int nb = hi - lo;
+            __syncthreads();
+            for (int j = tid; j < nb; j += NT) stage_record_x<V>(rec, vals[rg.x + lo + j], tg.tx0, tg.ty0, sm[j]);
+            __syncthreads();
+            for (int j = nb - 1; j >= 0; --j) {
+                const StagedX<V>& p = sm[j];
+                const uint32_t idx = (uint32_t)(lo + j);
+                bool any = false;
+#pragma unroll
+                for (int i = 0; i < PIX; ++i) any |= idx < last[i];
+                if (__ballot_sync(0xffffffffu, any) == 0u) continue;
+                float sp[PIX];
+                int sf[PIX], sb[PIX];
+                bool c[PIX];
+                bool anyc = false;
+                spans_x<V, PIX, true>(p, (float)lx0, (float)ly, rn, sp, sf, sb, nullptr);
+#pragma unroll
+                for (int i = 0; i < PIX; ++i) {
+                    c[i] = idx < last[i] && sp[i] > 0.f;
+                    anyc |= c[i];
+                }
+                if (__ballot_sync(0xffffffffu, anyc) == 0u) continue;
+                float A[ACC];
+#pragma unroll
+                for (int q = 0; q < ACC; ++q) A[q] = 0.f;
+                if (anyc) {
+#pragma unroll
+                    for (int i = 0; i < PIX; ++i) {
+                        if (!c[i]) continue;
+                        const float tau = span_tau(p.sigma, sp[i]);
+                        const float o = 1.f - tau;
+                        const float Ti = first[i] ? Tcur[i] : __fdividef(Tcur[i], tau);
+                        first[i] = false;
+                        Tcur[i] = Ti;
+                        const float w = Ti * o;
+                        A[4 * F + 0] = fmaf(w, g0[i], A[4 * F + 0]);
+                        A[4 * F + 1] = fmaf(w, g1[i], A[4 * F + 1]);
+                        A[4 * F + 2] = fmaf(w, g2[i], A[4 * F + 2]);
+                        const float dLdo = Ti * ((p.r - B0[i]) * g0[i] + (p.g - B1[i]) * g1[i] +
+                                                 (p.b - B2[i]) * g2[i]);
+                        B0[i] = fmaf(o, p.r, tau * B0[i]);
+                        B1[i] = fmaf(o, p.g, tau * B1[i]);
+                        B2[i] = fmaf(o, p.b, tau * B2[i]);
+                        A[4 * F + 3] = fmaf(dLdo * sp[i], tau, A[4 * F + 3]);   // dL/dsigma
+                        const float gs = dLdo * p.sigma * tau * rn[i];          // dL/d(delta_out - delta_in)
+                        const float X = (float)(lx0 + i) + p.dx0, Y = (float)ly + p.dy0;
+#pragma unroll
+                        for (int side = 0; side < 2; ++side) {
+                            const int f = side ? sb[i] : sf[i];
+                            const float gd = side ? gs : -gs;
+                            // the face's L, D and delta at this pixel (recomputed)
+                            float4 pl;
+#pragma unroll
+                            for (int ff = 0; ff < F; ++ff)
+                                if (ff == f) pl = p.pl[ff];
+                            const float L = __fmaf_rn(pl.x, (float)(lx0 + i), __fmaf_rn(pl.y, (float)ly, pl.z));
+                            const float D = __fadd_rn(L, pl.w);
+                            const float iD = 1.f / D;
+                            const float dl = __fmaf_rn(-p.cz, L, 1.f) * iD;
+                            const float gL = -gd * (p.cz + dl) * iD;
+#pragma unroll
+                            for (int ff = 0; ff < F; ++ff) {
+                                if (ff == f) {
+                                    A[4 * ff + 0] = fmaf(gL, X, A[4 * ff + 0]);
+                                    A[4 * ff + 1] = fmaf(gL, Y, A[4 * ff + 1]);
+                                    A[4 * ff + 2] += gL;
+                                    A[4 * ff + 3] = fmaf(-gd * dl, iD, A[4 * ff + 3]);
+                                }
+                            }
+                            A[4 * F + 4] = fmaf(-gd * L, iD, A[4 * F + 4]);   // dL/dc_z
+                        }
+                    }
+                }
+                float* Ag = acc + (size_t)p.rec * ACC;
+#pragma unroll
+                for (int q = 0; q < ACC; ++q) {
+                    const float s = warp_sum(A[q]);
+                    if (lane == 0 && s != 0.f) atomicAdd(Ag + q, s);
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------- chain
+template <int V, int DEG>
+__global__ void __launch_bounds__(128) k_chain_x(PrimsDev P, CamsParam cams, const uint32_t* __restrict__ counts,
+                                                 const float* __restrict__ acc, float* __restrict__ dcentre,
+                                                 float* __restrict__ dverts, float* __restrict__ dopacity,
+                                                 float* __restrict__ dsh, int accumulate) {
+    constexpr int F = Kind<V>::F;
+    constexpr int K = (DEG + 1) * (DEG + 1);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P.n) return;
+    float c[3], v[V][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) c[a] = __ldg(P.centre + 3 * (size_t)i + a);
+#pragma unroll
+    for (int k = 0; k < V; ++k)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) v[k][a] = __ldg(P.verts + ((size_t)i * V + k) * 3 + a);
+    const float alpha = __ldg(P.opacity + i);
+    float sh[K * 3];
+#pragma unroll
+    for (int q = 0; q < K * 3; ++q) sh[q] = __ldg(P.sh + (size_t)i * K * 3 + q);
+    float dmin = CUDART_INF_F;
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+        const float dx = v[k][0] - c[0], dy = v[k][1] - c[1], dz = v[k][2] - c[2];
+        dmin = fminf(dmin, sqrtf(dx * dx + dy * dy + dz * dz));
+    }
+    float gc[3] = {0.f, 0.f, 0.f}, gv[V][3], gsh[K * 3], gsigma = 0.f;
+#pragma unroll
+    for (int k = 0; k < V; ++k) gv[k][0] = gv[k][1] = gv[k][2] = 0.f;
+#pragma unroll
+    for (int q = 0; q < K * 3; ++q) gsh[q] = 0.f;
+
+    for (int cv = 0; cv < cams.n; ++cv) {
+        const size_t r = (size_t)cv * P.n + i;
+        if (counts[r] == 0) continue;
+        const float* A = acc + r * AccX<V>::kFloats;
+        bool any = false;
+#pragma unroll
+        for (int q = 0; q < AccX<V>::kFloats; ++q) any |= A[q] != 0.f;
+        if (!any) continue;
+        const CamDev& cm = cams.cam[cv];
+        Geom g;
+        centre_geom(cm, c, g);
+        float d[V][3];
+#pragma unroll
+        for (int k = 0; k < V; ++k) vertex_offset(cm, v[k], c, d[k]);
+        float gd[V][3];
+#pragma unroll
+        for (int k = 0; k < V; ++k) gd[k][0] = gd[k][1] = gd[k][2] = 0.f;
+        // The hit lambda = h / (n . d) of a face does not depend on the centre:
+        // the centre-relative form only serves precision, and its centre terms
+        // (through D0, c_z and the anchor) cancel exactly.  Only the partial
+        // derivatives with the centre held fixed are taken, which are the
+        // vertices' total derivatives; the centre gets the colour's gradient.
+        const float cx = g.tc[0], cy = g.tc[1], icz = 1.f / g.tc[2];
+#pragma unroll
+        for (int f = 0; f < F; ++f) {
+            const float Gp = A[4 * f], Gq = A[4 * f + 1], GL0 = A[4 * f + 2], GD0 = A[4 * f + 3];
+            if (Gp == 0.f && Gq == 0.f && GL0 == 0.f && GD0 == 0.f) continue;
+            int i0, i1, i2;
+            face_vertices<V>(f, i0, i1, i2);
+            float n[3];
+            face_normal(d[i0], d[i1], d[i2], n);
+            const float h = n[0] * d[i0][0] + n[1] * d[i0][1] + n[2] * d[i0][2];
+            if (h == 0.f) continue;
+            const float ih = 1.f / h;
+            const float np[3] = {n[0] * ih, n[1] * ih, n[2] * ih};
+            // L0 = -(p fxo + q fyo); p = n'_x / fx, q = n'_y / fy, D0 = n' . c / c_z
+            const float Gpt = Gp - g.fxo * GL0, Gqt = Gq - g.fyo * GL0;
+            float G[3] = {Gpt / cm.fx + GD0 * cx * icz, Gqt / cm.fy + GD0 * cy * icz, GD0};
+            // n' = n / h with h = n . d0
+            const float Gn = G[0] * np[0] + G[1] * np[1] + G[2] * np[2];
+            float gn[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                gn[a] = (G[a] - Gn * d[i0][a]) * ih;
+                gd[i0][a] -= Gn * np[a];
+            }
+            // n = e1 x e2
+            const float e1[3] = {d[i1][0] - d[i0][0], d[i1][1] - d[i0][1], d[i1][2] - d[i0][2]};
+            const float e2[3] = {d[i2][0] - d[i0][0], d[i2][1] - d[i0][1], d[i2][2] - d[i0][2]};
+            const float g1[3] = {e2[1] * gn[2] - e2[2] * gn[1], e2[2] * gn[0] - e2[0] * gn[2],
+                                 e2[0] * gn[1] - e2[1] * gn[0]};
+            const float g2[3] = {gn[1] * e1[2] - gn[2] * e1[1], gn[2] * e1[0] - gn[0] * e1[2],
+                                 gn[0] * e1[1] - gn[1] * e1[0]};
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                gd[i1][a] += g1[a];
+                gd[i2][a] += g2[a];
+                gd[i0][a] -= g1[a] + g2[a];
+            }
+        }
+        // d_k = R (v_k - c)
+#pragma unroll
+        for (int k = 0; k < V; ++k)
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+                gv[k][a] += cm.R[a] * gd[k][0] + cm.R[3 + a] * gd[k][1] + cm.R[6 + a] * gd[k][2];
+
+        // colour -> SH coefficients and view direction (as in the ray-space mode)
+        float dir[3] = {c[0] - cm.campos[0], c[1] - cm.campos[1], c[2] - cm.campos[2]};
+        const float dist = sqrtf(dir[0] * dir[0] + dir[1] * dir[1] + dir[2] * dir[2]);
+        const float idl = 1.f / dist;
+        dir[0] *= idl; dir[1] *= idl; dir[2] *= idl;
+        float Y[16];
+        sh_basis<DEG>(dir[0], dir[1], dir[2], Y);
+        float grgb[3];
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            float s = 0.5f;
+#pragma unroll
+            for (int k = 0; k < K; ++k) s = fmaf(Y[k], sh[3 * k + ch], s);
+            grgb[ch] = s > 0.f ? A[4 * F + ch] : 0.f;
+        }
+        float wk[16];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            wk[k] = sh[3 * k] * grgb[0] + sh[3 * k + 1] * grgb[1] + sh[3 * k + 2] * grgb[2];
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) gsh[3 * k + ch] += Y[k] * grgb[ch];
+        }
+        float gdir[3];
+        sh_basis_vjp<DEG>(dir[0], dir[1], dir[2], wk, gdir);
+        const float dd = gdir[0] * dir[0] + gdir[1] * dir[1] + gdir[2] * dir[2];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) gc[a] += (gdir[a] - dir[a] * dd) * idl;
+        gsigma += A[4 * F + 3];
+    }
+    const float galpha = gsigma != 0.f ? gsigma * kAlphaScale / ((1.f - kAlphaScale * alpha) * 2.f * dmin) : 0.f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        float& o = dcentre[3 * (size_t)i + a];
+        o = accumulate ? o + gc[a] : gc[a];
+    }
+#pragma unroll
+    for (int k = 0; k < V; ++k)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            float& o = dverts[((size_t)i * V + k) * 3 + a];
+            o = accumulate ? o + gv[k][a] : gv[k][a];
+        }
+    dopacity[i] = accumulate ? dopacity[i] + galpha : galpha;
+#pragma unroll
+    for (int q = 0; q < K * 3; ++q) {
+        float& o = dsh[(size_t)i * K * 3 + q];
+        o = accumulate ? o + gsh[q] : gsh[q];
+    }
+}
+
+template <int V, int DEG>
+cudaError_t pre_x_t(const PrimsDev& P, const CamsParam& cams, float* rec, uint32_t* counts, int4* trect,
+                    uint32_t* zbits, cudaStream_t st) {
+    const int grid = (P.n + 127) / 128;
+    if (grid > 0) k_preprocess_x<V, DEG><<<grid, 128, 0, st>>>(P, cams, rec, counts, trect, zbits);
+    return cudaGetLastError();
+}
+
+template <int V, int DEG>
+cudaError_t chain_x_t(const PrimsDev& P, const CamsParam& cams, const uint32_t* counts, const float* acc,
+                      float* dc, float* dv, float* dop, float* dsh, int accumulate, cudaStream_t st) {
+    const int grid = (P.n + 127) / 128;
+    if (grid > 0) k_chain_x<V, DEG><<<grid, 128, 0, st>>>(P, cams, counts, acc, dc, dv, dop, dsh, accumulate);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+int rec_floats_x(int V) { return V == 6 ? RecX<6>::kFloats : RecX<4>::kFloats; }
+int acc_floats_x(int V) { return V == 6 ? AccX<6>::kFloats : AccX<4>::kFloats; }
+
+#define LP_X_DISPATCH(V, DEG, CALL)                                      \
+    switch (DEG) {                                                       \
+        case 0: return (V == 6) ? CALL(6, 0) : CALL(4, 0);               \
+        case 1: return (V == 6) ? CALL(6, 1) : CALL(4, 1);               \
+        case 2: return (V == 6) ? CALL(6, 2) : CALL(4, 2);               \
+        default: return (V == 6) ? CALL(6, 3) : CALL(4, 3);              \
+    }
+
+cudaError_t launch_preprocess_x(int V, int deg, const PrimsDev& P, const CamsParam& cams, float* rec,
+                                uint32_t* counts, int4* trect, uint32_t* zbits, cudaStream_t st) {
+#define CALL(v, d) pre_x_t<v, d>(P, cams, rec, counts, trect, zbits, st)
+    LP_X_DISPATCH(V, deg, CALL)
+#undef CALL
+}
+
+cudaError_t launch_chain_x(int V, int deg, const PrimsDev& P, const CamsParam& cams, const uint32_t* counts,
+                           const float* acc, float* dc, float* dv, float* dop, float* dsh, int accumulate,
+                           cudaStream_t st) {
+#define CALL(v, d) chain_x_t<v, d>(P, cams, counts, acc, dc, dv, dop, dsh, accumulate, st)
+    LP_X_DISPATCH(V, deg, CALL)
+#undef CALL
+}
+
+cudaError_t launch_blend_fwd_x(int V, const BlendArgs& a, cudaStream_t st) {
+#define FWD(v, m)                                                                                        \
+    k_blend_fwd_x<v, m><<<a.grid, kThreadsX, 0, st>>>(a.rec, a.vals, a.ranges, *a.cams, a.bg[0], a.bg[1], \
+                                                      a.bg[2], a.image, a.last, a.tl, a.tile_counter,    \
+                                                      a.pair_counts, a.depth)
+    const int m = a.depth ? 2 : (a.count ? 1 : 0);
+    if (V == 6) {
+        if (m == 2) FWD(6, 2); else if (m == 1) FWD(6, 1); else FWD(6, 0);
+    } else {
+        if (m == 2) FWD(4, 2); else if (m == 1) FWD(4, 1); else FWD(4, 0);
+    }
+#undef FWD
+    return cudaGetLastError();
+}
+
+cudaError_t launch_blend_bwd_x(int V, const BlendArgs& a, cudaStream_t st) {
+    if (V == 6)
+        k_blend_bwd_x<6><<<a.grid, kThreadsX, 0, st>>>(a.rec, a.vals, a.ranges, *a.cams, a.bg[0], a.bg[1],
+                                                        a.bg[2], a.dimage, a.last, a.tl, a.acc, a.tile_counter);
+    else
+        k_blend_bwd_x<4><<<a.grid, kThreadsX, 0, st>>>(a.rec, a.vals, a.ranges, *a.cams, a.bg[0], a.bg[1],
+                                                        a.bg[2], a.dimage, a.last, a.tl, a.acc, a.tile_counter);
+    return cudaGetLastError();
+}
+
+int blend_x_occupancy(int V, bool fwd) {
+    int nb = 0;
+    if (V == 6)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fwd ? (const void*)k_blend_fwd_x<6, 0>
+                                                               : (const void*)k_blend_bwd_x<6>, kThreadsX, 0);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fwd ? (const void*)k_blend_fwd_x<4, 0>
+                                                               : (const void*)k_blend_bwd_x<4>, kThreadsX, 0);
+    return nb;
+}
+
+}  // namespace lp

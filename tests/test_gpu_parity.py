@@ -136,6 +136,63 @@ def test_depth_parity(rast, case):
     print(f"{case}: depth on {n_ok} pixels ({n_valid} with a depth)")
 
 
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_exact_mode_parity(rast, case):
+    """App. "Ray Space Approximation", the variant without it: tile lists
+    bit-exact, images, gradients and depth against the oracle's exact mode."""
+    w = CASES[case]()
+    bg = (0.1, 0.2, 0.3)
+    ref, info = oracle.render(w.scene, w.cameras, bg=bg, info=True, exact=True)
+    dL = mask_borderline(scenes.image_gradient(w, seed=4), info, w.cameras)
+    rast.set_exact(True)
+    try:
+        assert rast.exact()
+        img, grads = gpu_forward_backward(rast, w.scene, w.cameras, bg, dL)
+        k, v = rast.debug_keys()
+        depth = rast.depth().cpu().numpy().astype(np.float64)
+    finally:
+        rast.set_exact(False)
+    ko, vo, _ = oracle.keys(w.scene, w.cameras, tile=16, exact=True)
+    np.testing.assert_array_equal(k, ko)
+    np.testing.assert_array_equal(v, vo)
+    _, ref_g = oracle.render(w.scene, w.cameras, bg=bg, dL_dimage=dL, exact=True)
+    err = assert_images_match(img, ref, info, w.cameras)
+    rel = assert_grads_match(grads, ref_g)
+    do, flags = oracle.depth(w.scene, w.cameras, exact=True)
+    _depth_match(depth, do, flags)
+    img_rs, _ = gpu_forward_backward(rast, w.scene, w.cameras, bg)
+    print(f"{case}: exact mode, max image err {err:.2e}, grad rel L2 {rel}, "
+          f"max difference to the ray-space image {np.abs(img - img_rs).max():.2e}")
+
+
+def test_exact_mode_edge_cases(rast):
+    """Near cull (a vertex at depth <= 0.2), the 2D filter switched off, and a
+    primitive covering the whole image."""
+    bg = (0.25, 0.5, 0.75)
+    cam = scenes.make_camera((0, 0, 4), 48, 40, 60)
+    near = scenes.Scene(6, np.array([[0, 0, 3.5]], np.float32),
+                        scenes.octahedra_from_axes(np.array([[0, 0, 3.5]]), np.eye(3)[None],
+                                                   np.array([[0.2, 0.2, 0.35]])).astype(np.float32),
+                        np.array([0.8], np.float32), np.zeros((1, 1, 3), np.float32), 0)
+    big = scenes.Scene(6, np.array([[0, 0, 2.0]], np.float32),
+                       scenes.octahedra_from_axes(np.array([[0, 0, 2.0]]), np.eye(3)[None],
+                                                  np.array([[3.0, 2.5, 0.5]])).astype(np.float32),
+                       np.array([0.7], np.float32), np.full((1, 1, 3), 0.4, np.float32), 0)
+    rast.set_exact(True)
+    rast.set_filter_2d(0.1)
+    try:
+        img_near, _ = gpu_forward_backward(rast, near, [cam], bg)
+        img_big, g_big = gpu_forward_backward(rast, big, [cam], bg,
+                                              np.ones(3 * cam.pixels, np.float32))
+    finally:
+        rast.set_exact(False)
+        rast.set_filter_2d(0.0)
+    np.testing.assert_array_equal(img_near.reshape(3, -1), np.repeat(np.array(bg)[:, None], cam.pixels, 1).astype(np.float32))
+    ref, info, ref_g = oracle.render(big, [cam], bg=bg, dL_dimage=np.ones(3 * cam.pixels), info=True, exact=True)
+    assert_images_match(img_big, ref, info, [cam])
+    assert_grads_match(g_big, ref_g)
+
+
 def test_full_size_workload(rast):
     """The 500k-octahedron, 8 x 1264x832 workload in the launch configuration
     the benchmark times: every pixel of camera 0 and sampled pixels of camera 5
