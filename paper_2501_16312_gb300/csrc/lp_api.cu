@@ -588,8 +588,8 @@ lp_status lp_render_backward(lp_ctx* ctx, const float* dL_dimages, float* dcentr
 
     lp::PrimsDev P{pr.n, pr.centre, pr.verts, pr.opacity, pr.sh};
     if (exact)
-        LP_CUDA(lp::launch_chain_x(V, pr.sh_degree, P, ctx->cams, ctx->counts.p, ctx->acc.p, dcentre, dverts,
-                                   dopacity, dsh, accumulate, st));
+        LP_CUDA(lp::launch_chain_x(V, pr.sh_degree, P, ctx->cams, ctx->rec.p, ctx->counts.p, ctx->acc.p, dcentre,
+                                   dverts, dopacity, dsh, accumulate, st));
     else
         LP_CUDA(lp::launch_chain(V, pr.sh_degree, P, ctx->cams, ctx->rec.p, ctx->counts.p, ctx->acc.p, dcentre,
                                  dverts, dopacity, dsh, accumulate, st));

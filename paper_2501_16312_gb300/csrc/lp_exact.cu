@@ -9,6 +9,11 @@
 // |d| (world units).  Which faces enter depends on the pixel, so each face is
 // classified per pixel by the sign of n . d.
 //
+// Which faces a ray can enter through does not depend on the pixel: the
+// camera lies outside exactly those faces' half-spaces (for the others a
+// ray can only leave), so the faces are split once per record, entry faces
+// first, as in the ray-space mode.
+//
 // Each face is stored as the camera-space half-space n' . (t - c) <= 1 around
 // the primitive's centre c (outward normal n scaled so the right side is 1),
 // evaluated relative to the centre depth: with L = n'_x (x - x_c)/fx +
@@ -148,15 +153,32 @@ __global__ void __launch_bounds__(128) k_preprocess_x(PrimsDev P, CamsParam cams
 
         float out[RecX<V>::kFloats];
         const float icz = 1.f / g.tc[2];
+        float pl[F][4];
+        bool front[F];
+        int nf = 0;
 #pragma unroll
         for (int f = 0; f < F; ++f) {
             float np[3], h;
             face_plane_x<V>(d, f, np, h);
             const float p = np[0] / cm.fx, q = np[1] / cm.fy;
-            out[8 + 4 * f + 0] = p;
-            out[8 + 4 * f + 1] = q;
-            out[8 + 4 * f + 2] = -__fmaf_rn(p, g.fxo, __fmul_rn(q, g.fyo));
-            out[8 + 4 * f + 3] = (np[0] * g.tc[0] + np[1] * g.tc[1] + np[2] * g.tc[2]) * icz;
+            pl[f][0] = p;
+            pl[f][1] = q;
+            pl[f][2] = -__fmaf_rn(p, g.fxo, __fmul_rn(q, g.fyo));
+            pl[f][3] = (np[0] * g.tc[0] + np[1] * g.tc[1] + np[2] * g.tc[2]) * icz;
+            // the camera (the origin) lies outside the face's half-space
+            // n' . t <= 1 + n' . c: every ray can only enter through it
+            front[f] = 1.f + np[0] * g.tc[0] + np[1] * g.tc[1] + np[2] * g.tc[2] < 0.f;
+            nf += front[f] ? 1 : 0;
+        }
+        // slots: faces the camera sees from outside first (entry faces)
+        uint32_t meta = (uint32_t)nf;
+        int sf = 0, sb = nf;
+#pragma unroll
+        for (int f = 0; f < F; ++f) {
+            const int s = front[f] ? sf++ : sb++;
+            meta |= (uint32_t)f << (4 + 3 * s);
+#pragma unroll
+            for (int m = 0; m < 4; ++m) out[8 + 4 * s + m] = pl[f][m];
         }
         float dir[3] = {c[0] - cm.campos[0], c[1] - cm.campos[1], c[2] - cm.campos[2]};
         const float idl = rsqrtf(dir[0] * dir[0] + dir[1] * dir[1] + dir[2] * dir[2]);
@@ -171,7 +193,7 @@ __global__ void __launch_bounds__(128) k_preprocess_x(PrimsDev P, CamsParam cams
             out[4 + ch] = fmaxf(s, 0.f);
         }
         out[0] = __int_as_float(g.X0); out[1] = __int_as_float(g.Y0); out[2] = sigma;
-        out[3] = __uint_as_float((uint32_t)F);
+        out[3] = __uint_as_float(meta);
         out[7] = g.tc[2];
         float4* dst = reinterpret_cast<float4*>(rec + r * RecX<V>::kFloats);
 #pragma unroll
@@ -186,6 +208,7 @@ template <int V> struct alignas(16) StagedX {
     float4 pl[F];      // (p, q, L at the tile's first pixel, D0)
     float sigma, r, g, b;
     float cz, dx0, dy0;
+    int nf;            // entry faces (slots 0 .. nf - 1)
     int rec;
 };
 
@@ -206,23 +229,34 @@ __device__ __forceinline__ void stage_record_x(const float* __restrict__ rec, in
     s.r = h1.x; s.g = h1.y; s.b = h1.z;
     s.cz = h1.w;
     s.dx0 = dx0; s.dy0 = dy0;
+    s.nf = meta_nf(__float_as_uint(h0.w));
     s.rec = r;
 }
 
-// Spans of a strip of PIX pixels.  rn[i] = |d| of pixel i.  With ARG the
-// entry / exit faces are returned too; ent[i] = entry hit minus c_z.
-template <int V, int PIX, bool ARG>
-__device__ __forceinline__ void spans_x(const StagedX<V>& s, float lx0, float ly, const float* rn, float* sp,
-                                        int* sf, int* sb, float* ent_out) {
+// Spans of a strip of PIX pixels.  rn[i] = |d| of pixel i.  Slots < NF are
+// entry faces: a ray meets the primitive only if it crosses each of them
+// inward (D < 0), and then enters no earlier than its hit; the other faces
+// bound the exit where the ray leaves them (D > 0).  With ARG the entry /
+// exit slots are returned too; ent[i] = entry hit minus c_z.
+template <int V, int PIX, int NF, bool ARG>
+__device__ __forceinline__ void spans_x_nf(const StagedX<V>& s, float lx0, float ly, const float* rn, float* sp,
+                                           int* sf, int* sb, float* ent_out) {
     constexpr int F = Kind<V>::F;
+    if constexpr (NF <= 0 || NF >= F) {   // no entry or no exit face: not a closed primitive seen from outside
+#pragma unroll
+        for (int i = 0; i < PIX; ++i) {
+            sp[i] = -1.f;
+            if (ARG) { sf[i] = 0; sb[i] = F - 1; }
+            if (ent_out) ent_out[i] = 0.f;
+        }
+        return;
+    }
     float en[PIX], ex[PIX];
-    bool miss[PIX];
 #pragma unroll
     for (int i = 0; i < PIX; ++i) {
         en[i] = -s.cz;   // lambda > 0: the hit must lie in front of the camera
         ex[i] = CUDART_INF_F;
-        miss[i] = false;
-        if (ARG) { sf[i] = 0; sb[i] = 0; }
+        if (ARG) { sf[i] = 0; sb[i] = NF; }
     }
 #pragma unroll
     for (int f = 0; f < F; ++f) {
@@ -232,22 +266,47 @@ __device__ __forceinline__ void spans_x(const StagedX<V>& s, float lx0, float ly
         for (int i = 0; i < PIX; ++i) {
             const float L = __fmaf_rn(p.x, lx0 + (float)i, t);
             const float D = __fadd_rn(L, p.w);
-            const float N = __fmaf_rn(-s.cz, L, 1.f);
-            const float dl = __fdividef(N, D);
-            if (ARG) {
-                if (D < 0.f && dl > en[i]) { en[i] = dl; sf[i] = f; }
-                if (D > 0.f && dl < ex[i]) { ex[i] = dl; sb[i] = f; }
+            const float dl = __fdividef(__fmaf_rn(-s.cz, L, 1.f), D);
+            if (f < NF) {
+                const float e = D < 0.f ? dl : CUDART_INF_F;   // not crossed inward: no hit
+                if (ARG) { if (e > en[i]) { en[i] = e; sf[i] = f; } }
+                else en[i] = fmaxf(en[i], e);
             } else {
-                en[i] = D < 0.f ? fmaxf(en[i], dl) : en[i];
-                ex[i] = D > 0.f ? fminf(ex[i], dl) : ex[i];
+                const float x = D > 0.f ? dl : CUDART_INF_F;   // never left: no bound
+                if (ARG) { if (x < ex[i]) { ex[i] = x; sb[i] = f; } }
+                else ex[i] = fminf(ex[i], x);
             }
-            miss[i] = miss[i] || (D == 0.f && N < 0.f);
         }
     }
 #pragma unroll
     for (int i = 0; i < PIX; ++i) {
-        sp[i] = miss[i] ? -1.f : __fmul_rn(__fsub_rn(ex[i], en[i]), rn[i]);
+        sp[i] = __fmul_rn(__fsub_rn(ex[i], en[i]), rn[i]);   // +inf - inf, -inf: no hit
+        if (!(sp[i] < CUDART_INF_F)) sp[i] = -1.f;
         if (ent_out) ent_out[i] = en[i];
+    }
+}
+
+template <int V, int PIX, bool ARG>
+__device__ __forceinline__ void spans_x(const StagedX<V>& s, float lx0, float ly, const float* rn, float* sp,
+                                        int* sf, int* sb, float* ent_out) {
+    if (V == 6) {
+        switch (s.nf) {
+            case 1: spans_x_nf<V, PIX, 1, ARG>(s, lx0, ly, rn, sp, sf, sb, ent_out); break;
+            case 2: spans_x_nf<V, PIX, 2, ARG>(s, lx0, ly, rn, sp, sf, sb, ent_out); break;
+            case 3: spans_x_nf<V, PIX, 3, ARG>(s, lx0, ly, rn, sp, sf, sb, ent_out); break;
+            case 4: spans_x_nf<V, PIX, 4, ARG>(s, lx0, ly, rn, sp, sf, sb, ent_out); break;
+            case 5: spans_x_nf<V, PIX, 5, ARG>(s, lx0, ly, rn, sp, sf, sb, ent_out); break;
+            case 6: spans_x_nf<V, PIX, 6, ARG>(s, lx0, ly, rn, sp, sf, sb, ent_out); break;
+            case 7: spans_x_nf<V, PIX, 7, ARG>(s, lx0, ly, rn, sp, sf, sb, ent_out); break;
+            default: spans_x_nf<V, PIX, 0, ARG>(s, lx0, ly, rn, sp, sf, sb, ent_out); break;
+        }
+    } else {
+        switch (s.nf) {
+            case 1: spans_x_nf<V, PIX, 1, ARG>(s, lx0, ly, rn, sp, sf, sb, ent_out); break;
+            case 2: spans_x_nf<V, PIX, 2, ARG>(s, lx0, ly, rn, sp, sf, sb, ent_out); break;
+            case 3: spans_x_nf<V, PIX, 3, ARG>(s, lx0, ly, rn, sp, sf, sb, ent_out); break;
+            default: spans_x_nf<V, PIX, 0, ARG>(s, lx0, ly, rn, sp, sf, sb, ent_out); break;
+        }
     }
 }
 
@@ -452,62 +511,103 @@ __global__ void __launch_bounds__(kThreadsX) k_blend_bwd_x(
                     anyc |= c[i];
                 }
                 if (__ballot_sync(0xffffffffu, anyc) == 0u) continue;
-                float A[ACC];
+                // per contributing pixel: the entry and exit faces' terms
+                // dL/d(p, q, L0, D0); per thread: rgb, sigma, c_z sums
+                float ge[PIX][4], gx[PIX][4];
+                float h0 = 0.f, h1 = 0.f, h2 = 0.f, hs = 0.f, hz = 0.f;
+                unsigned used = 0;
 #pragma unroll
-                for (int q = 0; q < ACC; ++q) A[q] = 0.f;
-                if (anyc) {
+                for (int i = 0; i < PIX; ++i) {
 #pragma unroll
-                    for (int i = 0; i < PIX; ++i) {
-                        if (!c[i]) continue;
-                        const float tau = span_tau(p.sigma, sp[i]);
-                        const float o = 1.f - tau;
-                        const float Ti = first[i] ? Tcur[i] : __fdividef(Tcur[i], tau);
-                        first[i] = false;
-                        Tcur[i] = Ti;
-                        const float w = Ti * o;
-                        A[4 * F + 0] = fmaf(w, g0[i], A[4 * F + 0]);
-                        A[4 * F + 1] = fmaf(w, g1[i], A[4 * F + 1]);
-                        A[4 * F + 2] = fmaf(w, g2[i], A[4 * F + 2]);
-                        const float dLdo = Ti * ((p.r - B0[i]) * g0[i] + (p.g - B1[i]) * g1[i] +
-                                                 (p.b - B2[i]) * g2[i]);
-                        B0[i] = fmaf(o, p.r, tau * B0[i]);
-                        B1[i] = fmaf(o, p.g, tau * B1[i]);
-                        B2[i] = fmaf(o, p.b, tau * B2[i]);
-                        A[4 * F + 3] = fmaf(dLdo * sp[i], tau, A[4 * F + 3]);   // dL/dsigma
-                        const float gs = dLdo * p.sigma * tau * rn[i];          // dL/d(delta_out - delta_in)
-                        const float X = (float)(lx0 + i) + p.dx0, Y = (float)ly + p.dy0;
+                    for (int m = 0; m < 4; ++m) ge[i][m] = gx[i][m] = 0.f;
+                    if (!c[i]) continue;
+                    const float tau = span_tau(p.sigma, sp[i]);
+                    const float o = 1.f - tau;
+                    const float Ti = first[i] ? Tcur[i] : __fdividef(Tcur[i], tau);
+                    first[i] = false;
+                    Tcur[i] = Ti;
+                    const float w = Ti * o;
+                    h0 = fmaf(w, g0[i], h0);
+                    h1 = fmaf(w, g1[i], h1);
+                    h2 = fmaf(w, g2[i], h2);
+                    const float dLdo = Ti * ((p.r - B0[i]) * g0[i] + (p.g - B1[i]) * g1[i] + (p.b - B2[i]) * g2[i]);
+                    B0[i] = fmaf(o, p.r, tau * B0[i]);
+                    B1[i] = fmaf(o, p.g, tau * B1[i]);
+                    B2[i] = fmaf(o, p.b, tau * B2[i]);
+                    hs = fmaf(dLdo * sp[i], tau, hs);                     // dL/dsigma
+                    const float gs = dLdo * p.sigma * tau * rn[i];        // dL/d(delta_out - delta_in)
+                    const float X = (float)(lx0 + i) + p.dx0, Y = (float)ly + p.dy0;
+                    used |= (1u << sf[i]) | (1u << sb[i]);
 #pragma unroll
-                        for (int side = 0; side < 2; ++side) {
-                            const int f = side ? sb[i] : sf[i];
-                            const float gd = side ? gs : -gs;
-                            // the face's L, D and delta at this pixel (recomputed)
-                            float4 pl;
+                    for (int side = 0; side < 2; ++side) {
+                        const int f = side ? sb[i] : sf[i];
+                        const float gd = side ? gs : -gs;
+                        float4 pl = p.pl[0];
 #pragma unroll
-                            for (int ff = 0; ff < F; ++ff)
-                                if (ff == f) pl = p.pl[ff];
-                            const float L = __fmaf_rn(pl.x, (float)(lx0 + i), __fmaf_rn(pl.y, (float)ly, pl.z));
-                            const float D = __fadd_rn(L, pl.w);
-                            const float iD = 1.f / D;
-                            const float dl = __fmaf_rn(-p.cz, L, 1.f) * iD;
-                            const float gL = -gd * (p.cz + dl) * iD;
-#pragma unroll
-                            for (int ff = 0; ff < F; ++ff) {
-                                if (ff == f) {
-                                    A[4 * ff + 0] = fmaf(gL, X, A[4 * ff + 0]);
-                                    A[4 * ff + 1] = fmaf(gL, Y, A[4 * ff + 1]);
-                                    A[4 * ff + 2] += gL;
-                                    A[4 * ff + 3] = fmaf(-gd * dl, iD, A[4 * ff + 3]);
-                                }
-                            }
-                            A[4 * F + 4] = fmaf(-gd * L, iD, A[4 * F + 4]);   // dL/dc_z
-                        }
+                        for (int ff = 1; ff < F; ++ff)
+                            if (ff == f) pl = p.pl[ff];
+                        const float L = __fmaf_rn(pl.x, (float)(lx0 + i), __fmaf_rn(pl.y, (float)ly, pl.z));
+                        const float D = __fadd_rn(L, pl.w);
+                        const float iD = 1.f / D;
+                        const float dl = __fmaf_rn(-p.cz, L, 1.f) * iD;
+                        const float gL = -gd * (p.cz + dl) * iD;
+                        float* t = side ? gx[i] : ge[i];
+                        t[0] = gL * X;
+                        t[1] = gL * Y;
+                        t[2] = gL;
+                        t[3] = -gd * dl * iD;
+                        hz = fmaf(-gd * L, iD, hz);                       // dL/dc_z
                     }
                 }
                 float* Ag = acc + (size_t)p.rec * ACC;
+                const unsigned bal = __ballot_sync(0xffffffffu, anyc);
+                if (__popc(bal) <= 4) {
+                    // few contributing lanes: each adds its own terms
+                    if (anyc) {
+                        atomicAdd(Ag + 4 * F + 0, h0);
+                        atomicAdd(Ag + 4 * F + 1, h1);
+                        atomicAdd(Ag + 4 * F + 2, h2);
+                        atomicAdd(Ag + 4 * F + 3, hs);
+                        atomicAdd(Ag + 4 * F + 4, hz);
 #pragma unroll
-                for (int q = 0; q < ACC; ++q) {
-                    const float s = warp_sum(A[q]);
-                    if (lane == 0 && s != 0.f) atomicAdd(Ag + q, s);
+                        for (int i = 0; i < PIX; ++i) {
+                            if (!c[i]) continue;
+#pragma unroll
+                            for (int m = 0; m < 4; ++m) {
+                                atomicAdd(Ag + 4 * sf[i] + m, ge[i][m]);
+                                atomicAdd(Ag + 4 * sb[i] + m, gx[i][m]);
+                            }
+                        }
+                    }
+                    continue;
+                }
+                h0 = warp_sum(h0); h1 = warp_sum(h1); h2 = warp_sum(h2); hs = warp_sum(hs); hz = warp_sum(hz);
+                if (lane == 0) {
+                    atomicAdd(Ag + 4 * F + 0, h0);
+                    atomicAdd(Ag + 4 * F + 1, h1);
+                    atomicAdd(Ag + 4 * F + 2, h2);
+                    atomicAdd(Ag + 4 * F + 3, hs);
+                    atomicAdd(Ag + 4 * F + 4, hz);
+                }
+                used = __reduce_or_sync(0xffffffffu, used);
+                while (used) {
+                    const int f = __ffs(used) - 1;
+                    used &= used - 1;
+                    float v[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                    for (int i = 0; i < PIX; ++i) {
+#pragma unroll
+                        for (int m = 0; m < 4; ++m) {
+                            v[m] += (c[i] && sf[i] == f) ? ge[i][m] : 0.f;
+                            v[m] += (c[i] && sb[i] == f) ? gx[i][m] : 0.f;
+                        }
+                    }
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) v[m] = warp_sum(v[m]);
+                    if (lane == 0) {
+#pragma unroll
+                        for (int m = 0; m < 4; ++m) atomicAdd(Ag + 4 * f + m, v[m]);
+                    }
                 }
             }
         }
@@ -517,7 +617,8 @@ __global__ void __launch_bounds__(kThreadsX) k_blend_bwd_x(
 
 // ------------------------------------------------------------------- chain
 template <int V, int DEG>
-__global__ void __launch_bounds__(128) k_chain_x(PrimsDev P, CamsParam cams, const uint32_t* __restrict__ counts,
+__global__ void __launch_bounds__(128) k_chain_x(PrimsDev P, CamsParam cams, const float* __restrict__ rec,
+                                                 const uint32_t* __restrict__ counts,
                                                  const float* __restrict__ acc, float* __restrict__ dcentre,
                                                  float* __restrict__ dverts, float* __restrict__ dopacity,
                                                  float* __restrict__ dsh, int accumulate) {
@@ -571,10 +672,12 @@ __global__ void __launch_bounds__(128) k_chain_x(PrimsDev P, CamsParam cams, con
         // derivatives with the centre held fixed are taken, which are the
         // vertices' total derivatives; the centre gets the colour's gradient.
         const float cx = g.tc[0], cy = g.tc[1], icz = 1.f / g.tc[2];
+        const uint32_t meta = __float_as_uint(rec[r * RecX<V>::kFloats + 3]);
 #pragma unroll
-        for (int f = 0; f < F; ++f) {
-            const float Gp = A[4 * f], Gq = A[4 * f + 1], GL0 = A[4 * f + 2], GD0 = A[4 * f + 3];
+        for (int s = 0; s < F; ++s) {
+            const float Gp = A[4 * s], Gq = A[4 * s + 1], GL0 = A[4 * s + 2], GD0 = A[4 * s + 3];
             if (Gp == 0.f && Gq == 0.f && GL0 == 0.f && GD0 == 0.f) continue;
+            const int f = meta_face(meta, s);
             int i0, i1, i2;
             face_vertices<V>(f, i0, i1, i2);
             float n[3];
@@ -674,10 +777,11 @@ cudaError_t pre_x_t(const PrimsDev& P, const CamsParam& cams, float* rec, uint32
 }
 
 template <int V, int DEG>
-cudaError_t chain_x_t(const PrimsDev& P, const CamsParam& cams, const uint32_t* counts, const float* acc,
+cudaError_t chain_x_t(const PrimsDev& P, const CamsParam& cams, const float* rec, const uint32_t* counts,
+                      const float* acc,
                       float* dc, float* dv, float* dop, float* dsh, int accumulate, cudaStream_t st) {
     const int grid = (P.n + 127) / 128;
-    if (grid > 0) k_chain_x<V, DEG><<<grid, 128, 0, st>>>(P, cams, counts, acc, dc, dv, dop, dsh, accumulate);
+    if (grid > 0) k_chain_x<V, DEG><<<grid, 128, 0, st>>>(P, cams, rec, counts, acc, dc, dv, dop, dsh, accumulate);
     return cudaGetLastError();
 }
 
@@ -701,10 +805,10 @@ cudaError_t launch_preprocess_x(int V, int deg, const PrimsDev& P, const CamsPar
 #undef CALL
 }
 
-cudaError_t launch_chain_x(int V, int deg, const PrimsDev& P, const CamsParam& cams, const uint32_t* counts,
-                           const float* acc, float* dc, float* dv, float* dop, float* dsh, int accumulate,
-                           cudaStream_t st) {
-#define CALL(v, d) chain_x_t<v, d>(P, cams, counts, acc, dc, dv, dop, dsh, accumulate, st)
+cudaError_t launch_chain_x(int V, int deg, const PrimsDev& P, const CamsParam& cams, const float* rec,
+                           const uint32_t* counts, const float* acc, float* dc, float* dv, float* dop, float* dsh,
+                           int accumulate, cudaStream_t st) {
+#define CALL(v, d) chain_x_t<v, d>(P, cams, rec, counts, acc, dc, dv, dop, dsh, accumulate, st)
     LP_X_DISPATCH(V, deg, CALL)
 #undef CALL
 }

@@ -82,9 +82,9 @@ int rec_floats_x(int V);
 int acc_floats_x(int V);
 cudaError_t launch_preprocess_x(int V, int deg, const PrimsDev& P, const CamsParam& cams, float* rec,
                                 uint32_t* counts, int4* trect, uint32_t* zbits, cudaStream_t st);
-cudaError_t launch_chain_x(int V, int deg, const PrimsDev& P, const CamsParam& cams, const uint32_t* counts,
-                           const float* acc, float* dc, float* dv, float* dop, float* dsh, int accumulate,
-                           cudaStream_t st);
+cudaError_t launch_chain_x(int V, int deg, const PrimsDev& P, const CamsParam& cams, const float* rec,
+                           const uint32_t* counts, const float* acc, float* dc, float* dv, float* dop, float* dsh,
+                           int accumulate, cudaStream_t st);
 cudaError_t launch_blend_fwd_x(int V, const BlendArgs& a, cudaStream_t st);
 cudaError_t launch_blend_bwd_x(int V, const BlendArgs& a, cudaStream_t st);
 int blend_x_occupancy(int V, bool fwd);
