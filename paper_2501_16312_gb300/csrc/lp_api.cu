@@ -40,7 +40,7 @@ struct lp_ctx {
     char err[512] = {0};
 
     DevBuf<float> rec;
-    DevBuf<uint32_t> counts, offsets, zbits, scan_tmp, hist, last, emit_part;
+    DevBuf<uint32_t> counts, offsets, zbits, scan_tmp, hist, last, emit_part, contrib;
     DevBuf<int4> trect;
     DevBuf<uint64_t> keys0, keys1;
     DevBuf<uint32_t> vals0, vals1;
@@ -275,6 +275,7 @@ void lp_destroy(lp_ctx* ctx) {
     cudaDeviceSynchronize();
     release(ctx->rec); release(ctx->counts); release(ctx->offsets); release(ctx->zbits);
     release(ctx->scan_tmp); release(ctx->hist); release(ctx->last); release(ctx->trect); release(ctx->emit_part);
+    release(ctx->contrib);
     release(ctx->keys0); release(ctx->keys1); release(ctx->vals0); release(ctx->vals1);
     release(ctx->ranges); release(ctx->tl); release(ctx->acc); release(ctx->scratch_image);
     release(ctx->dkeys0); release(ctx->dkeys1); release(ctx->dvals0); release(ctx->dvals1);
@@ -365,6 +366,7 @@ static lp_status reserve_impl(lp_ctx* ctx, long long records, long long entries,
     long long sb2 = lp::scan_blocks((long long)lp::sort_hist_elems(hmax));
     LP_TRY(ensure(ctx, ctx->scan_tmp, sb > sb2 ? sb : sb2, false, "scan blocks"));
     LP_TRY(ensure(ctx, ctx->emit_part, (long long)lp::emit_blocks(records, kcap) + 1, false, "emit partition"));
+    LP_TRY(ensure(ctx, ctx->contrib, kcap / 32 + 2, false, "contributor mask"));
     LP_TRY(ensure(ctx, ctx->ranges, tiles, false, "tile ranges"));
     LP_TRY(ensure(ctx, ctx->last, pixels, false, "pixel state"));
     LP_TRY(ensure(ctx, ctx->tl, pixels, false, "pixel state"));
@@ -471,6 +473,7 @@ lp_status lp_render_forward(lp_ctx* ctx, const lp_prims* prims, const lp_camera*
                   "scan blocks"));
     LP_TRY(ensure(ctx, ctx->emit_part, (long long)lp::emit_blocks(records, bound) + 1, cap_mode,
                   "emit partition"));
+    LP_TRY(ensure(ctx, ctx->contrib, bound / 32 + 2, cap_mode, "contributor mask"));
 
     const int tile_bits = bits_for(tiles);
     int key_bits;
@@ -523,6 +526,10 @@ lp_status lp_render_forward(lp_ctx* ctx, const lp_prims* prims, const lp_camera*
     a.tile_counter = ctx->d_tile_counter;
     a.pair_counts = ctx->d_pairs;
     a.count = false;
+    if (!exact) {
+        a.contrib = ctx->contrib.p;
+        LP_CUDA(cudaMemsetAsync(ctx->contrib.p, 0, (size_t)(bound / 32 + 2) * sizeof(uint32_t), st));
+    }
     LP_CUDA(cudaMemsetAsync(ctx->d_tile_counter, 0, sizeof(int), st));
     if (a.grid > 0) {
         if (exact) LP_CUDA(lp::launch_blend_fwd_x(V, a, st));
@@ -578,6 +585,7 @@ lp_status lp_render_backward(lp_ctx* ctx, const float* dL_dimages, float* dcentr
     a.last = ctx->last.p;
     a.tl = ctx->tl.p;
     a.acc = ctx->acc.p;
+    a.contrib = exact ? nullptr : ctx->contrib.p;
     a.tile_counter = ctx->d_tile_counter + 1;
     LP_CUDA(cudaMemsetAsync(ctx->d_tile_counter + 1, 0, sizeof(int), st));
     if (a.grid > 0) {

@@ -1,5 +1,8 @@
 // Backward per-tile rasterization (sm_103a).
 //
+// Entries the forward blended at no pixel of their tile (its per-entry mask)
+// are skipped without evaluating their spans.
+//
 // Sec. 3.4 "Rasterization Backpropagation": each tile walks its list back to
 // front from the furthest last contributor of its pixels, recomputes every
 // span bit-identically to the forward (same staging, same span routine),
@@ -29,7 +32,7 @@ __global__ void __launch_bounds__(kTilePixels / PIX) k_blend_bwd(
     const float* __restrict__ rec, const uint32_t* __restrict__ vals, const uint2* __restrict__ ranges,
     CamsParam cams, float bg0, float bg1, float bg2, const float* __restrict__ dimage,
     const uint32_t* __restrict__ last_in, const float* __restrict__ tl_in, float* __restrict__ acc,
-    int* __restrict__ tile_counter) {
+    int* __restrict__ tile_counter, const uint32_t* __restrict__ contrib) {
     constexpr int F = Kind<V>::F;
     constexpr int ACC = Acc<V>::kFloats;
     constexpr int NT = kTilePixels / PIX;
@@ -81,8 +84,13 @@ __global__ void __launch_bounds__(kTilePixels / PIX) k_blend_bwd(
             for (int j = tid; j < nb; j += NT) stage_record<V>(rec, vals[rg.x + lo + j], tg.tx0, tg.ty0, sm[j]);
             __syncthreads();
             for (int j = nb - 1; j >= 0; --j) {
-                const Staged<V>& p = sm[j];
                 const uint32_t idx = (uint32_t)(lo + j);
+                if (contrib) {
+                    // the forward blended this entry at no pixel of the tile
+                    const uint32_t e = rg.x + idx;
+                    if (!((__ldg(contrib + (e >> 5)) >> (e & 31u)) & 1u)) continue;
+                }
+                const Staged<V>& p = sm[j];
                 bool any = false;
 #pragma unroll
                 for (int i = 0; i < PIX; ++i) any |= idx < last[i];
@@ -195,7 +203,7 @@ template <int V, int BATCH, int PIX>
 cudaError_t bwd_t(const BlendArgs& a, cudaStream_t st) {
     k_blend_bwd<V, BATCH, PIX><<<a.grid, kTilePixels / PIX, 0, st>>>(
         a.rec, a.vals, a.ranges, *a.cams, a.bg[0], a.bg[1], a.bg[2], a.dimage, a.last, a.tl, a.acc,
-        a.tile_counter);
+        a.tile_counter, a.contrib);
     return cudaGetLastError();
 }
 

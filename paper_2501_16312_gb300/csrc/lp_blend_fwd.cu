@@ -25,7 +25,8 @@ __global__ void __launch_bounds__(kTilePixels / PIX) k_blend_fwd(
     const float* __restrict__ rec, const uint32_t* __restrict__ vals, const uint2* __restrict__ ranges,
     CamsParam cams, float bg0, float bg1, float bg2, float* __restrict__ image,
     uint32_t* __restrict__ last_out, float* __restrict__ tl_out, int* __restrict__ tile_counter,
-    unsigned long long* __restrict__ pair_counts, float* __restrict__ depth_out) {
+    unsigned long long* __restrict__ pair_counts, float* __restrict__ depth_out,
+    uint32_t* __restrict__ contrib) {
     constexpr bool COUNT = MODE == 1;
     constexpr bool DEPTH = MODE == 2;
     constexpr float kStop = DEPTH ? 0.5f : kStopT;
@@ -34,7 +35,9 @@ __global__ void __launch_bounds__(kTilePixels / PIX) k_blend_fwd(
     __shared__ Staged<V> sm[BATCH];
     __shared__ int s_tile;
     const int tid = threadIdx.x;
+    const int lane = tid & 31;
     const int ly = tid / RW, lx0 = (tid % RW) * PIX;
+    const bool write_mask = !DEPTH && contrib != nullptr;
     unsigned long long n_iter = 0, n_eval = 0, n_hit = 0, n_eval_last = 0;
     for (;;) {
         if (tid == 0) s_tile = atomicAdd(tile_counter, 1);
@@ -64,43 +67,63 @@ __global__ void __launch_bounds__(kTilePixels / PIX) k_blend_fwd(
             const int nb = min(BATCH, n - b0);
             for (int j = tid; j < nb; j += NT) stage_record<V>(rec, vals[rg.x + b0 + j], tg.tx0, tg.ty0, sm[j]);
             __syncthreads();
-            if (!tdone) {
-                for (int j = 0; j < nb; ++j) {
-                    const Staged<V>& p = sm[j];
-                    if (COUNT) {
+            if (__any_sync(0xffffffffu, !tdone)) {   // warp-uniform, as the exit below
+                bool stop = false;
+                for (int jw = 0; jw < nb && !stop; jw += 32) {
+                    uint32_t bm = 0;   // bit j - jw: this thread blended entry b0 + j
+                    const int je = min(nb, jw + 32);
+                    for (int j = jw; j < je; ++j) {
+                        const Staged<V>& p = sm[j];
+                        if (COUNT) {
 #pragma unroll
-                        for (int i = 0; i < PIX; ++i) n_iter += !done[i];
-                    }
-                    float sp[PIX];
-                    spans<V, PIX, false>(p, (float)lx0, (float)ly, sp, nullptr, nullptr);
-                    tdone = true;
-#pragma unroll
-                    for (int i = 0; i < PIX; ++i) {
-                        const bool in = !done[i];   // every visited entry is evaluated
-                        if (COUNT) { n_eval += in; ce[i] += in; }
-                        if (in && sp[i] > 0.f) {
-                            if (COUNT) { ++n_hit; cl[i] = ce[i]; }
-                            const float tau = span_tau(p.sigma, sp[i]);
-                            const float w = T[i] * (1.f - tau);
-                            c0[i] = fmaf(w, p.r, c0[i]);
-                            c1[i] = fmaf(w, p.g, c1[i]);
-                            c2[i] = fmaf(w, p.b, c2[i]);
-                            tl[i] = T[i];
-                            T[i] *= tau;
-                            last[i] = (uint32_t)(b0 + j + 1);
-                            done[i] = T[i] < kStop;
-                            if (DEPTH && done[i]) {
-                                // entry depth: centre depth + max over the entry faces
-                                float e = -CUDART_INF_F;
-                                for (int f = 0; f < p.nf; ++f)
-                                    e = fmaxf(e, __fmaf_rn(p.pl[f].x, (float)(lx0 + i),
-                                                           __fmaf_rn(p.pl[f].y, (float)ly, p.pl[f].z)));
-                                dep[i] = __fadd_rn(p.pl[0].w, e);
-                            }
+                            for (int i = 0; i < PIX; ++i) n_iter += !done[i];
                         }
-                        tdone &= done[i];
+                        float sp[PIX];
+                        spans<V, PIX, false>(p, (float)lx0, (float)ly, sp, nullptr, nullptr);
+                        tdone = true;
+                        bool blended = false;
+#pragma unroll
+                        for (int i = 0; i < PIX; ++i) {
+                            const bool in = !done[i];   // every visited entry is evaluated
+                            if (COUNT) { n_eval += in; ce[i] += in; }
+                            if (in && sp[i] > 0.f) {
+                                blended = true;
+                                if (COUNT) { ++n_hit; cl[i] = ce[i]; }
+                                const float tau = span_tau(p.sigma, sp[i]);
+                                const float w = T[i] * (1.f - tau);
+                                c0[i] = fmaf(w, p.r, c0[i]);
+                                c1[i] = fmaf(w, p.g, c1[i]);
+                                c2[i] = fmaf(w, p.b, c2[i]);
+                                tl[i] = T[i];
+                                T[i] *= tau;
+                                last[i] = (uint32_t)(b0 + j + 1);
+                                done[i] = T[i] < kStop;
+                                if (DEPTH && done[i]) {
+                                    // entry depth: centre depth + max over the entry faces
+                                    float e = -CUDART_INF_F;
+                                    for (int f = 0; f < p.nf; ++f)
+                                        e = fmaxf(e, __fmaf_rn(p.pl[f].x, (float)(lx0 + i),
+                                                               __fmaf_rn(p.pl[f].y, (float)ly, p.pl[f].z)));
+                                    dep[i] = __fadd_rn(p.pl[0].w, e);
+                                }
+                            }
+                            tdone &= done[i];
+                        }
+                        if (write_mask && blended) bm |= 1u << (j - jw);
+                        // warp-uniform exit (the mask reduction below needs every
+                        // lane); a warp issues the loop while any lane is active
+                        if (__all_sync(0xffffffffu, tdone)) { stop = true; break; }
                     }
-                    if (tdone) break;
+                    if (write_mask) {
+                        // entries b0 + jw .. b0 + jw + 31 of the tile's list
+                        bm = __reduce_or_sync(0xffffffffu, bm);
+                        if (lane == 0 && bm) {
+                            const uint32_t e0 = rg.x + (uint32_t)(b0 + jw);
+                            const uint32_t w = e0 >> 5, sh = e0 & 31u;
+                            atomicOr(contrib + w, bm << sh);
+                            if (sh) atomicOr(contrib + w + 1, bm >> (32u - sh));
+                        }
+                    }
                 }
             }
         }
@@ -152,15 +175,15 @@ cudaError_t fwd_t(const BlendArgs& a, cudaStream_t st) {
     if (a.depth)
         k_blend_fwd<V, BATCH, PIX, 2><<<a.grid, NT, 0, st>>>(
             a.rec, a.vals, a.ranges, *a.cams, a.bg[0], a.bg[1], a.bg[2], a.image, a.last, a.tl,
-            a.tile_counter, a.pair_counts, a.depth);
+            a.tile_counter, a.pair_counts, a.depth, nullptr);
     else if (a.count)
         k_blend_fwd<V, BATCH, PIX, 1><<<a.grid, NT, 0, st>>>(
             a.rec, a.vals, a.ranges, *a.cams, a.bg[0], a.bg[1], a.bg[2], a.image, a.last, a.tl,
-            a.tile_counter, a.pair_counts, nullptr);
+            a.tile_counter, a.pair_counts, nullptr, a.contrib);
     else
         k_blend_fwd<V, BATCH, PIX, 0><<<a.grid, NT, 0, st>>>(
             a.rec, a.vals, a.ranges, *a.cams, a.bg[0], a.bg[1], a.bg[2], a.image, a.last, a.tl,
-            a.tile_counter, a.pair_counts, nullptr);
+            a.tile_counter, a.pair_counts, nullptr, a.contrib);
     return cudaGetLastError();
 }
 

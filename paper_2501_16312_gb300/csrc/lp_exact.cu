@@ -249,8 +249,7 @@ __device__ __forceinline__ void spans_x_nf(const StagedX<V>& s, float lx0, float
             if (ARG) { sf[i] = 0; sb[i] = F - 1; }
             if (ent_out) ent_out[i] = 0.f;
         }
-        return;
-    }
+    } else {
     float en[PIX], ex[PIX];
 #pragma unroll
     for (int i = 0; i < PIX; ++i) {
@@ -283,6 +282,7 @@ __device__ __forceinline__ void spans_x_nf(const StagedX<V>& s, float lx0, float
         sp[i] = __fmul_rn(__fsub_rn(ex[i], en[i]), rn[i]);   // +inf - inf, -inf: no hit
         if (!(sp[i] < CUDART_INF_F)) sp[i] = -1.f;
         if (ent_out) ent_out[i] = en[i];
+    }
     }
 }
 

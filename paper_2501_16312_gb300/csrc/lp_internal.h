@@ -70,6 +70,8 @@ struct BlendArgs {
     unsigned long long* pair_counts;
     bool count;
     float* depth;          // depth pass output (forward kernel in depth mode when non-null)
+    uint32_t* contrib;     // one bit per tile-list entry: it contributes to some pixel of its tile
+                           // (written by the forward when non-null, read by the backward)
 };
 
 cudaError_t launch_blend_fwd(int V, int batch, int pix, const BlendArgs& a, cudaStream_t st);
