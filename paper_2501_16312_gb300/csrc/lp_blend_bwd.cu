@@ -168,12 +168,11 @@ __global__ void __launch_bounds__(kTilePixels / PIX) k_blend_bwd(
                     }
                     continue;
                 }
-                gr0 = warp_sum(gr0); gr1 = warp_sum(gr1); gr2 = warp_sum(gr2); gsig = warp_sum(gsig);
-                if (lane == 0) {
-                    atomicAdd(A + 3 * F + 0, gr0);
-                    atomicAdd(A + 3 * F + 1, gr1);
-                    atomicAdd(A + 3 * F + 2, gr2);
-                    atomicAdd(A + 3 * F + 3, gsig);
+                {
+                    // colour and sigma: four totals, one per lane group of 8
+                    float hv[4] = {gr0, gr1, gr2, gsig};
+                    const float t = warp_sum_multi<4>(hv, lane);
+                    if ((lane & 7) == 0) atomicAdd(A + 3 * F + warp_sum_index<4>(lane), t);
                 }
                 used = __reduce_or_sync(0xffffffffu, used);
                 while (used) {
