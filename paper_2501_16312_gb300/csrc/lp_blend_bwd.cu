@@ -101,7 +101,9 @@ __global__ void __launch_bounds__(kTilePixels / PIX) k_blend_bwd(
 #pragma unroll
                 for (int i = 0; i < PIX; ++i) c[i] = false;
                 if (any) {
-                    spans<V, PIX, false>(p, (float)lx0, (float)ly, sp, nullptr, nullptr);
+                    // one pass with the entry/exit slots: with entries that no
+                    // pixel of the tile blended skipped, most warps contribute
+                    spans<V, PIX, true>(p, (float)lx0, (float)ly, sp, sf, sb);
 #pragma unroll
                     for (int i = 0; i < PIX; ++i) {
                         c[i] = idx < last[i] && sp[i] > 0.f;
@@ -116,8 +118,6 @@ __global__ void __launch_bounds__(kTilePixels / PIX) k_blend_bwd(
 #pragma unroll
                 for (int i = 0; i < PIX; ++i) gsp[i] = 0.f;
                 if (anyc) {
-                    // entry/exit faces only where a pixel contributes (same spans)
-                    spans<V, PIX, true>(p, (float)lx0, (float)ly, sp, sf, sb);
 #pragma unroll
                     for (int i = 0; i < PIX; ++i) {
                         if (c[i]) {
