@@ -23,9 +23,10 @@ namespace lp {
 
 namespace {
 
-// Warps with at most this many contributing lanes skip the shuffle
+// Warps with at most this many contributing lanes (8: measured best on both
+// the 500k-octahedron and the 1M-tetrahedron workloads) skip the shuffle
 // reductions and let each contributing lane issue its own atomic adds.
-constexpr int kSparseLanes = 4;
+constexpr int kSparseLanes = 8;
 
 // 768 resident threads per SM (at most 80 registers): measured faster than
 // the 96-register schedule the compiler picks on its own.
