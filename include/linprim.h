@@ -184,6 +184,27 @@ lp_status lp_render_depth(lp_ctx* ctx, float* depth, void* stream);
 lp_status lp_set_filter_2d(lp_ctx* ctx, float kernel_px);
 lp_status lp_get_filter_2d(lp_ctx* ctx, float* kernel_px);
 
+/* Densification statistics (Sec. 3.4 "Adaptive Population Control", App.
+ * "Experimental Setting"), gathered into caller-owned device arrays of at
+ * least n primitives, indexed like lp_prims, by every later call on the
+ * context until they are unset:
+ *   px_max      unsigned[n]: each forward raises it to the largest side, in
+ *               pixels, of the primitive's pixel rectangle (clipped to the
+ *               image) over the forward's cameras;
+ *   grad_sum    float[n]: each backward adds, for every camera in which the
+ *               primitive has a non-empty pixel rectangle, the norm of the
+ *               view-space position gradient -- the gradient of the loss
+ *               w.r.t. a translation of the whole primitive (centre and
+ *               vertices) parallel to that camera's image plane, in NDC units
+ *               (x_ndc = 2 x_px / W - 1);
+ *   grad_count  unsigned[n]: each backward adds the number of those cameras.
+ * The caller zeroes the arrays; one thread updates each primitive, so no two
+ * calls may run concurrently on them.  All three NULL turns gathering off (the
+ * default).  Calls with more than n primitives fail with LP_ERR_INVALID.
+ * Errors: LP_ERR_INVALID if only some pointers are NULL or n < 0.          */
+lp_status lp_set_densify_stats(lp_ctx* ctx, float* grad_sum, unsigned int* grad_count,
+                               unsigned int* px_max, long long n);
+
 /* Pre-size the library-owned workspace.  Needed before a forward/backward
  * pair is captured into a CUDA graph: a captured call cannot read the
  * tile-list length back, so it uses this capacity and latches
@@ -322,6 +343,73 @@ typedef struct {
 } lp_adam_group;
 lp_status lp_adam_step(float* params, const float* grads, float* m, float* v, const lp_adam_group* groups,
                        int n_groups, float beta1, float beta2, float eps, int* step, void* stream);
+
+/* Population control (Sec. 3.4 "Adaptive Population Control"; thresholds of
+ * App. "Experimental Setting": opacity 0.025, 40% of the scene, 20 pixels,
+ * gradient 1.5e-4, 1% of the scene, children 1/1.2 the size).
+ *
+ * Size of a primitive: an octahedron's longest axis 2 max_i |d_i|, a
+ * tetrahedron's sqrt(2) max_k |d_k| (binary32, single rounding).
+ *
+ * lp_population_decide: action[i] (unsigned char) =
+ *   LP_POP_PRUNE if logit < (float)log(min_opacity / (1 - min_opacity)) or
+ *                size > max_scene_frac * scene_extent or px_max > max_pixels;
+ *   else LP_POP_CLONE / LP_POP_SPLIT if grad_count > 0 and
+ *                grad_sum / grad_count > grad_threshold, cloned when size <
+ *                clone_scene_frac * scene_extent, split otherwise;
+ *   else LP_POP_KEEP.
+ * (products and the quotient rounded to binary32 once each), dest[i] = the
+ * exclusive prefix sum of the output counts 0 / 1 / 2 / 2, *n_out (device
+ * unsigned) = their total.  dist float[n][D], logit float[n] and the
+ * statistics (see lp_set_densify_stats) are inputs.  scratch: device,
+ * lp_population_scratch(n) unsigned ints.  Errors: LP_ERR_INVALID for a bad
+ * kind, n < 0, NULL pointers or rules outside (0, inf).                   */
+#define LP_POP_PRUNE 0
+#define LP_POP_KEEP 1
+#define LP_POP_CLONE 2
+#define LP_POP_SPLIT 3
+typedef struct {
+    float scene_extent;
+    float min_opacity;
+    float max_scene_frac;
+    unsigned int max_pixels;
+    float grad_threshold;
+    float clone_scene_frac;
+} lp_population_rules;
+long long lp_population_scratch(long long n);
+lp_status lp_population_decide(int kind, int n, const float* dist, const float* logit, const float* grad_sum,
+                               const unsigned int* grad_count, const unsigned int* px_max,
+                               const lp_population_rules* rules, unsigned char* action, unsigned int* dest,
+                               unsigned int* n_out, unsigned int* scratch, void* stream);
+
+/* lp_population_apply: the new population, written to dst[s] for each of
+ * n_sets array sets (device float arrays in the layout of lp_params_forward:
+ * centre [n][3], quat [n][4], dist [n][D], logit [n], sh [n][sh_coeffs][3]).
+ * Set 0 holds the parameters, sets 1.. per-parameter optimiser state (Adam's
+ * moments).  Primitive i goes to rows dest[i].. of every set:
+ *   KEEP   one row, a copy;
+ *   CLONE  two rows: the copy, then a clone with the same parameters and
+ *          zero state (Sec. 3.4);
+ *   SPLIT  two children with the origin's quat, logit and sh, distances
+ *          d / 1.2, zero state, and centres c + R(q) (|d| * z_j) (octahedron:
+ *          standard deviations equal to the distances along the rotated axes)
+ *          or c + (max |d| / 2) z_j (tetrahedron), z_j = normals[i][j][0..2]
+ *          (device float[n][2][3], standard-normal draws of the caller);
+ *   PRUNE  nothing.
+ * dst arrays hold at least *n_out rows and must not overlap src.  action and
+ * dest come from lp_population_decide.  1 <= n_sets <= 4.
+ * Errors: LP_ERR_INVALID for a bad kind, sh_coeffs not in {1, 4, 9, 16},
+ * n < 0, NULL pointers.                                                    */
+typedef struct {
+    float* centre;
+    float* quat;
+    float* dist;
+    float* logit;
+    float* sh;
+} lp_param_arrays;
+lp_status lp_population_apply(int kind, int sh_coeffs, int n, const unsigned char* action,
+                              const unsigned int* dest, const float* normals, const lp_param_arrays* src,
+                              const lp_param_arrays* dst, int n_sets, void* stream);
 
 /* Allocation-free forward render of ONE camera.  The paper has no
  * counterpart: this entry point exists for callers that cannot call

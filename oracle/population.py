@@ -12,7 +12,8 @@ Readings of the paper (each also listed with the design notes):
     tetrahedron's sqrt(2) times the distance to its furthest corner (Sec. 3.4).
     Distances enter by magnitude.
   * prune (App.): opacity sigmoid(logit) below 0.025 -- decided as logit below
-    the binary32 rounding of log(0.025 / 0.975); size above 40% of the scene
+    the binary32 rounding of log(p / (1 - p)), p the binary32 0.025 evaluated
+    in binary64; size above 40% of the scene
     extent; or more than 20 pixels of a known view -- the largest side, in
     pixels, of the primitive's pixel rectangle (clipped to the image) over the
     views rendered since the last adjustment.
@@ -97,17 +98,17 @@ def view_gradient(camera, centre, g_centre, g_verts):
     return np.stack([gx, gy], axis=1)
 
 
-def gradient_stats(orc, scene, cameras, dL_dimage, aa=0.0, exact=False):
+def gradient_stats(orc, scene, cameras, dL_dimage, bg=(0.0, 0.0, 0.0), aa=0.0, exact=False):
     """(sum of view-space gradient norms, number of visible views) per
     primitive for one backward over `cameras` with image gradient dL_dimage
-    (the cameras' images concatenated, [H, W, 3] each)."""
+    (the cameras' images concatenated, 3 H W floats each)."""
     dL = np.asarray(dL_dimage, np.float64).reshape(-1)
     acc = np.zeros(scene.n)
     cnt = np.zeros(scene.n, np.int64)
     off = 0
     for cam in cameras:
         m = 3 * cam.width * cam.height
-        _, g = orc.render(scene, [cam], dL_dimage=dL[off:off + m], aa=aa, exact=exact)
+        _, g = orc.render(scene, [cam], bg=bg, dL_dimage=dL[off:off + m], aa=aa, exact=exact)
         off += m
         pp = orc.preprocess(scene, cam, aa=aa, exact=exact)
         r = pp["rect"]
@@ -120,14 +121,16 @@ def gradient_stats(orc, scene, cameras, dL_dimage, aa=0.0, exact=False):
 
 # ------------------------------------------------------------ decision
 
-def decide(kind, dist, logit, grad_sum, grad_count, max_pixels, scene_extent):
-    """Per primitive: PRUNE, KEEP, CLONE or SPLIT (binary32 decisions)."""
+def decide(kind, dist, logit, grad_sum, grad_count, max_pixels, scene_extent, grad_threshold=DENSIFY_GRAD):
+    """Per primitive: PRUNE, KEEP, CLONE or SPLIT (binary32 decisions).  The
+    thresholds are the paper's; the gradient one may be overridden."""
     n = len(logit)
     act = np.zeros(n, np.int64)
-    logit_min = f32(math.log(PRUNE_OPACITY / (1.0 - PRUNE_OPACITY)))
+    p = float(f32(PRUNE_OPACITY))          # the threshold is a binary32 operand
+    logit_min = f32(math.log(p / (1.0 - p)))
     big = f32(f32(PRUNE_SCENE_FRAC) * f32(scene_extent))
     small = f32(f32(CLONE_SCENE_FRAC) * f32(scene_extent))
-    thr = f32(DENSIFY_GRAD)
+    thr = f32(grad_threshold)
     for i in range(n):
         s = size32(kind, dist[i])
         if f32(logit[i]) < logit_min or s > big or int(max_pixels[i]) > PRUNE_PIXELS:

@@ -119,6 +119,21 @@ class Rasterizer:
         forward calls."""
         _native.check(self.ctx, self.lib.lp_set_exact(self.ctx, int(bool(exact))), "lp_set_exact")
 
+    def set_densify_stats(self, grad_sum=None, grad_count=None, px_max=None):
+        """Gather densification statistics (Sec. 3.4 "Adaptive Population
+        Control") into device tensors of one entry per primitive: float32
+        grad_sum and int32 grad_count (view-space position-gradient norms and
+        visible views, added by each backward) and int32 px_max (largest
+        pixel-rectangle side, raised by each forward).  No arguments: stop."""
+        ts = (grad_sum, grad_count, px_max)
+        if all(t is None for t in ts):
+            st = self.lib.lp_set_densify_stats(self.ctx, None, None, None, 0)
+        else:
+            n = min(int(t.numel()) for t in ts)
+            st = self.lib.lp_set_densify_stats(self.ctx, _fptr(grad_sum), _fptr(grad_count), _fptr(px_max), n)
+        _native.check(self.ctx, st, "lp_set_densify_stats")
+        self._densify_stats = ts
+
     def exact(self) -> bool:
         v = C.c_int()
         _native.check(self.ctx, self.lib.lp_get_exact(self.ctx, C.byref(v)), "lp_get_exact")

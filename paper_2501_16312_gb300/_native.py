@@ -21,7 +21,8 @@ EXPORTS = ("lp_create", "lp_destroy", "lp_set_tuning", "lp_get_tuning", "lp_set_
            "lp_debug_keys", "lp_debug_counts", "lp_debug_pixel_state", "lp_count_pairs",
            "lp_last_error", "lp_status_string", "lp_set_timing", "lp_stage_times",
            "lp_render_forward_noalloc", "lp_params_forward", "lp_params_backward",
-           "lp_l1_loss_grad", "lp_adam_step", "lp_render_depth", "lp_set_exact", "lp_get_exact")
+           "lp_l1_loss_grad", "lp_adam_step", "lp_render_depth", "lp_set_exact", "lp_get_exact",
+           "lp_set_densify_stats", "lp_population_scratch", "lp_population_decide", "lp_population_apply")
 LP_ADAM_MAX_GROUPS = 8
 STAGES = ("preprocess", "scan_emit", "sort", "ranges", "blend_fwd", "blend_bwd", "chain")
 
@@ -52,6 +53,19 @@ class lp_adam_group(C.Structure):
     _fields_ = [("offset", C.c_longlong), ("count", C.c_longlong), ("lr", C.c_float),
                 ("lr_final", C.c_float), ("decay_steps", C.c_int), ("period", C.c_int),
                 ("head", C.c_int), ("lr_tail", C.c_float)]
+
+
+LP_POP_PRUNE, LP_POP_KEEP, LP_POP_CLONE, LP_POP_SPLIT = range(4)
+
+
+class lp_population_rules(C.Structure):
+    _fields_ = [("scene_extent", C.c_float), ("min_opacity", C.c_float), ("max_scene_frac", C.c_float),
+                ("max_pixels", C.c_uint), ("grad_threshold", C.c_float), ("clone_scene_frac", C.c_float)]
+
+
+class lp_param_arrays(C.Structure):
+    _fields_ = [("centre", C.c_void_p), ("quat", C.c_void_p), ("dist", C.c_void_p), ("logit", C.c_void_p),
+                ("sh", C.c_void_p)]
 
 
 class LinPrimError(RuntimeError):
@@ -107,6 +121,13 @@ def load(path: str = LIB_PATH):
     L.lp_l1_loss_grad.argtypes = [vp, vp, ll, vp, vp, vp]
     L.lp_adam_step.argtypes = [vp, vp, vp, vp, C.POINTER(lp_adam_group), i, C.c_float, C.c_float,
                                C.c_float, vp, vp]
+    L.lp_set_densify_stats.argtypes = [vp, vp, vp, vp, ll]
+    L.lp_population_scratch.argtypes = [ll]
+    L.lp_population_scratch.restype = ll
+    L.lp_population_decide.argtypes = [i, i, vp, vp, vp, vp, vp, C.POINTER(lp_population_rules), vp, vp, vp,
+                                       vp, vp]
+    L.lp_population_apply.argtypes = [i, i, i, vp, vp, vp, C.POINTER(lp_param_arrays),
+                                      C.POINTER(lp_param_arrays), i, vp]
     for name in EXPORTS:
         getattr(L, name)
     _lib = L

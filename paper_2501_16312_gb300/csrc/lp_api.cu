@@ -37,6 +37,11 @@ struct lp_ctx {
     float aa_kernel = 0.f;      // 2D filter size in pixels (0 = off)
     bool exact = false;         // spans along the true perspective ray
     bool fwd_exact = false;     // mode of the last forward
+    // densification statistics gathered by forward and backward (null: off)
+    float* st_grad_sum = nullptr;
+    uint32_t* st_grad_count = nullptr;
+    uint32_t* st_px_max = nullptr;
+    long long st_n = 0;
     char err[512] = {0};
 
     DevBuf<float> rec;
@@ -319,6 +324,19 @@ lp_status lp_set_filter_2d(lp_ctx* ctx, float kernel_px) {
     return LP_OK;
 }
 
+lp_status lp_set_densify_stats(lp_ctx* ctx, float* grad_sum, unsigned int* grad_count,
+                               unsigned int* px_max, long long n) {
+    if (!ctx) return LP_ERR_INVALID;
+    const bool none = !grad_sum && !grad_count && !px_max;
+    if (!none && (!grad_sum || !grad_count || !px_max || n < 0))
+        return fail(ctx, LP_ERR_INVALID, "densification statistics need all three arrays and n >= 0");
+    ctx->st_grad_sum = grad_sum;
+    ctx->st_grad_count = grad_count;
+    ctx->st_px_max = px_max;
+    ctx->st_n = none ? 0 : n;
+    return LP_OK;
+}
+
 lp_status lp_set_exact(lp_ctx* ctx, int exact) {
     if (!ctx) return LP_ERR_INVALID;
     ctx->exact = exact != 0;
@@ -419,6 +437,12 @@ lp_status lp_render_forward(lp_ctx* ctx, const lp_prims* prims, const lp_camera*
     LP_TRY(ensure(ctx, ctx->tl, pixels, cap_mode, "pixel state"));
 
     lp::PrimsDev P{prims->n, prims->centre, prims->verts, prims->opacity, prims->sh};
+    if (ctx->st_px_max) {
+        if (prims->n > ctx->st_n)
+            return fail(ctx, LP_ERR_INVALID, "densification statistics hold %lld primitives, the call has %d",
+                        ctx->st_n, prims->n);
+        P.px_max = ctx->st_px_max;
+    }
     mark(ctx, st, 0, cap_mode);
     if (exact)
         LP_CUDA(lp::launch_preprocess_x(V, prims->sh_degree, P, cp, ctx->rec.p, ctx->counts.p, ctx->trect.p,
@@ -595,6 +619,13 @@ lp_status lp_render_backward(lp_ctx* ctx, const float* dL_dimages, float* dcentr
     mark(ctx, st, 7, cap_mode);
 
     lp::PrimsDev P{pr.n, pr.centre, pr.verts, pr.opacity, pr.sh};
+    if (ctx->st_grad_sum) {
+        if (pr.n > ctx->st_n)
+            return fail(ctx, LP_ERR_INVALID, "densification statistics hold %lld primitives, the call has %d",
+                        ctx->st_n, pr.n);
+        P.grad_sum = ctx->st_grad_sum;
+        P.grad_count = ctx->st_grad_count;
+    }
     if (exact)
         LP_CUDA(lp::launch_chain_x(V, pr.sh_degree, P, ctx->cams, ctx->rec.p, ctx->counts.p, ctx->acc.p, dcentre,
                                    dverts, dopacity, dsh, accumulate, st));

@@ -47,7 +47,22 @@ struct PrimsDev {
     const float* verts;
     const float* opacity;
     const float* sh;
+    // Densification statistics (App. "Experimental Setting"), null when not
+    // gathered: the forward raises px_max to the largest pixel-rectangle side
+    // of each view, the backward adds each visible view's view-space position
+    // gradient norm to grad_sum and counts the view in grad_count.
+    uint32_t* px_max = nullptr;
+    float* grad_sum = nullptr;
+    uint32_t* grad_count = nullptr;
 };
+
+// NDC norm of a camera-space translation gradient g (the primitive moved
+// parallel to the image plane at depth z): d x_ndc = 2 f_x / (W z) d t_x.
+__device__ __forceinline__ float ndc_grad_norm(const CamDev& cm, const float g[3], float z) {
+    const float gx = g[0] * (float)cm.width * z / (2.f * cm.fx);
+    const float gy = g[1] * (float)cm.height * z / (2.f * cm.fy);
+    return sqrtf(gx * gx + gy * gy);
+}
 
 template <int V> struct Kind;
 template <> struct Kind<6> { static constexpr int F = 8; };   // octahedron

@@ -105,6 +105,7 @@ __global__ void __launch_bounds__(128) k_preprocess_x(PrimsDev P, CamsParam cams
     }
     const float sigma = -log1pf(-kAlphaScale * alpha) / (2.f * dmin);
     degenerate |= !(sigma < CUDART_INF_F);
+    uint32_t px_side = 0;   // largest pixel-rectangle side over the views
 
     for (int cv = 0; cv < cams.n; ++cv) {
         const CamDev& cm = cams.cam[cv];
@@ -148,6 +149,7 @@ __global__ void __launch_bounds__(128) k_preprocess_x(PrimsDev P, CamsParam cams
         }
         const int T = cams.tile;
         const int tx0 = (int)fx0 / T, tx1 = (int)fx1 / T, ty0 = (int)fy0 / T, ty1 = (int)fy1 / T;
+        px_side = max(px_side, (uint32_t)max((int)fx1 - (int)fx0 + 1, (int)fy1 - (int)fy0 + 1));
         counts[r] = (uint32_t)((tx1 - tx0 + 1) * (ty1 - ty0 + 1));
         trect[r] = make_int4(cm.tile_base + ty0 * cm.tiles_x + tx0, cm.tiles_x, tx1 - tx0 + 1, ty1 - ty0 + 1);
 
@@ -200,6 +202,7 @@ __global__ void __launch_bounds__(128) k_preprocess_x(PrimsDev P, CamsParam cams
         for (int k = 0; k < RecX<V>::kVec4; ++k)
             dst[k] = make_float4(out[4 * k], out[4 * k + 1], out[4 * k + 2], out[4 * k + 3]);
     }
+    if (P.px_max && px_side > P.px_max[i]) P.px_max[i] = px_side;   // one thread per primitive
 }
 
 // ------------------------------------------------------------------- blend
@@ -648,10 +651,13 @@ __global__ void __launch_bounds__(128) k_chain_x(PrimsDev P, CamsParam cams, con
     for (int k = 0; k < V; ++k) gv[k][0] = gv[k][1] = gv[k][2] = 0.f;
 #pragma unroll
     for (int q = 0; q < K * 3; ++q) gsh[q] = 0.f;
+    float vg_sum = 0.f;     // view-space position-gradient norms of the visible views
+    uint32_t vg_count = 0;
 
     for (int cv = 0; cv < cams.n; ++cv) {
         const size_t r = (size_t)cv * P.n + i;
         if (counts[r] == 0) continue;
+        ++vg_count;
         const float* A = acc + r * AccX<V>::kFloats;
         bool any = false;
 #pragma unroll
@@ -743,9 +749,29 @@ __global__ void __launch_bounds__(128) k_chain_x(PrimsDev P, CamsParam cams, con
         float gdir[3];
         sh_basis_vjp<DEG>(dir[0], dir[1], dir[2], wk, gdir);
         const float dd = gdir[0] * dir[0] + gdir[1] * dir[1] + gdir[2] * dir[2];
+        float gw[3];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) gc[a] += (gdir[a] - dir[a] * dd) * idl;
+        for (int a = 0; a < 3; ++a) {
+            gw[a] = (gdir[a] - dir[a] * dd) * idl;
+            gc[a] += gw[a];
+        }
+        if (P.grad_sum) {
+            // a translation moves every vertex: camera-space gradient sum_k gd_k
+            // plus the colour's
+            float gt[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                gt[a] = cm.R[3 * a] * gw[0] + cm.R[3 * a + 1] * gw[1] + cm.R[3 * a + 2] * gw[2];
+#pragma unroll
+                for (int k = 0; k < V; ++k) gt[a] += gd[k][a];
+            }
+            vg_sum += ndc_grad_norm(cm, gt, g.tc[2]);
+        }
         gsigma += A[4 * F + 3];
+    }
+    if (P.grad_sum) {
+        P.grad_sum[i] += vg_sum;
+        P.grad_count[i] += vg_count;
     }
     const float galpha = gsigma != 0.f ? gsigma * kAlphaScale / ((1.f - kAlphaScale * alpha) * 2.f * dmin) : 0.f;
 #pragma unroll

@@ -58,6 +58,7 @@ __global__ void __launch_bounds__(128) k_preprocess(PrimsDev P, CamsParam cams, 
     // second test only catches offsets so small (below ~1e-19) that d_min
     // underflows in binary32, and a non-finite opacity.
     degenerate |= !(sigma < CUDART_INF_F);
+    uint32_t px_side = 0;   // largest pixel-rectangle side over the views
 
     for (int cv = 0; cv < cams.n; ++cv) {
         const CamDev& cm = cams.cam[cv];
@@ -97,6 +98,7 @@ __global__ void __launch_bounds__(128) k_preprocess(PrimsDev P, CamsParam cams, 
         }
         const int T = cams.tile;
         const int tx0 = (int)fx0 / T, tx1 = (int)fx1 / T, ty0 = (int)fy0 / T, ty1 = (int)fy1 / T;
+        px_side = max(px_side, (uint32_t)max((int)fx1 - (int)fx0 + 1, (int)fy1 - (int)fy0 + 1));
         counts[r] = (uint32_t)((tx1 - tx0 + 1) * (ty1 - ty0 + 1));
         // global id of the rectangle's first tile, row stride, width, height
         trect[r] = make_int4(cm.tile_base + ty0 * cm.tiles_x + tx0, cm.tiles_x, tx1 - tx0 + 1, ty1 - ty0 + 1);
@@ -166,6 +168,7 @@ __global__ void __launch_bounds__(128) k_preprocess(PrimsDev P, CamsParam cams, 
         for (int k = 0; k < Rec<V>::kVec4; ++k)
             dst[k] = make_float4(out[4 * k], out[4 * k + 1], out[4 * k + 2], out[4 * k + 3]);
     }
+    if (P.px_max && px_side > P.px_max[i]) P.px_max[i] = px_side;   // one thread per primitive
 }
 
 // ------------------------------------------------------------------ backward
@@ -208,10 +211,13 @@ __global__ void __launch_bounds__(128) k_chain(PrimsDev P, CamsParam cams,
 #pragma unroll
     for (int q = 0; q < K * 3; ++q) gsh[q] = 0.f;
     float gsigma = 0.f;
+    float vg_sum = 0.f;     // view-space position-gradient norms of the visible views
+    uint32_t vg_count = 0;
 
     for (int cv = 0; cv < cams.n; ++cv) {
         const size_t r = (size_t)cv * P.n + i;
         if (counts[r] == 0) continue;
+        ++vg_count;
         const CamDev& cm = cams.cam[cv];
         const float* A = acc + r * Acc<V>::kFloats;
         bool any = false;
@@ -279,8 +285,10 @@ __global__ void __launch_bounds__(128) k_chain(PrimsDev P, CamsParam cams,
             }
         }
 
-        // q_k = J (t_k - tc); x_c = phi_x(tc), y_c = phi_y(tc)
-        float gtc[3] = {0.f, 0.f, 0.f};
+        // q_k = J (t_k - tc); x_c = phi_x(tc), y_c = phi_y(tc).  gtc collects
+        // the terms of tc as the linearisation anchor, gsum the vertex terms
+        // (which enter tc with the opposite sign).
+        float gtc[3] = {0.f, 0.f, 0.f}, gsum[3] = {0.f, 0.f, 0.f};
         float gJ00 = 0.f, gJ02 = 0.f, gJ11 = 0.f, gJ12 = 0.f, gJ2[3] = {0.f, 0.f, 0.f};
 #pragma unroll
         for (int k = 0; k < V; ++k) {
@@ -294,7 +302,7 @@ __global__ void __launch_bounds__(128) k_chain(PrimsDev P, CamsParam cams,
             gJ2[0] += gq[k][2] * d[k][0];
             gJ2[1] += gq[k][2] * d[k][1];
             gJ2[2] += gq[k][2] * d[k][2];
-            gtc[0] -= gd0; gtc[1] -= gd1; gtc[2] -= gd2;
+            gsum[0] += gd0; gsum[1] += gd1; gsum[2] += gd2;
             // world vertex: t = R v + T
 #pragma unroll
             for (int a = 0; a < 3; ++a)
@@ -321,7 +329,8 @@ __global__ void __launch_bounds__(128) k_chain(PrimsDev P, CamsParam cams,
         }
 #pragma unroll
         for (int a = 0; a < 3; ++a)
-            gc[a] += cm.R[a] * gtc[0] + cm.R[3 + a] * gtc[1] + cm.R[6 + a] * gtc[2];
+            gc[a] += cm.R[a] * (gtc[0] - gsum[0]) + cm.R[3 + a] * (gtc[1] - gsum[1]) +
+                     cm.R[6 + a] * (gtc[2] - gsum[2]);
 
         // colour -> SH coefficients and view direction
         float dir[3] = {c[0] - cm.campos[0], c[1] - cm.campos[1], c[2] - cm.campos[2]};
@@ -348,10 +357,27 @@ __global__ void __launch_bounds__(128) k_chain(PrimsDev P, CamsParam cams,
         float gdir[3];
         sh_basis_vjp<DEG>(dir[0], dir[1], dir[2], w, gdir);
         const float dd = gdir[0] * dir[0] + gdir[1] * dir[1] + gdir[2] * dir[2];
+        float gw[3];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) gc[a] += (gdir[a] - dir[a] * dd) * idl;
+        for (int a = 0; a < 3; ++a) {
+            gw[a] = (gdir[a] - dir[a] * dd) * idl;
+            gc[a] += gw[a];
+        }
+        if (P.grad_sum) {
+            // translating the whole primitive leaves t_k - tc unchanged: its
+            // camera-space gradient is the anchor terms plus the colour's
+            float gt[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+                gt[a] = gtc[a] + cm.R[3 * a] * gw[0] + cm.R[3 * a + 1] * gw[1] + cm.R[3 * a + 2] * gw[2];
+            vg_sum += ndc_grad_norm(cm, gt, g.tc[2]);
+        }
 
         gsigma += ga_sig;
+    }
+    if (P.grad_sum) {
+        P.grad_sum[i] += vg_sum;
+        P.grad_count[i] += vg_count;
     }
 
     // Eq. 1 with d_min frozen: d sigma / d alpha = 0.99 / ((1 - 0.99 alpha) 2 d_min)

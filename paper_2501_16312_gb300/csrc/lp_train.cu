@@ -15,8 +15,11 @@
 
 #include <cstdint>
 
+#include <cmath>
+
 #include "linprim.h"
 #include "lp_device.cuh"
+#include "lp_internal.h"
 
 namespace lp {
 
@@ -254,6 +257,145 @@ __global__ void __launch_bounds__(256) k_adam4(float4* __restrict__ p, const flo
 
 __global__ void k_increment(int* step) { *step += 1; }
 
+// ---------------------------------------------------------------- population
+// Sec. 3.4 "Adaptive Population Control" with App. "Experimental Setting"'s
+// thresholds.  A decision pass writes each primitive's action and output
+// count, an exclusive scan turns the counts into destination rows, and an
+// apply pass compacts every array set into the new population.
+
+constexpr uint8_t kPrune = LP_POP_PRUNE, kKeep = LP_POP_KEEP, kClone = LP_POP_CLONE, kSplit = LP_POP_SPLIT;
+
+struct PopRules {
+    float logit_min, max_scene_frac, clone_scene_frac, extent, thr;
+    uint32_t max_px;
+};
+
+// Sec. 3.4's size: an octahedron's longest axis, twice its largest distance;
+// a tetrahedron's sqrt(2) times the distance to its furthest corner.
+template <int V>
+__global__ void __launch_bounds__(256) k_pop_decide(int n, const float* __restrict__ dist,
+                                                    const float* __restrict__ logit,
+                                                    const float* __restrict__ gsum,
+                                                    const uint32_t* __restrict__ gcount,
+                                                    const uint32_t* __restrict__ pxmax, PopRules R,
+                                                    uint8_t* __restrict__ action, uint32_t* __restrict__ outc) {
+    constexpr int ND = V == 6 ? 3 : 4;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float m = 0.f;
+#pragma unroll
+    for (int a = 0; a < ND; ++a) m = fmaxf(m, fabsf(dist[(size_t)i * ND + a]));
+    const float size = __fmul_rn(V == 6 ? 2.f : 1.41421356f, m);
+    uint8_t act;
+    if (logit[i] < R.logit_min || size > __fmul_rn(R.max_scene_frac, R.extent) || pxmax[i] > R.max_px) {
+        act = kPrune;
+    } else {
+        const uint32_t c = gcount[i];
+        const float g = c > 0 ? __fdiv_rn(gsum[i], (float)c) : 0.f;
+        act = g > R.thr ? (size < __fmul_rn(R.clone_scene_frac, R.extent) ? kClone : kSplit) : kKeep;
+    }
+    action[i] = act;
+    outc[i] = act == kPrune ? 0u : (act == kKeep ? 1u : 2u);
+}
+
+// One (array set, field) pair of the apply pass: `width` floats per row.
+// kind 0: parameters copied to both children; 1: distances, divided by 1.2
+// for split children; 2: optimiser state, zero for new rows; 3: the centre
+// parameter (written by k_pop_centre instead).
+struct PopJob {
+    const float* src;
+    float* dst;
+    int width;
+    int kind;
+};
+constexpr int kPopMaxJobs = 20;   // 4 sets x 5 fields
+struct PopJobs {
+    PopJob job[kPopMaxJobs];
+};
+
+__global__ void __launch_bounds__(256) k_pop_apply(int n, const uint8_t* __restrict__ action,
+                                                   const uint32_t* __restrict__ dest, PopJobs J) {
+    const PopJob jb = J.job[blockIdx.y];
+    if (jb.kind == 3) return;
+    const long long total = (long long)n * jb.width;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e / jb.width);
+        const int j = (int)(e - (long long)i * jb.width);
+        const uint8_t act = action[i];
+        if (act == kPrune) continue;
+        const size_t o = (size_t)dest[i] * jb.width + j;
+        const float v = jb.src[e];
+        if (act == kKeep) {
+            jb.dst[o] = v;
+        } else if (act == kClone) {
+            jb.dst[o] = v;
+            jb.dst[o + jb.width] = jb.kind == 2 ? 0.f : v;
+        } else {
+            const float c = jb.kind == 2 ? 0.f : (jb.kind == 1 ? __fdiv_rn(v, 1.2f) : v);
+            jb.dst[o] = c;
+            jb.dst[o + jb.width] = c;
+        }
+    }
+}
+
+// Split children's centres: c + R(q) (|d| * z) for an octahedron (standard
+// deviations equal to the distances along the rotated axes), c + (max|d| / 2) z
+// for a tetrahedron; kept and cloned rows copy the centre.
+template <int V>
+__global__ void __launch_bounds__(256) k_pop_centre(int n, const uint8_t* __restrict__ action,
+                                                    const uint32_t* __restrict__ dest,
+                                                    const float* __restrict__ centre,
+                                                    const float* __restrict__ quat,
+                                                    const float* __restrict__ dist,
+                                                    const float* __restrict__ normals,
+                                                    float* __restrict__ out) {
+    constexpr int ND = V == 6 ? 3 : 4;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint8_t act = action[i];
+    if (act == kPrune) return;
+    const size_t o = dest[i];
+    float c[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) c[a] = centre[3 * (size_t)i + a];
+    if (act != kSplit) {
+#pragma unroll
+        for (int r = 0; r < (act == kClone ? 2 : 1); ++r)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) out[3 * (o + r) + a] = c[a];
+        return;
+    }
+    float d[ND];
+#pragma unroll
+    for (int a = 0; a < ND; ++a) d[a] = fabsf(dist[(size_t)i * ND + a]);
+    float R[3][3], nrm;
+    if (V == 6) {
+        float q[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) q[a] = quat[4 * (size_t)i + a];
+        quat_rot(q, R, nrm);
+    }
+#pragma unroll
+    for (int ch = 0; ch < 2; ++ch) {
+        const float* z = normals + ((size_t)i * 2 + ch) * 3;
+        float off[3];
+        if (V == 6) {
+            const float s0 = d[0] * z[0], s1 = d[1] * z[1], s2 = d[2] * z[2];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) off[a] = R[a][0] * s0 + R[a][1] * s1 + R[a][2] * s2;
+        } else {
+            float m = 0.f;
+#pragma unroll
+            for (int a = 0; a < ND; ++a) m = fmaxf(m, d[a]);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) off[a] = 0.5f * m * z[a];
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) out[3 * (o + ch) + a] = c[a] + off[a];
+    }
+}
+
 int grid_for(long long n, int bs, int cap) {
     const long long g = (n + bs - 1) / bs;
     return (int)(g < cap ? (g > 0 ? g : 1) : cap);
@@ -339,6 +481,82 @@ lp_status lp_adam_step(float* params, const float* grads, float* m, float* v, co
         lp::k_adam<<<lp::grid_for(total, 256, 152 * 16), 256, 0, st>>>(params, grads, m, v, G, total, beta1,
                                                                       beta2, eps, step);
     lp::k_increment<<<1, 1, 0, st>>>(step);
+    return cudaGetLastError() == cudaSuccess ? LP_OK : LP_ERR_CUDA;
+}
+
+long long lp_population_scratch(long long n) {
+    if (n < 0) return 0;
+    return ((n + 3) / 4) * 4 + lp::scan_blocks(n) + 4;
+}
+
+lp_status lp_population_decide(int kind, int n, const float* dist, const float* logit, const float* grad_sum,
+                               const unsigned int* grad_count, const unsigned int* px_max,
+                               const lp_population_rules* rules, unsigned char* action, unsigned int* dest,
+                               unsigned int* n_out, unsigned int* scratch, void* stream) {
+    if ((kind != LP_OCTAHEDRON && kind != LP_TETRAHEDRON) || n < 0 || !rules || !n_out) return LP_ERR_INVALID;
+    const lp_population_rules& r = *rules;
+    auto pos = [](float x) { return x > 0.f && std::isfinite(x); };
+    if (!pos(r.scene_extent) || !(r.min_opacity > 0.f && r.min_opacity < 1.f) || !pos(r.max_scene_frac) ||
+        !pos(r.grad_threshold) || !pos(r.clone_scene_frac))
+        return LP_ERR_INVALID;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (n == 0) return cudaMemsetAsync(n_out, 0, sizeof(unsigned int), st) == cudaSuccess ? LP_OK : LP_ERR_CUDA;
+    if (!dist || !logit || !grad_sum || !grad_count || !px_max || !action || !dest || !scratch)
+        return LP_ERR_INVALID;
+    lp::PopRules R;
+    const double p = r.min_opacity;
+    R.logit_min = (float)std::log(p / (1.0 - p));   // sigmoid(logit) < p
+    R.max_scene_frac = r.max_scene_frac;
+    R.clone_scene_frac = r.clone_scene_frac;
+    R.extent = r.scene_extent;
+    R.thr = r.grad_threshold;
+    R.max_px = r.max_pixels;
+    uint32_t* outc = scratch;
+    uint32_t* sums = scratch + ((n + 3) / 4) * 4;
+    const int grid = (n + 255) / 256;
+    if (kind == LP_OCTAHEDRON)
+        lp::k_pop_decide<6><<<grid, 256, 0, st>>>(n, dist, logit, grad_sum, grad_count, px_max, R, action, outc);
+    else
+        lp::k_pop_decide<4><<<grid, 256, 0, st>>>(n, dist, logit, grad_sum, grad_count, px_max, R, action, outc);
+    if (cudaGetLastError() != cudaSuccess) return LP_ERR_CUDA;
+    return lp::launch_scan(outc, n, dest, sums, n_out, st) == cudaSuccess ? LP_OK : LP_ERR_CUDA;
+}
+
+lp_status lp_population_apply(int kind, int sh_coeffs, int n, const unsigned char* action,
+                              const unsigned int* dest, const float* normals, const lp_param_arrays* src,
+                              const lp_param_arrays* dst, int n_sets, void* stream) {
+    if ((kind != LP_OCTAHEDRON && kind != LP_TETRAHEDRON) || n < 0) return LP_ERR_INVALID;
+    if (!(sh_coeffs == 1 || sh_coeffs == 4 || sh_coeffs == 9 || sh_coeffs == 16)) return LP_ERR_INVALID;
+    if (n_sets < 1 || n_sets > 4 || !src || !dst) return LP_ERR_INVALID;
+    if (n == 0) return LP_OK;
+    if (!action || !dest || !normals) return LP_ERR_INVALID;
+    const int D = kind == LP_OCTAHEDRON ? 3 : 4;
+    lp::PopJobs J;
+    int nj = 0;
+    for (int s = 0; s < n_sets; ++s) {
+        const float* sp[5] = {src[s].centre, src[s].quat, src[s].dist, src[s].logit, src[s].sh};
+        float* dp[5] = {dst[s].centre, dst[s].quat, dst[s].dist, dst[s].logit, dst[s].sh};
+        const int w[5] = {3, 4, D, 1, 3 * sh_coeffs};
+        for (int f = 0; f < 5; ++f) {
+            if (!sp[f] || !dp[f]) return LP_ERR_INVALID;
+            J.job[nj].src = sp[f];
+            J.job[nj].dst = dp[f];
+            J.job[nj].width = w[f];
+            J.job[nj].kind = s > 0 ? 2 : (f == 0 ? 3 : (f == 2 ? 1 : 0));
+            ++nj;
+        }
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const long long widest = (long long)n * 3 * sh_coeffs > 4ll * n ? (long long)n * 3 * sh_coeffs : 4ll * n;
+    dim3 grid(lp::grid_for(widest, 256, 152 * 8), nj);
+    lp::k_pop_apply<<<grid, 256, 0, st>>>(n, action, dest, J);
+    const int g1 = (n + 255) / 256;
+    if (kind == LP_OCTAHEDRON)
+        lp::k_pop_centre<6><<<g1, 256, 0, st>>>(n, action, dest, src[0].centre, src[0].quat, src[0].dist, normals,
+                                                dst[0].centre);
+    else
+        lp::k_pop_centre<4><<<g1, 256, 0, st>>>(n, action, dest, src[0].centre, src[0].quat, src[0].dist, normals,
+                                                dst[0].centre);
     return cudaGetLastError() == cudaSuccess ? LP_OK : LP_ERR_CUDA;
 }
 

@@ -116,6 +116,56 @@ def adam_step(params, grads, m, v, groups, step, beta1=0.9, beta2=0.999, eps=1e-
                           float(beta2), float(eps), _ptr(step), _stream(params.device)), "lp_adam_step")
 
 
+def population_rules(extent: float, min_opacity=0.025, max_scene_frac=0.4, max_pixels=20,
+                     grad_threshold=1.5e-4, clone_scene_frac=0.01):
+    """App. "Experimental Setting"'s population thresholds (the defaults)."""
+    return _native.lp_population_rules(float(extent), float(min_opacity), float(max_scene_frac), int(max_pixels),
+                                       float(grad_threshold), float(clone_scene_frac))
+
+
+def population_decide(kind, dist, logit, grad_sum, grad_count, px_max, rules):
+    """Per-primitive action (uint8: 0 prune, 1 keep, 2 clone, 3 split), the
+    destination row of each primitive (int32) and the new count (int32 [1]),
+    all on the device."""
+    torch = _torch()
+    dev = logit.device
+    n = int(logit.shape[0])
+    L = _native.load()
+    action = torch.empty(n, dtype=torch.uint8, device=dev)
+    dest = torch.empty(n, dtype=torch.int32, device=dev)
+    n_out = torch.zeros(1, dtype=torch.int32, device=dev)
+    scratch = torch.empty(max(1, int(L.lp_population_scratch(n))), dtype=torch.int32, device=dev)
+    _check(L.lp_population_decide(int(kind), n, _ptr(dist), _ptr(logit), _ptr(grad_sum), _ptr(grad_count),
+                                  _ptr(px_max), C.byref(rules), _ptr(action), _ptr(dest), _ptr(n_out),
+                                  _ptr(scratch), _stream(dev)), "lp_population_decide")
+    return action, dest, n_out
+
+
+_FIELDS = ("centre", "quat", "dist", "logit", "sh")
+
+
+def _arrays(d):
+    return _native.lp_param_arrays(*(C.c_void_p(d[k].data_ptr()) for k in _FIELDS))
+
+
+def population_apply(kind, action, dest, normals, sets, n_out: int, out_sets=None):
+    """Compact every set (dicts of the parameter-layer arrays; set 0 the
+    parameters, the rest optimiser state) into n_out rows.  normals: device
+    float32 [n, 2, 3] standard-normal draws for split children."""
+    torch = _torch()
+    if out_sets is None:
+        out_sets = [{k: torch.empty((n_out,) + tuple(s[k].shape[1:]), dtype=torch.float32, device=s[k].device)
+                     for k in _FIELDS} for s in sets]
+    n = int(action.shape[0])
+    K = int(sets[0]["sh"].shape[1])
+    src = (_native.lp_param_arrays * len(sets))(*(_arrays(s) for s in sets))
+    dst = (_native.lp_param_arrays * len(sets))(*(_arrays(s) for s in out_sets))
+    L = _native.load()
+    _check(L.lp_population_apply(int(kind), K, n, _ptr(action), _ptr(dest), _ptr(normals), src, dst, len(sets),
+                                 _stream(action.device)), "lp_population_apply")
+    return out_sets
+
+
 def _make_params_fn():
     torch = _torch()
 
@@ -179,30 +229,10 @@ class Trainer:
         self.bg = tuple(float(x) for x in bg)
         self.rast = rasterizer if rasterizer is not None else Rasterizer(device)
         dev = self.rast.device
-        n = int(np.asarray(centre.shape)[0])
-        D = _ndist(kind)
-        K = int(sh.shape[1])
-        self.n, self.D, self.K = n, D, K
-        shapes = dict(centre=(n, 3), quat=(n, 4), dist=(n, D), logit=(n,), sh=(n, K, 3))
-        sizes = {k: int(np.prod(s)) for k, s in shapes.items()}
-        self.offsets, off = {}, 0
-        for k in self.GROUPS:
-            self.offsets[k] = off
-            off += sizes[k]
-        self.total = off
-        self.P = torch.empty(off, device=dev)
-        self.G = torch.zeros(off, device=dev)
-        self.m = torch.zeros(off, device=dev)
-        self.v = torch.zeros(off, device=dev)
-        view = lambda buf, k: buf[self.offsets[k]:self.offsets[k] + sizes[k]].view(*shapes[k])
-        self.p = {k: view(self.P, k) for k in self.GROUPS}
-        self.g = {k: view(self.G, k) for k in self.GROUPS}
+        self.D, self.K = _ndist(kind), int(sh.shape[1])
+        self._layout(int(np.asarray(centre.shape)[0]))
         for k, src in zip(self.GROUPS, (centre, quat, dist, logit, sh)):
-            self.p[k].copy_(torch.as_tensor(src, dtype=torch.float32).reshape(shapes[k]))
-        self.verts = torch.empty(n, kind, 3, device=dev)
-        self.opacity = torch.empty(n, device=dev)
-        self.dverts = torch.empty_like(self.verts)
-        self.dopacity = torch.empty_like(self.opacity)
+            self.p[k].copy_(torch.as_tensor(src, dtype=torch.float32).reshape(self.p[k].shape))
         self.pixels = sum(c.width * c.height for c in self.cameras)
         self.targets = torch.as_tensor(targets, dtype=torch.float32).reshape(3 * self.pixels).to(dev)
         self.images = torch.empty(3 * self.pixels, device=dev)
@@ -214,20 +244,95 @@ class Trainer:
         if lrs:
             lr.update(lrs)
         self.lr = lr
-        o = self.offsets
-        self.groups = [
-            adam_group(o["centre"], sizes["centre"], lr["centre"], lr["centre_final"], lr["centre_decay_steps"]),
-            adam_group(o["quat"], sizes["quat"], lr["quat"]),
-            adam_group(o["dist"], sizes["dist"], lr["dist"]),
-            adam_group(o["logit"], sizes["logit"], lr["logit"]),
-            adam_group(o["sh"], sizes["sh"], lr["sh_dc"], period=3 * K, head=3, lr_tail=lr["sh_rest"]),
-        ]
-        self._groups_arr = (_native.lp_adam_group * len(self.groups))(*self.groups)
-        self.prims = Primitives(kind, self.p["centre"], self.verts, self.opacity, self.p["sh"])
         self._cams = _native.camera_struct(self.cameras)
         self._bgv = (C.c_float * 3)(*self.bg)
+        self.stats = None
+        self._bind()
+
+    def _layout(self, n: int):
+        """Flat parameter, gradient and moment arrays for n primitives (the
+        parameters uninitialised, the rest zero) and the per-primitive buffers."""
+        torch = _torch()
+        dev = self.rast.device
+        D, K = self.D, self.K
+        self.n = n
+        self.shapes = dict(centre=(n, 3), quat=(n, 4), dist=(n, D), logit=(n,), sh=(n, K, 3))
+        self.sizes = {k: int(np.prod(s)) for k, s in self.shapes.items()}
+        self.offsets, off = {}, 0
+        for k in self.GROUPS:
+            self.offsets[k] = off
+            off += self.sizes[k]
+        self.total = off
+        self.P = torch.empty(off, device=dev)
+        self.G = torch.zeros(off, device=dev)
+        self.m = torch.zeros(off, device=dev)
+        self.v = torch.zeros(off, device=dev)
+        self.p, self.g = self._views(self.P), self._views(self.G)
+        self.verts = torch.empty(n, self.kind, 3, device=dev)
+        self.opacity = torch.empty(n, device=dev)
+        self.dverts = torch.empty_like(self.verts)
+        self.dopacity = torch.empty_like(self.opacity)
+
+    def _views(self, buf):
+        return {k: buf[self.offsets[k]:self.offsets[k] + self.sizes[k]].view(*self.shapes[k]) for k in self.GROUPS}
+
+    def _bind(self):
+        """Adam groups and the boundary structs of the current arrays."""
+        lr, o, sz = self.lr, self.offsets, self.sizes
+        self.groups = [
+            adam_group(o["centre"], sz["centre"], lr["centre"], lr["centre_final"], lr["centre_decay_steps"]),
+            adam_group(o["quat"], sz["quat"], lr["quat"]),
+            adam_group(o["dist"], sz["dist"], lr["dist"]),
+            adam_group(o["logit"], sz["logit"], lr["logit"]),
+            adam_group(o["sh"], sz["sh"], lr["sh_dc"], period=3 * self.K, head=3, lr_tail=lr["sh_rest"]),
+        ]
+        self._groups_arr = (_native.lp_adam_group * len(self.groups))(*self.groups)
+        self.prims = Primitives(self.kind, self.p["centre"], self.verts, self.opacity, self.p["sh"])
         self._ps = self.prims.struct()
         self.graph = None
+
+    # ------------------------------------------------ population control
+    def enable_densify_stats(self):
+        """Gather the densification statistics from the next step on (zeroed
+        here).  A captured graph is dropped: capture again afterwards."""
+        torch = _torch()
+        dev = self.rast.device
+        self.stats = dict(grad_sum=torch.zeros(self.n, device=dev),
+                          grad_count=torch.zeros(self.n, dtype=torch.int32, device=dev),
+                          px_max=torch.zeros(self.n, dtype=torch.int32, device=dev))
+        self.rast.set_densify_stats(self.stats["grad_sum"], self.stats["grad_count"], self.stats["px_max"])
+        self.graph = None
+
+    def densify(self, rules=None, normals=None, generator=None) -> dict:
+        """Adjust the population once (Sec. 3.4 "Adaptive Population
+        Control"; the paper does so every 250 steps): prune, clone and split
+        by the gathered statistics, compact parameters and Adam moments into
+        new arrays, zero the gradients and the statistics.  normals: optional
+        device float32 [n, 2, 3] draws for split children (else drawn with
+        `generator`).  Synchronises once to read the new count; drops a
+        captured graph.  Returns the per-action counts."""
+        torch = _torch()
+        if self.stats is None:
+            raise RuntimeError("enable_densify_stats() before densify()")
+        dev = self.rast.device
+        rules = population_rules(self.extent) if rules is None else rules
+        st = self.stats
+        action, dest, n_out = population_decide(self.kind, self.p["dist"], self.p["logit"], st["grad_sum"],
+                                                st["grad_count"], st["px_max"], rules)
+        if normals is None:
+            normals = torch.randn(self.n, 2, 3, device=dev, generator=generator)
+        n_new = int(n_out.item())
+        counts = torch.bincount(action.long(), minlength=4).tolist()
+        old = [self.p, self._views(self.m), self._views(self.v)]
+        keep = (self.P, self.m, self.v, action, dest, normals)   # alive until the copies ran
+        self._layout(n_new)
+        population_apply(self.kind, action, dest, normals, old, n_new,
+                         out_sets=[self.p, self._views(self.m), self._views(self.v)])
+        self._bind()
+        self.enable_densify_stats()
+        torch.cuda.current_stream(dev).synchronize()
+        del keep
+        return dict(pruned=counts[0], kept=counts[1], cloned=counts[2], split=counts[3], n=n_new)
 
     def step(self):
         """Enqueue one optimisation step on the current stream; the loss of

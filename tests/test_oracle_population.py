@@ -52,7 +52,8 @@ def _one(kind, dist, logit, gsum=0.0, gcnt=1, px=0, extent=10.0):
 
 
 def test_decide_opacity_threshold():
-    thr = math.log(0.025 / 0.975)
+    p = float(f32(0.025))
+    thr = math.log(p / (1.0 - p))
     below = float(np.nextafter(f32(thr), f32(-10)))
     assert 1.0 / (1.0 + math.exp(-below)) < 0.025
     assert _one(6, [0.1] * 3, below) == pop.PRUNE
