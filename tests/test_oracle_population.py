@@ -84,6 +84,37 @@ def test_decide_screen_size_threshold():
     assert _one(6, [0.1] * 3, 0.0, px=21) == pop.PRUNE
 
 
+@pytest.mark.parametrize("kind", [6, 4])
+def test_decide_clone_bound(kind):
+    """Cloned strictly below 1% of the scene extent: a size exactly on the
+    bound is split."""
+    ext = 7.0
+    small = f32(f32(0.01) * f32(ext))
+    D = 3 if kind == 6 else 4
+    d = f32(small / f32(2.0 if kind == 6 else math.sqrt(2.0)))
+    while pop.size32(kind, [d] * D) > small:
+        d = np.nextafter(d, f32(0))
+    while pop.size32(kind, [np.nextafter(d, f32(np.inf))] * D) <= small:
+        d = np.nextafter(d, f32(np.inf))
+    below = np.nextafter(d, f32(0))
+    while pop.size32(kind, [below] * D) >= small:     # sqrt(2) d: neighbours can round alike
+        below = np.nextafter(below, f32(0))
+    assert _one(kind, [float(below)] * D, 0.0, gsum=1.0, gcnt=1, extent=ext) == pop.CLONE
+    if pop.size32(kind, [d] * D) == small:
+        assert _one(kind, [float(d)] * D, 0.0, gsum=1.0, gcnt=1, extent=ext) == pop.SPLIT
+    assert _one(kind, [float(np.nextafter(d, f32(np.inf)))] * D, 0.0, gsum=1.0, gcnt=1, extent=ext) == pop.SPLIT
+
+
+@pytest.mark.parametrize("cnt", [1, 2, 4])
+def test_decide_gradient_bound(cnt):
+    """Densified only strictly above the threshold: a mean exactly on it is kept."""
+    thr = f32(1.5e-4)
+    on = f32(thr * f32(cnt))                  # exact: cnt is a power of two
+    assert _one(6, [0.01] * 3, 0.0, gsum=float(on), gcnt=cnt) == pop.KEEP
+    up = np.nextafter(on, f32(1))
+    assert _one(6, [0.01] * 3, 0.0, gsum=float(up), gcnt=cnt) == pop.CLONE
+
+
 def test_decide_densification():
     ext = 10.0
     # mean gradient strictly above 1.5e-4 over the visible views
@@ -164,6 +195,23 @@ def test_split_octahedron_child_on_a_vertex(orc):
             np.testing.assert_allclose(got, ends, atol=1e-12)
 
 
+def test_split_octahedron_std_is_the_distance_magnitude(orc):
+    """A standard deviation is non-negative: with the draw z = +e_a the child
+    is offset by |d_a| along the rotated axis R e_a, which the parameter layer
+    gives as (v_2a - c) / d_a, whatever the sign of d_a."""
+    rng = np.random.default_rng(17)
+    p = _params(6, 8, rng)
+    p["dist"][::2] *= -1.0
+    v, _ = orc.params_forward(6, p["centre"], p["quat"], p["dist"], p["logit"])
+    for a in range(3):
+        normals = np.zeros((8, 2, 3))
+        normals[:, 0, a] = 1.0
+        q, _ = pop.apply(6, p, [], np.full(8, pop.SPLIT), normals)
+        axis = (v[:, 2 * a] - p["centre"]) / p["dist"][:, a:a + 1]
+        np.testing.assert_allclose(q["centre"][0::2], p["centre"] + np.abs(p["dist"][:, a:a + 1]) * axis,
+                                   atol=1e-12)
+
+
 def test_split_tetrahedron_child_halfway_to_corner(orc):
     """Isotropic standard deviation of half the largest distance: with equal
     distances and z the unit direction to a corner, the child lies halfway
@@ -203,25 +251,29 @@ def test_split_offset_covariance(kind):
 
 # ------------------------------------------------------------ statistics
 
-def test_screen_pixels_of_a_facing_octahedron(orc):
+@pytest.mark.parametrize("dists", [(0.31, 0.07, 0.05), (0.06, 0.27, 0.05)])
+def test_screen_pixels_of_a_facing_octahedron(orc, dists):
     """An axis-aligned octahedron straight ahead of the camera projects its x
-    vertices to x_c +- f_x d / z: the covered columns are the pixel centres in
-    that interval."""
+    (y) vertices to x_c +- f_x d_x / z (y_c +- f_y d_y / z): the covered
+    columns (rows) are the pixel centres in that interval; the size is the
+    larger count."""
     cam = scenes.make_camera((0.0, 0.0, 0.0), 96, 64, 60.0, target=(0.0, 0.0, 1.0))
     M = cam.viewmat.astype(np.float64)
     z = 3.0
     c = np.array([[0.0, 0.0, z]])
     R = M[:3, :3].T                          # camera axes in world coordinates
-    dists = np.array([[0.31, 0.07, 0.05]])
-    verts = scenes.octahedra_from_axes(c, R[None], dists)
+    verts = scenes.octahedra_from_axes(c, R[None], np.array([dists]))
     sc = scenes.Scene(6, c.astype(f32), verts.astype(f32), np.array([0.5], f32),
                       np.zeros((1, 1, 3), f32), 0)
     ext = pop.screen_pixels(orc, sc, [cam])
     tc = M[:3, :3] @ c[0] + M[:3, 3]
     xc = float(cam.fx) * tc[0] / tc[2] + float(cam.cx)
-    w = float(cam.fx) * 0.31 / tc[2]
-    cols = [x for x in range(cam.width) if xc - w <= x + 0.5 <= xc + w]
-    assert ext[0] == len(cols) and len(cols) > 10
+    yc = float(cam.fy) * tc[1] / tc[2] + float(cam.cy)
+    wx = float(cam.fx) * dists[0] / tc[2]
+    wy = float(cam.fy) * dists[1] / tc[2]
+    cols = [x for x in range(cam.width) if xc - wx <= x + 0.5 <= xc + wx]
+    rows = [y for y in range(cam.height) if yc - wy <= y + 0.5 <= yc + wy]
+    assert ext[0] == max(len(cols), len(rows)) and abs(len(cols) - len(rows)) > 5
 
 
 def test_view_gradient_matches_finite_differences(orc):
@@ -229,7 +281,9 @@ def test_view_gradient_matches_finite_differences(orc):
     <g, image> under a translation of one primitive parallel to the image
     plane (centre and vertices moved together)."""
     w = scenes.workload(0)
-    sc, cam = w.scene, w.cameras[0]
+    sc = w.scene
+    # an oblique, non-square view (a generic rotation; W != H)
+    cam = scenes.make_camera((2.6, -1.3, 2.9), 112, 72, 55.0)
     rng = np.random.default_rng(11)
     gimg = rng.normal(size=3 * cam.pixels)
     dmin = orc.preprocess(sc, cam)["dmin"]
