@@ -687,6 +687,8 @@ def train_arm(args):
            "d2h_bytes_per_step": 8, "ms_per_step": t_e2e,
            "path": "pinned host targets -> device, Trainer.step (eager launches), loss -> host"}
 
+    popm = population_measure(tr, dev, timed)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(param_workload_scene(w, tr.params_numpy()), args.cpu_seconds)
@@ -708,10 +710,85 @@ def train_arm(args):
                          "steps_before_timing": args.warmup + 2},
                 "workload_counts": {"records": st["records"], "tile_list_entries": st["entries"],
                                     "pairs": pairs, "sort_passes": st["sort_passes"]},
+                "population": popm,
                 "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def hbm_population_bytes(n, n_pruned, n_new, n_split, D, K):
+    """Algorithmic bytes of one population adjustment: decide (distances,
+    logit, three statistics in; action and count out), the scan (counts read
+    twice, destinations written) and the compaction of three array sets
+    (parameters and both Adam moments): action and destination of every
+    primitive, the rows of the surviving ones read, normals of the split
+    ones, the new rows written."""
+    n_par = 3 + 4 + D + 1 + 3 * K
+    decide = n * (4 * D + 4 + 12 + 1 + 4) + n * 12
+    apply = n * 5 + (n - n_pruned) * 3 * n_par * 4 + n_split * 24 + n_new * 3 * n_par * 4
+    return decide, apply
+
+
+def population_measure(tr, dev, timed):
+    """Population control at the workload's size (App. "Experimental
+    Setting": every 250 steps), each kernel timed alone with events (10
+    repetitions on unchanged inputs).  Two states: the workload's own
+    statistics, gathered over one optimisation step, and seeded synthetic
+    statistics that send about 10% of the primitives to densification and
+    5% to pruning (a mid-training mix that exercises every branch)."""
+    import ctypes as C
+    import torch
+    from paper_2501_16312_gb300 import _native, train
+    tr.enable_densify_stats()
+    tr.step()
+    torch.cuda.synchronize()
+    L, sp, ptr = tr.lib, train._stream(dev), train._ptr
+    n, kind = tr.n, tr.kind
+    K = int(tr.p["sh"].shape[1])
+    rules = train.population_rules(tr.extent)
+    action = torch.empty(n, dtype=torch.uint8, device=dev)
+    dest = torch.empty(n, dtype=torch.int32, device=dev)
+    n_out = torch.zeros(1, dtype=torch.int32, device=dev)
+    scratch = torch.empty(int(L.lp_population_scratch(n)), dtype=torch.int32, device=dev)
+    normals = torch.randn(n, 2, 3, device=dev, generator=torch.Generator(dev).manual_seed(0))
+    sets = [tr.p, tr._views(tr.m), tr._views(tr.v)]
+    src = (_native.lp_param_arrays * 3)(*(train._arrays(x) for x in sets))
+    peak = measured_peaks()[0].get("hbm_gbs")
+
+    def one(st):
+        def decide():
+            return L.lp_population_decide(kind, n, ptr(tr.p["dist"]), ptr(tr.p["logit"]), ptr(st["grad_sum"]),
+                                          ptr(st["grad_count"]), ptr(st["px_max"]), C.byref(rules), ptr(action),
+                                          ptr(dest), ptr(n_out), ptr(scratch), sp)
+        t_decide = timed(decide)
+        n_new = int(n_out.item())
+        counts = torch.bincount(action.long(), minlength=4).tolist()
+        outs = [{k: torch.empty((n_new,) + tuple(x.shape[1:]), device=dev) for k, x in s_.items()} for s_ in sets]
+        dst = (_native.lp_param_arrays * 3)(*(train._arrays(x) for x in outs))
+        t_apply = timed(lambda: L.lp_population_apply(kind, K, n, ptr(action), ptr(dest), ptr(normals), src, dst,
+                                                      3, sp))
+        b_dec, b_app = hbm_population_bytes(n, counts[0], n_new, counts[3], tr.D, K)
+        del outs
+        gbs = b_app / (t_apply * 1e-3) / 1e9
+        return {"ms": t_decide + t_apply, "primitives_out": n_new,
+                "actions": dict(zip(("pruned", "kept", "cloned", "split"), counts)),
+                "decide_scan": {"ms": t_decide, "GB/s": b_dec / (t_decide * 1e-3) / 1e9},
+                "apply": {"ms": t_apply, "GB/s": gbs, "frac_hbm": gbs / peak if peak else None, "bytes": b_app}}
+
+    own = one(tr.stats)
+    g = torch.Generator(dev).manual_seed(1)
+    thr = float(rules.grad_threshold)
+    cnt = torch.full((n,), 4, dtype=torch.int32, device=dev)
+    # mean gradients uniform in [0.9, 1.01) x threshold: about 10% above it
+    synth = {"grad_count": cnt,
+             "grad_sum": 4 * thr * (0.9 + 0.11 * torch.rand(n, device=dev, generator=g)),
+             "px_max": (torch.rand(n, device=dev, generator=g) < 0.05).to(torch.int32) * 21}
+    mixed = one(synth)
+    return {"primitives_in": n, "timed": "alone, eager, events, 10 repetitions",
+            "amortised_ms_per_step": own["ms"] / 250.0,
+            "workload_state": dict(own, statistics="one optimisation step (4 views) with gathering on"),
+            "mixed_state": dict(mixed, statistics="seeded: about 10% above the gradient threshold, 5% over 20 px")}
 
 
 def param_workload_scene(w, params):

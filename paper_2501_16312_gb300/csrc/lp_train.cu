@@ -313,29 +313,74 @@ struct PopJobs {
     PopJob job[kPopMaxJobs];
 };
 
+// Each thread takes kPopUnroll elements a block apart and issues all their
+// loads before any store, so that enough bytes are in flight to cover HBM
+// latency (one dependent load chain per thread measured 1-2 TB/s).
+constexpr int kPopUnroll = 8;
+
+template <int W, typename I>
+__device__ __forceinline__ void pop_job(I total, const uint8_t* __restrict__ action,
+                                        const uint32_t* __restrict__ dest, const PopJob& jb) {
+    const float* __restrict__ src = jb.src;
+    float* __restrict__ dst = jb.dst;
+    const I step = (I)blockDim.x;
+    const I stride = (I)gridDim.x * blockDim.x * kPopUnroll;
+    for (I base = (I)blockIdx.x * blockDim.x * kPopUnroll + threadIdx.x; base < total; base += stride) {
+        uint8_t act[kPopUnroll];
+        size_t o[kPopUnroll];
+        float v[kPopUnroll];
+#pragma unroll
+        for (int u = 0; u < kPopUnroll; ++u) {
+            const I e = base + (I)u * step;
+            act[u] = kPrune;
+            o[u] = 0;
+            if (e < total) {
+                const I i = e / W;   // a division by a constant
+                act[u] = action[i];
+                o[u] = (size_t)dest[i] * W + (size_t)(e - i * W);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kPopUnroll; ++u) v[u] = act[u] != kPrune ? src[base + (I)u * step] : 0.f;
+#pragma unroll
+        for (int u = 0; u < kPopUnroll; ++u) {
+            if (act[u] == kPrune) continue;
+            if (act[u] == kKeep) {
+                dst[o[u]] = v[u];
+            } else if (act[u] == kClone) {
+                dst[o[u]] = v[u];
+                dst[o[u] + W] = jb.kind == 2 ? 0.f : v[u];
+            } else {
+                const float c = jb.kind == 2 ? 0.f : (jb.kind == 1 ? __fdiv_rn(v[u], 1.2f) : v[u]);
+                dst[o[u]] = c;
+                dst[o[u] + W] = c;
+            }
+        }
+    }
+}
+
+template <int W>
+__device__ __forceinline__ void pop_job_any(int n, const uint8_t* __restrict__ action,
+                                            const uint32_t* __restrict__ dest, const PopJob& jb) {
+    const unsigned long long total = (unsigned long long)n * W;
+    // 32-bit indexing whenever the padded index range fits
+    if (total + (unsigned long long)gridDim.x * blockDim.x * kPopUnroll < 0xffffffffull)
+        pop_job<W, uint32_t>((uint32_t)total, action, dest, jb);
+    else
+        pop_job<W, unsigned long long>(total, action, dest, jb);
+}
+
 __global__ void __launch_bounds__(256) k_pop_apply(int n, const uint8_t* __restrict__ action,
                                                    const uint32_t* __restrict__ dest, PopJobs J) {
     const PopJob jb = J.job[blockIdx.y];
     if (jb.kind == 3) return;
-    const long long total = (long long)n * jb.width;
-    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-         e += (long long)gridDim.x * blockDim.x) {
-        const int i = (int)(e / jb.width);
-        const int j = (int)(e - (long long)i * jb.width);
-        const uint8_t act = action[i];
-        if (act == kPrune) continue;
-        const size_t o = (size_t)dest[i] * jb.width + j;
-        const float v = jb.src[e];
-        if (act == kKeep) {
-            jb.dst[o] = v;
-        } else if (act == kClone) {
-            jb.dst[o] = v;
-            jb.dst[o + jb.width] = jb.kind == 2 ? 0.f : v;
-        } else {
-            const float c = jb.kind == 2 ? 0.f : (jb.kind == 1 ? __fdiv_rn(v, 1.2f) : v);
-            jb.dst[o] = c;
-            jb.dst[o + jb.width] = c;
-        }
+    switch (jb.width) {   // the widths of the parameter arrays: 1, 3, 4 and 3 K
+        case 1: pop_job_any<1>(n, action, dest, jb); break;
+        case 3: pop_job_any<3>(n, action, dest, jb); break;
+        case 4: pop_job_any<4>(n, action, dest, jb); break;
+        case 12: pop_job_any<12>(n, action, dest, jb); break;
+        case 27: pop_job_any<27>(n, action, dest, jb); break;
+        default: pop_job_any<48>(n, action, dest, jb); break;
     }
 }
 
@@ -548,7 +593,7 @@ lp_status lp_population_apply(int kind, int sh_coeffs, int n, const unsigned cha
     }
     cudaStream_t st = (cudaStream_t)stream;
     const long long widest = (long long)n * 3 * sh_coeffs > 4ll * n ? (long long)n * 3 * sh_coeffs : 4ll * n;
-    dim3 grid(lp::grid_for(widest, 256, 152 * 8), nj);
+    dim3 grid(lp::grid_for((widest + lp::kPopUnroll - 1) / lp::kPopUnroll, 256, 152 * 8), nj);
     lp::k_pop_apply<<<grid, 256, 0, st>>>(n, action, dest, J);
     const int g1 = (n + 255) / 256;
     if (kind == LP_OCTAHEDRON)
