@@ -16,7 +16,9 @@
 // plane gradients -+ dL/ds (x, y, 1) of the arg-max entry and arg-min exit
 // faces -- the plane form of the paper's MTIA barycentric derivatives.  A
 // thread first sums its strip of pixels, each warp then reduces with shuffles
-// and issues one atomic add per value into the record's accumulator.
+// (the colour and sigma terms in one butterfly, the faces' moments two faces
+// per butterfly) and issues one atomic add per value into the record's
+// accumulator.
 #include "lp_blend.cuh"
 
 namespace lp {
@@ -178,22 +180,32 @@ __global__ void __launch_bounds__(kTilePixels / PIX, 3 * PIX) k_blend_bwd(
                     if ((lane & 7) == 0) atomicAdd(A + 3 * F + warp_sum_index<4>(lane), t);
                 }
                 used = __reduce_or_sync(0xffffffffu, used);
+                // two faces per butterfly: (x, y, 1) moments of both in one
+                // 8-value reduction, six lanes then add one total each
                 while (used) {
-                    const int f = __ffs(used) - 1;
+                    const int f1 = __ffs(used) - 1;
                     used &= used - 1;
-                    float vs = 0.f, vx = 0.f;
+                    const int f2 = used ? __ffs(used) - 1 : -1;
+                    if (used) used &= used - 1;
+                    float hv[8];
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) hv[k] = 0.f;
 #pragma unroll
                     for (int i = 0; i < PIX; ++i) {
-                        const float v = c[i] ? (f == sf[i] ? -gsp[i] : (f == sb[i] ? gsp[i] : 0.f)) : 0.f;
-                        vs += v;
-                        vx = fmaf(v, (float)(lx0 + i) + p.dx0, vx);
+                        const float lxc = (float)(lx0 + i) + p.dx0;
+                        const float v1 = c[i] ? (f1 == sf[i] ? -gsp[i] : (f1 == sb[i] ? gsp[i] : 0.f)) : 0.f;
+                        const float v2 = c[i] ? (f2 == sf[i] ? -gsp[i] : (f2 == sb[i] ? gsp[i] : 0.f)) : 0.f;
+                        hv[0] = fmaf(v1, lxc, hv[0]);
+                        hv[2] += v1;
+                        hv[3] = fmaf(v2, lxc, hv[3]);
+                        hv[5] += v2;
                     }
-                    const float ga = warp_sum(vx), gb = warp_sum(vs * lyc), ge = warp_sum(vs);
-                    if (lane == 0) {
-                        atomicAdd(A + 3 * f + 0, ga);
-                        atomicAdd(A + 3 * f + 1, gb);
-                        atomicAdd(A + 3 * f + 2, ge);
-                    }
+                    hv[1] = hv[2] * lyc;
+                    hv[4] = hv[5] * lyc;
+                    const float t = warp_sum_multi<8>(hv, lane);
+                    const int k = warp_sum_index<8>(lane);
+                    if ((lane & 3) == 0 && k < 6 && (k < 3 || f2 >= 0))
+                        atomicAdd(A + (k < 3 ? 3 * f1 + k : 3 * f2 + k - 3), t);
                 }
             }
         }
