@@ -100,13 +100,20 @@ typedef struct {
  *                 sort of the tile ids (same resulting order).
  *   pixels_per_thread  1, 2 or 4 horizontally adjacent pixels per blend
  *                 thread (256 / pixels_per_thread threads per tile).
- * Every setting renders bit-identical images.                               */
+ *   chain_split   0: the backward's chain to world space in one pass per
+ *                 primitive; 1: in two passes, geometry then colour, each
+ *                 holding fewer registers (ignored while densification
+ *                 statistics are gathered, which need one pass).
+ * Every setting renders bit-identical images and tile lists.  chain_split
+ * changes the order in which a primitive's centre-gradient terms are summed,
+ * so dL/dcentre can differ in the last bits between its two settings.      */
 typedef struct {
     int tile;
     int batch;
     int blocks_per_sm;
     int sort_mode;
     int pixels_per_thread;
+    int chain_split;
 } lp_tuning;
 
 /* Sizes of the last forward call (filled by lp_get_stats).                 */
@@ -143,7 +150,7 @@ lp_status lp_create(lp_ctx** out, int device);
 void lp_destroy(lp_ctx* ctx);
 
 /* Set / read the tuning parameters (defaults: tile 16, batch 64,
- * blocks_per_sm 0, sort_mode 0, pixels_per_thread 4).                       */
+ * blocks_per_sm 0, sort_mode 0, pixels_per_thread 4, chain_split 0).        */
 lp_status lp_set_tuning(lp_ctx* ctx, const lp_tuning* t);
 lp_status lp_get_tuning(lp_ctx* ctx, lp_tuning* t);
 

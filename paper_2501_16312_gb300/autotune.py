@@ -1,11 +1,13 @@
 """Autotuner for the rasterizer's launch parameters.
 
 The tuning knobs (sort mode, pixels per blend thread, records per shared-memory
-batch, resident blend blocks per SM) change only the schedule: every setting
-renders bit-identical images.  The tuner times forward + backward of the
-caller's own workload with the library's per-stage CUDA events, picks the
-sort mode by the sort stages and the blend parameters by the two blend
-stages, and caches the choice as JSON keyed by GPU name, primitive kind and
+batch, resident blend blocks per SM, one- or two-pass backward chain) change
+only the schedule: every setting renders bit-identical images (the chain's
+split only reorders the sum of a primitive's centre-gradient terms).  The
+tuner times forward + backward of the caller's own workload with the
+library's per-stage CUDA events, picks the sort mode by the sort stages, the
+blend parameters by the two blend stages and the chain form by the chain
+stage, and caches the choice as JSON keyed by GPU name, primitive kind and
 size buckets of the workload.
 """
 from __future__ import annotations
@@ -87,7 +89,17 @@ def tune(rast, prims, cameras, bg=(0.0, 0.0, 0.0), dL=None, reps: int = 3,
         blend_times[(pix, batch, bps)] = sum(t[s] for s in BLEND_STAGES)
         results.append({"pixels_per_thread": pix, "batch": batch, "blocks_per_sm": bps, **t})
     pix, batch, bps = min(blend_times, key=blend_times.get)
-    choice = dict(base, sort_mode=best_sort, pixels_per_thread=pix, batch=batch, blocks_per_sm=bps)
+    rast.set_tuning(pixels_per_thread=pix, batch=batch, blocks_per_sm=bps)
+    # the backward chain in one or two passes, judged on its own stage
+    chain_times = {}
+    for split in (0, 1):
+        rast.set_tuning(chain_split=split)
+        t = _time(rast, prims, cameras, bg, dL, grads, images, reps)
+        chain_times[split] = t["chain"]
+        results.append({"chain_split": split, **t})
+    best_chain = min(chain_times, key=chain_times.get)
+    choice = dict(base, sort_mode=best_sort, pixels_per_thread=pix, batch=batch, blocks_per_sm=bps,
+                  chain_split=best_chain)
     rast.set_tuning(**choice)
     rast.set_timing(was_timing)
     entry = {"tuning": choice, "sort_ms": sort_times[best_sort],

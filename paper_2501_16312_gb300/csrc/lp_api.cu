@@ -33,7 +33,7 @@ template <typename T> struct DevBuf {
 struct lp_ctx {
     int device = 0;
     int sms = 0;
-    lp_tuning tune{16, 64, 0, 0, 4};
+    lp_tuning tune{16, 64, 0, 0, 4, 0};
     float aa_kernel = 0.f;      // 2D filter size in pixels (0 = off)
     bool exact = false;         // spans along the true perspective ray
     bool fwd_exact = false;     // mode of the last forward
@@ -306,6 +306,8 @@ lp_status lp_set_tuning(lp_ctx* ctx, const lp_tuning* t) {
         return fail(ctx, LP_ERR_INVALID, "pixels_per_thread %d not in {1, 2, 4}", t->pixels_per_thread);
     if (t->sort_mode != 0 && t->sort_mode != 1)
         return fail(ctx, LP_ERR_INVALID, "sort_mode %d not in {0, 1}", t->sort_mode);
+    if (t->chain_split != 0 && t->chain_split != 1)
+        return fail(ctx, LP_ERR_INVALID, "chain_split %d not in {0, 1}", t->chain_split);
     ctx->tune = *t;
     return LP_OK;
 }
@@ -631,7 +633,7 @@ lp_status lp_render_backward(lp_ctx* ctx, const float* dL_dimages, float* dcentr
                                    dverts, dopacity, dsh, accumulate, st));
     else
         LP_CUDA(lp::launch_chain(V, pr.sh_degree, P, ctx->cams, ctx->rec.p, ctx->counts.p, ctx->acc.p, dcentre,
-                                 dverts, dopacity, dsh, accumulate, st));
+                                 dverts, dopacity, dsh, accumulate, ctx->tune.chain_split, st));
     mark(ctx, st, 8, cap_mode);
     ctx->bwd_timed = ctx->timing;
     return LP_OK;

@@ -15,7 +15,7 @@ cudaError_t launch_preprocess(int V, int deg, const PrimsDev& P, const CamsParam
 
 cudaError_t launch_chain(int V, int deg, const PrimsDev& P, const CamsParam& cams, const float* rec,
                          const uint32_t* counts, const float* acc, float* dc, float* dv, float* dop,
-                         float* dsh, int accumulate, cudaStream_t st);
+                         float* dsh, int accumulate, int split, cudaStream_t st);
 
 int scan_blocks(long long n);
 cudaError_t launch_scan(const uint32_t* in, long long n, uint32_t* out, uint32_t* block_sums,

@@ -21,6 +21,22 @@ namespace lp {
 
 namespace {
 
+// A 16-byte load the compiler keeps where it is written (inside a camera
+// loop), so that a loop-invariant input is re-read from L1 instead of held in
+// registers across the loop.
+__device__ __forceinline__ float4 ld4_each(const float* p) {
+    float4 v;
+    asm volatile("ld.global.nc.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "l"(p));
+    return v;
+}
+__device__ __forceinline__ float ld_each(const float* p) {
+    float v;
+    asm volatile("ld.global.nc.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    return v;
+}
+
 template <int V, int DEG>
 __global__ void __launch_bounds__(128) k_preprocess(PrimsDev P, CamsParam cams, float* __restrict__ rec,
                                                     uint32_t* __restrict__ counts,
@@ -59,6 +75,12 @@ __global__ void __launch_bounds__(128) k_preprocess(PrimsDev P, CamsParam cams, 
     // underflows in binary32, and a non-finite opacity.
     degenerate |= !(sigma < CUDART_INF_F);
     uint32_t px_side = 0;   // largest pixel-rectangle side over the views
+    // The record is assembled in shared memory, where the face planes go to
+    // their slots by computed address, then copied out in 16-byte stores.  A
+    // thread's row is padded by 16 bytes so that rows start on distinct banks.
+    constexpr int kRow = Rec<V>::kVec4 + 1;
+    __shared__ float4 srec[128 * kRow];
+    float* o = reinterpret_cast<float*>(srec + threadIdx.x * kRow);
 
     for (int cv = 0; cv < cams.n; ++cv) {
         const CamDev& cm = cams.cam[cv];
@@ -107,7 +129,6 @@ __global__ void __launch_bounds__(128) k_preprocess(PrimsDev P, CamsParam cams, 
         // which lies inside the primitive): outward normal n, entry face iff
         // n_z < 0; depth - z_c = a x + b y + e with a = -n_x/n_z, b = -n_y/n_z,
         // e = (n . q0) / n_z.
-        float out[Rec<V>::kFloats];
         int nf = 0;
         float pl[F][3];
         bool front[F];
@@ -139,9 +160,9 @@ __global__ void __launch_bounds__(128) k_preprocess(PrimsDev P, CamsParam cams, 
         for (int f = 0; f < F; ++f) {
             const int s = front[f] ? sf++ : sb++;
             meta |= (uint32_t)f << (4 + 3 * s);
-            out[8 + 3 * s] = pl[f][0];
-            out[9 + 3 * s] = pl[f][1];
-            out[10 + 3 * s] = __fmaf_rn(-pl[f][0], g.fxo, __fmaf_rn(-pl[f][1], g.fyo, pl[f][2]));
+            o[8 + 3 * s] = pl[f][0];
+            o[9 + 3 * s] = pl[f][1];
+            o[10 + 3 * s] = __fmaf_rn(-pl[f][0], g.fxo, __fmaf_rn(-pl[f][1], g.fyo, pl[f][2]));
         }
 
         // Colour: rgb = max(0, sum_k Y_k(dir) sh_k + 0.5), dir from the camera
@@ -159,20 +180,25 @@ __global__ void __launch_bounds__(128) k_preprocess(PrimsDev P, CamsParam cams, 
             for (int k = 0; k < K; ++k) s = fmaf(Y[k], sh[3 * k + ch], s);
             rgb[ch] = fmaxf(s, 0.f);
         }
-        out[0] = __int_as_float(g.X0); out[1] = __int_as_float(g.Y0); out[2] = sigma;
-        out[3] = __uint_as_float(meta);
-        out[4] = rgb[0]; out[5] = rgb[1]; out[6] = rgb[2];
-        out[7] = g.len;   // ray-space depth of the centre (the planes are relative to it)
+        srec[threadIdx.x * kRow] = make_float4(__int_as_float(g.X0), __int_as_float(g.Y0), sigma,
+                                               __uint_as_float(meta));
+        // rgb, then the ray-space depth of the centre (the planes are relative to it)
+        srec[threadIdx.x * kRow + 1] = make_float4(rgb[0], rgb[1], rgb[2], g.len);
         float4* dst = reinterpret_cast<float4*>(rec + r * Rec<V>::kFloats);
 #pragma unroll
-        for (int k = 0; k < Rec<V>::kVec4; ++k)
-            dst[k] = make_float4(out[4 * k], out[4 * k + 1], out[4 * k + 2], out[4 * k + 3]);
+        for (int k = 0; k < Rec<V>::kVec4; ++k) dst[k] = srec[threadIdx.x * kRow + k];
     }
     if (P.px_max && px_side > P.px_max[i]) P.px_max[i] = px_side;   // one thread per primitive
 }
 
 // ------------------------------------------------------------------ backward
-template <int V, int DEG>
+// PART 0: the geometry (planes -> vertices, centre anchor, density); PART 1:
+// the colour (SH coefficients and the view direction's centre term); PART 2:
+// both in one pass (always used when the view-space statistics are
+// gathered, which need both parts per view).  The split form lowers the
+// registers a thread holds (the SH coefficients and their gradients live
+// only in PART 1), which pays where many cameras make the loop long.
+template <int V, int DEG, int PART>
 __global__ void __launch_bounds__(128) k_chain(PrimsDev P, CamsParam cams,
                                                const float* __restrict__ rec,
                                                const uint32_t* __restrict__ counts,
@@ -193,9 +219,18 @@ __global__ void __launch_bounds__(128) k_chain(PrimsDev P, CamsParam cams,
 #pragma unroll
         for (int a = 0; a < 3; ++a) v[k][a] = __ldg(P.verts + ((size_t)i * V + k) * 3 + a);
     const float alpha = __ldg(P.opacity + i);
-    float sh[K * 3];
+    // The fused form re-reads the SH coefficients per camera (L1 hits; 16-byte
+    // loads when a row is a multiple of 16 bytes and the array is 16-byte
+    // aligned); PART 1 keeps them in registers.
+    constexpr bool kVecSH = PART == 2 && (K * 3) % 4 == 0;
+    const bool sh_aligned = ((uintptr_t)P.sh & 15u) == 0;
+    constexpr int kRegSH = PART != 0 && !kVecSH ? K * 3 : 1;
+    float sh_reg[kRegSH];
+    if constexpr (kRegSH > 1) {
 #pragma unroll
-    for (int q = 0; q < K * 3; ++q) sh[q] = __ldg(P.sh + (size_t)i * K * 3 + q);
+        for (int q = 0; q < K * 3; ++q) sh_reg[q] = __ldg(P.sh + (size_t)i * K * 3 + q);
+    }
+    const float* shp = P.sh + (size_t)i * K * 3;
     float dmin = CUDART_INF_F;
 #pragma unroll
     for (int k = 0; k < V; ++k) {
@@ -207,9 +242,11 @@ __global__ void __launch_bounds__(128) k_chain(PrimsDev P, CamsParam cams,
     float gv[V][3];
 #pragma unroll
     for (int k = 0; k < V; ++k) gv[k][0] = gv[k][1] = gv[k][2] = 0.f;
-    float gsh[K * 3];
+    float gsh[PART != 0 ? K * 3 : 1];
+    if constexpr (PART != 0) {
 #pragma unroll
-    for (int q = 0; q < K * 3; ++q) gsh[q] = 0.f;
+        for (int q = 0; q < K * 3; ++q) gsh[q] = 0.f;
+    }
     float gsigma = 0.f;
     float vg_sum = 0.f;     // view-space position-gradient norms of the visible views
     uint32_t vg_count = 0;
@@ -221,8 +258,13 @@ __global__ void __launch_bounds__(128) k_chain(PrimsDev P, CamsParam cams,
         const CamDev& cm = cams.cam[cv];
         const float* A = acc + r * Acc<V>::kFloats;
         bool any = false;
+        if constexpr (PART == 1) {
 #pragma unroll
-        for (int q = 0; q < Acc<V>::kFloats; ++q) any |= A[q] != 0.f;
+            for (int q = 0; q < 3; ++q) any |= A[3 * F + q] != 0.f;
+        } else {
+#pragma unroll
+            for (int q = 0; q < Acc<V>::kFloats; ++q) any |= A[q] != 0.f;
+        }
         if (!any) continue;   // no pixel produced a gradient for this record
         float ga_rgb[3], ga_sig;
         ga_rgb[0] = A[3 * F]; ga_rgb[1] = A[3 * F + 1]; ga_rgb[2] = A[3 * F + 2];
@@ -230,6 +272,8 @@ __global__ void __launch_bounds__(128) k_chain(PrimsDev P, CamsParam cams,
         const uint32_t meta = __float_as_uint(rec[r * Rec<V>::kFloats + 3]);
 
         Geom g;
+        float gtc[3] = {0.f, 0.f, 0.f};
+        if constexpr (PART != 1) {
         centre_geom(cm, c, g);
         float q[V][3], d[V][3];
 #pragma unroll
@@ -288,7 +332,7 @@ __global__ void __launch_bounds__(128) k_chain(PrimsDev P, CamsParam cams,
         // q_k = J (t_k - tc); x_c = phi_x(tc), y_c = phi_y(tc).  gtc collects
         // the terms of tc as the linearisation anchor, gsum the vertex terms
         // (which enter tc with the opposite sign).
-        float gtc[3] = {0.f, 0.f, 0.f}, gsum[3] = {0.f, 0.f, 0.f};
+        float gsum[3] = {0.f, 0.f, 0.f};
         float gJ00 = 0.f, gJ02 = 0.f, gJ11 = 0.f, gJ12 = 0.f, gJ2[3] = {0.f, 0.f, 0.f};
 #pragma unroll
         for (int k = 0; k < V; ++k) {
@@ -331,7 +375,9 @@ __global__ void __launch_bounds__(128) k_chain(PrimsDev P, CamsParam cams,
         for (int a = 0; a < 3; ++a)
             gc[a] += cm.R[a] * (gtc[0] - gsum[0]) + cm.R[3 + a] * (gtc[1] - gsum[1]) +
                      cm.R[6 + a] * (gtc[2] - gsum[2]);
+        }
 
+        if constexpr (PART != 0) {
         // colour -> SH coefficients and view direction
         float dir[3] = {c[0] - cm.campos[0], c[1] - cm.campos[1], c[2] - cm.campos[2]};
         const float dist = sqrtf(dir[0] * dir[0] + dir[1] * dir[1] + dir[2] * dir[2]);
@@ -339,6 +385,22 @@ __global__ void __launch_bounds__(128) k_chain(PrimsDev P, CamsParam cams,
         dir[0] *= idl; dir[1] *= idl; dir[2] *= idl;
         float Y[16];
         sh_basis<DEG>(dir[0], dir[1], dir[2], Y);
+        float sh[K * 3];
+        if constexpr (kVecSH) {
+            if (sh_aligned) {
+#pragma unroll
+                for (int q = 0; q < K * 3 / 4; ++q) {
+                    const float4 t = ld4_each(shp + 4 * q);
+                    sh[4 * q] = t.x; sh[4 * q + 1] = t.y; sh[4 * q + 2] = t.z; sh[4 * q + 3] = t.w;
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < K * 3; ++q) sh[q] = ld_each(shp + q);
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < K * 3; ++q) sh[q] = sh_reg[kRegSH > 1 ? q : 0];
+        }
         float grgb[3];
 #pragma unroll
         for (int ch = 0; ch < 3; ++ch) {
@@ -363,17 +425,20 @@ __global__ void __launch_bounds__(128) k_chain(PrimsDev P, CamsParam cams,
             gw[a] = (gdir[a] - dir[a] * dd) * idl;
             gc[a] += gw[a];
         }
-        if (P.grad_sum) {
-            // translating the whole primitive leaves t_k - tc unchanged: its
-            // camera-space gradient is the anchor terms plus the colour's
-            float gt[3];
+        if constexpr (PART == 2) {
+            if (P.grad_sum) {
+                // translating the whole primitive leaves t_k - tc unchanged:
+                // its camera-space gradient is the anchor terms plus the colour's
+                float gt[3];
 #pragma unroll
-            for (int a = 0; a < 3; ++a)
-                gt[a] = gtc[a] + cm.R[3 * a] * gw[0] + cm.R[3 * a + 1] * gw[1] + cm.R[3 * a + 2] * gw[2];
-            vg_sum += ndc_grad_norm(cm, gt, g.tc[2]);
+                for (int a = 0; a < 3; ++a)
+                    gt[a] = gtc[a] + cm.R[3 * a] * gw[0] + cm.R[3 * a + 1] * gw[1] + cm.R[3 * a + 2] * gw[2];
+                vg_sum += ndc_grad_norm(cm, gt, g.tc[2]);
+            }
+        }
         }
 
-        gsigma += ga_sig;
+        if constexpr (PART != 1) gsigma += ga_sig;
     }
     if (P.grad_sum) {
         P.grad_sum[i] += vg_sum;
@@ -382,6 +447,17 @@ __global__ void __launch_bounds__(128) k_chain(PrimsDev P, CamsParam cams,
 
     // Eq. 1 with d_min frozen: d sigma / d alpha = 0.99 / ((1 - 0.99 alpha) 2 d_min)
     const float galpha = gsigma != 0.f ? gsigma * kAlphaScale / ((1.f - kAlphaScale * alpha) * 2.f * dmin) : 0.f;
+    if constexpr (PART == 1) {
+        // after PART 0, which wrote (or added) the geometric terms
+#pragma unroll
+        for (int a = 0; a < 3; ++a) dcentre[3 * (size_t)i + a] += gc[a];
+#pragma unroll
+        for (int q = 0; q < K * 3; ++q) {
+            float& o = dsh[(size_t)i * K * 3 + q];
+            o = accumulate ? o + gsh[q] : gsh[q];
+        }
+        return;
+    }
     if (accumulate) {
 #pragma unroll
         for (int a = 0; a < 3; ++a) dcentre[3 * (size_t)i + a] += gc[a];
@@ -390,8 +466,10 @@ __global__ void __launch_bounds__(128) k_chain(PrimsDev P, CamsParam cams,
 #pragma unroll
             for (int a = 0; a < 3; ++a) dverts[((size_t)i * V + k) * 3 + a] += gv[k][a];
         dopacity[i] += galpha;
+        if constexpr (PART == 2) {
 #pragma unroll
-        for (int q = 0; q < K * 3; ++q) dsh[(size_t)i * K * 3 + q] += gsh[q];
+            for (int q = 0; q < K * 3; ++q) dsh[(size_t)i * K * 3 + q] += gsh[q];
+        }
     } else {
 #pragma unroll
         for (int a = 0; a < 3; ++a) dcentre[3 * (size_t)i + a] = gc[a];
@@ -400,8 +478,10 @@ __global__ void __launch_bounds__(128) k_chain(PrimsDev P, CamsParam cams,
 #pragma unroll
             for (int a = 0; a < 3; ++a) dverts[((size_t)i * V + k) * 3 + a] = gv[k][a];
         dopacity[i] = galpha;
+        if constexpr (PART == 2) {
 #pragma unroll
-        for (int q = 0; q < K * 3; ++q) dsh[(size_t)i * K * 3 + q] = gsh[q];
+            for (int q = 0; q < K * 3; ++q) dsh[(size_t)i * K * 3 + q] = gsh[q];
+        }
     }
 }
 
@@ -417,11 +497,17 @@ cudaError_t launch_pre_t(const PrimsDev& P, const CamsParam& cams, float* rec, u
 template <int V, int DEG>
 cudaError_t launch_chain_t(const PrimsDev& P, const CamsParam& cams, const float* rec,
                            const uint32_t* counts, const float* acc, float* dc, float* dv, float* dop,
-                           float* dsh, int accumulate, cudaStream_t st) {
+                           float* dsh, int accumulate, int split, cudaStream_t st) {
     const int bs = 128;
     const int grid = (P.n + bs - 1) / bs;
-    if (grid > 0)
-        k_chain<V, DEG><<<grid, bs, 0, st>>>(P, cams, rec, counts, acc, dc, dv, dop, dsh, accumulate);
+    if (grid > 0) {
+        if (P.grad_sum || !split) {
+            k_chain<V, DEG, 2><<<grid, bs, 0, st>>>(P, cams, rec, counts, acc, dc, dv, dop, dsh, accumulate);
+        } else {
+            k_chain<V, DEG, 0><<<grid, bs, 0, st>>>(P, cams, rec, counts, acc, dc, dv, dop, dsh, accumulate);
+            k_chain<V, DEG, 1><<<grid, bs, 0, st>>>(P, cams, rec, counts, acc, dc, dv, dop, dsh, accumulate);
+        }
+    }
     return cudaGetLastError();
 }
 
@@ -444,8 +530,8 @@ cudaError_t launch_preprocess(int V, int deg, const PrimsDev& P, const CamsParam
 
 cudaError_t launch_chain(int V, int deg, const PrimsDev& P, const CamsParam& cams, const float* rec,
                          const uint32_t* counts, const float* acc, float* dc, float* dv, float* dop,
-                         float* dsh, int accumulate, cudaStream_t st) {
-#define CALL(v, d) launch_chain_t<v, d>(P, cams, rec, counts, acc, dc, dv, dop, dsh, accumulate, st)
+                         float* dsh, int accumulate, int split, cudaStream_t st) {
+#define CALL(v, d) launch_chain_t<v, d>(P, cams, rec, counts, acc, dc, dv, dop, dsh, accumulate, split, st)
     LP_DISPATCH(V, deg, CALL)
 #undef CALL
 }
