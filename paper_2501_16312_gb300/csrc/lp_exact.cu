@@ -41,7 +41,6 @@ constexpr int kThreadsX = kTilePixels / kPixX;
 template <int V> struct RecX {
     static constexpr int F = Kind<V>::F;
     static constexpr int kFloats = 8 + 4 * F;   // 40 (octahedron), 24 (tetrahedron)
-    static constexpr int kVec4 = kFloats / 4;
 };
 
 // per face slot (= face) dL/d(p, q, L0, D0); then rgb, sigma, c_z (the last
@@ -153,7 +152,7 @@ __global__ void __launch_bounds__(128) k_preprocess_x(PrimsDev P, CamsParam cams
         counts[r] = (uint32_t)((tx1 - tx0 + 1) * (ty1 - ty0 + 1));
         trect[r] = make_int4(cm.tile_base + ty0 * cm.tiles_x + tx0, cm.tiles_x, tx1 - tx0 + 1, ty1 - ty0 + 1);
 
-        float out[RecX<V>::kFloats];
+        float out[8];   // header: anchor, sigma, meta, rgb, centre depth
         const float icz = 1.f / g.tc[2];
         float pl[F][4];
         bool front[F];
@@ -172,15 +171,16 @@ __global__ void __launch_bounds__(128) k_preprocess_x(PrimsDev P, CamsParam cams
             front[f] = 1.f + np[0] * g.tc[0] + np[1] * g.tc[1] + np[2] * g.tc[2] < 0.f;
             nf += front[f] ? 1 : 0;
         }
-        // slots: faces the camera sees from outside first (entry faces)
+        // slots: faces the camera sees from outside first (entry faces); a
+        // slot is one float4, stored at its computed address
+        float4* dst = reinterpret_cast<float4*>(rec + r * RecX<V>::kFloats);
         uint32_t meta = (uint32_t)nf;
         int sf = 0, sb = nf;
 #pragma unroll
         for (int f = 0; f < F; ++f) {
             const int s = front[f] ? sf++ : sb++;
             meta |= (uint32_t)f << (4 + 3 * s);
-#pragma unroll
-            for (int m = 0; m < 4; ++m) out[8 + 4 * s + m] = pl[f][m];
+            dst[2 + s] = make_float4(pl[f][0], pl[f][1], pl[f][2], pl[f][3]);
         }
         float dir[3] = {c[0] - cm.campos[0], c[1] - cm.campos[1], c[2] - cm.campos[2]};
         const float idl = rsqrtf(dir[0] * dir[0] + dir[1] * dir[1] + dir[2] * dir[2]);
@@ -194,13 +194,8 @@ __global__ void __launch_bounds__(128) k_preprocess_x(PrimsDev P, CamsParam cams
             for (int k = 0; k < K; ++k) s = fmaf(Y[k], sh[3 * k + ch], s);
             out[4 + ch] = fmaxf(s, 0.f);
         }
-        out[0] = __int_as_float(g.X0); out[1] = __int_as_float(g.Y0); out[2] = sigma;
-        out[3] = __uint_as_float(meta);
-        out[7] = g.tc[2];
-        float4* dst = reinterpret_cast<float4*>(rec + r * RecX<V>::kFloats);
-#pragma unroll
-        for (int k = 0; k < RecX<V>::kVec4; ++k)
-            dst[k] = make_float4(out[4 * k], out[4 * k + 1], out[4 * k + 2], out[4 * k + 3]);
+        dst[0] = make_float4(__int_as_float(g.X0), __int_as_float(g.Y0), sigma, __uint_as_float(meta));
+        dst[1] = make_float4(out[4], out[5], out[6], g.tc[2]);
     }
     if (P.px_max && px_side > P.px_max[i]) P.px_max[i] = px_side;   // one thread per primitive
 }
