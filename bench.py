@@ -136,7 +136,11 @@ def blend_flops(F, pairs):
 # kernel from one ncu capture of this workload, keyed by a hash of the kernel's
 # sources: a kernel edited since its capture reports traffic null.
 MEASURED_TRAFFIC = {
-    # "blend_bwd": {"bytes": ..., "sources_sha1": "...", "capture": "..."},
+    # dram__bytes_read.sum + dram__bytes_write.sum of one launch at full size
+    # (one ncu pass; profiles/dram_traffic_blend_bwd_octa500k_8x1264x832.md);
+    # ignored once the kernel's sources change
+    "blend_bwd": {"bytes": 183971072 + 3079424, "sources_sha1": "e91e24bb9f55e659cfb43100339642366590f710",
+                  "capture": "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum -k regex:k_blend_bwd -s 2 -c 1"},
 }
 KERNEL_SOURCES = {
     "blend_fwd": ("lp_blend_fwd.cu", "lp_blend.cuh", "lp_device.cuh"),
