@@ -38,8 +38,8 @@ def parse_args():
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 4],
-                   help="1-3: render fwd+bwd workloads; 4: the optimisation step "
+    p.add_argument("--config", type=int, default=2, choices=[0, 1, 2, 3, 4],
+                   help="0-3: render fwd+bwd workloads; 4: the optimisation step "
                         "(parameter layer, render, L1, backward, Adam) on 2M octahedra")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-per-view", action="store_true")
@@ -238,7 +238,8 @@ def roofline(rast, stages, kind, sh_degree, n, n_cams, clk, dev):
 # ---------------------------------------------------------------- CPU oracle
 def cpu_baseline(workload, target_s, gpu_image=None, seed=11):
     """Time the FP64 oracle (forward + adjoint) on a bounded sample of pixels:
-    random pixels of camera 0, then whole further cameras while the time
+    random pixels of camera 0 (a sample grown until one run takes a quarter of
+    the budget, or all of the camera), then whole further cameras while the
     budget lasts; returns the rate in Mpixel/s."""
     import numpy as np
     import oracle
@@ -254,14 +255,16 @@ def cpu_baseline(workload, target_s, gpu_image=None, seed=11):
 
     cam0 = workload.cameras[0]
     n0 = cam0.width * cam0.height
-    # fixed (preprocess + sort of all primitives) and per-pixel cost on camera 0
-    t1 = run(0, rng.choice(n0, 256, replace=False))[0]
-    t2 = run(0, rng.choice(n0, 1024, replace=False))[0]
-    per_px = max((t2 - t1) / 768, 1e-7)
-    fixed = max(t1 - 256 * per_px, 0.0)
-    npix0 = int(min(n0, max(1024, (target_s - fixed) / per_px)))
-    q0 = rng.choice(n0, npix0, replace=False)
-    dt, rgb, info = run(0, q0)
+    # random pixels of camera 0, the sample growing 4x while a run stays under
+    # a quarter of the budget (the cost per pixel varies too much between
+    # scenes to extrapolate from one small run); the last run is the sample
+    npix0 = min(n0, 1024)
+    while True:
+        q0 = rng.choice(n0, npix0, replace=False)
+        dt, rgb, info = run(0, q0)
+        if npix0 >= n0 or dt >= target_s / 4:
+            break
+        npix0 = min(n0, npix0 * 4)
     total_px, total_t, cams_used = npix0, dt, 1
     for ci in range(1, len(workload.cameras)):
         if total_t >= target_s:
@@ -304,10 +307,12 @@ def reference_arm(args, workload, metric=METRIC):
         oracle.render_pixels(workload.scene, cam, px, py, bg=workload.bg, dL_dC=g)
         return time.perf_counter() - t0
 
-    t1, t2 = step(256), step(1024)
-    per_px = max((t2 - t1) / 768, 1e-7)
-    fixed = max(t1 - 256 * per_px, 0.0)
-    npix = int(min(n_all, max(1024, (per_step_s - fixed) / per_px)))
+    # grow the per-step sample 4x while one step stays under a quarter of its
+    # time (extrapolating from a small run misjudges scenes whose per-pixel
+    # cost varies)
+    npix = min(n_all, 1024)
+    while npix < n_all and step(npix) < per_step_s / 4:
+        npix = min(n_all, npix * 4)
     for _ in range(args.warmup):
         step(npix)
     times = [step(npix) for _ in range(args.steps)]
