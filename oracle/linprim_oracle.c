@@ -217,11 +217,20 @@ static void keyfields_f32(const orc_prims* P, const orc_camera* cam, int i, orc_
         const double* v = P->verts + (size_t)(i * P->nv + k) * 3;
         if ((float)v[0] == c[0] && (float)v[1] == c[1] && (float)v[2] == c[2]) return;
     }
-    kf->visible = 1;
     u = tc[0] / tc[2];
     w = tc[1] / tc[2];
     xc = fx * u; xc = xc + cx;
     yc = fy * w; yc = yc + cy;
+    /* reading: only primitives in the view frustum are drawn (the "Frustum"
+     * count of App. Table 7); the frustum is taken as the projected centre
+     * within 1.3 times the image, normalised device coordinates in [-1.3, 1.3],
+     * decided in binary32 on the key-field values */
+    {
+        const float W = (float)cam->width, H = (float)cam->height;
+        const float lox = -0.15f * W, hix = 1.15f * W, loy = -0.15f * H, hiy = 1.15f * H;
+        if (!(xc >= lox && xc <= hix && yc >= loy && yc <= hiy)) return;
+    }
+    kf->visible = 1;
     j00 = fx / tc[2]; j02 = -(j00 * u);
     j11 = fy / tc[2]; j12 = -(j11 * w);
     for (k = 0; k < P->nv; ++k) {

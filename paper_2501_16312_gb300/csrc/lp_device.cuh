@@ -12,6 +12,10 @@ namespace lp {
 
 constexpr int kMaxCams = 32;
 constexpr float kNearZ = 0.2f;      // centres at camera depth <= 0.2 are culled
+// View frustum in pixels: a centre projecting outside [lo W, hi W] x [lo H, hi H]
+// (normalised device coordinates beyond +-1.3) is culled.
+constexpr float kFrustumLo = -0.15f;
+constexpr float kFrustumHi = 1.15f;
 constexpr float kStopT = 1e-3f;     // Sec. 3.2: stop at cumulative opacity 0.999
 constexpr float kAlphaScale = 0.99f;  // Eq. 1
 constexpr int kStatusCapacity = 1;

@@ -66,6 +66,13 @@ __device__ __forceinline__ bool centre_geom(const CamDev& cm, const float c[3], 
     const float w = __fdiv_rn(g.tc[1], g.tc[2]);
     g.xc = __fadd_rn(__fmul_rn(cm.fx, u), cm.cx);
     g.yc = __fadd_rn(__fmul_rn(cm.fy, w), cm.cy);
+    // the view frustum: the projected centre within 1.3 times the image
+    // (|x_ndc|, |y_ndc| <= 1.3).  Off-axis primitives near the camera plane
+    // would otherwise get linearised boxes covering the whole image.
+    const float W = (float)cm.width, H = (float)cm.height;
+    if (!(g.xc >= __fmul_rn(kFrustumLo, W) && g.xc <= __fmul_rn(kFrustumHi, W) &&
+          g.yc >= __fmul_rn(kFrustumLo, H) && g.yc <= __fmul_rn(kFrustumHi, H)))
+        return false;
     g.j00 = __fdiv_rn(cm.fx, g.tc[2]);
     g.j02 = -__fmul_rn(g.j00, u);
     g.j11 = __fdiv_rn(cm.fy, g.tc[2]);

@@ -220,6 +220,34 @@ def test_full_size_workload(rast):
         off += n
 
 
+def test_full_size_sampled_gradient(rast):
+    """Gradients at full size (500k octahedra, all 8 cameras in one batched
+    forward + backward, the benchmark's schedule) for a loss on 4096 random
+    pixels of camera 0, against the oracle's adjoint of the same pixels."""
+    w = scenes.workload(2)
+    cam = w.cameras[0]
+    q = np.random.default_rng(9).choice(cam.width * cam.height, 4096, replace=False)
+    px, py = (q % cam.width).astype(np.int32), (q // cam.width).astype(np.int32)
+    _, info = oracle.render_pixels(w.scene, cam, px, py)
+    dLc = np.random.default_rng(8).normal(size=(px.size, 3))
+    dLc[info[:, 2] > 0] = 0.0                      # borderline pixels (stop or graze)
+    dL = np.zeros(3 * sum(c.width * c.height for c in w.cameras))
+    n0 = cam.width * cam.height
+    for ch in range(3):
+        dL[ch * n0 + py * cam.width + px] = dLc[:, ch]
+    base = rast.tuning()
+    try:
+        rast.set_tuning(sort_mode=1, batch=32, pixels_per_thread=4, chain_split=0)
+        _, g = gpu_forward_backward(rast, w.scene, w.cameras, (0, 0, 0), dL)
+    finally:
+        rast.set_tuning(**base)
+    _, _, ref = oracle.render_pixels(w.scene, cam, px, py, dL_dC=dLc)
+    rel = assert_grads_match(g, ref)
+    touched = int((np.abs(ref["opacity"]) > 0).sum())
+    print(f"full-size sampled gradient: {touched} primitives touched, relative L2 {rel}")
+    assert touched > 1000
+
+
 def test_permutation_invariance(rast):
     w = scenes.workload(1, scale=0.3)
     img, _ = gpu_forward_backward(rast, w.scene, w.cameras, (0, 0, 0))

@@ -15,6 +15,11 @@ import tests.test_oracle_pins as pins
 SRC = os.path.join(os.path.dirname(oracle.__file__), "linprim_oracle.c")
 
 MUTANTS = {
+    "frustum_off": ("if (!(xc >= lox && xc <= hix && yc >= loy && yc <= hiy)) return;",
+                    "(void)lox; (void)hix; (void)loy; (void)hiy;", ["frustum"]),
+    "frustum_margin_1": ("const float lox = -0.15f * W, hix = 1.15f * W, loy = -0.15f * H, hiy = 1.15f * H;",
+                         "const float lox = 0.0f * W, hix = 1.0f * W, loy = 0.0f * H, hiy = 1.0f * H;",
+                         ["frustum"]),
     "eq1_drop_099": ("-log1p(-0.99 * P->opacity[i])", "-log1p(-P->opacity[i])",
                      ["thin_axis"]),
     "eq1_drop_factor_2": ("/ (2.0 * pp->dmin);", "/ (pp->dmin);", ["thin_axis"]),
@@ -83,6 +88,7 @@ CHECKS = {
     "fd_tetra": pins.test_adjoint_fd_tetrahedra,
     "fd_octa": pins.test_adjoint_fd_octahedra_sh3,
     "keyfields": pins.test_keyfields_are_binary32_replay,
+    "frustum": pins.test_view_frustum_cull,
     "keys_structure": pins.test_keys_structure,
     "ties": pins.test_depth_ties_keep_index_order,
     "param_scipy": lambda o: [params_pins.test_vertices_match_scipy_rotation(k) for k in (6, 4)],

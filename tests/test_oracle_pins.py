@@ -304,6 +304,48 @@ def test_permutation_invariance(orc):
 
 # ------------------------------------------------------------- keys and tiles
 
+def _frustum_scene(pos, dist=0.05):
+    c = np.array([pos], np.float64)
+    v = scenes.octahedra_from_axes(c, np.eye(3)[None], np.array([[dist, dist, dist]]))
+    return scenes.Scene(6, c.astype(np.float32), v.astype(np.float32), np.array([0.8], np.float32),
+                        np.full((1, 1, 3), 0.5, np.float32), 0)
+
+
+def test_view_frustum_cull(orc):
+    """A primitive is drawn only if its projected centre lies within 1.3
+    times the image (normalised device coordinates in [-1.3, 1.3]): centres at
+    x_ndc = 1.25 are kept, at 1.35 culled (both axes, both sides).  A primitive
+    beside the camera, just in front of the near plane, would otherwise get a
+    linearised box covering the whole image."""
+    cam = scenes.make_camera((0.0, 0.0, 0.0), 160, 100, 60.0, target=(0.0, 0.0, 1.0))
+    M = cam.viewmat.astype(np.float64)
+    z = 3.0
+    for axis, size, f_, c_ in ((0, cam.width, cam.fx, cam.cx), (1, cam.height, cam.fy, cam.cy)):
+        for ndc, keep in ((1.25, True), (1.35, False), (-1.25, True), (-1.35, False)):
+            pix = (ndc + 1.0) * size / 2.0                # pixel coordinate of that NDC
+            t = np.zeros(3)
+            t[axis] = (pix - float(c_)) * z / float(f_)   # camera-space offset
+            t[2] = z
+            world = M[:3, :3].T @ (t - M[:3, 3])
+            pp = orc.preprocess(_frustum_scene(world), cam)
+            assert bool(pp["visible"][0]) == keep, (axis, ndc)
+    # beside the camera, 0.21 in front of it and 5 to the side: its ray-space
+    # box (x_c +- |J02| d, J02 = -f_x x / z^2) would span the whole image, yet
+    # it is culled; the same primitive straight ahead is drawn
+    z, side, d = 0.21, 5.0, 0.3
+    xc = float(cam.fx) * side / z + float(cam.cx)
+    half = float(cam.fx) * side / z ** 2 * d
+    assert xc - half < 0 and xc + half > cam.width
+    for side_, keep in ((side, False), (0.0, True)):
+        t = np.array([side_, 0.0, z])
+        world = M[:3, :3].T @ (t - M[:3, 3])
+        sc = _frustum_scene(world, dist=d)
+        pp = orc.preprocess(sc, cam)
+        assert bool(pp["visible"][0]) == keep
+        img = orc.render(sc, [cam]).reshape(3, -1)
+        assert (np.abs(img).max() > 0) == keep
+
+
 def test_keyfields_are_binary32_replay(orc):
     """The culling / depth key / pixel rectangle come from binary32 with one
     rounding per operation (the centre transformed to the camera frame, each
@@ -323,11 +365,14 @@ def test_keyfields_are_binary32_replay(orc):
         tc = tr(sc.centre[i])
         assert np.array([tc[2]], np.float32).view(np.uint32)[0] == pp["zbits"][i]
         vis = bool(tc[2] > f(0.2))
+        if vis:
+            u, w_ = f(tc[0] / tc[2]), f(tc[1] / tc[2])
+            xc, yc = f(f(f(cam.fx) * u) + f(cam.cx)), f(f(f(cam.fy) * w_) + f(cam.cy))
+            W, H = f(cam.width), f(cam.height)
+            vis = bool(f(f(-0.15) * W) <= xc <= f(f(1.15) * W) and f(f(-0.15) * H) <= yc <= f(f(1.15) * H))
         assert vis == pp["visible"][i]
         if not vis:
             continue
-        u, w_ = f(tc[0] / tc[2]), f(tc[1] / tc[2])
-        xc, yc = f(f(f(cam.fx) * u) + f(cam.cx)), f(f(f(cam.fy) * w_) + f(cam.cy))
         j00, j11 = f(f(cam.fx) / tc[2]), f(f(cam.fy) / tc[2])
         j02, j12 = -f(j00 * u), -f(j11 * w_)
         qx, qy = [], []
