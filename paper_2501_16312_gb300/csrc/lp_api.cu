@@ -37,6 +37,7 @@ struct lp_ctx {
     float aa_kernel = 0.f;      // 2D filter size in pixels (0 = off)
     bool exact = false;         // spans along the true perspective ray
     bool fwd_exact = false;     // mode of the last forward
+    uint32_t contrib_stride = 0;
     // densification statistics gathered by forward and backward (null: off)
     float* st_grad_sum = nullptr;
     uint32_t* st_grad_count = nullptr;
@@ -386,7 +387,7 @@ static lp_status reserve_impl(lp_ctx* ctx, long long records, long long entries,
     long long sb2 = lp::scan_blocks((long long)lp::sort_hist_elems(hmax));
     LP_TRY(ensure(ctx, ctx->scan_tmp, sb > sb2 ? sb : sb2, false, "scan blocks"));
     LP_TRY(ensure(ctx, ctx->emit_part, (long long)lp::emit_blocks(records, kcap) + 1, false, "emit partition"));
-    LP_TRY(ensure(ctx, ctx->contrib, kcap / 32 + 2, false, "contributor mask"));
+    LP_TRY(ensure(ctx, ctx->contrib, (kcap / 32 + 2) * 8, false, "contributor mask"));
     LP_TRY(ensure(ctx, ctx->ranges, tiles, false, "tile ranges"));
     LP_TRY(ensure(ctx, ctx->last, pixels, false, "pixel state"));
     LP_TRY(ensure(ctx, ctx->tl, pixels, false, "pixel state"));
@@ -499,7 +500,8 @@ lp_status lp_render_forward(lp_ctx* ctx, const lp_prims* prims, const lp_camera*
                   "scan blocks"));
     LP_TRY(ensure(ctx, ctx->emit_part, (long long)lp::emit_blocks(records, bound) + 1, cap_mode,
                   "emit partition"));
-    LP_TRY(ensure(ctx, ctx->contrib, bound / 32 + 2, cap_mode, "contributor mask"));
+    LP_TRY(ensure(ctx, ctx->contrib, (bound / 32 + 2) * 8, cap_mode, "contributor mask"));
+    ctx->contrib_stride = (uint32_t)(bound / 32 + 2);
 
     const int tile_bits = bits_for(tiles);
     int key_bits;
@@ -554,7 +556,8 @@ lp_status lp_render_forward(lp_ctx* ctx, const lp_prims* prims, const lp_camera*
     a.count = false;
     if (!exact) {
         a.contrib = ctx->contrib.p;
-        LP_CUDA(cudaMemsetAsync(ctx->contrib.p, 0, (size_t)(bound / 32 + 2) * sizeof(uint32_t), st));
+        a.contrib_stride = ctx->contrib_stride;
+        LP_CUDA(cudaMemsetAsync(ctx->contrib.p, 0, (size_t)(bound / 32 + 2) * 8 * sizeof(uint32_t), st));
     }
     LP_CUDA(cudaMemsetAsync(ctx->d_tile_counter, 0, sizeof(int), st));
     if (a.grid > 0) {
@@ -612,6 +615,7 @@ lp_status lp_render_backward(lp_ctx* ctx, const float* dL_dimages, float* dcentr
     a.tl = ctx->tl.p;
     a.acc = ctx->acc.p;
     a.contrib = exact ? nullptr : ctx->contrib.p;
+    a.contrib_stride = ctx->contrib_stride;
     a.tile_counter = ctx->d_tile_counter + 1;
     LP_CUDA(cudaMemsetAsync(ctx->d_tile_counter + 1, 0, sizeof(int), st));
     if (a.grid > 0) {

@@ -1,7 +1,7 @@
 // Backward per-tile rasterization (sm_103a).
 //
-// Entries the forward blended at no pixel of their tile (its per-entry mask)
-// are skipped without evaluating their spans.
+// A warp skips the entries the forward blended at none of its pixels (the
+// forward's per-warp mask) without evaluating their spans.
 //
 // Sec. 3.4 "Rasterization Backpropagation": each tile walks its list back to
 // front from the furthest last contributor of its pixels, recomputes every
@@ -37,7 +37,7 @@ __global__ void __launch_bounds__(kTilePixels / PIX, 3 * PIX) k_blend_bwd(
     const float* __restrict__ rec, const uint32_t* __restrict__ vals, const uint2* __restrict__ ranges,
     CamsParam cams, float bg0, float bg1, float bg2, const float* __restrict__ dimage,
     const uint32_t* __restrict__ last_in, const float* __restrict__ tl_in, float* __restrict__ acc,
-    int* __restrict__ tile_counter, const uint32_t* __restrict__ contrib) {
+    int* __restrict__ tile_counter, const uint32_t* __restrict__ contrib, uint32_t cstride) {
     constexpr int F = Kind<V>::F;
     constexpr int ACC = Acc<V>::kFloats;
     constexpr int NT = kTilePixels / PIX;
@@ -91,9 +91,10 @@ __global__ void __launch_bounds__(kTilePixels / PIX, 3 * PIX) k_blend_bwd(
             for (int j = nb - 1; j >= 0; --j) {
                 const uint32_t idx = (uint32_t)(lo + j);
                 if (contrib) {
-                    // the forward blended this entry at no pixel of the tile
+                    // the forward blended this entry at none of this warp's pixels
                     const uint32_t e = rg.x + idx;
-                    if (!((__ldg(contrib + (e >> 5)) >> (e & 31u)) & 1u)) continue;
+                    const uint32_t* cw = contrib + (size_t)(tid >> 5) * cstride;
+                    if (!((__ldg(cw + (e >> 5)) >> (e & 31u)) & 1u)) continue;
                 }
                 const Staged<V>& p = sm[j];
                 bool any = false;
@@ -106,8 +107,8 @@ __global__ void __launch_bounds__(kTilePixels / PIX, 3 * PIX) k_blend_bwd(
 #pragma unroll
                 for (int i = 0; i < PIX; ++i) c[i] = false;
                 if (any) {
-                    // one pass with the entry/exit slots: with entries that no
-                    // pixel of the tile blended skipped, most warps contribute
+                    // one pass with the entry/exit slots: with the entries this
+                    // warp blended nowhere skipped, most warps contribute
                     spans<V, PIX, true>(p, (float)lx0, (float)ly, sp, sf, sb);
 #pragma unroll
                     for (int i = 0; i < PIX; ++i) {
@@ -217,7 +218,7 @@ template <int V, int BATCH, int PIX>
 cudaError_t bwd_t(const BlendArgs& a, cudaStream_t st) {
     k_blend_bwd<V, BATCH, PIX><<<a.grid, kTilePixels / PIX, 0, st>>>(
         a.rec, a.vals, a.ranges, *a.cams, a.bg[0], a.bg[1], a.bg[2], a.dimage, a.last, a.tl, a.acc,
-        a.tile_counter, a.contrib);
+        a.tile_counter, a.contrib, a.contrib_stride);
     return cudaGetLastError();
 }
 

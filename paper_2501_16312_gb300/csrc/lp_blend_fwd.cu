@@ -26,7 +26,7 @@ __global__ void __launch_bounds__(kTilePixels / PIX) k_blend_fwd(
     CamsParam cams, float bg0, float bg1, float bg2, float* __restrict__ image,
     uint32_t* __restrict__ last_out, float* __restrict__ tl_out, int* __restrict__ tile_counter,
     unsigned long long* __restrict__ pair_counts, float* __restrict__ depth_out,
-    uint32_t* __restrict__ contrib) {
+    uint32_t* __restrict__ contrib, uint32_t cstride) {
     constexpr bool COUNT = MODE == 1;
     constexpr bool DEPTH = MODE == 2;
     constexpr float kStop = DEPTH ? 0.5f : kStopT;
@@ -65,7 +65,10 @@ __global__ void __launch_bounds__(kTilePixels / PIX) k_blend_fwd(
         for (int b0 = 0; b0 < n; b0 += BATCH) {
             if (__syncthreads_count(!tdone) == 0) break;
             const int nb = min(BATCH, n - b0);
-            for (int j = tid; j < nb; j += NT) stage_record<V>(rec, vals[rg.x + b0 + j], tg.tx0, tg.ty0, sm[j]);
+            for (int j = tid; j < nb; j += NT) {
+                stage_record<V>(rec, vals[rg.x + b0 + j], tg.tx0, tg.ty0, sm[j]);
+                sm[j].bands = band_mask<V, 2 * PIX>(sm[j]);
+            }
             __syncthreads();
             if (__any_sync(0xffffffffu, !tdone)) {   // warp-uniform, as the exit below
                 bool stop = false;
@@ -78,6 +81,8 @@ __global__ void __launch_bounds__(kTilePixels / PIX) k_blend_fwd(
 #pragma unroll
                             for (int i = 0; i < PIX; ++i) n_iter += !done[i];
                         }
+                        // warp-uniform: no pixel of this warp's rows can meet it
+                        if (!((p.bands >> (tid >> 5)) & 1u)) continue;
                         float sp[PIX];
                         spans<V, PIX, false>(p, (float)lx0, (float)ly, sp, nullptr, nullptr);
                         tdone = true;
@@ -120,8 +125,9 @@ __global__ void __launch_bounds__(kTilePixels / PIX) k_blend_fwd(
                         if (lane == 0 && bm) {
                             const uint32_t e0 = rg.x + (uint32_t)(b0 + jw);
                             const uint32_t w = e0 >> 5, sh = e0 & 31u;
-                            atomicOr(contrib + w, bm << sh);
-                            if (sh) atomicOr(contrib + w + 1, bm >> (32u - sh));
+                            uint32_t* cw = contrib + (size_t)(tid >> 5) * cstride;   // this warp's mask
+                            atomicOr(cw + w, bm << sh);
+                            if (sh) atomicOr(cw + w + 1, bm >> (32u - sh));
                         }
                     }
                 }
@@ -175,15 +181,15 @@ cudaError_t fwd_t(const BlendArgs& a, cudaStream_t st) {
     if (a.depth)
         k_blend_fwd<V, BATCH, PIX, 2><<<a.grid, NT, 0, st>>>(
             a.rec, a.vals, a.ranges, *a.cams, a.bg[0], a.bg[1], a.bg[2], a.image, a.last, a.tl,
-            a.tile_counter, a.pair_counts, a.depth, nullptr);
+            a.tile_counter, a.pair_counts, a.depth, nullptr, 0u);
     else if (a.count)
         k_blend_fwd<V, BATCH, PIX, 1><<<a.grid, NT, 0, st>>>(
             a.rec, a.vals, a.ranges, *a.cams, a.bg[0], a.bg[1], a.bg[2], a.image, a.last, a.tl,
-            a.tile_counter, a.pair_counts, nullptr, a.contrib);
+            a.tile_counter, a.pair_counts, nullptr, a.contrib, a.contrib_stride);
     else
         k_blend_fwd<V, BATCH, PIX, 0><<<a.grid, NT, 0, st>>>(
             a.rec, a.vals, a.ranges, *a.cams, a.bg[0], a.bg[1], a.bg[2], a.image, a.last, a.tl,
-            a.tile_counter, a.pair_counts, nullptr, a.contrib);
+            a.tile_counter, a.pair_counts, nullptr, a.contrib, a.contrib_stride);
     return cudaGetLastError();
 }
 

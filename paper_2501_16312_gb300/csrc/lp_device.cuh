@@ -251,7 +251,41 @@ template <int V> struct alignas(16) Staged {
     float dx0, dy0;    // tx0 - X0, ty0 - Y0 (integers)
     int nf;
     int rec;           // record index (camera * n + primitive)
+    // bit w: band w of the tile (rows [w BH, (w + 1) BH)) may hold a pixel
+    // whose ray meets the primitive; clear only when some entry/exit face
+    // pair proves it cannot, with a margin above binary32 rounding
+    uint32_t bands;
 };
+
+// The ray meets the primitive at pixel p only if every entry face is below
+// every exit face there: d_f(p) < d_b(p).  Each pair's difference is linear
+// in p, so its largest value over a band of rows is at a corner; a band where
+// some pair stays below -margin holds no covered pixel.
+template <int V, int BH>
+__device__ __forceinline__ uint32_t band_mask(const Staged<V>& s) {
+    constexpr int F = Kind<V>::F;
+    constexpr int NB = 16 / BH;
+    const int nf = s.nf;
+    if (nf <= 0 || nf >= F) return 0u;
+    uint32_t mask = (1u << NB) - 1u;
+    for (int f = 0; f < nf; ++f) {
+        const float4 pf = s.pl[f];
+        for (int b = nf; b < F; ++b) {
+            const float4 pb = s.pl[b];
+            const float da = pb.x - pf.x, db = pb.y - pf.y, de = pb.z - pf.z;
+            const float margin = 1e-5f * (fabsf(pb.z) + fabsf(pf.z) + 15.f * (fabsf(pb.x) + fabsf(pf.x) +
+                                                                             fabsf(pb.y) + fabsf(pf.y))) + 1e-30f;
+            const float xmax = fmaxf(0.f, 15.f * da);
+#pragma unroll
+            for (int w = 0; w < NB; ++w) {
+                const float y0 = (float)(w * BH), y1 = (float)(w * BH + BH - 1);
+                const float m = de + xmax + fmaxf(db * y0, db * y1);
+                if (m < -margin) mask &= ~(1u << w);
+            }
+        }
+    }
+    return mask;
+}
 
 template <int V>
 __device__ __forceinline__ void stage_record(const float* __restrict__ rec, int r, int tx0, int ty0,

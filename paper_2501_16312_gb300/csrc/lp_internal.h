@@ -70,7 +70,9 @@ struct BlendArgs {
     unsigned long long* pair_counts;
     bool count;
     float* depth;          // depth pass output (forward kernel in depth mode when non-null)
-    uint32_t* contrib;     // one bit per tile-list entry: it contributes to some pixel of its tile
+    uint32_t contrib_stride = 0;   // words per warp of the contributor mask
+    uint32_t* contrib;     // per warp w of a tile (its bits at contrib + w * contrib_stride), one
+                           // bit per tile-list entry: some pixel of that warp blended the entry
                            // (written by the forward when non-null, read by the backward)
 };
 
