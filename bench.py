@@ -214,7 +214,9 @@ def roofline(rast, stages, kind, sh_degree, n, n_cams, clk, dev):
         work = fl_fwd if dom == "blend_fwd" else fl_bwd
         achieved = work / (stages[dom] * 1e-3) / 1e12
         roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": alu_peak,
-                "unit": "TFLOP/s", "frac": achieved / alu_peak, "traffic": measured_traffic(dom),
+                "unit": "TFLOP/s", "frac": achieved / alu_peak,
+                # the captured traffic is the ray-space kernel's; the exact mode runs other kernels
+                "traffic": None if rast.exact() else measured_traffic(dom),
                 "peak_source": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 flop x "
                                f"{sm_max:.0f} MHz ({peak_src} max clock)"}
     else:
@@ -480,8 +482,10 @@ def ours(args, workload):
     host_in["dL"] = dL.cpu().pin_memory()
     host_out = {"images": torch.empty(3 * P, pin_memory=True),
                 **{k: torch.empty(v.shape, pin_memory=True) for k, v in grads.items()}}
-    pipe = HostPipeline(Rasterizer(local, tuning=rast.tuning()), prims.kind, prims.n, prims.sh_degree,
-                        w.cameras, w.bg)
+    pipe_rast = Rasterizer(local, tuning=rast.tuning())   # same span mode, filter and schedule
+    pipe_rast.set_exact(rast.exact())
+    pipe_rast.set_filter_2d(rast.filter_2d())
+    pipe = HostPipeline(pipe_rast, prims.kind, prims.n, prims.sh_degree, w.cameras, w.bg)
     for _ in range(2):
         pipe.submit(host_in, host_out)
     pipe.synchronize()

@@ -554,11 +554,9 @@ lp_status lp_render_forward(lp_ctx* ctx, const lp_prims* prims, const lp_camera*
     a.tile_counter = ctx->d_tile_counter;
     a.pair_counts = ctx->d_pairs;
     a.count = false;
-    if (!exact) {
-        a.contrib = ctx->contrib.p;
-        a.contrib_stride = ctx->contrib_stride;
-        LP_CUDA(cudaMemsetAsync(ctx->contrib.p, 0, (size_t)(bound / 32 + 2) * 8 * sizeof(uint32_t), st));
-    }
+    a.contrib = ctx->contrib.p;
+    a.contrib_stride = ctx->contrib_stride;
+    LP_CUDA(cudaMemsetAsync(ctx->contrib.p, 0, (size_t)(bound / 32 + 2) * 8 * sizeof(uint32_t), st));
     LP_CUDA(cudaMemsetAsync(ctx->d_tile_counter, 0, sizeof(int), st));
     if (a.grid > 0) {
         if (exact) LP_CUDA(lp::launch_blend_fwd_x(V, a, st));
@@ -614,7 +612,7 @@ lp_status lp_render_backward(lp_ctx* ctx, const float* dL_dimages, float* dcentr
     a.last = ctx->last.p;
     a.tl = ctx->tl.p;
     a.acc = ctx->acc.p;
-    a.contrib = exact ? nullptr : ctx->contrib.p;
+    a.contrib = ctx->contrib.p;
     a.contrib_stride = ctx->contrib_stride;
     a.tile_counter = ctx->d_tile_counter + 1;
     LP_CUDA(cudaMemsetAsync(ctx->d_tile_counter + 1, 0, sizeof(int), st));

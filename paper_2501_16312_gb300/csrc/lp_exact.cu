@@ -320,14 +320,17 @@ __global__ void __launch_bounds__(kThreadsX) k_blend_fwd_x(
     const float* __restrict__ rec, const uint32_t* __restrict__ vals, const uint2* __restrict__ ranges,
     CamsParam cams, float bg0, float bg1, float bg2, float* __restrict__ image,
     uint32_t* __restrict__ last_out, float* __restrict__ tl_out, int* __restrict__ tile_counter,
-    unsigned long long* __restrict__ pair_counts, float* __restrict__ depth_out) {
+    unsigned long long* __restrict__ pair_counts, float* __restrict__ depth_out,
+    uint32_t* __restrict__ contrib, uint32_t cstride) {
     constexpr int PIX = kPixX, NT = kThreadsX, RW = kTile / PIX, BATCH = kBatchX;
     constexpr bool COUNT = MODE == 1, DEPTH = MODE == 2;
     constexpr float kStop = DEPTH ? 0.5f : kStopT;
     __shared__ StagedX<V> sm[BATCH];
     __shared__ int s_tile;
     const int tid = threadIdx.x;
+    const int lane = tid & 31;
     const int ly = tid / RW, lx0 = (tid % RW) * PIX;
+    const bool write_mask = !DEPTH && contrib != nullptr;
     unsigned long long n_iter = 0, n_eval = 0, n_hit = 0, n_eval_last = 0;
     for (;;) {
         if (tid == 0) s_tile = atomicAdd(tile_counter, 1);
@@ -356,8 +359,12 @@ __global__ void __launch_bounds__(kThreadsX) k_blend_fwd_x(
             const int nb = min(BATCH, n - b0);
             for (int j = tid; j < nb; j += NT) stage_record_x<V>(rec, vals[rg.x + b0 + j], tg.tx0, tg.ty0, sm[j]);
             __syncthreads();
-            if (!tdone) {
-                for (int j = 0; j < nb; ++j) {
+            if (__any_sync(0xffffffffu, !tdone)) {   // warp-uniform, as the exit below
+                bool stop = false;
+                for (int jw = 0; jw < nb && !stop; jw += 32) {
+                  uint32_t bm = 0;   // bit j - jw: this thread blended entry b0 + j
+                  const int je = min(nb, jw + 32);
+                  for (int j = jw; j < je; ++j) {
                     const StagedX<V>& p = sm[j];
                     if (COUNT) {
 #pragma unroll
@@ -366,11 +373,13 @@ __global__ void __launch_bounds__(kThreadsX) k_blend_fwd_x(
                     float sp[PIX], en[PIX];
                     spans_x<V, PIX, false>(p, (float)lx0, (float)ly, rn, sp, nullptr, nullptr, DEPTH ? en : nullptr);
                     tdone = true;
+                    bool blended = false;
 #pragma unroll
                     for (int i = 0; i < PIX; ++i) {
                         const bool in = !done[i];
                         if (COUNT) { n_eval += in; ce[i] += in; }
                         if (in && sp[i] > 0.f) {
+                            blended = true;
                             if (COUNT) { ++n_hit; cl[i] = ce[i]; }
                             const float tau = span_tau(p.sigma, sp[i]);
                             const float w = T[i] * (1.f - tau);
@@ -385,7 +394,21 @@ __global__ void __launch_bounds__(kThreadsX) k_blend_fwd_x(
                         }
                         tdone &= done[i];
                     }
-                    if (tdone) break;
+                    if (write_mask && blended) bm |= 1u << (j - jw);
+                    // warp-uniform exit (the mask reduction below needs every lane)
+                    if (__all_sync(0xffffffffu, tdone)) { stop = true; break; }
+                  }
+                  if (write_mask) {
+                      // this warp's bits for entries b0 + jw .. b0 + jw + 31 of the list
+                      bm = __reduce_or_sync(0xffffffffu, bm);
+                      if (lane == 0 && bm) {
+                          const uint32_t e0 = rg.x + (uint32_t)(b0 + jw);
+                          const uint32_t w = e0 >> 5, sh = e0 & 31u;
+                          uint32_t* cw = contrib + (size_t)(tid >> 5) * cstride;
+                          atomicOr(cw + w, bm << sh);
+                          if (sh) atomicOr(cw + w + 1, bm >> (32u - sh));
+                      }
+                  }
                 }
             }
         }
@@ -439,7 +462,7 @@ __global__ void __launch_bounds__(kThreadsX) k_blend_bwd_x(
     const float* __restrict__ rec, const uint32_t* __restrict__ vals, const uint2* __restrict__ ranges,
     CamsParam cams, float bg0, float bg1, float bg2, const float* __restrict__ dimage,
     const uint32_t* __restrict__ last_in, const float* __restrict__ tl_in, float* __restrict__ acc,
-    int* __restrict__ tile_counter) {
+    int* __restrict__ tile_counter, const uint32_t* __restrict__ contrib, uint32_t cstride) {
     constexpr int F = Kind<V>::F;
     constexpr int ACC = AccX<V>::kFloats;
     constexpr int PIX = kPixX, NT = kThreadsX, RW = kTile / PIX, BATCH = kBatchX;
@@ -494,6 +517,12 @@ __global__ void __launch_bounds__(kThreadsX) k_blend_bwd_x(
             for (int j = nb - 1; j >= 0; --j) {
                 const StagedX<V>& p = sm[j];
                 const uint32_t idx = (uint32_t)(lo + j);
+                if (contrib) {
+                    // the forward blended this entry at none of this warp's pixels
+                    const uint32_t e = rg.x + idx;
+                    const uint32_t* cw = contrib + (size_t)(tid >> 5) * cstride;
+                    if (!((__ldg(cw + (e >> 5)) >> (e & 31u)) & 1u)) continue;
+                }
                 bool any = false;
 #pragma unroll
                 for (int i = 0; i < PIX; ++i) any |= idx < last[i];
@@ -838,7 +867,8 @@ cudaError_t launch_blend_fwd_x(int V, const BlendArgs& a, cudaStream_t st) {
 #define FWD(v, m)                                                                                        \
     k_blend_fwd_x<v, m><<<a.grid, kThreadsX, 0, st>>>(a.rec, a.vals, a.ranges, *a.cams, a.bg[0], a.bg[1], \
                                                       a.bg[2], a.image, a.last, a.tl, a.tile_counter,    \
-                                                      a.pair_counts, a.depth)
+                                                      a.pair_counts, a.depth, m == 2 ? nullptr : a.contrib, \
+                                                      a.contrib_stride)
     const int m = a.depth ? 2 : (a.count ? 1 : 0);
     if (V == 6) {
         if (m == 2) FWD(6, 2); else if (m == 1) FWD(6, 1); else FWD(6, 0);
@@ -852,10 +882,12 @@ cudaError_t launch_blend_fwd_x(int V, const BlendArgs& a, cudaStream_t st) {
 cudaError_t launch_blend_bwd_x(int V, const BlendArgs& a, cudaStream_t st) {
     if (V == 6)
         k_blend_bwd_x<6><<<a.grid, kThreadsX, 0, st>>>(a.rec, a.vals, a.ranges, *a.cams, a.bg[0], a.bg[1],
-                                                        a.bg[2], a.dimage, a.last, a.tl, a.acc, a.tile_counter);
+                                                        a.bg[2], a.dimage, a.last, a.tl, a.acc, a.tile_counter,
+                                                        a.contrib, a.contrib_stride);
     else
         k_blend_bwd_x<4><<<a.grid, kThreadsX, 0, st>>>(a.rec, a.vals, a.ranges, *a.cams, a.bg[0], a.bg[1],
-                                                        a.bg[2], a.dimage, a.last, a.tl, a.acc, a.tile_counter);
+                                                        a.bg[2], a.dimage, a.last, a.tl, a.acc, a.tile_counter,
+                                                        a.contrib, a.contrib_stride);
     return cudaGetLastError();
 }
 
