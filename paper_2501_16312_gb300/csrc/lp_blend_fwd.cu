@@ -8,7 +8,9 @@
 // stops once its transmittance falls below 1e-3 (cumulative opacity 0.999),
 // after blending the primitive that crossed it.  A tile stops when all of its
 // pixels have.  Per pixel the kernel keeps, for the backward, the number of
-// list entries up to the last contributor and the transmittance before it.
+// list entries up to the last contributor and the transmittance before it,
+// and per warp one bit per list entry its pixels blended.  A warp skips the
+// records that the staging test proves cover none of its rows.
 //
 // MODE 1 also counts (pixel, primitive) pairs.  MODE 2 is the depth pass
 // (App. "Depth and Surface Reconstruction"): the same walk, stopping each
@@ -89,7 +91,7 @@ __global__ void __launch_bounds__(kTilePixels / PIX) k_blend_fwd(
                         bool blended = false;
 #pragma unroll
                         for (int i = 0; i < PIX; ++i) {
-                            const bool in = !done[i];   // every visited entry is evaluated
+                            const bool in = !done[i];   // visited and not proven uncovered: evaluated
                             if (COUNT) { n_eval += in; ce[i] += in; }
                             if (in && sp[i] > 0.f) {
                                 blended = true;
