@@ -238,6 +238,26 @@ def roofline(rast, stages, kind, sh_degree, n, n_cams, clk, dev):
 
 
 # ---------------------------------------------------------------- CPU oracle
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), or None."""
+    import subprocess
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return None
+
+
 def cpu_baseline(workload, target_s, gpu_image=None, seed=11):
     """Time the FP64 oracle (forward + adjoint) on a bounded sample of pixels:
     random pixels of camera 0 (a sample grown until one run takes a quarter of
@@ -278,10 +298,20 @@ def cpu_baseline(workload, target_s, gpu_image=None, seed=11):
         total_px += c.width * c.height
         total_t += dtc
         cams_used += 1
-    out = {"value": total_px / total_t / 1e6, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+    threads = oracle.set_threads(0)
+    out = {"value": total_px / total_t / 1e6, "unit": UNIT, "cores": threads, "kind": "oracle",
            "sample": f"{total_px} pixels: {npix0} random pixels of camera 0 ({cam0.width}x{cam0.height})"
                      + (f" and all pixels of cameras 1..{cams_used - 1}" if cams_used > 1 else "")
-                     + ", forward + adjoint, binary64, OpenMP over pixels", "seconds": round(total_t, 2)}
+                     + ", forward + adjoint, binary64, OpenMP over pixels", "seconds": round(total_t, 2),
+           "cpu_model": cpu_model()}
+    # one core, on a slice of the sample sized for a quarter of the budget
+    oracle.set_threads(1)
+    try:
+        n1 = max(64, min(npix0, int(npix0 * (target_s / 4) / max(dt * threads, 1e-9))))
+        dt1, _, _ = run(0, q0[:n1])
+        out["single_core"] = {"value": n1 / dt1 / 1e6, "unit": UNIT, "pixels": n1, "seconds": round(dt1, 2)}
+    finally:
+        oracle.set_threads(0)
     if gpu_image is not None:
         got = gpu_image[:3 * n0].reshape(3, n0)[:, q0].T
         clean = info[:, 2] == 0
@@ -327,8 +357,11 @@ def reference_arm(args, workload, metric=METRIC):
     line = {"impl": "reference", "metric": metric, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": config_dict(args, workload),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "data": "synthetic",
+            "config": dict(config_dict(args, workload),
+                           form="the FP64 oracle on the host cores, a sample of camera 0's pixels per step"),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.set_threads(0), "kind": "oracle",
+                             "cpu_model": cpu_model(),
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)

@@ -103,6 +103,14 @@ def _cams(cameras):
     return arr
 
 
+def set_threads(n: int) -> int:
+    """Threads of the oracle's loops over pixels (n <= 0: all); returns the
+    count in effect.  For timing the oracle on one core or all cores."""
+    L = lib()
+    L.orc_set_threads.restype = C.c_int
+    return int(L.orc_set_threads(int(n)))
+
+
 def render(scene, cameras, bg=(0.0, 0.0, 0.0), dL_dimage=None, dmin=None, info=False, aa=0.0, exact=False):
     """Images packed [cam][3][H][W] (float64).  With dL_dimage, also returns
     the gradients of L = <dL_dimage, image> w.r.t. centre, verts, opacity, sh.

@@ -41,6 +41,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORC_MAX_V 6
 #define ORC_MAX_F 8
@@ -133,6 +136,18 @@ static void sh_basis(int degree, const double d[3], double Y[16], double dY[16][
     Y[15] = -c3a * x * (x * x - 3 * y * y);
                                SETD(15, -c3a * (3 * x * x - 3 * y * y), -c3a * (-6 * x * y), 0.0);
 #undef SETD
+}
+
+/* Threads of the OpenMP loops over pixels (n <= 0: all processors); returns
+ * the count in effect, 1 when built without OpenMP.  Timing only. */
+int orc_set_threads(int n) {
+#ifdef _OPENMP
+    omp_set_num_threads(n > 0 ? n : omp_get_num_procs());
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
 }
 
 int orc_sh_basis(int degree, const double dir[3], double* Y, double* dY) {
