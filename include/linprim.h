@@ -104,9 +104,12 @@ typedef struct {
  *                 primitive; 1: in two passes, geometry then colour, each
  *                 holding fewer registers (ignored while densification
  *                 statistics are gathered, which need one pass).
+ *   sparse_lanes  0..32: a backward warp in which at most this many lanes
+ *                 contribute to a record adds their terms with one atomic
+ *                 per lane and value instead of reducing over the warp.
  * Every setting renders bit-identical images and tile lists.  chain_split
- * changes the order in which a primitive's centre-gradient terms are summed,
- * so dL/dcentre can differ in the last bits between its two settings.      */
+ * and sparse_lanes change the order in which gradient terms are summed, so
+ * gradients can differ in the last bits between settings.                  */
 typedef struct {
     int tile;
     int batch;
@@ -114,6 +117,7 @@ typedef struct {
     int sort_mode;
     int pixels_per_thread;
     int chain_split;
+    int sparse_lanes;
 } lp_tuning;
 
 /* Sizes of the last forward call (filled by lp_get_stats).                 */
@@ -150,7 +154,8 @@ lp_status lp_create(lp_ctx** out, int device);
 void lp_destroy(lp_ctx* ctx);
 
 /* Set / read the tuning parameters (defaults: tile 16, batch 64,
- * blocks_per_sm 0, sort_mode 0, pixels_per_thread 4, chain_split 0).        */
+ * blocks_per_sm 0, sort_mode 0, pixels_per_thread 4, chain_split 0,
+ * sparse_lanes 8).                                                          */
 lp_status lp_set_tuning(lp_ctx* ctx, const lp_tuning* t);
 lp_status lp_get_tuning(lp_ctx* ctx, lp_tuning* t);
 

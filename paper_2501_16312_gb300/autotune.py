@@ -98,8 +98,18 @@ def tune(rast, prims, cameras, bg=(0.0, 0.0, 0.0), dL=None, reps: int = 3,
         chain_times[split] = t["chain"]
         results.append({"chain_split": split, **t})
     best_chain = min(chain_times, key=chain_times.get)
+    rast.set_tuning(chain_split=best_chain)
+    # when a backward warp reduces over its lanes rather than letting each
+    # contributing lane add its own terms, judged on the backward blend
+    sparse_times = {}
+    for sl in (8, 16):
+        rast.set_tuning(sparse_lanes=sl)
+        t = _time(rast, prims, cameras, bg, dL, grads, images, reps)
+        sparse_times[sl] = t["blend_bwd"]
+        results.append({"sparse_lanes": sl, **t})
+    best_sparse = min(sparse_times, key=sparse_times.get)
     choice = dict(base, sort_mode=best_sort, pixels_per_thread=pix, batch=batch, blocks_per_sm=bps,
-                  chain_split=best_chain)
+                  chain_split=best_chain, sparse_lanes=best_sparse)
     rast.set_tuning(**choice)
     rast.set_timing(was_timing)
     entry = {"tuning": choice, "sort_ms": sort_times[best_sort],

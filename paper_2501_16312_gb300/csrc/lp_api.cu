@@ -33,7 +33,7 @@ template <typename T> struct DevBuf {
 struct lp_ctx {
     int device = 0;
     int sms = 0;
-    lp_tuning tune{16, 64, 0, 0, 4, 0};
+    lp_tuning tune{16, 64, 0, 0, 4, 0, 8};
     float aa_kernel = 0.f;      // 2D filter size in pixels (0 = off)
     bool exact = false;         // spans along the true perspective ray
     bool fwd_exact = false;     // mode of the last forward
@@ -309,6 +309,8 @@ lp_status lp_set_tuning(lp_ctx* ctx, const lp_tuning* t) {
         return fail(ctx, LP_ERR_INVALID, "sort_mode %d not in {0, 1}", t->sort_mode);
     if (t->chain_split != 0 && t->chain_split != 1)
         return fail(ctx, LP_ERR_INVALID, "chain_split %d not in {0, 1}", t->chain_split);
+    if (t->sparse_lanes < 0 || t->sparse_lanes > 32)
+        return fail(ctx, LP_ERR_INVALID, "sparse_lanes %d outside 0..32", t->sparse_lanes);
     ctx->tune = *t;
     return LP_OK;
 }
@@ -614,6 +616,7 @@ lp_status lp_render_backward(lp_ctx* ctx, const float* dL_dimages, float* dcentr
     a.acc = ctx->acc.p;
     a.contrib = ctx->contrib.p;
     a.contrib_stride = ctx->contrib_stride;
+    a.sparse_lanes = ctx->tune.sparse_lanes;
     a.tile_counter = ctx->d_tile_counter + 1;
     LP_CUDA(cudaMemsetAsync(ctx->d_tile_counter + 1, 0, sizeof(int), st));
     if (a.grid > 0) {

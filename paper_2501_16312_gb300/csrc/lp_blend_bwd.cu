@@ -25,10 +25,6 @@ namespace lp {
 
 namespace {
 
-// Warps with at most this many contributing lanes (8: measured best on both
-// the 500k-octahedron and the 1M-tetrahedron workloads) skip the shuffle
-// reductions and let each contributing lane issue its own atomic adds.
-constexpr int kSparseLanes = 8;
 
 // 768 resident threads per SM (at most 80 registers): measured faster than
 // the 96-register schedule the compiler picks on its own.
@@ -37,7 +33,8 @@ __global__ void __launch_bounds__(kTilePixels / PIX, 3 * PIX) k_blend_bwd(
     const float* __restrict__ rec, const uint32_t* __restrict__ vals, const uint2* __restrict__ ranges,
     CamsParam cams, float bg0, float bg1, float bg2, const float* __restrict__ dimage,
     const uint32_t* __restrict__ last_in, const float* __restrict__ tl_in, float* __restrict__ acc,
-    int* __restrict__ tile_counter, const uint32_t* __restrict__ contrib, uint32_t cstride) {
+    int* __restrict__ tile_counter, const uint32_t* __restrict__ contrib, uint32_t cstride,
+    int sparse_lanes) {
     constexpr int F = Kind<V>::F;
     constexpr int ACC = Acc<V>::kFloats;
     constexpr int NT = kTilePixels / PIX;
@@ -152,7 +149,10 @@ __global__ void __launch_bounds__(kTilePixels / PIX, 3 * PIX) k_blend_bwd(
                 float* A = acc + (size_t)p.rec * ACC;
                 // plane gradients use offsets (px - X0, py - Y0) from the anchor
                 const float lyc = (float)ly + p.dy0;
-                if (__popc(bal) <= kSparseLanes) {
+                // warps with at most sparse_lanes contributing lanes (a tuning
+                // value, 8 by default) skip the shuffle reductions and let each
+                // contributing lane issue its own atomic adds
+                if (__popc(bal) <= sparse_lanes) {
                     // few contributing lanes: each adds its own terms
                     if (anyc) {
                         atomicAdd(A + 3 * F + 0, gr0);
@@ -218,7 +218,7 @@ template <int V, int BATCH, int PIX>
 cudaError_t bwd_t(const BlendArgs& a, cudaStream_t st) {
     k_blend_bwd<V, BATCH, PIX><<<a.grid, kTilePixels / PIX, 0, st>>>(
         a.rec, a.vals, a.ranges, *a.cams, a.bg[0], a.bg[1], a.bg[2], a.dimage, a.last, a.tl, a.acc,
-        a.tile_counter, a.contrib, a.contrib_stride);
+        a.tile_counter, a.contrib, a.contrib_stride, a.sparse_lanes);
     return cudaGetLastError();
 }
 

@@ -71,6 +71,7 @@ struct BlendArgs {
     bool count;
     float* depth;          // depth pass output (forward kernel in depth mode when non-null)
     uint32_t contrib_stride = 0;   // words per warp of the contributor mask
+    int sparse_lanes = 8;          // backward: per-lane atomics up to this many contributing lanes
     uint32_t* contrib;     // per warp w of a tile (its bits at contrib + w * contrib_stride), one
                            // bit per tile-list entry: some pixel of that warp blended the entry
                            // (written by the forward when non-null, read by the backward)

@@ -384,21 +384,23 @@ def test_cuda_graph_capture_replays(rast):
 
 
 def test_every_tuning_renders_identical_images(rast):
-    """Sort mode, pixels per thread, batch and grid size change the schedule,
-    never the arithmetic of a pixel: images are bitwise identical and
-    gradients agree to float rounding (atomics reorder the sums)."""
+    """Sort mode, pixels per thread, batch, grid size, chain form and the
+    sparse-atomics threshold change the schedule, never the arithmetic of a
+    pixel: images are bitwise identical and gradients agree to float rounding
+    (atomics and the chain form reorder the sums)."""
     import itertools
     w = multiview_small()
     dL = scenes.image_gradient(w, seed=3)
     base = rast.tuning()
     ref_img, ref_g = gpu_forward_backward(rast, w.scene, w.cameras, (0.1, 0.1, 0.1), dL)
     try:
-        for sm, pix, batch, bps, cs in itertools.product([0, 1], [1, 2, 4], [32, 128], [0, 1], [0, 1]):
-            rast.set_tuning(sort_mode=sm, pixels_per_thread=pix, batch=batch, blocks_per_sm=bps, chain_split=cs)
+        for sm, pix, batch, bps, cs, sl in itertools.product([0, 1], [1, 2, 4], [32, 128], [0, 1], [0, 1], [0, 32]):
+            rast.set_tuning(sort_mode=sm, pixels_per_thread=pix, batch=batch, blocks_per_sm=bps, chain_split=cs,
+                            sparse_lanes=sl)
             img, g = gpu_forward_backward(rast, w.scene, w.cameras, (0.1, 0.1, 0.1), dL)
             np.testing.assert_array_equal(img, ref_img)
             for k in g:
-                assert rel_l2(g[k], ref_g[k]) <= 1e-5, (sm, pix, batch, bps, cs, k)
+                assert rel_l2(g[k], ref_g[k]) <= 1e-5, (sm, pix, batch, bps, cs, sl, k)
     finally:
         rast.set_tuning(**base)
 
