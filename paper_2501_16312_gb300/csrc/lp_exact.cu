@@ -676,14 +676,22 @@ __global__ void __launch_bounds__(128) k_chain_x(PrimsDev P, CamsParam cams, con
 #pragma unroll
     for (int q = 0; q < K * 3; ++q) gsh[q] = 0.f;
     float vg_sum = 0.f;     // view-space position-gradient norms of the visible views
-    uint32_t vg_count = 0;
 
-    for (int cv = 0; cv < cams.n; ++cv) {
+    // the cameras that see the primitive, from tile counts read up front
+    uint32_t vis = 0;
+#pragma unroll 8
+    for (int cv = 0; cv < cams.n; ++cv) vis |= (counts[(size_t)cv * P.n + i] != 0u ? 1u : 0u) << cv;
+    const uint32_t vg_count = __popc(vis);
+
+    while (vis) {
+        const int cv = __ffs(vis) - 1;
+        vis &= vis - 1;
         const size_t r = (size_t)cv * P.n + i;
-        if (counts[r] == 0) continue;
-        ++vg_count;
         const float* A = acc + r * AccX<V>::kFloats;
-        bool any = false;
+        // face order read with the row (top four bits always zero; the test
+        // keeps the load ahead of the branch)
+        const uint32_t meta = __float_as_uint(rec[r * RecX<V>::kFloats + 3]);
+        bool any = (meta >> 28) != 0u;
 #pragma unroll
         for (int q = 0; q < AccX<V>::kFloats; ++q) any |= A[q] != 0.f;
         if (!any) continue;
@@ -702,7 +710,6 @@ __global__ void __launch_bounds__(128) k_chain_x(PrimsDev P, CamsParam cams, con
         // derivatives with the centre held fixed are taken, which are the
         // vertices' total derivatives; the centre gets the colour's gradient.
         const float cx = g.tc[0], cy = g.tc[1], icz = 1.f / g.tc[2];
-        const uint32_t meta = __float_as_uint(rec[r * RecX<V>::kFloats + 3]);
 #pragma unroll
         for (int s = 0; s < F; ++s) {
             const float Gp = A[4 * s], Gq = A[4 * s + 1], GL0 = A[4 * s + 2], GD0 = A[4 * s + 3];

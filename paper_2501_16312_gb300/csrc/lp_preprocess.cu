@@ -249,15 +249,26 @@ __global__ void __launch_bounds__(128) k_chain(PrimsDev P, CamsParam cams,
     }
     float gsigma = 0.f;
     float vg_sum = 0.f;     // view-space position-gradient norms of the visible views
-    uint32_t vg_count = 0;
 
-    for (int cv = 0; cv < cams.n; ++cv) {
+    // The cameras that see the primitive: all tile counts are read up front
+    // (independent loads, in flight together), so a visible camera then costs
+    // one dependent memory round trip, for its accumulator row.
+    uint32_t vis = 0;
+#pragma unroll 8
+    for (int cv = 0; cv < cams.n; ++cv) vis |= (counts[(size_t)cv * P.n + i] != 0u ? 1u : 0u) << cv;
+    const uint32_t vg_count = __popc(vis);
+
+    while (vis) {
+        const int cv = __ffs(vis) - 1;
+        vis &= vis - 1;
         const size_t r = (size_t)cv * P.n + i;
-        if (counts[r] == 0) continue;
-        ++vg_count;
         const CamDev& cm = cams.cam[cv];
         const float* A = acc + r * Acc<V>::kFloats;
-        bool any = false;
+        // The record's face order is read together with the accumulator row.
+        // Its top four bits are always zero; testing them keeps the load ahead
+        // of the branch on the row.
+        const uint32_t meta = PART != 1 ? __float_as_uint(rec[r * Rec<V>::kFloats + 3]) : 0u;
+        bool any = (meta >> 28) != 0u;
         if constexpr (PART == 1) {
 #pragma unroll
             for (int q = 0; q < 3; ++q) any |= A[3 * F + q] != 0.f;
@@ -269,7 +280,6 @@ __global__ void __launch_bounds__(128) k_chain(PrimsDev P, CamsParam cams,
         float ga_rgb[3], ga_sig;
         ga_rgb[0] = A[3 * F]; ga_rgb[1] = A[3 * F + 1]; ga_rgb[2] = A[3 * F + 2];
         ga_sig = A[3 * F + 3];
-        const uint32_t meta = __float_as_uint(rec[r * Rec<V>::kFloats + 3]);
 
         Geom g;
         float gtc[3] = {0.f, 0.f, 0.f};
@@ -287,12 +297,12 @@ __global__ void __launch_bounds__(128) k_chain(PrimsDev P, CamsParam cams,
 #pragma unroll
         for (int k = 0; k < V; ++k) gq[k][0] = gq[k][1] = gq[k][2] = 0.f;
         float gxc = 0.f, gyc = 0.f;
+        uint32_t slot_of = 0;   // inverse of the record's permutation, 3 bits per face
+#pragma unroll
+        for (int t = 0; t < F; ++t) slot_of |= (uint32_t)t << (3 * meta_face(meta, t));
 #pragma unroll
         for (int f = 0; f < F; ++f) {
-            int s = 0;
-#pragma unroll
-            for (int t = 0; t < F; ++t)
-                if (meta_face(meta, t) == f) s = t;
+            const int s = (int)((slot_of >> (3 * f)) & 7u);
             // accumulators hold sums over g (px - X0, py - Y0, 1); the pixel's
             // offset from the projected centre is (px - X0 - fxo, py - Y0 - fyo)
             const float Ge = A[3 * s + 2];
