@@ -197,15 +197,15 @@ __global__ void __launch_bounds__(128) k_preprocess(PrimsDev P, CamsParam cams, 
 // both in one pass (always used when the view-space statistics are
 // gathered, which need both parts per view).  The split form lowers the
 // registers a thread holds (the SH coefficients and their gradients live
-// only in PART 1), which pays where many cameras make the loop long.
+// only in PART 1), which pays where many cameras make the loop long.  The
+// split passes are held to four resident blocks per SM (128 registers; a few
+// spill to L1): the loop waits on memory once per camera, and the extra warps
+// hide more of it than the spills cost.
 template <int V, int DEG, int PART>
-__global__ void __launch_bounds__(128) k_chain(PrimsDev P, CamsParam cams,
-                                               const float* __restrict__ rec,
-                                               const uint32_t* __restrict__ counts,
-                                               const float* __restrict__ acc,
-                                               float* __restrict__ dcentre, float* __restrict__ dverts,
-                                               float* __restrict__ dopacity, float* __restrict__ dsh,
-                                               int accumulate) {
+__global__ void __launch_bounds__(128, PART == 2 ? 1 : 4)
+k_chain(PrimsDev P, CamsParam cams, const float* __restrict__ rec, const uint32_t* __restrict__ counts,
+        const float* __restrict__ acc, float* __restrict__ dcentre, float* __restrict__ dverts,
+        float* __restrict__ dopacity, float* __restrict__ dsh, int accumulate) {
     constexpr int F = Kind<V>::F;
     constexpr int K = (DEG + 1) * (DEG + 1);
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
