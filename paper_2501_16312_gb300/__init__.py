@@ -87,6 +87,7 @@ class Rasterizer:
         self.ctx = h
         self.generation = 0
         self._fwd = None
+        self._timing = False
         if tuning:
             self.set_tuning(**tuning)
 
@@ -237,6 +238,11 @@ class Rasterizer:
 
     def set_timing(self, enabled=True):
         _native.check(self.ctx, self.lib.lp_set_timing(self.ctx, int(bool(enabled))), "lp_set_timing")
+        self._timing = bool(enabled)
+
+    def timing(self) -> bool:
+        """Whether per-stage CUDA events are recorded (`set_timing`)."""
+        return self._timing
 
     def stage_times(self) -> dict:
         ms = (C.c_float * len(_native.STAGES))()

@@ -1,14 +1,17 @@
 """Autotuner for the rasterizer's launch parameters.
 
 The tuning knobs (sort mode, pixels per blend thread, records per shared-memory
-batch, resident blend blocks per SM, one- or two-pass backward chain) change
-only the schedule: every setting renders bit-identical images (the chain's
-split only reorders the sum of a primitive's centre-gradient terms).  The
-tuner times forward + backward of the caller's own workload with the
-library's per-stage CUDA events, picks the sort mode by the sort stages, the
-blend parameters by the two blend stages and the chain form by the chain
-stage, and caches the choice as JSON keyed by GPU name, primitive kind and
-size buckets of the workload.
+batch, resident blend blocks per SM, one- or two-pass backward chain, and the
+number of contributing lanes up to which a backward warp lets each lane add
+its own terms) change only the schedule: every setting renders bit-identical
+images (the chain's split and the backward's reduction form only reorder
+floating-point sums of gradients).  The tuner times forward + backward of the
+caller's own workload with the library's per-stage CUDA events.  It settles
+the knobs one group at a time, each judged on the stages it affects: the sort
+mode on the sort stages, the blend schedule on the two blend stages, the
+chain form on the chain stage and the lane threshold on the backward blend.
+The choice is cached as JSON keyed by GPU name, primitive kind and size
+buckets of the workload.
 """
 from __future__ import annotations
 
@@ -47,84 +50,98 @@ def _time(rast, prims, cameras, bg, dL, grads, images, reps: int):
     return acc
 
 
+# The search: each group of knobs, its candidates, and the stages it is
+# judged on.  Later groups are timed at the earlier groups' choices.
+GROUPS = (
+    (("sort_mode",), ((0,), (1,)), SORT_STAGES),
+    (("pixels_per_thread", "batch", "blocks_per_sm"),
+     tuple(itertools.product((2, 4), (32, 64), (0,))), BLEND_STAGES),
+    (("chain_split",), ((0,), (1,)), ("chain",)),
+    (("sparse_lanes",), ((8,), (16,)), ("blend_bwd",)),
+)
+
+
+def search(apply, measure, base: dict) -> dict:
+    """Coordinate search over GROUPS.  apply(settings) sets knob values (a
+    dict); measure() returns the stage times in ms of one timed forward +
+    backward at the current settings.  Returns the choice (base updated with
+    the winners, which are left applied), each group's best summed time and
+    every trial."""
+    choice = dict(base)
+    best_ms, results = {}, []
+    for names, candidates, stages in GROUPS:
+        times = {}
+        for values in candidates:
+            setting = dict(zip(names, values))
+            apply(setting)
+            t = measure()
+            times[values] = sum(t[s] for s in stages)
+            results.append({**setting, **t})
+        win = min(times, key=times.get)      # the first candidate wins ties
+        choice.update(zip(names, win))
+        apply(dict(zip(names, win)))         # later groups are timed at this choice
+        best_ms["+".join(names)] = times[win]
+    return {"tuning": choice, "best_ms": best_ms, "trials": results}
+
+
+def load_cache(cache: Optional[str], key: str) -> Optional[dict]:
+    """The cached entry for key, or None (missing or unreadable file)."""
+    if not cache or not os.path.exists(cache):
+        return None
+    try:
+        with open(cache) as f:
+            return json.load(f).get(key)
+    except (OSError, ValueError, AttributeError):
+        return None
+
+
+def store_cache(cache: Optional[str], key: str, entry: dict) -> None:
+    """Adds entry under key, replacing the file atomically; errors are ignored
+    (the cache is an optimisation)."""
+    if not cache:
+        return
+    try:
+        os.makedirs(os.path.dirname(cache) or ".", exist_ok=True)
+        known = {}
+        if os.path.exists(cache):
+            try:
+                with open(cache) as f:
+                    known = json.load(f)
+            except ValueError:
+                known = {}
+        known[key] = entry
+        with open(cache + ".tmp", "w") as f:
+            json.dump(known, f, indent=1)
+        os.replace(cache + ".tmp", cache)
+    except OSError:
+        pass
+
+
 def tune(rast, prims, cameras, bg=(0.0, 0.0, 0.0), dL=None, reps: int = 3,
          cache: Optional[str] = DEFAULT_CACHE, force: bool = False) -> dict:
-    """Pick and apply the fastest tuning for this workload; returns it."""
+    """Pick and apply the fastest tuning for this workload; returns the entry
+    (its "tuning" is the choice, now set on rast)."""
     import torch
     gpu = torch.cuda.get_device_name(rast.device)
     key = cache_key(gpu, prims.kind, prims.n, cameras)
-    if cache and not force and os.path.exists(cache):
-        try:
-            with open(cache) as f:
-                known = json.load(f)
-            if key in known:
-                rast.set_tuning(**known[key]["tuning"])
-                return known[key]
-        except (OSError, ValueError):
-            pass
+    if not force:
+        known = load_cache(cache, key)
+        if known is not None:
+            rast.set_tuning(**known["tuning"])
+            return known
     P = sum(c.width * c.height for c in cameras)
     images = torch.empty(3 * P, device=rast.device)
     if dL is None:
         dL = torch.ones(3 * P, device=rast.device)
     grads = dict(centre=torch.empty_like(prims.centre), verts=torch.empty_like(prims.verts),
                  opacity=torch.empty_like(prims.opacity), sh=torch.empty_like(prims.sh))
-    was_timing = True
+    was_timing = rast.timing()
     rast.set_timing(True)
-    base = rast.tuning()
-    results = []
-    # sort mode, judged on the sort stages at the current blend setting
-    sort_times = {}
-    for sm in (0, 1):
-        rast.set_tuning(sort_mode=sm)
-        t = _time(rast, prims, cameras, bg, dL, grads, images, reps)
-        sort_times[sm] = sum(t[s] for s in SORT_STAGES)
-        results.append({"sort_mode": sm, **t})
-    best_sort = min(sort_times, key=sort_times.get)
-    rast.set_tuning(sort_mode=best_sort)
-    # blend schedule
-    blend_times = {}
-    for pix, batch, bps in itertools.product((2, 4), (32, 64), (0,)):
-        rast.set_tuning(pixels_per_thread=pix, batch=batch, blocks_per_sm=bps)
-        t = _time(rast, prims, cameras, bg, dL, grads, images, reps)
-        blend_times[(pix, batch, bps)] = sum(t[s] for s in BLEND_STAGES)
-        results.append({"pixels_per_thread": pix, "batch": batch, "blocks_per_sm": bps, **t})
-    pix, batch, bps = min(blend_times, key=blend_times.get)
-    rast.set_tuning(pixels_per_thread=pix, batch=batch, blocks_per_sm=bps)
-    # the backward chain in one or two passes, judged on its own stage
-    chain_times = {}
-    for split in (0, 1):
-        rast.set_tuning(chain_split=split)
-        t = _time(rast, prims, cameras, bg, dL, grads, images, reps)
-        chain_times[split] = t["chain"]
-        results.append({"chain_split": split, **t})
-    best_chain = min(chain_times, key=chain_times.get)
-    rast.set_tuning(chain_split=best_chain)
-    # when a backward warp reduces over its lanes rather than letting each
-    # contributing lane add its own terms, judged on the backward blend
-    sparse_times = {}
-    for sl in (8, 16):
-        rast.set_tuning(sparse_lanes=sl)
-        t = _time(rast, prims, cameras, bg, dL, grads, images, reps)
-        sparse_times[sl] = t["blend_bwd"]
-        results.append({"sparse_lanes": sl, **t})
-    best_sparse = min(sparse_times, key=sparse_times.get)
-    choice = dict(base, sort_mode=best_sort, pixels_per_thread=pix, batch=batch, blocks_per_sm=bps,
-                  chain_split=best_chain, sparse_lanes=best_sparse)
-    rast.set_tuning(**choice)
-    rast.set_timing(was_timing)
-    entry = {"tuning": choice, "sort_ms": sort_times[best_sort],
-             "blend_ms": blend_times[(pix, batch, bps)], "trials": results}
-    if cache:
-        try:
-            os.makedirs(os.path.dirname(cache), exist_ok=True)
-            known = {}
-            if os.path.exists(cache):
-                with open(cache) as f:
-                    known = json.load(f)
-            known[key] = entry
-            with open(cache + ".tmp", "w") as f:
-                json.dump(known, f, indent=1)
-            os.replace(cache + ".tmp", cache)
-        except (OSError, ValueError):
-            pass
+    try:
+        entry = search(lambda setting: rast.set_tuning(**setting),
+                       lambda: _time(rast, prims, cameras, bg, dL, grads, images, reps), rast.tuning())
+        rast.set_tuning(**entry["tuning"])
+    finally:
+        rast.set_timing(was_timing)
+    store_cache(cache, key, entry)
     return entry
