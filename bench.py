@@ -260,7 +260,7 @@ def cpu_model():
 
 def cpu_baseline(workload, target_s, gpu_image=None, seed=11):
     """Time the FP64 oracle (forward + adjoint) on a bounded sample of pixels:
-    random pixels of camera 0 (a sample grown until one run takes a quarter of
+    random pixels of camera 0 (a sample grown until one run takes a third of
     the budget, or all of the camera), then whole further cameras while the
     budget lasts; returns the rate in Mpixel/s."""
     import numpy as np
@@ -278,13 +278,14 @@ def cpu_baseline(workload, target_s, gpu_image=None, seed=11):
     cam0 = workload.cameras[0]
     n0 = cam0.width * cam0.height
     # random pixels of camera 0, the sample growing 4x while a run stays under
-    # a quarter of the budget (the cost per pixel varies too much between
-    # scenes to extrapolate from one small run); the last run is the sample
+    # a third of the budget (the cost per pixel varies too much between scenes
+    # to extrapolate from one small run); the last run is the sample, between
+    # a third of the budget and four thirds of it
     npix0 = min(n0, 1024)
     while True:
         q0 = rng.choice(n0, npix0, replace=False)
         dt, rgb, info = run(0, q0)
-        if npix0 >= n0 or dt >= target_s / 4:
+        if npix0 >= n0 or dt >= target_s / 3:
             break
         npix0 = min(n0, npix0 * 4)
     total_px, total_t, cams_used = npix0, dt, 1
