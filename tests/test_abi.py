@@ -75,3 +75,49 @@ def test_missing_library_fails_loudly(tmp_path):
             _native.load(str(tmp_path / "nope.so"))
     finally:
         _native._lib = saved
+
+
+STRUCTS = ("lp_camera", "lp_prims", "lp_tuning", "lp_stats", "lp_adam_group", "lp_population_rules",
+           "lp_param_arrays")
+CONSTANTS = ("LP_OK", "LP_ERR_INVALID", "LP_ERR_CAPACITY", "LP_ERR_CUDA", "LP_ERR_TIMEOUT",
+             "LP_ERR_UNSUPPORTED", "LP_ERR_STATE", "LP_TETRAHEDRON", "LP_OCTAHEDRON", "LP_MAX_CAMERAS",
+             "LP_ADAM_MAX_GROUPS", "LP_POP_PRUNE", "LP_POP_KEEP", "LP_POP_CLONE", "LP_POP_SPLIT")
+
+
+def test_struct_layouts_and_constants_match_the_header(tmp_path):
+    """The binding's ctypes structures have the header's size and field
+    offsets, and its constants the header's values: a C program compiled
+    against include/linprim.h prints them (host compiler only)."""
+    import shutil
+    import subprocess
+    from paper_2501_16312_gb300 import _native
+    header = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    assert sorted(re.findall(r"}\s*(lp_[a-z_]+)\s*;", header)) == sorted(STRUCTS + ("lp_status",))
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "linprim.h"', "int main(void) {"]
+    for s in STRUCTS:
+        lines.append(f'  printf("{s} size %zu\\n", sizeof({s}));')
+        for name, _ in getattr(_native, s)._fields_:
+            lines.append(f'  printf("{s} {name} %zu\\n", offsetof({s}, {name}));')
+    for k in CONSTANTS:
+        lines.append(f'  printf("{k} const %lld\\n", (long long)({k}));')
+    lines.append('  printf("stages const %d\\n", (int)LP_NUM_STAGES);')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.check_call([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    got = {}
+    for line in subprocess.check_output([str(exe)], text=True).splitlines():
+        a, b, v = line.split()
+        got[(a, b)] = int(v)
+    for s in STRUCTS:
+        cls = getattr(_native, s)
+        assert got[(s, "size")] == ctypes.sizeof(cls), s
+        for name, _ in cls._fields_:
+            assert got[(s, name)] == getattr(cls, name).offset, (s, name)
+    for k in CONSTANTS:
+        assert got[(k, "const")] == getattr(_native, k), k
+    assert got[("stages", "const")] == len(_native.STAGES)
