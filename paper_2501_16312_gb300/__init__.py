@@ -42,10 +42,12 @@ class Primitives:
         K = sh.shape[1] if sh.dim() == 3 else sh.numel() // max(1, 3 * n)
         if sh_degree is None:
             sh_degree = {1: 0, 4: 1, 9: 2, 16: 3}[K]
-        for name, t, shape in (("centre", centre, (n, 3)), ("verts", verts, (n, kind, 3)),
-                               ("opacity", opacity, (n,)), ("sh", sh, (n, (sh_degree + 1) ** 2, 3))):
+        arrays = (("centre", centre, (n, 3)), ("verts", verts, (n, kind, 3)),
+                  ("opacity", opacity, (n,)), ("sh", sh, (n, (sh_degree + 1) ** 2, 3)))
+        for name, t, shape in arrays:
             if tuple(t.shape) != shape:
                 raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {shape}")
+        for name, t, _ in arrays:
             if t.dtype != torch.float32 or not t.is_cuda:
                 raise ValueError(f"{name} must be a float32 CUDA tensor")
         self.kind, self.n, self.sh_degree = kind, n, sh_degree
