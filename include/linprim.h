@@ -238,7 +238,12 @@ lp_status lp_reserve(lp_ctx* ctx, long long max_records, long long max_entries,
  * The context keeps the sorted tile lists and per-pixel state (8 bytes per
  * pixel) for the next lp_render_backward.  Outside stream capture the call
  * synchronises `stream` once, to read the tile-list length and size its
- * workspace.                                                                */
+ * workspace.
+ * Limits: at most 2^30 pixels and 2^30 tiles over all cameras, each camera at
+ * most 65536 pixels on a side (LP_ERR_INVALID otherwise).  Tile-list offsets
+ * are 32-bit: the list (one entry per primitive, camera and covered tile)
+ * must stay below 2^32 entries, about 51 GB of keys and values.  A longer
+ * list is not detected; it wraps.                                            */
 lp_status lp_render_forward(lp_ctx* ctx, const lp_prims* prims, const lp_camera* cams,
                             int n_cams, const float bg[3], float* images, void* stream);
 
