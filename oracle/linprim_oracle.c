@@ -625,7 +625,18 @@ typedef struct {
     orc_pp* pp;
     int* order;         /* visible primitives in ascending (depth bits, index) */
     int n_order;
+    /* Sec. 3.2 "Global Sorting and Tiling": the primitives whose rectangle
+     * meets each 16x16 tile of the image, in the order above.  A pixel's
+     * candidates are those of its tile; the rectangle test in blend_pixel
+     * rejects the rest of them exactly as it rejects every primitive outside
+     * the tile, so each pixel visits the same primitives in the same order
+     * as a walk over the whole sorted list would. */
+    int tiles_x, tiles_y;
+    long long* tile_start;   /* [tiles + 1] */
+    int* tile_list;
 } orc_view;
+
+#define ORC_BIN 16
 
 static const orc_pp* g_sort_pp;
 static int cmp_depth(const void* a, const void* b) {
@@ -638,6 +649,8 @@ static int cmp_depth(const void* a, const void* b) {
 static int view_build(const orc_prims* P, const orc_camera* cam, orc_view* V) {
     int i;
     V->n = P->n;
+    V->tile_start = NULL;
+    V->tile_list = NULL;
     V->pp = (orc_pp*)calloc((size_t)(P->n > 0 ? P->n : 1), sizeof(orc_pp));
     V->order = (int*)malloc(sizeof(int) * (size_t)(P->n > 0 ? P->n : 1));
     if (!V->pp || !V->order) return -1;
@@ -650,12 +663,50 @@ static int view_build(const orc_prims* P, const orc_camera* cam, orc_view* V) {
      * by centre depth; reading: ties by primitive index. */
     g_sort_pp = V->pp;
     qsort(V->order, (size_t)V->n_order, sizeof(int), cmp_depth);
+    /* per-tile candidate lists: count, prefix, fill in sorted order */
+    {
+        long long nt, t, total = 0;
+        int pass, j, tx, ty;
+        V->tiles_x = (cam->width + ORC_BIN - 1) / ORC_BIN;
+        V->tiles_y = (cam->height + ORC_BIN - 1) / ORC_BIN;
+        nt = (long long)V->tiles_x * V->tiles_y;
+        V->tile_start = (long long*)calloc((size_t)(nt + 1), sizeof(long long));
+        if (!V->tile_start) return -1;
+        for (pass = 0; pass < 2; ++pass) {
+            if (pass == 1) {
+                long long run = 0;
+                for (t = 0; t < nt; ++t) {
+                    long long c = V->tile_start[t];
+                    V->tile_start[t] = run;
+                    run += c;
+                }
+                V->tile_start[nt] = total = run;
+                V->tile_list = (int*)malloc(sizeof(int) * (size_t)(total > 0 ? total : 1));
+                if (!V->tile_list) return -1;
+            }
+            for (j = 0; j < V->n_order; ++j) {
+                const orc_keyfields* kf = &V->pp[V->order[j]].kf;
+                if (kf->px0 > kf->px1 || kf->py0 > kf->py1) continue;
+                for (ty = kf->py0 / ORC_BIN; ty <= kf->py1 / ORC_BIN; ++ty)
+                    for (tx = kf->px0 / ORC_BIN; tx <= kf->px1 / ORC_BIN; ++tx) {
+                        t = (long long)ty * V->tiles_x + tx;
+                        if (pass == 0) ++V->tile_start[t];
+                        else V->tile_list[V->tile_start[t]++] = V->order[j];
+                    }
+            }
+        }
+        /* the fill advanced every start to the next tile's start */
+        for (t = nt; t > 0; --t) V->tile_start[t] = V->tile_start[t - 1];
+        V->tile_start[0] = 0;
+    }
     return 0;
 }
 
 static void view_free(orc_view* V) {
     free(V->pp);
     free(V->order);
+    free(V->tile_start);
+    free(V->tile_list);
 }
 
 /* --------------------------------------------------------- per-pixel blend */
@@ -683,12 +734,17 @@ static int blend_pixel(const orc_prims* P, const orc_view* V, const double bg[3]
                        orc_contrib* list, int cap, orc_pixel* out) {
     double rx = x + 0.5, ry = y + 0.5;   /* reading: sample at the pixel centre */
     double T = 1.0, C[3] = {0.0, 0.0, 0.0};
-    int j, nc = 0, ch;
+    int nc = 0, ch;
     out->borderline = 0;
     out->min_span = INFINITY;
     out->depth = 0.0;
-    for (j = 0; j < V->n_order; ++j) {
-        int i = V->order[j];
+    /* a pixel outside the image lies in no rectangle: no candidates */
+    const int inside = x >= 0 && y >= 0 && x / ORC_BIN < V->tiles_x && y / ORC_BIN < V->tiles_y;
+    const long long t = inside ? (long long)(y / ORC_BIN) * V->tiles_x + x / ORC_BIN : 0;
+    const long long j_end = inside ? V->tile_start[t + 1] : 0;
+    long long jj;
+    for (jj = inside ? V->tile_start[t] : 0; jj < j_end; ++jj) {
+        int i = V->tile_list[jj];
         const orc_pp* pp = &V->pp[i];
         double i1, i2, s, tau, o, Tn;
         int f1 = -1, f2 = -1;
