@@ -267,6 +267,19 @@ lp_status lp_render_backward(lp_ctx* ctx, const float* dL_dimages, float* dcentr
  * device by earlier calls (LP_ERR_CAPACITY, LP_ERR_TIMEOUT), or LP_OK.     */
 lp_status lp_sync_status(lp_ctx* ctx, void* stream);
 
+/* Bounds canaries (a debugging aid; the paper has no counterpart).
+ * lp_set_debug_guard(ctx, 1): every workspace buffer the context allocates
+ * from then on carries a zone of 4096 bytes after its capacity, filled with
+ * the byte 0xA5; each such allocation also synchronises the device.  Buffers
+ * allocated earlier carry no zone (create the context, enable guards, then
+ * call lp_reserve or render).  lp_check_guards synchronises the device and
+ * reads every zone back: *checked receives the number of guarded buffers and
+ * *damaged the number of zone bytes that changed -- 0 unless some kernel
+ * wrote past a buffer's capacity (lp_last_error then names the first such
+ * buffer).  Host pointers; errors: LP_ERR_INVALID for NULL, LP_ERR_CUDA.    */
+lp_status lp_set_debug_guard(lp_ctx* ctx, int enabled);
+lp_status lp_check_guards(lp_ctx* ctx, long long* checked, long long* damaged);
+
 /* Sizes of the last forward (host struct).                                 */
 lp_status lp_get_stats(lp_ctx* ctx, lp_stats* out);
 
@@ -430,20 +443,22 @@ lp_status lp_population_apply(int kind, int sh_coeffs, int n, const unsigned cha
 
 /* Allocation-free forward render of ONE camera.  The paper has no
  * counterpart: this entry point exists for callers that cannot call
- * cudaMalloc -- code running while a CUDA graph is being captured, services
- * whose device memory belongs to a pool or budget they may not bypass,
- * embedded or real-time hosts that forbid allocation after start-up.
- * It runs the same kernels as lp_render_forward (default tuning, 64-bit key
- * sort) and writes the same image, but takes no context and allocates
- * nothing: its scratch is one fixed array of about 10.6 MiB inside the
- * library, held by every GPU that uses it until the process exits.
+ * cudaMalloc -- services whose device memory belongs to a pool or budget they
+ * may not bypass, embedded or real-time hosts that forbid allocation after
+ * start-up.  It runs the same kernels as lp_render_forward (default tuning,
+ * 64-bit key sort) and writes the same image, but takes no context and
+ * allocates nothing: its scratch is one fixed array of about 10.6 MiB inside
+ * the library, held by every GPU that uses it until the process exits.
  *   prims   as for lp_render_forward; n <= 16384.
  *   cam     one camera, width * height <= 262144 and at most 2048 16x16 tiles.
  *   bg      host float[3]; image: device float[3][H][W], overwritten.
+ *   stream  must belong to the current device (LP_ERR_INVALID otherwise).
  * Returns LP_ERR_CAPACITY, before launching anything, when n, the pixel or
  * the tile count exceeds those limits, and after the key scan when the tile
  * list would exceed 262144 entries (the image is then not written).  The
- * call synchronises `stream` once, to read the tile-list length.
+ * call synchronises `stream` twice: after the key scan, to read the
+ * tile-list length, and at the end, to read the status the kernels latch on
+ * the device (returned as LP_ERR_CAPACITY or LP_ERR_TIMEOUT).
  * All calls share the scratch array and it keeps the previous call's
  * contents (each call clears what must start at zero): calls whose GPU work
  * overlaps -- on different streams or host threads -- race and must be

@@ -238,6 +238,21 @@ class Rasterizer:
                       "lp_debug_pixel_state")
         return last[:m], tl[:m]
 
+    def set_debug_guard(self, enabled=True):
+        """Canary zones after every workspace buffer allocated from now on
+        (a debugging aid; see check_guards)."""
+        _native.check(self.ctx, self.lib.lp_set_debug_guard(self.ctx, int(bool(enabled))), "lp_set_debug_guard")
+
+    def check_guards(self) -> dict:
+        """Synchronise and read every canary zone back: the number of guarded
+        buffers and of zone bytes that changed (0 unless a kernel wrote past
+        a buffer's capacity), with the first damaged buffer's name."""
+        checked, damaged = C.c_longlong(0), C.c_longlong(0)
+        _native.check(self.ctx, self.lib.lp_check_guards(self.ctx, C.byref(checked), C.byref(damaged)),
+                      "lp_check_guards")
+        return {"checked": checked.value, "damaged": damaged.value,
+                "first": self.lib.lp_last_error(self.ctx).decode() if damaged.value else ""}
+
     def set_timing(self, enabled=True):
         _native.check(self.ctx, self.lib.lp_set_timing(self.ctx, int(bool(enabled))), "lp_set_timing")
         self._timing = bool(enabled)

@@ -22,7 +22,8 @@ EXPORTS = ("lp_create", "lp_destroy", "lp_set_tuning", "lp_get_tuning", "lp_set_
            "lp_last_error", "lp_status_string", "lp_set_timing", "lp_stage_times",
            "lp_render_forward_noalloc", "lp_params_forward", "lp_params_backward",
            "lp_l1_loss_grad", "lp_adam_step", "lp_render_depth", "lp_set_exact", "lp_get_exact",
-           "lp_set_densify_stats", "lp_population_scratch", "lp_population_decide", "lp_population_apply")
+           "lp_set_densify_stats", "lp_population_scratch", "lp_population_decide", "lp_population_apply",
+           "lp_set_debug_guard", "lp_check_guards")
 LP_ADAM_MAX_GROUPS = 8
 STAGES = ("preprocess", "scan_emit", "sort", "ranges", "blend_fwd", "blend_bwd", "chain")
 
@@ -106,6 +107,8 @@ def load(path: str = LIB_PATH):
     L.lp_debug_counts.argtypes = [vp, vp, ll]
     L.lp_debug_pixel_state.argtypes = [vp, vp, vp, ll]
     L.lp_count_pairs.argtypes = [vp, C.POINTER(ll)]
+    L.lp_set_debug_guard.argtypes = [vp, i]
+    L.lp_check_guards.argtypes = [vp, C.POINTER(ll), C.POINTER(ll)]
     L.lp_render_depth.argtypes = [vp, vp, vp]
     L.lp_set_exact.argtypes = [vp, i]
     L.lp_get_exact.argtypes = [vp, C.POINTER(i)]

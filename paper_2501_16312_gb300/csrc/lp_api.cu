@@ -22,11 +22,17 @@
 
 namespace {
 
-// Grow-only device allocation.
+// Grow-only device allocation.  With the context's guard mode on, each
+// allocation carries a canary zone of kGuardBytes past its capacity, filled
+// with kGuardByte; lp_check_guards reports any byte there that changed.
 template <typename T> struct DevBuf {
     T* p = nullptr;
-    size_t cap = 0;   // elements
+    size_t cap = 0;     // elements
+    size_t guard = 0;   // bytes of canary zone after cap elements (0: none)
 };
+
+constexpr size_t kGuardBytes = 4096;
+constexpr unsigned char kGuardByte = 0xA5;
 
 }  // namespace
 
@@ -74,6 +80,19 @@ struct lp_ctx {
     bool timing = false;
     cudaEvent_t ev[9] = {};
     bool fwd_timed = false, bwd_timed = false;
+
+    bool guard = false;   // canary zones on later allocations (lp_set_debug_guard)
+
+    // every grow-only buffer, with a name (guard checks, release)
+    template <typename F> void each_buf(F&& f) {
+        f(rec, "records"); f(counts, "counts"); f(offsets, "offsets"); f(zbits, "zbits");
+        f(scan_tmp, "scan blocks"); f(hist, "histograms"); f(last, "pixel state"); f(emit_part, "emit partition");
+        f(contrib, "contributor mask"); f(trect, "tile rects"); f(keys0, "keys"); f(keys1, "keys");
+        f(vals0, "values"); f(vals1, "values"); f(ranges, "tile ranges"); f(tl, "pixel state");
+        f(acc, "gradient accumulators"); f(scratch_image, "scratch image"); f(dkeys0, "depth keys");
+        f(dkeys1, "depth keys"); f(dvals0, "depth values"); f(dvals1, "depth values");
+        f(counts_sorted, "sorted counts");
+    }
 };
 
 namespace {
@@ -122,13 +141,21 @@ lp_status ensure(lp_ctx* ctx, DevBuf<T>& b, long long n, bool cap_mode, const ch
         b.cap = 0;
     }
     const size_t grow = want + want / 4;
-    cudaError_t e = cudaMalloc((void**)&b.p, grow * sizeof(T));
+    const size_t guard = ctx->guard ? kGuardBytes : 0;
+    cudaError_t e = cudaMalloc((void**)&b.p, grow * sizeof(T) + guard);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        return fail(ctx, LP_ERR_CUDA, "cudaMalloc(%s, %zu bytes): %s", what, grow * sizeof(T),
+        return fail(ctx, LP_ERR_CUDA, "cudaMalloc(%s, %zu bytes): %s", what, grow * sizeof(T) + guard,
                     cudaGetErrorString(e));
     }
     b.cap = grow;
+    b.guard = guard;
+    if (guard) {
+        // filled and finished before any later launch can touch the buffer
+        e = cudaMemset(reinterpret_cast<unsigned char*>(b.p) + grow * sizeof(T), kGuardByte, guard);
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) return fail(ctx, LP_ERR_CUDA, "guard fill: %s", cudaGetErrorString(e));
+    }
     return LP_OK;
 }
 
@@ -136,6 +163,7 @@ template <typename T> void release(DevBuf<T>& b) {
     if (b.p) cudaFree(b.p);
     b.p = nullptr;
     b.cap = 0;
+    b.guard = 0;
 }
 
 int rec_floats(int V) { return V == 6 ? lp::Rec<6>::kFloats : lp::Rec<4>::kFloats; }
@@ -279,13 +307,7 @@ void lp_destroy(lp_ctx* ctx) {
     if (!ctx) return;
     cudaSetDevice(ctx->device);
     cudaDeviceSynchronize();
-    release(ctx->rec); release(ctx->counts); release(ctx->offsets); release(ctx->zbits);
-    release(ctx->scan_tmp); release(ctx->hist); release(ctx->last); release(ctx->trect); release(ctx->emit_part);
-    release(ctx->contrib);
-    release(ctx->keys0); release(ctx->keys1); release(ctx->vals0); release(ctx->vals1);
-    release(ctx->ranges); release(ctx->tl); release(ctx->acc); release(ctx->scratch_image);
-    release(ctx->dkeys0); release(ctx->dkeys1); release(ctx->dvals0); release(ctx->dvals1);
-    release(ctx->counts_sorted);
+    ctx->each_buf([](auto& b, const char*) { release(b); });
     if (ctx->d_status) cudaFree(ctx->d_status);
     if (ctx->d_E) cudaFree(ctx->d_E);
     if (ctx->d_tile_counter) cudaFree(ctx->d_tile_counter);
@@ -702,6 +724,40 @@ lp_status lp_stage_times(lp_ctx* ctx, float* ms) {
         LP_CUDA(cudaEventElapsedTime(&ms[LP_STAGE_CHAIN], ctx->ev[7], ctx->ev[8]));
     }
     return LP_OK;
+}
+
+lp_status lp_set_debug_guard(lp_ctx* ctx, int enabled) {
+    if (!ctx) return LP_ERR_INVALID;
+    ctx->guard = enabled != 0;
+    return LP_OK;
+}
+
+lp_status lp_check_guards(lp_ctx* ctx, long long* checked, long long* damaged) {
+    if (!ctx || !checked || !damaged) return LP_ERR_INVALID;
+    LP_CUDA(cudaSetDevice(ctx->device));
+    LP_CUDA(cudaDeviceSynchronize());
+    *checked = 0;
+    *damaged = 0;
+    unsigned char host[kGuardBytes];
+    lp_status st = LP_OK;
+    const char* first = nullptr;
+    ctx->each_buf([&](auto& b, const char* name) {
+        if (st != LP_OK || !b.p || !b.guard) return;
+        const unsigned char* zone = reinterpret_cast<const unsigned char*>(b.p + b.cap);
+        if (cudaMemcpy(host, zone, b.guard, cudaMemcpyDeviceToHost) != cudaSuccess) {
+            cudaGetLastError();
+            st = fail(ctx, LP_ERR_CUDA, "guard read of %s failed", name);
+            return;
+        }
+        ++*checked;
+        for (size_t q = 0; q < b.guard; ++q)
+            if (host[q] != kGuardByte) {
+                ++*damaged;
+                if (!first) first = name;
+            }
+    });
+    if (st == LP_OK && first) fail(ctx, LP_OK, "guard zone of %s written", first);
+    return st;
 }
 
 lp_status lp_debug_keys(lp_ctx* ctx, unsigned long long* keys, unsigned int* vals, long long cap,

@@ -7,8 +7,9 @@ Tolerances (from the rasterizer's specification):
     flags as borderline (the transmittance at some step is within 1e-3
     relative of the 1e-3 stop threshold, so binary32 and binary64 may stop at
     different primitives); those may number at most max(2, 1e-4 * pixels);
-  * gradients: per array, ||g - g*|| / ||g*|| <= 1e-3, for a dL/dimage that
-    is zero at the borderline pixels (both sides get the same dL).  The
+  * gradients: per array, ||g - g*|| / ||g*|| <= 1e-3, and per element
+    |g - g*| <= 1e-3 max(|g*|, 1e-2 rms(g*)), for a dL/dimage that is zero at
+    the borderline pixels (both sides get the same dL).  The
     oracle also flags pixels whose ray passes within rounding of some
     primitive's silhouette: the colour is continuous there but its
     derivative with respect to the vertices jumps, so binary32 and binary64
@@ -63,13 +64,40 @@ def rel_l2(a, b):
     return float(np.linalg.norm(a - b) / nb) if nb > 0 else float(np.linalg.norm(a))
 
 
-def assert_grads_match(gpu, ref, tol=GRAD_REL_L2):
-    out = {}
+GRAD_ELEM = 1e-3
+GRAD_ELEM_FLOOR = 1e-2
+
+
+def elem_ratio(a, b):
+    """Worst |a - b| / max(|b|, 1e-2 rms(b)) over the elements of one array,
+    and the index of that element (the per-element gradient bound is ratio
+    <= 1e-3).  An all-zero reference admits only exact zeros."""
+    a = np.asarray(a, np.float64).reshape(-1)
+    b = np.asarray(b, np.float64).reshape(-1)
+    if a.size == 0:
+        return 0.0, -1
+    rms = float(np.sqrt(np.mean(b * b)))
+    scale = np.maximum(np.abs(b), GRAD_ELEM_FLOOR * rms)
+    d = np.abs(a - b)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        r = np.where(scale > 0, d / np.where(scale > 0, scale, 1.0), np.where(d > 0, np.inf, 0.0))
+    i = int(np.argmax(r))
+    return float(r[i]), i
+
+
+def assert_grads_match(gpu, ref, tol=GRAD_REL_L2, elem_tol=GRAD_ELEM):
+    """Relative L2 per array and the per-element bound; returns the relative
+    L2 errors (the worst per-element ratios are in the assertion message)."""
+    out, worst = {}, {}
     for k in ("centre", "verts", "opacity", "sh"):
-        r = rel_l2(gpu[k], ref[k])
-        out[k] = r
+        out[k] = rel_l2(gpu[k], ref[k])
+        r, i = elem_ratio(gpu[k], ref[k])
+        worst[k] = (r, i, float(np.asarray(gpu[k]).reshape(-1)[i]) if i >= 0 else 0.0,
+                    float(np.asarray(ref[k]).reshape(-1)[i]) if i >= 0 else 0.0)
     bad = {k: v for k, v in out.items() if not v <= tol}
     assert not bad, f"gradient relative L2 errors {out}"
+    bad_e = {k: v for k, v in worst.items() if not v[0] <= elem_tol}
+    assert not bad_e, f"per-element gradient bound exceeded (ratio, index, gpu, oracle): {bad_e}"
     return out
 
 
