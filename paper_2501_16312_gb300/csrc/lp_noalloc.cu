@@ -1,12 +1,14 @@
 // Allocation-free forward render of one camera.
 //
-// Some callers cannot call cudaMalloc: code that runs while a CUDA graph is
-// being captured, memory-budgeted services whose device memory is owned by a
-// pool or an allocator they may not bypass, and embedded or real-time hosts
-// that forbid allocation after start-up.  lp_render_forward_noalloc renders
-// one camera with the same kernels as lp_render_forward, but every scratch
-// buffer it needs lives in one file-scope __device__ array of fixed size, so
-// the call itself never allocates device (or pinned host) memory.
+// Some callers cannot call cudaMalloc: memory-budgeted services whose device
+// memory is owned by a pool or an allocator they may not bypass, and embedded
+// or real-time hosts that forbid allocation after start-up.
+// lp_render_forward_noalloc renders one camera with the same kernels as
+// lp_render_forward, but every scratch buffer it needs lives in one
+// file-scope __device__ array of fixed size, so the call itself never
+// allocates device (or pinned host) memory.  It reads the tile-list length
+// back after the key scan and the device status word at the end, so it
+// synchronises the caller's stream twice.
 //
 // The array belongs to the library image: every GPU that loads the library
 // holds it until the process exits.  All calls share it, so two calls whose
@@ -61,7 +63,7 @@ constexpr size_t kOffRanges = kOffScanTmp + kScanTmpBytes;
 constexpr size_t kOffLast = kOffRanges + kRangeBytes;
 constexpr size_t kOffTl = kOffLast + kPixBytes;
 constexpr size_t kOffPart = kOffTl + kPixBytes;
-constexpr size_t kOffMisc = kOffPart + kPartBytes;   // E, status, tile counter, pair counts
+constexpr size_t kOffMisc = kOffPart + kPartBytes;   // E, status, tile counter, 4 pair counters
 constexpr size_t kScratchBytes = kOffMisc + kMiscBytes;   // about 10.6 MiB
 
 // The scratch itself.  In host code `g_scratch` names a host-side stand-in,
@@ -74,12 +76,8 @@ std::mutex g_mutex;
 unsigned char* g_base[kMaxDevices] = {};
 
 // Once per device, with that device current: the device address of the array.
-lp_status scratch_base(unsigned char** out) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
-        cudaGetLastError();
-        return LP_ERR_CUDA;
-    }
+lp_status scratch_base(int dev, unsigned char** out) {
+    if (dev < 0 || dev >= kMaxDevices) return LP_ERR_CUDA;
     std::lock_guard<std::mutex> lock(g_mutex);
     if (!g_base[dev]) {
         void* p = nullptr;
@@ -109,14 +107,25 @@ extern "C" lp_status lp_render_forward_noalloc(const lp_prims* prims, const lp_c
     if (prims->n > 0 && (!prims->centre || !prims->verts || !prims->opacity || !prims->sh))
         return LP_ERR_INVALID;
     if (cam->width < 1 || cam->height < 1) return LP_ERR_INVALID;
+    // sizes checked before any arithmetic on them
+    if (prims->n > kMaxPrims || cam->width > kMaxPixels || cam->height > kMaxPixels) return LP_ERR_CAPACITY;
     const long long pixels = (long long)cam->width * cam->height;
     const int tile = 16;
     const int tiles_x = (cam->width + tile - 1) / tile, tiles_y = (cam->height + tile - 1) / tile;
     const long long tiles = (long long)tiles_x * tiles_y;
-    if (prims->n > kMaxPrims || pixels > kMaxPixels || tiles > kMaxTiles) return LP_ERR_CAPACITY;
+    if (pixels > kMaxPixels || tiles > kMaxTiles) return LP_ERR_CAPACITY;
 
+    // the stream must belong to the current device, whose copy of the
+    // scratch array the kernels are given
+    cudaStream_t st = (cudaStream_t)stream;
+    int dev = 0, sdev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaStreamGetDevice(st, &sdev) != cudaSuccess) {
+        cudaGetLastError();
+        return LP_ERR_CUDA;
+    }
+    if (sdev != dev) return LP_ERR_INVALID;
     unsigned char* base = nullptr;
-    lp_status s = scratch_base(&base);
+    lp_status s = scratch_base(dev, &base);
     if (s != LP_OK) return s;
     float* rec = reinterpret_cast<float*>(base + kOffRec);
     uint32_t* counts = reinterpret_cast<uint32_t*>(base + kOffCounts);
@@ -136,7 +145,7 @@ extern "C" lp_status lp_render_forward_noalloc(const lp_prims* prims, const lp_c
     uint32_t* d_E = reinterpret_cast<uint32_t*>(base + kOffMisc);
     int* d_status = reinterpret_cast<int*>(base + kOffMisc + 4);
     int* d_tile_counter = reinterpret_cast<int*>(base + kOffMisc + 8);
-    unsigned long long* d_pairs = reinterpret_cast<unsigned long long*>(base + kOffMisc + 16);   // 3 counters
+    unsigned long long* d_pairs = reinterpret_cast<unsigned long long*>(base + kOffMisc + 16);   // 4 counters
 
     // camera, digested as for lp_render_forward
     lp::CamsParam cp;
@@ -161,7 +170,6 @@ extern "C" lp_status lp_render_forward_noalloc(const lp_prims* prims, const lp_c
     d.tiles_x = tiles_x; d.tiles_y = tiles_y;
     d.tile_base = 0; d.pix_base = 0;
 
-    cudaStream_t st = (cudaStream_t)stream;
     const int V = prims->kind;
     const long long records = prims->n;
     lp::PrimsDev P{prims->n, prims->centre, prims->verts, prims->opacity, prims->sh};
@@ -189,8 +197,6 @@ extern "C" lp_status lp_render_forward_noalloc(const lp_prims* prims, const lp_c
     const bool in1 = (passes & 1) != 0;
     NA_CUDA(cudaMemsetAsync(ranges, 0, (size_t)tiles * sizeof(uint2), st));
     int sms = 0;
-    int dev = 0;
-    NA_CUDA(cudaGetDevice(&dev));
     NA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     NA_CUDA(lp::launch_ranges(in1 ? keys1 : keys0, d_E, E, d_status, ranges, sms, st));
     lp::BlendArgs a{};
@@ -211,6 +217,12 @@ extern "C" lp_status lp_render_forward_noalloc(const lp_prims* prims, const lp_c
     a.count = false;
     NA_CUDA(cudaMemsetAsync(d_tile_counter, 0, sizeof(int), st));
     NA_CUDA(lp::launch_blend_fwd(V, batch, pix, a, st));
+    // the status the emission and range kernels latch on the device
+    int status = 0;
+    NA_CUDA(cudaMemcpyAsync(&status, d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    NA_CUDA(cudaStreamSynchronize(st));
 #undef NA_CUDA
+    if (status & lp::kStatusCapacity) return LP_ERR_CAPACITY;
+    if (status & lp::kStatusTimeout) return LP_ERR_TIMEOUT;
     return LP_OK;
 }
