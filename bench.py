@@ -145,8 +145,8 @@ MEASURED_TRAFFIC = {
                   "capture": "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum -k regex:k_blend_bwd -s 2 -c 1"},
 }
 KERNEL_SOURCES = {
-    "blend_fwd": ("lp_blend_fwd.cu", "lp_blend.cuh", "lp_device.cuh"),
-    "blend_bwd": ("lp_blend_bwd.cu", "lp_blend.cuh", "lp_device.cuh"),
+    "blend_fwd": ("lp_blend_fwd.cuh", "lp_blend.cuh", "lp_device.cuh"),
+    "blend_bwd": ("lp_blend_bwd.cuh", "lp_blend.cuh", "lp_device.cuh"),
 }
 
 
@@ -166,7 +166,7 @@ def measured_traffic(kernel):
     return t["bytes"]
 
 
-def hbm_bytes(kind_v, K, n, n_cams, E, passes, tiles, sort_mode=0, key_bits=0):
+def hbm_bytes(kind_v, K, n, n_cams, E, passes, tiles, sort_mode=0, key_bits=0, radix_bits=8):
     """Algorithmic bytes per launch of the HBM-bound stages: each radix pass
     reads and writes every key and value once (histogram reads excluded).
     Sort mode 0 emits 64-bit (tile, depth) keys and sorts them; mode 1 sorts
@@ -185,7 +185,7 @@ def hbm_bytes(kind_v, K, n, n_cams, E, passes, tiles, sort_mode=0, key_bits=0):
         out["scan_emit"] = R * (4 + 4 + 4 + 16 + 4) + E * 12
         out["sort"] = passes * E * 24
     else:
-        p2 = (key_bits + 7) // 8
+        p2 = (key_bits + radix_bits - 1) // radix_bits
         p1 = max(passes - p2, 0)
         out["scan_emit"] = (R * (4 + 4 + 8)            # depth keys
                             + p1 * R * 16             # record sort by depth
@@ -208,8 +208,9 @@ def roofline(rast, stages, kind, sh_degree, n, n_cams, clk, dev):
     props = torch.cuda.get_device_properties(dev)
     sm_max = peaks.get("sm_max_mhz") or clk.get("sm_max_mhz") or 2070.0
     alu_peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12   # TFLOP/s
+    tun = rast.tuning()
     hb = hbm_bytes(kind, (sh_degree + 1) ** 2, n, n_cams, st["entries"], st["sort_passes"], st["tiles"],
-                   rast.tuning()["sort_mode"], st["key_bits"])
+                   tun["sort_mode"], st["key_bits"], tun.get("radix_bits", 8))
     render_stages = {k: v for k, v in stages.items() if k in hb or k in ("blend_fwd", "blend_bwd")}
     dom = max(render_stages, key=render_stages.get)
     if dom in ("blend_fwd", "blend_bwd"):
@@ -628,6 +629,7 @@ def ours(args, workload):
     if rank == 0:
         cfg = config_dict(args, w)
         cfg["tuning"] = m["tuning"]
+        cfg["tile"] = m["tuning"]["tile"]
         line = {"metric": METRIC, "value": m["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": m["ms_per_step"], "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -817,7 +819,7 @@ def train_arm(args):
         cfg = {"workload": w.name + " (workload 4, optimisation step)", "primitives": n, "kind": "octahedron",
                "sh_degree": tr.prims.sh_degree, "cameras": len(w.cameras),
                "resolutions": sorted({f"{c.width}x{c.height}" for c in w.cameras}), "pixels_per_step": P,
-               "tile": 16, "form": "params -> render -> L1 -> backward -> params adjoint -> Adam, one CUDA graph",
+               "tile": tuned["tile"], "form": "params -> render -> L1 -> backward -> params adjoint -> Adam, one CUDA graph",
                "l2": "inputs larger than L2 (2M primitives x 59 parameters x 4 arrays, images > 129 MB)",
                "parallelism": f"replicas x{world}", "tuning": tuned, "learning_rates": tr.lr}
         line = {"metric": TRAIN_METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -89,8 +89,9 @@ typedef struct {
 } lp_prims;
 
 /* Launch / algorithm parameters (the autotuner's search space).
- *   tile          tile edge in pixels; 16, the paper's patch size (App.
- *                 "Rendering Performance", Table 7).
+ *   tile          tile edge in pixels: 8, 16 (the paper's patch size, App.
+ *                 "Rendering Performance", Table 7) or 32.  Smaller tiles
+ *                 give longer tile lists but fewer list entries per pixel.
  *   batch         projected primitives staged in shared memory per round of
  *                 the blend: 32, 64 or 128.
  *   blocks_per_sm resident blend blocks per SM for the persistent grid;
@@ -99,7 +100,10 @@ typedef struct {
  *                 keys; 1: stable sort of records by depth, then a stable
  *                 sort of the tile ids (same resulting order).
  *   pixels_per_thread  1, 2 or 4 horizontally adjacent pixels per blend
- *                 thread (256 / pixels_per_thread threads per tile).
+ *                 thread (tile^2 / pixels_per_thread threads per tile);
+ *                 built pairs: tile 8 with 1 or 2, tile 16 with 1, 2 or 4,
+ *                 tile 32 with 2 or 4.  The exact-span mode takes 2 pixels
+ *                 per thread on 8x8 tiles and 4 otherwise.
  *   chain_split   0: the backward's chain to world space in one pass per
  *                 primitive; 1: in two passes, geometry then colour, each
  *                 holding fewer registers (ignored while densification
@@ -107,9 +111,16 @@ typedef struct {
  *   sparse_lanes  0..32: a backward warp in which at most this many lanes
  *                 contribute to a record adds their terms with one atomic
  *                 per lane and value instead of reducing over the warp.
- * Every setting renders bit-identical images and tile lists.  chain_split
- * and sparse_lanes change the order in which gradient terms are summed, so
- * gradients can differ in the last bits between settings.                  */
+ *   radix_bits    digit width of the radix sort passes: 4, 6, 8 or 11 bits
+ *                 (ceil(key bits / radix_bits) passes, each with a histogram
+ *                 of 2^radix_bits bins per 4096 keys).
+ * For one tile edge every setting renders bit-identical images and tile
+ * lists.  Another tile edge gives other tile lists (each in the paper's
+ * per-tile order) and re-bases the face planes at other tile origins, which
+ * changes image values by rounding only.  chain_split and sparse_lanes change
+ * the order in which gradient terms are summed, so gradients can differ in
+ * the last bits between settings.  A backward, depth pass or pair count uses
+ * the tile edge, batch and pixels per thread of its forward.                */
 typedef struct {
     int tile;
     int batch;
@@ -118,6 +129,7 @@ typedef struct {
     int pixels_per_thread;
     int chain_split;
     int sparse_lanes;
+    int radix_bits;
 } lp_tuning;
 
 /* Sizes of the last forward call (filled by lp_get_stats).                 */
@@ -155,7 +167,8 @@ void lp_destroy(lp_ctx* ctx);
 
 /* Set / read the tuning parameters (defaults: tile 16, batch 64,
  * blocks_per_sm 0, sort_mode 0, pixels_per_thread 4, chain_split 0,
- * sparse_lanes 8).                                                          */
+ * sparse_lanes 8, radix_bits 8).  LP_ERR_INVALID for a value outside the
+ * sets above, or a (tile, pixels_per_thread) pair that is not built.        */
 lp_status lp_set_tuning(lp_ctx* ctx, const lp_tuning* t);
 lp_status lp_get_tuning(lp_ctx* ctx, lp_tuning* t);
 

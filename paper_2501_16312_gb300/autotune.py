@@ -1,17 +1,19 @@
 """Autotuner for the rasterizer's launch parameters.
 
-The tuning knobs (sort mode, pixels per blend thread, records per shared-memory
-batch, resident blend blocks per SM, one- or two-pass backward chain, and the
-number of contributing lanes up to which a backward warp lets each lane add
-its own terms) change only the schedule: every setting renders bit-identical
-images (the chain's split and the backward's reduction form only reorder
-floating-point sums of gradients).  The tuner times forward + backward of the
-caller's own workload with the library's per-stage CUDA events.  It settles
-the knobs one group at a time, each judged on the stages it affects: the sort
-mode on the sort stages, the blend schedule on the two blend stages, the
-chain form on the chain stage and the lane threshold on the backward blend.
-The choice is cached as JSON keyed by GPU name, primitive kind and size
-buckets of the workload.
+The tuning knobs (sort mode and radix digit width, tile edge, pixels per
+blend thread, records per shared-memory batch, resident blend blocks per SM,
+one- or two-pass backward chain, and the number of contributing lanes up to
+which a backward warp lets each lane add its own terms) change only the
+schedule: for one tile edge every setting renders bit-identical images (the
+chain's split and the backward's reduction form only reorder floating-point
+sums of gradients), and another tile edge changes images by rounding only.  The tuner times forward + backward of the caller's own workload
+with the library's per-stage CUDA events.  It settles the knobs one group at
+a time, each judged on the stages it affects: the sort mode and digit width
+on the sort stages; the tile edge and blend schedule on the sort and blend
+stages (the tile edge sets the tile-list length as well as the blend's work);
+the chain form on the chain stage and the lane threshold on the backward
+blend.  The choice is cached as JSON keyed by GPU name, primitive kind and
+size buckets of the workload.
 """
 from __future__ import annotations
 
@@ -50,12 +52,16 @@ def _time(rast, prims, cameras, bg, dL, grads, images, reps: int):
     return acc
 
 
+# (tile edge, pixels per thread) pairs the blends are built for, as the
+# library's lp_set_tuning accepts them
+TILE_PIX = ((8, 1), (8, 2), (16, 2), (16, 4), (32, 2), (32, 4))
+
 # The search: each group of knobs, its candidates, and the stages it is
 # judged on.  Later groups are timed at the earlier groups' choices.
 GROUPS = (
-    (("sort_mode",), ((0,), (1,)), SORT_STAGES),
-    (("pixels_per_thread", "batch", "blocks_per_sm"),
-     tuple(itertools.product((2, 4), (32, 64), (0,))), BLEND_STAGES),
+    (("sort_mode", "radix_bits"), tuple(itertools.product((0, 1), (4, 6, 8, 11))), SORT_STAGES),
+    (("tile", "pixels_per_thread", "batch", "blocks_per_sm"),
+     tuple((t, p, b, 0) for (t, p), b in itertools.product(TILE_PIX, (32, 64))), SORT_STAGES + BLEND_STAGES),
     (("chain_split",), ((0,), (1,)), ("chain",)),
     (("sparse_lanes",), ((8,), (16,)), ("blend_bwd",)),
 )

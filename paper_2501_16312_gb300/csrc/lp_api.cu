@@ -39,11 +39,12 @@ constexpr unsigned char kGuardByte = 0xA5;
 struct lp_ctx {
     int device = 0;
     int sms = 0;
-    lp_tuning tune{16, 64, 0, 0, 4, 0, 8};
+    lp_tuning tune{16, 64, 0, 0, 4, 0, 8, 8};
     float aa_kernel = 0.f;      // 2D filter size in pixels (0 = off)
     bool exact = false;         // spans along the true perspective ray
     bool fwd_exact = false;     // mode of the last forward
     uint32_t contrib_stride = 0;
+    lp_tuning fwd_tune{16, 64, 0, 0, 4, 0, 8, 8};   // schedule of the last forward (its tiles, mask layout)
     // densification statistics gathered by forward and backward (null: off)
     float* st_grad_sum = nullptr;
     uint32_t* st_grad_count = nullptr;
@@ -234,20 +235,27 @@ void mark(lp_ctx* ctx, cudaStream_t st, int i, bool cap_mode) {
     cudaEventRecordWithFlags(ctx->ev[i], st, cap_mode ? cudaEventRecordExternal : cudaEventRecordDefault);
 }
 
-// Persistent blend grid: resident blocks per SM (tuned, or what fits) x SMs,
-// never more blocks than tiles.
-int blend_grid(const lp_ctx* ctx, int V, bool fwd, long long tiles, bool exact = false) {
-    int bps = ctx->tune.blocks_per_sm;
+// Persistent blend grid for schedule t: resident blocks per SM (tuned, or
+// what fits) x SMs, never more blocks than tiles.
+int blend_grid(const lp_ctx* ctx, const lp_tuning& t, int V, bool fwd, long long tiles, bool exact = false) {
+    int bps = t.blocks_per_sm;
     if (exact) {
-        bps = lp::blend_x_occupancy(V, fwd);
+        bps = lp::blend_x_occupancy(t.tile, V, fwd);
         if (bps <= 0) bps = 1;
     } else if (bps <= 0) {
-        bps = fwd ? lp::blend_fwd_occupancy(V, ctx->tune.batch, ctx->tune.pixels_per_thread)
-                  : lp::blend_bwd_occupancy(V, ctx->tune.batch, ctx->tune.pixels_per_thread);
+        bps = fwd ? lp::blend_fwd_occupancy(t.tile, V, t.batch, t.pixels_per_thread)
+                  : lp::blend_bwd_occupancy(t.tile, V, t.batch, t.pixels_per_thread);
         if (bps <= 0) bps = 1;
     }
     const long long g = (long long)ctx->sms * bps;
     return (int)(tiles < g ? tiles : g);
+}
+
+// Rows of the per-warp contributor mask (one per warp of a tile) for a
+// schedule; kMaskWarpsMax bounds every supported schedule.
+constexpr int kMaskWarpsMax = 16;
+int mask_warps(const lp_tuning& t, bool exact) {
+    return exact ? lp::blend_x_warps(t.tile) : lp::blend_warps(t.tile, t.pixels_per_thread);
 }
 
 int bits_for(long long n) {   // bits needed to represent values 0 .. n-1
@@ -320,19 +328,25 @@ void lp_destroy(lp_ctx* ctx) {
 
 lp_status lp_set_tuning(lp_ctx* ctx, const lp_tuning* t) {
     if (!ctx || !t) return LP_ERR_INVALID;
-    if (t->tile != 16) return fail(ctx, LP_ERR_UNSUPPORTED, "tile %d: only 16 is built", t->tile);
+    if (t->tile != 8 && t->tile != 16 && t->tile != 32)
+        return fail(ctx, LP_ERR_INVALID, "tile %d not in {8, 16, 32}", t->tile);
     if (t->batch != 32 && t->batch != 64 && t->batch != 128)
         return fail(ctx, LP_ERR_INVALID, "batch %d not in {32, 64, 128}", t->batch);
     if (t->blocks_per_sm < 0 || t->blocks_per_sm > 32)
         return fail(ctx, LP_ERR_INVALID, "blocks_per_sm %d outside 0..32", t->blocks_per_sm);
     if (t->pixels_per_thread != 1 && t->pixels_per_thread != 2 && t->pixels_per_thread != 4)
         return fail(ctx, LP_ERR_INVALID, "pixels_per_thread %d not in {1, 2, 4}", t->pixels_per_thread);
+    if (!lp::tile_pix_ok(t->tile, t->pixels_per_thread))
+        return fail(ctx, LP_ERR_INVALID, "pixels_per_thread %d is not built for %dx%d tiles (8: 1, 2; 16: 1, 2, 4; "
+                    "32: 2, 4)", t->pixels_per_thread, t->tile, t->tile);
     if (t->sort_mode != 0 && t->sort_mode != 1)
         return fail(ctx, LP_ERR_INVALID, "sort_mode %d not in {0, 1}", t->sort_mode);
     if (t->chain_split != 0 && t->chain_split != 1)
         return fail(ctx, LP_ERR_INVALID, "chain_split %d not in {0, 1}", t->chain_split);
     if (t->sparse_lanes < 0 || t->sparse_lanes > 32)
         return fail(ctx, LP_ERR_INVALID, "sparse_lanes %d outside 0..32", t->sparse_lanes);
+    if (t->radix_bits != 4 && t->radix_bits != 6 && t->radix_bits != 8 && t->radix_bits != 11)
+        return fail(ctx, LP_ERR_INVALID, "radix_bits %d not in {4, 6, 8, 11}", t->radix_bits);
     ctx->tune = *t;
     return LP_OK;
 }
@@ -411,7 +425,7 @@ static lp_status reserve_impl(lp_ctx* ctx, long long records, long long entries,
     long long sb2 = lp::scan_blocks((long long)lp::sort_hist_elems(hmax));
     LP_TRY(ensure(ctx, ctx->scan_tmp, sb > sb2 ? sb : sb2, false, "scan blocks"));
     LP_TRY(ensure(ctx, ctx->emit_part, (long long)lp::emit_blocks(records, kcap) + 1, false, "emit partition"));
-    LP_TRY(ensure(ctx, ctx->contrib, (kcap / 32 + 2) * 8, false, "contributor mask"));
+    LP_TRY(ensure(ctx, ctx->contrib, (kcap / 32 + 2) * kMaskWarpsMax, false, "contributor mask"));
     LP_TRY(ensure(ctx, ctx->ranges, tiles, false, "tile ranges"));
     LP_TRY(ensure(ctx, ctx->last, pixels, false, "pixel state"));
     LP_TRY(ensure(ctx, ctx->tl, pixels, false, "pixel state"));
@@ -493,7 +507,8 @@ lp_status lp_render_forward(lp_ctx* ctx, const lp_prims* prims, const lp_camera*
         // stage 1: records by centre depth
         LP_CUDA(lp::launch_depth_keys(ctx->counts.p, ctx->zbits.p, records, ctx->dkeys0.p, ctx->dvals0.p, st));
         LP_CUDA(lp::launch_radix_sort32(ctx->dkeys0.p, ctx->dvals0.p, ctx->dkeys1.p, ctx->dvals1.p, nullptr,
-                                        records, 32, ctx->hist.p, ctx->scan_tmp.p, &passes1, st));
+                                        records, 32, ctx->tune.radix_bits, ctx->hist.p, ctx->scan_tmp.p,
+                                        &passes1, st));
         order = (passes1 & 1) ? ctx->dvals1.p : ctx->dvals0.p;
         LP_CUDA(lp::launch_gather_counts(ctx->counts.p, order, records, ctx->counts_sorted.p, st));
         LP_CUDA(lp::launch_scan(ctx->counts_sorted.p, records, ctx->offsets.p, ctx->scan_tmp.p, ctx->d_E,
@@ -524,7 +539,8 @@ lp_status lp_render_forward(lp_ctx* ctx, const lp_prims* prims, const lp_camera*
                   "scan blocks"));
     LP_TRY(ensure(ctx, ctx->emit_part, (long long)lp::emit_blocks(records, bound) + 1, cap_mode,
                   "emit partition"));
-    LP_TRY(ensure(ctx, ctx->contrib, (bound / 32 + 2) * 8, cap_mode, "contributor mask"));
+    const int mwarps = mask_warps(ctx->tune, exact);
+    LP_TRY(ensure(ctx, ctx->contrib, (bound / 32 + 2) * mwarps, cap_mode, "contributor mask"));
     ctx->contrib_stride = (uint32_t)(bound / 32 + 2);
 
     const int tile_bits = bits_for(tiles);
@@ -540,7 +556,7 @@ lp_status lp_render_forward(lp_ctx* ctx, const lp_prims* prims, const lp_camera*
         mark(ctx, st, 2, cap_mode);
         key_bits = tile_bits;
         LP_CUDA(lp::launch_radix_sort32(t0, ctx->vals0.p, t1, ctx->vals1.p, ctx->d_E, bound, key_bits,
-                                        ctx->hist.p, ctx->scan_tmp.p, &passes, st));
+                                        ctx->tune.radix_bits, ctx->hist.p, ctx->scan_tmp.p, &passes, st));
         const bool in1 = (passes & 1) != 0;
         svals = in1 ? ctx->vals1.p : ctx->vals0.p;
         mark(ctx, st, 3, cap_mode);
@@ -554,7 +570,8 @@ lp_status lp_render_forward(lp_ctx* ctx, const lp_prims* prims, const lp_camera*
         mark(ctx, st, 2, cap_mode);
         key_bits = 32 + tile_bits;
         LP_CUDA(lp::launch_radix_sort(ctx->keys0.p, ctx->vals0.p, ctx->keys1.p, ctx->vals1.p, ctx->d_E,
-                                      bound, key_bits, ctx->hist.p, ctx->scan_tmp.p, &passes, st));
+                                      bound, key_bits, ctx->tune.radix_bits, ctx->hist.p, ctx->scan_tmp.p,
+                                      &passes, st));
         const bool in1 = (passes & 1) != 0;
         svals = in1 ? ctx->vals1.p : ctx->vals0.p;
         mark(ctx, st, 3, cap_mode);
@@ -566,7 +583,7 @@ lp_status lp_render_forward(lp_ctx* ctx, const lp_prims* prims, const lp_camera*
     mark(ctx, st, 4, cap_mode);
 
     lp::BlendArgs a{};
-    a.grid = blend_grid(ctx, V, true, tiles, exact);
+    a.grid = blend_grid(ctx, ctx->tune, V, true, tiles, exact);
     a.rec = ctx->rec.p;
     a.vals = svals;
     a.ranges = ctx->ranges.p;
@@ -580,11 +597,11 @@ lp_status lp_render_forward(lp_ctx* ctx, const lp_prims* prims, const lp_camera*
     a.count = false;
     a.contrib = ctx->contrib.p;
     a.contrib_stride = ctx->contrib_stride;
-    LP_CUDA(cudaMemsetAsync(ctx->contrib.p, 0, (size_t)(bound / 32 + 2) * 8 * sizeof(uint32_t), st));
+    LP_CUDA(cudaMemsetAsync(ctx->contrib.p, 0, (size_t)(bound / 32 + 2) * mwarps * sizeof(uint32_t), st));
     LP_CUDA(cudaMemsetAsync(ctx->d_tile_counter, 0, sizeof(int), st));
     if (a.grid > 0) {
-        if (exact) LP_CUDA(lp::launch_blend_fwd_x(V, a, st));
-        else LP_CUDA(lp::launch_blend_fwd(V, ctx->tune.batch, ctx->tune.pixels_per_thread, a, st));
+        if (exact) LP_CUDA(lp::launch_blend_fwd_x(ctx->tune.tile, V, a, st));
+        else LP_CUDA(lp::launch_blend_fwd(ctx->tune.tile, V, ctx->tune.batch, ctx->tune.pixels_per_thread, a, st));
     }
     mark(ctx, st, 5, cap_mode);
     ctx->fwd_timed = ctx->timing;
@@ -603,6 +620,7 @@ lp_status lp_render_forward(lp_ctx* ctx, const lp_prims* prims, const lp_camera*
     ctx->sort_passes = passes1 + passes;
     ctx->keys32 = mode == 1;
     ctx->fwd_exact = exact;
+    ctx->fwd_tune = ctx->tune;
     return LP_OK;
 }
 
@@ -626,7 +644,8 @@ lp_status lp_render_backward(lp_ctx* ctx, const float* dL_dimages, float* dcentr
     LP_CUDA(cudaMemsetAsync(ctx->acc.p, 0, (size_t)acc_n * sizeof(float), st));
 
     lp::BlendArgs a{};
-    a.grid = blend_grid(ctx, ctx->prims.kind, false, ctx->tiles, exact);
+    const lp_tuning& ft = ctx->fwd_tune;   // the backward walks the forward's tiles and masks
+    a.grid = blend_grid(ctx, ft, ctx->prims.kind, false, ctx->tiles, exact);
     a.rec = ctx->rec.p;
     a.vals = ctx->result_in_1 ? ctx->vals1.p : ctx->vals0.p;
     a.ranges = ctx->ranges.p;
@@ -642,8 +661,8 @@ lp_status lp_render_backward(lp_ctx* ctx, const float* dL_dimages, float* dcentr
     a.tile_counter = ctx->d_tile_counter + 1;
     LP_CUDA(cudaMemsetAsync(ctx->d_tile_counter + 1, 0, sizeof(int), st));
     if (a.grid > 0) {
-        if (exact) LP_CUDA(lp::launch_blend_bwd_x(V, a, st));
-        else LP_CUDA(lp::launch_blend_bwd(V, ctx->tune.batch, ctx->tune.pixels_per_thread, a, st));
+        if (exact) LP_CUDA(lp::launch_blend_bwd_x(ft.tile, V, a, st));
+        else LP_CUDA(lp::launch_blend_bwd(ft.tile, V, ft.batch, ft.pixels_per_thread, a, st));
     }
     mark(ctx, st, 7, cap_mode);
 
@@ -829,7 +848,8 @@ lp_status lp_render_depth(lp_ctx* ctx, float* depth, void* stream) {
     LP_CUDA(cudaSetDevice(ctx->device));
     cudaStream_t st = (cudaStream_t)stream;
     lp::BlendArgs a{};
-    a.grid = blend_grid(ctx, ctx->prims.kind, true, ctx->tiles, ctx->fwd_exact);
+    const lp_tuning& ft = ctx->fwd_tune;
+    a.grid = blend_grid(ctx, ft, ctx->prims.kind, true, ctx->tiles, ctx->fwd_exact);
     a.rec = ctx->rec.p;
     a.vals = ctx->result_in_1 ? ctx->vals1.p : ctx->vals0.p;
     a.ranges = ctx->ranges.p;
@@ -839,9 +859,9 @@ lp_status lp_render_depth(lp_ctx* ctx, float* depth, void* stream) {
     a.depth = depth;
     LP_CUDA(cudaMemsetAsync(ctx->d_tile_counter, 0, sizeof(int), st));
     if (a.grid > 0 && ctx->fwd_exact)
-        LP_CUDA(lp::launch_blend_fwd_x(ctx->prims.kind, a, st));
+        LP_CUDA(lp::launch_blend_fwd_x(ft.tile, ctx->prims.kind, a, st));
     else if (a.grid > 0)
-        LP_CUDA(lp::launch_blend_fwd(ctx->prims.kind, ctx->tune.batch, ctx->tune.pixels_per_thread, a, st));
+        LP_CUDA(lp::launch_blend_fwd(ft.tile, ctx->prims.kind, ft.batch, ft.pixels_per_thread, a, st));
     else if (ctx->pixels > 0)
         LP_CUDA(cudaMemsetAsync(depth, 0, (size_t)ctx->pixels * sizeof(float), st));
     return LP_OK;
@@ -854,7 +874,8 @@ lp_status lp_count_pairs(lp_ctx* ctx, long long* counts) {
     LP_CUDA(cudaDeviceSynchronize());
     LP_TRY(ensure(ctx, ctx->scratch_image, 3 * ctx->pixels, false, "scratch image"));
     lp::BlendArgs a{};
-    a.grid = blend_grid(ctx, ctx->prims.kind, true, ctx->tiles, ctx->fwd_exact);
+    const lp_tuning& ft = ctx->fwd_tune;
+    a.grid = blend_grid(ctx, ft, ctx->prims.kind, true, ctx->tiles, ctx->fwd_exact);
     a.rec = ctx->rec.p;
     a.vals = ctx->result_in_1 ? ctx->vals1.p : ctx->vals0.p;
     a.ranges = ctx->ranges.p;
@@ -868,9 +889,9 @@ lp_status lp_count_pairs(lp_ctx* ctx, long long* counts) {
     a.count = true;
     LP_CUDA(cudaMemset(ctx->d_pairs, 0, 4 * sizeof(unsigned long long)));
     LP_CUDA(cudaMemset(ctx->d_tile_counter, 0, sizeof(int)));
-    if (a.grid > 0 && ctx->fwd_exact) LP_CUDA(lp::launch_blend_fwd_x(ctx->prims.kind, a, 0));
+    if (a.grid > 0 && ctx->fwd_exact) LP_CUDA(lp::launch_blend_fwd_x(ft.tile, ctx->prims.kind, a, 0));
     else if (a.grid > 0)
-        LP_CUDA(lp::launch_blend_fwd(ctx->prims.kind, ctx->tune.batch, ctx->tune.pixels_per_thread, a, 0));
+        LP_CUDA(lp::launch_blend_fwd(ft.tile, ctx->prims.kind, ft.batch, ft.pixels_per_thread, a, 0));
     LP_CUDA(cudaDeviceSynchronize());
     unsigned long long h[4] = {0, 0, 0, 0};
     LP_CUDA(cudaMemcpy(h, ctx->d_pairs, sizeof(h), cudaMemcpyDeviceToHost));

@@ -1,10 +1,12 @@
 // Shared pieces of the forward and backward blend kernels (sm_103a).
 //
-// A tile of 16x16 pixels is processed by 256 / PIX threads; thread t owns the
-// strip of PIX horizontally adjacent pixels starting at
-// (lx0, ly) = ((t % (16 / PIX)) * PIX, t / (16 / PIX)), so that one 128-bit
-// shared-memory load of a face plane feeds PIX pixels.  Blocks are
-// persistent and pull tiles of all cameras from one atomic queue.
+// A tile of TILE x TILE pixels (TILE = 8, 16 or 32, a tuning choice; 16 is
+// the paper's patch size) is processed by TILE^2 / PIX threads; thread t owns
+// the strip of PIX horizontally adjacent pixels starting at
+// (lx0, ly) = ((t % (TILE / PIX)) * PIX, t / (TILE / PIX)), so that one
+// 128-bit shared-memory load of a face plane feeds PIX pixels.  A warp covers
+// 32 PIX / TILE whole rows.  Blocks are persistent and pull tiles of all
+// cameras from one atomic queue.
 #pragma once
 
 #include "lp_device.cuh"
@@ -12,8 +14,6 @@
 
 namespace lp {
 
-constexpr int kTile = 16;
-constexpr int kTilePixels = kTile * kTile;
 
 __device__ __forceinline__ float warp_sum(float x) {
 #pragma unroll
@@ -56,11 +56,12 @@ struct TileGeom {
     int pix_base;
 };
 
+template <int TILE>
 __device__ __forceinline__ TileGeom tile_geom(const CamsParam& cams, int tile) {
     const CamDev& cm = cams.cam[camera_of_tile(cams, tile)];
     const int lt = tile - cm.tile_base;
     const int ty = lt / cm.tiles_x, tx = lt - ty * cm.tiles_x;
-    return TileGeom{tile, tx * kTile, ty * kTile, cm.width, cm.height, cm.pix_base};
+    return TileGeom{tile, tx * TILE, ty * TILE, cm.width, cm.height, cm.pix_base};
 }
 
 }  // namespace lp

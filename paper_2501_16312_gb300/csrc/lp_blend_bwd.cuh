@@ -19,17 +19,23 @@
 // (the colour and sigma terms in one butterfly, the faces' moments two faces
 // per butterfly) and issues one atomic add per value into the record's
 // accumulator.
+//
+// The kernels are templates over the tile edge; each of lp_blend_bwd_t8.cu,
+// _t16.cu and _t32.cu instantiates one edge.
+#pragma once
+
 #include "lp_blend.cuh"
 
 namespace lp {
 
 namespace {
 
-
 // 768 resident threads per SM (at most 80 registers): measured faster than
-// the 96-register schedule the compiler picks on its own.
-template <int V, int BATCH, int PIX>
-__global__ void __launch_bounds__(kTilePixels / PIX, 3 * PIX) k_blend_bwd(
+// the 96-register schedule the compiler picks on its own (16x16 tiles).
+template <int NT> constexpr int bwd_min_blocks() { return 768 / NT > 0 ? 768 / NT : 1; }
+
+template <int V, int BATCH, int PIX, int TILE>
+__global__ void __launch_bounds__(TILE * TILE / PIX, bwd_min_blocks<TILE * TILE / PIX>()) k_blend_bwd(
     const float* __restrict__ rec, const uint32_t* __restrict__ vals, const uint2* __restrict__ ranges,
     CamsParam cams, float bg0, float bg1, float bg2, const float* __restrict__ dimage,
     const uint32_t* __restrict__ last_in, const float* __restrict__ tl_in, float* __restrict__ acc,
@@ -37,8 +43,11 @@ __global__ void __launch_bounds__(kTilePixels / PIX, 3 * PIX) k_blend_bwd(
     int sparse_lanes) {
     constexpr int F = Kind<V>::F;
     constexpr int ACC = Acc<V>::kFloats;
-    constexpr int NT = kTilePixels / PIX;
-    constexpr int RW = kTile / PIX;
+    constexpr int NT = TILE * TILE / PIX;
+    constexpr int RW = TILE / PIX;
+    constexpr int MW = BATCH / 32;   // contributor-mask words per batch
+    static_assert(NT % 32 == 0 && 32 % RW == 0, "whole warps of whole rows");
+    static_assert(BATCH % 32 == 0, "whole mask words per batch");
     __shared__ Staged<V> sm[BATCH];
     __shared__ int s_tile;
     __shared__ int s_max;
@@ -53,7 +62,7 @@ __global__ void __launch_bounds__(kTilePixels / PIX, 3 * PIX) k_blend_bwd(
         __syncthreads();
         const int tile = s_tile;
         if (tile >= cams.total_tiles) break;
-        const TileGeom tg = tile_geom(cams, tile);
+        const TileGeom tg = tile_geom<TILE>(cams, tile);
         const int py = tg.ty0 + ly;
         const uint2 rg = ranges[tile];
         const int plane = tg.width * tg.height;
@@ -84,15 +93,38 @@ __global__ void __launch_bounds__(kTilePixels / PIX, 3 * PIX) k_blend_bwd(
             const int nb = hi - lo;
             __syncthreads();
             for (int j = tid; j < nb; j += NT) stage_record<V>(rec, vals[rg.x + lo + j], tg.tx0, tg.ty0, sm[j]);
-            __syncthreads();
-            for (int j = nb - 1; j >= 0; --j) {
-                const uint32_t idx = (uint32_t)(lo + j);
-                if (contrib) {
-                    // the forward blended this entry at none of this warp's pixels
-                    const uint32_t e = rg.x + idx;
-                    const uint32_t* cw = contrib + (size_t)(tid >> 5) * cstride;
-                    if (!((__ldg(cw + (e >> 5)) >> (e & 31u)) & 1u)) continue;
+            // This warp's bits of the forward's contributor mask for entries
+            // lo .. hi - 1 (bit j of bm: entry lo + j), loaded once per batch:
+            // lane q fetches word q of the run, the warp shifts them into
+            // place, and the walk below visits the set bits only.
+            uint32_t bm[MW];
+            {
+                const uint32_t e0 = rg.x + (uint32_t)lo;
+                const uint32_t w0 = e0 >> 5, sh = e0 & 31u;
+                const uint32_t w_last = (e0 + (uint32_t)nb - 1u) >> 5;   // last word of the run
+                uint32_t src = 0u;
+                if (lane <= MW && w0 + (uint32_t)lane <= w_last)
+                    src = contrib ? __ldg(contrib + (size_t)(tid >> 5) * cstride + w0 + lane) : 0xffffffffu;
+#pragma unroll
+                for (int q = 0; q < MW; ++q) {
+                    const uint32_t lo_w = __shfl_sync(0xffffffffu, src, q);
+                    const uint32_t hi_w = __shfl_sync(0xffffffffu, src, q + 1);
+                    uint32_t m = sh ? (lo_w >> sh) | (hi_w << (32u - sh)) : lo_w;
+                    const int valid = nb - 32 * q;   // entries of this word inside the batch
+                    if (valid < 32) m &= valid > 0 ? (1u << valid) - 1u : 0u;
+                    bm[q] = m;
                 }
+            }
+            __syncthreads();
+#pragma unroll 1
+            for (int q = MW - 1; q >= 0; --q)
+            for (uint32_t mq = bm[q]; mq != 0u;) {
+                // entries the forward blended at none of this warp's pixels are
+                // never visited
+                const int bit = 31 - __clz(mq);
+                mq ^= 1u << bit;
+                const int j = 32 * q + bit;
+                const uint32_t idx = (uint32_t)(lo + j);
                 const Staged<V>& p = sm[j];
                 bool any = false;
 #pragma unroll
@@ -124,8 +156,9 @@ __global__ void __launch_bounds__(kTilePixels / PIX, 3 * PIX) k_blend_bwd(
 #pragma unroll
                     for (int i = 0; i < PIX; ++i) {
                         if (c[i]) {
-                            const float tau = span_tau(p.sigma, sp[i]);
-                            const float o = 1.f - tau;
+                            const float xs = span_x(p.sigma, sp[i]);
+                            const float tau = span_tau(xs);
+                            const float o = span_opacity(xs, tau);
                             // tau >= 1e-3 wherever we divide (T stayed >= 1e-3 before
                             // the last contributor), so the fast division is safe
                             const float Ti = first[i] ? Tcur[i] : __fdividef(Tcur[i], tau);
@@ -214,38 +247,47 @@ __global__ void __launch_bounds__(kTilePixels / PIX, 3 * PIX) k_blend_bwd(
     }
 }
 
-template <int V, int BATCH, int PIX>
+template <int V, int BATCH, int PIX, int TILE>
 cudaError_t bwd_t(const BlendArgs& a, cudaStream_t st) {
-    k_blend_bwd<V, BATCH, PIX><<<a.grid, kTilePixels / PIX, 0, st>>>(
+    k_blend_bwd<V, BATCH, PIX, TILE><<<a.grid, TILE * TILE / PIX, 0, st>>>(
         a.rec, a.vals, a.ranges, *a.cams, a.bg[0], a.bg[1], a.bg[2], a.dimage, a.last, a.tl, a.acc,
         a.tile_counter, a.contrib, a.contrib_stride, a.sparse_lanes);
     return cudaGetLastError();
 }
 
-template <int V, int BATCH, int PIX>
+template <int V, int BATCH, int PIX, int TILE>
 int bwd_occ() {
     int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_blend_bwd<V, BATCH, PIX>, kTilePixels / PIX, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_blend_bwd<V, BATCH, PIX, TILE>, TILE * TILE / PIX, 0);
     return nb;
 }
 
-}  // namespace
+#define LP_PIX_CASES_B(FN, V, B, T, ...)                                                     \
+    if constexpr (tile_pix_ok(T, 1)) { if (pix == 1) return FN<V, B, 1, T>(__VA_ARGS__); }   \
+    if constexpr (tile_pix_ok(T, 2)) { if (pix == 2) return FN<V, B, 2, T>(__VA_ARGS__); }   \
+    if constexpr (tile_pix_ok(T, 4)) { if (pix == 4) return FN<V, B, 4, T>(__VA_ARGS__); }
+#define LP_BLEND_DISPATCH_B(FN, T, BAD, ...)                                                 \
+    if (V == 6) {                                                                            \
+        if (batch == 32) { LP_PIX_CASES_B(FN, 6, 32, T, __VA_ARGS__) }                       \
+        else if (batch == 128) { LP_PIX_CASES_B(FN, 6, 128, T, __VA_ARGS__) }                \
+        else { LP_PIX_CASES_B(FN, 6, 64, T, __VA_ARGS__) }                                   \
+    } else {                                                                                 \
+        if (batch == 32) { LP_PIX_CASES_B(FN, 4, 32, T, __VA_ARGS__) }                       \
+        else if (batch == 128) { LP_PIX_CASES_B(FN, 4, 128, T, __VA_ARGS__) }                \
+        else { LP_PIX_CASES_B(FN, 4, 64, T, __VA_ARGS__) }                                   \
+    }                                                                                        \
+    return BAD;
 
-#define LP_BWD_DISPATCH(FN, V, B, P, ...)                                                   \
-    if (V == 6) {                                                                           \
-        if (B == 32) { if (P == 1) return FN<6, 32, 1>(__VA_ARGS__); if (P == 2) return FN<6, 32, 2>(__VA_ARGS__); return FN<6, 32, 4>(__VA_ARGS__); } \
-        if (B == 128) { if (P == 1) return FN<6, 128, 1>(__VA_ARGS__); if (P == 2) return FN<6, 128, 2>(__VA_ARGS__); return FN<6, 128, 4>(__VA_ARGS__); } \
-        if (P == 1) return FN<6, 64, 1>(__VA_ARGS__); if (P == 2) return FN<6, 64, 2>(__VA_ARGS__); return FN<6, 64, 4>(__VA_ARGS__); \
-    } else {                                                                                \
-        if (B == 32) { if (P == 1) return FN<4, 32, 1>(__VA_ARGS__); if (P == 2) return FN<4, 32, 2>(__VA_ARGS__); return FN<4, 32, 4>(__VA_ARGS__); } \
-        if (B == 128) { if (P == 1) return FN<4, 128, 1>(__VA_ARGS__); if (P == 2) return FN<4, 128, 2>(__VA_ARGS__); return FN<4, 128, 4>(__VA_ARGS__); } \
-        if (P == 1) return FN<4, 64, 1>(__VA_ARGS__); if (P == 2) return FN<4, 64, 2>(__VA_ARGS__); return FN<4, 64, 4>(__VA_ARGS__); \
-    }
-
-cudaError_t launch_blend_bwd(int V, int batch, int pix, const BlendArgs& a, cudaStream_t st) {
-    LP_BWD_DISPATCH(bwd_t, V, batch, pix, a, st)
+template <int TILE>
+cudaError_t launch_bwd_tile(int V, int batch, int pix, const BlendArgs& a, cudaStream_t st) {
+    LP_BLEND_DISPATCH_B(bwd_t, TILE, cudaErrorInvalidValue, a, st)
 }
 
-int blend_bwd_occupancy(int V, int batch, int pix) { LP_BWD_DISPATCH(bwd_occ, V, batch, pix) }
+template <int TILE>
+int occ_bwd_tile(int V, int batch, int pix) {
+    LP_BLEND_DISPATCH_B(bwd_occ, TILE, 0)
+}
+
+}  // namespace
 
 }  // namespace lp

@@ -16,14 +16,20 @@
 // (App. "Depth and Surface Reconstruction"): the same walk, stopping each
 // pixel at the first primitive that takes the cumulative opacity above 0.5
 // and writing the depth where the ray enters that primitive (0 if none).
+//
+// The kernels are templates over the tile edge; each of lp_blend_fwd_t8.cu,
+// _t16.cu and _t32.cu instantiates one edge (one translation unit each, so
+// they compile in parallel).
+#pragma once
+
 #include "lp_blend.cuh"
 
 namespace lp {
 
 namespace {
 
-template <int V, int BATCH, int PIX, int MODE>
-__global__ void __launch_bounds__(kTilePixels / PIX) k_blend_fwd(
+template <int V, int BATCH, int PIX, int MODE, int TILE>
+__global__ void __launch_bounds__(TILE * TILE / PIX) k_blend_fwd(
     const float* __restrict__ rec, const uint32_t* __restrict__ vals, const uint2* __restrict__ ranges,
     CamsParam cams, float bg0, float bg1, float bg2, float* __restrict__ image,
     uint32_t* __restrict__ last_out, float* __restrict__ tl_out, int* __restrict__ tile_counter,
@@ -32,8 +38,10 @@ __global__ void __launch_bounds__(kTilePixels / PIX) k_blend_fwd(
     constexpr bool COUNT = MODE == 1;
     constexpr bool DEPTH = MODE == 2;
     constexpr float kStop = DEPTH ? 0.5f : kStopT;
-    constexpr int NT = kTilePixels / PIX;
-    constexpr int RW = kTile / PIX;
+    constexpr int NT = TILE * TILE / PIX;
+    constexpr int RW = TILE / PIX;
+    constexpr int BH = 32 / RW;   // rows per warp
+    static_assert(NT % 32 == 0 && BH >= 1, "whole warps of whole rows");
     __shared__ Staged<V> sm[BATCH];
     __shared__ int s_tile;
     const int tid = threadIdx.x;
@@ -46,7 +54,7 @@ __global__ void __launch_bounds__(kTilePixels / PIX) k_blend_fwd(
         __syncthreads();
         const int tile = s_tile;
         if (tile >= cams.total_tiles) break;
-        const TileGeom tg = tile_geom(cams, tile);
+        const TileGeom tg = tile_geom<TILE>(cams, tile);
         const int py = tg.ty0 + ly;
         const uint2 rg = ranges[tile];
         const int n = (int)(rg.y - rg.x);
@@ -69,7 +77,7 @@ __global__ void __launch_bounds__(kTilePixels / PIX) k_blend_fwd(
             const int nb = min(BATCH, n - b0);
             for (int j = tid; j < nb; j += NT) {
                 stage_record<V>(rec, vals[rg.x + b0 + j], tg.tx0, tg.ty0, sm[j]);
-                sm[j].bands = band_mask<V, 2 * PIX>(sm[j]);
+                sm[j].bands = band_mask<V, TILE, BH>(sm[j]);
             }
             __syncthreads();
             if (__any_sync(0xffffffffu, !tdone)) {   // warp-uniform, as the exit below
@@ -96,8 +104,9 @@ __global__ void __launch_bounds__(kTilePixels / PIX) k_blend_fwd(
                             if (in && sp[i] > 0.f) {
                                 blended = true;
                                 if (COUNT) { ++n_hit; cl[i] = ce[i]; }
-                                const float tau = span_tau(p.sigma, sp[i]);
-                                const float w = T[i] * (1.f - tau);
+                                const float xs = span_x(p.sigma, sp[i]);
+                                const float tau = span_tau(xs);
+                                const float w = T[i] * span_opacity(xs, tau);
                                 c0[i] = fmaf(w, p.r, c0[i]);
                                 c1[i] = fmaf(w, p.g, c1[i]);
                                 c2[i] = fmaf(w, p.b, c2[i]);
@@ -177,49 +186,60 @@ __global__ void __launch_bounds__(kTilePixels / PIX) k_blend_fwd(
     }
 }
 
-template <int V, int BATCH, int PIX>
+template <int V, int BATCH, int PIX, int TILE>
 cudaError_t fwd_t(const BlendArgs& a, cudaStream_t st) {
-    constexpr int NT = kTilePixels / PIX;
+    constexpr int NT = TILE * TILE / PIX;
     if (a.depth)
-        k_blend_fwd<V, BATCH, PIX, 2><<<a.grid, NT, 0, st>>>(
+        k_blend_fwd<V, BATCH, PIX, 2, TILE><<<a.grid, NT, 0, st>>>(
             a.rec, a.vals, a.ranges, *a.cams, a.bg[0], a.bg[1], a.bg[2], a.image, a.last, a.tl,
             a.tile_counter, a.pair_counts, a.depth, nullptr, 0u);
     else if (a.count)
-        k_blend_fwd<V, BATCH, PIX, 1><<<a.grid, NT, 0, st>>>(
+        k_blend_fwd<V, BATCH, PIX, 1, TILE><<<a.grid, NT, 0, st>>>(
             a.rec, a.vals, a.ranges, *a.cams, a.bg[0], a.bg[1], a.bg[2], a.image, a.last, a.tl,
             a.tile_counter, a.pair_counts, nullptr, a.contrib, a.contrib_stride);
     else
-        k_blend_fwd<V, BATCH, PIX, 0><<<a.grid, NT, 0, st>>>(
+        k_blend_fwd<V, BATCH, PIX, 0, TILE><<<a.grid, NT, 0, st>>>(
             a.rec, a.vals, a.ranges, *a.cams, a.bg[0], a.bg[1], a.bg[2], a.image, a.last, a.tl,
             a.tile_counter, a.pair_counts, nullptr, a.contrib, a.contrib_stride);
     return cudaGetLastError();
 }
 
-template <int V, int BATCH, int PIX>
+template <int V, int BATCH, int PIX, int TILE>
 int fwd_occ() {
     int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_blend_fwd<V, BATCH, PIX, 0>,
-                                                  kTilePixels / PIX, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_blend_fwd<V, BATCH, PIX, 0, TILE>,
+                                                  TILE * TILE / PIX, 0);
     return nb;
 }
 
-}  // namespace
+// Dispatch over (V, BATCH, PIX) for one tile edge; a (tile, pix) pair the
+// kernels are not built for is rejected (lp_set_tuning checks it first).
+#define LP_PIX_CASES(FN, V, B, T, ...)                                                       \
+    if constexpr (tile_pix_ok(T, 1)) { if (pix == 1) return FN<V, B, 1, T>(__VA_ARGS__); }   \
+    if constexpr (tile_pix_ok(T, 2)) { if (pix == 2) return FN<V, B, 2, T>(__VA_ARGS__); }   \
+    if constexpr (tile_pix_ok(T, 4)) { if (pix == 4) return FN<V, B, 4, T>(__VA_ARGS__); }
+#define LP_BLEND_DISPATCH(FN, T, BAD, ...)                                                   \
+    if (V == 6) {                                                                            \
+        if (batch == 32) { LP_PIX_CASES(FN, 6, 32, T, __VA_ARGS__) }                         \
+        else if (batch == 128) { LP_PIX_CASES(FN, 6, 128, T, __VA_ARGS__) }                  \
+        else { LP_PIX_CASES(FN, 6, 64, T, __VA_ARGS__) }                                     \
+    } else {                                                                                 \
+        if (batch == 32) { LP_PIX_CASES(FN, 4, 32, T, __VA_ARGS__) }                         \
+        else if (batch == 128) { LP_PIX_CASES(FN, 4, 128, T, __VA_ARGS__) }                  \
+        else { LP_PIX_CASES(FN, 4, 64, T, __VA_ARGS__) }                                     \
+    }                                                                                        \
+    return BAD;
 
-#define LP_FWD_DISPATCH(FN, V, B, P, ...)                                                   \
-    if (V == 6) {                                                                           \
-        if (B == 32) { if (P == 1) return FN<6, 32, 1>(__VA_ARGS__); if (P == 2) return FN<6, 32, 2>(__VA_ARGS__); return FN<6, 32, 4>(__VA_ARGS__); } \
-        if (B == 128) { if (P == 1) return FN<6, 128, 1>(__VA_ARGS__); if (P == 2) return FN<6, 128, 2>(__VA_ARGS__); return FN<6, 128, 4>(__VA_ARGS__); } \
-        if (P == 1) return FN<6, 64, 1>(__VA_ARGS__); if (P == 2) return FN<6, 64, 2>(__VA_ARGS__); return FN<6, 64, 4>(__VA_ARGS__); \
-    } else {                                                                                \
-        if (B == 32) { if (P == 1) return FN<4, 32, 1>(__VA_ARGS__); if (P == 2) return FN<4, 32, 2>(__VA_ARGS__); return FN<4, 32, 4>(__VA_ARGS__); } \
-        if (B == 128) { if (P == 1) return FN<4, 128, 1>(__VA_ARGS__); if (P == 2) return FN<4, 128, 2>(__VA_ARGS__); return FN<4, 128, 4>(__VA_ARGS__); } \
-        if (P == 1) return FN<4, 64, 1>(__VA_ARGS__); if (P == 2) return FN<4, 64, 2>(__VA_ARGS__); return FN<4, 64, 4>(__VA_ARGS__); \
-    }
-
-cudaError_t launch_blend_fwd(int V, int batch, int pix, const BlendArgs& a, cudaStream_t st) {
-    LP_FWD_DISPATCH(fwd_t, V, batch, pix, a, st)
+template <int TILE>
+cudaError_t launch_fwd_tile(int V, int batch, int pix, const BlendArgs& a, cudaStream_t st) {
+    LP_BLEND_DISPATCH(fwd_t, TILE, cudaErrorInvalidValue, a, st)
 }
 
-int blend_fwd_occupancy(int V, int batch, int pix) { LP_FWD_DISPATCH(fwd_occ, V, batch, pix) }
+template <int TILE>
+int occ_fwd_tile(int V, int batch, int pix) {
+    LP_BLEND_DISPATCH(fwd_occ, TILE, 0)
+}
+
+}  // namespace
 
 }  // namespace lp

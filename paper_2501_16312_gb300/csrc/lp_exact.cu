@@ -35,8 +35,10 @@ namespace lp {
 namespace {
 
 constexpr int kBatchX = 32;
-constexpr int kPixX = 4;
-constexpr int kThreadsX = kTilePixels / kPixX;
+// pixels per thread and threads per block of the exact-span blends for a
+// TILE x TILE tile: strips of 4 pixels, of 2 on 8x8 tiles (one whole warp)
+template <int TILE> constexpr int pix_x() { return TILE == 8 ? 2 : 4; }
+template <int TILE> constexpr int threads_x() { return TILE * TILE / pix_x<TILE>(); }
 
 template <int V> struct RecX {
     static constexpr int F = Kind<V>::F;
@@ -315,14 +317,14 @@ __device__ __forceinline__ float ray_norm(const CamDev& cm, int px, int py) {
 }
 
 // MODE 0: image; 1: also the pair counters; 2: depth pass.
-template <int V, int MODE>
-__global__ void __launch_bounds__(kThreadsX) k_blend_fwd_x(
+template <int V, int MODE, int TILE>
+__global__ void __launch_bounds__(threads_x<TILE>()) k_blend_fwd_x(
     const float* __restrict__ rec, const uint32_t* __restrict__ vals, const uint2* __restrict__ ranges,
     CamsParam cams, float bg0, float bg1, float bg2, float* __restrict__ image,
     uint32_t* __restrict__ last_out, float* __restrict__ tl_out, int* __restrict__ tile_counter,
     unsigned long long* __restrict__ pair_counts, float* __restrict__ depth_out,
     uint32_t* __restrict__ contrib, uint32_t cstride) {
-    constexpr int PIX = kPixX, NT = kThreadsX, RW = kTile / PIX, BATCH = kBatchX;
+    constexpr int PIX = pix_x<TILE>(), NT = threads_x<TILE>(), RW = TILE / PIX, BATCH = kBatchX;
     constexpr bool COUNT = MODE == 1, DEPTH = MODE == 2;
     constexpr float kStop = DEPTH ? 0.5f : kStopT;
     __shared__ StagedX<V> sm[BATCH];
@@ -337,7 +339,7 @@ __global__ void __launch_bounds__(kThreadsX) k_blend_fwd_x(
         __syncthreads();
         const int tile = s_tile;
         if (tile >= cams.total_tiles) break;
-        const TileGeom tg = tile_geom(cams, tile);
+        const TileGeom tg = tile_geom<TILE>(cams, tile);
         const CamDev& cm = cams.cam[camera_of_tile(cams, tile)];
         const int py = tg.ty0 + ly;
         const uint2 rg = ranges[tile];
@@ -381,8 +383,9 @@ __global__ void __launch_bounds__(kThreadsX) k_blend_fwd_x(
                         if (in && sp[i] > 0.f) {
                             blended = true;
                             if (COUNT) { ++n_hit; cl[i] = ce[i]; }
-                            const float tau = span_tau(p.sigma, sp[i]);
-                            const float w = T[i] * (1.f - tau);
+                            const float xs = span_x(p.sigma, sp[i]);
+                            const float tau = span_tau(xs);
+                            const float w = T[i] * span_opacity(xs, tau);
                             c0[i] = fmaf(w, p.r, c0[i]);
                             c1[i] = fmaf(w, p.g, c1[i]);
                             c2[i] = fmaf(w, p.b, c2[i]);
@@ -457,15 +460,15 @@ __global__ void __launch_bounds__(kThreadsX) k_blend_fwd_x(
 // s = (delta_out - delta_in) |d| of a face f with delta = N / D, N = 1 - c_z L,
 // D = L + D0, L = p X + q Y + L0 (X, Y the pixel offsets from the anchor) has
 //   d delta/dL = -(c_z + delta)/D,  d delta/dD0 = -delta/D,  d delta/dc_z = -L/D.
-template <int V>
-__global__ void __launch_bounds__(kThreadsX) k_blend_bwd_x(
+template <int V, int TILE>
+__global__ void __launch_bounds__(threads_x<TILE>()) k_blend_bwd_x(
     const float* __restrict__ rec, const uint32_t* __restrict__ vals, const uint2* __restrict__ ranges,
     CamsParam cams, float bg0, float bg1, float bg2, const float* __restrict__ dimage,
     const uint32_t* __restrict__ last_in, const float* __restrict__ tl_in, float* __restrict__ acc,
     int* __restrict__ tile_counter, const uint32_t* __restrict__ contrib, uint32_t cstride) {
     constexpr int F = Kind<V>::F;
     constexpr int ACC = AccX<V>::kFloats;
-    constexpr int PIX = kPixX, NT = kThreadsX, RW = kTile / PIX, BATCH = kBatchX;
+    constexpr int PIX = pix_x<TILE>(), NT = threads_x<TILE>(), RW = TILE / PIX, BATCH = kBatchX;
     __shared__ StagedX<V> sm[BATCH];
     __shared__ int s_tile;
     __shared__ int s_max;
@@ -480,7 +483,7 @@ __global__ void __launch_bounds__(kThreadsX) k_blend_bwd_x(
         __syncthreads();
         const int tile = s_tile;
         if (tile >= cams.total_tiles) break;
-        const TileGeom tg = tile_geom(cams, tile);
+        const TileGeom tg = tile_geom<TILE>(cams, tile);
         const CamDev& cm = cams.cam[camera_of_tile(cams, tile)];
         const int py = tg.ty0 + ly;
         const uint2 rg = ranges[tile];
@@ -548,8 +551,9 @@ __global__ void __launch_bounds__(kThreadsX) k_blend_bwd_x(
 #pragma unroll
                     for (int m = 0; m < 4; ++m) ge[i][m] = gx[i][m] = 0.f;
                     if (!c[i]) continue;
-                    const float tau = span_tau(p.sigma, sp[i]);
-                    const float o = 1.f - tau;
+                    const float xs = span_x(p.sigma, sp[i]);
+                    const float tau = span_tau(xs);
+                    const float o = span_opacity(xs, tau);
                     const float Ti = first[i] ? Tcur[i] : __fdividef(Tcur[i], tau);
                     first[i] = false;
                     Tcur[i] = Ti;
@@ -870,12 +874,14 @@ cudaError_t launch_chain_x(int V, int deg, const PrimsDev& P, const CamsParam& c
 #undef CALL
 }
 
-cudaError_t launch_blend_fwd_x(int V, const BlendArgs& a, cudaStream_t st) {
+namespace {
+
+template <int TILE>
+cudaError_t fwd_x_t(int V, const BlendArgs& a, cudaStream_t st) {
 #define FWD(v, m)                                                                                        \
-    k_blend_fwd_x<v, m><<<a.grid, kThreadsX, 0, st>>>(a.rec, a.vals, a.ranges, *a.cams, a.bg[0], a.bg[1], \
-                                                      a.bg[2], a.image, a.last, a.tl, a.tile_counter,    \
-                                                      a.pair_counts, a.depth, m == 2 ? nullptr : a.contrib, \
-                                                      a.contrib_stride)
+    k_blend_fwd_x<v, m, TILE><<<a.grid, threads_x<TILE>(), 0, st>>>(                                    \
+        a.rec, a.vals, a.ranges, *a.cams, a.bg[0], a.bg[1], a.bg[2], a.image, a.last, a.tl, a.tile_counter, \
+        a.pair_counts, a.depth, m == 2 ? nullptr : a.contrib, a.contrib_stride)
     const int m = a.depth ? 2 : (a.count ? 1 : 0);
     if (V == 6) {
         if (m == 2) FWD(6, 2); else if (m == 1) FWD(6, 1); else FWD(6, 0);
@@ -886,27 +892,45 @@ cudaError_t launch_blend_fwd_x(int V, const BlendArgs& a, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_blend_bwd_x(int V, const BlendArgs& a, cudaStream_t st) {
+template <int TILE>
+cudaError_t bwd_x_t(int V, const BlendArgs& a, cudaStream_t st) {
     if (V == 6)
-        k_blend_bwd_x<6><<<a.grid, kThreadsX, 0, st>>>(a.rec, a.vals, a.ranges, *a.cams, a.bg[0], a.bg[1],
-                                                        a.bg[2], a.dimage, a.last, a.tl, a.acc, a.tile_counter,
-                                                        a.contrib, a.contrib_stride);
+        k_blend_bwd_x<6, TILE><<<a.grid, threads_x<TILE>(), 0, st>>>(
+            a.rec, a.vals, a.ranges, *a.cams, a.bg[0], a.bg[1], a.bg[2], a.dimage, a.last, a.tl, a.acc,
+            a.tile_counter, a.contrib, a.contrib_stride);
     else
-        k_blend_bwd_x<4><<<a.grid, kThreadsX, 0, st>>>(a.rec, a.vals, a.ranges, *a.cams, a.bg[0], a.bg[1],
-                                                        a.bg[2], a.dimage, a.last, a.tl, a.acc, a.tile_counter,
-                                                        a.contrib, a.contrib_stride);
+        k_blend_bwd_x<4, TILE><<<a.grid, threads_x<TILE>(), 0, st>>>(
+            a.rec, a.vals, a.ranges, *a.cams, a.bg[0], a.bg[1], a.bg[2], a.dimage, a.last, a.tl, a.acc,
+            a.tile_counter, a.contrib, a.contrib_stride);
     return cudaGetLastError();
 }
 
-int blend_x_occupancy(int V, bool fwd) {
+template <int TILE>
+int occ_x_t(int V, bool fwd) {
     int nb = 0;
     if (V == 6)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fwd ? (const void*)k_blend_fwd_x<6, 0>
-                                                               : (const void*)k_blend_bwd_x<6>, kThreadsX, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fwd ? (const void*)k_blend_fwd_x<6, 0, TILE>
+                                                               : (const void*)k_blend_bwd_x<6, TILE>,
+                                                      threads_x<TILE>(), 0);
     else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fwd ? (const void*)k_blend_fwd_x<4, 0>
-                                                               : (const void*)k_blend_bwd_x<4>, kThreadsX, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fwd ? (const void*)k_blend_fwd_x<4, 0, TILE>
+                                                               : (const void*)k_blend_bwd_x<4, TILE>,
+                                                      threads_x<TILE>(), 0);
     return nb;
+}
+
+}  // namespace
+
+cudaError_t launch_blend_fwd_x(int tile, int V, const BlendArgs& a, cudaStream_t st) {
+    return tile == 8 ? fwd_x_t<8>(V, a, st) : tile == 32 ? fwd_x_t<32>(V, a, st) : fwd_x_t<16>(V, a, st);
+}
+
+cudaError_t launch_blend_bwd_x(int tile, int V, const BlendArgs& a, cudaStream_t st) {
+    return tile == 8 ? bwd_x_t<8>(V, a, st) : tile == 32 ? bwd_x_t<32>(V, a, st) : bwd_x_t<16>(V, a, st);
+}
+
+int blend_x_occupancy(int tile, int V, bool fwd) {
+    return tile == 8 ? occ_x_t<8>(V, fwd) : tile == 32 ? occ_x_t<32>(V, fwd) : occ_x_t<16>(V, fwd);
 }
 
 }  // namespace lp

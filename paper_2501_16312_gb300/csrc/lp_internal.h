@@ -7,6 +7,13 @@
 
 namespace lp {
 
+// (tile edge, pixels per thread) pairs the ray-space blends are built for: at
+// least one full warp per tile, at most 512 threads per block.
+constexpr bool tile_pix_ok(int tile, int pix) {
+    return (tile == 8 && (pix == 1 || pix == 2)) || (tile == 16 && (pix == 1 || pix == 2 || pix == 4)) ||
+           (tile == 32 && (pix == 2 || pix == 4));
+}
+
 struct CamsParam;
 struct PrimsDev;
 
@@ -32,16 +39,18 @@ cudaError_t launch_emit(const uint32_t* counts, const uint32_t* offsets, const i
 
 int sort_blocks(long long bound);
 size_t sort_hist_elems(long long bound);
+// radix_bits: digit width, 4, 6, 8 or 11 (cudaErrorInvalidValue otherwise);
+// hist holds sort_hist_elems(bound) words, enough for any width.
 cudaError_t launch_radix_sort(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1,
-                              const uint32_t* n_dev, long long bound, int key_bits, uint32_t* hist,
-                              uint32_t* scan_tmp, int* passes_out, cudaStream_t st);
+                              const uint32_t* n_dev, long long bound, int key_bits, int radix_bits,
+                              uint32_t* hist, uint32_t* scan_tmp, int* passes_out, cudaStream_t st);
 
 cudaError_t launch_ranges(const uint64_t* keys, const uint32_t* n_dev, long long bound,
                           const int* status, uint2* ranges, int sms, cudaStream_t st);
 
 // two-stage sort: records by depth, then entries by 32-bit tile id
 cudaError_t launch_radix_sort32(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1,
-                                const uint32_t* n_dev, long long bound, int key_bits,
+                                const uint32_t* n_dev, long long bound, int key_bits, int radix_bits,
                                 uint32_t* hist, uint32_t* scan_tmp, int* passes_out, cudaStream_t st);
 cudaError_t launch_depth_keys(const uint32_t* counts, const uint32_t* zbits, long long n, uint32_t* keys,
                               uint32_t* vals, cudaStream_t st);
@@ -77,10 +86,38 @@ struct BlendArgs {
                            // (written by the forward when non-null, read by the backward)
 };
 
-cudaError_t launch_blend_fwd(int V, int batch, int pix, const BlendArgs& a, cudaStream_t st);
-cudaError_t launch_blend_bwd(int V, int batch, int pix, const BlendArgs& a, cudaStream_t st);
-int blend_fwd_occupancy(int V, int batch, int pix);   // resident blocks per SM
-int blend_bwd_occupancy(int V, int batch, int pix);
+// Blends for one tile edge each (lp_blend_{fwd,bwd}_t{8,16,32}.cu).
+cudaError_t launch_blend_fwd_t8(int V, int batch, int pix, const BlendArgs& a, cudaStream_t st);
+cudaError_t launch_blend_fwd_t16(int V, int batch, int pix, const BlendArgs& a, cudaStream_t st);
+cudaError_t launch_blend_fwd_t32(int V, int batch, int pix, const BlendArgs& a, cudaStream_t st);
+cudaError_t launch_blend_bwd_t8(int V, int batch, int pix, const BlendArgs& a, cudaStream_t st);
+cudaError_t launch_blend_bwd_t16(int V, int batch, int pix, const BlendArgs& a, cudaStream_t st);
+cudaError_t launch_blend_bwd_t32(int V, int batch, int pix, const BlendArgs& a, cudaStream_t st);
+int blend_fwd_occupancy_t8(int V, int batch, int pix);   // resident blocks per SM
+int blend_fwd_occupancy_t16(int V, int batch, int pix);
+int blend_fwd_occupancy_t32(int V, int batch, int pix);
+int blend_bwd_occupancy_t8(int V, int batch, int pix);
+int blend_bwd_occupancy_t16(int V, int batch, int pix);
+int blend_bwd_occupancy_t32(int V, int batch, int pix);
+
+inline cudaError_t launch_blend_fwd(int tile, int V, int batch, int pix, const BlendArgs& a, cudaStream_t st) {
+    return tile == 8 ? launch_blend_fwd_t8(V, batch, pix, a, st)
+         : tile == 32 ? launch_blend_fwd_t32(V, batch, pix, a, st) : launch_blend_fwd_t16(V, batch, pix, a, st);
+}
+inline cudaError_t launch_blend_bwd(int tile, int V, int batch, int pix, const BlendArgs& a, cudaStream_t st) {
+    return tile == 8 ? launch_blend_bwd_t8(V, batch, pix, a, st)
+         : tile == 32 ? launch_blend_bwd_t32(V, batch, pix, a, st) : launch_blend_bwd_t16(V, batch, pix, a, st);
+}
+inline int blend_fwd_occupancy(int tile, int V, int batch, int pix) {
+    return tile == 8 ? blend_fwd_occupancy_t8(V, batch, pix)
+         : tile == 32 ? blend_fwd_occupancy_t32(V, batch, pix) : blend_fwd_occupancy_t16(V, batch, pix);
+}
+inline int blend_bwd_occupancy(int tile, int V, int batch, int pix) {
+    return tile == 8 ? blend_bwd_occupancy_t8(V, batch, pix)
+         : tile == 32 ? blend_bwd_occupancy_t32(V, batch, pix) : blend_bwd_occupancy_t16(V, batch, pix);
+}
+// warps per tile of the ray-space blends (one contributor-mask row each)
+inline int blend_warps(int tile, int pix) { return tile * tile / pix / 32; }
 
 // exact spans (no ray-space approximation): own records, accumulators and kernels
 int rec_floats_x(int V);
@@ -90,8 +127,11 @@ cudaError_t launch_preprocess_x(int V, int deg, const PrimsDev& P, const CamsPar
 cudaError_t launch_chain_x(int V, int deg, const PrimsDev& P, const CamsParam& cams, const float* rec,
                            const uint32_t* counts, const float* acc, float* dc, float* dv, float* dop, float* dsh,
                            int accumulate, cudaStream_t st);
-cudaError_t launch_blend_fwd_x(int V, const BlendArgs& a, cudaStream_t st);
-cudaError_t launch_blend_bwd_x(int V, const BlendArgs& a, cudaStream_t st);
-int blend_x_occupancy(int V, bool fwd);
+cudaError_t launch_blend_fwd_x(int tile, int V, const BlendArgs& a, cudaStream_t st);
+cudaError_t launch_blend_bwd_x(int tile, int V, const BlendArgs& a, cudaStream_t st);
+int blend_x_occupancy(int tile, int V, bool fwd);
+// pixels per thread and warps per tile of the exact-span blends
+inline int blend_x_pix(int tile) { return tile == 8 ? 2 : 4; }
+inline int blend_x_warps(int tile) { return tile * tile / blend_x_pix(tile) / 32; }
 
 }  // namespace lp

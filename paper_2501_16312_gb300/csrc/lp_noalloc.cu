@@ -192,7 +192,7 @@ extern "C" lp_status lp_render_forward_noalloc(const lp_prims* prims, const lp_c
     NA_CUDA(lp::launch_emit(counts, offsets, trect, zbits, records, d_E, E, part, keys0, vals0, kMaxEntries,
                             d_status, st));
     int passes = 0;
-    NA_CUDA(lp::launch_radix_sort(keys0, vals0, keys1, vals1, d_E, E, 32 + bits_for(tiles), hist, scan_tmp,
+    NA_CUDA(lp::launch_radix_sort(keys0, vals0, keys1, vals1, d_E, E, 32 + bits_for(tiles), 8, hist, scan_tmp,
                                   &passes, st));
     const bool in1 = (passes & 1) != 0;
     NA_CUDA(cudaMemsetAsync(ranges, 0, (size_t)tiles * sizeof(uint2), st));
@@ -201,7 +201,7 @@ extern "C" lp_status lp_render_forward_noalloc(const lp_prims* prims, const lp_c
     NA_CUDA(lp::launch_ranges(in1 ? keys1 : keys0, d_E, E, d_status, ranges, sms, st));
     lp::BlendArgs a{};
     const int pix = 4, batch = 64;
-    int bps = lp::blend_fwd_occupancy(V, batch, pix);
+    int bps = lp::blend_fwd_occupancy(tile, V, batch, pix);
     if (bps <= 0) bps = 1;
     a.grid = (int)(tiles < (long long)sms * bps ? tiles : (long long)sms * bps);
     a.rec = rec;
@@ -216,7 +216,7 @@ extern "C" lp_status lp_render_forward_noalloc(const lp_prims* prims, const lp_c
     a.pair_counts = d_pairs;
     a.count = false;
     NA_CUDA(cudaMemsetAsync(d_tile_counter, 0, sizeof(int), st));
-    NA_CUDA(lp::launch_blend_fwd(V, batch, pix, a, st));
+    NA_CUDA(lp::launch_blend_fwd(tile, V, batch, pix, a, st));
     // the status the emission and range kernels latch on the device
     int status = 0;
     NA_CUDA(cudaMemcpyAsync(&status, d_status, sizeof(int), cudaMemcpyDeviceToHost, st));

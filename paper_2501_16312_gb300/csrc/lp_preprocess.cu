@@ -306,43 +306,48 @@ k_chain(PrimsDev P, CamsParam cams, const float* __restrict__ rec, const uint32_
             // accumulators hold sums over g (px - X0, py - Y0, 1); the pixel's
             // offset from the projected centre is (px - X0 - fxo, py - Y0 - fyo)
             const float Ge = A[3 * s + 2];
-            const float Ga = A[3 * s] - g.fxo * Ge, Gb = A[3 * s + 1] - g.fyo * Ge;
+            const float Ga = __fmaf_rn(-g.fxo, Ge, A[3 * s]), Gb = __fmaf_rn(-g.fyo, Ge, A[3 * s + 1]);
             if (Ga == 0.f && Gb == 0.f && Ge == 0.f) continue;
-            int i0, i1, i2;
-            face_vertices<V>(f, i0, i1, i2);
+            int iv[3];
+            face_vertices<V>(f, iv[0], iv[1], iv[2]);
             float n[3];
-            face_normal(q[i0], q[i1], q[i2], n);
+            face_normal(q[iv[0]], q[iv[1]], q[iv[2]], n);
             if (plane_degenerate(n)) continue;
             const float inz = 1.f / n[2];
             const float a = -n[0] * inz, b = -n[1] * inz;
-            const float e = (n[0] * q[i0][0] + n[1] * q[i0][1] + n[2] * q[i0][2]) * inz;
-            // the pixel offset from the projected centre is (x - x_c, y - y_c)
+            // moving the projected centre moves every plane with it
             gxc -= a * Ge;
             gyc -= b * Ge;
-            // a = -n_x/n_z, b = -n_y/n_z, e = (n . q0)/n_z
-            float gn[3];
-            gn[0] = (Ge * q[i0][0] - Ga) * inz;
-            gn[1] = (Ge * q[i0][1] - Gb) * inz;
-            gn[2] = (Ge * (q[i0][2] - e) - Ga * a - Gb * b) * inz;
-            const float e1[3] = {q[i1][0] - q[i0][0], q[i1][1] - q[i0][1], q[i1][2] - q[i0][2]};
-            const float e2[3] = {q[i2][0] - q[i0][0], q[i2][1] - q[i0][1], q[i2][2] - q[i0][2]};
-            // n = e1 x e2: dL/de1 = e2 x gn, dL/de2 = gn x e1
-            const float g1[3] = {e2[1] * gn[2] - e2[2] * gn[1], e2[2] * gn[0] - e2[0] * gn[2],
-                                 e2[0] * gn[1] - e2[1] * gn[0]};
-            const float g2[3] = {gn[1] * e1[2] - gn[2] * e1[1], gn[2] * e1[0] - gn[0] * e1[2],
-                                 gn[0] * e1[1] - gn[1] * e1[0]};
+            // The plane's depth at pixel p is sum_k lambda_k(p) q_k.z with
+            // lambda the face's 2D barycentric coordinates, and moving vertex k
+            // by (dx, dy) changes it by -lambda_k (a dx + b dy).  So with
+            // G_k = sum_p g lambda_k(p), dL/dq_k = G_k (-a, -b, 1).  lambda_k(p)
+            // = cross(q_l - q_j, p - q_j) / n_z for the next two vertices j, l
+            // in the face's order, hence G_k = cross(q_l - q_j, (Ga, Gb) -
+            // q_j Ge) / n_z: no term is multiplied by the (possibly large)
+            // slopes before the cross product, which keeps nearly edge-on
+            // faces as accurate as the others.
 #pragma unroll
-            for (int m = 0; m < 3; ++m) {
-                gq[i1][m] += g1[m];
-                gq[i2][m] += g2[m];
-                gq[i0][m] += Ge * n[m] * inz - g1[m] - g2[m];
+            for (int kk = 0; kk < 3; ++kk) {
+                const float* qj = q[iv[(kk + 1) % 3]];
+                const float* ql = q[iv[(kk + 2) % 3]];
+                const float ex = ql[0] - qj[0], ey = ql[1] - qj[1];
+                const float mx = __fmaf_rn(-qj[0], Ge, Ga), my = __fmaf_rn(-qj[1], Ge, Gb);
+                const float Gk = (ex * my - ey * mx) * inz;
+                float* gk = gq[iv[kk]];
+                gk[0] = fmaf(-a, Gk, gk[0]);
+                gk[1] = fmaf(-b, Gk, gk[1]);
+                gk[2] += Gk;
             }
         }
 
-        // q_k = J (t_k - tc); x_c = phi_x(tc), y_c = phi_y(tc).  gtc collects
-        // the terms of tc as the linearisation anchor, gsum the vertex terms
-        // (which enter tc with the opposite sign).
-        float gsum[3] = {0.f, 0.f, 0.f};
+        // q_k = J (t_k - tc); x_c = phi_x(tc), y_c = phi_y(tc).  The planes
+        // depend on tc through the projected centre plus q_k, whose sum
+        // phi(tc) + J (t_k - tc) has derivative dJ/dtc (t_k - tc) in tc: the
+        // anchor's J and the vertices' -J cancel exactly and are left out of
+        // the centre gradient (their binary32 residue would be all error).
+        // The densification statistic, a translation of the whole primitive,
+        // takes the anchor terms alone.
         float gJ00 = 0.f, gJ02 = 0.f, gJ11 = 0.f, gJ12 = 0.f, gJ2[3] = {0.f, 0.f, 0.f};
 #pragma unroll
         for (int k = 0; k < V; ++k) {
@@ -356,7 +361,6 @@ k_chain(PrimsDev P, CamsParam cams, const float* __restrict__ rec, const uint32_
             gJ2[0] += gq[k][2] * d[k][0];
             gJ2[1] += gq[k][2] * d[k][1];
             gJ2[2] += gq[k][2] * d[k][2];
-            gsum[0] += gd0; gsum[1] += gd1; gsum[2] += gd2;
             // world vertex: t = R v + T
 #pragma unroll
             for (int a = 0; a < 3; ++a)
@@ -364,27 +368,29 @@ k_chain(PrimsDev P, CamsParam cams, const float* __restrict__ rec, const uint32_
         }
         const float tx = g.tc[0], ty = g.tc[1], tz = g.tc[2];
         const float itz = 1.f / tz, itz2 = itz * itz;
-        // d phi_xy / d tc = J rows 0, 1
+        // d phi_xy / d tc = J rows 0, 1 (the anchor; statistic only)
         gtc[0] += g.j00 * gxc;
         gtc[1] += g.j11 * gyc;
         gtc[2] += g.j02 * gxc + g.j12 * gyc;
         // d J / d tc
-        gtc[2] += gJ00 * (-cm.fx * itz2);
-        gtc[0] += gJ02 * (-cm.fx * itz2);
-        gtc[2] += gJ02 * (2.f * cm.fx * tx * itz2 * itz);
-        gtc[2] += gJ11 * (-cm.fy * itz2);
-        gtc[1] += gJ12 * (-cm.fy * itz2);
-        gtc[2] += gJ12 * (2.f * cm.fy * ty * itz2 * itz);
+        float gjt[3] = {0.f, 0.f, 0.f};
+        gjt[2] += gJ00 * (-cm.fx * itz2);
+        gjt[0] += gJ02 * (-cm.fx * itz2);
+        gjt[2] += gJ02 * (2.f * cm.fx * tx * itz2 * itz);
+        gjt[2] += gJ11 * (-cm.fy * itz2);
+        gjt[1] += gJ12 * (-cm.fy * itz2);
+        gjt[2] += gJ12 * (2.f * cm.fy * ty * itz2 * itz);
         {
             const float il = 1.f / g.len;
             const float dot = gJ2[0] * g.j2[0] + gJ2[1] * g.j2[1] + gJ2[2] * g.j2[2];
 #pragma unroll
-            for (int a = 0; a < 3; ++a) gtc[a] += (gJ2[a] - g.j2[a] * dot) * il;
+            for (int a = 0; a < 3; ++a) gjt[a] += (gJ2[a] - g.j2[a] * dot) * il;
         }
 #pragma unroll
+        for (int a = 0; a < 3; ++a) gtc[a] += gjt[a];
+#pragma unroll
         for (int a = 0; a < 3; ++a)
-            gc[a] += cm.R[a] * (gtc[0] - gsum[0]) + cm.R[3 + a] * (gtc[1] - gsum[1]) +
-                     cm.R[6 + a] * (gtc[2] - gsum[2]);
+            gc[a] += cm.R[a] * gjt[0] + cm.R[3 + a] * gjt[1] + cm.R[6 + a] * gjt[2];
         }
 
         if constexpr (PART != 0) {

@@ -221,27 +221,30 @@ __global__ void __launch_bounds__(kEmitBlock) k_emit_lb(const uint32_t* __restri
 }
 
 // ---------------------------------------------------------- LSD radix sort
-// Digit width 8.  A block owns a contiguous chunk of kSortChunk items; warp w
-// of the block owns the w-th contiguous sub-chunk, which keeps the pass
-// stable: ranks follow (block, warp, round, lane) = input order.
+// Digit width RB = 4, 6, 8 or 11 bits (a tuning choice).  A block owns a
+// contiguous chunk of kSortChunk items; warp w of the block owns the w-th
+// contiguous sub-chunk, which keeps the pass stable: ranks follow (block,
+// warp, round, lane) = input order.
 constexpr int kSortThreads = 256;
 constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kSortPerWarp = 512;
 constexpr int kSortChunk = kSortWarps * kSortPerWarp;   // 4096
-constexpr int kRadix = 256;
 constexpr int kScatterIPT = kSortPerWarp / 32;   // items per lane
+constexpr int kRadixMaxBits = 11;
 
 // Digit counts of one block's chunk: each warp counts its sub-chunk into its
-// own shared histogram (less contention than one histogram per block).
-template <typename K>
+// own shared histogram (less contention than one histogram per block); with
+// 11-bit digits the block shares one histogram (the bins rarely collide).
+template <typename K, int RB>
 __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const K* __restrict__ keys,
                                                              const uint32_t* __restrict__ n_dev,
                                                              long long bound, int shift, int nblocks,
                                                              uint32_t* __restrict__ hist) {
-    __shared__ uint32_t h[kSortWarps][kRadix];
+    constexpr int R = 1 << RB;
+    constexpr int NH = RB > 8 ? 1 : kSortWarps;
+    __shared__ uint32_t h[NH][R];
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-#pragma unroll
-    for (int ww = 0; ww < kSortWarps; ++ww) h[ww][tid] = 0;
+    for (int d = tid; d < NH * R; d += kSortThreads) (&h[0][0])[d] = 0;
     __syncthreads();
     const long long n = n_dev ? min((long long)*n_dev, bound) : bound;
     const long long wbase = (long long)blockIdx.x * kSortChunk + (long long)w * kSortPerWarp;
@@ -249,25 +252,28 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const K* __restrict
 #pragma unroll
     for (int r = 0; r < kScatterIPT; ++r) {
         const long long q = wbase + r * 32 + lane;
-        dig[r] = q < n ? ((uint32_t)(keys[q] >> shift) & (kRadix - 1)) : (uint32_t)kRadix;
+        dig[r] = q < n ? ((uint32_t)(keys[q] >> shift) & (R - 1)) : (uint32_t)R;
     }
 #pragma unroll
     for (int r = 0; r < kScatterIPT; ++r)
-        if (dig[r] < kRadix) atomicAdd(&h[w][dig[r]], 1u);
+        if (dig[r] < R) atomicAdd(&h[NH > 1 ? w : 0][dig[r]], 1u);
     __syncthreads();
-    uint32_t t = 0;
+    for (int d = tid; d < R; d += kSortThreads) {
+        uint32_t t = 0;
 #pragma unroll
-    for (int ww = 0; ww < kSortWarps; ++ww) t += h[ww][tid];
-    hist[(size_t)tid * nblocks + blockIdx.x] = t;
+        for (int ww = 0; ww < NH; ++ww) t += h[ww][d];
+        hist[(size_t)d * nblocks + blockIdx.x] = t;
+    }
 }
 
-// Lanes of the warp whose digit equals this lane's (digits < 512): one ballot
-// per digit bit.  Measured faster than __match_any_sync on sm_103 when the
-// kernel streams from DRAM.
+// Lanes of the warp whose digit equals this lane's (digits < 2^(RB+1); the
+// value 2^RB marks "no item"): one ballot per digit bit.  Measured faster than
+// __match_any_sync on sm_103 when the kernel streams from DRAM.
+template <int RB>
 __device__ __forceinline__ unsigned digit_peers(uint32_t d) {
     unsigned m = 0xffffffffu;
 #pragma unroll
-    for (int b = 0; b < 9; ++b) {
+    for (int b = 0; b <= RB; ++b) {
         const unsigned bit = (d >> b) & 1u;
         const unsigned bb = __ballot_sync(0xffffffffu, bit);
         m &= bit ? bb : ~bb;
@@ -282,64 +288,78 @@ __device__ __forceinline__ unsigned digit_peers(uint32_t d) {
 // and the block writes them out in index order: consecutive threads then write
 // consecutive addresses of each digit's run.  Keys and values are read once.
 
-template <typename K>
+template <typename K, int RB>
 constexpr size_t scatter_smem_bytes() {
-    return (size_t)kSortChunk * (sizeof(K) + sizeof(uint32_t)) + (size_t)kSortWarps * kRadix * 4 + kRadix * 4;
+    return (size_t)kSortChunk * (sizeof(K) + sizeof(uint32_t)) + (size_t)kSortWarps * (1 << RB) * 4 +
+           (size_t)(1 << RB) * 4;
 }
 
-template <typename K>
+template <typename K, int RB>
 __global__ void __launch_bounds__(kSortThreads, sizeof(K) == 4 ? 4 : 3) k_radix_scatter(
     const K* __restrict__ kin, const uint32_t* __restrict__ vin,
     K* __restrict__ kout, uint32_t* __restrict__ vout, const uint32_t* __restrict__ n_dev,
     long long bound, int shift, int nblocks, const uint32_t* __restrict__ offs) {
+    constexpr int R = 1 << RB;
+    constexpr uint32_t DMASK = (2u << RB) - 1u;        // digit field of a packed item (sentinel included)
+    constexpr int DPT = R > kSortThreads ? R / kSortThreads : 1;   // digits per thread in the block scan
     extern __shared__ __align__(16) unsigned char smem[];
     K* skeys = reinterpret_cast<K*>(smem);
     uint32_t* svals = reinterpret_cast<uint32_t*>(smem + sizeof(K) * kSortChunk);
-    uint32_t* wcnt = svals + kSortChunk;            // [kSortWarps][kRadix]
-    uint32_t* gbase = wcnt + kSortWarps * kRadix;   // [kRadix]
+    uint32_t* wcnt = svals + kSortChunk;       // [kSortWarps][R]
+    uint32_t* gbase = wcnt + kSortWarps * R;   // [R]
     __shared__ uint32_t wsum[kSortWarps];
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const long long n = n_dev ? min((long long)*n_dev, bound) : bound;
     const long long bbase = (long long)blockIdx.x * kSortChunk;
     if (bbase >= n) return;   // uniform over the block
-    for (int d = lane; d < kRadix; d += 32) wcnt[w * kRadix + d] = 0;
+    for (int d = lane; d < R; d += 32) wcnt[w * R + d] = 0;
     __syncwarp();
 
     const long long wbase = bbase + (long long)w * kSortPerWarp;
     K key[kScatterIPT];
-    uint32_t pk[kScatterIPT];   // pk = digit | warp-local rank << 9
+    uint32_t pk[kScatterIPT];   // pk = digit | warp-local rank << (RB + 1)
 #pragma unroll
     for (int r = 0; r < kScatterIPT; ++r) {
         const long long q = wbase + r * 32 + lane;
         const bool ok = q < n;
         key[r] = ok ? kin[q] : K(0);
-        pk[r] = ok ? ((uint32_t)(key[r] >> shift) & (kRadix - 1)) : (uint32_t)kRadix;   // kRadix: no item
+        pk[r] = ok ? ((uint32_t)(key[r] >> shift) & (R - 1)) : (uint32_t)R;   // R: no item
     }
     const unsigned lt = (1u << lane) - 1u;
 #pragma unroll
     for (int r = 0; r < kScatterIPT; ++r) {
         const uint32_t d = pk[r];
-        const unsigned peers = digit_peers(d);
+        const unsigned peers = digit_peers<RB>(d);
         const uint32_t rank = __popc(peers & lt);
         uint32_t base = 0;
-        if (d < kRadix) base = wcnt[w * kRadix + d];
+        if (d < R) base = wcnt[w * R + d];
         __syncwarp();
-        if (d < kRadix && rank == 0) wcnt[w * kRadix + d] = base + __popc(peers);
+        if (d < R && rank == 0) wcnt[w * R + d] = base + __popc(peers);
         __syncwarp();
-        pk[r] = d | ((base + rank) << 9);
+        pk[r] = d | ((base + rank) << (RB + 1));
     }
     __syncthreads();
 
-    // thread d: starts of (warp, d) within digit d, then the block-local start of d
-    const int d = tid;   // kSortThreads == kRadix
-    uint32_t tot = 0;
+    // thread t: digits [t DPT, t DPT + DPT): starts of (warp, d) within digit
+    // d, the digits' totals, then the block-local start of each digit
+    uint32_t tot[DPT];
+    uint32_t tsum = 0;
 #pragma unroll
-    for (int ww = 0; ww < kSortWarps; ++ww) {
-        const uint32_t c = wcnt[ww * kRadix + d];
-        wcnt[ww * kRadix + d] = tot;
-        tot += c;
+    for (int q = 0; q < DPT; ++q) {
+        const int d = tid * DPT + q;
+        uint32_t run = 0;
+        if (d < R) {
+#pragma unroll
+            for (int ww = 0; ww < kSortWarps; ++ww) {
+                const uint32_t c = wcnt[ww * R + d];
+                wcnt[ww * R + d] = run;
+                run += c;
+            }
+        }
+        tot[q] = run;
+        tsum += run;
     }
-    uint32_t x = tot;
+    uint32_t x = tsum;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
@@ -347,20 +367,27 @@ __global__ void __launch_bounds__(kSortThreads, sizeof(K) == 4 ? 4 : 3) k_radix_
     }
     if (lane == 31) wsum[w] = x;
     __syncthreads();
-    uint32_t dstart = x - tot;
+    uint32_t dstart = x - tsum;
     for (int ww = 0; ww < w; ++ww) dstart += wsum[ww];
 #pragma unroll
-    for (int ww = 0; ww < kSortWarps; ++ww) wcnt[ww * kRadix + d] += dstart;
-    // global position of block-local index i of digit d: gbase[d] + i (mod 2^32)
-    gbase[d] = offs[(size_t)d * nblocks + blockIdx.x] - dstart;
+    for (int q = 0; q < DPT; ++q) {
+        const int d = tid * DPT + q;
+        if (d < R) {
+#pragma unroll
+            for (int ww = 0; ww < kSortWarps; ++ww) wcnt[ww * R + d] += dstart;
+            // global position of block-local index i of digit d: gbase[d] + i (mod 2^32)
+            gbase[d] = offs[(size_t)d * nblocks + blockIdx.x] - dstart;
+        }
+        dstart += tot[q];
+    }
     __syncthreads();
 
     // values are read only now, while the keys' ranks are known
 #pragma unroll
     for (int r = 0; r < kScatterIPT; ++r) {
-        const uint32_t dd = pk[r] & 511u;
-        if (dd < kRadix) {
-            const uint32_t p = wcnt[w * kRadix + dd] + (pk[r] >> 9);
+        const uint32_t dd = pk[r] & DMASK;
+        if (dd < R) {
+            const uint32_t p = wcnt[w * R + dd] + (pk[r] >> (RB + 1));
             skeys[p] = key[r];
             svals[p] = vin[wbase + r * 32 + lane];
         }
@@ -369,7 +396,7 @@ __global__ void __launch_bounds__(kSortThreads, sizeof(K) == 4 ? 4 : 3) k_radix_
     const int cnt = (int)min((long long)kSortChunk, n - bbase);
     for (int i = tid; i < cnt; i += kSortThreads) {
         const K k = skeys[i];
-        const uint32_t g = gbase[(uint32_t)(k >> shift) & (kRadix - 1)] + (uint32_t)i;
+        const uint32_t g = gbase[(uint32_t)(k >> shift) & (R - 1)] + (uint32_t)i;
         kout[g] = k;
         vout[g] = svals[i];
     }
@@ -458,11 +485,11 @@ cudaError_t launch_emit(const uint32_t* counts, const uint32_t* offsets, const i
 
 int sort_blocks(long long bound) { return (int)((bound + kSortChunk - 1) / kSortChunk); }
 
-// The scatter's shared memory exceeds the 48 KB default for 64-bit keys: opt
-// in once per device.
-template <typename K>
+// The scatter's shared memory exceeds the 48 KB default for 64-bit keys and
+// for wide digits: opt in once per device.
+template <typename K, int RB>
 static cudaError_t scatter_attr() {
-    constexpr size_t bytes = scatter_smem_bytes<K>();
+    constexpr size_t bytes = scatter_smem_bytes<K, RB>();
     if (bytes <= 48 * 1024) return cudaSuccess;
     static std::atomic<unsigned long long> done{0};
     int dev = 0;
@@ -470,28 +497,28 @@ static cudaError_t scatter_attr() {
     if (e != cudaSuccess) return e;
     const unsigned long long bit = 1ull << (dev & 63);
     if (done.load() & bit) return cudaSuccess;
-    e = cudaFuncSetAttribute(k_radix_scatter<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    e = cudaFuncSetAttribute(k_radix_scatter<K, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e == cudaSuccess) done.fetch_or(bit);
     return e;
 }
 
-template <typename K>
+template <typename K, int RB>
 static cudaError_t radix_sort_t(K* k0, uint32_t* v0, K* k1, uint32_t* v1, const uint32_t* n_dev,
                                 long long bound, int key_bits, uint32_t* hist, uint32_t* scan_tmp,
                                 int* passes_out, cudaStream_t st) {
     const int nb = sort_blocks(bound);
     int passes = 0;
     if (nb > 0) {
-        cudaError_t ea = scatter_attr<K>();
+        cudaError_t ea = scatter_attr<K, RB>();
         if (ea != cudaSuccess) return ea;
         K* kin = k0; uint32_t* vin = v0;
         K* kout = k1; uint32_t* vout = v1;
-        for (int shift = 0; shift < key_bits; shift += 8) {
-            k_radix_hist<K><<<nb, kSortThreads, 0, st>>>(kin, n_dev, bound, shift, nb, hist);
-            cudaError_t e = launch_scan(hist, (long long)kRadix * nb, hist, scan_tmp, nullptr, st);
+        for (int shift = 0; shift < key_bits; shift += RB) {
+            k_radix_hist<K, RB><<<nb, kSortThreads, 0, st>>>(kin, n_dev, bound, shift, nb, hist);
+            cudaError_t e = launch_scan(hist, (long long)(1 << RB) * nb, hist, scan_tmp, nullptr, st);
             if (e != cudaSuccess) return e;
-            k_radix_scatter<K><<<nb, kSortThreads, scatter_smem_bytes<K>(), st>>>(kin, vin, kout, vout, n_dev,
-                                                                                   bound, shift, nb, hist);
+            k_radix_scatter<K, RB><<<nb, kSortThreads, scatter_smem_bytes<K, RB>(), st>>>(
+                kin, vin, kout, vout, n_dev, bound, shift, nb, hist);
             K* tk = kin; kin = kout; kout = tk;
             uint32_t* tv = vin; vin = vout; vout = tv;
             ++passes;
@@ -501,19 +528,36 @@ static cudaError_t radix_sort_t(K* k0, uint32_t* v0, K* k1, uint32_t* v1, const 
     return cudaGetLastError();
 }
 
+template <typename K>
+static cudaError_t radix_sort_rb(K* k0, uint32_t* v0, K* k1, uint32_t* v1, const uint32_t* n_dev,
+                                 long long bound, int key_bits, int radix_bits, uint32_t* hist,
+                                 uint32_t* scan_tmp, int* passes_out, cudaStream_t st) {
+    switch (radix_bits) {
+        case 4: return radix_sort_t<K, 4>(k0, v0, k1, v1, n_dev, bound, key_bits, hist, scan_tmp, passes_out, st);
+        case 6: return radix_sort_t<K, 6>(k0, v0, k1, v1, n_dev, bound, key_bits, hist, scan_tmp, passes_out, st);
+        case 8: return radix_sort_t<K, 8>(k0, v0, k1, v1, n_dev, bound, key_bits, hist, scan_tmp, passes_out, st);
+        case 11:
+            return radix_sort_t<K, 11>(k0, v0, k1, v1, n_dev, bound, key_bits, hist, scan_tmp, passes_out, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 cudaError_t launch_radix_sort(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1,
-                              const uint32_t* n_dev, long long bound, int key_bits,
+                              const uint32_t* n_dev, long long bound, int key_bits, int radix_bits,
                               uint32_t* hist, uint32_t* scan_tmp, int* passes_out, cudaStream_t st) {
-    return radix_sort_t<uint64_t>(k0, v0, k1, v1, n_dev, bound, key_bits, hist, scan_tmp, passes_out, st);
+    return radix_sort_rb<uint64_t>(k0, v0, k1, v1, n_dev, bound, key_bits, radix_bits, hist, scan_tmp,
+                                   passes_out, st);
 }
 
 cudaError_t launch_radix_sort32(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1,
-                                const uint32_t* n_dev, long long bound, int key_bits,
+                                const uint32_t* n_dev, long long bound, int key_bits, int radix_bits,
                                 uint32_t* hist, uint32_t* scan_tmp, int* passes_out, cudaStream_t st) {
-    return radix_sort_t<uint32_t>(k0, v0, k1, v1, n_dev, bound, key_bits, hist, scan_tmp, passes_out, st);
+    return radix_sort_rb<uint32_t>(k0, v0, k1, v1, n_dev, bound, key_bits, radix_bits, hist, scan_tmp,
+                                   passes_out, st);
 }
 
-size_t sort_hist_elems(long long bound) { return (size_t)kRadix * (size_t)sort_blocks(bound); }
+// Histogram words of one pass at the widest digit (sizes every width).
+size_t sort_hist_elems(long long bound) { return (size_t)(1 << kRadixMaxBits) * (size_t)sort_blocks(bound); }
 
 cudaError_t launch_depth_keys(const uint32_t* counts, const uint32_t* zbits, long long n, uint32_t* keys,
                               uint32_t* vals, cudaStream_t st) {

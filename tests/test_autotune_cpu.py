@@ -10,14 +10,20 @@ import pytest
 from paper_2501_16312_gb300 import autotune
 
 BASE = dict(tile=16, batch=64, blocks_per_sm=0, sort_mode=0, pixels_per_thread=4, chain_split=0,
-            sparse_lanes=8)
+            sparse_lanes=8, radix_bits=8)
 
 
 def stage_model(k):
     """Stage times (ms) with a unique best setting per group; the blend and
-    chain times depend on earlier groups' knobs too, so the order matters."""
-    sort = 0.5 if k["sort_mode"] == 1 else 0.9
-    fwd = {(2, 32): 1.9, (2, 64): 1.7, (4, 32): 1.6, (4, 64): 1.4}[(k["pixels_per_thread"], k["batch"])]
+    chain times depend on earlier groups' knobs too, so the order matters.
+    The sort group is best at (1, 11); the blend group at tile 16, 4 pixels,
+    batch 64 -- though 8x8 tiles would make a faster blend, their longer tile
+    lists cost more in the sort stages, which the tile group is judged on."""
+    sort = (0.5 if k["sort_mode"] == 1 else 0.9) * {4: 1.3, 6: 1.1, 8: 1.0, 11: 0.9}[k["radix_bits"]]
+    sort *= {8: 3.0, 16: 1.0, 32: 0.6}[k["tile"]]
+    fwd = {(2, 32): 1.9, (2, 64): 1.7, (4, 32): 1.6, (4, 64): 1.4, (1, 32): 2.0, (1, 64): 1.8}[
+        (k["pixels_per_thread"], k["batch"])]
+    fwd *= {8: 0.9, 16: 1.0, 32: 1.3}[k["tile"]]
     bwd = 3.0 + (0.3 if k["pixels_per_thread"] == 2 else 0.0) - (0.2 if k["sparse_lanes"] == 16 else 0.0)
     if k["sort_mode"] == 1:
         fwd += 0.05                      # a slower blend must not change the sort choice
@@ -70,18 +76,21 @@ def test_search_picks_each_groups_best_in_order():
         knobs.update(setting)
 
     entry = autotune.search(apply, lambda: stage_model(knobs), BASE)
-    want = dict(BASE, sort_mode=1, pixels_per_thread=4, batch=64, blocks_per_sm=0, chain_split=1,
-                sparse_lanes=16)
+    want = dict(BASE, sort_mode=1, radix_bits=11, tile=16, pixels_per_thread=4, batch=64, blocks_per_sm=0,
+                chain_split=1, sparse_lanes=16)
     assert entry["tuning"] == want
     assert knobs == want                                # the winners are left applied
-    assert len(entry["trials"]) == 2 + 4 + 2 + 2
+    assert len(entry["trials"]) == 8 + 12 + 2 + 2
     # the sort group is judged on its own stages only
-    assert entry["best_ms"]["sort_mode"] == pytest.approx(0.5)
-    assert entry["best_ms"]["pixels_per_thread+batch+blocks_per_sm"] == pytest.approx(1.45 + 3.0)
+    assert entry["best_ms"]["sort_mode+radix_bits"] == pytest.approx(0.45)
+    # the tile group on the sort and blend stages together
+    assert entry["best_ms"]["tile+pixels_per_thread+batch+blocks_per_sm"] == pytest.approx(0.45 + 1.45 + 3.0)
     # each trial of a later group ran at the earlier groups' winners
     for t in entry["trials"]:
         if "chain_split" in t:
             assert t["blend_fwd"] == pytest.approx(1.45)
+        if t.get("tile") == 16:                            # timed at sort mode 1, 11-bit digits
+            assert t["scan_emit"] == pytest.approx(0.45 * 0.6)
 
 
 def test_search_ties_keep_the_first_candidate():
@@ -89,8 +98,8 @@ def test_search_ties_keep_the_first_candidate():
     flat = {"preprocess": 0.0, "scan_emit": 1.0, "sort": 1.0, "ranges": 1.0, "blend_fwd": 1.0,
             "blend_bwd": 1.0, "chain": 1.0}
     entry = autotune.search(knobs.update, lambda: flat, BASE)
-    assert entry["tuning"] == dict(BASE, sort_mode=0, pixels_per_thread=2, batch=32, chain_split=0,
-                                   sparse_lanes=8)
+    assert entry["tuning"] == dict(BASE, sort_mode=0, radix_bits=4, tile=8, pixels_per_thread=1, batch=32,
+                                   chain_split=0, sparse_lanes=8)
 
 
 def test_cache_key_buckets():
@@ -125,9 +134,9 @@ def test_tune_caches_reuses_and_restores_timing(fake_cuda, tmp_path):
     cache = str(tmp_path / "sub" / "tuning.json")
     rast = FakeRast()
     entry = autotune.tune(rast, prims, cams, reps=2, cache=cache)
-    want = dict(BASE, sort_mode=1, pixels_per_thread=4, batch=64, chain_split=1, sparse_lanes=16)
+    want = dict(BASE, sort_mode=1, radix_bits=11, pixels_per_thread=4, batch=64, chain_split=1, sparse_lanes=16)
     assert entry["tuning"] == want and rast.knobs == want
-    assert rast.measured == 10 * 3                       # 10 trials x (warm-up + 2 timed)
+    assert rast.measured == 24 * 3                       # 24 trials x (warm-up + 2 timed)
     assert rast.timing_calls == [True, False]            # timing restored to off
     stored = json.load(open(cache))
     key = autotune.cache_key("FakeGPU", 6, 10, cams)
@@ -141,7 +150,7 @@ def test_tune_caches_reuses_and_restores_timing(fake_cuda, tmp_path):
     rast3 = FakeRast()
     rast3.set_timing(True)
     autotune.tune(rast3, prims, cams, reps=1, cache=cache, force=True)
-    assert rast3.measured == 10 * 2 and rast3.timing() is True
+    assert rast3.measured == 24 * 2 and rast3.timing() is True
     # other workloads share the file
     autotune.tune(FakeRast(), prims, cams[:1], reps=1, cache=cache)
     assert len(json.load(open(cache))) == 2

@@ -39,17 +39,21 @@ CASES = {
 }
 
 
+@pytest.mark.parametrize("tile", [8, 16, 32])
 @pytest.mark.parametrize("sort_mode", [0, 1])
 @pytest.mark.parametrize("case", sorted(CASES))
-def test_tile_lists_bit_exact(rast, case, sort_mode):
+def test_tile_lists_bit_exact(rast, case, sort_mode, tile):
+    """Sec. 3.2 "Global Sorting and Tiling" at every tile edge the tuner
+    may pick: counts, keys and values equal the oracle's bit for bit."""
     w = CASES[case]()
-    rast.set_tuning(sort_mode=sort_mode)
+    base = rast.tuning()
+    rast.set_tuning(sort_mode=sort_mode, tile=tile, pixels_per_thread=2)
     try:
         gpu_forward_backward(rast, w.scene, w.cameras, (0, 0, 0))
     finally:
-        rast.set_tuning(sort_mode=0)
+        rast.set_tuning(**base)
     k, v = rast.debug_keys()
-    ko, vo, co = oracle.keys(w.scene, w.cameras, tile=16)
+    ko, vo, co = oracle.keys(w.scene, w.cameras, tile=tile)
     np.testing.assert_array_equal(rast.debug_counts(), co)
     assert k.shape == ko.shape
     np.testing.assert_array_equal(k, ko)
@@ -384,25 +388,67 @@ def test_cuda_graph_capture_replays(rast):
 
 
 def test_every_tuning_renders_identical_images(rast):
-    """Sort mode, pixels per thread, batch, grid size, chain form and the
-    sparse-atomics threshold change the schedule, never the arithmetic of a
-    pixel: images are bitwise identical and gradients agree to float rounding
-    (atomics and the chain form reorder the sums)."""
+    """Sort mode, radix width, pixels per thread, batch, grid size, chain form
+    and the sparse-atomics threshold change the schedule, never the
+    arithmetic of a pixel: for one tile edge, images are bitwise identical and
+    gradients agree to float rounding (atomics and the chain form reorder the
+    sums).  Another tile edge re-bases the face planes at other tile origins,
+    which changes images by rounding only."""
     import itertools
     w = multiview_small()
     dL = scenes.image_gradient(w, seed=3)
     base = rast.tuning()
-    ref_img, ref_g = gpu_forward_backward(rast, w.scene, w.cameras, (0.1, 0.1, 0.1), dL)
+    tile_pix = [(8, 1), (8, 2), (16, 1), (16, 2), (16, 4), (32, 2), (32, 4)]
+    ref = {}
     try:
-        for sm, pix, batch, bps, cs, sl in itertools.product([0, 1], [1, 2, 4], [32, 128], [0, 1], [0, 1], [0, 32]):
-            rast.set_tuning(sort_mode=sm, pixels_per_thread=pix, batch=batch, blocks_per_sm=bps, chain_split=cs,
-                            sparse_lanes=sl)
+        rast.set_tuning(tile=16, pixels_per_thread=4)
+        img16, g16 = gpu_forward_backward(rast, w.scene, w.cameras, (0.1, 0.1, 0.1), dL)
+        for (tile, pix), sm, rb, batch, bps, (cs, sl) in itertools.product(
+                tile_pix, [0, 1], [4, 11, 8], [32, 128], [0, 1], [(0, 0), (1, 32)]):
+            if rb != 8 and (batch, bps, cs) != (32, 0, 0):
+                continue    # the digit width touches the sort only
+            rast.set_tuning(tile=tile, sort_mode=sm, radix_bits=rb, pixels_per_thread=pix, batch=batch,
+                            blocks_per_sm=bps, chain_split=cs, sparse_lanes=sl)
             img, g = gpu_forward_backward(rast, w.scene, w.cameras, (0.1, 0.1, 0.1), dL)
-            np.testing.assert_array_equal(img, ref_img)
+            if tile not in ref:
+                ref[tile] = (img, g)
+                assert np.abs(img - img16).max() <= 2e-5, (tile, np.abs(img - img16).max())
+                for k in g:
+                    assert rel_l2(g[k], g16[k]) <= 1e-4, (tile, k)
+            np.testing.assert_array_equal(img, ref[tile][0])
             for k in g:
-                assert rel_l2(g[k], ref_g[k]) <= 1e-5, (sm, pix, batch, bps, cs, sl, k)
+                assert rel_l2(g[k], ref[tile][1][k]) <= 1e-5, (tile, sm, rb, pix, batch, bps, cs, sl, k)
     finally:
         rast.set_tuning(**base)
+
+
+def test_tuning_rejects_unbuilt_schedules(rast):
+    from paper_2501_16312_gb300 import LinPrimError
+    base = rast.tuning()
+    for bad in (dict(tile=12), dict(tile=8, pixels_per_thread=4), dict(tile=32, pixels_per_thread=1)):
+        with pytest.raises(LinPrimError):
+            rast.set_tuning(**dict(base, **bad))
+    assert rast.tuning() == base
+
+
+@pytest.mark.parametrize("tile", [8, 32])
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_tile_sizes_vs_oracle(rast, case, tile):
+    """Images and gradients at the other tile edges against the oracle (the
+    tile changes only which tile lists a pixel walks, never its order)."""
+    w = CASES[case]()
+    bg = (0.1, 0.2, 0.3)
+    ref, info = oracle.render(w.scene, w.cameras, bg=bg, info=True)
+    dL = mask_borderline(scenes.image_gradient(w, seed=1), info, w.cameras)
+    base = rast.tuning()
+    try:
+        rast.set_tuning(tile=tile, pixels_per_thread=2)
+        img, grads = gpu_forward_backward(rast, w.scene, w.cameras, bg, dL)
+    finally:
+        rast.set_tuning(**base)
+    _, ref_g = oracle.render(w.scene, w.cameras, bg=bg, dL_dimage=dL)
+    assert_images_match(img, ref, info, w.cameras)
+    assert_grads_match(grads, ref_g)
 
 
 @pytest.mark.parametrize("case", sorted(CASES))
