@@ -564,10 +564,13 @@ static int span_mtia(const orc_pp* pp, int nv, double rx, double ry, double* i1,
 
 /* Independent second formulation: clip the ray against the face half-spaces
  * of the convex primitive (entry = max over faces whose outward normal faces
- * the camera, exit = min over the others).  Used only to cross-check MTIA. */
-static int span_clip(const orc_pp* pp, int nv, double rx, double ry, double* i1, double* i2) {
+ * the camera, exit = min over the others).  Used to cross-check MTIA and to
+ * flag rays that graze the primitive.  lo2 / hi2 (may be NULL) receive the
+ * second largest entry depth and the second smallest exit depth. */
+static int span_clip2(const orc_pp* pp, int nv, double rx, double ry, double* i1, double* i2, double* lo2_out,
+                      double* hi2_out) {
     int f, F = n_faces(nv);
-    double lo = -INFINITY, hi = INFINITY;
+    double lo = -INFINITY, hi = INFINITY, lo2 = -INFINITY, hi2 = INFINITY;
     if (pp->exact) {
         /* the ray lam d against each face's half-space n . t <= h (outward n) */
         double d[3], dl = exact_dir(pp, rx, ry, d);
@@ -588,10 +591,17 @@ static int span_clip(const orc_pp* pp, int nv, double rx, double ry, double* i1,
                 if (h < 0.0) { *i1 = INFINITY; *i2 = -INFINITY; return 0; }
                 continue;
             }
-            if (den < 0) { if (h / den * dl > lo) lo = h / den * dl; }
-            else         { if (h / den * dl < hi) hi = h / den * dl; }
+            if (den < 0) {
+                const double t = h / den * dl;
+                if (t > lo) { lo2 = lo; lo = t; } else if (t > lo2) lo2 = t;
+            } else {
+                const double t = h / den * dl;
+                if (t < hi) { hi2 = hi; hi = t; } else if (t < hi2) hi2 = t;
+            }
         }
         *i1 = lo; *i2 = hi;
+        if (lo2_out) *lo2_out = lo2;
+        if (hi2_out) *hi2_out = hi2;
         return hi > lo && lo > 0.0;
     }
     for (f = 0; f < F; ++f) {
@@ -612,11 +622,17 @@ static int span_clip(const orc_pp* pp, int nv, double rx, double ry, double* i1,
             continue;
         }
         z = (h - n[0] * rx - n[1] * ry) / n[2];
-        if (n[2] < 0) { if (z > lo) lo = z; }
-        else          { if (z < hi) hi = z; }
+        if (n[2] < 0) { if (z > lo) { lo2 = lo; lo = z; } else if (z > lo2) lo2 = z; }
+        else          { if (z < hi) { hi2 = hi; hi = z; } else if (z < hi2) hi2 = z; }
     }
     *i1 = lo; *i2 = hi;
+    if (lo2_out) *lo2_out = lo2;
+    if (hi2_out) *hi2_out = hi2;
     return hi > lo;
+}
+
+static int span_clip(const orc_pp* pp, int nv, double rx, double ry, double* i1, double* i2) {
+    return span_clip2(pp, nv, rx, ry, i1, i2, NULL, NULL);
 }
 
 /* ----------------------------------------------------------- per-camera set */
@@ -753,16 +769,23 @@ static int blend_pixel(const orc_prims* P, const orc_view* V, const double bg[3]
          * with respect to the vertices is not (the span's derivative is
          * finite just inside and zero outside), so a ray passing within
          * rounding of a silhouette may take either side in binary32: flag
-         * spans within 1e-5 of the primitive's depth extent of zero */
+         * spans within 1e-5 of the primitive's depth extent of zero.  The
+         * same holds across an edge between two entry faces or two exit
+         * faces of a primitive the ray crosses: the span is continuous there
+         * but its derivative follows whichever face bounds it, so a ray
+         * whose two nearest entry (or exit) depths agree to within 1e-5 of
+         * the depth extent is flagged too. */
         {
-            double c1, c2, zlo = INFINITY, zhi = -INFINITY;
+            double c1, c2, lo2, hi2, zlo = INFINITY, zhi = -INFINITY;
             int k;
             for (k = 0; k < P->nv; ++k) {
                 if (pp->p[k][2] < zlo) zlo = pp->p[k][2];
                 if (pp->p[k][2] > zhi) zhi = pp->p[k][2];
             }
-            span_clip(pp, P->nv, rx, ry, &c1, &c2);
+            span_clip2(pp, P->nv, rx, ry, &c1, &c2, &lo2, &hi2);
             if (fabs(c2 - c1) <= 1e-5 * (zhi - zlo)) out->borderline |= 2;
+            if (c2 > c1 && (c1 - lo2 <= 1e-5 * (zhi - zlo) || hi2 - c2 <= 1e-5 * (zhi - zlo)))
+                out->borderline |= 2;
         }
         if (!span_mtia(pp, P->nv, rx, ry, &i1, &i2, &f1, &f2)) continue;
         s = i2 - i1;

@@ -682,17 +682,34 @@ def test_aa_filter_adjoint_fd(orc):
 
 def test_silhouette_grazing_pixels_are_flagged(orc):
     """A ray through a silhouette vertex has a zero span: the oracle flags it
-    (bit 1 of the borderline word), and a ray well inside is not flagged."""
+    (bit 1 of the borderline word), and rays well inside, off the faces'
+    edges, are not flagged."""
     D, a = 4.0, 0.3
     cam = cam_on_axis(D, 65, 65, 20.0)
     # the +x vertex projects onto the centre of pixel (40, 32)
     X = (40.5 - cam.cx) * D / cam.fx
     sc = one_scene(6, [0, 0, 0], axis_octa([0, 0, 0], X, 0.2, 0.1), 0.5)
-    px = np.array([40, 38, 32], np.int32)
-    py = np.array([32, 32, 32], np.int32)
+    px = np.array([40, 38, 36], np.int32)
+    py = np.array([32, 30, 29], np.int32)
     _, info = orc.render_pixels(sc, cam, px, py)
     flags = info[:, 2].astype(int)
     assert flags[0] & 2 and not flags[1] & 2 and not flags[2] & 2
+
+
+def test_interior_edge_pixels_are_flagged(orc):
+    """An axis-aligned octahedron on the optical axis: its front faces meet
+    (and its back faces meet) along the image axes through the centre, where
+    the span is continuous but its derivative switches between faces.  Rays
+    through those edges are flagged (bit 1), a ray between them is not."""
+    D = 4.0
+    cam = cam_on_axis(D, 65, 65, 20.0)      # pixel 32 is centred on each axis
+    sc = one_scene(6, [0, 0, 0], axis_octa([0, 0, 0], 0.17, 0.2, 0.1), 0.5)
+    px = np.array([32, 36, 32, 36], np.int32)
+    py = np.array([29, 32, 32, 29], np.int32)
+    _, info = orc.render_pixels(sc, cam, px, py)
+    flags = info[:, 2].astype(int)
+    assert info[:, 0].min() == 1                       # each ray crosses the primitive
+    assert flags[0] & 2 and flags[1] & 2 and flags[2] & 2 and not flags[3] & 2
 
 
 # --------------------------------------------------- depth (App. "Depth and Surface Reconstruction")
@@ -732,7 +749,9 @@ def test_depth_two_layers(orc):
         # through the centres each layer's span is its full thickness 2c: opacity 0.99 alpha
         assert abs((1 - np.exp(-sig[0] * 0.1)) - 0.99 * a_front) < 1e-12
         d, f = orc.depth_pixels(sc, cam, np.array([16], np.int32), np.array([16], np.int32))
-        assert f[0] == 0 and abs(d[0] - want) < 1e-12, (a_front, d[0])
+        # the axis ray meets both layers at their vertices, where faces meet
+        # (bit 1); the 0.5 crossing itself is not borderline (bit 2)
+        assert not f[0] & 4 and abs(d[0] - want) < 1e-12, (a_front, d[0])
     empty = one_scene(6, [0, 0, 0], axis_octa([0, 0, 0], 0.1, 0.1, 0.1), 0.9)
     d, _ = orc.depth_pixels(empty, cam, np.array([0], np.int32), np.array([0], np.int32))
     assert d[0] == 0.0
