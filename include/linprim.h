@@ -114,10 +114,9 @@ typedef struct {
  *   radix_bits    digit width of the radix sort passes: 4, 6, 8 or 11 bits
  *                 (ceil(key bits / radix_bits) passes, each with a histogram
  *                 of 2^radix_bits bins per 4096 keys).
- * For one tile edge every setting renders bit-identical images and tile
- * lists.  Another tile edge gives other tile lists (each in the paper's
- * per-tile order) and re-bases the face planes at other tile origins, which
- * changes image values by rounding only.  chain_split and sparse_lanes change
+ * Every setting renders bit-identical images (a pixel's arithmetic does not
+ * depend on the schedule); tile lists are identical for one tile edge and in
+ * the paper's per-tile order at each.  chain_split and sparse_lanes change
  * the order in which gradient terms are summed, so gradients can differ in
  * the last bits between settings.  A backward, depth pass or pair count uses
  * the tile edge, batch and pixels per thread of its forward.                */

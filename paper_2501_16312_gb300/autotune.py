@@ -4,9 +4,9 @@ The tuning knobs (sort mode and radix digit width, tile edge, pixels per
 blend thread, records per shared-memory batch, resident blend blocks per SM,
 one- or two-pass backward chain, and the number of contributing lanes up to
 which a backward warp lets each lane add its own terms) change only the
-schedule: for one tile edge every setting renders bit-identical images (the
-chain's split and the backward's reduction form only reorder floating-point
-sums of gradients), and another tile edge changes images by rounding only.  The tuner times forward + backward of the caller's own workload
+schedule: every setting renders bit-identical images (the chain's split and
+the backward's reduction form only reorder floating-point sums of
+gradients).  The tuner times forward + backward of the caller's own workload
 with the library's per-stage CUDA events.  It settles the knobs one group at
 a time, each judged on the stages it affects: the sort mode and digit width
 on the sort stages; the tile edge and blend schedule on the sort and blend

@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(TILE * TILE / PIX, bwd_min_blocks<TILE * TILE 
                 if (any) {
                     // one pass with the entry/exit slots: with the entries this
                     // warp blended nowhere skipped, most warps contribute
-                    spans<V, PIX, true>(p, (float)lx0, (float)ly, sp, sf, sb);
+                    spans<V, PIX, true>(p, (float)lx0 + p.dx0, (float)ly + p.dy0, sp, sf, sb);
 #pragma unroll
                     for (int i = 0; i < PIX; ++i) {
                         c[i] = idx < last[i] && sp[i] > 0.f;

@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(TILE * TILE / PIX) k_blend_fwd(
                         // warp-uniform: no pixel of this warp's rows can meet it
                         if (!((p.bands >> (tid >> 5)) & 1u)) continue;
                         float sp[PIX];
-                        spans<V, PIX, false>(p, (float)lx0, (float)ly, sp, nullptr, nullptr);
+                        spans<V, PIX, false>(p, (float)lx0 + p.dx0, (float)ly + p.dy0, sp, nullptr, nullptr);
                         tdone = true;
                         bool blended = false;
 #pragma unroll
@@ -118,8 +118,8 @@ __global__ void __launch_bounds__(TILE * TILE / PIX) k_blend_fwd(
                                     // entry depth: centre depth + max over the entry faces
                                     float e = -CUDART_INF_F;
                                     for (int f = 0; f < p.nf; ++f)
-                                        e = fmaxf(e, __fmaf_rn(p.pl[f].x, (float)(lx0 + i),
-                                                               __fmaf_rn(p.pl[f].y, (float)ly, p.pl[f].z)));
+                                        e = fmaxf(e, __fmaf_rn(p.pl[f].x, (float)(lx0 + i) + p.dx0,
+                                                               __fmaf_rn(p.pl[f].y, (float)ly + p.dy0, p.pl[f].z)));
                                     dep[i] = __fadd_rn(p.pl[0].w, e);
                                 }
                             }

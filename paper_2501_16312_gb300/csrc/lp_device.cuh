@@ -236,14 +236,18 @@ __device__ __forceinline__ float min3f(float a, float b, float c) {
 }
 
 // -------------------------------------------------------------------------
-// A record staged in shared memory for one tile: the planes are re-based to
-// the tile's first pixel (tx0, ty0), an exact integer offset (dx0, dy0) from
-// (X0, Y0), so that pixel (tx0 + lx, ty0 + ly) evaluates depth = a lx + b ly
-// + e'.  Planes are float4 (a, b, e', 0) for 128-bit shared loads.  The
-// forward and backward blends both stage through stage_record() and evaluate
-// through the same span routines, so they compute bit-identical spans.
-// pl[0].w carries the ray-space depth of the centre, to which the planes'
-// depths are relative (used by the depth pass only).
+// A record staged in shared memory for one tile.  Planes are float4
+// (a, b, e0, 0) for 128-bit shared loads, anchored at the record's integer
+// pixel (X0, Y0): pixel (tx0 + lx, ty0 + ly) of the tile evaluates depth =
+// a X + b Y + e0 at the exact integer offsets X = lx + dx0, Y = ly + dy0 from
+// the anchor, with (dx0, dy0) = (tx0 - X0, ty0 - Y0).  The arithmetic of a
+// pixel is then the same whatever tile holds it, and near the primitive
+// (where its spans matter) the terms are no larger than its own depth
+// extent.  The forward and backward blends both stage through
+// stage_record() and evaluate through the same span routines, so they
+// compute bit-identical spans.  pl[0].w carries the ray-space depth of the
+// centre, to which the planes' depths are relative (used by the depth pass
+// only).
 template <int V> struct alignas(16) Staged {
     static constexpr int F = Kind<V>::F;
     float4 pl[F];
@@ -270,13 +274,19 @@ __device__ __forceinline__ uint32_t band_mask(const Staged<V>& s) {
     const int nf = s.nf;
     if (nf <= 0 || nf >= F) return 0u;
     uint32_t mask = NB == 32 ? 0xffffffffu : (1u << NB) - 1u;
+    // the margin bounds the rounding of every term of a plane's evaluation at
+    // a pixel of the tile (offsets up to |dx0| + TILE - 1 from the anchor)
+    const float ox = fabsf(s.dx0) + XM, oy = fabsf(s.dy0) + XM;
     for (int f = 0; f < nf; ++f) {
         const float4 pf = s.pl[f];
+        const float ef = __fmaf_rn(pf.x, s.dx0, __fmaf_rn(pf.y, s.dy0, pf.z));   // at the tile origin
         for (int b = nf; b < F; ++b) {
             const float4 pb = s.pl[b];
-            const float da = pb.x - pf.x, db = pb.y - pf.y, de = pb.z - pf.z;
-            const float margin = 1e-5f * (fabsf(pb.z) + fabsf(pf.z) + XM * (fabsf(pb.x) + fabsf(pf.x) +
-                                                                             fabsf(pb.y) + fabsf(pf.y))) + 1e-30f;
+            const float eb = __fmaf_rn(pb.x, s.dx0, __fmaf_rn(pb.y, s.dy0, pb.z));
+            const float da = pb.x - pf.x, db = pb.y - pf.y, de = eb - ef;
+            const float margin = 1e-5f * (fabsf(pb.z) + fabsf(pf.z) + fabsf(eb) + fabsf(ef) +
+                                          ox * (fabsf(pb.x) + fabsf(pf.x)) + oy * (fabsf(pb.y) + fabsf(pf.y))) +
+                                 1e-30f;
             const float xmax = fmaxf(0.f, XM * da);
 #pragma unroll
             for (int w = 0; w < NB; ++w) {
@@ -305,7 +315,7 @@ __device__ __forceinline__ void stage_record(const float* __restrict__ rec, int 
 #pragma unroll
     for (int f = 0; f < F; ++f) {
         const float a = buf[8 + 3 * f], b = buf[9 + 3 * f], e = buf[10 + 3 * f];
-        s.pl[f] = make_float4(a, b, __fmaf_rn(a, dx0, __fmaf_rn(b, dy0, e)), 0.f);
+        s.pl[f] = make_float4(a, b, e, 0.f);
     }
     s.pl[0].w = buf[7];
     s.sigma = buf[2];
@@ -315,7 +325,8 @@ __device__ __forceinline__ void stage_record(const float* __restrict__ rec, int 
     s.rec = r;
 }
 
-// Ray/primitive spans of a strip of PIX pixels (lx0 + i, ly), i < PIX, by
+// Ray/primitive spans of a strip of PIX pixels at anchor offsets (X0 + i, Y),
+// i < PIX (X0 = lx0 + dx0, Y = ly + dy0, exact integers), by
 // half-space clipping of each pixel ray against the convex primitive: entry
 // = max over the NF entry faces, exit = min over the others.  This equals the
 // distance between the two MTIA hits of Sec. 3.2 "Rasterization".  NF is a

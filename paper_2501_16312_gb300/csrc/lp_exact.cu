@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(128) k_preprocess_x(PrimsDev P, CamsParam cams
 // ------------------------------------------------------------------- blend
 template <int V> struct alignas(16) StagedX {
     static constexpr int F = Kind<V>::F;
-    float4 pl[F];      // (p, q, L at the tile's first pixel, D0)
+    float4 pl[F];      // (p, q, L0, D0): L = p X + q Y + L0 at the anchor offset (X, Y)
     float sigma, r, g, b;
     float cz, dx0, dy0;
     int nf;            // entry faces (slots 0 .. nf - 1)
@@ -223,7 +223,7 @@ __device__ __forceinline__ void stage_record_x(const float* __restrict__ rec, in
 #pragma unroll
     for (int f = 0; f < F; ++f) {
         const float4 pl = __ldg(src + 2 + f);
-        s.pl[f] = make_float4(pl.x, pl.y, __fmaf_rn(pl.x, dx0, __fmaf_rn(pl.y, dy0, pl.z)), pl.w);
+        s.pl[f] = pl;   // evaluated at anchor offsets, whatever the tile
     }
     s.sigma = h0.z;
     s.r = h1.x; s.g = h1.y; s.b = h1.z;
@@ -373,7 +373,8 @@ __global__ void __launch_bounds__(threads_x<TILE>()) k_blend_fwd_x(
                         for (int i = 0; i < PIX; ++i) n_iter += !done[i];
                     }
                     float sp[PIX], en[PIX];
-                    spans_x<V, PIX, false>(p, (float)lx0, (float)ly, rn, sp, nullptr, nullptr, DEPTH ? en : nullptr);
+                    spans_x<V, PIX, false>(p, (float)lx0 + p.dx0, (float)ly + p.dy0, rn, sp, nullptr, nullptr,
+                                           DEPTH ? en : nullptr);
                     tdone = true;
                     bool blended = false;
 #pragma unroll
@@ -534,7 +535,7 @@ __global__ void __launch_bounds__(threads_x<TILE>()) k_blend_bwd_x(
                 int sf[PIX], sb[PIX];
                 bool c[PIX];
                 bool anyc = false;
-                spans_x<V, PIX, true>(p, (float)lx0, (float)ly, rn, sp, sf, sb, nullptr);
+                spans_x<V, PIX, true>(p, (float)lx0 + p.dx0, (float)ly + p.dy0, rn, sp, sf, sb, nullptr);
 #pragma unroll
                 for (int i = 0; i < PIX; ++i) {
                     c[i] = idx < last[i] && sp[i] > 0.f;
@@ -577,7 +578,7 @@ __global__ void __launch_bounds__(threads_x<TILE>()) k_blend_bwd_x(
 #pragma unroll
                         for (int ff = 1; ff < F; ++ff)
                             if (ff == f) pl = p.pl[ff];
-                        const float L = __fmaf_rn(pl.x, (float)(lx0 + i), __fmaf_rn(pl.y, (float)ly, pl.z));
+                        const float L = __fmaf_rn(pl.x, X, __fmaf_rn(pl.y, Y, pl.z));
                         const float D = __fadd_rn(L, pl.w);
                         const float iD = 1.f / D;
                         const float dl = __fmaf_rn(-p.cz, L, 1.f) * iD;
