@@ -114,6 +114,10 @@ typedef struct {
  *   radix_bits    digit width of the radix sort passes: 4, 6, 8 or 11 bits
  *                 (ceil(key bits / radix_bits) passes, each with a histogram
  *                 of 2^radix_bits bins per 4096 keys).
+ *   tile_order    0: the persistent blends take tiles in index order; 1:
+ *                 longest tile list first (tiles bucketed by the binary
+ *                 logarithm of their list length), so that no long tile
+ *                 starts last.
  * Every setting renders bit-identical images (a pixel's arithmetic does not
  * depend on the schedule); tile lists are identical for one tile edge and in
  * the paper's per-tile order at each.  chain_split and sparse_lanes change
@@ -129,6 +133,7 @@ typedef struct {
     int chain_split;
     int sparse_lanes;
     int radix_bits;
+    int tile_order;
 } lp_tuning;
 
 /* Sizes of the last forward call (filled by lp_get_stats).                 */
@@ -166,7 +171,7 @@ void lp_destroy(lp_ctx* ctx);
 
 /* Set / read the tuning parameters (defaults: tile 16, batch 64,
  * blocks_per_sm 0, sort_mode 0, pixels_per_thread 4, chain_split 0,
- * sparse_lanes 8, radix_bits 8).  LP_ERR_INVALID for a value outside the
+ * sparse_lanes 8, radix_bits 8, tile_order 0).  LP_ERR_INVALID for a value outside the
  * sets above, or a (tile, pixels_per_thread) pair that is not built.        */
 lp_status lp_set_tuning(lp_ctx* ctx, const lp_tuning* t);
 lp_status lp_get_tuning(lp_ctx* ctx, lp_tuning* t);

@@ -12,7 +12,8 @@ a time, each judged on the stages it affects: the sort mode and digit width
 on the sort stages; the tile edge and blend schedule on the sort and blend
 stages (the tile edge sets the tile-list length as well as the blend's work);
 the chain form on the chain stage and the lane threshold on the backward
-blend.  The choice is cached as JSON keyed by GPU name, primitive kind and
+blend, and the tile order on the range and blend stages (its kernels run
+with the ranges).  The choice is cached as JSON keyed by GPU name, primitive kind and
 size buckets of the workload.
 """
 from __future__ import annotations
@@ -63,7 +64,8 @@ GROUPS = (
     (("tile", "pixels_per_thread", "batch", "blocks_per_sm"),
      tuple((t, p, b, 0) for (t, p), b in itertools.product(TILE_PIX, (32, 64))), SORT_STAGES + BLEND_STAGES),
     (("chain_split",), ((0,), (1,)), ("chain",)),
-    (("sparse_lanes",), ((8,), (16,)), ("blend_bwd",)),
+    (("sparse_lanes",), ((4,), (8,), (16,)), ("blend_bwd",)),
+    (("tile_order",), ((0,), (1,)), ("ranges",) + BLEND_STAGES),
 )
 
 

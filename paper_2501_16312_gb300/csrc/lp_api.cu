@@ -39,12 +39,12 @@ constexpr unsigned char kGuardByte = 0xA5;
 struct lp_ctx {
     int device = 0;
     int sms = 0;
-    lp_tuning tune{16, 64, 0, 0, 4, 0, 8, 8};
+    lp_tuning tune{16, 64, 0, 0, 4, 0, 8, 8, 0};
     float aa_kernel = 0.f;      // 2D filter size in pixels (0 = off)
     bool exact = false;         // spans along the true perspective ray
     bool fwd_exact = false;     // mode of the last forward
     uint32_t contrib_stride = 0;
-    lp_tuning fwd_tune{16, 64, 0, 0, 4, 0, 8, 8};   // schedule of the last forward (its tiles, mask layout)
+    lp_tuning fwd_tune{16, 64, 0, 0, 4, 0, 8, 8, 0};   // schedule of the last forward (its tiles, mask layout)
     // densification statistics gathered by forward and backward (null: off)
     float* st_grad_sum = nullptr;
     uint32_t* st_grad_count = nullptr;
@@ -60,6 +60,8 @@ struct lp_ctx {
     DevBuf<uint2> ranges;
     DevBuf<float> tl, acc, scratch_image;
     DevBuf<uint32_t> dkeys0, dkeys1, dvals0, dvals1, counts_sorted;   // two-stage sort
+    DevBuf<uint32_t> tile_order;     // longest-list-first queue order of the tiles
+    uint32_t* d_order_scratch = nullptr;   // bucket counts and cursors of the order
     int* d_status = nullptr;         // latched status bits
     uint32_t* d_E = nullptr;         // tile-list length of the last forward
     int* d_tile_counter = nullptr;   // [0] forward queue, [1] backward queue
@@ -92,7 +94,7 @@ struct lp_ctx {
         f(vals0, "values"); f(vals1, "values"); f(ranges, "tile ranges"); f(tl, "pixel state");
         f(acc, "gradient accumulators"); f(scratch_image, "scratch image"); f(dkeys0, "depth keys");
         f(dkeys1, "depth keys"); f(dvals0, "depth values"); f(dvals1, "depth values");
-        f(counts_sorted, "sorted counts");
+        f(counts_sorted, "sorted counts"); f(tile_order, "tile order");
     }
 };
 
@@ -299,6 +301,8 @@ lp_status lp_create(lp_ctx** out, int device) {
     if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->d_E, sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->d_tile_counter, 2 * sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->d_pairs, 4 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&ctx->d_order_scratch, 68 * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMemset(ctx->d_order_scratch, 0, 68 * sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->h_E, sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMemset(ctx->d_status, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(ctx->d_E, 0, sizeof(uint32_t));
@@ -320,6 +324,7 @@ void lp_destroy(lp_ctx* ctx) {
     if (ctx->d_E) cudaFree(ctx->d_E);
     if (ctx->d_tile_counter) cudaFree(ctx->d_tile_counter);
     if (ctx->d_pairs) cudaFree(ctx->d_pairs);
+    if (ctx->d_order_scratch) cudaFree(ctx->d_order_scratch);
     if (ctx->h_E) cudaFreeHost(ctx->h_E);
     for (cudaEvent_t& e : ctx->ev)
         if (e) cudaEventDestroy(e);
@@ -347,6 +352,8 @@ lp_status lp_set_tuning(lp_ctx* ctx, const lp_tuning* t) {
         return fail(ctx, LP_ERR_INVALID, "sparse_lanes %d outside 0..32", t->sparse_lanes);
     if (t->radix_bits != 4 && t->radix_bits != 6 && t->radix_bits != 8 && t->radix_bits != 11)
         return fail(ctx, LP_ERR_INVALID, "radix_bits %d not in {4, 6, 8, 11}", t->radix_bits);
+    if (t->tile_order != 0 && t->tile_order != 1)
+        return fail(ctx, LP_ERR_INVALID, "tile_order %d not in {0, 1}", t->tile_order);
     ctx->tune = *t;
     return LP_OK;
 }
@@ -427,6 +434,7 @@ static lp_status reserve_impl(lp_ctx* ctx, long long records, long long entries,
     LP_TRY(ensure(ctx, ctx->emit_part, (long long)lp::emit_blocks(records, kcap) + 1, false, "emit partition"));
     LP_TRY(ensure(ctx, ctx->contrib, (kcap / 32 + 2) * kMaskWarpsMax, false, "contributor mask"));
     LP_TRY(ensure(ctx, ctx->ranges, tiles, false, "tile ranges"));
+    LP_TRY(ensure(ctx, ctx->tile_order, tiles, false, "tile order"));
     LP_TRY(ensure(ctx, ctx->last, pixels, false, "pixel state"));
     LP_TRY(ensure(ctx, ctx->tl, pixels, false, "pixel state"));
     const int af = V ? acc_floats_mode(V, ctx->exact) : acc_floats_max();
@@ -580,10 +588,15 @@ lp_status lp_render_forward(lp_ctx* ctx, const lp_prims* prims, const lp_camera*
                                   ctx->ranges.p, ctx->sms, st));
         ctx->result_in_1 = in1;
     }
+    if (ctx->tune.tile_order) {
+        LP_TRY(ensure(ctx, ctx->tile_order, tiles, cap_mode, "tile order"));
+        LP_CUDA(lp::launch_tile_order(ctx->ranges.p, tiles, ctx->tile_order.p, ctx->d_order_scratch, st));
+    }
     mark(ctx, st, 4, cap_mode);
 
     lp::BlendArgs a{};
     a.grid = blend_grid(ctx, ctx->tune, V, true, tiles, exact);
+    a.order = ctx->tune.tile_order ? ctx->tile_order.p : nullptr;
     a.rec = ctx->rec.p;
     a.vals = svals;
     a.ranges = ctx->ranges.p;
@@ -606,7 +619,8 @@ lp_status lp_render_forward(lp_ctx* ctx, const lp_prims* prims, const lp_camera*
     mark(ctx, st, 5, cap_mode);
     ctx->fwd_timed = ctx->timing;
     ctx->launches_fwd = 1 + (records > 0 ? 3 : 0) + (records > 0 ? 1 : 0) + 5 * (passes + passes1) +
-                        (mode == 1 && records > 0 ? 2 : 0) + (bound > 0 ? 1 : 0) + (a.grid > 0 ? 1 : 0);
+                        (mode == 1 && records > 0 ? 2 : 0) + (bound > 0 ? 1 : 0) + (a.grid > 0 ? 1 : 0) +
+                        (ctx->tune.tile_order && tiles > 0 ? 3 : 0);
 
     ctx->have_fwd = true;
     ctx->prims = *prims;
@@ -646,6 +660,7 @@ lp_status lp_render_backward(lp_ctx* ctx, const float* dL_dimages, float* dcentr
     lp::BlendArgs a{};
     const lp_tuning& ft = ctx->fwd_tune;   // the backward walks the forward's tiles and masks
     a.grid = blend_grid(ctx, ft, ctx->prims.kind, false, ctx->tiles, exact);
+    a.order = ft.tile_order ? ctx->tile_order.p : nullptr;
     a.rec = ctx->rec.p;
     a.vals = ctx->result_in_1 ? ctx->vals1.p : ctx->vals0.p;
     a.ranges = ctx->ranges.p;
@@ -850,6 +865,7 @@ lp_status lp_render_depth(lp_ctx* ctx, float* depth, void* stream) {
     lp::BlendArgs a{};
     const lp_tuning& ft = ctx->fwd_tune;
     a.grid = blend_grid(ctx, ft, ctx->prims.kind, true, ctx->tiles, ctx->fwd_exact);
+    a.order = ft.tile_order ? ctx->tile_order.p : nullptr;
     a.rec = ctx->rec.p;
     a.vals = ctx->result_in_1 ? ctx->vals1.p : ctx->vals0.p;
     a.ranges = ctx->ranges.p;
@@ -876,6 +892,7 @@ lp_status lp_count_pairs(lp_ctx* ctx, long long* counts) {
     lp::BlendArgs a{};
     const lp_tuning& ft = ctx->fwd_tune;
     a.grid = blend_grid(ctx, ft, ctx->prims.kind, true, ctx->tiles, ctx->fwd_exact);
+    a.order = ft.tile_order ? ctx->tile_order.p : nullptr;
     a.rec = ctx->rec.p;
     a.vals = ctx->result_in_1 ? ctx->vals1.p : ctx->vals0.p;
     a.ranges = ctx->ranges.p;

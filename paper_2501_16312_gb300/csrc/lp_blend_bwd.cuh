@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(TILE * TILE / PIX, bwd_min_blocks<TILE * TILE 
     CamsParam cams, float bg0, float bg1, float bg2, const float* __restrict__ dimage,
     const uint32_t* __restrict__ last_in, const float* __restrict__ tl_in, float* __restrict__ acc,
     int* __restrict__ tile_counter, const uint32_t* __restrict__ contrib, uint32_t cstride,
-    int sparse_lanes) {
+    int sparse_lanes, const uint32_t* __restrict__ order) {
     constexpr int F = Kind<V>::F;
     constexpr int ACC = Acc<V>::kFloats;
     constexpr int NT = TILE * TILE / PIX;
@@ -56,7 +56,8 @@ __global__ void __launch_bounds__(TILE * TILE / PIX, bwd_min_blocks<TILE * TILE 
     const int ly = tid / RW, lx0 = (tid % RW) * PIX;
     for (;;) {
         if (tid == 0) {
-            s_tile = atomicAdd(tile_counter, 1);
+            const int q = atomicAdd(tile_counter, 1);
+            s_tile = order && q < cams.total_tiles ? (int)order[q] : q;
             s_max = 0;
         }
         __syncthreads();
@@ -251,7 +252,7 @@ template <int V, int BATCH, int PIX, int TILE>
 cudaError_t bwd_t(const BlendArgs& a, cudaStream_t st) {
     k_blend_bwd<V, BATCH, PIX, TILE><<<a.grid, TILE * TILE / PIX, 0, st>>>(
         a.rec, a.vals, a.ranges, *a.cams, a.bg[0], a.bg[1], a.bg[2], a.dimage, a.last, a.tl, a.acc,
-        a.tile_counter, a.contrib, a.contrib_stride, a.sparse_lanes);
+        a.tile_counter, a.contrib, a.contrib_stride, a.sparse_lanes, a.order);
     return cudaGetLastError();
 }
 

@@ -34,7 +34,7 @@ __global__ void __launch_bounds__(TILE * TILE / PIX) k_blend_fwd(
     CamsParam cams, float bg0, float bg1, float bg2, float* __restrict__ image,
     uint32_t* __restrict__ last_out, float* __restrict__ tl_out, int* __restrict__ tile_counter,
     unsigned long long* __restrict__ pair_counts, float* __restrict__ depth_out,
-    uint32_t* __restrict__ contrib, uint32_t cstride) {
+    uint32_t* __restrict__ contrib, uint32_t cstride, const uint32_t* __restrict__ order) {
     constexpr bool COUNT = MODE == 1;
     constexpr bool DEPTH = MODE == 2;
     constexpr float kStop = DEPTH ? 0.5f : kStopT;
@@ -50,7 +50,10 @@ __global__ void __launch_bounds__(TILE * TILE / PIX) k_blend_fwd(
     const bool write_mask = !DEPTH && contrib != nullptr;
     unsigned long long n_iter = 0, n_eval = 0, n_hit = 0, n_eval_last = 0;
     for (;;) {
-        if (tid == 0) s_tile = atomicAdd(tile_counter, 1);
+        if (tid == 0) {
+            const int q = atomicAdd(tile_counter, 1);
+            s_tile = order && q < cams.total_tiles ? (int)order[q] : q;
+        }
         __syncthreads();
         const int tile = s_tile;
         if (tile >= cams.total_tiles) break;
@@ -192,15 +195,15 @@ cudaError_t fwd_t(const BlendArgs& a, cudaStream_t st) {
     if (a.depth)
         k_blend_fwd<V, BATCH, PIX, 2, TILE><<<a.grid, NT, 0, st>>>(
             a.rec, a.vals, a.ranges, *a.cams, a.bg[0], a.bg[1], a.bg[2], a.image, a.last, a.tl,
-            a.tile_counter, a.pair_counts, a.depth, nullptr, 0u);
+            a.tile_counter, a.pair_counts, a.depth, nullptr, 0u, a.order);
     else if (a.count)
         k_blend_fwd<V, BATCH, PIX, 1, TILE><<<a.grid, NT, 0, st>>>(
             a.rec, a.vals, a.ranges, *a.cams, a.bg[0], a.bg[1], a.bg[2], a.image, a.last, a.tl,
-            a.tile_counter, a.pair_counts, nullptr, a.contrib, a.contrib_stride);
+            a.tile_counter, a.pair_counts, nullptr, a.contrib, a.contrib_stride, a.order);
     else
         k_blend_fwd<V, BATCH, PIX, 0, TILE><<<a.grid, NT, 0, st>>>(
             a.rec, a.vals, a.ranges, *a.cams, a.bg[0], a.bg[1], a.bg[2], a.image, a.last, a.tl,
-            a.tile_counter, a.pair_counts, nullptr, a.contrib, a.contrib_stride);
+            a.tile_counter, a.pair_counts, nullptr, a.contrib, a.contrib_stride, a.order);
     return cudaGetLastError();
 }
 

@@ -323,7 +323,7 @@ __global__ void __launch_bounds__(threads_x<TILE>()) k_blend_fwd_x(
     CamsParam cams, float bg0, float bg1, float bg2, float* __restrict__ image,
     uint32_t* __restrict__ last_out, float* __restrict__ tl_out, int* __restrict__ tile_counter,
     unsigned long long* __restrict__ pair_counts, float* __restrict__ depth_out,
-    uint32_t* __restrict__ contrib, uint32_t cstride) {
+    uint32_t* __restrict__ contrib, uint32_t cstride, const uint32_t* __restrict__ order) {
     constexpr int PIX = pix_x<TILE>(), NT = threads_x<TILE>(), RW = TILE / PIX, BATCH = kBatchX;
     constexpr bool COUNT = MODE == 1, DEPTH = MODE == 2;
     constexpr float kStop = DEPTH ? 0.5f : kStopT;
@@ -335,7 +335,10 @@ __global__ void __launch_bounds__(threads_x<TILE>()) k_blend_fwd_x(
     const bool write_mask = !DEPTH && contrib != nullptr;
     unsigned long long n_iter = 0, n_eval = 0, n_hit = 0, n_eval_last = 0;
     for (;;) {
-        if (tid == 0) s_tile = atomicAdd(tile_counter, 1);
+        if (tid == 0) {
+            const int q = atomicAdd(tile_counter, 1);
+            s_tile = order && q < cams.total_tiles ? (int)order[q] : q;
+        }
         __syncthreads();
         const int tile = s_tile;
         if (tile >= cams.total_tiles) break;
@@ -466,7 +469,8 @@ __global__ void __launch_bounds__(threads_x<TILE>()) k_blend_bwd_x(
     const float* __restrict__ rec, const uint32_t* __restrict__ vals, const uint2* __restrict__ ranges,
     CamsParam cams, float bg0, float bg1, float bg2, const float* __restrict__ dimage,
     const uint32_t* __restrict__ last_in, const float* __restrict__ tl_in, float* __restrict__ acc,
-    int* __restrict__ tile_counter, const uint32_t* __restrict__ contrib, uint32_t cstride) {
+    int* __restrict__ tile_counter, const uint32_t* __restrict__ contrib, uint32_t cstride,
+    const uint32_t* __restrict__ order) {
     constexpr int F = Kind<V>::F;
     constexpr int ACC = AccX<V>::kFloats;
     constexpr int PIX = pix_x<TILE>(), NT = threads_x<TILE>(), RW = TILE / PIX, BATCH = kBatchX;
@@ -478,7 +482,8 @@ __global__ void __launch_bounds__(threads_x<TILE>()) k_blend_bwd_x(
     const int ly = tid / RW, lx0 = (tid % RW) * PIX;
     for (;;) {
         if (tid == 0) {
-            s_tile = atomicAdd(tile_counter, 1);
+            const int q = atomicAdd(tile_counter, 1);
+            s_tile = order && q < cams.total_tiles ? (int)order[q] : q;
             s_max = 0;
         }
         __syncthreads();
@@ -882,7 +887,7 @@ cudaError_t fwd_x_t(int V, const BlendArgs& a, cudaStream_t st) {
 #define FWD(v, m)                                                                                        \
     k_blend_fwd_x<v, m, TILE><<<a.grid, threads_x<TILE>(), 0, st>>>(                                    \
         a.rec, a.vals, a.ranges, *a.cams, a.bg[0], a.bg[1], a.bg[2], a.image, a.last, a.tl, a.tile_counter, \
-        a.pair_counts, a.depth, m == 2 ? nullptr : a.contrib, a.contrib_stride)
+        a.pair_counts, a.depth, m == 2 ? nullptr : a.contrib, a.contrib_stride, a.order)
     const int m = a.depth ? 2 : (a.count ? 1 : 0);
     if (V == 6) {
         if (m == 2) FWD(6, 2); else if (m == 1) FWD(6, 1); else FWD(6, 0);
@@ -898,11 +903,11 @@ cudaError_t bwd_x_t(int V, const BlendArgs& a, cudaStream_t st) {
     if (V == 6)
         k_blend_bwd_x<6, TILE><<<a.grid, threads_x<TILE>(), 0, st>>>(
             a.rec, a.vals, a.ranges, *a.cams, a.bg[0], a.bg[1], a.bg[2], a.dimage, a.last, a.tl, a.acc,
-            a.tile_counter, a.contrib, a.contrib_stride);
+            a.tile_counter, a.contrib, a.contrib_stride, a.order);
     else
         k_blend_bwd_x<4, TILE><<<a.grid, threads_x<TILE>(), 0, st>>>(
             a.rec, a.vals, a.ranges, *a.cams, a.bg[0], a.bg[1], a.bg[2], a.dimage, a.last, a.tl, a.acc,
-            a.tile_counter, a.contrib, a.contrib_stride);
+            a.tile_counter, a.contrib, a.contrib_stride, a.order);
     return cudaGetLastError();
 }
 

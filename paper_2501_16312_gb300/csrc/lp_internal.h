@@ -63,6 +63,11 @@ cudaError_t launch_emit_sorted(const uint32_t* order, const uint32_t* counts_sor
 cudaError_t launch_ranges32(const uint32_t* keys, const uint32_t* n_dev, long long bound,
                             const int* status, uint2* ranges, int sms, cudaStream_t st);
 
+// Longest-list-first tile order (order: tiles words; scratch: 68 words,
+// zero before the first call, left zero by each call).
+cudaError_t launch_tile_order(const uint2* ranges, long long tiles, uint32_t* order, uint32_t* scratch,
+                              cudaStream_t st);
+
 struct BlendArgs {
     int grid;
     const float* rec;
@@ -79,6 +84,7 @@ struct BlendArgs {
     unsigned long long* pair_counts;
     bool count;
     float* depth;          // depth pass output (forward kernel in depth mode when non-null)
+    const uint32_t* order = nullptr;   // queue position -> tile (null: tiles in index order)
     uint32_t contrib_stride = 0;   // words per warp of the contributor mask
     int sparse_lanes = 8;          // backward: per-lane atomics up to this many contributing lanes
     uint32_t* contrib;     // per warp w of a tile (its bits at contrib + w * contrib_stride), one

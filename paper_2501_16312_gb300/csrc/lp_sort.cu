@@ -441,7 +441,88 @@ __global__ void __launch_bounds__(256) k_ranges(const K* __restrict__ keys,
     }
 }
 
+// ------------------------------------------------- longest-list-first order
+// The persistent blends take tiles from one queue; taking the tiles with
+// the longest lists first keeps a long tile from starting last and running
+// alone at the end.  Tiles are counting-sorted by floor(log2(list length))
+// into kOrderBuckets buckets, longest bucket first, empty tiles last; the
+// order within a bucket is whatever the block atomics give (each tile's
+// result does not depend on when it is processed).
+constexpr int kOrderBuckets = 34;   // 0: empty, 1 + floor(log2(len)) for len >= 1
+constexpr int kOrderThreads = 256;
+
+__device__ __forceinline__ int order_bucket(uint2 r) {
+    const uint32_t len = r.y - r.x;
+    return len == 0u ? 0 : 32 - __clz(len);   // 1 .. 33
+}
+
+__global__ void __launch_bounds__(kOrderThreads) k_order_count(const uint2* __restrict__ ranges, int T,
+                                                               uint32_t* __restrict__ cnt) {
+    __shared__ uint32_t h[kOrderBuckets];
+    if (threadIdx.x < kOrderBuckets) h[threadIdx.x] = 0;
+    __syncthreads();
+    const int t = blockIdx.x * kOrderThreads + threadIdx.x;
+    if (t < T) atomicAdd(&h[order_bucket(ranges[t])], 1u);
+    __syncthreads();
+    if (threadIdx.x < kOrderBuckets && h[threadIdx.x]) atomicAdd(&cnt[threadIdx.x], h[threadIdx.x]);
+}
+
+// One warp: cursor[b] = number of tiles in buckets longer than b (the empty
+// bucket 0 goes last); the counts are cleared for the next call.
+__global__ void __launch_bounds__(32) k_order_base(uint32_t* __restrict__ cnt, uint32_t* __restrict__ cursor) {
+    const int lane = threadIdx.x;
+    // lane l handles buckets 33 - l and, for l < 2, 1 - l (descending order)
+    const int b0 = kOrderBuckets - 1 - lane;
+    const uint32_t c0 = cnt[b0];
+    const uint32_t c1 = lane < 2 ? cnt[1 - lane] : 0u;
+    uint32_t x = c0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    const uint32_t total32 = __shfl_sync(0xffffffffu, x, 31);
+    cursor[b0] = x - c0;
+    const uint32_t c1a = __shfl_sync(0xffffffffu, c1, 0);   // bucket 1, then bucket 0
+    if (lane == 0) cursor[1] = total32;
+    if (lane == 1) cursor[0] = total32 + c1a;
+    __syncwarp();
+    cnt[b0] = 0u;
+    if (lane < 2) cnt[1 - lane] = 0u;
+}
+
+__global__ void __launch_bounds__(kOrderThreads) k_order_scatter(const uint2* __restrict__ ranges, int T,
+                                                                 uint32_t* __restrict__ cursor,
+                                                                 uint32_t* __restrict__ order) {
+    __shared__ uint32_t h[kOrderBuckets];
+    __shared__ uint32_t base[kOrderBuckets];
+    if (threadIdx.x < kOrderBuckets) h[threadIdx.x] = 0;
+    __syncthreads();
+    const int t = blockIdx.x * kOrderThreads + threadIdx.x;
+    int b = 0;
+    uint32_t rank = 0;
+    if (t < T) {
+        b = order_bucket(ranges[t]);
+        rank = atomicAdd(&h[b], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x < kOrderBuckets && h[threadIdx.x]) base[threadIdx.x] = atomicAdd(&cursor[threadIdx.x], h[threadIdx.x]);
+    __syncthreads();
+    if (t < T) order[base[b] + rank] = (uint32_t)t;
+}
+
 }  // namespace
+
+cudaError_t launch_tile_order(const uint2* ranges, long long tiles, uint32_t* order, uint32_t* scratch,
+                              cudaStream_t st) {
+    if (tiles <= 0) return cudaSuccess;
+    const int T = (int)tiles;
+    const int nb = (T + kOrderThreads - 1) / kOrderThreads;
+    k_order_count<<<nb, kOrderThreads, 0, st>>>(ranges, T, scratch);
+    k_order_base<<<1, 32, 0, st>>>(scratch, scratch + kOrderBuckets);
+    k_order_scatter<<<nb, kOrderThreads, 0, st>>>(ranges, T, scratch + kOrderBuckets, order);
+    return cudaGetLastError();
+}
 
 int scan_blocks(long long n) { return (int)((n + kScanTile - 1) / kScanTile); }
 

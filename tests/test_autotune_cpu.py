@@ -10,7 +10,7 @@ import pytest
 from paper_2501_16312_gb300 import autotune
 
 BASE = dict(tile=16, batch=64, blocks_per_sm=0, sort_mode=0, pixels_per_thread=4, chain_split=0,
-            sparse_lanes=8, radix_bits=8)
+            sparse_lanes=8, radix_bits=8, tile_order=0)
 
 
 def stage_model(k):
@@ -80,7 +80,7 @@ def test_search_picks_each_groups_best_in_order():
                 chain_split=1, sparse_lanes=16)
     assert entry["tuning"] == want
     assert knobs == want                                # the winners are left applied
-    assert len(entry["trials"]) == 8 + 12 + 2 + 2
+    assert len(entry["trials"]) == 8 + 12 + 2 + 3 + 2
     # the sort group is judged on its own stages only
     assert entry["best_ms"]["sort_mode+radix_bits"] == pytest.approx(0.45)
     # the tile group on the sort and blend stages together
@@ -99,7 +99,7 @@ def test_search_ties_keep_the_first_candidate():
             "blend_bwd": 1.0, "chain": 1.0}
     entry = autotune.search(knobs.update, lambda: flat, BASE)
     assert entry["tuning"] == dict(BASE, sort_mode=0, radix_bits=4, tile=8, pixels_per_thread=1, batch=32,
-                                   chain_split=0, sparse_lanes=8)
+                                   chain_split=0, sparse_lanes=4)
 
 
 def test_cache_key_buckets():
@@ -136,7 +136,7 @@ def test_tune_caches_reuses_and_restores_timing(fake_cuda, tmp_path):
     entry = autotune.tune(rast, prims, cams, reps=2, cache=cache)
     want = dict(BASE, sort_mode=1, radix_bits=11, pixels_per_thread=4, batch=64, chain_split=1, sparse_lanes=16)
     assert entry["tuning"] == want and rast.knobs == want
-    assert rast.measured == 24 * 3                       # 24 trials x (warm-up + 2 timed)
+    assert rast.measured == 27 * 3                       # 27 trials x (warm-up + 2 timed)
     assert rast.timing_calls == [True, False]            # timing restored to off
     stored = json.load(open(cache))
     key = autotune.cache_key("FakeGPU", 6, 10, cams)
@@ -150,7 +150,7 @@ def test_tune_caches_reuses_and_restores_timing(fake_cuda, tmp_path):
     rast3 = FakeRast()
     rast3.set_timing(True)
     autotune.tune(rast3, prims, cams, reps=1, cache=cache, force=True)
-    assert rast3.measured == 24 * 2 and rast3.timing() is True
+    assert rast3.measured == 27 * 2 and rast3.timing() is True
     # other workloads share the file
     autotune.tune(FakeRast(), prims, cams[:1], reps=1, cache=cache)
     assert len(json.load(open(cache))) == 2
