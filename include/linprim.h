@@ -118,6 +118,10 @@ typedef struct {
  *                 longest tile list first (tiles bucketed by the binary
  *                 logarithm of their list length), so that no long tile
  *                 starts last.
+ *   onesweep      0: each radix pass is a histogram, a scan of it and a
+ *                 scatter; 1: one histogram of every digit place up front,
+ *                 then one kernel per pass whose blocks find their digit
+ *                 offsets by decoupled look-back (below 2^30 entries).
  * Every setting renders bit-identical images (a pixel's arithmetic does not
  * depend on the schedule); tile lists are identical for one tile edge and in
  * the paper's per-tile order at each.  chain_split and sparse_lanes change
@@ -134,6 +138,7 @@ typedef struct {
     int sparse_lanes;
     int radix_bits;
     int tile_order;
+    int onesweep;
 } lp_tuning;
 
 /* Sizes of the last forward call (filled by lp_get_stats).                 */
@@ -171,7 +176,7 @@ void lp_destroy(lp_ctx* ctx);
 
 /* Set / read the tuning parameters (defaults: tile 16, batch 64,
  * blocks_per_sm 0, sort_mode 0, pixels_per_thread 4, chain_split 0,
- * sparse_lanes 8, radix_bits 8, tile_order 0).  LP_ERR_INVALID for a value outside the
+ * sparse_lanes 8, radix_bits 8, tile_order 0, onesweep 0).  LP_ERR_INVALID for a value outside the
  * sets above, or a (tile, pixels_per_thread) pair that is not built.        */
 lp_status lp_set_tuning(lp_ctx* ctx, const lp_tuning* t);
 lp_status lp_get_tuning(lp_ctx* ctx, lp_tuning* t);
@@ -296,6 +301,17 @@ lp_status lp_sync_status(lp_ctx* ctx, void* stream);
  * buffer).  Host pointers; errors: LP_ERR_INVALID for NULL, LP_ERR_CUDA.    */
 lp_status lp_set_debug_guard(lp_ctx* ctx, int enabled);
 lp_status lp_check_guards(lp_ctx* ctx, long long* checked, long long* damaged);
+
+/* Failure-path test hook (the paper has no counterpart).  The tile-list sort
+ * runs its passes with a decoupled look-back: each block waits for the
+ * blocks before it to publish their digit counts, every wait bounded to
+ * about a second, after which the block latches LP_ERR_TIMEOUT (returned by
+ * lp_sync_status) and writes nothing outside its buffers.  With block >= 0
+ * and the onesweep tuning on, that block of the first pass of later
+ * forwards on this context publishes nothing, so the blocks after it time
+ * out; the rendered result is then invalid.  -1 (the default) turns it off.
+ * LP_ERR_INVALID below -1.                                                  */
+lp_status lp_debug_sort_stall(lp_ctx* ctx, int block);
 
 /* Sizes of the last forward (host struct).                                 */
 lp_status lp_get_stats(lp_ctx* ctx, lp_stats* out);

@@ -103,13 +103,13 @@ class Rasterizer:
 
     def set_tuning(self, tile=None, batch=None, blocks_per_sm=None, sort_mode=None,
                    pixels_per_thread=None, chain_split=None, sparse_lanes=None, radix_bits=None,
-                   tile_order=None):
+                   tile_order=None, onesweep=None):
         t = _native.lp_tuning()
         _native.check(self.ctx, self.lib.lp_get_tuning(self.ctx, C.byref(t)), "lp_get_tuning")
         for k, v in (("tile", tile), ("batch", batch), ("blocks_per_sm", blocks_per_sm),
                      ("sort_mode", sort_mode), ("pixels_per_thread", pixels_per_thread),
                      ("chain_split", chain_split), ("sparse_lanes", sparse_lanes), ("radix_bits", radix_bits),
-                     ("tile_order", tile_order)):
+                     ("tile_order", tile_order), ("onesweep", onesweep)):
             if v is not None:
                 setattr(t, k, int(v))
         _native.check(self.ctx, self.lib.lp_set_tuning(self.ctx, C.byref(t)), "lp_set_tuning")

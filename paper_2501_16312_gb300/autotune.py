@@ -60,7 +60,8 @@ TILE_PIX = ((8, 1), (8, 2), (16, 2), (16, 4), (32, 2), (32, 4))
 # The search: each group of knobs, its candidates, and the stages it is
 # judged on.  Later groups are timed at the earlier groups' choices.
 GROUPS = (
-    (("sort_mode", "radix_bits"), tuple(itertools.product((0, 1), (4, 6, 8, 11))), SORT_STAGES),
+    (("sort_mode", "radix_bits", "onesweep"), tuple(itertools.product((0, 1), (4, 6, 8, 11), (0, 1))),
+     SORT_STAGES),
     (("tile", "pixels_per_thread", "batch", "blocks_per_sm"),
      tuple((t, p, b, 0) for (t, p), b in itertools.product(TILE_PIX, (32, 64))), SORT_STAGES + BLEND_STAGES),
     (("chain_split",), ((0,), (1,)), ("chain",)),

@@ -39,12 +39,12 @@ constexpr unsigned char kGuardByte = 0xA5;
 struct lp_ctx {
     int device = 0;
     int sms = 0;
-    lp_tuning tune{16, 64, 0, 0, 4, 0, 8, 8, 0};
+    lp_tuning tune{16, 64, 0, 0, 4, 0, 8, 8, 0, 0};
     float aa_kernel = 0.f;      // 2D filter size in pixels (0 = off)
     bool exact = false;         // spans along the true perspective ray
     bool fwd_exact = false;     // mode of the last forward
     uint32_t contrib_stride = 0;
-    lp_tuning fwd_tune{16, 64, 0, 0, 4, 0, 8, 8, 0};   // schedule of the last forward (its tiles, mask layout)
+    lp_tuning fwd_tune{16, 64, 0, 0, 4, 0, 8, 8, 0, 0};   // schedule of the last forward (its tiles, mask layout)
     // densification statistics gathered by forward and backward (null: off)
     float* st_grad_sum = nullptr;
     uint32_t* st_grad_count = nullptr;
@@ -61,6 +61,7 @@ struct lp_ctx {
     DevBuf<float> tl, acc, scratch_image;
     DevBuf<uint32_t> dkeys0, dkeys1, dvals0, dvals1, counts_sorted;   // two-stage sort
     DevBuf<uint32_t> tile_order;     // longest-list-first queue order of the tiles
+    DevBuf<uint32_t> meta;           // per-record face order (ray-space records), read by the chain
     uint32_t* d_order_scratch = nullptr;   // bucket counts and cursors of the order
     int* d_status = nullptr;         // latched status bits
     uint32_t* d_E = nullptr;         // tile-list length of the last forward
@@ -85,6 +86,7 @@ struct lp_ctx {
     bool fwd_timed = false, bwd_timed = false;
 
     bool guard = false;   // canary zones on later allocations (lp_set_debug_guard)
+    int stall_block = -1; // a sort block that publishes nothing (lp_debug_sort_stall)
 
     // every grow-only buffer, with a name (guard checks, release)
     template <typename F> void each_buf(F&& f) {
@@ -94,7 +96,7 @@ struct lp_ctx {
         f(vals0, "values"); f(vals1, "values"); f(ranges, "tile ranges"); f(tl, "pixel state");
         f(acc, "gradient accumulators"); f(scratch_image, "scratch image"); f(dkeys0, "depth keys");
         f(dkeys1, "depth keys"); f(dvals0, "depth values"); f(dvals1, "depth values");
-        f(counts_sorted, "sorted counts"); f(tile_order, "tile order");
+        f(counts_sorted, "sorted counts"); f(tile_order, "tile order"); f(meta, "face orders");
     }
 };
 
@@ -354,6 +356,8 @@ lp_status lp_set_tuning(lp_ctx* ctx, const lp_tuning* t) {
         return fail(ctx, LP_ERR_INVALID, "radix_bits %d not in {4, 6, 8, 11}", t->radix_bits);
     if (t->tile_order != 0 && t->tile_order != 1)
         return fail(ctx, LP_ERR_INVALID, "tile_order %d not in {0, 1}", t->tile_order);
+    if (t->onesweep != 0 && t->onesweep != 1)
+        return fail(ctx, LP_ERR_INVALID, "onesweep %d not in {0, 1}", t->onesweep);
     ctx->tune = *t;
     return LP_OK;
 }
@@ -408,6 +412,7 @@ static lp_status reserve_impl(lp_ctx* ctx, long long records, long long entries,
     const int rf = V ? rec_floats_mode(V, ctx->exact) : rec_floats_max();
     LP_TRY(ensure(ctx, ctx->rec, records * rf, false, "records"));
     LP_TRY(ensure(ctx, ctx->counts, records, false, "counts"));
+    LP_TRY(ensure(ctx, ctx->meta, records, false, "face orders"));
     LP_TRY(ensure(ctx, ctx->offsets, records, false, "offsets"));
     LP_TRY(ensure(ctx, ctx->zbits, records, false, "zbits"));
     LP_TRY(ensure(ctx, ctx->trect, records, false, "tile rects"));
@@ -496,9 +501,11 @@ lp_status lp_render_forward(lp_ctx* ctx, const lp_prims* prims, const lp_camera*
     if (exact)
         LP_CUDA(lp::launch_preprocess_x(V, prims->sh_degree, P, cp, ctx->rec.p, ctx->counts.p, ctx->trect.p,
                                         ctx->zbits.p, st));
-    else
+    else {
+        LP_TRY(ensure(ctx, ctx->meta, records, cap_mode, "face orders"));
         LP_CUDA(lp::launch_preprocess(V, prims->sh_degree, P, cp, ctx->rec.p, ctx->counts.p, ctx->trect.p,
-                                      ctx->zbits.p, st));
+                                      ctx->zbits.p, ctx->meta.p, st));
+    }
     mark(ctx, st, 1, cap_mode);
     const int mode = ctx->tune.sort_mode;
     int passes = 0, passes1 = 0;
@@ -516,7 +523,7 @@ lp_status lp_render_forward(lp_ctx* ctx, const lp_prims* prims, const lp_camera*
         LP_CUDA(lp::launch_depth_keys(ctx->counts.p, ctx->zbits.p, records, ctx->dkeys0.p, ctx->dvals0.p, st));
         LP_CUDA(lp::launch_radix_sort32(ctx->dkeys0.p, ctx->dvals0.p, ctx->dkeys1.p, ctx->dvals1.p, nullptr,
                                         records, 32, ctx->tune.radix_bits, ctx->hist.p, ctx->scan_tmp.p,
-                                        &passes1, st));
+                                        lp::SortCtl{ctx->sms, ctx->d_status, -1, ctx->tune.onesweep != 0}, &passes1, st));
         order = (passes1 & 1) ? ctx->dvals1.p : ctx->dvals0.p;
         LP_CUDA(lp::launch_gather_counts(ctx->counts.p, order, records, ctx->counts_sorted.p, st));
         LP_CUDA(lp::launch_scan(ctx->counts_sorted.p, records, ctx->offsets.p, ctx->scan_tmp.p, ctx->d_E,
@@ -564,7 +571,9 @@ lp_status lp_render_forward(lp_ctx* ctx, const lp_prims* prims, const lp_camera*
         mark(ctx, st, 2, cap_mode);
         key_bits = tile_bits;
         LP_CUDA(lp::launch_radix_sort32(t0, ctx->vals0.p, t1, ctx->vals1.p, ctx->d_E, bound, key_bits,
-                                        ctx->tune.radix_bits, ctx->hist.p, ctx->scan_tmp.p, &passes, st));
+                                        ctx->tune.radix_bits, ctx->hist.p, ctx->scan_tmp.p,
+                                        lp::SortCtl{ctx->sms, ctx->d_status, ctx->stall_block, ctx->tune.onesweep != 0}, &passes,
+                                        st));
         const bool in1 = (passes & 1) != 0;
         svals = in1 ? ctx->vals1.p : ctx->vals0.p;
         mark(ctx, st, 3, cap_mode);
@@ -579,7 +588,8 @@ lp_status lp_render_forward(lp_ctx* ctx, const lp_prims* prims, const lp_camera*
         key_bits = 32 + tile_bits;
         LP_CUDA(lp::launch_radix_sort(ctx->keys0.p, ctx->vals0.p, ctx->keys1.p, ctx->vals1.p, ctx->d_E,
                                       bound, key_bits, ctx->tune.radix_bits, ctx->hist.p, ctx->scan_tmp.p,
-                                      &passes, st));
+                                      lp::SortCtl{ctx->sms, ctx->d_status, ctx->stall_block, ctx->tune.onesweep != 0}, &passes,
+                                        st));
         const bool in1 = (passes & 1) != 0;
         svals = in1 ? ctx->vals1.p : ctx->vals0.p;
         mark(ctx, st, 3, cap_mode);
@@ -618,7 +628,11 @@ lp_status lp_render_forward(lp_ctx* ctx, const lp_prims* prims, const lp_camera*
     }
     mark(ctx, st, 5, cap_mode);
     ctx->fwd_timed = ctx->timing;
-    ctx->launches_fwd = 1 + (records > 0 ? 3 : 0) + (records > 0 ? 1 : 0) + 5 * (passes + passes1) +
+    // kernels of a sort in the onesweep form: histogram and bases, then one per pass
+    const bool sweep = ctx->tune.onesweep != 0;
+    auto sort_kernels = [sweep](int p, long long n) { return p == 0 ? 0 : (sweep && n < (1ll << 30) ? 2 + p : 5 * p); };
+    ctx->launches_fwd = 1 + (records > 0 ? 3 : 0) + (records > 0 ? 1 : 0) + sort_kernels(passes, bound) +
+                        sort_kernels(passes1, records) +
                         (mode == 1 && records > 0 ? 2 : 0) + (bound > 0 ? 1 : 0) + (a.grid > 0 ? 1 : 0) +
                         (ctx->tune.tile_order && tiles > 0 ? 3 : 0);
 
@@ -670,6 +684,9 @@ lp_status lp_render_backward(lp_ctx* ctx, const float* dL_dimages, float* dcentr
     a.last = ctx->last.p;
     a.tl = ctx->tl.p;
     a.acc = ctx->acc.p;
+    // the colour block follows the plane block (ray-space accumulators)
+    a.acc_col = exact ? nullptr
+                      : ctx->acc.p + (size_t)ctx->records * (V == 6 ? lp::Acc<6>::kPlane : lp::Acc<4>::kPlane);
     a.contrib = ctx->contrib.p;
     a.contrib_stride = ctx->contrib_stride;
     a.sparse_lanes = ctx->tune.sparse_lanes;
@@ -693,7 +710,7 @@ lp_status lp_render_backward(lp_ctx* ctx, const float* dL_dimages, float* dcentr
         LP_CUDA(lp::launch_chain_x(V, pr.sh_degree, P, ctx->cams, ctx->rec.p, ctx->counts.p, ctx->acc.p, dcentre,
                                    dverts, dopacity, dsh, accumulate, st));
     else
-        LP_CUDA(lp::launch_chain(V, pr.sh_degree, P, ctx->cams, ctx->rec.p, ctx->counts.p, ctx->acc.p, dcentre,
+        LP_CUDA(lp::launch_chain(V, pr.sh_degree, P, ctx->cams, ctx->meta.p, ctx->counts.p, ctx->acc.p, dcentre,
                                  dverts, dopacity, dsh, accumulate, ctx->tune.chain_split, st));
     mark(ctx, st, 8, cap_mode);
     ctx->bwd_timed = ctx->timing;
@@ -757,6 +774,12 @@ lp_status lp_stage_times(lp_ctx* ctx, float* ms) {
         LP_CUDA(cudaEventElapsedTime(&ms[LP_STAGE_BLEND_BWD], ctx->ev[6], ctx->ev[7]));
         LP_CUDA(cudaEventElapsedTime(&ms[LP_STAGE_CHAIN], ctx->ev[7], ctx->ev[8]));
     }
+    return LP_OK;
+}
+
+lp_status lp_debug_sort_stall(lp_ctx* ctx, int block) {
+    if (!ctx || block < -1) return LP_ERR_INVALID;
+    ctx->stall_block = block;
     return LP_OK;
 }
 

@@ -39,10 +39,10 @@ __global__ void __launch_bounds__(TILE * TILE / PIX, bwd_min_blocks<TILE * TILE 
     const float* __restrict__ rec, const uint32_t* __restrict__ vals, const uint2* __restrict__ ranges,
     CamsParam cams, float bg0, float bg1, float bg2, const float* __restrict__ dimage,
     const uint32_t* __restrict__ last_in, const float* __restrict__ tl_in, float* __restrict__ acc,
+    float* __restrict__ acc_col,
     int* __restrict__ tile_counter, const uint32_t* __restrict__ contrib, uint32_t cstride,
     int sparse_lanes, const uint32_t* __restrict__ order) {
-    constexpr int F = Kind<V>::F;
-    constexpr int ACC = Acc<V>::kFloats;
+    constexpr int ACC = Acc<V>::kPlane;
     constexpr int NT = TILE * TILE / PIX;
     constexpr int RW = TILE / PIX;
     constexpr int MW = BATCH / 32;   // contributor-mask words per batch
@@ -180,7 +180,8 @@ __global__ void __launch_bounds__(TILE * TILE / PIX, bwd_min_blocks<TILE * TILE 
                         }
                     }
                 }
-                float* A = acc + (size_t)p.rec * ACC;
+                float* A = acc + (size_t)p.rec * ACC;        // plane moments
+                float* Ac = acc_col + (size_t)p.rec * 4;     // colour and density
                 // plane gradients use offsets (px - X0, py - Y0) from the anchor
                 const float lyc = (float)ly + p.dy0;
                 // warps with at most sparse_lanes contributing lanes (a tuning
@@ -189,10 +190,10 @@ __global__ void __launch_bounds__(TILE * TILE / PIX, bwd_min_blocks<TILE * TILE 
                 if (__popc(bal) <= sparse_lanes) {
                     // few contributing lanes: each adds its own terms
                     if (anyc) {
-                        atomicAdd(A + 3 * F + 0, gr0);
-                        atomicAdd(A + 3 * F + 1, gr1);
-                        atomicAdd(A + 3 * F + 2, gr2);
-                        atomicAdd(A + 3 * F + 3, gsig);
+                        atomicAdd(Ac + 0, gr0);
+                        atomicAdd(Ac + 1, gr1);
+                        atomicAdd(Ac + 2, gr2);
+                        atomicAdd(Ac + 3, gsig);
 #pragma unroll
                         for (int i = 0; i < PIX; ++i) {
                             if (c[i]) {
@@ -208,15 +209,51 @@ __global__ void __launch_bounds__(TILE * TILE / PIX, bwd_min_blocks<TILE * TILE 
                     }
                     continue;
                 }
-                {
+                if constexpr (PIX <= 2) {
+                    // the colour and sigma terms and the (x, y, 1) moments of
+                    // up to four faces in one 16-value butterfly; sixteen lanes
+                    // then add one total each (measured faster than separate
+                    // butterflies with one or two pixels per thread, slower
+                    // with four, whose face terms cost twice as much to build)
+                    used = __reduce_or_sync(0xffffffffu, used);
+                    int fq[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        fq[q] = used ? __ffs(used) - 1 : -1;
+                        used &= used - 1;
+                    }
+                    float hv[16];
+                    hv[0] = gr0; hv[1] = gr1; hv[2] = gr2; hv[3] = gsig;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        float mx = 0.f, m1 = 0.f;
+#pragma unroll
+                        for (int i = 0; i < PIX; ++i) {
+                            const float lxc = (float)(lx0 + i) + p.dx0;
+                            const float v = c[i] ? (fq[q] == sf[i] ? -gsp[i] : (fq[q] == sb[i] ? gsp[i] : 0.f)) : 0.f;
+                            mx = fmaf(v, lxc, mx);
+                            m1 += v;
+                        }
+                        hv[4 + 3 * q] = mx;
+                        hv[5 + 3 * q] = m1 * lyc;
+                        hv[6 + 3 * q] = m1;
+                    }
+                    const float t = warp_sum_multi<16>(hv, lane);
+                    const int k = warp_sum_index<16>(lane);
+                    if ((lane & 1) == 0) {
+                        const int q = (k - 4) / 3;
+                        if (k < 4) atomicAdd(Ac + k, t);
+                        else if (fq[q] >= 0) atomicAdd(A + 3 * fq[q] + (k - 4 - 3 * q), t);
+                    }
+                } else {
                     // colour and sigma: four totals, one per lane group of 8
                     float hv[4] = {gr0, gr1, gr2, gsig};
                     const float t = warp_sum_multi<4>(hv, lane);
-                    if ((lane & 7) == 0) atomicAdd(A + 3 * F + warp_sum_index<4>(lane), t);
+                    if ((lane & 7) == 0) atomicAdd(Ac + warp_sum_index<4>(lane), t);
+                    used = __reduce_or_sync(0xffffffffu, used);
                 }
-                used = __reduce_or_sync(0xffffffffu, used);
-                // two faces per butterfly: (x, y, 1) moments of both in one
-                // 8-value reduction, six lanes then add one total each
+                // (further) faces two per butterfly: (x, y, 1) moments of both
+                // in one 8-value reduction, six lanes then add one total each
                 while (used) {
                     const int f1 = __ffs(used) - 1;
                     used &= used - 1;
@@ -252,7 +289,7 @@ template <int V, int BATCH, int PIX, int TILE>
 cudaError_t bwd_t(const BlendArgs& a, cudaStream_t st) {
     k_blend_bwd<V, BATCH, PIX, TILE><<<a.grid, TILE * TILE / PIX, 0, st>>>(
         a.rec, a.vals, a.ranges, *a.cams, a.bg[0], a.bg[1], a.bg[2], a.dimage, a.last, a.tl, a.acc,
-        a.tile_counter, a.contrib, a.contrib_stride, a.sparse_lanes, a.order);
+        a.acc_col, a.tile_counter, a.contrib, a.contrib_stride, a.sparse_lanes, a.order);
     return cudaGetLastError();
 }
 

@@ -112,13 +112,17 @@ __device__ __forceinline__ int meta_face(uint32_t meta, int slot) {
     return (int)((meta >> (4 + 3 * slot)) & 7u);
 }
 
-// Per-record gradient accumulator written by the backward blend:
-//   [3s .. 3s+2]  sums of g * (px - X0, py - Y0, 1) over the pixels where slot
-//                 s bounds the span, g = dL/d(plane depth)
-//   [3F .. 3F+2]  dL/d rgb,  [3F + 3] dL/d sigma
+// Per-record gradient accumulators written by the backward blend, in two
+// blocks of one array (records R):
+//   planes, [R][3F] at the start: [3s .. 3s+2] sums of g * (px - X0, py - Y0,
+//          1) over the pixels where slot s bounds the span, g = dL/d(plane
+//          depth);
+//   colour, [R][4] after the planes: dL/d rgb, dL/d sigma (one 16-byte row).
+// The chain's geometry and colour passes each read only their own block.
 template <int V> struct Acc {
     static constexpr int F = Kind<V>::F;
-    static constexpr int kFloats = 3 * F + 4;   // 28, 16
+    static constexpr int kPlane = 3 * F;           // 24, 12
+    static constexpr int kFloats = kPlane + 4;     // per record over both blocks
 };
 
 // -------------------------------------------------------------------------

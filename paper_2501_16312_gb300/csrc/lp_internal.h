@@ -17,10 +17,13 @@ constexpr bool tile_pix_ok(int tile, int pix) {
 struct CamsParam;
 struct PrimsDev;
 
+// meta: one word per record, the record's face order (as in its word 3),
+// read by the chain; may be null when no chain follows.
 cudaError_t launch_preprocess(int V, int deg, const PrimsDev& P, const CamsParam& cams, float* rec,
-                              uint32_t* counts, int4* trect, uint32_t* zbits, cudaStream_t st);
+                              uint32_t* counts, int4* trect, uint32_t* zbits, uint32_t* meta, cudaStream_t st);
 
-cudaError_t launch_chain(int V, int deg, const PrimsDev& P, const CamsParam& cams, const float* rec,
+// acc: the backward's accumulators, planes [R][3F] then colour [R][4].
+cudaError_t launch_chain(int V, int deg, const PrimsDev& P, const CamsParam& cams, const uint32_t* meta,
                          const uint32_t* counts, const float* acc, float* dc, float* dv, float* dop,
                          float* dsh, int accumulate, int split, cudaStream_t st);
 
@@ -39,11 +42,26 @@ cudaError_t launch_emit(const uint32_t* counts, const uint32_t* offsets, const i
 
 int sort_blocks(long long bound);
 size_t sort_hist_elems(long long bound);
+// Radix sort control: SMs (grid of the histogram pass), the status word a
+// timed-out look-back latches kStatusTimeout in, and a block of the first
+// pass that publishes nothing (-1: none; a test of the bounded wait).
+struct SortCtl {
+    int sms;
+    int* status;
+    int stall_block;
+    bool onesweep;   // below 2^30 items: the onesweep form (else the per-pass form)
+};
+
 // radix_bits: digit width, 4, 6, 8 or 11 (cudaErrorInvalidValue otherwise);
-// hist holds sort_hist_elems(bound) words, enough for any width.
+// hist holds sort_hist_elems(bound) words, enough for any width.  The sort
+// runs either a histogram, a scan and a scatter per digit place, or (when
+// ctl.onesweep and below 2^30 items) the onesweep form: one histogram pass
+// for all digit places, then one kernel per place with a decoupled look-back
+// whose waits are bounded.
 cudaError_t launch_radix_sort(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1,
                               const uint32_t* n_dev, long long bound, int key_bits, int radix_bits,
-                              uint32_t* hist, uint32_t* scan_tmp, int* passes_out, cudaStream_t st);
+                              uint32_t* hist, uint32_t* scan_tmp, const SortCtl& ctl, int* passes_out,
+                              cudaStream_t st);
 
 cudaError_t launch_ranges(const uint64_t* keys, const uint32_t* n_dev, long long bound,
                           const int* status, uint2* ranges, int sms, cudaStream_t st);
@@ -51,7 +69,8 @@ cudaError_t launch_ranges(const uint64_t* keys, const uint32_t* n_dev, long long
 // two-stage sort: records by depth, then entries by 32-bit tile id
 cudaError_t launch_radix_sort32(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1,
                                 const uint32_t* n_dev, long long bound, int key_bits, int radix_bits,
-                                uint32_t* hist, uint32_t* scan_tmp, int* passes_out, cudaStream_t st);
+                                uint32_t* hist, uint32_t* scan_tmp, const SortCtl& ctl, int* passes_out,
+                                cudaStream_t st);
 cudaError_t launch_depth_keys(const uint32_t* counts, const uint32_t* zbits, long long n, uint32_t* keys,
                               uint32_t* vals, cudaStream_t st);
 cudaError_t launch_gather_counts(const uint32_t* counts, const uint32_t* order, long long n, uint32_t* out,
@@ -79,7 +98,8 @@ struct BlendArgs {
     const float* dimage;   // backward input
     uint32_t* last;
     float* tl;
-    float* acc;
+    float* acc;            // plane accumulators [R][3F]
+    float* acc_col;        // colour and density accumulators [R][4]
     int* tile_counter;
     unsigned long long* pair_counts;
     bool count;

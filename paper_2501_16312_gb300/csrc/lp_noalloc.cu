@@ -40,7 +40,9 @@ constexpr size_t kCountBytes = align256(kMaxPrims * 4);
 constexpr size_t kRectBytes = align256(kMaxPrims * 16);
 constexpr size_t kKeyBytes = align256(kMaxEntries * 8);
 constexpr size_t kValBytes = align256(kMaxEntries * 4);
-constexpr size_t kHistElems = 256 * ((kMaxEntries + 4095) / 4096);
+// the sort's workspace at 8-bit digits: histograms, digit bases and block
+// counters of up to 16 passes, then one status word per (block, digit)
+constexpr size_t kHistElems = 2 * 16 * 256 + 16 + 256 * ((kMaxEntries + 4095) / 4096);
 constexpr size_t kHistBytes = align256(kHistElems * 4);
 constexpr size_t kScanTmpBytes = align256(((kHistElems + 4095) / 4096 + 16) * 4);
 constexpr size_t kRangeBytes = align256(kMaxTiles * 8);
@@ -182,7 +184,7 @@ extern "C" lp_status lp_render_forward_noalloc(const lp_prims* prims, const lp_c
     } while (0)
     // the status word and the tile queue must start at zero
     NA_CUDA(cudaMemsetAsync(d_status, 0, sizeof(int), st));
-    NA_CUDA(lp::launch_preprocess(V, prims->sh_degree, P, cp, rec, counts, trect, zbits, st));
+    NA_CUDA(lp::launch_preprocess(V, prims->sh_degree, P, cp, rec, counts, trect, zbits, nullptr, st));
     NA_CUDA(lp::launch_scan(counts, records, offsets, scan_tmp, d_E, st));
     uint32_t E = 0;
     NA_CUDA(cudaMemcpyAsync(&E, d_E, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
@@ -192,12 +194,12 @@ extern "C" lp_status lp_render_forward_noalloc(const lp_prims* prims, const lp_c
     NA_CUDA(lp::launch_emit(counts, offsets, trect, zbits, records, d_E, E, part, keys0, vals0, kMaxEntries,
                             d_status, st));
     int passes = 0;
-    NA_CUDA(lp::launch_radix_sort(keys0, vals0, keys1, vals1, d_E, E, 32 + bits_for(tiles), 8, hist, scan_tmp,
-                                  &passes, st));
-    const bool in1 = (passes & 1) != 0;
-    NA_CUDA(cudaMemsetAsync(ranges, 0, (size_t)tiles * sizeof(uint2), st));
     int sms = 0;
     NA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    NA_CUDA(lp::launch_radix_sort(keys0, vals0, keys1, vals1, d_E, E, 32 + bits_for(tiles), 8, hist, scan_tmp,
+                                  lp::SortCtl{sms, d_status, -1, false}, &passes, st));
+    const bool in1 = (passes & 1) != 0;
+    NA_CUDA(cudaMemsetAsync(ranges, 0, (size_t)tiles * sizeof(uint2), st));
     NA_CUDA(lp::launch_ranges(in1 ? keys1 : keys0, d_E, E, d_status, ranges, sms, st));
     lp::BlendArgs a{};
     const int pix = 4, batch = 64;

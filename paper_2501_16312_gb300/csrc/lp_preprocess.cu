@@ -41,7 +41,8 @@ template <int V, int DEG>
 __global__ void __launch_bounds__(128) k_preprocess(PrimsDev P, CamsParam cams, float* __restrict__ rec,
                                                     uint32_t* __restrict__ counts,
                                                     int4* __restrict__ trect,
-                                                    uint32_t* __restrict__ zbits) {
+                                                    uint32_t* __restrict__ zbits,
+                                                    uint32_t* __restrict__ meta_out) {
     constexpr int F = Kind<V>::F;
     constexpr int K = (DEG + 1) * (DEG + 1);
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -182,6 +183,7 @@ __global__ void __launch_bounds__(128) k_preprocess(PrimsDev P, CamsParam cams, 
         }
         srec[threadIdx.x * kRow] = make_float4(__int_as_float(g.X0), __int_as_float(g.Y0), sigma,
                                                __uint_as_float(meta));
+        if (meta_out) meta_out[r] = meta;   // the chain reads the face order densely
         // rgb, then the ray-space depth of the centre (the planes are relative to it)
         srec[threadIdx.x * kRow + 1] = make_float4(rgb[0], rgb[1], rgb[2], g.len);
         float4* dst = reinterpret_cast<float4*>(rec + r * Rec<V>::kFloats);
@@ -198,16 +200,19 @@ __global__ void __launch_bounds__(128) k_preprocess(PrimsDev P, CamsParam cams, 
 // gathered, which need both parts per view).  The split form lowers the
 // registers a thread holds (the SH coefficients and their gradients live
 // only in PART 1), which pays where many cameras make the loop long.  The
-// split passes are held to four resident blocks per SM (128 registers; a few
-// spill to L1): the loop waits on memory once per camera, and the extra warps
-// hide more of it than the spills cost.
+// geometry pass is held to four resident blocks per SM (128 registers), the
+// colour pass, which holds 48 SH gradients, to three (170 registers), so that
+// neither spills: the loop waits on memory once per camera, and the resident
+// warps hide it.
 template <int V, int DEG, int PART>
-__global__ void __launch_bounds__(128, PART == 2 ? 1 : 4)
-k_chain(PrimsDev P, CamsParam cams, const float* __restrict__ rec, const uint32_t* __restrict__ counts,
+__global__ void __launch_bounds__(128, PART == 2 ? 1 : (PART == 1 ? 3 : 4))
+k_chain(PrimsDev P, CamsParam cams, const uint32_t* __restrict__ meta_in, const uint32_t* __restrict__ counts,
         const float* __restrict__ acc, float* __restrict__ dcentre, float* __restrict__ dverts,
         float* __restrict__ dopacity, float* __restrict__ dsh, int accumulate) {
     constexpr int F = Kind<V>::F;
     constexpr int K = (DEG + 1) * (DEG + 1);
+    constexpr int KP = Acc<V>::kPlane;
+    const float* acc_col = acc + (size_t)cams.n * P.n * KP;   // the colour block follows the planes
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= P.n) return;
 
@@ -219,16 +224,29 @@ k_chain(PrimsDev P, CamsParam cams, const float* __restrict__ rec, const uint32_
 #pragma unroll
         for (int a = 0; a < 3; ++a) v[k][a] = __ldg(P.verts + ((size_t)i * V + k) * 3 + a);
     const float alpha = __ldg(P.opacity + i);
-    // The fused form re-reads the SH coefficients per camera (L1 hits; 16-byte
-    // loads when a row is a multiple of 16 bytes and the array is 16-byte
-    // aligned); PART 1 keeps them in registers.
-    constexpr bool kVecSH = PART == 2 && (K * 3) % 4 == 0;
+    // The colour passes re-read the SH coefficients per camera (L1 hits;
+    // 16-byte loads when a row is a multiple of 16 bytes and the array is
+    // 16-byte aligned), which leaves the registers to the gradients; other
+    // rows are held in registers, loaded once.  PART 1 stores its gradients
+    // 16 bytes at a time on the same condition.
+    constexpr bool kVecSH = PART != 0 && (K * 3) % 4 == 0;
+    constexpr bool kRow4 = (K * 3) % 4 == 0;
     const bool sh_aligned = ((uintptr_t)P.sh & 15u) == 0;
+    const bool dsh_aligned = ((uintptr_t)dsh & 15u) == 0;
     constexpr int kRegSH = PART != 0 && !kVecSH ? K * 3 : 1;
     float sh_reg[kRegSH];
     if constexpr (kRegSH > 1) {
+        if (kRow4 && sh_aligned) {
+            const float4* s4 = reinterpret_cast<const float4*>(P.sh + (size_t)i * K * 3);
 #pragma unroll
-        for (int q = 0; q < K * 3; ++q) sh_reg[q] = __ldg(P.sh + (size_t)i * K * 3 + q);
+            for (int q = 0; q < (kRow4 ? K * 3 / 4 : 1); ++q) {
+                const float4 t = __ldg(s4 + q);
+                sh_reg[4 * q] = t.x; sh_reg[4 * q + 1] = t.y; sh_reg[4 * q + 2] = t.z; sh_reg[4 * q + 3] = t.w;
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < K * 3; ++q) sh_reg[q] = __ldg(P.sh + (size_t)i * K * 3 + q);
+        }
     }
     const float* shp = P.sh + (size_t)i * K * 3;
     float dmin = CUDART_INF_F;
@@ -263,23 +281,26 @@ k_chain(PrimsDev P, CamsParam cams, const float* __restrict__ rec, const uint32_
         vis &= vis - 1;
         const size_t r = (size_t)cv * P.n + i;
         const CamDev& cm = cams.cam[cv];
-        const float* A = acc + r * Acc<V>::kFloats;
-        // The record's face order is read together with the accumulator row.
-        // Its top four bits are always zero; testing them keeps the load ahead
-        // of the branch on the row.
-        const uint32_t meta = PART != 1 ? __float_as_uint(rec[r * Rec<V>::kFloats + 3]) : 0u;
+        const float* A = acc + r * KP;
+        // The geometry reads the record's face order (dense array) with its
+        // plane row; its top four bits are always zero, and testing them
+        // keeps the load ahead of the branch on the row.  The colour pass
+        // reads one 16-byte row.
+        const uint32_t meta = PART != 1 ? meta_in[r] : 0u;
         bool any = (meta >> 28) != 0u;
-        if constexpr (PART == 1) {
+        float4 col = make_float4(0.f, 0.f, 0.f, 0.f);
+        if constexpr (PART != 0) {
+            col = __ldg(reinterpret_cast<const float4*>(acc_col) + r);
+            any |= col.x != 0.f || col.y != 0.f || col.z != 0.f || col.w != 0.f;
+        }
+        if constexpr (PART != 1) {
 #pragma unroll
-            for (int q = 0; q < 3; ++q) any |= A[3 * F + q] != 0.f;
-        } else {
-#pragma unroll
-            for (int q = 0; q < Acc<V>::kFloats; ++q) any |= A[q] != 0.f;
+            for (int q = 0; q < KP; ++q) any |= A[q] != 0.f;
         }
         if (!any) continue;   // no pixel produced a gradient for this record
         float ga_rgb[3], ga_sig;
-        ga_rgb[0] = A[3 * F]; ga_rgb[1] = A[3 * F + 1]; ga_rgb[2] = A[3 * F + 2];
-        ga_sig = A[3 * F + 3];
+        ga_rgb[0] = col.x; ga_rgb[1] = col.y; ga_rgb[2] = col.z;
+        ga_sig = col.w;
 
         Geom g;
         float gtc[3] = {0.f, 0.f, 0.f};
@@ -454,7 +475,7 @@ k_chain(PrimsDev P, CamsParam cams, const float* __restrict__ rec, const uint32_
         }
         }
 
-        if constexpr (PART != 1) gsigma += ga_sig;
+        if constexpr (PART != 0) gsigma += ga_sig;
     }
     if (P.grad_sum) {
         P.grad_sum[i] += vg_sum;
@@ -467,10 +488,24 @@ k_chain(PrimsDev P, CamsParam cams, const float* __restrict__ rec, const uint32_
         // after PART 0, which wrote (or added) the geometric terms
 #pragma unroll
         for (int a = 0; a < 3; ++a) dcentre[3 * (size_t)i + a] += gc[a];
+        dopacity[i] = accumulate ? dopacity[i] + galpha : galpha;
+        if (kRow4 && dsh_aligned) {
+            float4* d4 = reinterpret_cast<float4*>(dsh + (size_t)i * K * 3);
 #pragma unroll
-        for (int q = 0; q < K * 3; ++q) {
-            float& o = dsh[(size_t)i * K * 3 + q];
-            o = accumulate ? o + gsh[q] : gsh[q];
+            for (int q = 0; q < (kRow4 ? K * 3 / 4 : 1); ++q) {
+                float4 o = make_float4(gsh[4 * q], gsh[4 * q + 1], gsh[4 * q + 2], gsh[4 * q + 3]);
+                if (accumulate) {
+                    const float4 t = d4[q];
+                    o.x += t.x; o.y += t.y; o.z += t.z; o.w += t.w;
+                }
+                d4[q] = o;
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < K * 3; ++q) {
+                float& o = dsh[(size_t)i * K * 3 + q];
+                o = accumulate ? o + gsh[q] : gsh[q];
+            }
         }
         return;
     }
@@ -481,7 +516,7 @@ k_chain(PrimsDev P, CamsParam cams, const float* __restrict__ rec, const uint32_
         for (int k = 0; k < V; ++k)
 #pragma unroll
             for (int a = 0; a < 3; ++a) dverts[((size_t)i * V + k) * 3 + a] += gv[k][a];
-        dopacity[i] += galpha;
+        if constexpr (PART == 2) dopacity[i] += galpha;
         if constexpr (PART == 2) {
 #pragma unroll
             for (int q = 0; q < K * 3; ++q) dsh[(size_t)i * K * 3 + q] += gsh[q];
@@ -493,7 +528,7 @@ k_chain(PrimsDev P, CamsParam cams, const float* __restrict__ rec, const uint32_
         for (int k = 0; k < V; ++k)
 #pragma unroll
             for (int a = 0; a < 3; ++a) dverts[((size_t)i * V + k) * 3 + a] = gv[k][a];
-        dopacity[i] = galpha;
+        if constexpr (PART == 2) dopacity[i] = galpha;
         if constexpr (PART == 2) {
 #pragma unroll
             for (int q = 0; q < K * 3; ++q) dsh[(size_t)i * K * 3 + q] = gsh[q];
@@ -503,25 +538,25 @@ k_chain(PrimsDev P, CamsParam cams, const float* __restrict__ rec, const uint32_
 
 template <int V, int DEG>
 cudaError_t launch_pre_t(const PrimsDev& P, const CamsParam& cams, float* rec, uint32_t* counts,
-                         int4* trect, uint32_t* zbits, cudaStream_t st) {
+                         int4* trect, uint32_t* zbits, uint32_t* meta, cudaStream_t st) {
     const int bs = 128;
     const int grid = (P.n + bs - 1) / bs;
-    if (grid > 0) k_preprocess<V, DEG><<<grid, bs, 0, st>>>(P, cams, rec, counts, trect, zbits);
+    if (grid > 0) k_preprocess<V, DEG><<<grid, bs, 0, st>>>(P, cams, rec, counts, trect, zbits, meta);
     return cudaGetLastError();
 }
 
 template <int V, int DEG>
-cudaError_t launch_chain_t(const PrimsDev& P, const CamsParam& cams, const float* rec,
+cudaError_t launch_chain_t(const PrimsDev& P, const CamsParam& cams, const uint32_t* meta,
                            const uint32_t* counts, const float* acc, float* dc, float* dv, float* dop,
                            float* dsh, int accumulate, int split, cudaStream_t st) {
     const int bs = 128;
     const int grid = (P.n + bs - 1) / bs;
     if (grid > 0) {
         if (P.grad_sum || !split) {
-            k_chain<V, DEG, 2><<<grid, bs, 0, st>>>(P, cams, rec, counts, acc, dc, dv, dop, dsh, accumulate);
+            k_chain<V, DEG, 2><<<grid, bs, 0, st>>>(P, cams, meta, counts, acc, dc, dv, dop, dsh, accumulate);
         } else {
-            k_chain<V, DEG, 0><<<grid, bs, 0, st>>>(P, cams, rec, counts, acc, dc, dv, dop, dsh, accumulate);
-            k_chain<V, DEG, 1><<<grid, bs, 0, st>>>(P, cams, rec, counts, acc, dc, dv, dop, dsh, accumulate);
+            k_chain<V, DEG, 0><<<grid, bs, 0, st>>>(P, cams, meta, counts, acc, dc, dv, dop, dsh, accumulate);
+            k_chain<V, DEG, 1><<<grid, bs, 0, st>>>(P, cams, meta, counts, acc, dc, dv, dop, dsh, accumulate);
         }
     }
     return cudaGetLastError();
@@ -538,16 +573,16 @@ cudaError_t launch_chain_t(const PrimsDev& P, const CamsParam& cams, const float
     }
 
 cudaError_t launch_preprocess(int V, int deg, const PrimsDev& P, const CamsParam& cams, float* rec,
-                              uint32_t* counts, int4* trect, uint32_t* zbits, cudaStream_t st) {
-#define CALL(v, d) launch_pre_t<v, d>(P, cams, rec, counts, trect, zbits, st)
+                              uint32_t* counts, int4* trect, uint32_t* zbits, uint32_t* meta, cudaStream_t st) {
+#define CALL(v, d) launch_pre_t<v, d>(P, cams, rec, counts, trect, zbits, meta, st)
     LP_DISPATCH(V, deg, CALL)
 #undef CALL
 }
 
-cudaError_t launch_chain(int V, int deg, const PrimsDev& P, const CamsParam& cams, const float* rec,
+cudaError_t launch_chain(int V, int deg, const PrimsDev& P, const CamsParam& cams, const uint32_t* meta,
                          const uint32_t* counts, const float* acc, float* dc, float* dv, float* dop,
                          float* dsh, int accumulate, int split, cudaStream_t st) {
-#define CALL(v, d) launch_chain_t<v, d>(P, cams, rec, counts, acc, dc, dv, dop, dsh, accumulate, split, st)
+#define CALL(v, d) launch_chain_t<v, d>(P, cams, meta, counts, acc, dc, dv, dop, dsh, accumulate, split, st)
     LP_DISPATCH(V, deg, CALL)
 #undef CALL
 }

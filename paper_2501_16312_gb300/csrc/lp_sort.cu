@@ -231,6 +231,10 @@ constexpr int kSortPerWarp = 512;
 constexpr int kSortChunk = kSortWarps * kSortPerWarp;   // 4096
 constexpr int kScatterIPT = kSortPerWarp / 32;   // items per lane
 constexpr int kRadixMaxBits = 11;
+// onesweep status words: flag in the top two bits, a count below
+constexpr uint32_t kFlagAgg = 1u << 30, kFlagInc = 2u << 30, kFlagMask = 3u << 30, kValMask = (1u << 30) - 1u;
+constexpr long long kSweepWaitCycles = 2000000000ll;   // about a second: bound of one look-back wait
+constexpr long long kSweepMaxItems = 1ll << 30;         // counts must fit in the status words
 
 // Digit counts of one block's chunk: each warp counts its sub-chunk into its
 // own shared histogram (less contention than one histogram per block); with
@@ -294,11 +298,19 @@ constexpr size_t scatter_smem_bytes() {
            (size_t)(1 << RB) * 4;
 }
 
-template <typename K, int RB>
+// SWEEP (one pass of the onesweep form): blocks take their chunk by a
+// dynamic block id, so that a block only ever waits for blocks that have
+// started, publish their digit counts, and find the counts of all earlier
+// blocks by decoupled look-back; the digits' global starts come from the
+// histogram of all passes made up front.  Otherwise offs holds the scanned
+// (digit, block) histogram of this pass.
+template <typename K, int RB, bool SWEEP>
 __global__ void __launch_bounds__(kSortThreads, sizeof(K) == 4 ? 4 : 3) k_radix_scatter(
     const K* __restrict__ kin, const uint32_t* __restrict__ vin,
     K* __restrict__ kout, uint32_t* __restrict__ vout, const uint32_t* __restrict__ n_dev,
-    long long bound, int shift, int nblocks, const uint32_t* __restrict__ offs) {
+    long long bound, int shift, int nblocks, const uint32_t* __restrict__ offs,
+    const uint32_t* __restrict__ digit_base, uint32_t* __restrict__ status, uint32_t* __restrict__ counter,
+    int* __restrict__ err, int stall_block) {
     constexpr int R = 1 << RB;
     constexpr uint32_t DMASK = (2u << RB) - 1u;        // digit field of a packed item (sentinel included)
     constexpr int DPT = R > kSortThreads ? R / kSortThreads : 1;   // digits per thread in the block scan
@@ -308,10 +320,17 @@ __global__ void __launch_bounds__(kSortThreads, sizeof(K) == 4 ? 4 : 3) k_radix_
     uint32_t* wcnt = svals + kSortChunk;       // [kSortWarps][R]
     uint32_t* gbase = wcnt + kSortWarps * R;   // [R]
     __shared__ uint32_t wsum[kSortWarps];
+    __shared__ uint32_t s_bid;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const long long n = n_dev ? min((long long)*n_dev, bound) : bound;
-    const long long bbase = (long long)blockIdx.x * kSortChunk;
-    if (bbase >= n) return;   // uniform over the block
+    uint32_t bid = blockIdx.x;
+    if constexpr (SWEEP) {
+        if (tid == 0) s_bid = atomicAdd(counter, 1u);
+        __syncthreads();
+        bid = s_bid;
+    }
+    const long long bbase = (long long)bid * kSortChunk;
+    if (bbase >= n) return;   // uniform over the block (never waited for: its id is past every chunk)
     for (int d = lane; d < R; d += 32) wcnt[w * R + d] = 0;
     __syncwarp();
 
@@ -369,6 +388,45 @@ __global__ void __launch_bounds__(kSortThreads, sizeof(K) == 4 ? 4 : 3) k_radix_
     __syncthreads();
     uint32_t dstart = x - tsum;
     for (int ww = 0; ww < w; ++ww) dstart += wsum[ww];
+    uint32_t before[DPT];   // SWEEP: items of digit d in all earlier blocks
+    if constexpr (SWEEP) {
+        // publish this block's count of each digit (inclusive at once for the
+        // first block), then walk back over earlier blocks until one that
+        // has published its inclusive count; every wait is bounded in time
+#pragma unroll
+        for (int q = 0; q < DPT; ++q) {
+            const int d = tid * DPT + q;
+            if (d < R && (int)bid != stall_block)
+                *(volatile uint32_t*)(status + (size_t)bid * R + d) = (bid == 0 ? kFlagInc : kFlagAgg) | tot[q];
+        }
+#pragma unroll
+        for (int q = 0; q < DPT; ++q) {
+            const int d = tid * DPT + q;
+            uint32_t pre = 0u;
+            if (d < R && bid > 0) {
+                for (long long j = (long long)bid - 1; j >= 0; --j) {
+                    const volatile uint32_t* sp = status + (size_t)j * R + d;
+                    uint32_t v = *sp;
+                    if (!(v & kFlagMask)) {
+                        const long long t0 = clock64();
+                        while (!((v = *sp) & kFlagMask)) {
+                            if (clock64() - t0 > kSweepWaitCycles) {
+                                atomicOr(err, kStatusTimeout);   // the output is invalid, never out of bounds
+                                v = kFlagInc;
+                                break;
+                            }
+                            __nanosleep(64);
+                        }
+                    }
+                    pre += v & kValMask;
+                    if (v & kFlagInc) break;
+                }
+                if ((int)bid != stall_block)
+                    *(volatile uint32_t*)(status + (size_t)bid * R + d) = kFlagInc | ((pre + tot[q]) & kValMask);
+            }
+            before[q] = pre;
+        }
+    }
 #pragma unroll
     for (int q = 0; q < DPT; ++q) {
         const int d = tid * DPT + q;
@@ -376,7 +434,8 @@ __global__ void __launch_bounds__(kSortThreads, sizeof(K) == 4 ? 4 : 3) k_radix_
 #pragma unroll
             for (int ww = 0; ww < kSortWarps; ++ww) wcnt[ww * R + d] += dstart;
             // global position of block-local index i of digit d: gbase[d] + i (mod 2^32)
-            gbase[d] = offs[(size_t)d * nblocks + blockIdx.x] - dstart;
+            if constexpr (SWEEP) gbase[d] = digit_base[d] + before[q] - dstart;
+            else gbase[d] = offs[(size_t)d * nblocks + blockIdx.x] - dstart;
         }
         dstart += tot[q];
     }
@@ -397,8 +456,64 @@ __global__ void __launch_bounds__(kSortThreads, sizeof(K) == 4 ? 4 : 3) k_radix_
     for (int i = tid; i < cnt; i += kSortThreads) {
         const K k = skeys[i];
         const uint32_t g = gbase[(uint32_t)(k >> shift) & (R - 1)] + (uint32_t)i;
-        kout[g] = k;
-        vout[g] = svals[i];
+        if (!SWEEP || (long long)g < n) {   // a timed-out look-back leaves g unknown: stay in bounds
+            kout[g] = k;
+            vout[g] = svals[i];
+        }
+    }
+}
+
+// Onesweep: the histograms of every digit place at once (one read of the
+// keys), then their exclusive scans, one block per place.
+template <typename K, int RB>
+__global__ void __launch_bounds__(kSortThreads) k_sweep_hist(const K* __restrict__ keys,
+                                                             const uint32_t* __restrict__ n_dev, long long bound,
+                                                             int passes, uint32_t* __restrict__ ghist) {
+    constexpr int R = 1 << RB;
+    extern __shared__ uint32_t sh[];   // [passes][R]
+    const int tid = threadIdx.x;
+    for (int i = tid; i < passes * R; i += kSortThreads) sh[i] = 0u;
+    __syncthreads();
+    const long long n = n_dev ? min((long long)*n_dev, bound) : bound;
+    for (long long q = (long long)blockIdx.x * kSortThreads + tid; q < n; q += (long long)gridDim.x * kSortThreads) {
+        const K k = keys[q];
+        for (int p = 0; p < passes; ++p) atomicAdd(&sh[p * R + ((uint32_t)(k >> (p * RB)) & (R - 1))], 1u);
+    }
+    __syncthreads();
+    for (int i = tid; i < passes * R; i += kSortThreads)
+        if (sh[i]) atomicAdd(&ghist[i], sh[i]);
+}
+
+template <int RB>
+__global__ void __launch_bounds__(kSortThreads) k_sweep_base(const uint32_t* __restrict__ ghist,
+                                                             uint32_t* __restrict__ gbase) {
+    constexpr int R = 1 << RB;
+    constexpr int DPT = R > kSortThreads ? R / kSortThreads : 1;
+    __shared__ uint32_t wsum[kSortWarps];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const uint32_t* h = ghist + (size_t)blockIdx.x * R;
+    uint32_t c[DPT], t = 0u;
+#pragma unroll
+    for (int q = 0; q < DPT; ++q) {
+        const int d = tid * DPT + q;
+        c[q] = d < R ? h[d] : 0u;
+        t += c[q];
+    }
+    uint32_t x = t;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    uint32_t run = x - t;
+    for (int ww = 0; ww < w; ++ww) run += wsum[ww];
+#pragma unroll
+    for (int q = 0; q < DPT; ++q) {
+        const int d = tid * DPT + q;
+        if (d < R) gbase[(size_t)blockIdx.x * R + d] = run;
+        run += c[q];
     }
 }
 
@@ -424,14 +539,15 @@ __global__ void __launch_bounds__(256) k_gather_counts(const uint32_t* __restric
     if (k < n) out[k] = counts[order[k]];
 }
 
-// Skipped entirely when the emission overflowed: the list then holds stale
-// entries whose tile ids need not be valid, and all ranges stay empty.
+// Skipped entirely when the emission overflowed or a sort wait expired: the
+// list then holds stale entries whose tile ids need not be valid, and all
+// ranges stay empty.
 template <typename K, int SHIFT>
 __global__ void __launch_bounds__(256) k_ranges(const K* __restrict__ keys,
                                                 const uint32_t* __restrict__ n_dev, long long bound,
                                                 const int* __restrict__ status,
                                                 uint2* __restrict__ ranges) {
-    if (*status & kStatusCapacity) return;
+    if (*status & (kStatusCapacity | kStatusTimeout)) return;
     const long long n = min((long long)*n_dev, bound);
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
@@ -568,7 +684,7 @@ int sort_blocks(long long bound) { return (int)((bound + kSortChunk - 1) / kSort
 
 // The scatter's shared memory exceeds the 48 KB default for 64-bit keys and
 // for wide digits: opt in once per device.
-template <typename K, int RB>
+template <typename K, int RB, bool SWEEP>
 static cudaError_t scatter_attr() {
     constexpr size_t bytes = scatter_smem_bytes<K, RB>();
     if (bytes <= 48 * 1024) return cudaSuccess;
@@ -578,31 +694,63 @@ static cudaError_t scatter_attr() {
     if (e != cudaSuccess) return e;
     const unsigned long long bit = 1ull << (dev & 63);
     if (done.load() & bit) return cudaSuccess;
-    e = cudaFuncSetAttribute(k_radix_scatter<K, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    e = cudaFuncSetAttribute(k_radix_scatter<K, RB, SWEEP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e == cudaSuccess) done.fetch_or(bit);
     return e;
 }
 
+// Workspace words of the onesweep form: the histograms and digit bases of up
+// to kMaxPasses places, one block counter per place, one status word per
+// (block, digit) reused by every pass.
+constexpr int kMaxPasses = 16;
+size_t sweep_ws_words(int nb, int R) { return (size_t)2 * kMaxPasses * R + kMaxPasses + (size_t)nb * R; }
+
 template <typename K, int RB>
 static cudaError_t radix_sort_t(K* k0, uint32_t* v0, K* k1, uint32_t* v1, const uint32_t* n_dev,
                                 long long bound, int key_bits, uint32_t* hist, uint32_t* scan_tmp,
-                                int* passes_out, cudaStream_t st) {
+                                const SortCtl& ctl, int* passes_out, cudaStream_t st) {
+    constexpr int R = 1 << RB;
     const int nb = sort_blocks(bound);
     int passes = 0;
     if (nb > 0) {
-        cudaError_t ea = scatter_attr<K, RB>();
-        if (ea != cudaSuccess) return ea;
         K* kin = k0; uint32_t* vin = v0;
         K* kout = k1; uint32_t* vout = v1;
-        for (int shift = 0; shift < key_bits; shift += RB) {
-            k_radix_hist<K, RB><<<nb, kSortThreads, 0, st>>>(kin, n_dev, bound, shift, nb, hist);
-            cudaError_t e = launch_scan(hist, (long long)(1 << RB) * nb, hist, scan_tmp, nullptr, st);
+        if (ctl.onesweep && bound < kSweepMaxItems) {
+            cudaError_t ea = scatter_attr<K, RB, true>();
+            if (ea != cudaSuccess) return ea;
+            const int np = (key_bits + RB - 1) / RB;
+            uint32_t* ghist = hist;
+            uint32_t* gbase = ghist + (size_t)kMaxPasses * R;
+            uint32_t* counter = gbase + (size_t)kMaxPasses * R;
+            uint32_t* status = counter + kMaxPasses;
+            cudaError_t e = cudaMemsetAsync(ghist, 0, sizeof(uint32_t) * ((size_t)2 * kMaxPasses * R + kMaxPasses), st);
             if (e != cudaSuccess) return e;
-            k_radix_scatter<K, RB><<<nb, kSortThreads, scatter_smem_bytes<K, RB>(), st>>>(
-                kin, vin, kout, vout, n_dev, bound, shift, nb, hist);
-            K* tk = kin; kin = kout; kout = tk;
-            uint32_t* tv = vin; vin = vout; vout = tv;
-            ++passes;
+            const int hb = nb < ctl.sms * 4 ? nb : ctl.sms * 4;
+            k_sweep_hist<K, RB><<<hb, kSortThreads, sizeof(uint32_t) * np * R, st>>>(kin, n_dev, bound, np, ghist);
+            k_sweep_base<RB><<<np, kSortThreads, 0, st>>>(ghist, gbase);
+            for (int p = 0; p < np; ++p) {
+                e = cudaMemsetAsync(status, 0, sizeof(uint32_t) * (size_t)nb * R, st);
+                if (e != cudaSuccess) return e;
+                k_radix_scatter<K, RB, true><<<nb, kSortThreads, scatter_smem_bytes<K, RB>(), st>>>(
+                    kin, vin, kout, vout, n_dev, bound, p * RB, nb, nullptr, gbase + (size_t)p * R, status,
+                    counter + p, ctl.status, p == 0 ? ctl.stall_block : -1);
+                K* tk = kin; kin = kout; kout = tk;
+                uint32_t* tv = vin; vin = vout; vout = tv;
+                ++passes;
+            }
+        } else {
+            cudaError_t ea = scatter_attr<K, RB, false>();
+            if (ea != cudaSuccess) return ea;
+            for (int shift = 0; shift < key_bits; shift += RB) {
+                k_radix_hist<K, RB><<<nb, kSortThreads, 0, st>>>(kin, n_dev, bound, shift, nb, hist);
+                cudaError_t e = launch_scan(hist, (long long)R * nb, hist, scan_tmp, nullptr, st);
+                if (e != cudaSuccess) return e;
+                k_radix_scatter<K, RB, false><<<nb, kSortThreads, scatter_smem_bytes<K, RB>(), st>>>(
+                    kin, vin, kout, vout, n_dev, bound, shift, nb, hist, nullptr, nullptr, nullptr, nullptr, -1);
+                K* tk = kin; kin = kout; kout = tk;
+                uint32_t* tv = vin; vin = vout; vout = tv;
+                ++passes;
+            }
         }
     }
     *passes_out = passes;
@@ -612,33 +760,39 @@ static cudaError_t radix_sort_t(K* k0, uint32_t* v0, K* k1, uint32_t* v1, const 
 template <typename K>
 static cudaError_t radix_sort_rb(K* k0, uint32_t* v0, K* k1, uint32_t* v1, const uint32_t* n_dev,
                                  long long bound, int key_bits, int radix_bits, uint32_t* hist,
-                                 uint32_t* scan_tmp, int* passes_out, cudaStream_t st) {
+                                 uint32_t* scan_tmp, const SortCtl& ctl, int* passes_out, cudaStream_t st) {
     switch (radix_bits) {
-        case 4: return radix_sort_t<K, 4>(k0, v0, k1, v1, n_dev, bound, key_bits, hist, scan_tmp, passes_out, st);
-        case 6: return radix_sort_t<K, 6>(k0, v0, k1, v1, n_dev, bound, key_bits, hist, scan_tmp, passes_out, st);
-        case 8: return radix_sort_t<K, 8>(k0, v0, k1, v1, n_dev, bound, key_bits, hist, scan_tmp, passes_out, st);
+        case 4: return radix_sort_t<K, 4>(k0, v0, k1, v1, n_dev, bound, key_bits, hist, scan_tmp, ctl, passes_out, st);
+        case 6: return radix_sort_t<K, 6>(k0, v0, k1, v1, n_dev, bound, key_bits, hist, scan_tmp, ctl, passes_out, st);
+        case 8: return radix_sort_t<K, 8>(k0, v0, k1, v1, n_dev, bound, key_bits, hist, scan_tmp, ctl, passes_out, st);
         case 11:
-            return radix_sort_t<K, 11>(k0, v0, k1, v1, n_dev, bound, key_bits, hist, scan_tmp, passes_out, st);
+            return radix_sort_t<K, 11>(k0, v0, k1, v1, n_dev, bound, key_bits, hist, scan_tmp, ctl, passes_out, st);
         default: return cudaErrorInvalidValue;
     }
 }
 
 cudaError_t launch_radix_sort(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1,
                               const uint32_t* n_dev, long long bound, int key_bits, int radix_bits,
-                              uint32_t* hist, uint32_t* scan_tmp, int* passes_out, cudaStream_t st) {
-    return radix_sort_rb<uint64_t>(k0, v0, k1, v1, n_dev, bound, key_bits, radix_bits, hist, scan_tmp,
+                              uint32_t* hist, uint32_t* scan_tmp, const SortCtl& ctl, int* passes_out,
+                              cudaStream_t st) {
+    return radix_sort_rb<uint64_t>(k0, v0, k1, v1, n_dev, bound, key_bits, radix_bits, hist, scan_tmp, ctl,
                                    passes_out, st);
 }
 
 cudaError_t launch_radix_sort32(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1,
                                 const uint32_t* n_dev, long long bound, int key_bits, int radix_bits,
-                                uint32_t* hist, uint32_t* scan_tmp, int* passes_out, cudaStream_t st) {
-    return radix_sort_rb<uint32_t>(k0, v0, k1, v1, n_dev, bound, key_bits, radix_bits, hist, scan_tmp,
+                                uint32_t* hist, uint32_t* scan_tmp, const SortCtl& ctl, int* passes_out,
+                                cudaStream_t st) {
+    return radix_sort_rb<uint32_t>(k0, v0, k1, v1, n_dev, bound, key_bits, radix_bits, hist, scan_tmp, ctl,
                                    passes_out, st);
 }
 
-// Histogram words of one pass at the widest digit (sizes every width).
-size_t sort_hist_elems(long long bound) { return (size_t)(1 << kRadixMaxBits) * (size_t)sort_blocks(bound); }
+// Workspace words of a sort of up to `bound` items at any digit width: the
+// onesweep form's histograms, bases, counters and status words, or the
+// per-pass (digit, block) histogram of the form used past 2^30 items.
+size_t sort_hist_elems(long long bound) {
+    return sweep_ws_words(sort_blocks(bound), 1 << kRadixMaxBits);
+}
 
 cudaError_t launch_depth_keys(const uint32_t* counts, const uint32_t* zbits, long long n, uint32_t* keys,
                               uint32_t* vals, cudaStream_t st) {

@@ -10,7 +10,7 @@ import pytest
 from paper_2501_16312_gb300 import autotune
 
 BASE = dict(tile=16, batch=64, blocks_per_sm=0, sort_mode=0, pixels_per_thread=4, chain_split=0,
-            sparse_lanes=8, radix_bits=8, tile_order=0)
+            sparse_lanes=8, radix_bits=8, tile_order=0, onesweep=0)
 
 
 def stage_model(k):
@@ -80,9 +80,9 @@ def test_search_picks_each_groups_best_in_order():
                 chain_split=1, sparse_lanes=16)
     assert entry["tuning"] == want
     assert knobs == want                                # the winners are left applied
-    assert len(entry["trials"]) == 8 + 12 + 2 + 3 + 2
+    assert len(entry["trials"]) == 16 + 12 + 2 + 3 + 2
     # the sort group is judged on its own stages only
-    assert entry["best_ms"]["sort_mode+radix_bits"] == pytest.approx(0.45)
+    assert entry["best_ms"]["sort_mode+radix_bits+onesweep"] == pytest.approx(0.45)
     # the tile group on the sort and blend stages together
     assert entry["best_ms"]["tile+pixels_per_thread+batch+blocks_per_sm"] == pytest.approx(0.45 + 1.45 + 3.0)
     # each trial of a later group ran at the earlier groups' winners
@@ -136,7 +136,7 @@ def test_tune_caches_reuses_and_restores_timing(fake_cuda, tmp_path):
     entry = autotune.tune(rast, prims, cams, reps=2, cache=cache)
     want = dict(BASE, sort_mode=1, radix_bits=11, pixels_per_thread=4, batch=64, chain_split=1, sparse_lanes=16)
     assert entry["tuning"] == want and rast.knobs == want
-    assert rast.measured == 27 * 3                       # 27 trials x (warm-up + 2 timed)
+    assert rast.measured == 35 * 3                       # 35 trials x (warm-up + 2 timed)
     assert rast.timing_calls == [True, False]            # timing restored to off
     stored = json.load(open(cache))
     key = autotune.cache_key("FakeGPU", 6, 10, cams)
@@ -150,7 +150,7 @@ def test_tune_caches_reuses_and_restores_timing(fake_cuda, tmp_path):
     rast3 = FakeRast()
     rast3.set_timing(True)
     autotune.tune(rast3, prims, cams, reps=1, cache=cache, force=True)
-    assert rast3.measured == 27 * 2 and rast3.timing() is True
+    assert rast3.measured == 35 * 2 and rast3.timing() is True
     # other workloads share the file
     autotune.tune(FakeRast(), prims, cams[:1], reps=1, cache=cache)
     assert len(json.load(open(cache))) == 2

@@ -107,3 +107,42 @@ def test_guard_zones_are_checked():
     r.backward(torch.ones(3 * w.pixels, device="cuda:0"))
     g = r.check_guards()
     assert g["checked"] >= 10 and g["damaged"] == 0, g
+
+
+@pytest.mark.parametrize("sort_mode", [0, 1])
+def test_sort_wait_times_out_and_recovers(sort_mode):
+    """The onesweep sort's look-back waits are bounded: when one block of the first
+    pass never publishes its counts (a test hook), the blocks after it give
+    up after about a second, latch LP_ERR_TIMEOUT and write nothing past any
+    buffer; with the hook off, the next call renders correctly again."""
+    import time
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2501_16312_gb300 import LinPrimError, Primitives, Rasterizer, _native
+    w = scenes.workload(1, scale=0.5)            # 5k octahedra, 512x512: tens of sort blocks
+    prims = Primitives.from_scene(w.scene, "cuda:0")
+    ref = Rasterizer(0)
+    ref.set_tuning(sort_mode=sort_mode)
+    img_ref = ref.forward(prims, w.cameras).clone()
+    torch.cuda.synchronize()
+    assert ref.stats()["entries"] > 3 * 4096
+
+    rast = Rasterizer(0)
+    rast.set_debug_guard(True)
+    rast.set_tuning(sort_mode=sort_mode, onesweep=1)
+    rast.forward(prims, w.cameras)               # sizes the workspace (with guard zones)
+    torch.cuda.synchronize()
+    _native.check(rast.ctx, rast.lib.lp_debug_sort_stall(rast.ctx, 1), "lp_debug_sort_stall")
+    t0 = time.time()
+    rast.forward(prims, w.cameras)
+    with pytest.raises(LinPrimError) as e:
+        rast.sync_status()
+    assert e.value.status == _native.LP_ERR_TIMEOUT
+    assert time.time() - t0 < 30
+    g = rast.check_guards()
+    assert g["checked"] > 0 and g["damaged"] == 0, g
+    _native.check(rast.ctx, rast.lib.lp_debug_sort_stall(rast.ctx, -1), "lp_debug_sort_stall")
+    img = rast.forward(prims, w.cameras)
+    rast.sync_status()
+    assert torch.equal(img, img_ref)

@@ -51,16 +51,18 @@ def _oracle_keys(i):
     return _KEYS[i]
 
 
+@pytest.mark.parametrize("onesweep", [0, 1])
 @pytest.mark.parametrize("sort_mode", [0, 1])
 @pytest.mark.parametrize("index", [2, 3])
-def test_full_size_tile_lists_bit_exact(rast, index, sort_mode):
+def test_full_size_tile_lists_bit_exact(rast, index, sort_mode, onesweep):
     """Every camera of the workload in one batched forward: per-record tile
     counts, keys and values equal the oracle's stable (tile, depth, record)
-    sort bit for bit; no workspace guard zone is touched."""
+    sort bit for bit, in both sort forms; no workspace guard zone is
+    touched."""
     w = _workload(index)
     base = rast.tuning()
     try:
-        rast.set_tuning(sort_mode=sort_mode)
+        rast.set_tuning(sort_mode=sort_mode, onesweep=onesweep)
         gpu_forward_backward(rast, w.scene, w.cameras, (0, 0, 0))
         k, v = rast.debug_keys()
         counts = rast.debug_counts()

@@ -39,15 +39,17 @@ CASES = {
 }
 
 
+@pytest.mark.parametrize("onesweep", [0, 1])
 @pytest.mark.parametrize("tile", [8, 16, 32])
 @pytest.mark.parametrize("sort_mode", [0, 1])
 @pytest.mark.parametrize("case", sorted(CASES))
-def test_tile_lists_bit_exact(rast, case, sort_mode, tile):
+def test_tile_lists_bit_exact(rast, case, sort_mode, tile, onesweep):
     """Sec. 3.2 "Global Sorting and Tiling" at every tile edge the tuner
-    may pick: counts, keys and values equal the oracle's bit for bit."""
+    may pick and in both sort forms: counts, keys and values equal the
+    oracle's bit for bit."""
     w = CASES[case]()
     base = rast.tuning()
-    rast.set_tuning(sort_mode=sort_mode, tile=tile, pixels_per_thread=2)
+    rast.set_tuning(sort_mode=sort_mode, tile=tile, pixels_per_thread=2, onesweep=onesweep)
     try:
         gpu_forward_backward(rast, w.scene, w.cameras, (0, 0, 0))
     finally:
@@ -402,16 +404,16 @@ def test_every_tuning_renders_identical_images(rast):
     try:
         rast.set_tuning(tile=16, pixels_per_thread=4)
         img16, g16 = gpu_forward_backward(rast, w.scene, w.cameras, (0.1, 0.1, 0.1), dL)
-        for (tile, pix), sm, rb, batch, bps, (cs, sl), to in itertools.product(
-                tile_pix, [0, 1], [4, 11, 8], [32, 128], [0, 1], [(0, 0), (1, 32)], [0, 1]):
-            if (rb != 8 or to) and (batch, bps, cs) != (32, 0, 0):
-                continue    # the digit width and the tile order touch one stage each
+        for (tile, pix), sm, rb, batch, bps, (cs, sl), to, ow in itertools.product(
+                tile_pix, [0, 1], [4, 11, 8], [32, 128], [0, 1], [(0, 0), (1, 32)], [0, 1], [0, 1]):
+            if (rb != 8 or to or ow) and (batch, bps, cs) != (32, 0, 0):
+                continue    # the digit width, sort form and tile order touch one stage each
             rast.set_tuning(tile=tile, sort_mode=sm, radix_bits=rb, pixels_per_thread=pix, batch=batch,
-                            blocks_per_sm=bps, chain_split=cs, sparse_lanes=sl, tile_order=to)
+                            blocks_per_sm=bps, chain_split=cs, sparse_lanes=sl, tile_order=to, onesweep=ow)
             img, g = gpu_forward_backward(rast, w.scene, w.cameras, (0.1, 0.1, 0.1), dL)
             np.testing.assert_array_equal(img, img16)
             for k in g:
-                assert rel_l2(g[k], g16[k]) <= 1e-5, (tile, sm, rb, pix, batch, bps, cs, sl, to, k)
+                assert rel_l2(g[k], g16[k]) <= 1e-5, (tile, sm, rb, pix, batch, bps, cs, sl, to, ow, k)
     finally:
         rast.set_tuning(**base)
 
