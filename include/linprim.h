@@ -111,9 +111,10 @@ typedef struct {
  *   sparse_lanes  0..32: a backward warp in which at most this many lanes
  *                 contribute to a record adds their terms with one atomic
  *                 per lane and value instead of reducing over the warp.
- *   radix_bits    digit width of the radix sort passes: 4, 6, 8 or 11 bits
- *                 (ceil(key bits / radix_bits) passes, each with a histogram
- *                 of 2^radix_bits bins per 4096 keys).
+ *   radix_bits    widest digit of the radix sort passes: 4, 6, 8 or 11 bits.
+ *                 A sort of k key bits takes p = ceil(k / radix_bits)
+ *                 passes of ceil(k / p) bits each (at least 4), each with a
+ *                 histogram of 2^bits bins per 4096 keys.
  *   tile_order    0: the persistent blends take tiles in index order; 1:
  *                 longest tile list first (tiles bucketed by the binary
  *                 logarithm of their list length), so that no long tile
@@ -264,8 +265,10 @@ lp_status lp_reserve(lp_ctx* ctx, long long max_records, long long max_entries,
  * Limits: at most 2^30 pixels and 2^30 tiles over all cameras, each camera at
  * most 65536 pixels on a side (LP_ERR_INVALID otherwise).  Tile-list offsets
  * are 32-bit: the list (one entry per primitive, camera and covered tile)
- * must stay below 2^32 entries, about 51 GB of keys and values.  A longer
- * list is not detected; it wraps.                                            */
+ * must stay below 2^32 - 1 entries, about 51 GB of keys and values.  The
+ * length is summed in 64 bits; a longer list returns LP_ERR_CAPACITY before
+ * anything is sized for it (under stream capture it renders nothing and
+ * lp_sync_status returns LP_ERR_CAPACITY).                                   */
 lp_status lp_render_forward(lp_ctx* ctx, const lp_prims* prims, const lp_camera* cams,
                             int n_cams, const float bg[3], float* images, void* stream);
 
@@ -312,6 +315,20 @@ lp_status lp_check_guards(lp_ctx* ctx, long long* checked, long long* damaged);
  * out; the rendered result is then invalid.  -1 (the default) turns it off.
  * LP_ERR_INVALID below -1.                                                  */
 lp_status lp_debug_sort_stall(lp_ctx* ctx, int block);
+
+/* Test hook for the tile-count scan (Sec. 3.2 "Global Sorting and Tiling":
+ * a record's entries start at the exclusive prefix sum of the tile counts).
+ * Runs the forward's scan on n device counts: offsets[i] (device, n words)
+ * receives the 32-bit exclusive prefix sum, and *total (host) the sum, or
+ * 0xFFFFFFFF when the sum reaches 2^32 - 1: the scan keeps its total in 64
+ * bits, and a forward whose tile list would be that long returns
+ * LP_ERR_CAPACITY (with a stream capture, lp_sync_status does) rather than
+ * wrap its 32-bit offsets.  Synchronises the stream.  Returns
+ * LP_ERR_CAPACITY on such a total, LP_ERR_INVALID for bad arguments or a
+ * status still latched from an earlier call, else LP_OK.  Invalidates the
+ * context's last forward for lp_render_backward.                            */
+lp_status lp_debug_scan(lp_ctx* ctx, const unsigned int* counts, long long n, unsigned int* offsets,
+                        unsigned int* total, void* stream);
 
 /* Sizes of the last forward (host struct).                                 */
 lp_status lp_get_stats(lp_ctx* ctx, lp_stats* out);

@@ -240,6 +240,20 @@ class Rasterizer:
                       "lp_debug_pixel_state")
         return last[:m], tl[:m]
 
+    def debug_scan(self, counts):
+        """The forward's tile-count scan on a uint32 numpy array: (exclusive
+        offsets as uint32, total).  Raises LinPrimError (LP_ERR_CAPACITY)
+        when the total reaches 2^32 - 1."""
+        import numpy as np
+        import torch
+        c = np.ascontiguousarray(counts, dtype=np.uint32)
+        d_in = torch.from_numpy(c.view(np.int32).copy()).to(self.device)
+        d_out = torch.empty_like(d_in)
+        total = C.c_uint(0)
+        _native.check(self.ctx, self.lib.lp_debug_scan(self.ctx, d_in.data_ptr(), c.size, d_out.data_ptr(),
+                                                       C.byref(total), self._stream()), "lp_debug_scan")
+        return d_out.cpu().numpy().view(np.uint32), total.value
+
     def set_debug_guard(self, enabled=True):
         """Canary zones after every workspace buffer allocated from now on
         (a debugging aid; see check_guards)."""

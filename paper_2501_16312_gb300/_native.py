@@ -23,7 +23,7 @@ EXPORTS = ("lp_create", "lp_destroy", "lp_set_tuning", "lp_get_tuning", "lp_set_
            "lp_render_forward_noalloc", "lp_params_forward", "lp_params_backward",
            "lp_l1_loss_grad", "lp_adam_step", "lp_render_depth", "lp_set_exact", "lp_get_exact",
            "lp_set_densify_stats", "lp_population_scratch", "lp_population_decide", "lp_population_apply",
-           "lp_set_debug_guard", "lp_check_guards", "lp_debug_sort_stall")
+           "lp_set_debug_guard", "lp_check_guards", "lp_debug_sort_stall", "lp_debug_scan")
 LP_ADAM_MAX_GROUPS = 8
 STAGES = ("preprocess", "scan_emit", "sort", "ranges", "blend_fwd", "blend_bwd", "chain")
 
@@ -110,6 +110,7 @@ def load(path: str = LIB_PATH):
     L.lp_count_pairs.argtypes = [vp, C.POINTER(ll)]
     L.lp_set_debug_guard.argtypes = [vp, i]
     L.lp_debug_sort_stall.argtypes = [vp, i]
+    L.lp_debug_scan.argtypes = [vp, vp, ll, vp, C.POINTER(C.c_uint), vp]
     L.lp_check_guards.argtypes = [vp, C.POINTER(ll), C.POINTER(ll)]
     L.lp_render_depth.argtypes = [vp, vp, vp]
     L.lp_set_exact.argtypes = [vp, i]

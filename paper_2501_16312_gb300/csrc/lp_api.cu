@@ -527,9 +527,10 @@ lp_status lp_render_forward(lp_ctx* ctx, const lp_prims* prims, const lp_camera*
         order = (passes1 & 1) ? ctx->dvals1.p : ctx->dvals0.p;
         LP_CUDA(lp::launch_gather_counts(ctx->counts.p, order, records, ctx->counts_sorted.p, st));
         LP_CUDA(lp::launch_scan(ctx->counts_sorted.p, records, ctx->offsets.p, ctx->scan_tmp.p, ctx->d_E,
-                                st));
+                                st, ctx->d_status));
     } else {
-        LP_CUDA(lp::launch_scan(ctx->counts.p, records, ctx->offsets.p, ctx->scan_tmp.p, ctx->d_E, st));
+        LP_CUDA(lp::launch_scan(ctx->counts.p, records, ctx->offsets.p, ctx->scan_tmp.p, ctx->d_E, st,
+                                ctx->d_status));
     }
 
     long long bound;
@@ -537,6 +538,12 @@ lp_status lp_render_forward(lp_ctx* ctx, const lp_prims* prims, const lp_camera*
         LP_CUDA(cudaMemcpyAsync(ctx->h_E, ctx->d_E, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
         LP_CUDA(cudaStreamSynchronize(st));
         bound = *ctx->h_E;
+        if (*ctx->h_E == lp::kListOverflow) {
+            // the scan latched the capacity bit too; clear it, this call reports it
+            LP_CUDA(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), st));
+            ctx->E_host = -1;
+            return fail(ctx, LP_ERR_CAPACITY, "tile list of 2^32 - 1 or more entries");
+        }
         ctx->E_host = bound;
         LP_TRY(ensure(ctx, ctx->keys0, bound, false, "keys"));
         LP_TRY(ensure(ctx, ctx->keys1, bound, false, "keys"));
@@ -773,6 +780,30 @@ lp_status lp_stage_times(lp_ctx* ctx, float* ms) {
         LP_CUDA(cudaEventSynchronize(ctx->ev[8]));
         LP_CUDA(cudaEventElapsedTime(&ms[LP_STAGE_BLEND_BWD], ctx->ev[6], ctx->ev[7]));
         LP_CUDA(cudaEventElapsedTime(&ms[LP_STAGE_CHAIN], ctx->ev[7], ctx->ev[8]));
+    }
+    return LP_OK;
+}
+
+lp_status lp_debug_scan(lp_ctx* ctx, const unsigned int* counts, long long n, unsigned int* offsets,
+                        unsigned int* total, void* stream) {
+    if (!ctx || n < 0 || (n > 0 && (!counts || !offsets)) || !total) return LP_ERR_INVALID;
+    LP_CUDA(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    LP_TRY(ensure(ctx, ctx->scan_tmp, lp::scan_blocks(n) + 1, false, "scan blocks"));
+    int s = 0;
+    LP_CUDA(cudaMemcpyAsync(&s, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    LP_CUDA(cudaStreamSynchronize(st));
+    if (s) return fail(ctx, LP_ERR_INVALID, "a status is latched; read it with lp_sync_status first");
+    LP_CUDA(lp::launch_scan(counts, n, offsets, ctx->scan_tmp.p, ctx->d_E, st, ctx->d_status));
+    LP_CUDA(cudaMemcpyAsync(ctx->h_E, ctx->d_E, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    LP_CUDA(cudaMemcpyAsync(&s, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    LP_CUDA(cudaStreamSynchronize(st));
+    *total = *ctx->h_E;
+    ctx->E_host = -1;
+    ctx->have_fwd = false;
+    if (s & lp::kStatusCapacity) {
+        LP_CUDA(cudaMemset(ctx->d_status, 0, sizeof(int)));
+        return fail(ctx, LP_ERR_CAPACITY, "scan total of 2^32 - 1 or more");
     }
     return LP_OK;
 }

@@ -21,6 +21,18 @@ constexpr float kAlphaScale = 0.99f;  // Eq. 1
 constexpr int kStatusCapacity = 1;
 constexpr int kStatusTimeout = 2;
 
+// Tile-list length the scan writes when the 64-bit total of the tile counts
+// reaches 2^32 - 1: 32-bit list offsets cannot address such a list, so every
+// stage treats it as empty (and the scan latches kStatusCapacity).
+constexpr uint32_t kListOverflow = 0xffffffffu;
+
+// The list length to process: E from the device, capped by the host's bound,
+// or 0 after an overflowed scan.
+__device__ __forceinline__ long long list_len(const uint32_t* n_dev, long long bound) {
+    const uint32_t e = *n_dev;
+    return e == kListOverflow ? 0ll : min((long long)e, bound);
+}
+
 // One camera, pre-digested on the host.  R, T: rows of the world->camera
 // matrix; campos = -R^T T.  Tiles of this camera occupy global tile ids
 // [tile_base, tile_base + tiles_x * tiles_y); its pixels start at pix_base in

@@ -28,8 +28,11 @@ cudaError_t launch_chain(int V, int deg, const PrimsDev& P, const CamsParam& cam
                          float* dsh, int accumulate, int split, cudaStream_t st);
 
 int scan_blocks(long long n);
+// Exclusive scan of n 32-bit counts.  total (optional): their sum, or
+// kListOverflow when it reaches 2^32 - 1, in which case kStatusCapacity is
+// latched in status (optional).
 cudaError_t launch_scan(const uint32_t* in, long long n, uint32_t* out, uint32_t* block_sums,
-                        uint32_t* total, cudaStream_t st);
+                        uint32_t* total, cudaStream_t st, int* status = nullptr);
 
 // Key emission.  n_dev: the list length E on the device (written by the
 // scan), bound: an upper bound of E for grid sizing, part: emit_blocks + 1

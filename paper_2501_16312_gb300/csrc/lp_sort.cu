@@ -66,32 +66,59 @@ __device__ __forceinline__ void scan_load(const uint32_t* __restrict__ in, long 
     }
 }
 
+// Sum of one 64-bit value per thread over the block (every thread gets it).
+__device__ __forceinline__ unsigned long long block_sum_u64(unsigned long long x) {
+    __shared__ unsigned long long warp_tot[kScanThreads / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if (lane == 0) warp_tot[w] = x;
+    __syncthreads();
+    unsigned long long t = 0;
+#pragma unroll
+    for (int k = 0; k < kScanThreads / 32; ++k) t += warp_tot[k];
+    __syncthreads();
+    return t;
+}
+
+// Block totals in 64 bits, saturated to 2^32 - 1 (a block of 4096 counts
+// can exceed 32 bits; the sums kernel then reports the overflow).
 __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t* __restrict__ in, long long n,
                                                               uint32_t* __restrict__ block_sums) {
     const long long base = (long long)blockIdx.x * kScanTile + (long long)threadIdx.x * kScanItems;
     uint32_t v[kScanItems];
     scan_load(in, n, base, ((uintptr_t)in & 15) == 0, v);
-    uint32_t s = 0;
+    unsigned long long s = 0;
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) s += v[k];
-    uint32_t total;
-    block_excl_scan(s, total);
-    if (threadIdx.x == 0) block_sums[blockIdx.x] = total;
+    const unsigned long long total = block_sum_u64(s);
+    if (threadIdx.x == 0) block_sums[blockIdx.x] = total < kListOverflow ? (uint32_t)total : kListOverflow;
 }
 
-// Single block: exclusive scan of the block sums in place; total -> *sum_out.
+// Single block: exclusive scan of the block sums in place; the total goes to
+// *sum_out.  The running total is kept in 64 bits: once it reaches 2^32 - 1
+// the offsets have wrapped, so *sum_out gets kListOverflow and, when status
+// is given, kStatusCapacity is latched.
 __global__ void __launch_bounds__(kScanThreads) k_scan_sums(uint32_t* __restrict__ sums, int nb,
-                                                            uint32_t* __restrict__ sum_out) {
-    uint32_t carry = 0;
+                                                            uint32_t* __restrict__ sum_out,
+                                                            int* __restrict__ status) {
+    unsigned long long carry = 0;
     for (int base = 0; base < nb; base += kScanThreads) {
         const int i = base + threadIdx.x;
         const uint32_t x = i < nb ? sums[i] : 0u;
         uint32_t total;
         const uint32_t ex = block_excl_scan(x, total);
-        if (i < nb) sums[i] = carry + ex;
-        carry += total;
+        if (i < nb) sums[i] = (uint32_t)carry + ex;
+        carry += block_sum_u64(x);
     }
-    if (threadIdx.x == 0 && sum_out) *sum_out = carry;
+    if (threadIdx.x == 0 && sum_out) {
+        if (carry >= kListOverflow) {
+            *sum_out = kListOverflow;
+            if (status) atomicOr(status, kStatusCapacity);
+        } else {
+            *sum_out = (uint32_t)carry;
+        }
+    }
 }
 
 __global__ void __launch_bounds__(kScanThreads) k_scan_down(const uint32_t* __restrict__ in, long long n,
@@ -146,6 +173,7 @@ __global__ void __launch_bounds__(256) k_emit_partition(const uint32_t* __restri
                                                         int nb, uint32_t* __restrict__ part) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b > nb) return;
+    if (*n_dev == kListOverflow) return;   // offsets wrapped: nothing is emitted
     const long long E = min((long long)*n_dev, bound);
     const long long d = min((long long)b * kEmitItems, R + E);
     long long lo = 0, hi = R;
@@ -178,6 +206,7 @@ __global__ void __launch_bounds__(kEmitBlock) k_emit_lb(const uint32_t* __restri
     __shared__ uint32_t s_z[SORTED ? 1 : kEmitItems + 1];
     const int b = blockIdx.x, tid = threadIdx.x;
     const long long Ed = (long long)*n_dev;
+    if (Ed == kListOverflow) return;         // latched by the scan; offsets wrapped
     if (b == 0 && tid == 0 && Ed > cap) atomicOr(status, kStatusCapacity);
     const long long E = min(Ed, bound);
     const long long d0 = (long long)b * kEmitItems;
@@ -250,7 +279,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const K* __restrict
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     for (int d = tid; d < NH * R; d += kSortThreads) (&h[0][0])[d] = 0;
     __syncthreads();
-    const long long n = n_dev ? min((long long)*n_dev, bound) : bound;
+    const long long n = n_dev ? list_len(n_dev, bound) : bound;
     const long long wbase = (long long)blockIdx.x * kSortChunk + (long long)w * kSortPerWarp;
     uint32_t dig[kScatterIPT];
 #pragma unroll
@@ -322,7 +351,7 @@ __global__ void __launch_bounds__(kSortThreads, sizeof(K) == 4 ? 4 : 3) k_radix_
     __shared__ uint32_t wsum[kSortWarps];
     __shared__ uint32_t s_bid;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    const long long n = n_dev ? min((long long)*n_dev, bound) : bound;
+    const long long n = n_dev ? list_len(n_dev, bound) : bound;
     uint32_t bid = blockIdx.x;
     if constexpr (SWEEP) {
         if (tid == 0) s_bid = atomicAdd(counter, 1u);
@@ -474,7 +503,7 @@ __global__ void __launch_bounds__(kSortThreads) k_sweep_hist(const K* __restrict
     const int tid = threadIdx.x;
     for (int i = tid; i < passes * R; i += kSortThreads) sh[i] = 0u;
     __syncthreads();
-    const long long n = n_dev ? min((long long)*n_dev, bound) : bound;
+    const long long n = n_dev ? list_len(n_dev, bound) : bound;
     for (long long q = (long long)blockIdx.x * kSortThreads + tid; q < n; q += (long long)gridDim.x * kSortThreads) {
         const K k = keys[q];
         for (int p = 0; p < passes; ++p) atomicAdd(&sh[p * R + ((uint32_t)(k >> (p * RB)) & (R - 1))], 1u);
@@ -548,7 +577,7 @@ __global__ void __launch_bounds__(256) k_ranges(const K* __restrict__ keys,
                                                 const int* __restrict__ status,
                                                 uint2* __restrict__ ranges) {
     if (*status & (kStatusCapacity | kStatusTimeout)) return;
-    const long long n = min((long long)*n_dev, bound);
+    const long long n = list_len(n_dev, bound);
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
         const uint32_t t = (uint32_t)(keys[i] >> SHIFT);
@@ -643,14 +672,14 @@ cudaError_t launch_tile_order(const uint2* ranges, long long tiles, uint32_t* or
 int scan_blocks(long long n) { return (int)((n + kScanTile - 1) / kScanTile); }
 
 cudaError_t launch_scan(const uint32_t* in, long long n, uint32_t* out, uint32_t* block_sums,
-                        uint32_t* total, cudaStream_t st) {
+                        uint32_t* total, cudaStream_t st, int* status) {
     const int nb = scan_blocks(n);
     if (nb == 0) {
         if (total) return cudaMemsetAsync(total, 0, sizeof(uint32_t), st);
         return cudaSuccess;
     }
     k_scan_reduce<<<nb, kScanThreads, 0, st>>>(in, n, block_sums);
-    k_scan_sums<<<1, kScanThreads, 0, st>>>(block_sums, nb, total);
+    k_scan_sums<<<1, kScanThreads, 0, st>>>(block_sums, nb, total, status);
     k_scan_down<<<nb, kScanThreads, 0, st>>>(in, n, block_sums, out);
     return cudaGetLastError();
 }
@@ -757,18 +786,29 @@ static cudaError_t radix_sort_t(K* k0, uint32_t* v0, K* k1, uint32_t* v1, const 
     return cudaGetLastError();
 }
 
+// radix_bits is the widest digit allowed: the sort takes the fewest passes
+// that digits of that width need for key_bits, and spreads the key bits
+// evenly over them (18-bit keys at most 8 bits wide: three passes of 6 bits;
+// at most 11: two passes of 9), never below 4 bits a digit.
+int digit_bits(int key_bits, int radix_bits) {
+    if (key_bits <= 0) return radix_bits;
+    const int np = (key_bits + radix_bits - 1) / radix_bits;
+    const int w = (key_bits + np - 1) / np;
+    return w < 4 ? 4 : w;
+}
+
 template <typename K>
 static cudaError_t radix_sort_rb(K* k0, uint32_t* v0, K* k1, uint32_t* v1, const uint32_t* n_dev,
                                  long long bound, int key_bits, int radix_bits, uint32_t* hist,
                                  uint32_t* scan_tmp, const SortCtl& ctl, int* passes_out, cudaStream_t st) {
-    switch (radix_bits) {
-        case 4: return radix_sort_t<K, 4>(k0, v0, k1, v1, n_dev, bound, key_bits, hist, scan_tmp, ctl, passes_out, st);
-        case 6: return radix_sort_t<K, 6>(k0, v0, k1, v1, n_dev, bound, key_bits, hist, scan_tmp, ctl, passes_out, st);
-        case 8: return radix_sort_t<K, 8>(k0, v0, k1, v1, n_dev, bound, key_bits, hist, scan_tmp, ctl, passes_out, st);
-        case 11:
-            return radix_sort_t<K, 11>(k0, v0, k1, v1, n_dev, bound, key_bits, hist, scan_tmp, ctl, passes_out, st);
+    if (radix_bits < 4 || radix_bits > kRadixMaxBits) return cudaErrorInvalidValue;
+#define LP_SORT_W(W) \
+    case W: return radix_sort_t<K, W>(k0, v0, k1, v1, n_dev, bound, key_bits, hist, scan_tmp, ctl, passes_out, st);
+    switch (digit_bits(key_bits, radix_bits)) {
+        LP_SORT_W(4) LP_SORT_W(5) LP_SORT_W(6) LP_SORT_W(7) LP_SORT_W(8) LP_SORT_W(9) LP_SORT_W(10) LP_SORT_W(11)
         default: return cudaErrorInvalidValue;
     }
+#undef LP_SORT_W
 }
 
 cudaError_t launch_radix_sort(uint64_t* k0, uint32_t* v0, uint64_t* k1, uint32_t* v1,

@@ -80,9 +80,10 @@ def test_search_picks_each_groups_best_in_order():
                 chain_split=1, sparse_lanes=16)
     assert entry["tuning"] == want
     assert knobs == want                                # the winners are left applied
-    assert len(entry["trials"]) == 16 + 12 + 2 + 3 + 2
-    # the sort group is judged on its own stages only
+    assert len(entry["trials"]) == 16 + 12 + 16 + 2 + 3 + 2
+    # the sort group is judged on its own stages only, at both visits
     assert entry["best_ms"]["sort_mode+radix_bits+onesweep"] == pytest.approx(0.45)
+    assert entry["best_ms"]["sort_mode+radix_bits+onesweep (again)"] == pytest.approx(0.45)
     # the tile group on the sort and blend stages together
     assert entry["best_ms"]["tile+pixels_per_thread+batch+blocks_per_sm"] == pytest.approx(0.45 + 1.45 + 3.0)
     # each trial of a later group ran at the earlier groups' winners
@@ -91,6 +92,28 @@ def test_search_picks_each_groups_best_in_order():
             assert t["blend_fwd"] == pytest.approx(1.45)
         if t.get("tile") == 16:                            # timed at sort mode 1, 11-bit digits
             assert t["scan_emit"] == pytest.approx(0.45 * 0.6)
+
+
+def test_sort_knobs_are_settled_again_at_the_chosen_tile():
+    """The best digit width depends on the key width, and so on the tile
+    edge: here 8-bit digits are best at 16x16 tiles and 11-bit digits at 8x8.
+    8x8 tiles win the tile group even with 8-bit digits, and the second visit
+    of the sort group then moves to 11 bits."""
+    knobs = dict(BASE)
+
+    def model(k):
+        t = stage_model(k)
+        sort = {16: {4: 1.3, 6: 1.1, 8: 1.0, 11: 1.2}, 8: {4: 1.6, 6: 1.25, 8: 1.25, 11: 1.0},
+                32: {4: 2.0, 6: 2.0, 8: 2.0, 11: 2.0}}[k["tile"]][k["radix_bits"]]
+        t.update(scan_emit=sort * 0.6, sort=sort * 0.35, ranges=sort * 0.05)
+        t["blend_fwd"] = 1.0 if k["tile"] == 8 else 1.5
+        return t
+
+    entry = autotune.search(knobs.update, lambda: model(knobs), BASE)
+    assert entry["tuning"]["tile"] == 8
+    assert entry["tuning"]["radix_bits"] == 11
+    first = [t for t in entry["trials"][:16] if t["radix_bits"] == 8 and t["sort_mode"] == 0]
+    assert first and all(t["sort"] == pytest.approx(0.35) for t in first)   # timed at 16x16
 
 
 def test_search_ties_keep_the_first_candidate():
@@ -136,7 +159,7 @@ def test_tune_caches_reuses_and_restores_timing(fake_cuda, tmp_path):
     entry = autotune.tune(rast, prims, cams, reps=2, cache=cache)
     want = dict(BASE, sort_mode=1, radix_bits=11, pixels_per_thread=4, batch=64, chain_split=1, sparse_lanes=16)
     assert entry["tuning"] == want and rast.knobs == want
-    assert rast.measured == 35 * 3                       # 35 trials x (warm-up + 2 timed)
+    assert rast.measured == 51 * 3                       # 51 trials x (warm-up + 2 timed)
     assert rast.timing_calls == [True, False]            # timing restored to off
     stored = json.load(open(cache))
     key = autotune.cache_key("FakeGPU", 6, 10, cams)
@@ -150,7 +173,7 @@ def test_tune_caches_reuses_and_restores_timing(fake_cuda, tmp_path):
     rast3 = FakeRast()
     rast3.set_timing(True)
     autotune.tune(rast3, prims, cams, reps=1, cache=cache, force=True)
-    assert rast3.measured == 35 * 2 and rast3.timing() is True
+    assert rast3.measured == 51 * 2 and rast3.timing() is True
     # other workloads share the file
     autotune.tune(FakeRast(), prims, cams[:1], reps=1, cache=cache)
     assert len(json.load(open(cache))) == 2

@@ -146,3 +146,48 @@ def test_sort_wait_times_out_and_recovers(sort_mode):
     img = rast.forward(prims, w.cameras)
     rast.sync_status()
     assert torch.equal(img, img_ref)
+
+
+def test_scan_total_is_64_bit():
+    """The tile-count scan (Sec. 3.2: a record's entries start at the
+    exclusive prefix sum of the tile counts) keeps its total in 64 bits: a sum
+    below 2^32 - 1 comes back exact with exact 32-bit offsets; a sum that
+    reaches 2^32 - 1 -- within one block of 4096 counts, or only across
+    blocks -- raises LP_ERR_CAPACITY instead of wrapping, and leaves no status
+    latched for the next forward."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2501_16312_gb300 import LinPrimError, Primitives, Rasterizer, _native
+    r = Rasterizer(0)
+    rng = np.random.default_rng(21)
+
+    def exact(c):
+        off, tot = r.debug_scan(c)
+        ex = np.concatenate([[0], np.cumsum(c.astype(np.uint64))[:-1]]) if c.size else np.zeros(0, np.uint64)
+        np.testing.assert_array_equal(off, ex.astype(np.uint32))
+        assert tot == int(c.astype(np.uint64).sum()), (tot, int(c.astype(np.uint64).sum()))
+
+    exact(np.zeros(0, np.uint32))
+    exact(rng.integers(0, 5000, 10007).astype(np.uint32))            # several blocks, ragged tail
+    exact(np.array([0xFFFFFFFE], np.uint32))                          # largest representable list
+    exact(np.full(3, (0xFFFFFFFE) // 3, np.uint32))
+    overflowing = [
+        np.array([0xFFFFFFFF], np.uint32),                            # exactly the sentinel
+        np.full(4, 1 << 30, np.uint32),                               # 2^32 in four counts
+        np.full(4096, 1 << 20, np.uint32),                            # one block's total is 2^32
+        np.concatenate([np.full(4096, 1 << 19, np.uint32),           # each block 2^31, together 2^32
+                        np.full(4096, 1 << 19, np.uint32)]),
+        np.full(40000, 1 << 28, np.uint32),                           # far past 32 bits
+    ]
+    for c in overflowing:
+        with pytest.raises(LinPrimError) as e:
+            r.debug_scan(c)
+        assert e.value.status == _native.LP_ERR_CAPACITY
+    r.sync_status()                                                   # nothing left latched
+    w = scenes.workload(0)
+    prims = Primitives.from_scene(w.scene, "cuda:0")
+    img = r.forward(prims, w.cameras).clone()
+    r.sync_status()
+    ref = Rasterizer(0)
+    assert torch.equal(img, ref.forward(prims, w.cameras))

@@ -51,6 +51,13 @@ def _oracle_keys(i):
     return _KEYS[i]
 
 
+def _oracle_keys8(i):
+    if (i, 8) not in _KEYS:
+        w = _workload(i)
+        _KEYS[(i, 8)] = oracle.keys(w.scene, w.cameras, tile=8)
+    return _KEYS[(i, 8)]
+
+
 @pytest.mark.parametrize("onesweep", [0, 1])
 @pytest.mark.parametrize("sort_mode", [0, 1])
 @pytest.mark.parametrize("index", [2, 3])
@@ -59,23 +66,37 @@ def test_full_size_tile_lists_bit_exact(rast, index, sort_mode, onesweep):
     counts, keys and values equal the oracle's stable (tile, depth, record)
     sort bit for bit, in both sort forms; no workspace guard zone is
     touched."""
+    _check_full_size_keys(rast, index, dict(sort_mode=sort_mode, onesweep=onesweep), _oracle_keys(index))
+
+
+@pytest.mark.parametrize("radix_bits", [8, 11])
+@pytest.mark.parametrize("index", [2, 3])
+def test_full_size_tile_lists_bit_exact_8x8(rast, index, radix_bits):
+    """8x8 tiles (18- and 19-bit tile ids: the two-stage sort runs three
+    passes of 6 or 7 bits at most 8 bits a digit, two of 9 or 10 at most
+    11), the list the tuner picks for these workloads: bit-exact."""
+    _check_full_size_keys(rast, index, dict(sort_mode=1, tile=8, pixels_per_thread=2, radix_bits=radix_bits),
+                          _oracle_keys8(index))
+
+
+def _check_full_size_keys(rast, index, tuning, oracle_keys):
     w = _workload(index)
     base = rast.tuning()
     try:
-        rast.set_tuning(sort_mode=sort_mode, onesweep=onesweep)
+        rast.set_tuning(**tuning)
         gpu_forward_backward(rast, w.scene, w.cameras, (0, 0, 0))
         k, v = rast.debug_keys()
         counts = rast.debug_counts()
     finally:
         rast.set_tuning(**base)
-    ko, vo, co = _oracle_keys(index)
+    ko, vo, co = oracle_keys
     np.testing.assert_array_equal(counts, co)
     assert k.shape == ko.shape, (k.shape, ko.shape)
     np.testing.assert_array_equal(k, ko)
     np.testing.assert_array_equal(v, vo)
     g = rast.check_guards()
     assert g["checked"] > 0 and g["damaged"] == 0, g
-    print(f"workload {index}, sort mode {sort_mode}: {k.shape[0]} entries bit-exact")
+    print(f"workload {index}, {tuning}: {k.shape[0]} entries bit-exact")
 
 
 def _compare_pixels(img_cam, cam, q, scene):

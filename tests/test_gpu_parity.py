@@ -62,6 +62,32 @@ def test_tile_lists_bit_exact(rast, case, sort_mode, tile, onesweep):
     np.testing.assert_array_equal(v, vo)
 
 
+@pytest.mark.parametrize("onesweep", [0, 1])
+@pytest.mark.parametrize("radix_bits", [4, 6, 11])
+@pytest.mark.parametrize("tile", [8, 16])
+@pytest.mark.parametrize("sort_mode", [0, 1])
+def test_tile_lists_bit_exact_every_digit_width(rast, sort_mode, tile, radix_bits, onesweep):
+    """The radix sort at each widest digit the tuner may pick: a sort of k key
+    bits takes ceil(k / radix_bits) passes of evenly spread digits, so these
+    cases run digits of 4, 5, 6, 10 and 11 bits (10k octahedra at 512x512:
+    tile ids of 10 or 12 bits, 32-bit depths, 42- or 44-bit combined keys;
+    the full-size 8x8 cases add 7, 8 and 9).  Keys and values equal the
+    oracle's bit for bit."""
+    w = CASES["cfg1_octa10k"]()
+    base = rast.tuning()
+    rast.set_tuning(sort_mode=sort_mode, tile=tile, pixels_per_thread=2, radix_bits=radix_bits,
+                    onesweep=onesweep)
+    try:
+        gpu_forward_backward(rast, w.scene, w.cameras, (0, 0, 0))
+    finally:
+        rast.set_tuning(**base)
+    k, v = rast.debug_keys()
+    ko, vo, _ = oracle.keys(w.scene, w.cameras, tile=tile)
+    assert k.shape == ko.shape
+    np.testing.assert_array_equal(k, ko)
+    np.testing.assert_array_equal(v, vo)
+
+
 @pytest.mark.parametrize("case", sorted(CASES))
 def test_forward_backward_parity(rast, case):
     w = CASES[case]()
