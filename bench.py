@@ -135,14 +135,12 @@ def blend_flops(F, pairs):
 
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of a
-# kernel from one ncu capture of this workload, keyed by a hash of the kernel's
-# sources: a kernel edited since its capture reports traffic null.
+# kernel from one ncu capture (one pass, -k that kernel, -c 1) of a workload
+# at one blend schedule, with the sha1 of the kernel's sources: a figure is
+# reported only for the same workload (primitives, cameras) and schedule, and
+# is ignored once the sources change (profiles/dram_traffic_blend_bwd_*.md).
 MEASURED_TRAFFIC = {
-    # dram__bytes_read.sum + dram__bytes_write.sum of one full-size launch of a
-    # kernel (one ncu pass), with the sha1 of the kernel's sources; a figure is
-    # ignored once they change (profiles/dram_traffic_blend_bwd_octa500k_8x1264x832.md)
-    "blend_bwd": {"bytes": 470547968 + 86695936, "sources_sha1": "4988b40e8e7583fb738d897550c0f697330b97d6",
-                  "capture": "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum -k regex:k_blend_bwd -s 2 -c 1"},
+    "blend_bwd": [],
 }
 KERNEL_SOURCES = {
     "blend_fwd": ("lp_blend_fwd.cuh", "lp_blend.cuh", "lp_device.cuh"),
@@ -159,11 +157,19 @@ def sources_sha1(kernel):
     return h.hexdigest()
 
 
-def measured_traffic(kernel):
-    t = MEASURED_TRAFFIC.get(kernel)
-    if not t or kernel not in KERNEL_SOURCES or t["sources_sha1"] != sources_sha1(kernel):
+def measured_traffic(kernel, n=None, n_cams=None, tuning=None):
+    """The captured DRAM bytes of one launch of kernel on this workload and
+    schedule, or None."""
+    if kernel not in KERNEL_SOURCES:
         return None
-    return t["bytes"]
+    sha = sources_sha1(kernel)
+    for t in MEASURED_TRAFFIC.get(kernel, ()):
+        if t["sources_sha1"] != sha or (n, n_cams) != (t["primitives"], t["cameras"]):
+            continue
+        if tuning is not None and any(tuning.get(k) != v for k, v in t["schedule"].items()):
+            continue
+        return t["bytes"]
+    return None
 
 
 def hbm_bytes(kind_v, K, n, n_cams, E, passes, tiles, sort_mode=0, key_bits=0, radix_bits=8):
@@ -219,13 +225,13 @@ def roofline(rast, stages, kind, sh_degree, n, n_cams, clk, dev):
         roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": alu_peak,
                 "unit": "TFLOP/s", "frac": achieved / alu_peak,
                 # the captured traffic is the ray-space kernel's; the exact mode runs other kernels
-                "traffic": None if rast.exact() else measured_traffic(dom),
+                "traffic": None if rast.exact() else measured_traffic(dom, n, n_cams, tun),
                 "peak_source": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 flop x "
                                f"{sm_max:.0f} MHz ({peak_src} max clock)"}
     else:
         achieved = hb[dom] / (stages[dom] * 1e-3) / 1e9
         roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
-                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": measured_traffic(dom),
+                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": measured_traffic(dom, n, n_cams, tun),
                 "peak_source": f"{peak_src} copy bandwidth"}
     stage_report = {}
     for k, ms in stages.items():

@@ -108,9 +108,13 @@ typedef struct {
  *                 primitive; 1: in two passes, geometry then colour, each
  *                 holding fewer registers (ignored while densification
  *                 statistics are gathered, which need one pass).
- *   sparse_lanes  0..32: a backward warp in which at most this many lanes
- *                 contribute to a record adds their terms with one atomic
- *                 per lane and value instead of reducing over the warp.
+ *   sparse_lanes  0..32: when more than this many lanes of a backward warp
+ *                 contribute to a record, the warp sums the record's colour
+ *                 and density terms with shuffles before adding them;
+ *                 otherwise each contributing lane adds its own 16-byte row
+ *                 with one vector atomic.  Face terms are always added per
+ *                 lane (one vector atomic per face and run of the lane's
+ *                 pixels that share it).  The exact-span mode ignores it.
  *   radix_bits    widest digit of the radix sort passes: 4, 6, 8 or 11 bits.
  *                 A sort of k key bits takes p = ceil(k / radix_bits)
  *                 passes of ceil(k / p) bits each (at least 4), each with a
@@ -177,8 +181,9 @@ void lp_destroy(lp_ctx* ctx);
 
 /* Set / read the tuning parameters (defaults: tile 16, batch 64,
  * blocks_per_sm 0, sort_mode 0, pixels_per_thread 4, chain_split 0,
- * sparse_lanes 8, radix_bits 8, tile_order 0, onesweep 0).  LP_ERR_INVALID for a value outside the
- * sets above, or a (tile, pixels_per_thread) pair that is not built.        */
+ * sparse_lanes 32, radix_bits 8, tile_order 0, onesweep 0).  LP_ERR_INVALID
+ * for a value outside the sets above, or a (tile, pixels_per_thread) pair
+ * that is not built.                                                        */
 lp_status lp_set_tuning(lp_ctx* ctx, const lp_tuning* t);
 lp_status lp_get_tuning(lp_ctx* ctx, lp_tuning* t);
 

@@ -3,7 +3,7 @@
 The tuning knobs (sort mode and radix digit width, tile edge, pixels per
 blend thread, records per shared-memory batch, resident blend blocks per SM,
 one- or two-pass backward chain, and the number of contributing lanes up to
-which a backward warp lets each lane add its own terms) change only the
+which a backward warp lets each lane add its own colour terms) change only the
 schedule: every setting renders bit-identical images (the chain's split and
 the backward's reduction form only reorder floating-point sums of
 gradients).  The tuner times forward + backward of the caller's own workload
@@ -71,7 +71,7 @@ GROUPS = (
      tuple((t, p, b, 0) for (t, p), b in itertools.product(TILE_PIX, (32, 64))), SORT_STAGES + BLEND_STAGES),
     _SORT_GROUP,
     (("chain_split",), ((0,), (1,)), ("chain",)),
-    (("sparse_lanes",), ((4,), (8,), (16,)), ("blend_bwd",)),
+    (("sparse_lanes",), ((8,), (16,), (32,)), ("blend_bwd",)),
     (("tile_order",), ((0,), (1,)), ("ranges",) + BLEND_STAGES),
 )
 

@@ -39,7 +39,7 @@ constexpr unsigned char kGuardByte = 0xA5;
 struct lp_ctx {
     int device = 0;
     int sms = 0;
-    lp_tuning tune{16, 64, 0, 0, 4, 0, 8, 8, 0, 0};
+    lp_tuning tune{16, 64, 0, 0, 4, 0, 32, 8, 0, 0};
     float aa_kernel = 0.f;      // 2D filter size in pixels (0 = off)
     bool exact = false;         // spans along the true perspective ray
     bool fwd_exact = false;     // mode of the last forward

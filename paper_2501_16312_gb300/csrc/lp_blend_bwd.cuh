@@ -15,10 +15,11 @@
 // and, since s = exit(x, y) - entry(x, y) with plane depth a x + b y + e, the
 // plane gradients -+ dL/ds (x, y, 1) of the arg-max entry and arg-min exit
 // faces -- the plane form of the paper's MTIA barycentric derivatives.  A
-// thread first sums its strip of pixels, each warp then reduces with shuffles
-// (the colour and sigma terms in one butterfly, the faces' moments two faces
-// per butterfly) and issues one atomic add per value into the record's
-// accumulator.
+// thread sums its strip of pixels: the colour and sigma terms into one
+// 16-byte row, each face's (x, y, 1) terms into one row per run of pixels
+// sharing the face; it adds each row to the record's accumulator with one
+// vector atomic (sm_90 and later).  Only the colour row may first be summed
+// over the warp with shuffles, when many lanes contribute.
 //
 // The kernels are templates over the tile edge; each of lp_blend_bwd_t8.cu,
 // _t16.cu and _t32.cu instantiates one edge.
@@ -150,7 +151,6 @@ __global__ void __launch_bounds__(TILE * TILE / PIX, bwd_min_blocks<TILE * TILE 
                 if (bal == 0u) continue;
                 float gr0 = 0.f, gr1 = 0.f, gr2 = 0.f, gsig = 0.f;
                 float gsp[PIX];
-                unsigned used = 0;
 #pragma unroll
                 for (int i = 0; i < PIX; ++i) gsp[i] = 0.f;
                 if (anyc) {
@@ -176,109 +176,51 @@ __global__ void __launch_bounds__(TILE * TILE / PIX, bwd_min_blocks<TILE * TILE 
                             B2[i] = fmaf(o, p.b, tau * B2[i]);
                             gsp[i] = dLdo * p.sigma * tau;        // dL/d span
                             gsig = fmaf(dLdo * sp[i], tau, gsig);  // dL/d sigma
-                            used |= (1u << sf[i]) | (1u << sb[i]);
                         }
                     }
                 }
                 float* A = acc + (size_t)p.rec * ACC;        // plane moments
                 float* Ac = acc_col + (size_t)p.rec * 4;     // colour and density
-                // plane gradients use offsets (px - X0, py - Y0) from the anchor
-                const float lyc = (float)ly + p.dy0;
-                // warps with at most sparse_lanes contributing lanes (a tuning
-                // value, 8 by default) skip the shuffle reductions and let each
-                // contributing lane issue its own atomic adds
-                if (__popc(bal) <= sparse_lanes) {
-                    // few contributing lanes: each adds its own terms
-                    if (anyc) {
-                        atomicAdd(Ac + 0, gr0);
-                        atomicAdd(Ac + 1, gr1);
-                        atomicAdd(Ac + 2, gr2);
-                        atomicAdd(Ac + 3, gsig);
-#pragma unroll
-                        for (int i = 0; i < PIX; ++i) {
-                            if (c[i]) {
-                                const float lxc = (float)(lx0 + i) + p.dx0;
-                                atomicAdd(A + 3 * sf[i] + 0, -gsp[i] * lxc);
-                                atomicAdd(A + 3 * sf[i] + 1, -gsp[i] * lyc);
-                                atomicAdd(A + 3 * sf[i] + 2, -gsp[i]);
-                                atomicAdd(A + 3 * sb[i] + 0, gsp[i] * lxc);
-                                atomicAdd(A + 3 * sb[i] + 1, gsp[i] * lyc);
-                                atomicAdd(A + 3 * sb[i] + 2, gsp[i]);
-                            }
-                        }
-                    }
-                    continue;
-                }
-                if constexpr (PIX <= 2) {
-                    // the colour and sigma terms and the (x, y, 1) moments of
-                    // up to four faces in one 16-value butterfly; sixteen lanes
-                    // then add one total each (measured faster than separate
-                    // butterflies with one or two pixels per thread, slower
-                    // with four, whose face terms cost twice as much to build)
-                    used = __reduce_or_sync(0xffffffffu, used);
-                    int fq[4];
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        fq[q] = used ? __ffs(used) - 1 : -1;
-                        used &= used - 1;
-                    }
-                    float hv[16];
-                    hv[0] = gr0; hv[1] = gr1; hv[2] = gr2; hv[3] = gsig;
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        float mx = 0.f, m1 = 0.f;
-#pragma unroll
-                        for (int i = 0; i < PIX; ++i) {
-                            const float lxc = (float)(lx0 + i) + p.dx0;
-                            const float v = c[i] ? (fq[q] == sf[i] ? -gsp[i] : (fq[q] == sb[i] ? gsp[i] : 0.f)) : 0.f;
-                            mx = fmaf(v, lxc, mx);
-                            m1 += v;
-                        }
-                        hv[4 + 3 * q] = mx;
-                        hv[5 + 3 * q] = m1 * lyc;
-                        hv[6 + 3 * q] = m1;
-                    }
-                    const float t = warp_sum_multi<16>(hv, lane);
-                    const int k = warp_sum_index<16>(lane);
-                    if ((lane & 1) == 0) {
-                        const int q = (k - 4) / 3;
-                        if (k < 4) atomicAdd(Ac + k, t);
-                        else if (fq[q] >= 0) atomicAdd(A + 3 * fq[q] + (k - 4 - 3 * q), t);
-                    }
-                } else {
-                    // colour and sigma: four totals, one per lane group of 8
+                // Colour and density: with more than sparse_lanes contributing
+                // lanes the whole warp first sums the four terms with shuffles
+                // (one total per lane group of 8); otherwise each contributing
+                // lane adds its own row with one 16-byte vector atomic.
+                if (__popc(bal) > sparse_lanes) {
                     float hv[4] = {gr0, gr1, gr2, gsig};
                     const float t = warp_sum_multi<4>(hv, lane);
                     if ((lane & 7) == 0) atomicAdd(Ac + warp_sum_index<4>(lane), t);
-                    used = __reduce_or_sync(0xffffffffu, used);
+                } else if (anyc) {
+                    atomicAdd(reinterpret_cast<float4*>(Ac), make_float4(gr0, gr1, gr2, gsig));
                 }
-                // (further) faces two per butterfly: (x, y, 1) moments of both
-                // in one 8-value reduction, six lanes then add one total each
-                while (used) {
-                    const int f1 = __ffs(used) - 1;
-                    used &= used - 1;
-                    const int f2 = used ? __ffs(used) - 1 : -1;
-                    if (used) used &= used - 1;
-                    float hv[8];
+                if (!anyc) continue;
+                // Planes: each contributing lane adds the (x, y, 1) row of an
+                // entry or exit face once per run of its pixels that share
+                // that face, one 16-byte vector atomic each (measured faster
+                // than warp butterflies over the faces, however many lanes
+                // contribute).  Offsets (px - X0, py - Y0) are from the anchor.
+                const float lyc = (float)ly + p.dy0;
+                float4 re = make_float4(0.f, 0.f, 0.f, 0.f), rb = re;
+                int fe = -1, fb = -1;
 #pragma unroll
-                    for (int k = 0; k < 8; ++k) hv[k] = 0.f;
-#pragma unroll
-                    for (int i = 0; i < PIX; ++i) {
-                        const float lxc = (float)(lx0 + i) + p.dx0;
-                        const float v1 = c[i] ? (f1 == sf[i] ? -gsp[i] : (f1 == sb[i] ? gsp[i] : 0.f)) : 0.f;
-                        const float v2 = c[i] ? (f2 == sf[i] ? -gsp[i] : (f2 == sb[i] ? gsp[i] : 0.f)) : 0.f;
-                        hv[0] = fmaf(v1, lxc, hv[0]);
-                        hv[2] += v1;
-                        hv[3] = fmaf(v2, lxc, hv[3]);
-                        hv[5] += v2;
+                for (int i = 0; i < PIX; ++i) {
+                    if (!c[i]) continue;
+                    const float lxc = (float)(lx0 + i) + p.dx0;
+                    const float gx = gsp[i] * lxc, gy = gsp[i] * lyc, g1 = gsp[i];
+                    if (sf[i] != fe) {
+                        if (fe >= 0) atomicAdd(reinterpret_cast<float4*>(A + 4 * fe), re);
+                        fe = sf[i];
+                        re = make_float4(0.f, 0.f, 0.f, 0.f);
                     }
-                    hv[1] = hv[2] * lyc;
-                    hv[4] = hv[5] * lyc;
-                    const float t = warp_sum_multi<8>(hv, lane);
-                    const int k = warp_sum_index<8>(lane);
-                    if ((lane & 3) == 0 && k < 6 && (k < 3 || f2 >= 0))
-                        atomicAdd(A + (k < 3 ? 3 * f1 + k : 3 * f2 + k - 3), t);
+                    if (sb[i] != fb) {
+                        if (fb >= 0) atomicAdd(reinterpret_cast<float4*>(A + 4 * fb), rb);
+                        fb = sb[i];
+                        rb = make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
+                    re.x -= gx; re.y -= gy; re.z -= g1;
+                    rb.x += gx; rb.y += gy; rb.z += g1;
                 }
+                atomicAdd(reinterpret_cast<float4*>(A + 4 * fe), re);
+                atomicAdd(reinterpret_cast<float4*>(A + 4 * fb), rb);
             }
         }
         __syncthreads();

@@ -126,14 +126,15 @@ __device__ __forceinline__ int meta_face(uint32_t meta, int slot) {
 
 // Per-record gradient accumulators written by the backward blend, in two
 // blocks of one array (records R):
-//   planes, [R][3F] at the start: [3s .. 3s+2] sums of g * (px - X0, py - Y0,
-//          1) over the pixels where slot s bounds the span, g = dL/d(plane
-//          depth);
+//   planes, [R][F][4] at the start: [4s .. 4s+2] sums of g * (px - X0,
+//          py - Y0, 1) over the pixels where slot s bounds the span, g =
+//          dL/d(plane depth); [4s + 3] stays zero.  Each slot is one 16-byte
+//          row, so one vector atomic adds a pixel's three terms;
 //   colour, [R][4] after the planes: dL/d rgb, dL/d sigma (one 16-byte row).
 // The chain's geometry and colour passes each read only their own block.
 template <int V> struct Acc {
     static constexpr int F = Kind<V>::F;
-    static constexpr int kPlane = 3 * F;           // 24, 12
+    static constexpr int kPlane = 4 * F;           // 32, 16
     static constexpr int kFloats = kPlane + 4;     // per record over both blocks
 };
 

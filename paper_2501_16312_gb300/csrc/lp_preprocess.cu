@@ -295,7 +295,10 @@ k_chain(PrimsDev P, CamsParam cams, const uint32_t* __restrict__ meta_in, const 
         }
         if constexpr (PART != 1) {
 #pragma unroll
-            for (int q = 0; q < KP; ++q) any |= A[q] != 0.f;
+            for (int q = 0; q < F; ++q) {
+                const float4 a = __ldg(reinterpret_cast<const float4*>(A) + q);
+                any |= a.x != 0.f || a.y != 0.f || a.z != 0.f;
+            }
         }
         if (!any) continue;   // no pixel produced a gradient for this record
         float ga_rgb[3], ga_sig;
@@ -326,8 +329,9 @@ k_chain(PrimsDev P, CamsParam cams, const uint32_t* __restrict__ meta_in, const 
             const int s = (int)((slot_of >> (3 * f)) & 7u);
             // accumulators hold sums over g (px - X0, py - Y0, 1); the pixel's
             // offset from the projected centre is (px - X0 - fxo, py - Y0 - fyo)
-            const float Ge = A[3 * s + 2];
-            const float Ga = __fmaf_rn(-g.fxo, Ge, A[3 * s]), Gb = __fmaf_rn(-g.fyo, Ge, A[3 * s + 1]);
+            const float4 a4 = __ldg(reinterpret_cast<const float4*>(A) + s);
+            const float Ge = a4.z;
+            const float Ga = __fmaf_rn(-g.fxo, Ge, a4.x), Gb = __fmaf_rn(-g.fyo, Ge, a4.y);
             if (Ga == 0.f && Gb == 0.f && Ge == 0.f) continue;
             int iv[3];
             face_vertices<V>(f, iv[0], iv[1], iv[2]);

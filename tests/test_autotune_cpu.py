@@ -122,7 +122,7 @@ def test_search_ties_keep_the_first_candidate():
             "blend_bwd": 1.0, "chain": 1.0}
     entry = autotune.search(knobs.update, lambda: flat, BASE)
     assert entry["tuning"] == dict(BASE, sort_mode=0, radix_bits=4, tile=8, pixels_per_thread=1, batch=32,
-                                   chain_split=0, sparse_lanes=4)
+                                   chain_split=0, sparse_lanes=8)
 
 
 def test_cache_key_buckets():
