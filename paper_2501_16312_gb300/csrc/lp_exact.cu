@@ -46,10 +46,11 @@ template <int V> struct RecX {
 };
 
 // per face slot (= face) dL/d(p, q, L0, D0); then rgb, sigma, c_z (the last
-// is collected by the backward but not needed by the chain, see k_chain_x)
+// is collected by the backward but not needed by the chain, see k_chain_x),
+// padded to whole 16-byte rows so that each row takes one vector atomic
 template <int V> struct AccX {
     static constexpr int F = Kind<V>::F;
-    static constexpr int kFloats = 4 * F + 5;   // 37, 21
+    static constexpr int kFloats = 4 * F + 8;   // 40, 24
 };
 
 // Camera-space offsets d = R (v - c) of a vertex (the key-field sequence).
@@ -551,7 +552,6 @@ __global__ void __launch_bounds__(threads_x<TILE>()) k_blend_bwd_x(
                 // dL/d(p, q, L0, D0); per thread: rgb, sigma, c_z sums
                 float ge[PIX][4], gx[PIX][4];
                 float h0 = 0.f, h1 = 0.f, h2 = 0.f, hs = 0.f, hz = 0.f;
-                unsigned used = 0;
 #pragma unroll
                 for (int i = 0; i < PIX; ++i) {
 #pragma unroll
@@ -574,7 +574,6 @@ __global__ void __launch_bounds__(threads_x<TILE>()) k_blend_bwd_x(
                     hs = fmaf(dLdo * sp[i], tau, hs);                     // dL/dsigma
                     const float gs = dLdo * p.sigma * tau * rn[i];        // dL/d(delta_out - delta_in)
                     const float X = (float)(lx0 + i) + p.dx0, Y = (float)ly + p.dy0;
-                    used |= (1u << sf[i]) | (1u << sb[i]);
 #pragma unroll
                     for (int side = 0; side < 2; ++side) {
                         const int f = side ? sb[i] : sf[i];
@@ -596,56 +595,33 @@ __global__ void __launch_bounds__(threads_x<TILE>()) k_blend_bwd_x(
                         hz = fmaf(-gd * L, iD, hz);                       // dL/dc_z
                     }
                 }
+                if (!anyc) continue;
+                // each contributing lane adds its own rows, one 16-byte vector
+                // atomic each: colour and density, c_z, and a face's four
+                // terms once per run of the lane's pixels sharing that face
                 float* Ag = acc + (size_t)p.rec * ACC;
-                const unsigned bal = __ballot_sync(0xffffffffu, anyc);
-                if (__popc(bal) <= 4) {
-                    // few contributing lanes: each adds its own terms
-                    if (anyc) {
-                        atomicAdd(Ag + 4 * F + 0, h0);
-                        atomicAdd(Ag + 4 * F + 1, h1);
-                        atomicAdd(Ag + 4 * F + 2, h2);
-                        atomicAdd(Ag + 4 * F + 3, hs);
-                        atomicAdd(Ag + 4 * F + 4, hz);
+                atomicAdd(reinterpret_cast<float4*>(Ag + 4 * F), make_float4(h0, h1, h2, hs));
+                atomicAdd(Ag + 4 * F + 4, hz);
+                float4 re = make_float4(0.f, 0.f, 0.f, 0.f), rb = re;
+                int fe = -1, fb = -1;
 #pragma unroll
-                        for (int i = 0; i < PIX; ++i) {
-                            if (!c[i]) continue;
-#pragma unroll
-                            for (int m = 0; m < 4; ++m) {
-                                atomicAdd(Ag + 4 * sf[i] + m, ge[i][m]);
-                                atomicAdd(Ag + 4 * sb[i] + m, gx[i][m]);
-                            }
-                        }
+                for (int i = 0; i < PIX; ++i) {
+                    if (!c[i]) continue;
+                    if (sf[i] != fe) {
+                        if (fe >= 0) atomicAdd(reinterpret_cast<float4*>(Ag + 4 * fe), re);
+                        fe = sf[i];
+                        re = make_float4(0.f, 0.f, 0.f, 0.f);
                     }
-                    continue;
-                }
-                h0 = warp_sum(h0); h1 = warp_sum(h1); h2 = warp_sum(h2); hs = warp_sum(hs); hz = warp_sum(hz);
-                if (lane == 0) {
-                    atomicAdd(Ag + 4 * F + 0, h0);
-                    atomicAdd(Ag + 4 * F + 1, h1);
-                    atomicAdd(Ag + 4 * F + 2, h2);
-                    atomicAdd(Ag + 4 * F + 3, hs);
-                    atomicAdd(Ag + 4 * F + 4, hz);
-                }
-                used = __reduce_or_sync(0xffffffffu, used);
-                while (used) {
-                    const int f = __ffs(used) - 1;
-                    used &= used - 1;
-                    float v[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-                    for (int i = 0; i < PIX; ++i) {
-#pragma unroll
-                        for (int m = 0; m < 4; ++m) {
-                            v[m] += (c[i] && sf[i] == f) ? ge[i][m] : 0.f;
-                            v[m] += (c[i] && sb[i] == f) ? gx[i][m] : 0.f;
-                        }
+                    if (sb[i] != fb) {
+                        if (fb >= 0) atomicAdd(reinterpret_cast<float4*>(Ag + 4 * fb), rb);
+                        fb = sb[i];
+                        rb = make_float4(0.f, 0.f, 0.f, 0.f);
                     }
-#pragma unroll
-                    for (int m = 0; m < 4; ++m) v[m] = warp_sum(v[m]);
-                    if (lane == 0) {
-#pragma unroll
-                        for (int m = 0; m < 4; ++m) atomicAdd(Ag + 4 * f + m, v[m]);
-                    }
+                    re.x += ge[i][0]; re.y += ge[i][1]; re.z += ge[i][2]; re.w += ge[i][3];
+                    rb.x += gx[i][0]; rb.y += gx[i][1]; rb.z += gx[i][2]; rb.w += gx[i][3];
                 }
+                atomicAdd(reinterpret_cast<float4*>(Ag + 4 * fe), re);
+                atomicAdd(reinterpret_cast<float4*>(Ag + 4 * fb), rb);
             }
         }
         __syncthreads();
