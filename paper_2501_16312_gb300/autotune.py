@@ -68,7 +68,7 @@ _SORT_GROUP = (("sort_mode", "radix_bits", "onesweep"), tuple(itertools.product(
 GROUPS = (
     _SORT_GROUP,
     (("tile", "pixels_per_thread", "batch", "blocks_per_sm"),
-     tuple((t, p, b, 0) for (t, p), b in itertools.product(TILE_PIX, (32, 64))), SORT_STAGES + BLEND_STAGES),
+     tuple((t, p, b, 0) for (t, p), b in itertools.product(TILE_PIX, (32, 64, 128))), SORT_STAGES + BLEND_STAGES),
     _SORT_GROUP,
     (("chain_split",), ((0,), (1,)), ("chain",)),
     (("sparse_lanes",), ((8,), (16,), (32,)), ("blend_bwd",)),

@@ -1,12 +1,12 @@
 // Shared pieces of the forward and backward blend kernels (sm_103a).
 //
 // A tile of TILE x TILE pixels (TILE = 8, 16 or 32, a tuning choice; 16 is
-// the paper's patch size) is processed by TILE^2 / PIX threads; thread t owns
-// the strip of PIX horizontally adjacent pixels starting at
-// (lx0, ly) = ((t % (TILE / PIX)) * PIX, t / (TILE / PIX)), so that one
-// 128-bit shared-memory load of a face plane feeds PIX pixels.  A warp covers
-// 32 PIX / TILE whole rows.  Blocks are persistent and pull tiles of all
-// cameras from one atomic queue.
+// the paper's patch size) is processed by TILE^2 / PIX threads; each thread
+// owns a strip of PIX horizontally adjacent pixels, so that one 128-bit
+// shared-memory load of a face plane feeds PIX pixels, and each warp a
+// rectangle of the tile (WarpGrid: 8 x 8 pixels, or 8 x 16 with four pixels
+// per thread), the unit of the per-warp skips.  Blocks are persistent and
+// pull tiles of all cameras from one atomic queue.
 #pragma once
 
 #include "lp_device.cuh"

@@ -45,16 +45,16 @@ __global__ void __launch_bounds__(TILE * TILE / PIX, bwd_min_blocks<TILE * TILE 
     int sparse_lanes, const uint32_t* __restrict__ order) {
     constexpr int ACC = Acc<V>::kPlane;
     constexpr int NT = TILE * TILE / PIX;
-    constexpr int RW = TILE / PIX;
     constexpr int MW = BATCH / 32;   // contributor-mask words per batch
-    static_assert(NT % 32 == 0 && 32 % RW == 0, "whole warps of whole rows");
+    static_assert(NT % 32 == 0, "whole warps");
     static_assert(BATCH % 32 == 0, "whole mask words per batch");
     __shared__ Staged<V> sm[BATCH];
     __shared__ int s_tile;
     __shared__ int s_max;
     const int tid = threadIdx.x;
     const int lane = tid & 31;
-    const int ly = tid / RW, lx0 = (tid % RW) * PIX;
+    int ly, lx0;   // the forward's pixel layout, so that warp w's mask bits are its own
+    WarpGrid<TILE, PIX>::pixel(tid, ly, lx0);
     for (;;) {
         if (tid == 0) {
             const int q = atomicAdd(tile_counter, 1);

@@ -10,7 +10,7 @@
 // pixels have.  Per pixel the kernel keeps, for the backward, the number of
 // list entries up to the last contributor and the transmittance before it,
 // and per warp one bit per list entry its pixels blended.  A warp skips the
-// records that the staging test proves cover none of its rows.
+// records that the staging test proves cover none of its pixels.
 //
 // MODE 1 also counts (pixel, primitive) pairs.  MODE 2 is the depth pass
 // (App. "Depth and Surface Reconstruction"): the same walk, stopping each
@@ -39,14 +39,12 @@ __global__ void __launch_bounds__(TILE * TILE / PIX) k_blend_fwd(
     constexpr bool DEPTH = MODE == 2;
     constexpr float kStop = DEPTH ? 0.5f : kStopT;
     constexpr int NT = TILE * TILE / PIX;
-    constexpr int RW = TILE / PIX;
-    constexpr int BH = 32 / RW;   // rows per warp
-    static_assert(NT % 32 == 0 && BH >= 1, "whole warps of whole rows");
     __shared__ Staged<V> sm[BATCH];
     __shared__ int s_tile;
     const int tid = threadIdx.x;
     const int lane = tid & 31;
-    const int ly = tid / RW, lx0 = (tid % RW) * PIX;
+    int ly, lx0;
+    WarpGrid<TILE, PIX>::pixel(tid, ly, lx0);
     const bool write_mask = !DEPTH && contrib != nullptr;
     unsigned long long n_iter = 0, n_eval = 0, n_hit = 0, n_eval_last = 0;
     for (;;) {
@@ -80,7 +78,7 @@ __global__ void __launch_bounds__(TILE * TILE / PIX) k_blend_fwd(
             const int nb = min(BATCH, n - b0);
             for (int j = tid; j < nb; j += NT) {
                 stage_record<V>(rec, vals[rg.x + b0 + j], tg.tx0, tg.ty0, sm[j]);
-                sm[j].bands = band_mask<V, TILE, BH>(sm[j]);
+                sm[j].bands = band_mask<V, TILE, PIX>(sm[j]);
             }
             __syncthreads();
             if (__any_sync(0xffffffffu, !tdone)) {   // warp-uniform, as the exit below
@@ -94,7 +92,7 @@ __global__ void __launch_bounds__(TILE * TILE / PIX) k_blend_fwd(
 #pragma unroll
                             for (int i = 0; i < PIX; ++i) n_iter += !done[i];
                         }
-                        // warp-uniform: no pixel of this warp's rows can meet it
+                        // warp-uniform: no pixel of this warp's rectangle can meet it
                         if (!((p.bands >> (tid >> 5)) & 1u)) continue;
                         float sp[PIX];
                         spans<V, PIX, false>(p, (float)lx0 + p.dx0, (float)ly + p.dy0, sp, nullptr, nullptr);

@@ -272,21 +272,43 @@ template <int V> struct alignas(16) Staged {
     float dx0, dy0;    // tx0 - X0, ty0 - Y0 (integers)
     int nf;
     int rec;           // record index (camera * n + primitive)
-    // bit w: band w of the tile (rows [w BH, (w + 1) BH)) may hold a pixel
-    // whose ray meets the primitive; clear only when some entry/exit face
-    // pair proves it cannot, with a margin above binary32 rounding
+    // bit w: the pixel rectangle of warp w (WarpGrid) may hold a pixel whose
+    // ray meets the primitive; clear only when some entry/exit face pair
+    // proves it cannot, with a margin above binary32 rounding
     uint32_t bands;
+};
+
+// Which pixels of a TILE x TILE tile a thread of a blend block owns, with
+// PIX horizontally adjacent pixels per thread.  Each warp covers one
+// rectangle of WR rows by WC columns: 8 x 8 pixels with one or two pixels
+// per thread (4 x 8 with one), 8 x 16 with four.  Warps tile the tile row by
+// row; inside a warp, TPR threads make one row.
+template <int TILE, int PIX> struct WarpGrid {
+    static constexpr int WC0 = PIX >= 4 ? 16 : 8;
+    static constexpr int WC = WC0 < TILE ? WC0 : TILE;   // warp width in pixels
+    static constexpr int WR = 32 * PIX / WC;             // warp height in rows
+    static constexpr int NWX = TILE / WC;                // warps across the tile
+    static constexpr int TPR = WC / PIX;                 // threads per warp row
+    static constexpr int NW = TILE * TILE / PIX / 32;    // warps per tile
+    static_assert(WC % PIX == 0 && TILE % WC == 0 && TILE % WR == 0 && NW * 32 * PIX == TILE * TILE,
+                  "warps of whole rectangles");
+    __device__ __forceinline__ static void pixel(int tid, int& ly, int& lx0) {
+        const int w = tid >> 5, lane = tid & 31;
+        ly = (w / NWX) * WR + lane / TPR;
+        lx0 = (w % NWX) * WC + (lane % TPR) * PIX;
+    }
 };
 
 // The ray meets the primitive at pixel p only if every entry face is below
 // every exit face there: d_f(p) < d_b(p).  Each pair's difference is linear
-// in p, so its largest value over a band of BH rows of a TILE-wide tile is at
-// a corner; a band where some pair stays below -margin holds no covered pixel.
-template <int V, int TILE, int BH>
+// in p, so its largest value over a warp's rectangle is at a corner; a
+// rectangle where some pair stays below -margin holds no covered pixel.
+template <int V, int TILE, int PIX>
 __device__ __forceinline__ uint32_t band_mask(const Staged<V>& s) {
+    using G = WarpGrid<TILE, PIX>;
     constexpr int F = Kind<V>::F;
-    constexpr int NB = TILE / BH;
-    static_assert(NB >= 1 && NB <= 32, "one bit per band");
+    constexpr int NB = G::NW;
+    static_assert(NB >= 1 && NB <= 32, "one bit per warp");
     constexpr float XM = (float)(TILE - 1);
     const int nf = s.nf;
     if (nf <= 0 || nf >= F) return 0u;
@@ -304,11 +326,11 @@ __device__ __forceinline__ uint32_t band_mask(const Staged<V>& s) {
             const float margin = 1e-5f * (fabsf(pb.z) + fabsf(pf.z) + fabsf(eb) + fabsf(ef) +
                                           ox * (fabsf(pb.x) + fabsf(pf.x)) + oy * (fabsf(pb.y) + fabsf(pf.y))) +
                                  1e-30f;
-            const float xmax = fmaxf(0.f, XM * da);
 #pragma unroll
             for (int w = 0; w < NB; ++w) {
-                const float y0 = (float)(w * BH), y1 = (float)(w * BH + BH - 1);
-                const float m = de + xmax + fmaxf(db * y0, db * y1);
+                const float x0 = (float)((w % G::NWX) * G::WC), x1 = x0 + (float)(G::WC - 1);
+                const float y0 = (float)((w / G::NWX) * G::WR), y1 = y0 + (float)(G::WR - 1);
+                const float m = de + fmaxf(da * x0, da * x1) + fmaxf(db * y0, db * y1);
                 if (m < -margin) mask &= ~(1u << w);
             }
         }

@@ -21,7 +21,8 @@ def stage_model(k):
     lists cost more in the sort stages, which the tile group is judged on."""
     sort = (0.5 if k["sort_mode"] == 1 else 0.9) * {4: 1.3, 6: 1.1, 8: 1.0, 11: 0.9}[k["radix_bits"]]
     sort *= {8: 3.0, 16: 1.0, 32: 0.6}[k["tile"]]
-    fwd = {(2, 32): 1.9, (2, 64): 1.7, (4, 32): 1.6, (4, 64): 1.4, (1, 32): 2.0, (1, 64): 1.8}[
+    fwd = {(2, 32): 1.9, (2, 64): 1.7, (4, 32): 1.6, (4, 64): 1.4, (1, 32): 2.0, (1, 64): 1.8,
+           (1, 128): 1.85, (2, 128): 1.75, (4, 128): 1.5}[
         (k["pixels_per_thread"], k["batch"])]
     fwd *= {8: 0.9, 16: 1.0, 32: 1.3}[k["tile"]]
     bwd = 3.0 + (0.3 if k["pixels_per_thread"] == 2 else 0.0) - (0.2 if k["sparse_lanes"] == 16 else 0.0)
@@ -80,7 +81,7 @@ def test_search_picks_each_groups_best_in_order():
                 chain_split=1, sparse_lanes=16)
     assert entry["tuning"] == want
     assert knobs == want                                # the winners are left applied
-    assert len(entry["trials"]) == 16 + 12 + 16 + 2 + 3 + 2
+    assert len(entry["trials"]) == 16 + 18 + 16 + 2 + 3 + 2
     # the sort group is judged on its own stages only, at both visits
     assert entry["best_ms"]["sort_mode+radix_bits+onesweep"] == pytest.approx(0.45)
     assert entry["best_ms"]["sort_mode+radix_bits+onesweep (again)"] == pytest.approx(0.45)
@@ -159,7 +160,7 @@ def test_tune_caches_reuses_and_restores_timing(fake_cuda, tmp_path):
     entry = autotune.tune(rast, prims, cams, reps=2, cache=cache)
     want = dict(BASE, sort_mode=1, radix_bits=11, pixels_per_thread=4, batch=64, chain_split=1, sparse_lanes=16)
     assert entry["tuning"] == want and rast.knobs == want
-    assert rast.measured == 51 * 3                       # 51 trials x (warm-up + 2 timed)
+    assert rast.measured == 57 * 3                       # 57 trials x (warm-up + 2 timed)
     assert rast.timing_calls == [True, False]            # timing restored to off
     stored = json.load(open(cache))
     key = autotune.cache_key("FakeGPU", 6, 10, cams)
@@ -173,7 +174,7 @@ def test_tune_caches_reuses_and_restores_timing(fake_cuda, tmp_path):
     rast3 = FakeRast()
     rast3.set_timing(True)
     autotune.tune(rast3, prims, cams, reps=1, cache=cache, force=True)
-    assert rast3.measured == 51 * 2 and rast3.timing() is True
+    assert rast3.measured == 57 * 2 and rast3.timing() is True
     # other workloads share the file
     autotune.tune(FakeRast(), prims, cams[:1], reps=1, cache=cache)
     assert len(json.load(open(cache))) == 2
