@@ -140,7 +140,16 @@ def blend_flops(F, pairs):
 # reported only for the same workload (primitives, cameras) and schedule, and
 # is ignored once the sources change (profiles/dram_traffic_blend_bwd_*.md).
 MEASURED_TRAFFIC = {
-    "blend_bwd": [],
+    "blend_bwd": [
+        {"primitives": 500000, "cameras": 8, "schedule": {"tile": 16, "pixels_per_thread": 2, "batch": 128},
+         "bytes": 560.8e6 + 125.5e6, "sources_sha1": "53cb1caa86c96d1469a6e0db829fcb53e13fc320",
+         "capture": "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum -k regex:^k_blend_bwd$ -s 2 -c 1"},
+    ],
+    "blend_fwd": [
+        {"primitives": 500000, "cameras": 8, "schedule": {"tile": 16, "pixels_per_thread": 2, "batch": 128},
+         "bytes": 239.2e6 + 122.5e6, "sources_sha1": "648f87ebe546836d7fdc90213d2e31c9c83eea1f",
+         "capture": "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum -k regex:^k_blend_fwd$ -s 2 -c 1"},
+    ],
 }
 KERNEL_SOURCES = {
     "blend_fwd": ("lp_blend_fwd.cuh", "lp_blend.cuh", "lp_device.cuh"),
