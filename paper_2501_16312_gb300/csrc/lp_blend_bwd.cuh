@@ -31,12 +31,22 @@ namespace lp {
 
 namespace {
 
-// 768 resident threads per SM (at most 80 registers): measured faster than
-// the 96-register schedule the compiler picks on its own (16x16 tiles).
-template <int NT> constexpr int bwd_min_blocks() { return 768 / NT > 0 ? 768 / NT : 1; }
+// Resident threads per SM the backward is compiled for, which sets its
+// register budget.  Measured best on the 500k-octahedron, 8-view and
+// 1M-tetrahedron, 16-view workloads: 1536 on 8x8 tiles (42 registers; 4-9%
+// faster than 768), 1024 on 16x16 tiles with two pixels per thread (64
+// registers; 8% faster, where 1280 was 35% slower), 768 otherwise (80
+// registers; four pixels per thread spill heavily below that).
+template <int TILE, int PIX> constexpr int bwd_resident_threads() {
+    return TILE == 8 ? 1536 : (TILE == 16 && PIX == 2 ? 1024 : 768);
+}
+template <int TILE, int PIX> constexpr int bwd_min_blocks() {
+    constexpr int nt = TILE * TILE / PIX;
+    return bwd_resident_threads<TILE, PIX>() / nt > 0 ? bwd_resident_threads<TILE, PIX>() / nt : 1;
+}
 
 template <int V, int BATCH, int PIX, int TILE>
-__global__ void __launch_bounds__(TILE * TILE / PIX, bwd_min_blocks<TILE * TILE / PIX>()) k_blend_bwd(
+__global__ void __launch_bounds__(TILE * TILE / PIX, bwd_min_blocks<TILE, PIX>()) k_blend_bwd(
     const float* __restrict__ rec, const uint32_t* __restrict__ vals, const uint2* __restrict__ ranges,
     CamsParam cams, float bg0, float bg1, float bg2, const float* __restrict__ dimage,
     const uint32_t* __restrict__ last_in, const float* __restrict__ tl_in, float* __restrict__ acc,

@@ -264,6 +264,7 @@ constexpr int kRadixMaxBits = 11;
 constexpr uint32_t kFlagAgg = 1u << 30, kFlagInc = 2u << 30, kFlagMask = 3u << 30, kValMask = (1u << 30) - 1u;
 constexpr long long kSweepWaitCycles = 2000000000ll;   // about a second: bound of one look-back wait
 constexpr long long kSweepMaxItems = 1ll << 30;         // counts must fit in the status words
+constexpr int kLookWindow = 8;                          // earlier blocks read per look-back step
 
 // Digit counts of one block's chunk: each warp counts its sub-chunk into its
 // own shared histogram (less contention than one histogram per block); with
@@ -433,22 +434,35 @@ __global__ void __launch_bounds__(kSortThreads, sizeof(K) == 4 ? 4 : 3) k_radix_
             const int d = tid * DPT + q;
             uint32_t pre = 0u;
             if (d < R && bid > 0) {
-                for (long long j = (long long)bid - 1; j >= 0; --j) {
-                    const volatile uint32_t* sp = status + (size_t)j * R + d;
-                    uint32_t v = *sp;
-                    if (!(v & kFlagMask)) {
-                        const long long t0 = clock64();
-                        while (!((v = *sp) & kFlagMask)) {
-                            if (clock64() - t0 > kSweepWaitCycles) {
-                                atomicOr(err, kStatusTimeout);   // the output is invalid, never out of bounds
-                                v = kFlagInc;
-                                break;
+                // kLookWindow earlier blocks' words are loaded together (one
+                // round trip to L2 instead of one per block), then taken in
+                // order; a word not yet published is re-read until it is
+                bool found = false;
+                for (long long j0 = (long long)bid - 1; j0 >= 0 && !found; j0 -= kLookWindow) {
+                    uint32_t win[kLookWindow];
+#pragma unroll
+                    for (int u = 0; u < kLookWindow; ++u)
+                        win[u] = j0 - u >= 0 ? *((const volatile uint32_t*)status + (size_t)(j0 - u) * R + d)
+                                             : kFlagInc;
+#pragma unroll
+                    for (int u = 0; u < kLookWindow; ++u) {
+                        if (found) break;
+                        uint32_t v = win[u];
+                        if (!(v & kFlagMask)) {
+                            const volatile uint32_t* sp = status + (size_t)(j0 - u) * R + d;
+                            const long long t0 = clock64();
+                            while (!((v = *sp) & kFlagMask)) {
+                                if (clock64() - t0 > kSweepWaitCycles) {
+                                    atomicOr(err, kStatusTimeout);   // the output is invalid, never out of bounds
+                                    v = kFlagInc;
+                                    break;
+                                }
+                                __nanosleep(64);
                             }
-                            __nanosleep(64);
                         }
+                        pre += v & kValMask;
+                        found = (v & kFlagInc) != 0u;
                     }
-                    pre += v & kValMask;
-                    if (v & kFlagInc) break;
                 }
                 if ((int)bid != stall_block)
                     *(volatile uint32_t*)(status + (size_t)bid * R + d) = kFlagInc | ((pre + tot[q]) & kValMask);
