@@ -108,13 +108,6 @@ typedef struct {
  *                 primitive; 1: in two passes, geometry then colour, each
  *                 holding fewer registers (ignored while densification
  *                 statistics are gathered, which need one pass).
- *   sparse_lanes  0..32: when more than this many lanes of a backward warp
- *                 contribute to a record, the warp sums the record's colour
- *                 and density terms with shuffles before adding them;
- *                 otherwise each contributing lane adds its own 16-byte row
- *                 with one vector atomic.  Face terms are always added per
- *                 lane (one vector atomic per face and run of the lane's
- *                 pixels that share it).  The exact-span mode ignores it.
  *   radix_bits    widest digit of the radix sort passes: 4, 6, 8 or 11 bits.
  *                 A sort of k key bits takes p = ceil(k / radix_bits)
  *                 passes of ceil(k / p) bits each (at least 4), each with a
@@ -129,8 +122,8 @@ typedef struct {
  *                 offsets by decoupled look-back (below 2^30 entries).
  * Every setting renders bit-identical images (a pixel's arithmetic does not
  * depend on the schedule); tile lists are identical for one tile edge and in
- * the paper's per-tile order at each.  chain_split and sparse_lanes change
- * the order in which gradient terms are summed, so gradients can differ in
+ * the paper's per-tile order at each.  chain_split and the blend schedule
+ * change the order in which gradient terms are summed, so gradients can differ in
  * the last bits between settings.  A backward, depth pass or pair count uses
  * the tile edge, batch and pixels per thread of its forward.                */
 typedef struct {
@@ -140,7 +133,6 @@ typedef struct {
     int sort_mode;
     int pixels_per_thread;
     int chain_split;
-    int sparse_lanes;
     int radix_bits;
     int tile_order;
     int onesweep;
@@ -181,7 +173,7 @@ void lp_destroy(lp_ctx* ctx);
 
 /* Set / read the tuning parameters (defaults: tile 16, batch 64,
  * blocks_per_sm 0, sort_mode 0, pixels_per_thread 4, chain_split 0,
- * sparse_lanes 32, radix_bits 8, tile_order 0, onesweep 0).  LP_ERR_INVALID
+ * radix_bits 8, tile_order 0, onesweep 0).  LP_ERR_INVALID
  * for a value outside the sets above, or a (tile, pixels_per_thread) pair
  * that is not built.                                                        */
 lp_status lp_set_tuning(lp_ctx* ctx, const lp_tuning* t);

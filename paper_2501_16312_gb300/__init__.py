@@ -102,13 +102,13 @@ class Rasterizer:
         return C.c_void_p(_torch().cuda.current_stream(self.device).cuda_stream)
 
     def set_tuning(self, tile=None, batch=None, blocks_per_sm=None, sort_mode=None,
-                   pixels_per_thread=None, chain_split=None, sparse_lanes=None, radix_bits=None,
+                   pixels_per_thread=None, chain_split=None, radix_bits=None,
                    tile_order=None, onesweep=None):
         t = _native.lp_tuning()
         _native.check(self.ctx, self.lib.lp_get_tuning(self.ctx, C.byref(t)), "lp_get_tuning")
         for k, v in (("tile", tile), ("batch", batch), ("blocks_per_sm", blocks_per_sm),
                      ("sort_mode", sort_mode), ("pixels_per_thread", pixels_per_thread),
-                     ("chain_split", chain_split), ("sparse_lanes", sparse_lanes), ("radix_bits", radix_bits),
+                     ("chain_split", chain_split), ("radix_bits", radix_bits),
                      ("tile_order", tile_order), ("onesweep", onesweep)):
             if v is not None:
                 setattr(t, k, int(v))

@@ -42,8 +42,7 @@ class lp_prims(C.Structure):
 class lp_tuning(C.Structure):
     _fields_ = [("tile", C.c_int), ("batch", C.c_int), ("blocks_per_sm", C.c_int),
                 ("sort_mode", C.c_int), ("pixels_per_thread", C.c_int), ("chain_split", C.c_int),
-                ("sparse_lanes", C.c_int), ("radix_bits", C.c_int), ("tile_order", C.c_int),
-                ("onesweep", C.c_int)]
+                ("radix_bits", C.c_int), ("tile_order", C.c_int), ("onesweep", C.c_int)]
 
 
 class lp_stats(C.Structure):

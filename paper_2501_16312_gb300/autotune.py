@@ -71,7 +71,6 @@ GROUPS = (
      tuple((t, p, b, 0) for (t, p), b in itertools.product(TILE_PIX, (32, 64, 128))), SORT_STAGES + BLEND_STAGES),
     _SORT_GROUP,
     (("chain_split",), ((0,), (1,)), ("chain",)),
-    (("sparse_lanes",), ((8,), (16,), (32,)), ("blend_bwd",)),
     (("tile_order",), ((0,), (1,)), ("ranges",) + BLEND_STAGES),
 )
 
@@ -100,15 +99,22 @@ def search(apply, measure, base: dict) -> dict:
     return {"tuning": choice, "best_ms": best_ms, "trials": results}
 
 
-def load_cache(cache: Optional[str], key: str) -> Optional[dict]:
-    """The cached entry for key, or None (missing or unreadable file)."""
+def load_cache(cache: Optional[str], key: str, knobs=None) -> Optional[dict]:
+    """The cached entry for key, or None (missing or unreadable file, or an
+    entry whose tuning names other knobs than `knobs`, e.g. one written by a
+    build with a different set of knobs)."""
     if not cache or not os.path.exists(cache):
         return None
     try:
         with open(cache) as f:
-            return json.load(f).get(key)
+            entry = json.load(f).get(key)
     except (OSError, ValueError, AttributeError):
         return None
+    if entry is None or not isinstance(entry.get("tuning"), dict):
+        return None
+    if knobs is not None and set(entry["tuning"]) != set(knobs):
+        return None
+    return entry
 
 
 def store_cache(cache: Optional[str], key: str, entry: dict) -> None:
@@ -141,7 +147,7 @@ def tune(rast, prims, cameras, bg=(0.0, 0.0, 0.0), dL=None, reps: int = 3,
     gpu = torch.cuda.get_device_name(rast.device)
     key = cache_key(gpu, prims.kind, prims.n, cameras)
     if not force:
-        known = load_cache(cache, key)
+        known = load_cache(cache, key, knobs=rast.tuning())
         if known is not None:
             rast.set_tuning(**known["tuning"])
             return known

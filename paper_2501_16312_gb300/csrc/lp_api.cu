@@ -39,12 +39,12 @@ constexpr unsigned char kGuardByte = 0xA5;
 struct lp_ctx {
     int device = 0;
     int sms = 0;
-    lp_tuning tune{16, 64, 0, 0, 4, 0, 32, 8, 0, 0};
+    lp_tuning tune{16, 64, 0, 0, 4, 0, 8, 0, 0};
     float aa_kernel = 0.f;      // 2D filter size in pixels (0 = off)
     bool exact = false;         // spans along the true perspective ray
     bool fwd_exact = false;     // mode of the last forward
     uint32_t contrib_stride = 0;
-    lp_tuning fwd_tune{16, 64, 0, 0, 4, 0, 8, 8, 0, 0};   // schedule of the last forward (its tiles, mask layout)
+    lp_tuning fwd_tune{16, 64, 0, 0, 4, 0, 8, 0, 0};   // schedule of the last forward (its tiles, mask layout)
     // densification statistics gathered by forward and backward (null: off)
     float* st_grad_sum = nullptr;
     uint32_t* st_grad_count = nullptr;
@@ -255,11 +255,12 @@ int blend_grid(const lp_ctx* ctx, const lp_tuning& t, int V, bool fwd, long long
     return (int)(tiles < g ? tiles : g);
 }
 
-// Rows of the per-warp contributor mask (one per warp of a tile) for a
-// schedule; kMaskWarpsMax bounds every supported schedule.
-constexpr int kMaskWarpsMax = 16;
-int mask_warps(const lp_tuning& t, bool exact) {
-    return exact ? lp::blend_x_warps(t.tile) : lp::blend_warps(t.tile, t.pixels_per_thread);
+// Rows of the contributor mask per tile for a schedule (one per lane group
+// of each warp; one per warp for the exact-span blends); kMaskRowsMax bounds
+// every supported schedule.
+constexpr int kMaskRowsMax = 16 * lp::kLaneGroupsMax;
+int mask_rows(const lp_tuning& t, bool exact) {
+    return exact ? lp::blend_x_warps(t.tile) : lp::blend_mask_rows(t.tile, t.pixels_per_thread);
 }
 
 int bits_for(long long n) {   // bits needed to represent values 0 .. n-1
@@ -350,8 +351,6 @@ lp_status lp_set_tuning(lp_ctx* ctx, const lp_tuning* t) {
         return fail(ctx, LP_ERR_INVALID, "sort_mode %d not in {0, 1}", t->sort_mode);
     if (t->chain_split != 0 && t->chain_split != 1)
         return fail(ctx, LP_ERR_INVALID, "chain_split %d not in {0, 1}", t->chain_split);
-    if (t->sparse_lanes < 0 || t->sparse_lanes > 32)
-        return fail(ctx, LP_ERR_INVALID, "sparse_lanes %d outside 0..32", t->sparse_lanes);
     if (t->radix_bits != 4 && t->radix_bits != 6 && t->radix_bits != 8 && t->radix_bits != 11)
         return fail(ctx, LP_ERR_INVALID, "radix_bits %d not in {4, 6, 8, 11}", t->radix_bits);
     if (t->tile_order != 0 && t->tile_order != 1)
@@ -437,7 +436,7 @@ static lp_status reserve_impl(lp_ctx* ctx, long long records, long long entries,
     long long sb2 = lp::scan_blocks((long long)lp::sort_hist_elems(hmax));
     LP_TRY(ensure(ctx, ctx->scan_tmp, sb > sb2 ? sb : sb2, false, "scan blocks"));
     LP_TRY(ensure(ctx, ctx->emit_part, (long long)lp::emit_blocks(records, kcap) + 1, false, "emit partition"));
-    LP_TRY(ensure(ctx, ctx->contrib, (kcap / 32 + 2) * kMaskWarpsMax, false, "contributor mask"));
+    LP_TRY(ensure(ctx, ctx->contrib, (kcap / 32 + 2) * kMaskRowsMax, false, "contributor mask"));
     LP_TRY(ensure(ctx, ctx->ranges, tiles, false, "tile ranges"));
     LP_TRY(ensure(ctx, ctx->tile_order, tiles, false, "tile order"));
     LP_TRY(ensure(ctx, ctx->last, pixels, false, "pixel state"));
@@ -561,8 +560,8 @@ lp_status lp_render_forward(lp_ctx* ctx, const lp_prims* prims, const lp_camera*
                   "scan blocks"));
     LP_TRY(ensure(ctx, ctx->emit_part, (long long)lp::emit_blocks(records, bound) + 1, cap_mode,
                   "emit partition"));
-    const int mwarps = mask_warps(ctx->tune, exact);
-    LP_TRY(ensure(ctx, ctx->contrib, (bound / 32 + 2) * mwarps, cap_mode, "contributor mask"));
+    const int mrows = mask_rows(ctx->tune, exact);
+    LP_TRY(ensure(ctx, ctx->contrib, (bound / 32 + 2) * mrows, cap_mode, "contributor mask"));
     ctx->contrib_stride = (uint32_t)(bound / 32 + 2);
 
     const int tile_bits = bits_for(tiles);
@@ -627,7 +626,7 @@ lp_status lp_render_forward(lp_ctx* ctx, const lp_prims* prims, const lp_camera*
     a.count = false;
     a.contrib = ctx->contrib.p;
     a.contrib_stride = ctx->contrib_stride;
-    LP_CUDA(cudaMemsetAsync(ctx->contrib.p, 0, (size_t)(bound / 32 + 2) * mwarps * sizeof(uint32_t), st));
+    LP_CUDA(cudaMemsetAsync(ctx->contrib.p, 0, (size_t)(bound / 32 + 2) * mrows * sizeof(uint32_t), st));
     LP_CUDA(cudaMemsetAsync(ctx->d_tile_counter, 0, sizeof(int), st));
     if (a.grid > 0) {
         if (exact) LP_CUDA(lp::launch_blend_fwd_x(ctx->tune.tile, V, a, st));
@@ -696,7 +695,6 @@ lp_status lp_render_backward(lp_ctx* ctx, const float* dL_dimages, float* dcentr
                       : ctx->acc.p + (size_t)ctx->records * (V == 6 ? lp::Acc<6>::kPlane : lp::Acc<4>::kPlane);
     a.contrib = ctx->contrib.p;
     a.contrib_stride = ctx->contrib_stride;
-    a.sparse_lanes = ctx->tune.sparse_lanes;
     a.tile_counter = ctx->d_tile_counter + 1;
     LP_CUDA(cudaMemsetAsync(ctx->d_tile_counter + 1, 0, sizeof(int), st));
     if (a.grid > 0) {

@@ -15,38 +15,49 @@
 namespace lp {
 
 
-__device__ __forceinline__ float warp_sum(float x) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    return x;
-}
-
-// Sums of N values (N a power of two, 2..32) over the warp by recursive
-// halving: at each step a lane keeps one half of its values and adds the
-// partner's copy of that half.  Returns, in every lane, the total of value
-// warp_sum_index<N>(lane); N values cost about 4N instructions instead of
-// 10N for N separate warp_sum calls.
-template <int N>
-__device__ __forceinline__ float warp_sum_multi(float (&v)[N], int lane) {
-#pragma unroll
-    for (int m = N, o = 16; m > 1; m >>= 1, o >>= 1) {
-        const bool up = (lane & o) != 0;
-#pragma unroll
-        for (int k = 0; k < m / 2; ++k) {
-            const float send = up ? v[k] : v[k + m / 2];
-            const float keep = up ? v[k + m / 2] : v[k];
-            v[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
-        }
+// Lane groups of a blend warp (lane_groups(TILE, PIX) of them: 1, 2 or 4).
+// The forward writes one contributor-mask row per group and the backward's
+// groups walk
+// their own rows independently, so that a group visits only the entries that
+// its own pixels blended.  Four groups are the quadrants of the warp's pixel
+// rectangle, two its upper and lower halves.  A warp rectangle has WR rows
+// of TPR threads (WR * TPR = 32): lanes 16..31 hold its lower half (lane bit
+// 4), and lane bit log2(TPR) - 1 marks a thread in the right half of a row.
+template <int TILE, int PIX> struct LaneGroups {
+    using WG = WarpGrid<TILE, PIX>;
+    static constexpr int G = lane_groups(TILE, PIX);
+    static_assert(G == 1 || G == 2 || G == 4, "1, 2 or 4 lane groups");
+    static_assert(WG::TPR * WG::WR == 32 && WG::TPR >= 2 && WG::TPR <= 16, "rows of whole threads");
+    static constexpr int kColBit = WG::TPR == 2 ? 0 : WG::TPR == 4 ? 1 : WG::TPR == 8 ? 2 : 3;
+    // the lane bits that name a group
+    static constexpr uint32_t kGroupBits = G == 1 ? 0u : G == 2 ? 16u : (16u | (1u << kColBit));
+    __device__ __forceinline__ static int group(int lane) {
+        return G == 1 ? 0 : G == 2 ? lane >> 4 : ((lane >> 4) << 1) | ((lane >> kColBit) & 1);
     }
-    float t = v[0];
+    // the group's first lane (every other lane bit clear) writes its mask row
+    __device__ __forceinline__ static bool leader(int lane) { return (lane & ~(int)kGroupBits) == 0; }
+    // OR of x over the lanes of each lane's group
+    __device__ __forceinline__ static uint32_t reduce_or(uint32_t x) {
+        if (G == 1) return __reduce_or_sync(0xffffffffu, x);
 #pragma unroll
-    for (int o = 16 / N; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-    return t;
-}
+        for (int b = 0; b < 5; ++b)
+            if (!((kGroupBits >> b) & 1u)) x |= __shfl_xor_sync(0xffffffffu, x, 1 << b);
+        return x;
+    }
+};
 
-template <int N>
-__device__ __forceinline__ int warp_sum_index(int lane) {
-    return (lane >> (5 - (N >= 32 ? 5 : N >= 16 ? 4 : N >= 8 ? 3 : N >= 4 ? 2 : 1))) & (N - 1);
+// Word w of lane group g's contributor-mask row for warp `warp` of a tile.
+// The G rows of a warp are interleaved word by word (a warp's block holds
+// cstride words per group), so that the groups' words of one chunk of
+// entries share a 32-byte sector.
+template <int G>
+__device__ __forceinline__ uint32_t* mask_word(uint32_t* contrib, uint32_t cstride, int warp, int g, uint32_t w) {
+    return contrib + (size_t)warp * G * cstride + (size_t)w * G + g;
+}
+template <int G>
+__device__ __forceinline__ const uint32_t* mask_word(const uint32_t* contrib, uint32_t cstride, int warp, int g,
+                                                     uint32_t w) {
+    return contrib + (size_t)warp * G * cstride + (size_t)w * G + g;
 }
 
 struct TileGeom {

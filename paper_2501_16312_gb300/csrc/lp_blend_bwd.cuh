@@ -1,7 +1,8 @@
 // Backward per-tile rasterization (sm_103a).
 //
-// A warp skips the entries the forward blended at none of its pixels (the
-// forward's per-warp mask) without evaluating their spans.
+// A lane group of a warp (LaneGroups) skips the entries the forward blended
+// at none of its pixels (the forward's mask row of that group) without
+// evaluating their spans; the groups of a warp walk their rows independently.
 //
 // Sec. 3.4 "Rasterization Backpropagation": each tile walks its list back to
 // front from the furthest last contributor of its pixels, recomputes every
@@ -18,8 +19,7 @@
 // thread sums its strip of pixels: the colour and sigma terms into one
 // 16-byte row, each face's (x, y, 1) terms into one row per run of pixels
 // sharing the face; it adds each row to the record's accumulator with one
-// vector atomic (sm_90 and later).  Only the colour row may first be summed
-// over the warp with shuffles, when many lanes contribute.
+// vector atomic (sm_90 and later).
 //
 // The kernels are templates over the tile edge; each of lp_blend_bwd_t8.cu,
 // _t16.cu and _t32.cu instantiates one edge.
@@ -52,7 +52,7 @@ __global__ void __launch_bounds__(TILE * TILE / PIX, bwd_min_blocks<TILE, PIX>()
     const uint32_t* __restrict__ last_in, const float* __restrict__ tl_in, float* __restrict__ acc,
     float* __restrict__ acc_col,
     int* __restrict__ tile_counter, const uint32_t* __restrict__ contrib, uint32_t cstride,
-    int sparse_lanes, const uint32_t* __restrict__ order) {
+    const uint32_t* __restrict__ order) {
     constexpr int ACC = Acc<V>::kPlane;
     constexpr int NT = TILE * TILE / PIX;
     constexpr int MW = BATCH / 32;   // contributor-mask words per batch
@@ -65,6 +65,7 @@ __global__ void __launch_bounds__(TILE * TILE / PIX, bwd_min_blocks<TILE, PIX>()
     const int lane = tid & 31;
     int ly, lx0;   // the forward's pixel layout, so that warp w's mask bits are its own
     WarpGrid<TILE, PIX>::pixel(tid, ly, lx0);
+    using LG = LaneGroups<TILE, PIX>;
     for (;;) {
         if (tid == 0) {
             const int q = atomicAdd(tile_counter, 1);
@@ -105,22 +106,26 @@ __global__ void __launch_bounds__(TILE * TILE / PIX, bwd_min_blocks<TILE, PIX>()
             const int nb = hi - lo;
             __syncthreads();
             for (int j = tid; j < nb; j += NT) stage_record<V>(rec, vals[rg.x + lo + j], tg.tx0, tg.ty0, sm[j]);
-            // This warp's bits of the forward's contributor mask for entries
-            // lo .. hi - 1 (bit j of bm: entry lo + j), loaded once per batch:
-            // lane q fetches word q of the run, the warp shifts them into
-            // place, and the walk below visits the set bits only.
+            // This lane group's bits of the forward's contributor mask for
+            // entries lo .. hi - 1 (bit j of bm: entry lo + j), loaded once
+            // per batch: lane g (MW + 1) + q fetches word q of group g's run,
+            // each lane shifts its own group's words into place, and the walk
+            // below visits the set bits only.
+            const int grp = LG::group(lane);
             uint32_t bm[MW];
             {
                 const uint32_t e0 = rg.x + (uint32_t)lo;
                 const uint32_t w0 = e0 >> 5, sh = e0 & 31u;
                 const uint32_t w_last = (e0 + (uint32_t)nb - 1u) >> 5;   // last word of the run
+                const int lg = lane / (MW + 1), lq = lane - lg * (MW + 1);
                 uint32_t src = 0u;
-                if (lane <= MW && w0 + (uint32_t)lane <= w_last)
-                    src = contrib ? __ldg(contrib + (size_t)(tid >> 5) * cstride + w0 + lane) : 0xffffffffu;
+                if (lg < LG::G && w0 + (uint32_t)lq <= w_last)
+                    src = contrib ? __ldg(mask_word<LG::G>(contrib, cstride, tid >> 5, lg, w0 + (uint32_t)lq))
+                                  : 0xffffffffu;
 #pragma unroll
                 for (int q = 0; q < MW; ++q) {
-                    const uint32_t lo_w = __shfl_sync(0xffffffffu, src, q);
-                    const uint32_t hi_w = __shfl_sync(0xffffffffu, src, q + 1);
+                    const uint32_t lo_w = __shfl_sync(0xffffffffu, src, grp * (MW + 1) + q);
+                    const uint32_t hi_w = __shfl_sync(0xffffffffu, src, grp * (MW + 1) + q + 1);
                     uint32_t m = sh ? (lo_w >> sh) | (hi_w << (32u - sh)) : lo_w;
                     const int valid = nb - 32 * q;   // entries of this word inside the batch
                     if (valid < 32) m &= valid > 0 ? (1u << valid) - 1u : 0u;
@@ -128,19 +133,27 @@ __global__ void __launch_bounds__(TILE * TILE / PIX, bwd_min_blocks<TILE, PIX>()
                 }
             }
             __syncthreads();
+            // Each lane group walks its own set bits, back to front, one mask
+            // word at a time; the warp steps while some group has a bit left
+            // in the word, and a group without one idles.  Entries the forward
+            // blended at none of a group's pixels are never visited by that
+            // group.
 #pragma unroll 1
             for (int q = MW - 1; q >= 0; --q)
-            for (uint32_t mq = bm[q]; mq != 0u;) {
-                // entries the forward blended at none of this warp's pixels are
-                // never visited
-                const int bit = 31 - __clz(mq);
-                mq ^= 1u << bit;
-                const int j = 32 * q + bit;
+            for (uint32_t mq = bm[q];;) {
+                const bool have = mq != 0u;
+                if (!__any_sync(0xffffffffu, have)) break;
+                int j = 0;
+                if (have) {
+                    const int bit = 31 - __clz(mq);
+                    mq ^= 1u << bit;
+                    j = 32 * q + bit;
+                }
                 const uint32_t idx = (uint32_t)(lo + j);
                 const Staged<V>& p = sm[j];
                 bool any = false;
 #pragma unroll
-                for (int i = 0; i < PIX; ++i) any |= idx < last[i];
+                for (int i = 0; i < PIX; ++i) any |= have && idx < last[i];
                 float sp[PIX];
                 int sf[PIX], sb[PIX];
                 bool c[PIX];
@@ -157,8 +170,7 @@ __global__ void __launch_bounds__(TILE * TILE / PIX, bwd_min_blocks<TILE, PIX>()
                         anyc |= c[i];
                     }
                 }
-                const unsigned bal = __ballot_sync(0xffffffffu, anyc);
-                if (bal == 0u) continue;
+                if (!__any_sync(0xffffffffu, anyc)) continue;
                 float gr0 = 0.f, gr1 = 0.f, gr2 = 0.f, gsig = 0.f;
                 float gsp[PIX];
 #pragma unroll
@@ -191,18 +203,12 @@ __global__ void __launch_bounds__(TILE * TILE / PIX, bwd_min_blocks<TILE, PIX>()
                 }
                 float* A = acc + (size_t)p.rec * ACC;        // plane moments
                 float* Ac = acc_col + (size_t)p.rec * 4;     // colour and density
-                // Colour and density: with more than sparse_lanes contributing
-                // lanes the whole warp first sums the four terms with shuffles
-                // (one total per lane group of 8); otherwise each contributing
-                // lane adds its own row with one 16-byte vector atomic.
-                if (__popc(bal) > sparse_lanes) {
-                    float hv[4] = {gr0, gr1, gr2, gsig};
-                    const float t = warp_sum_multi<4>(hv, lane);
-                    if ((lane & 7) == 0) atomicAdd(Ac + warp_sum_index<4>(lane), t);
-                } else if (anyc) {
-                    atomicAdd(reinterpret_cast<float4*>(Ac), make_float4(gr0, gr1, gr2, gsig));
-                }
                 if (!anyc) continue;
+                // Colour and density: each contributing lane adds its own row
+                // with one 16-byte vector atomic (measured faster than summing
+                // over the lane group with shuffles first, at every threshold
+                // of contributing lanes tried).
+                atomicAdd(reinterpret_cast<float4*>(Ac), make_float4(gr0, gr1, gr2, gsig));
                 // Planes: each contributing lane adds the (x, y, 1) row of an
                 // entry or exit face once per run of its pixels that share
                 // that face, one 16-byte vector atomic each (measured faster
@@ -241,7 +247,7 @@ template <int V, int BATCH, int PIX, int TILE>
 cudaError_t bwd_t(const BlendArgs& a, cudaStream_t st) {
     k_blend_bwd<V, BATCH, PIX, TILE><<<a.grid, TILE * TILE / PIX, 0, st>>>(
         a.rec, a.vals, a.ranges, *a.cams, a.bg[0], a.bg[1], a.bg[2], a.dimage, a.last, a.tl, a.acc,
-        a.acc_col, a.tile_counter, a.contrib, a.contrib_stride, a.sparse_lanes, a.order);
+        a.acc_col, a.tile_counter, a.contrib, a.contrib_stride, a.order);
     return cudaGetLastError();
 }
 

@@ -9,8 +9,9 @@
 // after blending the primitive that crossed it.  A tile stops when all of its
 // pixels have.  Per pixel the kernel keeps, for the backward, the number of
 // list entries up to the last contributor and the transmittance before it,
-// and per warp one bit per list entry its pixels blended.  A warp skips the
-// records that the staging test proves cover none of its pixels.
+// and per lane group of a warp (LaneGroups) one bit per list entry its
+// pixels blended.  A warp skips the records that the staging test proves
+// cover none of its pixels.
 //
 // MODE 1 also counts (pixel, primitive) pairs.  MODE 2 is the depth pass
 // (App. "Depth and Surface Reconstruction"): the same walk, stopping each
@@ -27,6 +28,14 @@
 namespace lp {
 
 namespace {
+
+// Word w of a contributor-mask row, at p: a plain store when the word holds
+// entries of this tile only (no other block writes it, and it is written
+// once), an atomic OR when it may share bits with a neighbouring tile's list.
+__device__ __forceinline__ void put_mask_word(uint32_t* p, uint32_t w, uint32_t v, uint2 rg) {
+    if (32ull * w >= rg.x && 32ull * w + 32ull <= rg.y) *p = v;
+    else atomicOr(p, v);
+}
 
 template <int V, int BATCH, int PIX, int MODE, int TILE>
 __global__ void __launch_bounds__(TILE * TILE / PIX) k_blend_fwd(
@@ -65,6 +74,9 @@ __global__ void __launch_bounds__(TILE * TILE / PIX) k_blend_fwd(
         float dep[PIX];              // depth pass only
         bool done[PIX];
         bool tdone = true;
+        // mask bits of this lane group waiting for the next chunk to complete
+        // their word (group leaders only)
+        uint32_t pend = 0u;
 #pragma unroll
         for (int i = 0; i < PIX; ++i) {
             T[i] = 1.f; c0[i] = c1[i] = c2[i] = 0.f; tl[i] = 1.f; last[i] = 0;
@@ -132,14 +144,29 @@ __global__ void __launch_bounds__(TILE * TILE / PIX) k_blend_fwd(
                         if (__all_sync(0xffffffffu, tdone)) { stop = true; break; }
                     }
                     if (write_mask) {
-                        // entries b0 + jw .. b0 + jw + 31 of the tile's list
-                        bm = __reduce_or_sync(0xffffffffu, bm);
-                        if (lane == 0 && bm) {
+                        // entries b0 + jw .. b0 + jw + 31 of the tile's list,
+                        // blended at some pixel of this lane's group.  Chunks
+                        // follow each other without gaps until the warp stops,
+                        // so word w is complete once this chunk's low part
+                        // joins the previous chunk's high part.
+                        using LG = LaneGroups<TILE, PIX>;
+                        bm = LG::reduce_or(bm);
+                        if (LG::leader(lane)) {
                             const uint32_t e0 = rg.x + (uint32_t)(b0 + jw);
                             const uint32_t w = e0 >> 5, sh = e0 & 31u;
-                            uint32_t* cw = contrib + (size_t)(tid >> 5) * cstride;   // this warp's mask
-                            atomicOr(cw + w, bm << sh);
-                            if (sh) atomicOr(cw + w + 1, bm >> (32u - sh));
+                            const uint32_t v = pend | (bm << sh);
+                            if (v) {
+                                put_mask_word(mask_word<LG::G>(contrib, cstride, tid >> 5, LG::group(lane), w), w,
+                                              v, rg);
+                            }
+                            pend = sh ? bm >> (32u - sh) : 0u;
+                            // no chunk follows after the tile's last one or once
+                            // the warp stops: the next word is complete as well
+                            if (pend && (stop || b0 + jw + 32 >= n)) {
+                                put_mask_word(mask_word<LG::G>(contrib, cstride, tid >> 5, LG::group(lane), w + 1u),
+                                              w + 1u, pend, rg);
+                                pend = 0u;
+                            }
                         }
                     }
                 }

@@ -108,11 +108,13 @@ struct BlendArgs {
     bool count;
     float* depth;          // depth pass output (forward kernel in depth mode when non-null)
     const uint32_t* order = nullptr;   // queue position -> tile (null: tiles in index order)
-    uint32_t contrib_stride = 0;   // words per warp of the contributor mask
-    int sparse_lanes = 8;          // backward: per-lane atomics up to this many contributing lanes
-    uint32_t* contrib;     // per warp w of a tile (its bits at contrib + w * contrib_stride), one
-                           // bit per tile-list entry: some pixel of that warp blended the entry
-                           // (written by the forward when non-null, read by the backward)
+    uint32_t contrib_stride = 0;   // words per lane-group row of the contributor mask
+    uint32_t* contrib;     // per lane group g of warp w of a tile, one bit per tile-list entry:
+                           // some pixel of that group blended the entry (written by the
+                           // forward when non-null, read by the backward).  Word x of group g
+                           // is at contrib + w * G * contrib_stride + x * G + g,
+                           // with G = lane_groups (groups interleaved word by word); the
+                           // exact-span blends keep one row per warp, at w * contrib_stride
 };
 
 // Blends for one tile edge each (lp_blend_{fwd,bwd}_t{8,16,32}.cu).
@@ -145,8 +147,14 @@ inline int blend_bwd_occupancy(int tile, int V, int batch, int pix) {
     return tile == 8 ? blend_bwd_occupancy_t8(V, batch, pix)
          : tile == 32 ? blend_bwd_occupancy_t32(V, batch, pix) : blend_bwd_occupancy_t16(V, batch, pix);
 }
-// warps per tile of the ray-space blends (one contributor-mask row each)
+// warps per tile of the ray-space blends
 inline int blend_warps(int tile, int pix) { return tile * tile / pix / 32; }
+// Lane groups per warp of the ray-space blends: the forward writes one
+// contributor-mask row per group (quadrants of the warp's pixel rectangle),
+// and each group of the backward walks its own row.
+constexpr int kLaneGroupsMax = 4;
+constexpr int lane_groups(int tile, int pix) { return 4; }
+inline int blend_mask_rows(int tile, int pix) { return blend_warps(tile, pix) * lane_groups(tile, pix); }
 
 // exact spans (no ray-space approximation): own records, accumulators and kernels
 int rec_floats_x(int V);

@@ -10,7 +10,7 @@ import pytest
 from paper_2501_16312_gb300 import autotune
 
 BASE = dict(tile=16, batch=64, blocks_per_sm=0, sort_mode=0, pixels_per_thread=4, chain_split=0,
-            sparse_lanes=8, radix_bits=8, tile_order=0, onesweep=0)
+            radix_bits=8, tile_order=0, onesweep=0)
 
 
 def stage_model(k):
@@ -25,7 +25,7 @@ def stage_model(k):
            (1, 128): 1.85, (2, 128): 1.75, (4, 128): 1.5}[
         (k["pixels_per_thread"], k["batch"])]
     fwd *= {8: 0.9, 16: 1.0, 32: 1.3}[k["tile"]]
-    bwd = 3.0 + (0.3 if k["pixels_per_thread"] == 2 else 0.0) - (0.2 if k["sparse_lanes"] == 16 else 0.0)
+    bwd = 3.0 + (0.3 if k["pixels_per_thread"] == 2 else 0.0)
     if k["sort_mode"] == 1:
         fwd += 0.05                      # a slower blend must not change the sort choice
     chain = 0.5 if k["chain_split"] == 1 else 0.6
@@ -78,10 +78,10 @@ def test_search_picks_each_groups_best_in_order():
 
     entry = autotune.search(apply, lambda: stage_model(knobs), BASE)
     want = dict(BASE, sort_mode=1, radix_bits=11, tile=16, pixels_per_thread=4, batch=64, blocks_per_sm=0,
-                chain_split=1, sparse_lanes=16)
+                chain_split=1)
     assert entry["tuning"] == want
     assert knobs == want                                # the winners are left applied
-    assert len(entry["trials"]) == 16 + 18 + 16 + 2 + 3 + 2
+    assert len(entry["trials"]) == 16 + 18 + 16 + 2 + 2
     # the sort group is judged on its own stages only, at both visits
     assert entry["best_ms"]["sort_mode+radix_bits+onesweep"] == pytest.approx(0.45)
     assert entry["best_ms"]["sort_mode+radix_bits+onesweep (again)"] == pytest.approx(0.45)
@@ -123,7 +123,7 @@ def test_search_ties_keep_the_first_candidate():
             "blend_bwd": 1.0, "chain": 1.0}
     entry = autotune.search(knobs.update, lambda: flat, BASE)
     assert entry["tuning"] == dict(BASE, sort_mode=0, radix_bits=4, tile=8, pixels_per_thread=1, batch=32,
-                                   chain_split=0, sparse_lanes=8)
+                                   chain_split=0)
 
 
 def test_cache_key_buckets():
@@ -158,9 +158,9 @@ def test_tune_caches_reuses_and_restores_timing(fake_cuda, tmp_path):
     cache = str(tmp_path / "sub" / "tuning.json")
     rast = FakeRast()
     entry = autotune.tune(rast, prims, cams, reps=2, cache=cache)
-    want = dict(BASE, sort_mode=1, radix_bits=11, pixels_per_thread=4, batch=64, chain_split=1, sparse_lanes=16)
+    want = dict(BASE, sort_mode=1, radix_bits=11, pixels_per_thread=4, batch=64, chain_split=1)
     assert entry["tuning"] == want and rast.knobs == want
-    assert rast.measured == 57 * 3                       # 57 trials x (warm-up + 2 timed)
+    assert rast.measured == 54 * 3                       # 54 trials x (warm-up + 2 timed)
     assert rast.timing_calls == [True, False]            # timing restored to off
     stored = json.load(open(cache))
     key = autotune.cache_key("FakeGPU", 6, 10, cams)
@@ -174,10 +174,27 @@ def test_tune_caches_reuses_and_restores_timing(fake_cuda, tmp_path):
     rast3 = FakeRast()
     rast3.set_timing(True)
     autotune.tune(rast3, prims, cams, reps=1, cache=cache, force=True)
-    assert rast3.measured == 57 * 2 and rast3.timing() is True
+    assert rast3.measured == 54 * 2 and rast3.timing() is True
     # other workloads share the file
     autotune.tune(FakeRast(), prims, cams[:1], reps=1, cache=cache)
     assert len(json.load(open(cache))) == 2
+
+
+def test_tune_retimes_a_cached_entry_with_other_knobs(fake_cuda, tmp_path):
+    """An entry written by a build with another set of knobs is not applied:
+    the search runs again and replaces it."""
+    torch = fake_cuda
+    prims, cams = _fake_workload(torch)
+    cache = tmp_path / "tuning.json"
+    key = autotune.cache_key("FakeGPU", 6, 10, cams)
+    stale = dict(BASE, sparse_lanes=8)
+    cache.write_text(json.dumps({key: {"tuning": stale, "best_ms": {}, "trials": []}}))
+    assert autotune.load_cache(str(cache), key)["tuning"] == stale
+    assert autotune.load_cache(str(cache), key, knobs=BASE) is None
+    rast = FakeRast()
+    entry = autotune.tune(rast, prims, cams, reps=1, cache=str(cache))
+    assert rast.measured == 54 * 2 and set(entry["tuning"]) == set(BASE)   # warm-up + 1 timed
+    assert json.load(open(cache))[key]["tuning"] == entry["tuning"]
 
 
 def test_tune_tolerates_a_corrupt_cache(fake_cuda, tmp_path):

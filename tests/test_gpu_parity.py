@@ -417,9 +417,8 @@ def test_cuda_graph_capture_replays(rast):
 
 def test_every_tuning_renders_identical_images(rast):
     """Tile edge, tile order, sort mode, radix width, pixels per thread,
-    batch, grid size, chain form and the sparse-atomics threshold change the
-    schedule,
-    never the arithmetic of a pixel: images are bitwise identical and
+    batch, grid size and chain form change the schedule, never the
+    arithmetic of a pixel: images are bitwise identical and
     gradients agree to float rounding (atomics and the chain form reorder the
     sums)."""
     import itertools
@@ -430,16 +429,16 @@ def test_every_tuning_renders_identical_images(rast):
     try:
         rast.set_tuning(tile=16, pixels_per_thread=4)
         img16, g16 = gpu_forward_backward(rast, w.scene, w.cameras, (0.1, 0.1, 0.1), dL)
-        for (tile, pix), sm, rb, batch, bps, (cs, sl), to, ow in itertools.product(
-                tile_pix, [0, 1], [4, 11, 8], [32, 128], [0, 1], [(0, 0), (1, 32)], [0, 1], [0, 1]):
+        for (tile, pix), sm, rb, batch, bps, cs, to, ow in itertools.product(
+                tile_pix, [0, 1], [4, 11, 8], [32, 128], [0, 1], [0, 1], [0, 1], [0, 1]):
             if (rb != 8 or to or ow) and (batch, bps, cs) != (32, 0, 0):
                 continue    # the digit width, sort form and tile order touch one stage each
             rast.set_tuning(tile=tile, sort_mode=sm, radix_bits=rb, pixels_per_thread=pix, batch=batch,
-                            blocks_per_sm=bps, chain_split=cs, sparse_lanes=sl, tile_order=to, onesweep=ow)
+                            blocks_per_sm=bps, chain_split=cs, tile_order=to, onesweep=ow)
             img, g = gpu_forward_backward(rast, w.scene, w.cameras, (0.1, 0.1, 0.1), dL)
             np.testing.assert_array_equal(img, img16)
             for k in g:
-                assert rel_l2(g[k], g16[k]) <= 1e-5, (tile, sm, rb, pix, batch, bps, cs, sl, to, ow, k)
+                assert rel_l2(g[k], g16[k]) <= 1e-5, (tile, sm, rb, pix, batch, bps, cs, to, ow, k)
     finally:
         rast.set_tuning(**base)
 
