@@ -120,17 +120,20 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-# Algorithmic FP32 work of the blend kernels, in flops (an FMA counts 2):
-#   per evaluated (pixel, primitive) pair: F planes x 2 FMA + F min/max +
+# Algorithmic FP32 work of the blend kernels, in flops (an FMA counts 2), on
+# the pair counts of the paper's algorithm (every tile-list entry a pixel
+# walks; the kernels skip the ones they prove uncovered, so this is the work
+# the method asks for, not the work a schedule happens to do):
+#   per iterated (pixel, primitive) pair: F planes x 2 FMA + F min/max +
 #   span subtraction + span test                 = 5F + 2
 #   forward, per intersected pair: sigma*s, exp, 1 - tau, T*(1-tau),
 #   3 colour FMA, T*tau, stop test               = 12
-#   backward, per pair evaluated up to the pixel's last contributor: 5F + 2;
+#   backward, per pair iterated up to the pixel's last contributor: 5F + 2;
 #   per contributor: tau, T division, 3 colour grads, dL/do (3 FMA), suffix
 #   colour (3 FMA + 3 mul), span/sigma grads, (x, y, 1) weights of two faces ~ 40
 def blend_flops(F, pairs):
-    fwd = (5 * F + 2) * pairs["evaluated"] + 12 * pairs["intersected"]
-    bwd = (5 * F + 2) * pairs["evaluated_to_last"] + 40 * pairs["intersected"]
+    fwd = (5 * F + 2) * pairs["iterated"] + 12 * pairs["intersected"]
+    bwd = (5 * F + 2) * pairs["iterated_to_last"] + 40 * pairs["intersected"]
     return fwd, bwd
 
 

@@ -346,12 +346,14 @@ lp_status lp_debug_pixel_state(lp_ctx* ctx, unsigned int* last, float* T_last, l
 /* Workload counters of the last forward (synchronises; runs an instrumented
  * copy of the blend).  counts: host long long[4] receiving the numbers of
  * (pixel, primitive) pairs
- *   [0] iterated: tile-list entries each pixel visits before it stops,
- *   [1] evaluated: of those, pairs whose face planes are evaluated (every
- *       visited entry, in this implementation),
+ *   [0] iterated: tile-list entries each pixel walks, front to back, up to
+ *       the one that stops it (the whole list if none does),
+ *   [1] evaluated: of those, pairs whose face planes the blend evaluates
+ *       (not proven uncovered for the pixel's lane group by the staging
+ *       test; the exact-span mode evaluates every iterated pair),
  *   [2] intersected: the pixel ray crosses the primitive,
- *   [3] evaluated up to each pixel's last contributor (the pairs the
- *       backward re-evaluates).
+ *   [3] iterated up to each pixel's last contributor: the entries the
+ *       paper's backward walks, back to front from that contributor.
  * [0] and [2] are the "iterated" and "intersected" counts of the paper's
  * App. "Rendering Performance and Efficiency", Table 7.                     */
 lp_status lp_count_pairs(lp_ctx* ctx, long long* counts);

@@ -288,7 +288,7 @@ class Rasterizer:
         each pixel's last contributor (the backward's work)."""
         out = (C.c_longlong * 4)()
         _native.check(self.ctx, self.lib.lp_count_pairs(self.ctx, out), "lp_count_pairs")
-        return dict(iterated=out[0], evaluated=out[1], intersected=out[2], evaluated_to_last=out[3])
+        return dict(iterated=out[0], evaluated=out[1], intersected=out[2], iterated_to_last=out[3])
 
 
 def _make_fn():

@@ -54,8 +54,11 @@ __global__ void __launch_bounds__(TILE * TILE / PIX) k_blend_fwd(
     const int lane = tid & 31;
     int ly, lx0;
     WarpGrid<TILE, PIX>::pixel(tid, ly, lx0);
+    using LG = LaneGroups<TILE, PIX>;
+    const int grp = LG::group(lane);
+    const uint32_t group_lanes = __match_any_sync(0xffffffffu, grp);   // the lanes of this lane's group
     const bool write_mask = !DEPTH && contrib != nullptr;
-    unsigned long long n_iter = 0, n_eval = 0, n_hit = 0, n_eval_last = 0;
+    unsigned long long n_iter = 0, n_eval = 0, n_hit = 0, n_iter_last = 0;
     for (;;) {
         if (tid == 0) {
             const int q = atomicAdd(tile_counter, 1);
@@ -70,7 +73,6 @@ __global__ void __launch_bounds__(TILE * TILE / PIX) k_blend_fwd(
         const int n = (int)(rg.y - rg.x);
         float T[PIX], c0[PIX], c1[PIX], c2[PIX], tl[PIX];
         uint32_t last[PIX];
-        uint32_t ce[PIX], cl[PIX];   // counting only: evaluations so far / at the last contributor
         float dep[PIX];              // depth pass only
         bool done[PIX];
         bool tdone = true;
@@ -80,7 +82,6 @@ __global__ void __launch_bounds__(TILE * TILE / PIX) k_blend_fwd(
 #pragma unroll
         for (int i = 0; i < PIX; ++i) {
             T[i] = 1.f; c0[i] = c1[i] = c2[i] = 0.f; tl[i] = 1.f; last[i] = 0;
-            ce[i] = cl[i] = 0;
             dep[i] = 0.f;
             done[i] = !(tg.tx0 + lx0 + i < tg.width && py < tg.height);
             tdone &= done[i];
@@ -89,92 +90,110 @@ __global__ void __launch_bounds__(TILE * TILE / PIX) k_blend_fwd(
             if (__syncthreads_count(!tdone) == 0) break;
             const int nb = min(BATCH, n - b0);
             for (int j = tid; j < nb; j += NT) {
-                stage_record<V>(rec, vals[rg.x + b0 + j], tg.tx0, tg.ty0, sm[j]);
-                sm[j].bands = band_mask<V, TILE, PIX>(sm[j]);
+                const uint32_t meta = stage_record<V>(rec, vals[rg.x + b0 + j], tg.tx0, tg.ty0, sm[j]);
+                sm[j].bands = band_mask<V, TILE, PIX>(sm[j], meta);
             }
             __syncthreads();
             if (__any_sync(0xffffffffu, !tdone)) {   // warp-uniform, as the exit below
-                bool stop = false;
-                for (int jw = 0; jw < nb && !stop; jw += 32) {
-                    uint32_t bm = 0;   // bit j - jw: this thread blended entry b0 + j
-                    const int je = min(nb, jw + 32);
-                    for (int j = jw; j < je; ++j) {
-                        const Staged<V>& p = sm[j];
-                        if (COUNT) {
+                for (int jw = 0; jw < nb; jw += 32) {
+                    // Entries b0 + jw .. b0 + jw + 31: the ones the staging
+                    // test leaves possibly covered in this lane group's
+                    // rectangle (bit j - jw), one ballot per group.
+                    uint32_t mq = 0u;
+                    {
+                        const int jl = jw + lane;
+                        const uint64_t bl = jl < nb ? sm[jl].bands >> ((tid >> 5) * LG::G) : 0ull;
 #pragma unroll
-                            for (int i = 0; i < PIX; ++i) n_iter += !done[i];
+                        for (int g = 0; g < LG::G; ++g) {
+                            const uint32_t bal = __ballot_sync(0xffffffffu, (uint32_t)(bl >> g) & 1u);
+                            mq = grp == g ? bal : mq;
                         }
-                        // warp-uniform: no pixel of this warp's rectangle can meet it
-                        if (!((p.bands >> (tid >> 5)) & 1u)) continue;
-                        float sp[PIX];
-                        spans<V, PIX, false>(p, (float)lx0 + p.dx0, (float)ly + p.dy0, sp, nullptr, nullptr);
-                        tdone = true;
-                        bool blended = false;
-#pragma unroll
-                        for (int i = 0; i < PIX; ++i) {
-                            const bool in = !done[i];   // visited and not proven uncovered: evaluated
-                            if (COUNT) { n_eval += in; ce[i] += in; }
-                            if (in && sp[i] > 0.f) {
-                                blended = true;
-                                if (COUNT) { ++n_hit; cl[i] = ce[i]; }
-                                const float xs = span_x(p.sigma, sp[i]);
-                                const float tau = span_tau(xs);
-                                const float w = T[i] * span_opacity(xs, tau);
-                                c0[i] = fmaf(w, p.r, c0[i]);
-                                c1[i] = fmaf(w, p.g, c1[i]);
-                                c2[i] = fmaf(w, p.b, c2[i]);
-                                tl[i] = T[i];
-                                T[i] *= tau;
-                                last[i] = (uint32_t)(b0 + j + 1);
-                                done[i] = T[i] < kStop;
-                                if (DEPTH && done[i]) {
-                                    // entry depth: centre depth + max over the entry faces
-                                    float e = -CUDART_INF_F;
-                                    for (int f = 0; f < p.nf; ++f)
-                                        e = fmaxf(e, __fmaf_rn(p.pl[f].x, (float)(lx0 + i) + p.dx0,
-                                                               __fmaf_rn(p.pl[f].y, (float)ly + p.dy0, p.pl[f].z)));
-                                    dep[i] = __fadd_rn(p.pl[0].w, e);
-                                }
-                            }
-                            tdone &= done[i];
-                        }
-                        if (write_mask && blended) bm |= 1u << (j - jw);
-                        // warp-uniform exit (the mask reduction below needs every
-                        // lane); a warp issues the loop while any lane is active
-                        if (__all_sync(0xffffffffu, tdone)) { stop = true; break; }
                     }
+                    uint32_t bm = 0;   // bit j - jw: this thread blended entry b0 + j
+                    // Each lane group walks its own entries front to back, and
+                    // stops taking them once all of its pixels have stopped;
+                    // the warp steps while some group has one left.
+                    for (;;) {
+                        if (!(__ballot_sync(0xffffffffu, !tdone) & group_lanes)) mq = 0u;
+                        const bool have = mq != 0u;
+                        if (!__any_sync(0xffffffffu, have)) break;
+                        if (have) {
+                            const int bit = __ffs(mq) - 1;
+                            mq &= mq - 1u;
+                            const int j = jw + bit;
+                            const Staged<V>& p = sm[j];
+                            float sp[PIX];
+                            spans<V, PIX, false>(p, (float)lx0 + p.dx0, (float)ly + p.dy0, sp, nullptr, nullptr);
+                            tdone = true;
+                            bool blended = false;
+#pragma unroll
+                            for (int i = 0; i < PIX; ++i) {
+                                const bool in = !done[i];   // visited and not proven uncovered: evaluated
+                                if (COUNT) n_eval += in;
+                                if (in && sp[i] > 0.f) {
+                                    blended = true;
+                                    if (COUNT) ++n_hit;
+                                    const float xs = span_x(p.sigma, sp[i]);
+                                    const float tau = span_tau(xs);
+                                    const float w = T[i] * span_opacity(xs, tau);
+                                    c0[i] = fmaf(w, p.r, c0[i]);
+                                    c1[i] = fmaf(w, p.g, c1[i]);
+                                    c2[i] = fmaf(w, p.b, c2[i]);
+                                    tl[i] = T[i];
+                                    T[i] *= tau;
+                                    last[i] = (uint32_t)(b0 + j + 1);
+                                    done[i] = T[i] < kStop;
+                                    if (DEPTH && done[i]) {
+                                        // entry depth: centre depth + max over the entry faces
+                                        float e = -CUDART_INF_F;
+                                        for (int f = 0; f < p.nf; ++f)
+                                            e = fmaxf(e, __fmaf_rn(p.pl[f].x, (float)(lx0 + i) + p.dx0,
+                                                                   __fmaf_rn(p.pl[f].y, (float)ly + p.dy0, p.pl[f].z)));
+                                        dep[i] = __fadd_rn(p.pl[0].w, e);
+                                    }
+                                }
+                                tdone &= done[i];
+                            }
+                            if (write_mask && blended) bm |= 1u << bit;
+                        }
+                    }
+                    // the warp stops once all of its pixels have
+                    const bool stop = !__any_sync(0xffffffffu, !tdone);
                     if (write_mask) {
                         // entries b0 + jw .. b0 + jw + 31 of the tile's list,
-                        // blended at some pixel of this lane's group.  Chunks
+                        // blended at some pixel of this lane's group.  Words
                         // follow each other without gaps until the warp stops,
-                        // so word w is complete once this chunk's low part
-                        // joins the previous chunk's high part.
-                        using LG = LaneGroups<TILE, PIX>;
+                        // so word w is complete once this word's low part
+                        // joins the previous one's high part.
                         bm = LG::reduce_or(bm);
                         if (LG::leader(lane)) {
                             const uint32_t e0 = rg.x + (uint32_t)(b0 + jw);
                             const uint32_t w = e0 >> 5, sh = e0 & 31u;
                             const uint32_t v = pend | (bm << sh);
-                            if (v) {
-                                put_mask_word(mask_word<LG::G>(contrib, cstride, tid >> 5, LG::group(lane), w), w,
-                                              v, rg);
-                            }
+                            if (v) put_mask_word(mask_word<LG::G>(contrib, cstride, tid >> 5, grp, w), w, v, rg);
                             pend = sh ? bm >> (32u - sh) : 0u;
-                            // no chunk follows after the tile's last one or once
+                            // no word follows after the tile's last one or once
                             // the warp stops: the next word is complete as well
                             if (pend && (stop || b0 + jw + 32 >= n)) {
-                                put_mask_word(mask_word<LG::G>(contrib, cstride, tid >> 5, LG::group(lane), w + 1u),
-                                              w + 1u, pend, rg);
+                                put_mask_word(mask_word<LG::G>(contrib, cstride, tid >> 5, grp, w + 1u), w + 1u,
+                                              pend, rg);
                                 pend = 0u;
                             }
                         }
                     }
+                    if (stop) break;
                 }
             }
         }
         if (COUNT) {
+            // entries a pixel walked: up to the one that stopped it, else the
+            // whole list (the tile walks on while any pixel is active); and
+            // up to its last contributor
 #pragma unroll
-            for (int i = 0; i < PIX; ++i) n_eval_last += cl[i];
+            for (int i = 0; i < PIX; ++i) {
+                n_iter_last += last[i];
+                n_iter += done[i] ? last[i] : (uint32_t)n;
+            }
         }
         const int plane = tg.width * tg.height;
         float* img = image + 3 * (size_t)tg.pix_base;
@@ -197,7 +216,7 @@ __global__ void __launch_bounds__(TILE * TILE / PIX) k_blend_fwd(
         __syncthreads();
     }
     if (COUNT) {
-        unsigned long long a = n_iter, b = n_eval, c = n_hit, d = n_eval_last;
+        unsigned long long a = n_iter, b = n_eval, c = n_hit, d = n_iter_last;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             a += __shfl_xor_sync(0xffffffffu, a, o);

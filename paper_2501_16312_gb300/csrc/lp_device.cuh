@@ -272,10 +272,11 @@ template <int V> struct alignas(16) Staged {
     float dx0, dy0;    // tx0 - X0, ty0 - Y0 (integers)
     int nf;
     int rec;           // record index (camera * n + primitive)
-    // bit w: the pixel rectangle of warp w (WarpGrid) may hold a pixel whose
-    // ray meets the primitive; clear only when some entry/exit face pair
-    // proves it cannot, with a margin above binary32 rounding
-    uint32_t bands;
+    // bit w G + g: the pixel rectangle of lane group g of warp w (WarpGrid,
+    // LaneGroups) may hold a pixel whose ray meets the primitive; clear only
+    // when some entry/exit face pair proves it cannot, with a margin above
+    // binary32 rounding (forward only)
+    uint64_t bands;
 };
 
 // Which pixels of a TILE x TILE tile a thread of a blend block owns, with
@@ -299,48 +300,10 @@ template <int TILE, int PIX> struct WarpGrid {
     }
 };
 
-// The ray meets the primitive at pixel p only if every entry face is below
-// every exit face there: d_f(p) < d_b(p).  Each pair's difference is linear
-// in p, so its largest value over a warp's rectangle is at a corner; a
-// rectangle where some pair stays below -margin holds no covered pixel.
-template <int V, int TILE, int PIX>
-__device__ __forceinline__ uint32_t band_mask(const Staged<V>& s) {
-    using G = WarpGrid<TILE, PIX>;
-    constexpr int F = Kind<V>::F;
-    constexpr int NB = G::NW;
-    static_assert(NB >= 1 && NB <= 32, "one bit per warp");
-    constexpr float XM = (float)(TILE - 1);
-    const int nf = s.nf;
-    if (nf <= 0 || nf >= F) return 0u;
-    uint32_t mask = NB == 32 ? 0xffffffffu : (1u << NB) - 1u;
-    // the margin bounds the rounding of every term of a plane's evaluation at
-    // a pixel of the tile (offsets up to |dx0| + TILE - 1 from the anchor)
-    const float ox = fabsf(s.dx0) + XM, oy = fabsf(s.dy0) + XM;
-    for (int f = 0; f < nf; ++f) {
-        const float4 pf = s.pl[f];
-        const float ef = __fmaf_rn(pf.x, s.dx0, __fmaf_rn(pf.y, s.dy0, pf.z));   // at the tile origin
-        for (int b = nf; b < F; ++b) {
-            const float4 pb = s.pl[b];
-            const float eb = __fmaf_rn(pb.x, s.dx0, __fmaf_rn(pb.y, s.dy0, pb.z));
-            const float da = pb.x - pf.x, db = pb.y - pf.y, de = eb - ef;
-            const float margin = 1e-5f * (fabsf(pb.z) + fabsf(pf.z) + fabsf(eb) + fabsf(ef) +
-                                          ox * (fabsf(pb.x) + fabsf(pf.x)) + oy * (fabsf(pb.y) + fabsf(pf.y))) +
-                                 1e-30f;
-#pragma unroll
-            for (int w = 0; w < NB; ++w) {
-                const float x0 = (float)((w % G::NWX) * G::WC), x1 = x0 + (float)(G::WC - 1);
-                const float y0 = (float)((w / G::NWX) * G::WR), y1 = y0 + (float)(G::WR - 1);
-                const float m = de + fmaxf(da * x0, da * x1) + fmaxf(db * y0, db * y1);
-                if (m < -margin) mask &= ~(1u << w);
-            }
-        }
-    }
-    return mask;
-}
-
+// Stages record r for the tile at (tx0, ty0); returns the record's meta word.
 template <int V>
-__device__ __forceinline__ void stage_record(const float* __restrict__ rec, int r, int tx0, int ty0,
-                                             Staged<V>& s) {
+__device__ __forceinline__ uint32_t stage_record(const float* __restrict__ rec, int r, int tx0, int ty0,
+                                                 Staged<V>& s) {
     constexpr int F = Kind<V>::F;
     const float4* src = reinterpret_cast<const float4*>(rec + (size_t)r * Rec<V>::kFloats);
     float buf[Rec<V>::kFloats];
@@ -360,8 +323,10 @@ __device__ __forceinline__ void stage_record(const float* __restrict__ rec, int 
     s.sigma = buf[2];
     s.r = buf[4]; s.g = buf[5]; s.b = buf[6];
     s.dx0 = dx0; s.dy0 = dy0;
-    s.nf = meta_nf(__float_as_uint(buf[3]));
+    const uint32_t meta = __float_as_uint(buf[3]);
+    s.nf = meta_nf(meta);
     s.rec = r;
+    return meta;
 }
 
 // Ray/primitive spans of a strip of PIX pixels at anchor offsets (X0 + i, Y),

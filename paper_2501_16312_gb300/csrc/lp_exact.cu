@@ -334,7 +334,7 @@ __global__ void __launch_bounds__(threads_x<TILE>()) k_blend_fwd_x(
     const int lane = tid & 31;
     const int ly = tid / RW, lx0 = (tid % RW) * PIX;
     const bool write_mask = !DEPTH && contrib != nullptr;
-    unsigned long long n_iter = 0, n_eval = 0, n_hit = 0, n_eval_last = 0;
+    unsigned long long n_iter = 0, n_eval = 0, n_hit = 0, n_iter_last = 0;
     for (;;) {
         if (tid == 0) {
             const int q = atomicAdd(tile_counter, 1);
@@ -349,13 +349,12 @@ __global__ void __launch_bounds__(threads_x<TILE>()) k_blend_fwd_x(
         const uint2 rg = ranges[tile];
         const int n = (int)(rg.y - rg.x);
         float T[PIX], c0[PIX], c1[PIX], c2[PIX], tl[PIX], rn[PIX], dep[PIX];
-        uint32_t last[PIX], ce[PIX], cl[PIX];
+        uint32_t last[PIX];
         bool done[PIX];
         bool tdone = true;
 #pragma unroll
         for (int i = 0; i < PIX; ++i) {
             T[i] = 1.f; c0[i] = c1[i] = c2[i] = 0.f; tl[i] = 1.f; last[i] = 0; dep[i] = 0.f;
-            ce[i] = cl[i] = 0;
             rn[i] = ray_norm(cm, tg.tx0 + lx0 + i, py);
             done[i] = !(tg.tx0 + lx0 + i < tg.width && py < tg.height);
             tdone &= done[i];
@@ -384,10 +383,10 @@ __global__ void __launch_bounds__(threads_x<TILE>()) k_blend_fwd_x(
 #pragma unroll
                     for (int i = 0; i < PIX; ++i) {
                         const bool in = !done[i];
-                        if (COUNT) { n_eval += in; ce[i] += in; }
+                        if (COUNT) n_eval += in;
                         if (in && sp[i] > 0.f) {
                             blended = true;
-                            if (COUNT) { ++n_hit; cl[i] = ce[i]; }
+                            if (COUNT) ++n_hit;
                             const float xs = span_x(p.sigma, sp[i]);
                             const float tau = span_tau(xs);
                             const float w = T[i] * span_opacity(xs, tau);
@@ -422,7 +421,7 @@ __global__ void __launch_bounds__(threads_x<TILE>()) k_blend_fwd_x(
         }
         if (COUNT) {
 #pragma unroll
-            for (int i = 0; i < PIX; ++i) n_eval_last += cl[i];
+            for (int i = 0; i < PIX; ++i) n_iter_last += last[i];
         }
         const int plane = tg.width * tg.height;
         float* img = image + 3 * (size_t)tg.pix_base;
@@ -444,7 +443,7 @@ __global__ void __launch_bounds__(threads_x<TILE>()) k_blend_fwd_x(
         __syncthreads();
     }
     if (COUNT) {
-        unsigned long long a = n_iter, b = n_eval, c = n_hit, d = n_eval_last;
+        unsigned long long a = n_iter, b = n_eval, c = n_hit, d = n_iter_last;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             a += __shfl_xor_sync(0xffffffffu, a, o);

@@ -527,14 +527,18 @@ def test_unaligned_sh_array(rast):
 
 def test_pair_counters_match_oracle_contributors(rast):
     """The intersected-pair counter equals the oracle's number of blended
-    (pixel, primitive) pairs up to binary32 ties at silhouettes; the four
-    counters are ordered iterated >= evaluated >= evaluated-to-last and
-    evaluated >= intersected."""
+    (pixel, primitive) pairs up to binary32 ties at silhouettes; the counters
+    are ordered iterated >= evaluated >= intersected and iterated >=
+    iterated-to-last >= intersected, and iterated-to-last sums the pixels'
+    last-contributor list positions."""
     w = scenes.workload(1)
     gpu_forward_backward(rast, w.scene, w.cameras, (0, 0, 0))
     c = rast.count_pairs()
     _, info = oracle.render(w.scene, w.cameras, info=True)
     n_contrib = int(info[:, 0].sum())
     assert abs(c["intersected"] - n_contrib) <= 1e-4 * n_contrib + 2, (c, n_contrib)
-    assert c["iterated"] >= c["evaluated"] >= c["evaluated_to_last"] >= 0
+    assert c["iterated"] >= c["evaluated"] >= c["intersected"] >= 0
+    assert c["iterated"] >= c["iterated_to_last"] >= c["intersected"]
+    last, _ = rast.pixel_state()
+    assert c["iterated_to_last"] == int(last.astype(np.int64).sum())
     assert c["evaluated"] >= c["intersected"] > 0
