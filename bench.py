@@ -138,20 +138,20 @@ def blend_flops(F, pairs):
 
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of a
-# kernel from one ncu capture (one pass, -k that kernel, -c 1) of a workload
+# kernel from one ncu capture (-k that kernel, -c 1) of a workload
 # at one blend schedule, with the sha1 of the kernel's sources: a figure is
 # reported only for the same workload (primitives, cameras) and schedule, and
 # is ignored once the sources change (profiles/dram_traffic_blend_bwd_*.md).
 MEASURED_TRAFFIC = {
     "blend_bwd": [
         {"primitives": 500000, "cameras": 8, "schedule": {"tile": 16, "pixels_per_thread": 2, "batch": 128},
-         "bytes": 560.8e6 + 125.5e6, "sources_sha1": "53cb1caa86c96d1469a6e0db829fcb53e13fc320",
-         "capture": "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum -k regex:^k_blend_bwd$ -s 2 -c 1"},
+         "bytes": 574.3e6 + 127.9e6, "sources_sha1": "5455c3edab0f1ed1ec984dc070f21df0dba5796d",
+         "capture": "ncu --set full -k regex:^k_blend_bwd$ -s 2 -c 1 (dram__bytes_read.sum, dram__bytes_write.sum)"},
     ],
     "blend_fwd": [
         {"primitives": 500000, "cameras": 8, "schedule": {"tile": 16, "pixels_per_thread": 2, "batch": 128},
-         "bytes": 239.2e6 + 122.5e6, "sources_sha1": "648f87ebe546836d7fdc90213d2e31c9c83eea1f",
-         "capture": "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum -k regex:^k_blend_fwd$ -s 2 -c 1"},
+         "bytes": 245.9e6 + 128.8e6, "sources_sha1": "3f288dd8b586b96edd2ca8beacf6ad1fc5b503f0",
+         "capture": "ncu --set full -k regex:^k_blend_fwd$ -s 2 -c 1 (dram__bytes_read.sum, dram__bytes_write.sum)"},
     ],
 }
 KERNEL_SOURCES = {
