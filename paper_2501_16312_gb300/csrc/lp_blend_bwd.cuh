@@ -61,11 +61,16 @@ __global__ void __launch_bounds__(TILE * TILE / PIX, bwd_min_blocks<TILE, PIX>()
     __shared__ Staged<V> sm[BATCH];
     __shared__ int s_tile;
     __shared__ int s_max;
+    // entries of the batch that some lane group of the block visits (bit j:
+    // entry lo + j), two sets used by alternate batches
+    __shared__ uint32_t s_need[2][MW];
     const int tid = threadIdx.x;
     const int lane = tid & 31;
     int ly, lx0;   // the forward's pixel layout, so that warp w's mask bits are its own
     WarpGrid<TILE, PIX>::pixel(tid, ly, lx0);
     using LG = LaneGroups<TILE, PIX>;
+    if (tid < 2 * MW) s_need[tid / MW][tid % MW] = 0u;
+    int kb = 0;   // batches walked by this block, over all its tiles
     for (;;) {
         if (tid == 0) {
             const int q = atomicAdd(tile_counter, 1);
@@ -104,8 +109,6 @@ __global__ void __launch_bounds__(TILE * TILE / PIX, bwd_min_blocks<TILE, PIX>()
         for (int hi = hi_all; hi > 0; hi -= BATCH) {
             const int lo = max(0, hi - BATCH);
             const int nb = hi - lo;
-            __syncthreads();
-            for (int j = tid; j < nb; j += NT) stage_record<V>(rec, vals[rg.x + lo + j], tg.tx0, tg.ty0, sm[j]);
             // This lane group's bits of the forward's contributor mask for
             // entries lo .. hi - 1 (bit j of bm: entry lo + j), loaded once
             // per batch: lane g (MW + 1) + q fetches word q of group g's run,
@@ -132,6 +135,18 @@ __global__ void __launch_bounds__(TILE * TILE / PIX, bwd_min_blocks<TILE, PIX>()
                     bm[q] = m;
                 }
             }
+            // Only the entries some lane group of the block visits are staged.
+            uint32_t* need = s_need[kb & 1];
+#pragma unroll
+            for (int q = 0; q < MW; ++q) {
+                const uint32_t u = __reduce_or_sync(0xffffffffu, bm[q]);
+                if (lane == 0 && u) atomicOr(need + q, u);
+            }
+            __syncthreads();   // the sets are complete, and the last batch's walk is over
+            for (int j = tid; j < nb; j += NT)
+                if ((need[j >> 5] >> (j & 31)) & 1u) stage_record<V>(rec, vals[rg.x + lo + j], tg.tx0, tg.ty0, sm[j]);
+            if (tid < MW) s_need[(kb + 1) & 1][tid] = 0u;   // for the next batch
+            ++kb;
             __syncthreads();
             // Each lane group walks its own set bits, back to front, one mask
             // word at a time; the warp steps while some group has a bit left
