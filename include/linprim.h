@@ -98,7 +98,9 @@ typedef struct {
  *                 0 = as many as fit (occupancy query), else 1..32.
  *   sort_mode     0: one stable radix sort of 64-bit (tile << 32 | depth)
  *                 keys; 1: stable sort of records by depth, then a stable
- *                 sort of the tile ids (same resulting order).
+ *                 sort of the tile ids; 2: stable sort of the tile ids of
+ *                 entries emitted in record order, then a stable sort of
+ *                 each tile's run by depth (all three give the same order).
  *   pixels_per_thread  1, 2 or 4 horizontally adjacent pixels per blend
  *                 thread (tile^2 / pixels_per_thread threads per tile);
  *                 built pairs: tile 8 with 1 or 2, tile 16 with 1, 2 or 4,

@@ -63,7 +63,7 @@ TILE_PIX = ((8, 1), (8, 2), (16, 2), (16, 4), (32, 2), (32, 4))
 # knobs are settled twice: first at the starting tile edge, so that the tile
 # group compares edges with a sensible sort, then again at the chosen edge
 # (the key width, and with it the best digit width, depends on the edge).
-_SORT_GROUP = (("sort_mode", "radix_bits", "onesweep"), tuple(itertools.product((0, 1), (4, 6, 8, 11), (0, 1))),
+_SORT_GROUP = (("sort_mode", "radix_bits", "onesweep"), tuple(itertools.product((0, 1, 2), (4, 6, 8, 11), (0, 1))),
                SORT_STAGES)
 GROUPS = (
     _SORT_GROUP,

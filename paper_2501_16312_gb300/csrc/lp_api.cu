@@ -60,6 +60,7 @@ struct lp_ctx {
     DevBuf<uint2> ranges;
     DevBuf<float> tl, acc, scratch_image;
     DevBuf<uint32_t> dkeys0, dkeys1, dvals0, dvals1, counts_sorted;   // two-stage sort
+    DevBuf<uint32_t> tsort;   // per-tile sort: long-run list (one id per tile) and two counters
     DevBuf<uint32_t> tile_order;     // longest-list-first queue order of the tiles
     DevBuf<uint32_t> meta;           // per-record face order (ray-space records), read by the chain
     uint32_t* d_order_scratch = nullptr;   // bucket counts and cursors of the order
@@ -97,6 +98,7 @@ struct lp_ctx {
         f(acc, "gradient accumulators"); f(scratch_image, "scratch image"); f(dkeys0, "depth keys");
         f(dkeys1, "depth keys"); f(dvals0, "depth values"); f(dvals1, "depth values");
         f(counts_sorted, "sorted counts"); f(tile_order, "tile order"); f(meta, "face orders");
+        f(tsort, "tile sort list");
     }
 };
 
@@ -347,8 +349,8 @@ lp_status lp_set_tuning(lp_ctx* ctx, const lp_tuning* t) {
     if (!lp::tile_pix_ok(t->tile, t->pixels_per_thread))
         return fail(ctx, LP_ERR_INVALID, "pixels_per_thread %d is not built for %dx%d tiles (8: 1, 2; 16: 1, 2, 4; "
                     "32: 2, 4)", t->pixels_per_thread, t->tile, t->tile);
-    if (t->sort_mode != 0 && t->sort_mode != 1)
-        return fail(ctx, LP_ERR_INVALID, "sort_mode %d not in {0, 1}", t->sort_mode);
+    if (t->sort_mode < 0 || t->sort_mode > 2)
+        return fail(ctx, LP_ERR_INVALID, "sort_mode %d not in {0, 1, 2}", t->sort_mode);
     if (t->chain_split != 0 && t->chain_split != 1)
         return fail(ctx, LP_ERR_INVALID, "chain_split %d not in {0, 1}", t->chain_split);
     if (t->radix_bits != 4 && t->radix_bits != 6 && t->radix_bits != 8 && t->radix_bits != 11)
@@ -439,6 +441,7 @@ static lp_status reserve_impl(lp_ctx* ctx, long long records, long long entries,
     LP_TRY(ensure(ctx, ctx->contrib, (kcap / 32 + 2) * kMaskRowsMax, false, "contributor mask"));
     LP_TRY(ensure(ctx, ctx->ranges, tiles, false, "tile ranges"));
     LP_TRY(ensure(ctx, ctx->tile_order, tiles, false, "tile order"));
+    LP_TRY(ensure(ctx, ctx->tsort, (tiles > 0 ? tiles : 1) + 2, false, "tile sort list"));
     LP_TRY(ensure(ctx, ctx->last, pixels, false, "pixel state"));
     LP_TRY(ensure(ctx, ctx->tl, pixels, false, "pixel state"));
     const int af = V ? acc_floats_mode(V, ctx->exact) : acc_floats_max();
@@ -567,13 +570,17 @@ lp_status lp_render_forward(lp_ctx* ctx, const lp_prims* prims, const lp_camera*
     const int tile_bits = bits_for(tiles);
     int key_bits;
     const uint32_t* svals;
-    if (mode == 1) {
-        // stage 2: entries in depth order, stably sorted by their tile id
+    if (mode != 0) {
+        // mode 1, stage 2: entries in depth order, stably sorted by their tile
+        // id.  Mode 2: entries in record order, stably sorted by tile id, then
+        // each tile's run by depth.
         uint32_t* t0 = reinterpret_cast<uint32_t*>(ctx->keys0.p);
         uint32_t* t1 = reinterpret_cast<uint32_t*>(ctx->keys1.p);
-        LP_CUDA(lp::launch_emit_sorted(order, ctx->counts_sorted.p, ctx->offsets.p, ctx->trect.p, records,
-                                       ctx->d_E, bound, ctx->emit_part.p, t0, ctx->vals0.p, bound, ctx->d_status,
-                                       st));
+        if (mode == 2)
+            LP_TRY(ensure(ctx, ctx->tsort, (tiles > 0 ? tiles : 1) + 2, cap_mode, "tile sort list"));
+        LP_CUDA(lp::launch_emit_sorted(mode == 1 ? order : nullptr, mode == 1 ? ctx->counts_sorted.p : ctx->counts.p,
+                                       ctx->offsets.p, ctx->trect.p, records, ctx->d_E, bound, ctx->emit_part.p, t0,
+                                       ctx->vals0.p, bound, ctx->d_status, st));
         mark(ctx, st, 2, cap_mode);
         key_bits = tile_bits;
         LP_CUDA(lp::launch_radix_sort32(t0, ctx->vals0.p, t1, ctx->vals1.p, ctx->d_E, bound, key_bits,
@@ -586,6 +593,15 @@ lp_status lp_render_forward(lp_ctx* ctx, const lp_prims* prims, const lp_camera*
         LP_CUDA(cudaMemsetAsync(ctx->ranges.p, 0, (size_t)(tiles > 0 ? tiles : 1) * sizeof(uint2), st));
         LP_CUDA(lp::launch_ranges32(in1 ? t1 : t0, ctx->d_E, bound, ctx->d_status, ctx->ranges.p, ctx->sms,
                                     st));
+        if (mode == 2) {
+            // scratch: the key buffer that does not hold the sorted tile ids,
+            // as two 4-byte arrays of the list's length
+            uint32_t* sa = reinterpret_cast<uint32_t*>(in1 ? ctx->keys0.p : ctx->keys1.p);
+            const long long tiles_alloc = tiles > 0 ? tiles : 1;
+            LP_CUDA(lp::launch_tile_sort(in1 ? ctx->vals1.p : ctx->vals0.p, ctx->ranges.p, tiles, ctx->zbits.p,
+                                         reinterpret_cast<int*>(ctx->tsort.p + tiles_alloc), ctx->tsort.p, sa,
+                                         sa + bound, ctx->d_status, ctx->sms, st));
+        }
         ctx->result_in_1 = in1;
     } else {
         LP_CUDA(lp::launch_emit(ctx->counts.p, ctx->offsets.p, ctx->trect.p, ctx->zbits.p, records, ctx->d_E,
@@ -640,6 +656,7 @@ lp_status lp_render_forward(lp_ctx* ctx, const lp_prims* prims, const lp_camera*
     ctx->launches_fwd = 1 + (records > 0 ? 3 : 0) + (records > 0 ? 1 : 0) + sort_kernels(passes, bound) +
                         sort_kernels(passes1, records) +
                         (mode == 1 && records > 0 ? 2 : 0) + (bound > 0 ? 1 : 0) + (a.grid > 0 ? 1 : 0) +
+                        (mode == 2 && tiles > 0 ? 2 : 0) +
                         (ctx->tune.tile_order && tiles > 0 ? 3 : 0);
 
     ctx->have_fwd = true;
@@ -652,7 +669,7 @@ lp_status lp_render_forward(lp_ctx* ctx, const lp_prims* prims, const lp_camera*
     ctx->E_bound = bound;
     ctx->key_bits = key_bits;
     ctx->sort_passes = passes1 + passes;
-    ctx->keys32 = mode == 1;
+    ctx->keys32 = mode != 0;
     ctx->fwd_exact = exact;
     ctx->fwd_tune = ctx->tune;
     return LP_OK;

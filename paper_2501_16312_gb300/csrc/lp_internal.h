@@ -82,6 +82,13 @@ cudaError_t launch_emit_sorted(const uint32_t* order, const uint32_t* counts_sor
                                const int4* trect, long long n_records, const uint32_t* n_dev, long long bound,
                                uint32_t* part, uint32_t* keys, uint32_t* vals, long long cap, int* status,
                                cudaStream_t st);
+// Sort mode 2, after the tile sort and the ranges: each tile's run of vals
+// (record indices, in record order) sorted stably by the records' depth bits.
+// counters: 2 device ints (zeroed here); long_list: room for one id per tile;
+// scratch_a, scratch_b: 4-byte scratch of the list's length each.
+cudaError_t launch_tile_sort(uint32_t* vals, const uint2* ranges, long long tiles, const uint32_t* zbits,
+                             int* counters, uint32_t* long_list, uint32_t* scratch_a, uint32_t* scratch_b,
+                             const int* status, int sms, cudaStream_t st);
 cudaError_t launch_ranges32(const uint32_t* keys, const uint32_t* n_dev, long long bound,
                             const int* status, uint2* ranges, int sms, cudaStream_t st);
 

@@ -185,9 +185,10 @@ __global__ void __launch_bounds__(256) k_emit_partition(const uint32_t* __restri
     part[b] = (uint32_t)lo;
 }
 
-// SORTED: list position k holds record order[k] (stage 2 of the two-stage
-// sort) and the key is the 32-bit tile id; otherwise position k is record k
-// and the key is (tile << 32) | depth bits.
+// SORTED: the key is the 32-bit tile id, and list position k holds record
+// order[k] (stage 2 of the two-stage sort), or record k when order is null
+// (the per-tile sort); otherwise position k is record k and the key is
+// (tile << 32) | depth bits.
 template <bool SORTED>
 __global__ void __launch_bounds__(kEmitBlock) k_emit_lb(const uint32_t* __restrict__ order,
                                                         const uint32_t* __restrict__ counts,
@@ -220,7 +221,7 @@ __global__ void __launch_bounds__(kEmitBlock) k_emit_lb(const uint32_t* __restri
     for (int t = tid; t < nrec; t += kEmitBlock) {
         const long long k = ks + t;
         const uint32_t cnt = counts[k];
-        const uint32_t r = SORTED ? order[k] : (uint32_t)k;
+        const uint32_t r = SORTED && order ? order[k] : (uint32_t)k;
         s_off[t] = offsets[k];
         s_rec[t] = r;
         if (cnt) {
@@ -868,6 +869,219 @@ cudaError_t launch_emit_sorted(const uint32_t* order, const uint32_t* counts_sor
                                cudaStream_t st) {
     return emit_t<true>(order, counts_sorted, offsets, trect, nullptr, n_records, n_dev, bound, part, keys,
                         nullptr, vals, cap, status, st);
+}
+
+// ------------------------------------------------ per-tile depth sort (mode 2)
+// Sort mode 2 emits every record's entries in record order and stably sorts
+// them by tile id, so that each tile's run of the list is in record order;
+// sorting each run stably by its records' depth bits then gives (tile, depth,
+// record) order, the order of modes 0 and 1.  A warp sorts a run of up to
+// kTileWarpCap entries in shared memory (LSD radix, 8-bit digits, the digits
+// that do not vary across the run skipped); longer runs are listed and
+// k_tile_sort_long gives each one block, which sorts it through global
+// scratch in chunks, whatever its length.
+constexpr int kTileSortThreads = 128;
+constexpr int kTileWarpCap = 512;
+constexpr int kTileLongThreads = 256;
+
+// Stable LSD sort of n <= kTileWarpCap (key, value) pairs in a warp's shared
+// memory (ka, va; kb, vb a second buffer; cnt 256 counters).  Returns the
+// buffer pair that holds the result (0: ka/va, 1: kb/vb).
+__device__ int warp_radix_sort(uint32_t* ka, uint32_t* va, uint32_t* kb, uint32_t* vb, uint32_t* cnt, int n,
+                               int lane) {
+    uint32_t o = 0u, a = 0xffffffffu;
+    for (int i = lane; i < n; i += 32) { o |= ka[i]; a &= ka[i]; }
+    const uint32_t diff = __reduce_or_sync(0xffffffffu, o) & ~__reduce_and_sync(0xffffffffu, a);
+    int in = 0;
+    const unsigned lt = (1u << lane) - 1u;
+    for (int shift = 0; shift < 32; shift += 8) {
+        if (((diff >> shift) & 255u) == 0u) continue;   // one digit value across the run: already in order
+        uint32_t* ks = in ? kb : ka; uint32_t* vs = in ? vb : va;
+        uint32_t* kd = in ? ka : kb; uint32_t* vd = in ? va : vb;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) cnt[lane * 8 + q] = 0u;
+        __syncwarp();
+        for (int i = lane; i < n; i += 32) atomicAdd(&cnt[(ks[i] >> shift) & 255u], 1u);
+        __syncwarp();
+        // exclusive scan of the 256 counts: lane l holds digits 8l .. 8l + 7
+        uint32_t c[8], tot = 0u;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) { c[q] = cnt[lane * 8 + q]; tot += c[q]; }
+        uint32_t x = tot;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
+            if (lane >= d) x += y;
+        }
+        x -= tot;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) { cnt[lane * 8 + q] = x; x += c[q]; }
+        __syncwarp();
+        // rounds of 32 entries in order; equal digits keep their order
+        for (int base = 0; base < n; base += 32) {
+            const int i = base + lane;
+            const bool ok = i < n;
+            const uint32_t key = ok ? ks[i] : 0u, val = ok ? vs[i] : 0u;
+            const uint32_t d = ok ? (key >> shift) & 255u : 256u;
+            const unsigned peers = digit_peers<8>(d);
+            const uint32_t rank = __popc(peers & lt);
+            const uint32_t off = ok ? cnt[d] : 0u;
+            __syncwarp();
+            if (ok && rank == 0) cnt[d] = off + __popc(peers);
+            __syncwarp();
+            if (ok) { kd[off + rank] = key; vd[off + rank] = val; }
+        }
+        __syncwarp();
+        in ^= 1;
+    }
+    return in;
+}
+
+// One warp per tile (tiles from a queue).  Runs longer than kTileWarpCap go
+// to long_list.  Skipped when the list overflowed or a sort wait expired (the
+// ranges are then all empty).
+__global__ void __launch_bounds__(kTileSortThreads) k_tile_sort(uint32_t* __restrict__ vals,
+                                                                const uint2* __restrict__ ranges, int T,
+                                                                const uint32_t* __restrict__ zbits,
+                                                                int* __restrict__ counters,
+                                                                uint32_t* __restrict__ long_list,
+                                                                const int* __restrict__ status) {
+    constexpr int NW = kTileSortThreads / 32;
+    __shared__ uint32_t s_buf[NW][4][kTileWarpCap];
+    __shared__ uint32_t s_cnt[NW][256];
+    if (*status & (kStatusCapacity | kStatusTimeout)) return;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (;;) {
+        int t = 0;
+        if (lane == 0) t = atomicAdd(counters, 1);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= T) break;
+        const uint2 rg = ranges[t];
+        const int n = (int)(rg.y - rg.x);
+        if (n <= 1) continue;
+        if (n > kTileWarpCap) {
+            if (lane == 0) long_list[atomicAdd(counters + 1, 1)] = (uint32_t)t;
+            continue;
+        }
+        uint32_t* ka = s_buf[w][0]; uint32_t* va = s_buf[w][1];
+        for (int i = lane; i < n; i += 32) {
+            const uint32_t v = vals[rg.x + i];
+            va[i] = v;
+            ka[i] = zbits[v];
+        }
+        __syncwarp();
+        const int in = warp_radix_sort(ka, va, s_buf[w][2], s_buf[w][3], s_cnt[w], n, lane);
+        const uint32_t* vr = in ? s_buf[w][3] : va;
+        for (int i = lane; i < n; i += 32) vals[rg.x + i] = vr[i];
+        __syncwarp();
+    }
+}
+
+// One block per listed long run: a stable LSD sort of the run's records by
+// depth bits through the global scratch arrays sa and sb (the run's own
+// positions [rg.x, rg.y) of each; the depth bits are gathered again in each
+// pass), in chunks of kTileLongThreads entries taken in order, each chunk
+// ranked by warp, then across the block's warps.
+__global__ void __launch_bounds__(kTileLongThreads) k_tile_sort_long(uint32_t* __restrict__ vals,
+                                                                     const uint2* __restrict__ ranges,
+                                                                     const uint32_t* __restrict__ zbits,
+                                                                     const int* __restrict__ counters,
+                                                                     const uint32_t* __restrict__ long_list,
+                                                                     uint32_t* __restrict__ sa,
+                                                                     uint32_t* __restrict__ sb,
+                                                                     const int* __restrict__ status) {
+    constexpr int NW = kTileLongThreads / 32;
+    __shared__ uint32_t s_base[256];
+    __shared__ uint32_t s_wcnt[NW][256];
+    __shared__ uint32_t s_or, s_and;
+    if (*status & (kStatusCapacity | kStatusTimeout)) return;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    const int nlong = counters[1];
+    for (int li = blockIdx.x; li < nlong; li += gridDim.x) {
+        const uint2 rg = ranges[long_list[li]];
+        const long long n = (long long)(rg.y - rg.x);
+        uint32_t* src = sa + rg.x;
+        uint32_t* dst = sb + rg.x;
+        if (tid == 0) { s_or = 0u; s_and = 0xffffffffu; }
+        __syncthreads();
+        uint32_t o = 0u, a = 0xffffffffu;
+        for (long long i = tid; i < n; i += kTileLongThreads) {
+            const uint32_t v = vals[rg.x + i];
+            const uint32_t z = zbits[v];
+            src[i] = v;
+            o |= z; a &= z;
+        }
+        o = __reduce_or_sync(0xffffffffu, o);
+        a = __reduce_and_sync(0xffffffffu, a);
+        if (lane == 0) { atomicOr(&s_or, o); atomicAnd(&s_and, a); }
+        __syncthreads();
+        const uint32_t diff = s_or & ~s_and;
+        for (int shift = 0; shift < 32; shift += 8) {
+            if (((diff >> shift) & 255u) == 0u) continue;   // uniform over the block
+            s_base[tid] = 0u;
+            __syncthreads();
+            for (long long i = tid; i < n; i += kTileLongThreads)
+                atomicAdd(&s_base[(zbits[src[i]] >> shift) & 255u], 1u);
+            __syncthreads();
+            if (w == 0) {   // exclusive scan of the 256 counts, 8 per lane
+                uint32_t c[8], tot = 0u;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) { c[q] = s_base[lane * 8 + q]; tot += c[q]; }
+                uint32_t x = tot;
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
+                    if (lane >= d) x += y;
+                }
+                x -= tot;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) { s_base[lane * 8 + q] = x; x += c[q]; }
+            }
+            __syncthreads();
+            for (long long c0 = 0; c0 < n; c0 += kTileLongThreads) {
+                const long long i = c0 + tid;
+                const bool ok = i < n;
+                const uint32_t v = ok ? src[i] : 0u;
+                const uint32_t d = ok ? (zbits[v] >> shift) & 255u : 256u;
+                const unsigned peers = digit_peers<8>(d);
+                const uint32_t rank = __popc(peers & lt);
+#pragma unroll
+                for (int ww = 0; ww < NW; ++ww) s_wcnt[ww][tid] = 0u;   // thread t: digit t of every warp
+                __syncthreads();
+                if (ok && rank == 0) s_wcnt[w][d] = __popc(peers);
+                __syncthreads();
+                if (ok) {
+                    uint32_t pos = s_base[d] + rank;
+                    for (int ww = 0; ww < w; ++ww) pos += s_wcnt[ww][d];
+                    dst[pos] = v;
+                }
+                __syncthreads();
+                uint32_t add = 0u;
+#pragma unroll
+                for (int ww = 0; ww < NW; ++ww) add += s_wcnt[ww][tid];
+                s_base[tid] += add;
+                __syncthreads();
+            }
+            uint32_t* t = src; src = dst; dst = t;
+        }
+        for (long long i = tid; i < n; i += kTileLongThreads) vals[rg.x + i] = src[i];
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_tile_sort(uint32_t* vals, const uint2* ranges, long long tiles, const uint32_t* zbits,
+                             int* counters, uint32_t* long_list, uint32_t* scratch_a, uint32_t* scratch_b,
+                             const int* status, int sms, cudaStream_t st) {
+    if (tiles <= 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(counters, 0, 2 * sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    const long long want = (tiles + 3) / 4;
+    const int grid = (int)(want < (long long)sms * 8 ? want : (long long)sms * 8);
+    k_tile_sort<<<grid, kTileSortThreads, 0, st>>>(vals, ranges, (int)tiles, zbits, counters, long_list, status);
+    k_tile_sort_long<<<sms * 2, kTileLongThreads, 0, st>>>(vals, ranges, zbits, counters, long_list, scratch_a,
+                                                          scratch_b, status);
+    return cudaGetLastError();
 }
 
 static int ranges_grid(long long bound, int sms) {

@@ -81,7 +81,7 @@ def test_search_picks_each_groups_best_in_order():
                 chain_split=1)
     assert entry["tuning"] == want
     assert knobs == want                                # the winners are left applied
-    assert len(entry["trials"]) == 16 + 18 + 16 + 2 + 2
+    assert len(entry["trials"]) == 24 + 18 + 24 + 2 + 2
     # the sort group is judged on its own stages only, at both visits
     assert entry["best_ms"]["sort_mode+radix_bits+onesweep"] == pytest.approx(0.45)
     assert entry["best_ms"]["sort_mode+radix_bits+onesweep (again)"] == pytest.approx(0.45)
@@ -160,7 +160,7 @@ def test_tune_caches_reuses_and_restores_timing(fake_cuda, tmp_path):
     entry = autotune.tune(rast, prims, cams, reps=2, cache=cache)
     want = dict(BASE, sort_mode=1, radix_bits=11, pixels_per_thread=4, batch=64, chain_split=1)
     assert entry["tuning"] == want and rast.knobs == want
-    assert rast.measured == 54 * 3                       # 54 trials x (warm-up + 2 timed)
+    assert rast.measured == 70 * 3                       # 70 trials x (warm-up + 2 timed)
     assert rast.timing_calls == [True, False]            # timing restored to off
     stored = json.load(open(cache))
     key = autotune.cache_key("FakeGPU", 6, 10, cams)
@@ -174,7 +174,7 @@ def test_tune_caches_reuses_and_restores_timing(fake_cuda, tmp_path):
     rast3 = FakeRast()
     rast3.set_timing(True)
     autotune.tune(rast3, prims, cams, reps=1, cache=cache, force=True)
-    assert rast3.measured == 54 * 2 and rast3.timing() is True
+    assert rast3.measured == 70 * 2 and rast3.timing() is True
     # other workloads share the file
     autotune.tune(FakeRast(), prims, cams[:1], reps=1, cache=cache)
     assert len(json.load(open(cache))) == 2
@@ -193,7 +193,7 @@ def test_tune_retimes_a_cached_entry_with_other_knobs(fake_cuda, tmp_path):
     assert autotune.load_cache(str(cache), key, knobs=BASE) is None
     rast = FakeRast()
     entry = autotune.tune(rast, prims, cams, reps=1, cache=str(cache))
-    assert rast.measured == 54 * 2 and set(entry["tuning"]) == set(BASE)   # warm-up + 1 timed
+    assert rast.measured == 70 * 2 and set(entry["tuning"]) == set(BASE)   # warm-up + 1 timed
     assert json.load(open(cache))[key]["tuning"] == entry["tuning"]
 
 

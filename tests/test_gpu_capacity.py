@@ -29,7 +29,7 @@ def _capture(rast, prims, cams, bg, img, dL, grads):
     return g
 
 
-@pytest.mark.parametrize("sort_mode", [0, 1])
+@pytest.mark.parametrize("sort_mode", [0, 1, 2])
 def test_capacity_latch_in_captured_graph(sort_mode):
     import torch
     if not torch.cuda.is_available():
@@ -109,7 +109,7 @@ def test_guard_zones_are_checked():
     assert g["checked"] >= 10 and g["damaged"] == 0, g
 
 
-@pytest.mark.parametrize("sort_mode", [0, 1])
+@pytest.mark.parametrize("sort_mode", [0, 1, 2])
 def test_sort_wait_times_out_and_recovers(sort_mode):
     """The onesweep sort's look-back waits are bounded: when one block of the first
     pass never publishes its counts (a test hook), the blocks after it give

@@ -5,7 +5,7 @@ on the two 1080p-class workloads the benchmark reports:
   * 1M tetrahedra in a box, 16 cameras of mixed size (6 x 1920x1080,
     6 x 1280x720, 4 x 640x480), all rendered in one batched call.
 
-Tile lists of every camera are compared bit-exactly in both sort modes
+Tile lists of every camera are compared bit-exactly in every sort mode
 (Sec. 3.2 "Global Sorting and Tiling"); on the second workload every pixel of
 a 1920x1080 camera and samples of a 640x480 camera are compared with the
 oracle's images, and gradients of a loss on sampled pixels with the oracle's
@@ -59,12 +59,12 @@ def _oracle_keys8(i):
 
 
 @pytest.mark.parametrize("onesweep", [0, 1])
-@pytest.mark.parametrize("sort_mode", [0, 1])
+@pytest.mark.parametrize("sort_mode", [0, 1, 2])
 @pytest.mark.parametrize("index", [2, 3])
 def test_full_size_tile_lists_bit_exact(rast, index, sort_mode, onesweep):
     """Every camera of the workload in one batched forward: per-record tile
     counts, keys and values equal the oracle's stable (tile, depth, record)
-    sort bit for bit, in both sort forms; no workspace guard zone is
+    sort bit for bit, in every sort form; no workspace guard zone is
     touched."""
     _check_full_size_keys(rast, index, dict(sort_mode=sort_mode, onesweep=onesweep), _oracle_keys(index))
 
@@ -76,6 +76,8 @@ def test_full_size_tile_lists_bit_exact_8x8(rast, index, radix_bits):
     passes of 6 or 7 bits at most 8 bits a digit, two of 9 or 10 at most
     11), the list the tuner picks for these workloads: bit-exact."""
     _check_full_size_keys(rast, index, dict(sort_mode=1, tile=8, pixels_per_thread=2, radix_bits=radix_bits),
+                          _oracle_keys8(index))
+    _check_full_size_keys(rast, index, dict(sort_mode=2, tile=8, pixels_per_thread=2, radix_bits=radix_bits),
                           _oracle_keys8(index))
 
 
@@ -134,7 +136,7 @@ def test_workload3_full_size_images(rast):
           f"480p samples: max err {r1[0]:.2e}, {r1[1]} borderline ({r1[2]} differ)")
 
 
-@pytest.mark.parametrize("sort_mode", [0, 1])
+@pytest.mark.parametrize("sort_mode", [0, 1, 2])
 def test_workload3_sampled_gradient(rast, sort_mode):
     """Gradients at full size (1M tetrahedra, all 16 cameras in one batched
     forward + backward) of a loss on 4096 random pixels of the first 1080p

@@ -41,11 +41,11 @@ CASES = {
 
 @pytest.mark.parametrize("onesweep", [0, 1])
 @pytest.mark.parametrize("tile", [8, 16, 32])
-@pytest.mark.parametrize("sort_mode", [0, 1])
+@pytest.mark.parametrize("sort_mode", [0, 1, 2])
 @pytest.mark.parametrize("case", sorted(CASES))
 def test_tile_lists_bit_exact(rast, case, sort_mode, tile, onesweep):
     """Sec. 3.2 "Global Sorting and Tiling" at every tile edge the tuner
-    may pick and in both sort forms: counts, keys and values equal the
+    may pick and in every sort form: counts, keys and values equal the
     oracle's bit for bit."""
     w = CASES[case]()
     base = rast.tuning()
@@ -62,10 +62,41 @@ def test_tile_lists_bit_exact(rast, case, sort_mode, tile, onesweep):
     np.testing.assert_array_equal(v, vo)
 
 
+def _crowded_tiles():
+    """5,000 large tetrahedra filling a 96x64 view: 16x16 tiles list up to
+    about 3,700 entries (12 of 16 tiles above 512), 8x8 tiles up to the
+    same."""
+    scene = scenes.tetra_scene(seed=11, n=5000, box=0.6, s_range=(0.4, 0.9))
+    return scene, [scenes.make_camera((0.0, 0.0, 3.0), 96, 64, 60.0)]
+
+
+@pytest.mark.parametrize("sort_mode", [1, 2])
+@pytest.mark.parametrize("tile", [8, 16])
+def test_tile_lists_bit_exact_long_runs(rast, sort_mode, tile):
+    """Tile lists far longer than the per-tile sort's shared-memory run (512
+    entries), which sort mode 2 sorts through global scratch block by block:
+    keys and values bit-exact, images within the bar."""
+    scene, cams = _crowded_tiles()
+    base = rast.tuning()
+    rast.set_tuning(sort_mode=sort_mode, tile=tile, pixels_per_thread=2)
+    try:
+        img, _ = gpu_forward_backward(rast, scene, cams, (0.1, 0.1, 0.1))
+        k, v = rast.debug_keys()
+    finally:
+        rast.set_tuning(**base)
+    ko, vo, _ = oracle.keys(scene, cams, tile=tile)
+    runs = np.unique(ko >> np.uint64(32), return_counts=True)[1]   # entries per tile
+    assert runs.max() > 4 * 512, runs.max()
+    np.testing.assert_array_equal(k, ko)
+    np.testing.assert_array_equal(v, vo)
+    ref, info = oracle.render(scene, cams, bg=(0.1, 0.1, 0.1), info=True)
+    assert_images_match(img, ref, info, cams)
+
+
 @pytest.mark.parametrize("onesweep", [0, 1])
 @pytest.mark.parametrize("radix_bits", [4, 6, 11])
 @pytest.mark.parametrize("tile", [8, 16])
-@pytest.mark.parametrize("sort_mode", [0, 1])
+@pytest.mark.parametrize("sort_mode", [0, 1, 2])
 def test_tile_lists_bit_exact_every_digit_width(rast, sort_mode, tile, radix_bits, onesweep):
     """The radix sort at each widest digit the tuner may pick: a sort of k key
     bits takes ceil(k / radix_bits) passes of evenly spread digits, so these
@@ -104,7 +135,7 @@ def test_forward_backward_parity(rast, case):
 AA = float(np.float32(0.1))   # the paper's 2D filter size; both sides get the same binary32 value
 
 
-@pytest.mark.parametrize("sort_mode", [0, 1])
+@pytest.mark.parametrize("sort_mode", [0, 1, 2])
 @pytest.mark.parametrize("case", sorted(CASES))
 def test_filter_2d_parity(rast, case, sort_mode):
     """Sec. 3.3 2D filter on: tile lists bit-exact, images and gradients
