@@ -877,9 +877,10 @@ cudaError_t launch_emit_sorted(const uint32_t* order, const uint32_t* counts_sor
 // sorting each run stably by its records' depth bits then gives (tile, depth,
 // record) order, the order of modes 0 and 1.  A warp sorts a run of up to
 // kTileWarpCap entries in shared memory (LSD radix, 8-bit digits, the digits
-// that do not vary across the run skipped); longer runs are listed and
-// k_tile_sort_long gives each one block, which sorts it through global
-// scratch in chunks, whatever its length.
+// that do not vary across the run skipped; four warps per block, 9 KB each);
+// longer runs are listed and k_tile_sort_long gives each one block, which
+// sorts it in shared memory up to kTileBlockCap entries and through global
+// scratch in chunks beyond, whatever its length.
 constexpr int kTileSortThreads = 128;
 constexpr int kTileWarpCap = 512;
 constexpr int kTileLongThreads = 256;
@@ -977,11 +978,73 @@ __global__ void __launch_bounds__(kTileSortThreads) k_tile_sort(uint32_t* __rest
     }
 }
 
-// One block per listed long run: a stable LSD sort of the run's records by
-// depth bits through the global scratch arrays sa and sb (the run's own
-// positions [rg.x, rg.y) of each; the depth bits are gathered again in each
-// pass), in chunks of kTileLongThreads entries taken in order, each chunk
-// ranked by warp, then across the block's warps.
+// One LSD pass of a block over n entries (values v, keys key(v) by the
+// functor): digit counts, their scan, then chunks of kTileLongThreads entries
+// in order, each ranked by warp, then across the block's warps, so that equal
+// digits keep their order.  src and dst are shared or global arrays; with
+// keys in arrays ksrc/kdst they move along (KEYS), else key() gathers them.
+template <bool KEYS, typename KeyF>
+__device__ void block_lsd_pass(const uint32_t* src, uint32_t* dst, const uint32_t* ksrc, uint32_t* kdst,
+                               long long n, int shift, KeyF key, uint32_t* s_base, uint32_t (*s_wcnt)[256]) {
+    constexpr int NW = kTileLongThreads / 32;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    s_base[tid] = 0u;
+    __syncthreads();
+    for (long long i = tid; i < n; i += kTileLongThreads)
+        atomicAdd(&s_base[((KEYS ? ksrc[i] : key(src[i])) >> shift) & 255u], 1u);
+    __syncthreads();
+    if (w == 0) {   // exclusive scan of the 256 counts, 8 per lane
+        uint32_t c[8], tot = 0u;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) { c[q] = s_base[lane * 8 + q]; tot += c[q]; }
+        uint32_t x = tot;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
+            if (lane >= d) x += y;
+        }
+        x -= tot;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) { s_base[lane * 8 + q] = x; x += c[q]; }
+    }
+    __syncthreads();
+    for (long long c0 = 0; c0 < n; c0 += kTileLongThreads) {
+        const long long i = c0 + tid;
+        const bool ok = i < n;
+        const uint32_t v = ok ? src[i] : 0u;
+        const uint32_t k = ok ? (KEYS ? ksrc[i] : key(v)) : 0u;
+        const uint32_t d = ok ? (k >> shift) & 255u : 256u;
+        const unsigned peers = digit_peers<8>(d);
+        const uint32_t rank = __popc(peers & lt);
+#pragma unroll
+        for (int ww = 0; ww < NW; ++ww) s_wcnt[ww][tid] = 0u;   // thread t: digit t of every warp
+        __syncthreads();
+        if (ok && rank == 0) s_wcnt[w][d] = __popc(peers);
+        __syncthreads();
+        if (ok) {
+            uint32_t pos = s_base[d] + rank;
+            for (int ww = 0; ww < w; ++ww) pos += s_wcnt[ww][d];
+            dst[pos] = v;
+            if (KEYS) kdst[pos] = k;
+        }
+        __syncthreads();
+        uint32_t add = 0u;
+#pragma unroll
+        for (int ww = 0; ww < NW; ++ww) add += s_wcnt[ww][tid];
+        s_base[tid] += add;
+        __syncthreads();
+    }
+}
+
+// One block per listed long run, sorted stably by depth bits: runs of up to
+// kTileBlockCap entries in shared memory (dynamic, keys moving with the
+// values), longer ones through the global scratch arrays sa and sb (the
+// run's own positions [rg.x, rg.y) of each; the depth bits are gathered
+// again in each pass).
+constexpr int kTileBlockCap = 4096;
+constexpr size_t kTileLongSmem = (size_t)4 * kTileBlockCap * sizeof(uint32_t);
+
 __global__ void __launch_bounds__(kTileLongThreads) k_tile_sort_long(uint32_t* __restrict__ vals,
                                                                      const uint2* __restrict__ ranges,
                                                                      const uint32_t* __restrict__ zbits,
@@ -991,25 +1054,30 @@ __global__ void __launch_bounds__(kTileLongThreads) k_tile_sort_long(uint32_t* _
                                                                      uint32_t* __restrict__ sb,
                                                                      const int* __restrict__ status) {
     constexpr int NW = kTileLongThreads / 32;
+    extern __shared__ __align__(16) uint32_t s_run[];   // values, keys; second values, keys
     __shared__ uint32_t s_base[256];
     __shared__ uint32_t s_wcnt[NW][256];
     __shared__ uint32_t s_or, s_and;
     if (*status & (kStatusCapacity | kStatusTimeout)) return;
-    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    const unsigned lt = (1u << lane) - 1u;
+    const int tid = threadIdx.x, lane = tid & 31;
     const int nlong = counters[1];
+    auto key = [zbits](uint32_t v) { return zbits[v]; };
     for (int li = blockIdx.x; li < nlong; li += gridDim.x) {
         const uint2 rg = ranges[long_list[li]];
         const long long n = (long long)(rg.y - rg.x);
-        uint32_t* src = sa + rg.x;
-        uint32_t* dst = sb + rg.x;
+        const bool in_smem = n <= kTileBlockCap;   // uniform over the block
+        uint32_t* v0 = in_smem ? s_run : sa + rg.x;
+        uint32_t* v1 = in_smem ? s_run + 2 * kTileBlockCap : sb + rg.x;
+        uint32_t* k0 = s_run + kTileBlockCap;
+        uint32_t* k1 = s_run + 3 * kTileBlockCap;
         if (tid == 0) { s_or = 0u; s_and = 0xffffffffu; }
         __syncthreads();
         uint32_t o = 0u, a = 0xffffffffu;
         for (long long i = tid; i < n; i += kTileLongThreads) {
             const uint32_t v = vals[rg.x + i];
             const uint32_t z = zbits[v];
-            src[i] = v;
+            v0[i] = v;
+            if (in_smem) k0[i] = z;
             o |= z; a &= z;
         }
         o = __reduce_or_sync(0xffffffffu, o);
@@ -1019,53 +1087,12 @@ __global__ void __launch_bounds__(kTileLongThreads) k_tile_sort_long(uint32_t* _
         const uint32_t diff = s_or & ~s_and;
         for (int shift = 0; shift < 32; shift += 8) {
             if (((diff >> shift) & 255u) == 0u) continue;   // uniform over the block
-            s_base[tid] = 0u;
-            __syncthreads();
-            for (long long i = tid; i < n; i += kTileLongThreads)
-                atomicAdd(&s_base[(zbits[src[i]] >> shift) & 255u], 1u);
-            __syncthreads();
-            if (w == 0) {   // exclusive scan of the 256 counts, 8 per lane
-                uint32_t c[8], tot = 0u;
-#pragma unroll
-                for (int q = 0; q < 8; ++q) { c[q] = s_base[lane * 8 + q]; tot += c[q]; }
-                uint32_t x = tot;
-#pragma unroll
-                for (int d = 1; d < 32; d <<= 1) {
-                    const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
-                    if (lane >= d) x += y;
-                }
-                x -= tot;
-#pragma unroll
-                for (int q = 0; q < 8; ++q) { s_base[lane * 8 + q] = x; x += c[q]; }
-            }
-            __syncthreads();
-            for (long long c0 = 0; c0 < n; c0 += kTileLongThreads) {
-                const long long i = c0 + tid;
-                const bool ok = i < n;
-                const uint32_t v = ok ? src[i] : 0u;
-                const uint32_t d = ok ? (zbits[v] >> shift) & 255u : 256u;
-                const unsigned peers = digit_peers<8>(d);
-                const uint32_t rank = __popc(peers & lt);
-#pragma unroll
-                for (int ww = 0; ww < NW; ++ww) s_wcnt[ww][tid] = 0u;   // thread t: digit t of every warp
-                __syncthreads();
-                if (ok && rank == 0) s_wcnt[w][d] = __popc(peers);
-                __syncthreads();
-                if (ok) {
-                    uint32_t pos = s_base[d] + rank;
-                    for (int ww = 0; ww < w; ++ww) pos += s_wcnt[ww][d];
-                    dst[pos] = v;
-                }
-                __syncthreads();
-                uint32_t add = 0u;
-#pragma unroll
-                for (int ww = 0; ww < NW; ++ww) add += s_wcnt[ww][tid];
-                s_base[tid] += add;
-                __syncthreads();
-            }
-            uint32_t* t = src; src = dst; dst = t;
+            if (in_smem) block_lsd_pass<true>(v0, v1, k0, k1, n, shift, key, s_base, s_wcnt);
+            else block_lsd_pass<false>(v0, v1, nullptr, nullptr, n, shift, key, s_base, s_wcnt);
+            uint32_t* t = v0; v0 = v1; v1 = t;
+            t = k0; k0 = k1; k1 = t;
         }
-        for (long long i = tid; i < n; i += kTileLongThreads) vals[rg.x + i] = src[i];
+        for (long long i = tid; i < n; i += kTileLongThreads) vals[rg.x + i] = v0[i];
         __syncthreads();
     }
 }
@@ -1079,8 +1106,14 @@ cudaError_t launch_tile_sort(uint32_t* vals, const uint2* ranges, long long tile
     const long long want = (tiles + 3) / 4;
     const int grid = (int)(want < (long long)sms * 8 ? want : (long long)sms * 8);
     k_tile_sort<<<grid, kTileSortThreads, 0, st>>>(vals, ranges, (int)tiles, zbits, counters, long_list, status);
-    k_tile_sort_long<<<sms * 2, kTileLongThreads, 0, st>>>(vals, ranges, zbits, counters, long_list, scratch_a,
-                                                          scratch_b, status);
+    static std::atomic<int> attr_done{0};
+    if (!attr_done.load()) {
+        e = cudaFuncSetAttribute(k_tile_sort_long, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileLongSmem);
+        if (e != cudaSuccess) return e;
+        attr_done.store(1);
+    }
+    k_tile_sort_long<<<sms * 3, kTileLongThreads, kTileLongSmem, st>>>(vals, ranges, zbits, counters, long_list,
+                                                                       scratch_a, scratch_b, status);
     return cudaGetLastError();
 }
 
