@@ -145,8 +145,8 @@ def blend_flops(F, pairs):
 MEASURED_TRAFFIC = {
     "blend_bwd": [
         {"primitives": 500000, "cameras": 8, "schedule": {"tile": 16, "pixels_per_thread": 2, "batch": 128},
-         "bytes": 574.3e6 + 127.9e6, "sources_sha1": "5455c3edab0f1ed1ec984dc070f21df0dba5796d",
-         "capture": "ncu --set full -k regex:^k_blend_bwd$ -s 2 -c 1 (dram__bytes_read.sum, dram__bytes_write.sum)"},
+         "bytes": 520.0e6 + 122.2e6, "sources_sha1": "a7e7017f150a710cb5719beaf58fe1943db384a9",
+         "capture": "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum -k regex:^k_blend_bwd$ -s 2 -c 1"},
     ],
     "blend_fwd": [
         {"primitives": 500000, "cameras": 8, "schedule": {"tile": 16, "pixels_per_thread": 2, "batch": 128},
