@@ -38,7 +38,7 @@ __device__ __forceinline__ float ld_each(const float* p) {
 }
 
 template <int V, int DEG>
-__global__ void __launch_bounds__(128) k_preprocess(PrimsDev P, CamsParam cams, float* __restrict__ rec,
+__global__ void __launch_bounds__(128, 4) k_preprocess(PrimsDev P, CamsParam cams, float* __restrict__ rec,
                                                     uint32_t* __restrict__ counts,
                                                     int4* __restrict__ trect,
                                                     uint32_t* __restrict__ zbits,
@@ -332,7 +332,8 @@ k_chain(PrimsDev P, CamsParam cams, const uint32_t* __restrict__ meta_in, const 
             const float4 a4 = __ldg(reinterpret_cast<const float4*>(A) + s);
             const float Ge = a4.z;
             const float Ga = __fmaf_rn(-g.fxo, Ge, a4.x), Gb = __fmaf_rn(-g.fyo, Ge, a4.y);
-            if (Ga == 0.f && Gb == 0.f && Ge == 0.f) continue;
+            // (a face without gradient is not skipped: its terms are exact
+            // zeros, and lanes of a warp then stay together)
             int iv[3];
             face_vertices<V>(f, iv[0], iv[1], iv[2]);
             float n[3];
