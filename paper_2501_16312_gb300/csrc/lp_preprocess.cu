@@ -201,11 +201,11 @@ __global__ void __launch_bounds__(128, 4) k_preprocess(PrimsDev P, CamsParam cam
 // registers a thread holds (the SH coefficients and their gradients live
 // only in PART 1), which pays where many cameras make the loop long.  The
 // geometry pass is held to four resident blocks per SM (128 registers), the
-// colour pass, which holds 48 SH gradients, to three (170 registers), so that
-// neither spills: the loop waits on memory once per camera, and the resident
-// warps hide it.
+// colour pass, which holds 48 SH gradients, to four for octahedra (a few
+// spills, measured faster) and three for tetrahedra: the loop waits on
+// memory once per camera, and the resident warps hide it.
 template <int V, int DEG, int PART>
-__global__ void __launch_bounds__(128, PART == 2 ? 1 : (PART == 1 ? 3 : 4))
+__global__ void __launch_bounds__(128, PART == 2 ? 1 : (PART == 1 ? (V == 6 ? 4 : 3) : 4))
 k_chain(PrimsDev P, CamsParam cams, const uint32_t* __restrict__ meta_in, const uint32_t* __restrict__ counts,
         const float* __restrict__ acc, float* __restrict__ dcentre, float* __restrict__ dverts,
         float* __restrict__ dopacity, float* __restrict__ dsh, int accumulate) {
