@@ -884,6 +884,8 @@ cudaError_t launch_emit_sorted(const uint32_t* order, const uint32_t* counts_sor
 constexpr int kTileSortThreads = 128;
 constexpr int kTileWarpCap = 512;
 constexpr int kTileLongThreads = 256;
+constexpr int kTileBlockCap = 2048;
+constexpr size_t kTileLongSmem = (size_t)4 * kTileBlockCap * sizeof(uint32_t);
 
 // Stable LSD sort of n <= kTileWarpCap (key, value) pairs in a warp's shared
 // memory (ka, va; kb, vb a second buffer; cnt 256 counters).  Returns the
@@ -1037,13 +1039,80 @@ __device__ void block_lsd_pass(const uint32_t* src, uint32_t* dst, const uint32_
     }
 }
 
+// One LSD pass of a block over a run of n <= kTileBlockCap entries in shared
+// memory (keys ks, values vs -> kd, vd), as one chunk: warp w ranks the w-th
+// contiguous eighth of the run round by round (equal digits found by ballots,
+// a running count per (warp, digit) in s_wcnt), the per-digit starts come
+// from one block scan, and each entry goes to its digit's start plus the
+// counts of earlier warps plus its rank within the warp.  Equal digits keep
+// their order.  Four block barriers per pass.
+__device__ void block_lsd_pass_smem(const uint32_t* ks, const uint32_t* vs, uint32_t* kd, uint32_t* vd, int n,
+                                    int shift, uint32_t* s_base, uint32_t (*s_wcnt)[256], uint32_t* s_wsum) {
+    constexpr int NW = kTileLongThreads / 32;
+    constexpr int RMAX = kTileBlockCap / kTileLongThreads;   // rounds per warp at most
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    const int per_warp = ((n + NW - 1) / NW + 31) & ~31;     // whole rounds
+    const int rounds = per_warp / 32;
+#pragma unroll
+    for (int ww = 0; ww < NW; ++ww) s_wcnt[ww][tid] = 0u;
+    __syncthreads();
+    uint32_t pk[RMAX];   // digit | rank within (warp, digit) << 9
+#pragma unroll
+    for (int r = 0; r < RMAX; ++r) {
+        pk[r] = 256u;
+        if (r < rounds) {
+            const int i = w * per_warp + r * 32 + lane;
+            const uint32_t d = i < n ? (ks[i] >> shift) & 255u : 256u;
+            const unsigned peers = digit_peers<8>(d);
+            const uint32_t rank = __popc(peers & lt);
+            const uint32_t base = d < 256u ? s_wcnt[w][d] : 0u;
+            __syncwarp();
+            if (d < 256u && rank == 0) s_wcnt[w][d] = base + __popc(peers);
+            __syncwarp();
+            pk[r] = d | ((base + rank) << 9);
+        }
+    }
+    __syncthreads();
+    // thread t, digit t: starts of the warps within the digit, then the
+    // digit's start over the run (exclusive scan of the digit totals)
+    uint32_t run = 0u;
+#pragma unroll
+    for (int ww = 0; ww < NW; ++ww) {
+        const uint32_t c = s_wcnt[ww][tid];
+        s_wcnt[ww][tid] = run;
+        run += c;
+    }
+    uint32_t x = run;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_wsum[w] = x;
+    __syncthreads();
+    uint32_t start = x - run;
+    for (int ww = 0; ww < w; ++ww) start += s_wsum[ww];
+    s_base[tid] = start;
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < RMAX; ++r) {
+        const uint32_t d = pk[r] & 511u;
+        if (r < rounds && d < 256u) {
+            const int i = w * per_warp + r * 32 + lane;
+            const uint32_t pos = s_base[d] + s_wcnt[w][d] + (pk[r] >> 9);
+            kd[pos] = ks[i];
+            vd[pos] = vs[i];
+        }
+    }
+    __syncthreads();
+}
+
 // One block per listed long run, sorted stably by depth bits: runs of up to
 // kTileBlockCap entries in shared memory (dynamic, keys moving with the
-// values), longer ones through the global scratch arrays sa and sb (the
-// run's own positions [rg.x, rg.y) of each; the depth bits are gathered
-// again in each pass).
-constexpr int kTileBlockCap = 4096;
-constexpr size_t kTileLongSmem = (size_t)4 * kTileBlockCap * sizeof(uint32_t);
+// values; block_lsd_pass_smem, one chunk per pass), longer ones through the
+// global scratch arrays sa and sb (the run's own positions [rg.x, rg.y) of
+// each; block_lsd_pass in chunks, the depth bits gathered again in each pass).
 
 __global__ void __launch_bounds__(kTileLongThreads) k_tile_sort_long(uint32_t* __restrict__ vals,
                                                                      const uint2* __restrict__ ranges,
@@ -1057,6 +1126,7 @@ __global__ void __launch_bounds__(kTileLongThreads) k_tile_sort_long(uint32_t* _
     extern __shared__ __align__(16) uint32_t s_run[];   // values, keys; second values, keys
     __shared__ uint32_t s_base[256];
     __shared__ uint32_t s_wcnt[NW][256];
+    __shared__ uint32_t s_wsum[NW];
     __shared__ uint32_t s_or, s_and;
     if (*status & (kStatusCapacity | kStatusTimeout)) return;
     const int tid = threadIdx.x, lane = tid & 31;
@@ -1087,7 +1157,7 @@ __global__ void __launch_bounds__(kTileLongThreads) k_tile_sort_long(uint32_t* _
         const uint32_t diff = s_or & ~s_and;
         for (int shift = 0; shift < 32; shift += 8) {
             if (((diff >> shift) & 255u) == 0u) continue;   // uniform over the block
-            if (in_smem) block_lsd_pass<true>(v0, v1, k0, k1, n, shift, key, s_base, s_wcnt);
+            if (in_smem) block_lsd_pass_smem(k0, v0, k1, v1, (int)n, shift, s_base, s_wcnt, s_wsum);
             else block_lsd_pass<false>(v0, v1, nullptr, nullptr, n, shift, key, s_base, s_wcnt);
             uint32_t* t = v0; v0 = v1; v1 = t;
             t = k0; k0 = k1; k1 = t;
@@ -1112,7 +1182,7 @@ cudaError_t launch_tile_sort(uint32_t* vals, const uint2* ranges, long long tile
         if (e != cudaSuccess) return e;
         attr_done.store(1);
     }
-    k_tile_sort_long<<<sms * 3, kTileLongThreads, kTileLongSmem, st>>>(vals, ranges, zbits, counters, long_list,
+    k_tile_sort_long<<<sms * 5, kTileLongThreads, kTileLongSmem, st>>>(vals, ranges, zbits, counters, long_list,
                                                                        scratch_a, scratch_b, status);
     return cudaGetLastError();
 }
