@@ -1176,12 +1176,8 @@ cudaError_t launch_tile_sort(uint32_t* vals, const uint2* ranges, long long tile
     const long long want = (tiles + 3) / 4;
     const int grid = (int)(want < (long long)sms * 8 ? want : (long long)sms * 8);
     k_tile_sort<<<grid, kTileSortThreads, 0, st>>>(vals, ranges, (int)tiles, zbits, counters, long_list, status);
-    static std::atomic<int> attr_done{0};
-    if (!attr_done.load()) {
-        e = cudaFuncSetAttribute(k_tile_sort_long, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileLongSmem);
-        if (e != cudaSuccess) return e;
-        attr_done.store(1);
-    }
+    // 32 KB of dynamic shared memory: within the default limit, no attribute to set
+    static_assert(kTileLongSmem + 10 * 1024 <= 48 * 1024, "dynamic + static shared memory of k_tile_sort_long");
     k_tile_sort_long<<<sms * 5, kTileLongThreads, kTileLongSmem, st>>>(vals, ranges, zbits, counters, long_list,
                                                                        scratch_a, scratch_b, status);
     return cudaGetLastError();
