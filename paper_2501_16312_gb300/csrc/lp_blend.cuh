@@ -31,11 +31,11 @@ template <int TILE, int PIX> struct LaneGroups {
     static constexpr int kColBit = WG::TPR == 2 ? 0 : WG::TPR == 4 ? 1 : WG::TPR == 8 ? 2 : 3;
     // the lane bits that name a group
     static constexpr uint32_t kGroupBits = G == 1 ? 0u : G == 2 ? 16u : (16u | (1u << kColBit));
-    __device__ __forceinline__ static int group(int lane) {
+    __host__ __device__ __forceinline__ static int group(int lane) {
         return G == 1 ? 0 : G == 2 ? lane >> 4 : ((lane >> 4) << 1) | ((lane >> kColBit) & 1);
     }
     // the group's first lane (every other lane bit clear) writes its mask row
-    __device__ __forceinline__ static bool leader(int lane) { return (lane & ~(int)kGroupBits) == 0; }
+    __host__ __device__ __forceinline__ static bool leader(int lane) { return (lane & ~(int)kGroupBits) == 0; }
     // OR of x over the lanes of each lane's group
     __device__ __forceinline__ static uint32_t reduce_or(uint32_t x) {
         if (G == 1) return __reduce_or_sync(0xffffffffu, x);

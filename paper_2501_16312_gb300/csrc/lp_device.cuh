@@ -293,7 +293,7 @@ template <int TILE, int PIX> struct WarpGrid {
     static constexpr int NW = TILE * TILE / PIX / 32;    // warps per tile
     static_assert(WC % PIX == 0 && TILE % WC == 0 && TILE % WR == 0 && NW * 32 * PIX == TILE * TILE,
                   "warps of whole rectangles");
-    __device__ __forceinline__ static void pixel(int tid, int& ly, int& lx0) {
+    __host__ __device__ __forceinline__ static void pixel(int tid, int& ly, int& lx0) {
         const int w = tid >> 5, lane = tid & 31;
         ly = (w / NWX) * WR + lane / TPR;
         lx0 = (w % NWX) * WC + (lane % TPR) * PIX;
