@@ -983,18 +983,18 @@ __global__ void __launch_bounds__(kTileSortThreads) k_tile_sort(uint32_t* __rest
 // One LSD pass of a block over n entries (values v, keys key(v) by the
 // functor): digit counts, their scan, then chunks of kTileLongThreads entries
 // in order, each ranked by warp, then across the block's warps, so that equal
-// digits keep their order.  src and dst are shared or global arrays; with
-// keys in arrays ksrc/kdst they move along (KEYS), else key() gathers them.
-template <bool KEYS, typename KeyF>
-__device__ void block_lsd_pass(const uint32_t* src, uint32_t* dst, const uint32_t* ksrc, uint32_t* kdst,
-                               long long n, int shift, KeyF key, uint32_t* s_base, uint32_t (*s_wcnt)[256]) {
+// digits keep their order.  src and dst are global arrays; key() gathers
+// each entry's key again on every pass.
+template <typename KeyF>
+__device__ void block_lsd_pass(const uint32_t* src, uint32_t* dst, long long n, int shift, KeyF key,
+                               uint32_t* s_base, uint32_t (*s_wcnt)[256]) {
     constexpr int NW = kTileLongThreads / 32;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const unsigned lt = (1u << lane) - 1u;
     s_base[tid] = 0u;
     __syncthreads();
     for (long long i = tid; i < n; i += kTileLongThreads)
-        atomicAdd(&s_base[((KEYS ? ksrc[i] : key(src[i])) >> shift) & 255u], 1u);
+        atomicAdd(&s_base[(key(src[i]) >> shift) & 255u], 1u);
     __syncthreads();
     if (w == 0) {   // exclusive scan of the 256 counts, 8 per lane
         uint32_t c[8], tot = 0u;
@@ -1015,7 +1015,7 @@ __device__ void block_lsd_pass(const uint32_t* src, uint32_t* dst, const uint32_
         const long long i = c0 + tid;
         const bool ok = i < n;
         const uint32_t v = ok ? src[i] : 0u;
-        const uint32_t k = ok ? (KEYS ? ksrc[i] : key(v)) : 0u;
+        const uint32_t k = ok ? key(v) : 0u;
         const uint32_t d = ok ? (k >> shift) & 255u : 256u;
         const unsigned peers = digit_peers<8>(d);
         const uint32_t rank = __popc(peers & lt);
@@ -1028,7 +1028,6 @@ __device__ void block_lsd_pass(const uint32_t* src, uint32_t* dst, const uint32_
             uint32_t pos = s_base[d] + rank;
             for (int ww = 0; ww < w; ++ww) pos += s_wcnt[ww][d];
             dst[pos] = v;
-            if (KEYS) kdst[pos] = k;
         }
         __syncthreads();
         uint32_t add = 0u;
@@ -1158,7 +1157,7 @@ __global__ void __launch_bounds__(kTileLongThreads) k_tile_sort_long(uint32_t* _
         for (int shift = 0; shift < 32; shift += 8) {
             if (((diff >> shift) & 255u) == 0u) continue;   // uniform over the block
             if (in_smem) block_lsd_pass_smem(k0, v0, k1, v1, (int)n, shift, s_base, s_wcnt, s_wsum);
-            else block_lsd_pass<false>(v0, v1, nullptr, nullptr, n, shift, key, s_base, s_wcnt);
+            else block_lsd_pass(v0, v1, n, shift, key, s_base, s_wcnt);
             uint32_t* t = v0; v0 = v1; v1 = t;
             t = k0; k0 = k1; k1 = t;
         }
