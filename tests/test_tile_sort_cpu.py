@@ -8,9 +8,13 @@ whose value is the same for every entry of the run.  A warp takes the run in
 rounds of 32 entries: the lanes holding the same digit are found with one
 ballot per digit bit, a lane's rank among them is the number of such lanes
 before it, and a running count per digit places each round after the earlier
-ones.  A block takes the run in chunks of 256 entries, ranks each chunk per
-warp, adds the counts of the chunk's earlier warps for the same digit, and
-then the running per-digit offsets.
+ones.  A block holding a run of up to 2048 entries in shared memory gives
+warp w the w-th contiguous share of it, ranks each share round by round, and
+places an entry at its digit's start plus the earlier warps' counts of that
+digit plus its rank within its warp.  A block sorting a longer run through
+global memory takes it in chunks of 256 entries, ranks each chunk per warp,
+adds the counts of the chunk's earlier warps for the same digit, and then the
+running per-digit offsets.
 
 This restates those steps in Python and checks them against numpy's stable
 argsort on the (depth bits, record) pairs: runs of every length up to several
@@ -113,6 +117,47 @@ def block_sort(keys, vals, threads=256):
     return keys, vals
 
 
+def block_sort_smem(keys, vals, threads=256, drop_earlier_warps=False):
+    """A block's sort of a run held in shared memory (k_tile_sort_long, runs
+    of up to 2048 entries): per pass, warp w takes the w-th contiguous share of
+    the run (whole rounds of 32), ranks it round by round with a running count
+    per (warp, digit), and an entry goes to its digit's start plus the counts
+    of the earlier warps for that digit plus its rank within its warp."""
+    keys, vals = list(keys), list(vals)
+    n, nw = len(keys), threads // 32
+    per_warp = ((n + nw - 1) // nw + 31) & ~31
+    for shift in varying_digits(keys):
+        wcnt = [[0] * 256 for _ in range(nw)]
+        packed = {}                                   # entry -> (digit, rank within its warp)
+        for w in range(nw):
+            for r in range(per_warp // 32):
+                idx = [i for i in range(w * per_warp + r * 32, w * per_warp + r * 32 + 32) if i < n]
+                if not idx:
+                    continue
+                digits = [(keys[i] >> shift) & 255 for i in idx] + [256] * (32 - len(idx))
+                base = {d: wcnt[w][d] for d in set(digits[:len(idx)])}   # read before the leaders add
+                for lane, i in enumerate(idx):
+                    peers = digit_peers(digits, lane)
+                    rank = bin(peers & ((1 << lane) - 1)).count("1")
+                    packed[i] = (digits[lane], base[digits[lane]] + rank)
+                    if rank == 0:
+                        wcnt[w][digits[lane]] = base[digits[lane]] + bin(peers).count("1")
+        before = [[0 if drop_earlier_warps else sum(wcnt[ww][d] for ww in range(w)) for d in range(256)]
+                  for w in range(nw)]
+        totals = [sum(wcnt[w][d] for w in range(nw)) for d in range(256)]
+        start, run = [0] * 256, 0
+        for d in range(256):
+            start[d], run = run, run + totals[d]
+        nk, nv = [None] * n, [None] * n
+        for i, (d, rank) in packed.items():
+            w = i // per_warp
+            pos = start[d] + before[w][d] + rank
+            assert drop_earlier_warps or nk[pos] is None
+            nk[pos], nv[pos] = keys[i], vals[i]
+        keys, vals = nk, nv
+    return keys, vals
+
+
 def reference(keys, vals):
     order = np.lexsort((np.asarray(vals, np.uint64), np.asarray(keys, np.uint64)))
     return [int(keys[i]) for i in order], [int(vals[i]) for i in order]
@@ -134,6 +179,8 @@ def runs(seed):
     yield depth_bits(z)                                                # extremes
     yield depth_bits(rng.uniform(0.5, 40.0, 1))                        # a single entry
     yield depth_bits(rng.choice(rng.uniform(0.2, 5.0, 40), 700))       # several chunks, many ties
+    yield depth_bits(rng.uniform(0.3, 12.0, 2048))                     # the largest run held in shared memory
+    yield depth_bits(rng.choice(rng.uniform(1.0, 3.0, 9), 1531))       # ragged shares, few distinct depths
 
 
 @pytest.mark.parametrize("seed", [0, 1, 2])
@@ -146,6 +193,9 @@ def test_per_tile_sort_steps_are_stable_and_exact(seed):
             assert warp_sort(keys, vals) == want, n
         assert block_sort(keys, vals) == want, n
         assert block_sort(keys, vals, threads=64) == want, n
+        if n <= 2048:
+            assert block_sort_smem(keys, vals) == want, n
+            assert block_sort_smem(keys, vals, threads=64) == want, n
 
 
 def test_skipped_digits_are_the_constant_ones():
@@ -174,3 +224,17 @@ def test_planted_instability_is_caught():
 
     assert unstable(keys, vals) != reference(keys, vals)
     assert warp_sort(keys, vals) == reference(keys, vals)
+
+
+def test_planted_missing_warp_offsets_are_caught():
+    """Leaving out the earlier warps' counts of a digit (a plausible slip in
+    the shared-memory block form) puts two warps' entries in the same places,
+    and the check sees it."""
+    keys = depth_bits(np.random.default_rng(5).uniform(0.5, 9.0, 600))
+    vals = list(range(600))
+    try:
+        got = block_sort_smem(keys, vals, drop_earlier_warps=True)
+    except TypeError:     # holes left by the collisions reach the next pass
+        got = None
+    assert got != reference(keys, vals)
+    assert block_sort_smem(keys, vals) == reference(keys, vals)
