@@ -73,6 +73,14 @@ MUTANTS = {
     "exact_grad_sign": ("for (m = 0; m < 3; ++m) a[m] = (p0[m] - lam * d[m]) / dn;",
                         "for (m = 0; m < 3; ++m) a[m] = (p0[m] + lam * d[m]) / dn;", ["exact_fd"]),
     "aa_rect_unmoved": ("if (kf->shx[k] > 0) qx = qx + sh;", "if (kf->shx[k] > 0) qx = qx;", ["aa_rect"]),
+    "colour_clamp_grad_unmasked": ("double gc = pp->rgb_raw[ch] > 0.0 ? pg->drgb[ch] : 0.0;",
+                                   "double gc = pg->drgb[ch];", ["clamp"]),
+    "colour_offset_dropped": ("pp->rgb_raw[ch] = s + 0.5;", "pp->rgb_raw[ch] = s;", ["two_layer"]),
+    "dalpha_drop_099": ("dopacity[i] += pg->dsigma * 0.99 / ((1.0 - 0.99 * P->opacity[i]) * 2.0 * pp->dmin);",
+                        "dopacity[i] += pg->dsigma / ((1.0 - 0.99 * P->opacity[i]) * 2.0 * pp->dmin);",
+                        ["fd_tetra"]),
+    "background_unattenuated": ("for (ch = 0; ch < 3; ++ch) out->rgb[ch] = C[ch] + T * bg[ch];",
+                                "for (ch = 0; ch < 3; ++ch) out->rgb[ch] = C[ch] + bg[ch];", ["two_layer"]),
 }
 
 CHECKS = {
@@ -100,6 +108,7 @@ CHECKS = {
     "aa_span": lambda o: pins.test_aa_filter_octahedron_span_closed_form(o, 4.0),
     "aa_moves": pins.test_aa_filter_moves_box_vertices,
     "aa_rect": pins.test_aa_filter_widens_the_pixel_rectangle,
+    "clamp": pins.test_clamped_colour_channel_has_no_gradient,
 }
 
 

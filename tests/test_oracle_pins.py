@@ -511,6 +511,31 @@ def test_adjoint_fd_octahedra_sh3(orc):
     assert ok >= 0.8 * len(params)
 
 
+def test_clamped_colour_channel_has_no_gradient(orc):
+    """Sec. 3.1 (colour as in 3DGS): rgb = max(0, SH + 0.5).  A channel whose
+    SH value sits well below -0.5 is clamped to 0 on a whole neighbourhood of
+    the parameters, so the loss does not depend on that channel's SH
+    coefficients there, nor on the view direction through them: central
+    differences give zero, and the adjoint must too, for the SH coefficients
+    and for the centre (degree 1, so the direction term is live)."""
+    R = scenes.random_rotations(np.random.default_rng(3), 1)[0]
+    sh = np.zeros((1, 4, 3))
+    sh[0, 0, :] = scenes.sh_from_rgb(np.array([-0.4, 0.5, 0.7]))
+    sh[0, 1:, :] = [[0.06, -0.04, 0.05], [-0.05, 0.07, 0.03], [0.04, 0.05, -0.06]]
+    sc = one_scene(6, (0.05, -0.03, 0.0), axis_octa((0.05, -0.03, 0.0), 0.5, 0.4, 0.3, R), 0.8, sh=sh, degree=1)
+    cam = cam_on_axis(D=3.0, W=41, H=41)
+    img = orc.render(sc, [cam], bg=(0.1, 0.2, 0.3)).reshape(3, cam.height, cam.width)
+    assert np.count_nonzero(img[1] != 0.2) > 60           # the primitive covers pixels
+    gimg = np.random.default_rng(16).normal(size=3 * cam.pixels)
+    dmin = orc.preprocess(sc, cam)["dmin"]
+    _, grads = orc.render(sc, [cam], bg=(0.1, 0.2, 0.3), dL_dimage=gimg, dmin=dmin)
+    assert np.all(grads["sh"].reshape(4, 3)[:, 0] == 0.0)  # the clamped channel
+    assert np.all(np.abs(grads["sh"].reshape(4, 3)[:, 1:]) > 0.0)
+    params = [("sh", 3 * k + ch) for k in range(4) for ch in range(3)] + [("centre", a) for a in range(3)]
+    ok = _fd_check(orc, sc, cam, (0.1, 0.2, 0.3), gimg, params)
+    assert ok >= 0.8 * len(params)
+
+
 def test_ray_space_map_is_first_order_perspective(orc):
     """App. 'Ray Space Approximation': each ray-space vertex is the local affine
     (first-order) approximation of (fx x/z + cx, fy y/z + cy, |t|) around the
