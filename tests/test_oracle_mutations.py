@@ -81,6 +81,9 @@ MUTANTS = {
                         ["fd_tetra"]),
     "background_unattenuated": ("for (ch = 0; ch < 3; ++ch) out->rgb[ch] = C[ch] + T * bg[ch];",
                                 "for (ch = 0; ch < 3; ++ch) out->rgb[ch] = C[ch] + bg[ch];", ["two_layer"]),
+    "near_plane_off": ("    if (!(tc[2] > ORC_NEAR)) return;", "    if (!(tc[2] > -ORC_NEAR)) return;", ["near"]),
+    "camera_position_sign": ("campos[m] = -(R[0][m] * T[0] + R[1][m] * T[1] + R[2][m] * T[2]);",
+                             "campos[m] = (R[0][m] * T[0] + R[1][m] * T[1] + R[2][m] * T[2]);", ["colour_dir"]),
 }
 
 CHECKS = {
@@ -109,6 +112,8 @@ CHECKS = {
     "aa_moves": pins.test_aa_filter_moves_box_vertices,
     "aa_rect": pins.test_aa_filter_widens_the_pixel_rectangle,
     "clamp": pins.test_clamped_colour_channel_has_no_gradient,
+    "near": pins.test_near_plane_cull,
+    "colour_dir": pins.test_colour_direction_is_from_the_camera,
 }
 
 

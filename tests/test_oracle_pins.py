@@ -346,6 +346,43 @@ def test_view_frustum_cull(orc):
         assert (np.abs(img).max() > 0) == keep
 
 
+def test_near_plane_cull(orc):
+    """A primitive whose centre lies at camera depth 0.2 or less (the near
+    plane), or behind the camera, is not drawn: a small primitive straight
+    ahead at depth 0.19 is dropped, at 0.21 drawn, and 1.0 behind the camera
+    dropped."""
+    cam = scenes.make_camera((0.0, 0.0, 0.0), 160, 100, 60.0, target=(0.0, 0.0, 1.0))
+    M = cam.viewmat.astype(np.float64)
+    for z, keep in ((0.19, False), (0.21, True), (-1.0, False)):
+        world = M[:3, :3].T @ (np.array([0.0, 0.0, z]) - M[:3, 3])
+        sc = _frustum_scene(world, dist=0.01)
+        assert bool(orc.preprocess(sc, cam)["visible"][0]) == keep, z
+        img = orc.render(sc, [cam]).reshape(3, -1)
+        assert (np.abs(img).max() > 0) == keep, z
+
+
+def test_colour_direction_is_from_the_camera(orc):
+    """Sec. 3.1 (view-dependent colour as in 3DGS): the SH are evaluated at
+    the unit direction from the camera's position to the primitive's centre.
+    The camera position here is the eye the camera was built from (the
+    oracle recovers it from the view matrix), the basis is the one pinned to
+    scipy above, and the colour is max(0, SH + 0.5)."""
+    rng = np.random.default_rng(17)
+    eye = np.array([1.5, -0.7, 4.0])
+    cam = scenes.make_camera(tuple(eye), 64, 48, 50.0, target=(0.1, 0.2, -0.3))
+    for _ in range(10):
+        c = rng.uniform(-0.6, 0.6, 3)
+        sh = rng.normal(0.0, 0.4, (1, 16, 3))
+        sc = one_scene(6, c, axis_octa(c, 0.1, 0.08, 0.06), 0.6, sh=sh, degree=3)
+        pp = orc.preprocess(sc, cam)
+        assert pp["visible"][0]
+        d = c - eye
+        np.testing.assert_allclose(pp["dist"][0], np.linalg.norm(d), rtol=1e-6)
+        Y, _ = orc.sh_basis(3, d / np.linalg.norm(d))
+        want = np.maximum(Y @ sh[0] + 0.5, 0.0)
+        np.testing.assert_allclose(pp["rgb"][0], want, atol=1e-5)
+
+
 def test_keyfields_are_binary32_replay(orc):
     """The culling / depth key / pixel rectangle come from binary32 with one
     rounding per operation (the centre transformed to the camera frame, each
