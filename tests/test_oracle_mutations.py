@@ -84,6 +84,18 @@ MUTANTS = {
     "near_plane_off": ("    if (!(tc[2] > ORC_NEAR)) return;", "    if (!(tc[2] > -ORC_NEAR)) return;", ["near"]),
     "camera_position_sign": ("campos[m] = -(R[0][m] * T[0] + R[1][m] * T[1] + R[2][m] * T[2]);",
                              "campos[m] = (R[0][m] * T[0] + R[1][m] * T[1] + R[2][m] * T[2]);", ["colour_dir"]),
+    "keys_value_not_record": ("E[n].val = (uint32_t)((long long)c * P->n + i);", "E[n].val = (uint32_t)i;",
+                              ["keys_multiview"]),
+    "keys_tile_base_missing": ("            tile_base += (long long)tiles_x * tiles_y;\n", "", ["keys_multiview"]),
+    "keys_last_tile_column": ("for (tx = kf.px0 / tile; tx <= kf.px1 / tile; ++tx) {",
+                              "for (tx = kf.px0 / tile; tx < kf.px1 / tile; ++tx) {", ["keys_structure"]),
+    "keys_no_depth": ("E[n].key = (gt << 32) | kf.zbits;", "E[n].key = (gt << 32);", ["keys_structure"]),
+    "counts_flag_only": ("counts[(size_t)c * P->n + i] = (uint32_t)cnt;", "counts[(size_t)c * P->n + i] = (uint32_t)(cnt > 0);",
+                         ["keys_structure"]),
+    "rect_clamp_past_image": ("fx1 = fminf(fx1, (float)(cam->width - 1));", "fx1 = fminf(fx1, (float)(cam->width));",
+                              ["keyfields"]),
+    "aa_tetra_half_kernel": ("return (float)(P->nv == 6 ? 0.5 * P->aa_kernel : P->aa_kernel);",
+                             "return (float)(0.5 * P->aa_kernel);", ["aa_moves"]),
 }
 
 CHECKS = {
@@ -114,6 +126,7 @@ CHECKS = {
     "clamp": pins.test_clamped_colour_channel_has_no_gradient,
     "near": pins.test_near_plane_cull,
     "colour_dir": pins.test_colour_direction_is_from_the_camera,
+    "keys_multiview": pins.test_keys_multiview_tile_bases,
 }
 
 
