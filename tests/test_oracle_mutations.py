@@ -96,6 +96,15 @@ MUTANTS = {
                               ["keyfields"]),
     "aa_tetra_half_kernel": ("return (float)(P->nv == 6 ? 0.5 * P->aa_kernel : P->aa_kernel);",
                              "return (float)(0.5 * P->aa_kernel);", ["aa_moves"]),
+    "chain_drop_direction_row": ("            dtc[b] += dJ[2][a] * d_ab / len;\n", "", ["aa_fd"]),
+    "exact_near_plane_off": ("if (!(Z > ORC_NEAR)) { kf->visible = 0; return; }",
+                             "if (!(Z > -1e30f)) { kf->visible = 0; return; }", ["exact_near"]),
+    "silhouette_flag_off": ("if (fabs(c2 - c1) <= 1e-5 * (zhi - zlo)) out->borderline |= 2;",
+                            "if (0) out->borderline |= 2;", ["silhouette"]),
+    "stop_flag_too_tight": ("if (fabs(Tn - ORC_STOP_T) <= 1e-3 * ORC_STOP_T) out->borderline |= 1;",
+                            "if (fabs(Tn - ORC_STOP_T) <= 1e-9 * ORC_STOP_T) out->borderline |= 1;", ["stop_flag"]),
+    "depth_flag_off": ("if (fabs(Tn - 0.5) <= 1e-4 * 0.5) out->borderline |= 4;", "if (0) out->borderline |= 4;",
+                       ["depth_flag"]),
 }
 
 CHECKS = {
@@ -127,6 +136,11 @@ CHECKS = {
     "near": pins.test_near_plane_cull,
     "colour_dir": pins.test_colour_direction_is_from_the_camera,
     "keys_multiview": pins.test_keys_multiview_tile_bases,
+    "aa_fd": pins.test_aa_filter_adjoint_fd,
+    "exact_near": pins.test_exact_culls_primitives_reaching_the_near_plane,
+    "silhouette": pins.test_silhouette_grazing_pixels_are_flagged,
+    "stop_flag": lambda o: [pins.test_borderline_stop_flag(o, r, f) for r, f in ((2e-4, True), (5e-3, False))],
+    "depth_flag": lambda o: [pins.test_borderline_depth_flag(o, x, f) for x, f in ((0.5 + 2e-5, True), (0.501, False))],
 }
 
 

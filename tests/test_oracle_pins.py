@@ -283,6 +283,40 @@ def test_early_stop_at_cumulative_opacity_0999(orc, alpha):
     np.testing.assert_allclose(img[:, 16, 16], (1 - T) * 1.0 + T * 0.5, rtol=1e-12)
 
 
+@pytest.mark.parametrize("rel, flagged", [(2e-4, True), (-2e-4, True), (5e-3, False), (-5e-3, False)])
+def test_borderline_stop_flag(orc, rel, flagged):
+    """Two layers through their thin axes (opacity exactly 0.99 alpha each)
+    take T to (1 + rel) 1e-3.  Within 1e-3 (relative) of the stop threshold
+    the pixel is flagged (info bit 0): binary32 may stop one primitive
+    earlier or later there.  Farther from it, it is not."""
+    o1 = 0.96
+    t_end = STOP_T * (1 + rel)
+    o2 = 1 - t_end / (1 - o1)
+    sc = centred_octa_scene([1.0, -1.0], [(0.3, 0.3, 0.1)] * 2, [o1 / ALPHA_SCALE, o2 / ALPHA_SCALE],
+                            [[1.0, 1.0, 1.0]] * 2)
+    cam = cam_on_axis(4.0, 33, 33, 30.0)
+    _, info = orc.render(sc, [cam], info=True)
+    info = info.reshape(33, 33, 4)
+    assert info[16, 16, 0] == 2
+    assert abs(info[16, 16, 1] - t_end) < 1e-14
+    assert bool(int(info[16, 16, 2]) & 1) == flagged
+
+
+@pytest.mark.parametrize("o, flagged", [(0.5 + 2e-5, True), (0.5 - 2e-5, True), (0.5 + 1e-3, False),
+                                        (0.5 - 1e-3, False)])
+def test_borderline_depth_flag(orc, o, flagged):
+    """The depth map reads the first primitive that takes the cumulative
+    opacity above 0.5.  When the transmittance after a primitive lands within
+    1e-4 (relative) of 0.5, binary32 may choose the next primitive or none,
+    so the pixel is flagged (info bit 2); farther from it, it is not."""
+    sc = centred_octa_scene([0.0], [(0.3, 0.3, 0.1)], [o / ALPHA_SCALE], [[1.0, 1.0, 1.0]])
+    cam = cam_on_axis(4.0, 33, 33, 30.0)
+    _, info = orc.render(sc, [cam], info=True)
+    info = info.reshape(33, 33, 4)
+    assert abs(info[16, 16, 1] - (1 - o)) < 1e-14
+    assert bool(int(info[16, 16, 2]) & 4) == flagged
+
+
 def test_transmittance_bounds_and_empty_pixels(orc):
     w = scenes.workload(0)
     img, info = orc.render(w.scene, w.cameras, info=True)
