@@ -105,6 +105,14 @@ MUTANTS = {
                             "if (fabs(Tn - ORC_STOP_T) <= 1e-9 * ORC_STOP_T) out->borderline |= 1;", ["stop_flag"]),
     "depth_flag_off": ("if (fabs(Tn - 0.5) <= 1e-4 * 0.5) out->borderline |= 4;", "if (0) out->borderline |= 4;",
                        ["depth_flag"]),
+    "quat_rotation_sign": ("R[0][1] = 2 * (x * y - w * z);", "R[0][1] = 2 * (x * y + w * z);", ["param_scipy"]),
+    "quat_not_normalised": ("double w = q_in[0] / n, x = q_in[1] / n, y = q_in[2] / n, z = q_in[3] / n;",
+                            "double w = q_in[0], x = q_in[1], y = q_in[2], z = q_in[3];", ["param_scipy"]),
+    "opacity_sigmoid_sign": ("opacity[i] = 1.0 / (1.0 + exp(-logit[i]));", "opacity[i] = 1.0 / (1.0 + exp(logit[i]));",
+                             ["param_scipy"]),
+    "exact_ray_no_principal_point": ("d[0] = (rx - pp->cx) / pp->fx;", "d[0] = rx / pp->fx;", ["exact_chord"]),
+    "exact_grad_drop_plane_term": ("for (m = 0; m < 3; ++m) g[0][m] = n[m] / dn - g[1][m] - g[2][m];",
+                                   "for (m = 0; m < 3; ++m) g[0][m] = -g[1][m] - g[2][m];", ["exact_fd"]),
 }
 
 CHECKS = {
