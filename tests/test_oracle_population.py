@@ -282,8 +282,10 @@ def test_view_gradient_matches_finite_differences(orc):
     plane (centre and vertices moved together)."""
     w = scenes.workload(0)
     sc = w.scene
-    # an oblique, non-square view (a generic rotation; W != H)
+    # an oblique, non-square view (a generic rotation; W != H) with
+    # non-square pixels (f_y != f_x), so that each axis's scale is its own
     cam = scenes.make_camera((2.6, -1.3, 2.9), 112, 72, 55.0)
+    cam.fy = float(np.float32(1.25 * cam.fx))
     rng = np.random.default_rng(11)
     gimg = rng.normal(size=3 * cam.pixels)
     dmin = orc.preprocess(sc, cam)["dmin"]

@@ -48,6 +48,23 @@ MUTANTS = {
     "tetra_std_not_halved": ("(np.max(np.abs(d)) / 2.0)", "np.max(np.abs(d))"),
     "split_no_shrink": ("row[\"dist\"] = d / SPLIT_SHRINK", "row[\"dist\"] = d"),
     "prefix_inclusive": ("return dest[:-1], int(dest[-1])", "return dest[1:], int(dest[-1])"),
+    "dest_split_one_row": ("per = np.array([0, 1, 2, 2], np.int64)", "per = np.array([0, 1, 2, 1], np.int64)"),
+    # view gradient: NDC scale grows with depth, uses the axis's own focal
+    # length, and the depth is the camera-space z row
+    "ndc_scale_no_depth": ("gx = gc[:, 0] * camera.width * z / (2.0 * float(camera.fx))",
+                           "gx = gc[:, 0] * camera.width / (2.0 * float(camera.fx))"),
+    "ndc_y_uses_fx": ("gy = gc[:, 1] * camera.height * z / (2.0 * float(camera.fy))",
+                      "gy = gc[:, 1] * camera.height * z / (2.0 * float(camera.fx))"),
+    "depth_from_x_row": ("z = np.asarray(centre, np.float64) @ M[2, :3] + M[2, 3]",
+                         "z = np.asarray(centre, np.float64) @ M[0, :3] + M[0, 3]"),
+    # the densification statistic is a mean over visible views
+    "grad_sum_not_mean": ("g = f32(f32(grad_sum[i]) / f32(c)) if c > 0 else f32(0.0)", "g = f32(grad_sum[i])"),
+    # the opacity threshold is compared as a logit
+    "opacity_threshold_not_logit": ("logit_min = f32(math.log(p / (1.0 - p)))", "logit_min = f32(p)"),
+    # split children start with fresh optimiser state and their own draws
+    "split_keeps_state": ("rows = [(0, True), (1, True)]", "rows = [(0, False), (1, False)]"),
+    "split_children_share_draw": ("off = quat_rotation(row[\"quat\"]) @ (np.abs(d) * normals[i, child])",
+                                  "off = quat_rotation(row[\"quat\"]) @ (np.abs(d) * normals[i, 0])"),
 }
 
 
