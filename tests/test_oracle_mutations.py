@@ -113,6 +113,16 @@ MUTANTS = {
     "exact_ray_no_principal_point": ("d[0] = (rx - pp->cx) / pp->fx;", "d[0] = rx / pp->fx;", ["exact_chord"]),
     "exact_grad_drop_plane_term": ("for (m = 0; m < 3; ++m) g[0][m] = n[m] / dn - g[1][m] - g[2][m];",
                                    "for (m = 0; m < 3; ++m) g[0][m] = -g[1][m] - g[2][m];", ["exact_fd"]),
+    "ray_space_depth_is_z": ("pp->pc[2] = sqrt(pp->tc[0] * pp->tc[0] + pp->tc[1] * pp->tc[1] + pp->tc[2] * pp->tc[2]);",
+                             "pp->pc[2] = pp->tc[2];", ["first_order"]),
+    "sh_count_wrong": ("static int sh_count(int degree) { return (degree + 1) * (degree + 1); }",
+                       "static int sh_count(int degree) { return 3 * degree + 1; }", ["colour_dir"]),
+    "frozen_dmin_ignored": ("    if (P->dmin) pp->dmin = P->dmin[i];\n", "", ["fd_tetra"]),
+    "aa_y_move_from_x_side": ("pp->p[k][1] += pp->kf.shy[k] * (double)pp->kf.shift;",
+                              "pp->p[k][1] += pp->kf.shx[k] * (double)pp->kf.shift;", ["aa_moves"]),
+    "backward_T_after_primitive": ("c->i1 = i1; c->i2 = i2; c->s = s; c->tau = tau; c->o = o; c->T = T;",
+                                   "c->i1 = i1; c->i2 = i2; c->s = s; c->tau = tau; c->o = o; c->T = Tn;", ["fd_tetra"]),
+    "span_grad_sign": ("dL_ds = dL_do * pp->sigma * c->tau;", "dL_ds = -dL_do * pp->sigma * c->tau;", ["fd_tetra"]),
 }
 
 CHECKS = {
