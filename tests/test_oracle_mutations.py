@@ -123,6 +123,11 @@ MUTANTS = {
     "backward_T_after_primitive": ("c->i1 = i1; c->i2 = i2; c->s = s; c->tau = tau; c->o = o; c->T = T;",
                                    "c->i1 = i1; c->i2 = i2; c->s = s; c->tau = tau; c->o = o; c->T = Tn;", ["fd_tetra"]),
     "span_grad_sign": ("dL_ds = dL_do * pp->sigma * c->tau;", "dL_ds = -dL_do * pp->sigma * c->tau;", ["fd_tetra"]),
+    "octa_face_table": ("    {1, 2, 4}, {1, 2, 5}, {1, 3, 4}, {1, 3, 5}};", "    {1, 2, 4}, {1, 2, 5}, {1, 3, 4}, {0, 3, 5}};",
+                        ["chord"]),
+    "tetra_face_table": ("static const int TETRA_FACES[4][3] = {{1, 2, 3}, {0, 2, 3}, {0, 1, 3}, {0, 1, 2}};",
+                         "static const int TETRA_FACES[4][3] = {{1, 2, 3}, {0, 2, 3}, {0, 1, 3}, {0, 1, 3}};",
+                         ["chord_tetra"]),
 }
 
 CHECKS = {
@@ -133,6 +138,7 @@ CHECKS = {
     "mtia_fd": pins.test_mtia_gradient_fd,
     "first_order": pins.test_ray_space_map_is_first_order_perspective,
     "chord": lambda o: pins.test_span_centre_pixel_equals_world_chord(o, 6),
+    "chord_tetra": lambda o: pins.test_span_centre_pixel_equals_world_chord(o, 4),
     "scipy": pins.test_sh_basis_matches_scipy,
     "sh_fd": pins.test_sh_basis_derivative_fd,
     "fd_tetra": pins.test_adjoint_fd_tetrahedra,
